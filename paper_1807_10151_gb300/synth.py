@@ -1,0 +1,88 @@
+"""Seeded synthetic inputs shared by the tests, the benchmark and the oracle runs.
+
+This module holds no arithmetic of the reconstruction method: it draws random
+ellipse phantoms (sampled at pixel centres), optional smooth background
+texture, and measurement noise for a given noiseless sinogram.  The phantoms
+stand in for the head phantom of Sec. 4.1 of arXiv 1807.10151, which is not
+available; they keep its acquisition shape (see the benchmark configurations).
+
+Seed convention: configuration c, problem b -> seed 1000*c + b.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def pixel_centres(nx: int, ny: int, d: float):
+    """Centres (x_j, y_i) of an ny x nx image of pixel side d centred on 0,
+    row 0 at the top."""
+    xj = (np.arange(nx) - 0.5 * (nx - 1)) * d
+    yi = (0.5 * (ny - 1) - np.arange(ny)) * d
+    return xj, yi
+
+
+def ellipse_params(n_ellipses: int, seed: int, r_centre=0.35, axes=(0.03, 0.25)):
+    """Random ellipses in unit-square coordinates: (cx, cy, ax, ay, angle, density)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n_ellipses):
+        rad = r_centre * np.sqrt(rng.uniform())
+        phi = rng.uniform(0, 2 * np.pi)
+        out.append((rad * np.cos(phi), rad * np.sin(phi), rng.uniform(*axes), rng.uniform(*axes),
+                    rng.uniform(0, np.pi), rng.uniform(0, 1)))
+    return out
+
+
+def ellipse_phantom(N: int, n_ellipses: int, seed: int, nx: int | None = None, ny: int | None = None,
+                    d: float | None = None, dtype=np.float64) -> np.ndarray:
+    """Random-ellipse phantom on the unit square, values in [0, 1].
+
+    Later ellipses overwrite earlier ones; each pixel takes the value at its
+    centre.
+    """
+    nx = N if nx is None else nx
+    ny = N if ny is None else ny
+    d = 1.0 / max(nx, ny) if d is None else d
+    xj, yi = pixel_centres(nx, ny, d)
+    X, Y = np.meshgrid(xj, yi)
+    img = np.zeros((ny, nx))
+    for cx, cy, ax, ay, ang, rho in ellipse_params(n_ellipses, seed):
+        ca, sa = np.cos(ang), np.sin(ang)
+        u = (X - cx) * ca + (Y - cy) * sa
+        v = -(X - cx) * sa + (Y - cy) * ca
+        img[(u / ax) ** 2 + (v / ay) ** 2 <= 1.0] = rho
+    return img.astype(dtype)
+
+
+def textured_background(N: int, seed: int, sigma_px: float = 8.0, amplitude: float = 0.05,
+                        support_radius: float = 0.45) -> np.ndarray:
+    """Seeded white noise blurred by a Gaussian of sigma_px pixels (FFT
+    convolution, periodic), scaled to +-amplitude, inside a centred disk."""
+    rng = np.random.default_rng(seed)
+    w = rng.standard_normal((N, N))
+    k = np.fft.fftfreq(N)
+    g = np.exp(-2.0 * (np.pi * sigma_px) ** 2 * (k[:, None] ** 2 + k[None, :] ** 2))
+    sm = np.real(np.fft.ifft2(np.fft.fft2(w) * g))
+    sm *= amplitude / max(np.max(np.abs(sm)), 1e-30)
+    xj, yi = pixel_centres(N, N, 1.0 / N)
+    X, Y = np.meshgrid(xj, yi)
+    return np.where(X ** 2 + Y ** 2 <= support_radius ** 2, sm, 0.0)
+
+
+def gaussian_noise(clean: np.ndarray, level: float, seed: int) -> np.ndarray:
+    """b = clean + e, e ~ N(0, sigma^2), sigma = level * ||clean|| / sqrt(m)."""
+    rng = np.random.default_rng(seed)
+    sigma = level * np.linalg.norm(clean) / np.sqrt(clean.size)
+    return clean + sigma * rng.standard_normal(clean.shape)
+
+
+def poisson_log(clean: np.ndarray, I0: float, seed: int) -> np.ndarray:
+    """Photon counts ~ Poisson(I0 exp(-clean)); b = -ln(max(count, 1) / I0)."""
+    rng = np.random.default_rng(seed)
+    counts = rng.poisson(I0 * np.exp(-np.asarray(clean, dtype=np.float64)))
+    return -np.log(np.maximum(counts, 1) / I0)
+
+
+def random_field(shape, seed: int, dtype=np.float64) -> np.ndarray:
+    """Standard normal test vectors (adjoint checks, operator parity)."""
+    return np.random.default_rng(seed).standard_normal(shape).astype(dtype)
