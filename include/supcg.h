@@ -1,0 +1,190 @@
+/*
+ * supcg.h -- C ABI of libsupcg, a GB300 (sm_103a) implementation of the
+ * data-parallel hot path of Superiorized Preconditioned Conjugate Gradient
+ * (SupPCG) for 2-D parallel-beam tomography (Helou, Herman, Lin, Zibetti,
+ * arXiv 1807.10151).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Image: ny rows x nx columns, row-major, FP32 unless the geometry's
+ *    storage is SUPCG_BF16; element i*nx + j is pixel (i, j) (Sec. 3.1 puts
+ *    pixel (i, j) at component c(i-1)+j).  Row 0 is the top row.  Pixel (i, j)
+ *    has centre x_j = (j - (nx-1)/2) d, y_i = ((ny-1)/2 - i) d, d = pixel size.
+ *  - Sinogram: n_views rows x n_bins columns, row-major.  Ray (v, u) is the
+ *    line x cos(theta_v) + y sin(theta_v) = s_u, s_u = (u - (U-1)/2) ds + off
+ *    (Sec. 2 data model R x = b + e; Sec. 4.1 acquisition shape).
+ *  - R_{(v,u),(i,j)} is the length of ray (v, u) inside the closed pixel
+ *    square (a line on an edge shared by two pixels gives each half).
+ *  - "d_" pointers are device pointers owned by the caller; the library never
+ *    frees them.  "h_" pointers are host pointers.  Batched arrays are `batch`
+ *    images (or sinograms) stored back to back.
+ *  - Work is enqueued on `stream` (a cudaStream_t, NULL = legacy default
+ *    stream) and is asynchronous unless the entry point says otherwise.
+ *  - Every entry point returns SUPCG_OK (0) or a negative supcg_status.  No
+ *    entry point aborts the process or throws.  After an error the outputs
+ *    are unspecified; the geometry stays valid.
+ *  - Scratch memory is owned by the geometry object: allocated lazily on
+ *    first use (cudaMalloc) and freed by supcg_destroy_geometry.  A geometry
+ *    must not be used from two host threads at once.
+ */
+#ifndef SUPCG_H
+#define SUPCG_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct supcg_geometry_s *supcg_geometry;
+
+typedef enum {
+    SUPCG_OK = 0,
+    SUPCG_ERR_ARG = -1,       /* invalid argument (null pointer, size, parameter range) */
+    SUPCG_ERR_CUDA = -2,      /* a CUDA runtime/driver call failed                        */
+    SUPCG_ERR_NOMEM = -3,     /* device or host allocation failed                         */
+    SUPCG_ERR_BREAKDOWN = -4, /* CG breakdown: p^T h <= 0 or a non-finite scalar          */
+    SUPCG_ERR_BACKTRACK = -5, /* S_TV backtracking exceeded max_trials (Algorithm 1)      */
+    SUPCG_ERR_TIMEOUT = -6,   /* a bounded device-side wait expired                       */
+    SUPCG_ERR_PRECOND = -7,   /* preconditioner not positive definite (rho <= 1/2)        */
+    SUPCG_ERR_UNSUPPORTED = -8/* geometry outside the kernels' supported range             */
+} supcg_status;
+
+typedef enum { SUPCG_F32 = 0, SUPCG_BF16 = 1 } supcg_storage;
+
+/* Create a 2-D parallel-beam geometry (Sec. 2, Sec. 4.1).
+ *   nx, ny          image size in pixels (1 .. 16384 each)
+ *   pixel_size      d > 0 (the unit-square convention is d = 1/max(nx, ny))
+ *   n_views         V >= 1
+ *   angles          host array of V angles in radians, or NULL for v*pi/V
+ *                   (V equally spaced angles in [0, pi), as in Sec. 4.1)
+ *   n_bins          U >= 1
+ *   bin_spacing     ds; <= 0 selects ds = d (ray spacing = pixel size, Sec. 4.1)
+ *   det_center_offset  off, added to every s_u
+ *   storage         SUPCG_F32 or SUPCG_BF16: element type of the images and
+ *                   sinograms passed to supcg_project / supcg_backproject
+ * The host copies everything it needs; `angles` may be freed afterwards.
+ * cos/sin are evaluated in FP64 on the host and are exact at multiples of pi/2.
+ * Errors: SUPCG_ERR_ARG, SUPCG_ERR_UNSUPPORTED (bins much coarser than pixels),
+ * SUPCG_ERR_CUDA, SUPCG_ERR_NOMEM. */
+int supcg_create_geometry(int nx, int ny, double pixel_size, int n_views, const double *angles,
+                          int n_bins, double bin_spacing, double det_center_offset,
+                          int storage, supcg_geometry *out);
+
+/* Free the geometry and all scratch it owns (synchronises the device first). */
+int supcg_destroy_geometry(supcg_geometry g);
+
+/* Forward projection y = R x for `batch` images (the product R x of Sec. 2).
+ *   d_x  [batch][ny][nx]   d_y [batch][V][U]   (storage type of the geometry)
+ * Exact line-pixel intersection lengths, FP32 accumulation. */
+int supcg_project(supcg_geometry g, const void *d_x, void *d_y, int batch, void *stream);
+
+/* Backprojection x = R^T y (the transpose in the normal equations, Eq. (2.2)).
+ * Uses bit-identical weights to supcg_project: it is the exact transpose of
+ * the matrix applied there.  d_y [batch][V][U] -> d_x [batch][ny][nx]. */
+int supcg_backproject(supcg_geometry g, const void *d_y, void *d_x, int batch, void *stream);
+
+/* Preconditioner z = M g, M = F^-1 D F, D = h(w) of Eq. (3.2) with
+ * h(w) = (|w| + mu)(rho + (1 - rho) cos w), w the radial frequency of the
+ * ny x nx DFT clamped to pi.  d_g, d_z FP32 [batch][ny][nx]; may alias.
+ * Errors: SUPCG_ERR_PRECOND when rho <= 1/2 or mu < 0 (M not SPD). */
+int supcg_precondition(supcg_geometry g, double mu, double rho, const float *d_g, float *d_z,
+                       int batch, void *stream);
+
+/* Total variation and its nonascending vector (Sec. 3.1) for one image:
+ * d_tbar[p] = -dTV/dy_p where that partial derivative exists, else 0.
+ * h_out[0] = TV(y), h_out[1] = ||tbar||^2 (FP64 reductions).  Synchronous. */
+int supcg_tv_tbar(supcg_geometry g, const float *d_y, float *d_tbar, double *h_out, void *stream);
+
+/* S_TV(x, l, a, gamma, K), Algorithm 1, in place: d_x <- x + s (one image).
+ *   h_ell        in: l, out: l after the call
+ *   h_trials     nullable host array of K ints: trials of each nonascending step
+ *   max_trials   bound on each `repeat` loop (the paper gives none);
+ *                exceeding it returns SUPCG_ERR_BACKTRACK.
+ * Synchronous (reads the new l back). */
+int supcg_superiorize(supcg_geometry g, float *d_x, double a, double gamma, int K,
+                      long long max_trials, long long *h_ell, int *h_trials, void *stream);
+
+/* Parameters of supcg_solve (Algorithm 3 inputs plus the preconditioner of Eq. (3.2)). */
+typedef struct {
+    int K;                 /* nonascending steps per S_TV call (Algorithm 1)             */
+    double a;              /* step-length diminishing factor, 0 < a < 1                   */
+    double gamma;          /* starting step length, >= 0 (0 with perturb=0: plain PCG)    */
+    double mu, rho;        /* preconditioner parameters of Eq. (3.2); rho > 1/2           */
+    double eps;            /* stop when f(x_{k-1/2}) <= eps; eps < 0: never (fixed budget) */
+    int max_iter;          /* bound on executions of the while body of Algorithm 3        */
+    long long max_trials;  /* bound on each backtracking loop of Algorithm 1 (e.g. 10000)  */
+    int perturb;           /* 1: SupPCG; 0: skip S_TV (plain PCG)                         */
+    int precondition;      /* 1: M of Eq. (3.2); 0: M = I (SupCG / CG)                     */
+    int graph;             /* 1: replay each iteration as a captured CUDA graph            */
+} supcg_params;
+
+/* Outcome of a solve. */
+typedef struct {
+    int iters;          /* executions of the while body (steps 11-14)                    */
+    int k;              /* the k returned by Algorithm 3                                 */
+    long long ell;      /* l_k after the last body                                       */
+    double f_last;      /* f(x_{k-1/2}) = ||R x_{k-1/2} - b||^2 of the returned image     */
+    double f0;          /* f(x_0)                                                        */
+    double tv_last;     /* TV(x_{k-1/2})  (0 unless perturb = 1 and iters > 0)            */
+    int status;         /* SUPCG_OK or the error that stopped the iteration              */
+} supcg_report;
+
+/* Number of doubles per iteration written to the optional log of supcg_solve:
+ * f(x_{k+1/2}), TV(x_k), TV(x_{k+1/2}), l_{k+1}, alpha, beta, ||s_k||^2, trials. */
+#define SUPCG_LOG_STRIDE 8
+
+/* SupPCG(x0, a, gamma, K, eps), Algorithm 3 (steps 1-9 then the while loop;
+ * U_PCG of Algorithm 2; S_TV of Algorithm 1), for one problem.
+ *   d_b    FP32 [V][U] measured data b
+ *   d_x    FP32 [ny][nx]; in: x_0, out: x_{k-1/2} (the image Algorithm 3 returns)
+ *   d_log  nullable FP64 [max_iter][SUPCG_LOG_STRIDE] per-iteration metrics
+ * CG scalars (alpha, beta, inner products, f) are reduced in FP64.
+ * Synchronous: returns after the report has been read back. */
+int supcg_solve(supcg_geometry g, const float *d_b, float *d_x, const supcg_params *p,
+                supcg_report *rep, double *d_log, void *stream);
+
+/* supcg_solve with HOST buffers: copies h_b and h_x (x_0) to the device,
+ * solves, and copies x_{k-1/2} back into h_x.  Page-locked host memory gives
+ * the fastest copies.  Synchronous. */
+int supcg_solve_host(supcg_geometry g, const float *h_b, float *h_x, const supcg_params *p,
+                     supcg_report *rep, void *stream);
+
+/* Solve `count` independent problems of possibly different geometries in one
+ * set of batched launches: every kernel of an iteration processes all
+ * problems at once, and the iteration is replayed as one CUDA graph.
+ *   gs[c], d_b[c], d_x[c]  geometry, data and image (in x_0, out x_{k-1/2}) of problem c
+ *   reps   host array of `count` reports
+ * All problems share the parameters p.  The scratch lives in gs[0].
+ * Synchronous. */
+int supcg_solve_batched(const supcg_geometry *gs, const float *const *d_b, float *const *d_x,
+                        int count, const supcg_params *p, supcg_report *reps, void *stream);
+
+/* Kernel kinds of supcg_solve_profiled. */
+typedef enum {
+    SUPCG_KIND_FORWARD = 0,  /* forward projector (R x with residual, R p with ||R p||^2)   */
+    SUPCG_KIND_BACKWARD = 1, /* backprojector (R^T r, R^T q)                               */
+    SUPCG_KIND_FFT = 2,      /* preconditioner passes                                      */
+    SUPCG_KIND_STV = 3,      /* S_TV (Algorithm 1)                                         */
+    SUPCG_KIND_VECTOR = 4,   /* axpys, inner products, transposes, staging, bookkeeping    */
+    SUPCG_KIND_COUNT = 5
+} supcg_kernel_kind;
+
+/* supcg_solve without graph replay and with a CUDA event pair around every
+ * kernel launch (the same kernels and launch shapes as supcg_solve).
+ *   h_ms        host [SUPCG_KIND_COUNT]: total device milliseconds per kind
+ *   h_launches  host [SUPCG_KIND_COUNT]: launches per kind
+ * Synchronous.  The events perturb the schedule slightly; use supcg_solve for
+ * throughput and this call for the per-kernel breakdown. */
+int supcg_solve_profiled(supcg_geometry g, const float *d_b, float *d_x, const supcg_params *p,
+                         supcg_report *rep, double *h_ms, long long *h_launches, void *stream);
+
+/* Number of kernels the library has enqueued in this process so far (a CUDA
+ * graph replay counts every kernel node it launches). */
+long long supcg_kernel_launches(void);
+
+/* Human-readable name of a status code (static string). */
+const char *supcg_status_string(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SUPCG_H */

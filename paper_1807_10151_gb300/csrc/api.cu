@@ -1,0 +1,857 @@
+// C ABI of libsupcg: geometry objects, workspaces (batched problem
+// descriptors and scratch), and the host-side schedule of SupPCG
+// (Algorithm 3) as a fixed sequence of device launches per iteration,
+// optionally replayed as one CUDA graph.
+#include <math.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <mutex>
+#include <vector>
+
+#include "internal.cuh"
+
+using namespace supcg;
+
+namespace supcg {
+
+int cuda_fail(cudaError_t e, const char *what, const char *file, int line)
+{
+    if (getenv("SUPCG_DEBUG")) fprintf(stderr, "supcg: %s failed at %s:%d: %s\n", what, file, line, cudaGetErrorString(e));
+    (void)cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? SUPCG_ERR_NOMEM : SUPCG_ERR_CUDA;
+}
+
+static int round_up(int v, int m) { return (v + m - 1) / m * m; }
+
+// ------------------------------------------------------------------ TMA map encoding
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn()
+{
+    static EncodeTiledFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+    });
+    return fn;
+}
+
+// 2-D FP32 map over [outer][pitch] with logical extent inner x outer, box BW x rows.
+static int encode_map(CUtensorMap *m, float *base, int inner, int outer, int pitch, int BW, int rows)
+{
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return SUPCG_ERR_CUDA;
+    cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)outer};
+    cuuint64_t strides[1] = {(cuuint64_t)pitch * 4};
+    cuuint32_t box[2] = {(cuuint32_t)BW, (cuuint32_t)rows};
+    cuuint32_t es[2] = {1, 1};
+    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, es,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? SUPCG_OK : SUPCG_ERR_CUDA;
+}
+
+// ------------------------------------------------------------------ FFT plan
+static int fft_factor(int n, int *rad)
+{
+    int k = 0;
+    while (n % 4 == 0 && k < kMaxStages) { rad[k++] = 4; n /= 4; }
+    while (n % 2 == 0 && k < kMaxStages) { rad[k++] = 2; n /= 2; }
+    for (int p = 3; n > 1 && k < kMaxStages; p += 2)
+        while (n % p == 0 && k < kMaxStages) { rad[k++] = p; n /= p; }
+    return n == 1 ? k : -1;
+}
+
+} // namespace supcg
+
+// ------------------------------------------------------------------ objects
+enum { KT_FWD, KT_BWD, KT_VEC, KT_TR, KT_ROWS, KT_COLS, KT_SINO, KT_STV, KT_TV, KT_COUNT };
+
+struct Workspace {
+    int count = 0;
+    std::vector<supcg_geometry> geoms;
+    std::vector<Prob> hp;
+    Prob *dp = nullptr;
+    int *dprefix = nullptr;     // KT_COUNT x (count + 1)
+    int blocks[KT_COUNT] = {};
+    int smem_rows = 0, smem_cols = 0;
+    std::vector<void *> allocs;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraphExec_t body_exec = nullptr;
+    double key[6] = {};         // parameters the captured body depends on
+    int key_i[4] = {};
+    int *trials_dev = nullptr;
+    int trials_cap = 0;
+    long long body_nodes = 0;
+
+    Launch L(int kt, cudaStream_t st) const
+    {
+        Launch l;
+        l.probs = dp;
+        l.count = count;
+        l.prefix = dprefix + kt * (count + 1);
+        l.blocks = blocks[kt];
+        l.st = st;
+        return l;
+    }
+    ~Workspace()
+    {
+        if (body_exec) cudaGraphExecDestroy(body_exec);
+        if (cap_stream) cudaStreamDestroy(cap_stream);
+        for (void *p : allocs) cudaFree(p);
+        if (dp) cudaFree(dp);
+        if (dprefix) cudaFree(dprefix);
+        if (trials_dev) cudaFree(trials_dev);
+    }
+};
+
+struct supcg_geometry_s {
+    int nx, ny, V, U, storage;
+    double d, ds, off;
+    std::vector<double> theta;
+    std::vector<ViewP> views;
+    std::vector<int> vlist;
+    int nA, nB;
+    int BU, BW, ntu;
+    int nxp, nyp, Up;
+    float cx, cy, uc;
+    FFTPlan fx, fy;
+    ViewP *dviews = nullptr;
+    int *dvlist = nullptr;
+    float2 *dtwx = nullptr, *dtwy = nullptr;
+    Workspace *ws_ops = nullptr;    // standalone operators, `ops_batch` images
+    int ops_batch = 0;
+    Workspace *ws_solve = nullptr;  // single-problem solve
+    Workspace *ws_batch = nullptr;  // batched solve owned by this (first) geometry
+    std::vector<supcg_geometry> batch_key;
+};
+
+static void free_ws(Workspace *&w)
+{
+    delete w;
+    w = nullptr;
+}
+
+// ------------------------------------------------------------------ geometry
+static void exact_cos_sin(double th, double *c, double *s)
+{
+    const double q = th / (0.5 * M_PI);
+    const double r = nearbyint(q);
+    if (fabs(q - r) < 1e-12) {
+        const long k = (((long)r) % 4 + 4) % 4;
+        const double cc[4] = {1.0, 0.0, -1.0, 0.0}, ss[4] = {0.0, 1.0, 0.0, -1.0};
+        *c = cc[k];
+        *s = ss[k];
+    } else {
+        *c = cos(th);
+        *s = sin(th);
+    }
+}
+
+static int upload_twiddles(int n, float2 **out)
+{
+    std::vector<float2> tw(n);
+    for (int k = 0; k < n; ++k) {
+        const double a = -2.0 * M_PI * (double)k / (double)n;
+        tw[k] = make_float2((float)cos(a), (float)sin(a));
+    }
+    SUPCG_CUDA_TRY(cudaMalloc(out, sizeof(float2) * n));
+    SUPCG_CUDA_TRY(cudaMemcpy(*out, tw.data(), sizeof(float2) * n, cudaMemcpyHostToDevice));
+    return SUPCG_OK;
+}
+
+extern "C" int supcg_create_geometry(int nx, int ny, double pixel_size, int n_views, const double *angles, int n_bins,
+                                     double bin_spacing, double det_center_offset, int storage, supcg_geometry *out)
+{
+    if (!out) return SUPCG_ERR_ARG;
+    *out = nullptr;
+    if (nx < 1 || ny < 1 || nx > 16384 || ny > 16384 || n_views < 1 || n_bins < 1 || n_bins > (1 << 24) ||
+        n_views > (1 << 20) || !(pixel_size > 0.0) || !isfinite(pixel_size) || !isfinite(det_center_offset) ||
+        (storage != SUPCG_F32 && storage != SUPCG_BF16))
+        return SUPCG_ERR_ARG;
+    auto *g = new (std::nothrow) supcg_geometry_s();
+    if (!g) return SUPCG_ERR_NOMEM;
+    g->nx = nx; g->ny = ny; g->V = n_views; g->U = n_bins; g->storage = storage;
+    g->d = pixel_size;
+    g->ds = (bin_spacing > 0.0) ? bin_spacing : pixel_size;
+    g->off = det_center_offset;
+    g->theta.resize(n_views);
+    for (int v = 0; v < n_views; ++v) {
+        g->theta[v] = angles ? angles[v] : (double)v * M_PI / (double)n_views;
+        if (!isfinite(g->theta[v])) { delete g; return SUPCG_ERR_ARG; }
+    }
+    const double r = g->d / g->ds;
+    const double cx = 0.5 * (nx - 1), cy = 0.5 * (ny - 1);
+    g->cx = (float)cx; g->cy = (float)cy;
+    g->uc = (float)(0.5 * (n_bins - 1) - g->off / g->ds);
+    g->views.resize(n_views);
+    std::vector<int> A, B;
+    double maxE = 0.0, span_bwd = 0.0;
+    for (int v = 0; v < n_views; ++v) {
+        double c, s;
+        exact_cos_sin(g->theta[v], &c, &s);
+        const double ac = fabs(c), as = fabs(s);
+        const double a = std::max(ac, as), b = std::min(ac, as);
+        ViewP vp = {};
+        vp.cu = (float)(c * r);
+        vp.su = (float)(s * r);
+        vp.E = (float)(r * (a + b) / 2.0);
+        vp.S = (b > 0.0) ? (float)(g->ds / (a * b)) : 0.0f;
+        vp.P = (float)(g->d / a);
+        const bool classB = as > ac;
+        if (!classB) {
+            const double cu = c * r, su = s * r;
+            vp.a_tau = (float)(1.0 / cu);
+            vp.b_o = (float)(su / cu);
+            vp.g0 = (float)(cx - (su / cu) * cy);
+            A.push_back(v);
+        } else {
+            const double cu = c * r, su = s * r;
+            vp.a_tau = (float)(-1.0 / su);
+            vp.b_o = (float)(cu / su);
+            vp.g0 = (float)(cy - (cu / su) * cx);
+            B.push_back(v);
+        }
+        vp.flags = (b == 0.0 ? kViewAxis : 0) | (classB ? kViewClassB : 0);
+        g->views[v] = vp;
+        maxE = std::max(maxE, (double)vp.E);
+        span_bwd = std::max(span_bwd, (kBwdTileJ - 1) * fabs((double)vp.cu) + (kBwdTileI - 1) * fabs((double)vp.su));
+    }
+    // the three bins nearest a pixel's centre must cover its footprint, and a
+    // backprojector tile must fit its shared-memory window
+    if (maxE > 1.45 || span_bwd + 9.0 > kBwdWin) { delete g; return SUPCG_ERR_UNSUPPORTED; }
+    g->nA = (int)A.size();
+    g->nB = (int)B.size();
+    g->vlist = A;
+    g->vlist.insert(g->vlist.end(), B.begin(), B.end());
+    // forward tiling: the widest box any view needs must fit 256 columns
+    g->BU = 0;
+    for (int bu : {128, 96, 64, 32}) {
+        double span = 0.0;
+        for (const ViewP &vp : g->views)
+            span = std::max(span, fabs((double)vp.a_tau) * (bu - 1) + fabs((double)vp.b_o) * (kRowsPerChunk - 1));
+        const int bw = round_up((int)ceil(span + 9.0), 4);
+        if (bw <= 256) { g->BU = bu; g->BW = bw; break; }
+    }
+    if (!g->BU) { delete g; return SUPCG_ERR_UNSUPPORTED; }
+    g->ntu = (n_bins + g->BU - 1) / g->BU;
+    g->nxp = round_up(nx, 4);
+    g->nyp = round_up(ny, 4);
+    g->Up = round_up(n_bins, 4);
+    // FFT plans
+    g->fx.n = nx;
+    g->fy.n = ny;
+    g->fx.nst = fft_factor(nx, g->fx.radix);
+    g->fy.nst = fft_factor(ny, g->fy.radix);
+    if (g->fx.nst < 0 || g->fy.nst < 0) { delete g; return SUPCG_ERR_UNSUPPORTED; }
+    int rc;
+    if ((rc = upload_twiddles(nx, &g->dtwx)) || (rc = upload_twiddles(ny, &g->dtwy))) {
+        supcg_destroy_geometry(g);
+        return rc;
+    }
+    g->fx.tw = g->dtwx;
+    g->fy.tw = g->dtwy;
+    if (cudaMalloc(&g->dviews, sizeof(ViewP) * n_views) != cudaSuccess ||
+        cudaMalloc(&g->dvlist, sizeof(int) * n_views) != cudaSuccess) {
+        supcg_destroy_geometry(g);
+        return SUPCG_ERR_NOMEM;
+    }
+    if (cudaMemcpy(g->dviews, g->views.data(), sizeof(ViewP) * n_views, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(g->dvlist, g->vlist.data(), sizeof(int) * n_views, cudaMemcpyHostToDevice) != cudaSuccess) {
+        supcg_destroy_geometry(g);
+        return SUPCG_ERR_CUDA;
+    }
+    *out = g;
+    return SUPCG_OK;
+}
+
+extern "C" int supcg_destroy_geometry(supcg_geometry g)
+{
+    if (!g) return SUPCG_ERR_ARG;
+    cudaDeviceSynchronize();
+    free_ws(g->ws_ops);
+    free_ws(g->ws_solve);
+    free_ws(g->ws_batch);
+    if (g->dviews) cudaFree(g->dviews);
+    if (g->dvlist) cudaFree(g->dvlist);
+    if (g->dtwx) cudaFree(g->dtwx);
+    if (g->dtwy) cudaFree(g->dtwy);
+    delete g;
+    return SUPCG_OK;
+}
+
+// ------------------------------------------------------------------ workspace
+static int ws_create(const std::vector<supcg_geometry> &gs, Workspace **out)
+{
+    auto *w = new (std::nothrow) Workspace();
+    if (!w) return SUPCG_ERR_NOMEM;
+    w->count = (int)gs.size();
+    w->geoms = gs;
+    w->hp.resize(w->count);
+    int dev = 0, nsm = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    int rc = stv_max_blocks_per_sm(&per_sm);
+    if (rc) { delete w; return rc; }
+    const int stv_cap = std::max(1, nsm * per_sm);
+    if (w->count > stv_cap) { delete w; return SUPCG_ERR_UNSUPPORTED; }
+
+    // blocks per problem for every kernel type
+    std::vector<std::vector<int>> nb(KT_COUNT, std::vector<int>(w->count));
+    long long stv_want = 0;
+    std::vector<long long> npx(w->count);
+    for (int c = 0; c < w->count; ++c) {
+        const supcg_geometry g = gs[c];
+        nb[KT_FWD][c] = g->V * g->ntu;
+        nb[KT_BWD][c] = ((g->ny + kBwdTileI - 1) / kBwdTileI) * ((g->nx + kBwdTileJ - 1) / kBwdTileJ);
+        nb[KT_VEC][c] = (int)(((long long)g->ny * g->nxp + 1023) / 1024);
+        nb[KT_TR][c] = ((g->ny + 31) / 32) * ((g->nx + 31) / 32);
+        const int rpb = std::max(1, std::min(16, 4096 / g->nx));
+        const int cw = std::max(1, std::min(16, 8192 / g->ny));
+        nb[KT_ROWS][c] = (g->ny + rpb - 1) / rpb;
+        nb[KT_COLS][c] = (g->nx + cw - 1) / cw;
+        w->smem_rows = std::max(w->smem_rows, 2 * rpb * g->nx * 8);
+        w->smem_cols = std::max(w->smem_cols, 2 * cw * g->ny * 8);
+        nb[KT_SINO][c] = (int)(((long long)g->V * g->Up + 1023) / 1024);
+        npx[c] = (long long)g->nx * g->ny;
+        nb[KT_STV][c] = (int)std::max(1LL, std::min<long long>((npx[c] + 1023) / 1024, stv_cap));
+        stv_want += nb[KT_STV][c];
+        nb[KT_TV][c] = (int)std::max(1LL, std::min<long long>((npx[c] + 1023) / 1024, 4096));
+        w->hp[c].fft_rpb = rpb;
+        w->hp[c].fft_cw = cw;
+    }
+    if (w->smem_rows > 160 * 1024 || w->smem_cols > 160 * 1024) { delete w; return SUPCG_ERR_UNSUPPORTED; }
+    // co-residency of the cooperative S_TV launch: scale down to the device capacity
+    if (stv_want > stv_cap) {
+        long long tot = 0;
+        for (int c = 0; c < w->count; ++c) {
+            nb[KT_STV][c] = (int)std::max(1LL, (long long)nb[KT_STV][c] * (stv_cap - w->count) / stv_want);
+            tot += nb[KT_STV][c];
+        }
+        if (tot > stv_cap) { delete w; return SUPCG_ERR_UNSUPPORTED; }
+    }
+    std::vector<int> hprefix(KT_COUNT * (w->count + 1));
+    for (int kt = 0; kt < KT_COUNT; ++kt) {
+        int acc = 0;
+        for (int c = 0; c < w->count; ++c) {
+            hprefix[kt * (w->count + 1) + c] = acc;
+            acc += nb[kt][c];
+        }
+        hprefix[kt * (w->count + 1) + w->count] = acc;
+        w->blocks[kt] = acc;
+    }
+    if (cudaMalloc(&w->dprefix, sizeof(int) * hprefix.size()) != cudaSuccess ||
+        cudaMemcpy(w->dprefix, hprefix.data(), sizeof(int) * hprefix.size(), cudaMemcpyHostToDevice) != cudaSuccess) {
+        delete w;
+        return SUPCG_ERR_NOMEM;
+    }
+
+    // buffers: one allocation per problem, 256-byte aligned pieces
+    for (int c = 0; c < w->count; ++c) {
+        const supcg_geometry g = gs[c];
+        Prob &P = w->hp[c];
+        const size_t img = (size_t)g->ny * g->nxp, imgT = (size_t)g->nx * g->nyp, sino = (size_t)g->V * g->Up;
+        int maxblk = 0;
+        for (int kt = 0; kt < KT_COUNT; ++kt) maxblk = std::max(maxblk, nb[kt][c]);
+        const size_t npart = std::max<size_t>(8 * (size_t)nb[KT_STV][c], 2 * (size_t)maxblk) + 64;
+        auto al = [](size_t b) { return (b + 255) / 256 * 256; };
+        const size_t sizes[] = {img * 4, imgT * 4, img * 4, imgT * 4, img * 4, img * 4, img * 4, img * 4,
+                                sino * 4, sino * 4, sino * 4, (size_t)g->ny * g->nx * 8, sizeof(Scal),
+                                npart * 8, 16 * 4, 4 * 4};
+        size_t total = 0;
+        for (size_t s : sizes) total += al(s);
+        char *base = nullptr;
+        if (cudaMalloc(&base, total) != cudaSuccess) { delete w; return SUPCG_ERR_NOMEM; }
+        w->allocs.push_back(base);
+        if (cudaMemset(base, 0, total) != cudaSuccess) { delete w; return SUPCG_ERR_CUDA; }
+        char *ptrs[16];
+        size_t off = 0;
+        for (int k = 0; k < 16; ++k) { ptrs[k] = base + off; off += al(sizes[k]); }
+        P.x = (float *)ptrs[0]; P.xT = (float *)ptrs[1]; P.p = (float *)ptrs[2]; P.pT = (float *)ptrs[3];
+        P.g = (float *)ptrs[4]; P.z = (float *)ptrs[5]; P.h = (float *)ptrs[6]; P.tbar = (float *)ptrs[7];
+        P.r = (float *)ptrs[8]; P.q = (float *)ptrs[9]; P.bpad = (float *)ptrs[10];
+        P.C = (float2 *)ptrs[11]; P.sc = (Scal *)ptrs[12]; P.partial = (double *)ptrs[13];
+        P.counter = (unsigned *)ptrs[14]; P.bar = (unsigned *)ptrs[15];
+        P.nx = g->nx; P.ny = g->ny; P.V = g->V; P.U = g->U;
+        P.nxp = g->nxp; P.nyp = g->nyp; P.Up = g->Up;
+        P.BU = g->BU; P.BW = g->BW; P.ntu = g->ntu; P.nA = g->nA; P.nB = g->nB;
+        P.cx = g->cx; P.cy = g->cy; P.uc = g->uc;
+        P.views = g->dviews; P.vlist = g->dvlist;
+        P.fx = g->fx; P.fy = g->fy;
+        P.storage = g->storage;
+        P.stv_blocks = nb[KT_STV][c];
+        P.mu = 1e-5f; P.rho = 0.8f; P.precond = 1;
+        int e = 0;
+        e |= encode_map(&P.tm[0], P.x, g->nx, g->ny, g->nxp, g->BW, kRowsPerChunk);
+        e |= encode_map(&P.tm[1], P.xT, g->ny, g->nx, g->nyp, g->BW, kRowsPerChunk);
+        e |= encode_map(&P.tm[2], P.p, g->nx, g->ny, g->nxp, g->BW, kRowsPerChunk);
+        e |= encode_map(&P.tm[3], P.pT, g->ny, g->nx, g->nyp, g->BW, kRowsPerChunk);
+        if (e) { delete w; return SUPCG_ERR_CUDA; }
+    }
+    if (cudaMalloc(&w->dp, sizeof(Prob) * w->count) != cudaSuccess) { delete w; return SUPCG_ERR_NOMEM; }
+    if (cudaStreamCreateWithFlags(&w->cap_stream, cudaStreamNonBlocking) != cudaSuccess) { delete w; return SUPCG_ERR_CUDA; }
+    *out = w;
+    return SUPCG_OK;
+}
+
+static int ws_upload(Workspace *w, cudaStream_t st)
+{
+    // synchronous copy from pageable memory: safe to modify hp afterwards
+    SUPCG_CUDA_TRY(cudaStreamSynchronize(st));
+    SUPCG_CUDA_TRY(cudaMemcpy(w->dp, w->hp.data(), sizeof(Prob) * w->count, cudaMemcpyHostToDevice));
+    return SUPCG_OK;
+}
+
+static int ops_ws(supcg_geometry g, int batch, Workspace **out)
+{
+    if (!g->ws_ops || g->ops_batch != batch) {
+        free_ws(g->ws_ops);
+        std::vector<supcg_geometry> gs(batch, g);
+        int rc = ws_create(gs, &g->ws_ops);
+        if (rc) return rc;
+        g->ops_batch = batch;
+    }
+    *out = g->ws_ops;
+    return SUPCG_OK;
+}
+
+static size_t elem_size(int storage) { return storage == SUPCG_BF16 ? 2 : 4; }
+
+// ------------------------------------------------------------------ operators
+extern "C" int supcg_project(supcg_geometry g, const void *d_x, void *d_y, int batch, void *stream)
+{
+    if (!g || !d_x || !d_y || batch < 1) return SUPCG_ERR_ARG;
+    Workspace *w;
+    int rc = ops_ws(g, batch, &w);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t es = elem_size(g->storage);
+    for (int b = 0; b < batch; ++b) {
+        w->hp[b].in_user = (const char *)d_x + (size_t)b * g->nx * g->ny * es;
+        w->hp[b].out_user = (char *)d_y + (size_t)b * g->V * g->U * es;
+    }
+    if ((rc = ws_upload(w, st))) return rc;
+    if ((rc = launch_stage_in(w->L(KT_TR, st), 0))) return rc;
+    return launch_forward(w->L(KT_FWD, st), 0, FWD_PLAIN);
+}
+
+extern "C" int supcg_backproject(supcg_geometry g, const void *d_y, void *d_x, int batch, void *stream)
+{
+    if (!g || !d_x || !d_y || batch < 1) return SUPCG_ERR_ARG;
+    Workspace *w;
+    int rc = ops_ws(g, batch, &w);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t es = elem_size(g->storage);
+    for (int b = 0; b < batch; ++b) {
+        w->hp[b].in_user = (const char *)d_y + (size_t)b * g->V * g->U * es;
+        w->hp[b].out_user = (char *)d_x + (size_t)b * g->nx * g->ny * es;
+    }
+    if ((rc = ws_upload(w, st))) return rc;
+    if ((rc = launch_stage_sino(w->L(KT_SINO, st), 0))) return rc;
+    if ((rc = launch_backward(w->L(KT_BWD, st), BWD_PLAIN))) return rc;
+    return launch_store_out(w->L(KT_VEC, st), 1);
+}
+
+static int check_precond(double mu, double rho)
+{
+    return (!(rho > 0.5) || !(rho <= 1.0) || !(mu >= 0.0) || !isfinite(mu)) ? SUPCG_ERR_PRECOND : SUPCG_OK;
+}
+
+static int enqueue_precond(Workspace *w, cudaStream_t st, int standalone)
+{
+    int rc;
+    if ((rc = launch_fft_rows(w->L(KT_ROWS, st), 0, standalone, w->smem_rows))) return rc;
+    if ((rc = launch_fft_cols(w->L(KT_COLS, st), standalone, w->smem_cols))) return rc;
+    return launch_fft_rows(w->L(KT_ROWS, st), 1, standalone, w->smem_rows);
+}
+
+extern "C" int supcg_precondition(supcg_geometry g, double mu, double rho, const float *d_g, float *d_z, int batch,
+                                  void *stream)
+{
+    if (!g || !d_g || !d_z || batch < 1) return SUPCG_ERR_ARG;
+    int rc = check_precond(mu, rho);
+    if (rc) return rc;
+    Workspace *w;
+    if ((rc = ops_ws(g, batch, &w))) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    for (int b = 0; b < batch; ++b) {
+        Prob &P = w->hp[b];
+        P.in_user = d_g + (size_t)b * g->nx * g->ny;
+        P.out_user = d_z + (size_t)b * g->nx * g->ny;
+        P.mu = (float)mu;
+        P.rho = (float)rho;
+        P.storage = SUPCG_F32;
+    }
+    rc = ws_upload(w, st);
+    for (int b = 0; b < batch; ++b) w->hp[b].storage = g->storage;
+    if (rc) return rc;
+    if ((rc = launch_stage_in(w->L(KT_TR, st), 1))) return rc;
+    if ((rc = enqueue_precond(w, st, 1))) return rc;
+    return launch_store_out(w->L(KT_VEC, st), 2);
+}
+
+static int read_scal(const Prob &P, Scal *h, cudaStream_t st)
+{
+    SUPCG_CUDA_TRY(cudaMemcpyAsync(h, P.sc, sizeof(Scal), cudaMemcpyDeviceToHost, st));
+    SUPCG_CUDA_TRY(cudaStreamSynchronize(st));
+    return SUPCG_OK;
+}
+
+extern "C" int supcg_tv_tbar(supcg_geometry g, const float *d_y, float *d_tbar, double *h_out, void *stream)
+{
+    if (!g || !d_y || !d_tbar || !h_out) return SUPCG_ERR_ARG;
+    Workspace *w;
+    int rc = ops_ws(g, 1, &w);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    Prob &P = w->hp[0];
+    P.in_user = d_y;
+    P.out_user = d_tbar;
+    P.storage = SUPCG_F32;
+    rc = ws_upload(w, st);
+    P.storage = g->storage;
+    if (rc) return rc;
+    if ((rc = launch_stage_in(w->L(KT_TR, st), 0))) return rc;
+    if ((rc = launch_tv_tbar(w->L(KT_TV, st)))) return rc;
+    if ((rc = launch_store_out(w->L(KT_VEC, st), 3))) return rc;
+    Scal s;
+    if ((rc = read_scal(P, &s, st))) return rc;
+    h_out[0] = s.tv_k;
+    h_out[1] = s.snorm2;
+    return SUPCG_OK;
+}
+
+static int check_stv(double a, double gamma, int K, long long max_trials)
+{
+    if (K < 0 || !(a > 0.0) || !(a <= 1.0) || !(gamma >= 0.0) || !isfinite(gamma) || max_trials < 1)
+        return SUPCG_ERR_ARG;
+    return SUPCG_OK;
+}
+
+extern "C" int supcg_superiorize(supcg_geometry g, float *d_x, double a, double gamma, int K, long long max_trials,
+                                 long long *h_ell, int *h_trials, void *stream)
+{
+    if (!g || !d_x || !h_ell || *h_ell < 0) return SUPCG_ERR_ARG;
+    int rc = check_stv(a, gamma, K, max_trials);
+    if (rc) return rc;
+    Workspace *w;
+    if ((rc = ops_ws(g, 1, &w))) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    Prob &P = w->hp[0];
+    P.in_user = d_x;
+    P.out_user = d_x;
+    P.storage = SUPCG_F32;
+    rc = ws_upload(w, st);
+    P.storage = g->storage;
+    if (rc) return rc;
+    if (K > w->trials_cap) {
+        if (w->trials_dev) cudaFree(w->trials_dev);
+        w->trials_dev = nullptr;
+        w->trials_cap = 0;
+        SUPCG_CUDA_TRY(cudaMalloc(&w->trials_dev, sizeof(int) * K));
+        w->trials_cap = K;
+    }
+    Scal s0 = {};
+    s0.ell = *h_ell;
+    SUPCG_CUDA_TRY(cudaMemcpyAsync(P.sc, &s0, sizeof(Scal), cudaMemcpyHostToDevice, st));
+    SUPCG_CUDA_TRY(cudaMemsetAsync(P.bar, 0, 2 * sizeof(unsigned), st));
+    if ((rc = launch_stage_in(w->L(KT_TR, st), 0))) return rc;
+    if ((rc = launch_stv(w->L(KT_STV, st), K, a, gamma, max_trials, K > 0 ? w->trials_dev : nullptr, 0))) return rc;
+    if ((rc = launch_store_out(w->L(KT_VEC, st), 0))) return rc;
+    Scal s;
+    if ((rc = read_scal(P, &s, st))) return rc;
+    if (h_trials && K > 0) SUPCG_CUDA_TRY(cudaMemcpy(h_trials, w->trials_dev, sizeof(int) * K, cudaMemcpyDeviceToHost));
+    *h_ell = s.ell;
+    return s.status;
+}
+
+// ------------------------------------------------------------------ launch accounting
+#include <atomic>
+static std::atomic<long long> g_launches{0};
+
+struct Prof {
+    std::vector<cudaEvent_t> ev;
+    std::vector<int> kind;
+};
+static thread_local Prof *t_prof = nullptr;
+static thread_local long long t_capture_count = 0;
+
+#define LAUNCH(KIND, ST, CALL)                                                   \
+    do {                                                                         \
+        cudaEvent_t e0_ = nullptr;                                               \
+        if (t_prof) {                                                            \
+            SUPCG_CUDA_TRY(cudaEventCreate(&e0_));                               \
+            SUPCG_CUDA_TRY(cudaEventRecord(e0_, ST));                            \
+        }                                                                        \
+        int rc_ = (CALL);                                                        \
+        if (rc_) return rc_;                                                     \
+        ++g_launches;                                                            \
+        ++t_capture_count;                                                       \
+        if (t_prof) {                                                            \
+            cudaEvent_t e1_;                                                     \
+            SUPCG_CUDA_TRY(cudaEventCreate(&e1_));                               \
+            SUPCG_CUDA_TRY(cudaEventRecord(e1_, ST));                            \
+            t_prof->ev.push_back(e0_);                                           \
+            t_prof->ev.push_back(e1_);                                           \
+            t_prof->kind.push_back(KIND);                                        \
+        }                                                                        \
+    } while (0)
+
+extern "C" long long supcg_kernel_launches(void) { return g_launches.load(); }
+
+// ------------------------------------------------------------------ solve
+static int check_params(const supcg_params *p)
+{
+    if (!p || p->max_iter < 0 || p->K < 0) return SUPCG_ERR_ARG;
+    if (p->perturb) {
+        int rc = check_stv(p->a, p->gamma, p->K, p->max_trials);
+        if (rc) return rc;
+    }
+    if (p->precondition) return check_precond(p->mu, p->rho);
+    return SUPCG_OK;
+}
+
+// One while-body of Algorithm 3 (steps 10-14) over every problem of w.
+static int enqueue_precond_k(Workspace *w, cudaStream_t st)
+{
+    LAUNCH(SUPCG_KIND_FFT, st, launch_fft_rows(w->L(KT_ROWS, st), 0, 0, w->smem_rows));
+    LAUNCH(SUPCG_KIND_FFT, st, launch_fft_cols(w->L(KT_COLS, st), 0, w->smem_cols));
+    LAUNCH(SUPCG_KIND_FFT, st, launch_fft_rows(w->L(KT_ROWS, st), 1, 0, w->smem_rows));
+    return SUPCG_OK;
+}
+
+static int enqueue_body(Workspace *w, const supcg_params *p, cudaStream_t st, int want_snorm)
+{
+    int rc;
+    LAUNCH(SUPCG_KIND_VECTOR, st, launch_xupdate(w->L(KT_VEC, st)));            // step 10 + deferred step 7
+    if (p->perturb && p->K > 0)                                                 // steps 11-12
+        LAUNCH(SUPCG_KIND_STV, st, launch_stv(w->L(KT_STV, st), p->K, p->a, p->gamma, p->max_trials, nullptr,
+                                              want_snorm));
+    LAUNCH(SUPCG_KIND_VECTOR, st, launch_transpose(w->L(KT_TR, st), 0));
+    LAUNCH(SUPCG_KIND_FORWARD, st, launch_forward(w->L(KT_FWD, st), 0, FWD_RESID));   // r = R x - b, f
+    LAUNCH(SUPCG_KIND_BACKWARD, st, launch_backward(w->L(KT_BWD, st), BWD_G));         // g = R^T r
+    if (p->precondition && (rc = enqueue_precond_k(w, st))) return rc;                  // z = M g
+    LAUNCH(SUPCG_KIND_VECTOR, st, launch_beta(w->L(KT_VEC, st)));               // beta = z^T h / p^T h
+    LAUNCH(SUPCG_KIND_VECTOR, st, launch_pupdate(w->L(KT_VEC, st)));            // p = -z + beta p, g^T p
+    LAUNCH(SUPCG_KIND_VECTOR, st, launch_transpose(w->L(KT_TR, st), 1));
+    LAUNCH(SUPCG_KIND_FORWARD, st, launch_forward(w->L(KT_FWD, st), 1, FWD_NORM));    // q = R p, p^T h, alpha
+    LAUNCH(SUPCG_KIND_BACKWARD, st, launch_backward(w->L(KT_BWD, st), BWD_H));         // h = R^T q
+    LAUNCH(SUPCG_KIND_VECTOR, st, launch_log(w->L(KT_VEC, st)));                // k <- k + 1
+    return SUPCG_OK;
+}
+
+// Steps 1-9 of Algorithm 3: the same schedule with beta = 0 and no S_TV.
+static int enqueue_init(Workspace *w, const supcg_params *p, cudaStream_t st)
+{
+    int rc;
+    LAUNCH(SUPCG_KIND_FORWARD, st, launch_forward(w->L(KT_FWD, st), 0, FWD_RESID));
+    LAUNCH(SUPCG_KIND_BACKWARD, st, launch_backward(w->L(KT_BWD, st), BWD_G));
+    if (p->precondition && (rc = enqueue_precond_k(w, st))) return rc;
+    LAUNCH(SUPCG_KIND_VECTOR, st, launch_beta(w->L(KT_VEC, st)));
+    LAUNCH(SUPCG_KIND_VECTOR, st, launch_pupdate(w->L(KT_VEC, st)));
+    LAUNCH(SUPCG_KIND_VECTOR, st, launch_transpose(w->L(KT_TR, st), 1));
+    LAUNCH(SUPCG_KIND_FORWARD, st, launch_forward(w->L(KT_FWD, st), 1, FWD_NORM));
+    LAUNCH(SUPCG_KIND_BACKWARD, st, launch_backward(w->L(KT_BWD, st), BWD_H));
+    LAUNCH(SUPCG_KIND_VECTOR, st, launch_end_init(w->L(KT_VEC, st)));
+    return SUPCG_OK;
+}
+
+static int run_solve(Workspace *w, const float *const *d_b, float *const *d_x, const supcg_params *p,
+                     supcg_report *reps, double *d_log, cudaStream_t st)
+{
+    int rc;
+    for (int c = 0; c < w->count; ++c) {
+        Prob &P = w->hp[c];
+        P.in_user = d_x[c];
+        P.out_user = d_x[c];
+        P.in_user2 = d_b[c];
+        P.mu = (float)p->mu;
+        P.rho = (float)p->rho;
+        P.precond = p->precondition ? 1 : 0;
+        P.storage = SUPCG_F32;
+        P.log = (c == 0) ? d_log : nullptr;
+    }
+    rc = ws_upload(w, st);
+    for (int c = 0; c < w->count; ++c) w->hp[c].storage = w->geoms[c]->storage;
+    if (rc) return rc;
+    std::vector<Scal> s0(w->count);
+    for (int c = 0; c < w->count; ++c) {
+        const Prob &P = w->hp[c];
+        s0[c] = Scal();
+        s0[c].eps = p->eps;
+        s0[c].init = 1;
+        SUPCG_CUDA_TRY(cudaMemcpyAsync(P.sc, &s0[c], sizeof(Scal), cudaMemcpyHostToDevice, st));
+        SUPCG_CUDA_TRY(cudaMemsetAsync(P.counter, 0, 16 * sizeof(unsigned), st));
+        SUPCG_CUDA_TRY(cudaMemsetAsync(P.bar, 0, 2 * sizeof(unsigned), st));
+        SUPCG_CUDA_TRY(cudaMemsetAsync(P.p, 0, sizeof(float) * (size_t)P.ny * P.nxp, st));
+        SUPCG_CUDA_TRY(cudaMemsetAsync(P.h, 0, sizeof(float) * (size_t)P.ny * P.nxp, st));
+    }
+    LAUNCH(SUPCG_KIND_VECTOR, st, launch_stage_in(w->L(KT_TR, st), 0));
+    LAUNCH(SUPCG_KIND_VECTOR, st, launch_stage_sino(w->L(KT_SINO, st), 1));
+    if ((rc = enqueue_init(w, p, st))) return rc;
+
+    const int want_snorm = d_log != nullptr;
+    const bool eps_mode = p->eps >= 0.0;
+    int *hdone = nullptr;
+    if (eps_mode) SUPCG_CUDA_TRY(cudaMallocHost(&hdone, sizeof(int)));
+    bool use_graph = p->graph != 0 && t_prof == nullptr;
+    if (use_graph) {
+        const double key[6] = {p->a, p->gamma, (double)p->max_trials, (double)p->K, (double)p->perturb,
+                               (double)p->precondition};
+        const int key_i[4] = {want_snorm, 1, 0, 0};
+        if (!w->body_exec || memcmp(key, w->key, sizeof(key)) || memcmp(key_i, w->key_i, sizeof(key_i))) {
+            if (w->body_exec) cudaGraphExecDestroy(w->body_exec);
+            w->body_exec = nullptr;
+            cudaGraph_t graph = nullptr;
+            if (cudaStreamBeginCapture(w->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+                use_graph = false;
+            } else {
+                t_capture_count = 0;
+                int brc = enqueue_body(w, p, w->cap_stream, want_snorm);
+                w->body_nodes = t_capture_count;
+                cudaError_t e = cudaStreamEndCapture(w->cap_stream, &graph);
+                if (brc || e != cudaSuccess || cudaGraphInstantiate(&w->body_exec, graph, 0) != cudaSuccess) {
+                    use_graph = false;
+                    w->body_exec = nullptr;
+                    (void)cudaGetLastError();
+                }
+                if (graph) cudaGraphDestroy(graph);
+            }
+            if (use_graph) {
+                memcpy(w->key, key, sizeof(key));
+                memcpy(w->key_i, key_i, sizeof(key_i));
+            }
+        }
+    }
+    for (int it = 0; it < p->max_iter; ++it) {
+        if (use_graph) {
+            SUPCG_CUDA_TRY(cudaGraphLaunch(w->body_exec, st));
+            g_launches += w->body_nodes;
+        } else if ((rc = enqueue_body(w, p, st, want_snorm))) return rc;
+        if (eps_mode && w->count == 1 && (it % 8 == 7)) {
+            SUPCG_CUDA_TRY(cudaMemcpyAsync(hdone, &w->hp[0].sc->done, sizeof(int), cudaMemcpyDeviceToHost, st));
+            SUPCG_CUDA_TRY(cudaStreamSynchronize(st));
+            if (*hdone) break;
+        }
+    }
+    if (hdone) cudaFreeHost(hdone);
+    LAUNCH(SUPCG_KIND_VECTOR, st, launch_store_out(w->L(KT_VEC, st), 0));
+    std::vector<Scal> hs(w->count);
+    for (int c = 0; c < w->count; ++c)
+        SUPCG_CUDA_TRY(cudaMemcpyAsync(&hs[c], w->hp[c].sc, sizeof(Scal), cudaMemcpyDeviceToHost, st));
+    SUPCG_CUDA_TRY(cudaStreamSynchronize(st));
+    int worst = SUPCG_OK;
+    for (int c = 0; c < w->count; ++c) {
+        supcg_report &r = reps[c];
+        r.iters = hs[c].k;
+        r.k = hs[c].k + 1;
+        r.ell = hs[c].ell;
+        r.f_last = hs[c].f;
+        r.f0 = hs[c].f0;
+        r.tv_last = hs[c].tv_half;
+        r.status = hs[c].status;
+        if (hs[c].status && !worst) worst = hs[c].status;
+    }
+    return worst;
+}
+
+extern "C" int supcg_solve(supcg_geometry g, const float *d_b, float *d_x, const supcg_params *p, supcg_report *rep,
+                           double *d_log, void *stream)
+{
+    if (!g || !d_b || !d_x || !rep) return SUPCG_ERR_ARG;
+    int rc = check_params(p);
+    if (rc) return rc;
+    if (!g->ws_solve) {
+        std::vector<supcg_geometry> gs(1, g);
+        if ((rc = ws_create(gs, &g->ws_solve))) return rc;
+    }
+    return run_solve(g->ws_solve, &d_b, &d_x, p, rep, d_log, (cudaStream_t)stream);
+}
+
+extern "C" int supcg_solve_profiled(supcg_geometry g, const float *d_b, float *d_x, const supcg_params *p,
+                                    supcg_report *rep, double *h_ms, long long *h_launches, void *stream)
+{
+    if (!h_ms || !h_launches) return SUPCG_ERR_ARG;
+    Prof prof;
+    t_prof = &prof;
+    int rc = supcg_solve(g, d_b, d_x, p, rep, nullptr, stream);
+    t_prof = nullptr;
+    for (int k = 0; k < SUPCG_KIND_COUNT; ++k) { h_ms[k] = 0.0; h_launches[k] = 0; }
+    cudaStreamSynchronize((cudaStream_t)stream);
+    for (size_t i = 0; i < prof.kind.size(); ++i) {
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, prof.ev[2 * i], prof.ev[2 * i + 1]) == cudaSuccess) {
+            h_ms[prof.kind[i]] += ms;
+            h_launches[prof.kind[i]] += 1;
+        }
+    }
+    for (cudaEvent_t e : prof.ev) cudaEventDestroy(e);
+    return rc;
+}
+
+extern "C" int supcg_solve_host(supcg_geometry g, const float *h_b, float *h_x, const supcg_params *p,
+                                supcg_report *rep, void *stream)
+{
+    if (!g || !h_b || !h_x || !rep) return SUPCG_ERR_ARG;
+    int rc = check_params(p);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    float *db = nullptr, *dx = nullptr;
+    const size_t nb = sizeof(float) * (size_t)g->V * g->U, nx = sizeof(float) * (size_t)g->nx * g->ny;
+    SUPCG_CUDA_TRY(cudaMallocAsync(&db, nb, st));
+    SUPCG_CUDA_TRY(cudaMallocAsync(&dx, nx, st));
+    SUPCG_CUDA_TRY(cudaMemcpyAsync(db, h_b, nb, cudaMemcpyHostToDevice, st));
+    SUPCG_CUDA_TRY(cudaMemcpyAsync(dx, h_x, nx, cudaMemcpyHostToDevice, st));
+    rc = supcg_solve(g, db, dx, p, rep, nullptr, stream);
+    if (rc == SUPCG_OK || rc < SUPCG_ERR_NOMEM) {
+        SUPCG_CUDA_TRY(cudaMemcpyAsync(h_x, dx, nx, cudaMemcpyDeviceToHost, st));
+    }
+    cudaFreeAsync(db, st);
+    cudaFreeAsync(dx, st);
+    SUPCG_CUDA_TRY(cudaStreamSynchronize(st));
+    return rc;
+}
+
+extern "C" int supcg_solve_batched(const supcg_geometry *gs, const float *const *d_b, float *const *d_x, int count,
+                                   const supcg_params *p, supcg_report *reps, void *stream)
+{
+    if (!gs || !d_b || !d_x || !reps || count < 1) return SUPCG_ERR_ARG;
+    for (int c = 0; c < count; ++c)
+        if (!gs[c] || !d_b[c] || !d_x[c]) return SUPCG_ERR_ARG;
+    int rc = check_params(p);
+    if (rc) return rc;
+    supcg_geometry owner = gs[0];
+    std::vector<supcg_geometry> key(gs, gs + count);
+    if (!owner->ws_batch || owner->batch_key != key) {
+        free_ws(owner->ws_batch);
+        if ((rc = ws_create(key, &owner->ws_batch))) return rc;
+        owner->batch_key = key;
+    }
+    return run_solve(owner->ws_batch, d_b, d_x, p, reps, nullptr, (cudaStream_t)stream);
+}
+
+extern "C" const char *supcg_status_string(int status)
+{
+    switch (status) {
+    case SUPCG_OK: return "ok";
+    case SUPCG_ERR_ARG: return "invalid argument";
+    case SUPCG_ERR_CUDA: return "CUDA error";
+    case SUPCG_ERR_NOMEM: return "out of memory";
+    case SUPCG_ERR_BREAKDOWN: return "CG breakdown (p^T h <= 0 or non-finite scalar)";
+    case SUPCG_ERR_BACKTRACK: return "S_TV backtracking exceeded max_trials";
+    case SUPCG_ERR_TIMEOUT: return "bounded device wait expired";
+    case SUPCG_ERR_PRECOND: return "preconditioner not positive definite";
+    case SUPCG_ERR_UNSUPPORTED: return "geometry outside the supported range";
+    default: return "unknown status";
+    }
+}

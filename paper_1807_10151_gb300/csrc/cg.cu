@@ -1,0 +1,307 @@
+// CG vector algebra of U_PCG (Algorithm 2) and the state handling of
+// SupPCG (Algorithm 3): axpys with FP64-reduced inner products, the
+// termination test, staging of caller images into the padded / transposed
+// layouts the projector reads, and per-iteration logging.
+#include "internal.cuh"
+
+namespace supcg {
+
+constexpr int kVecPerThread = 4;
+constexpr int kVecPerBlock = kRedThreads * kVecPerThread;   // elements per block of the vector kernels
+
+// ------------------------------------------------------------ layout staging
+// 32 x 32 tile transpose through shared memory.  src [ny][sp] -> dst [nx][dp].
+__device__ __forceinline__ void transpose_tile(const float *src, int sp, float *dst, int dp, int ny, int nx,
+                                               int tile, float (*sh)[33])
+{
+    const int tiles_j = (nx + 31) / 32;
+    const int ti = tile / tiles_j, tj = tile - ti * tiles_j;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 256 threads: 32 x 8
+    for (int r = ty; r < 32; r += 8) {
+        const int i = ti * 32 + r, j = tj * 32 + tx;
+        sh[r][tx] = (i < ny && j < nx) ? src[(size_t)i * sp + j] : 0.0f;
+    }
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+        const int j = tj * 32 + r, i = ti * 32 + tx;
+        if (j < nx && i < ny) dst[(size_t)j * dp + i] = sh[tx][r];
+    }
+}
+
+__global__ void __launch_bounds__(256) k_transpose(const Prob *__restrict__ probs, const int *__restrict__ prefix,
+                                                   int count, int which)
+{
+    __shared__ float sh[32][33];
+    int local;
+    const Prob &P = probs[find_problem(prefix, count, blockIdx.x, &local)];
+    if (P.sc->done) return;
+    const float *src = which ? P.p : P.x;
+    float *dst = which ? P.pT : P.xT;
+    transpose_tile(src, P.nxp, dst, P.nyp, P.ny, P.nx, local, sh);
+}
+
+int launch_transpose(const Launch &L, int which)
+{
+    k_transpose<<<L.blocks, 256, 0, L.st>>>(L.probs, L.prefix, L.count, which);
+    SUPCG_CUDA_TRY(cudaGetLastError());
+    return SUPCG_OK;
+}
+
+__device__ __forceinline__ float load_user(const void *p, size_t i, int storage)
+{
+    return storage == SUPCG_BF16 ? __bfloat162float(reinterpret_cast<const __nv_bfloat16 *>(p)[i])
+                                 : reinterpret_cast<const float *>(p)[i];
+}
+
+// Caller image [ny][nx] -> x [ny][nxp] and x^T [nx][nyp] (zero padding kept).
+__global__ void __launch_bounds__(256) k_stage_in(const Prob *__restrict__ probs, const int *__restrict__ prefix,
+                                                  int count, int which)
+{
+    __shared__ float sh[32][33];
+    int local;
+    const Prob &P = probs[find_problem(prefix, count, blockIdx.x, &local)];
+    const int tiles_j = (P.nx + 31) / 32;
+    const int ti = local / tiles_j, tj = local - ti * tiles_j;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+    for (int r = ty; r < 32; r += 8) {
+        const int i = ti * 32 + r, j = tj * 32 + tx;
+        float v = 0.0f;
+        if (i < P.ny && j < P.nx) {
+            v = load_user(P.in_user, (size_t)i * P.nx + j, P.storage);
+            (which ? P.g : P.x)[(size_t)i * P.nxp + j] = v;
+        }
+        sh[r][tx] = v;
+    }
+    if (which) return;
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+        const int j = tj * 32 + r, i = ti * 32 + tx;
+        if (j < P.nx && i < P.ny) P.xT[(size_t)j * P.nyp + i] = sh[tx][r];
+    }
+}
+
+int launch_stage_in(const Launch &L, int which)
+{
+    k_stage_in<<<L.blocks, 256, 0, L.st>>>(L.probs, L.prefix, L.count, which);
+    SUPCG_CUDA_TRY(cudaGetLastError());
+    return SUPCG_OK;
+}
+
+// Caller sinogram [V][U] -> r (which 0) or bpad (which 1), pitch Up, zero padded.
+__global__ void __launch_bounds__(256) k_stage_sino(const Prob *__restrict__ probs, const int *__restrict__ prefix,
+                                                    int count, int which)
+{
+    int local;
+    const Prob &P = probs[find_problem(prefix, count, blockIdx.x, &local)];
+    float *dst = which ? P.bpad : P.r;
+    const size_t tot = (size_t)P.V * P.Up;
+    for (size_t e = (size_t)local * kVecPerBlock + threadIdx.x; e < tot && e < (size_t)(local + 1) * kVecPerBlock;
+         e += kRedThreads) {
+        const int v = (int)(e / P.Up), u = (int)(e - (size_t)v * P.Up);
+        const void *src = which ? P.in_user2 : P.in_user;
+        dst[e] = (u < P.U) ? load_user(src, (size_t)v * P.U + u, which ? SUPCG_F32 : P.storage) : 0.0f;
+    }
+}
+
+int launch_stage_sino(const Launch &L, int which)
+{
+    k_stage_sino<<<L.blocks, kRedThreads, 0, L.st>>>(L.probs, L.prefix, L.count, which);
+    SUPCG_CUDA_TRY(cudaGetLastError());
+    return SUPCG_OK;
+}
+
+// Padded image (which 0: x, 1: g, 2: z, 3: tbar) -> caller image [ny][nx].
+__global__ void __launch_bounds__(256) k_store_out(const Prob *__restrict__ probs, const int *__restrict__ prefix,
+                                                   int count, int which)
+{
+    int local;
+    const Prob &P = probs[find_problem(prefix, count, blockIdx.x, &local)];
+    const float *src = which == 0 ? P.x : (which == 1 ? P.g : (which == 2 ? P.z : P.tbar));
+    const size_t tot = (size_t)P.ny * P.nxp;
+    for (size_t e = (size_t)local * kVecPerBlock + threadIdx.x; e < tot && e < (size_t)(local + 1) * kVecPerBlock;
+         e += kRedThreads) {
+        const int i = (int)(e / P.nxp), j = (int)(e - (size_t)i * P.nxp);
+        if (j >= P.nx) continue;
+        const size_t o = (size_t)i * P.nx + j;
+        if (P.storage == SUPCG_BF16) reinterpret_cast<__nv_bfloat16 *>(P.out_user)[o] = __float2bfloat16_rn(src[e]);
+        else reinterpret_cast<float *>(P.out_user)[o] = src[e];
+    }
+}
+
+int launch_store_out(const Launch &L, int which)
+{
+    k_store_out<<<L.blocks, kRedThreads, 0, L.st>>>(L.probs, L.prefix, L.count, which);
+    SUPCG_CUDA_TRY(cudaGetLastError());
+    return SUPCG_OK;
+}
+
+// ------------------------------------------------------------ Algorithm 2 steps
+// Steps 3-4 (beta from z^T h computed earlier) and the g^T p half of step 6:
+//   p <- -z + beta p ;  partial g^T p.   In steps 2-7 of Algorithm 3 beta = 0.
+__global__ void __launch_bounds__(kRedThreads) k_pupdate(const Prob *__restrict__ probs,
+                                                         const int *__restrict__ prefix, int count)
+{
+    __shared__ double red[40];
+    __shared__ int flag;
+    int local;
+    const int pi = find_problem(prefix, count, blockIdx.x, &local);
+    const Prob &P = probs[pi];
+    if (P.sc->done) return;
+    const double beta_d = P.sc->init ? 0.0 : P.sc->beta;
+    const float beta = (float)beta_d;
+    const float *z = P.precond ? P.z : P.g;   // M = I: z = g
+    const size_t tot = (size_t)P.ny * P.nxp;
+    double s = 0.0;
+    for (size_t e = (size_t)local * kVecPerBlock + threadIdx.x; e < tot && e < (size_t)(local + 1) * kVecPerBlock;
+         e += kRedThreads) {
+        const float pn = __fmaf_rn(beta, P.p[e], -z[e]);
+        P.p[e] = pn;
+        s += (double)P.g[e] * (double)pn;
+    }
+    const double bs = block_sum<kRedThreads>(s, red);
+    if (threadIdx.x == 0) P.partial[local] = bs;
+    const int nblk = prefix[pi + 1] - prefix[pi];
+    if (last_block(&P.counter[1], nblk, &flag)) {
+        const double tot_s = block_sum_array<kRedThreads>(P.partial, nblk, red);
+        if (threadIdx.x == 0) {
+            P.sc->gtp = tot_s;
+            P.sc->beta = beta_d;
+            P.counter[1] = 0;
+        }
+    }
+}
+
+int launch_pupdate(const Launch &L)
+{
+    k_pupdate<<<L.blocks, kRedThreads, 0, L.st>>>(L.probs, L.prefix, L.count);
+    SUPCG_CUDA_TRY(cudaGetLastError());
+    return SUPCG_OK;
+}
+
+// Step 3 of Algorithm 2: beta = z^T h / p^T h (p, h of the previous step).
+// With M = I, z is g.
+__global__ void __launch_bounds__(kRedThreads) k_beta(const Prob *__restrict__ probs,
+                                                      const int *__restrict__ prefix, int count)
+{
+    __shared__ double red[40];
+    __shared__ int flag;
+    int local;
+    const int pi = find_problem(prefix, count, blockIdx.x, &local);
+    const Prob &P = probs[pi];
+    if (P.sc->done) return;
+    const float *z = P.precond ? P.z : P.g;
+    const size_t tot = (size_t)P.ny * P.nxp;
+    double s = 0.0;
+    for (size_t e = (size_t)local * kVecPerBlock + threadIdx.x; e < tot && e < (size_t)(local + 1) * kVecPerBlock;
+         e += kRedThreads)
+        s += (double)z[e] * (double)P.h[e];
+    const double bs = block_sum<kRedThreads>(s, red);
+    if (threadIdx.x == 0) P.partial[local] = bs;
+    const int nblk = prefix[pi + 1] - prefix[pi];
+    if (last_block(&P.counter[2], nblk, &flag)) {
+        const double tot_s = block_sum_array<kRedThreads>(P.partial, nblk, red);
+        if (threadIdx.x == 0) {
+            Scal *sc = P.sc;
+            sc->zth = tot_s;
+            if (sc->init) {
+                sc->beta = 0.0;
+            } else {
+                const double b = tot_s / sc->pth;
+                if (!isfinite(b)) atomicExch(&sc->status, (int)SUPCG_ERR_BREAKDOWN);
+                sc->beta = isfinite(b) ? b : 0.0;
+            }
+            P.counter[2] = 0;
+        }
+    }
+}
+
+int launch_beta(const Launch &L)
+{
+    k_beta<<<L.blocks, kRedThreads, 0, L.st>>>(L.probs, L.prefix, L.count);
+    SUPCG_CUDA_TRY(cudaGetLastError());
+    return SUPCG_OK;
+}
+
+// Start of a while-body of Algorithm 3: the condition f(x_{k-1/2}) > eps
+// (step 10) and, when it holds, step 7 of the previous U_PCG call
+// (x_k = x_{k-1/2} + alpha p_{k-1}), deferred to here so that x holds the
+// returned image x_{k-1/2} whenever the loop stops.
+__global__ void __launch_bounds__(kRedThreads) k_xupdate(const Prob *__restrict__ probs,
+                                                         const int *__restrict__ prefix, int count)
+{
+    int local;
+    const Prob &P = probs[find_problem(prefix, count, blockIdx.x, &local)];
+    Scal *sc = P.sc;
+    if (sc->done) return;
+    const bool stop = !(sc->f > sc->eps) || sc->status != 0;
+    if (stop) {
+        // every block takes the same decision from the same scalars; block 0 records it
+        // after all blocks have read it (done is read again only by later launches)
+        if (local == 0 && threadIdx.x == 0) sc->done = 2;   // 2: set during this launch
+        return;
+    }
+    const float al = (float)sc->alpha;
+    const size_t tot = (size_t)P.ny * P.nxp;
+    for (size_t e = (size_t)local * kVecPerBlock + threadIdx.x; e < tot && e < (size_t)(local + 1) * kVecPerBlock;
+         e += kRedThreads)
+        P.x[e] = __fmaf_rn(al, P.p[e], P.x[e]);
+}
+
+int launch_xupdate(const Launch &L)
+{
+    k_xupdate<<<L.blocks, kRedThreads, 0, L.st>>>(L.probs, L.prefix, L.count);
+    SUPCG_CUDA_TRY(cudaGetLastError());
+    return SUPCG_OK;
+}
+
+// End of steps 2-7 of Algorithm 3.
+__global__ void k_end_init(const Prob *__restrict__ probs, int count)
+{
+    const int pi = blockIdx.x * blockDim.x + threadIdx.x;
+    if (pi < count) probs[pi].sc->init = 0;
+}
+
+int launch_end_init(const Launch &L)
+{
+    k_end_init<<<(L.count + 127) / 128, 128, 0, L.st>>>(L.probs, L.count);
+    SUPCG_CUDA_TRY(cudaGetLastError());
+    return SUPCG_OK;
+}
+
+// End of a while-body: record the per-iteration metrics, k <- k + 1 (step 14).
+__global__ void k_body_end(const Prob *__restrict__ probs, int count)
+{
+    const int pi = blockIdx.x * blockDim.x + threadIdx.x;
+    if (pi >= count) return;
+    const Prob &P = probs[pi];
+    Scal *sc = P.sc;
+    if (sc->done) {
+        sc->done = 1;
+        return;
+    }
+    if (sc->status != 0) {
+        sc->done = 1;
+        return;
+    }
+    if (P.log) {
+        double *L = P.log + (size_t)sc->k * SUPCG_LOG_STRIDE;
+        L[0] = sc->f;
+        L[1] = sc->tv_k;
+        L[2] = sc->tv_half;
+        L[3] = (double)sc->ell;
+        L[4] = sc->alpha;
+        L[5] = sc->beta;
+        L[6] = sc->snorm2;
+        L[7] = (double)sc->trials;
+    }
+    sc->k += 1;
+}
+
+int launch_log(const Launch &L)
+{
+    k_body_end<<<(L.count + 127) / 128, 128, 0, L.st>>>(L.probs, L.count);
+    SUPCG_CUDA_TRY(cudaGetLastError());
+    return SUPCG_OK;
+}
+
+} // namespace supcg

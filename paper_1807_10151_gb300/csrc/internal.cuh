@@ -1,0 +1,314 @@
+// Internal definitions shared by the libsupcg translation units.
+//
+// Everything here is GPU-path code; none of it is shared with the CPU oracle.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/supcg.h"
+
+namespace supcg {
+
+// ----------------------------------------------------------------- limits
+constexpr int kMaxStages = 24;       // FFT stages (radices) per length
+constexpr int kMaxRadix = 64;        // largest prime factor handled by the generic butterfly
+constexpr int kRowsPerChunk = 32;    // forward projector: image rows staged per TMA box
+constexpr int kBwdTileI = 16;        // backprojector pixel tile (rows)
+constexpr int kBwdTileJ = 32;        // backprojector pixel tile (columns)
+constexpr int kBwdViewChunk = 32;    // backprojector: views staged per shared-memory chunk
+constexpr int kBwdWin = 64;          // backprojector: bins per staged window (floats)
+constexpr int kRedThreads = 256;     // block size of the reduction / vector kernels
+constexpr long long kSpinLimit = 1ll << 24;  // bounded waits (iterations of a ~100 ns poll)
+
+// ----------------------------------------------------------------- views
+// Per-view constants.  The detector coordinate of pixel (i, j) in bins is
+//   t_c(i, j) = fmaf(cu, X_j, su * Y_i),   X_j = j - (nx-1)/2,  Y_i = (ny-1)/2 - i
+// and ray (v, u) sits at tau_u = u - uc.  The intersection length of ray u with
+// pixel (i, j) is the trapezoid W(tau_u - t_c) (see weight()).  Both
+// projector kernels evaluate exactly this expression, so the backprojector
+// applies the exact transpose of the forward matrix.
+struct ViewP {
+    float cu, su;   // cos(theta) d/ds, sin(theta) d/ds
+    float E;        // footprint half-width in bins: (d/ds) (|cos|+|sin|) / 2
+    float S;        // ds / (|cos| |sin|): length per bin on the trapezoid's sides
+    float P;        // plateau length d / max(|cos|, |sin|)
+    float a_tau;    // forward: inner index of the ray centre = a_tau*tau + b_o*outer + g0
+    float b_o;
+    float g0;
+    int flags;      // bit 0: axis-aligned view (cos or sin exactly 0); bit 1: class B
+    int pad[3];
+};
+constexpr int kViewAxis = 1;
+constexpr int kViewClassB = 2;
+
+// Intersection length for a ray at signed detector distance `delta` (bins)
+// from the pixel centre.  Axis-aligned views use the box limit with half
+// weight exactly on the edge; others the trapezoid.  Explicit _rn intrinsics
+// pin the rounding so that every call site produces identical bits.
+__device__ __forceinline__ float weight(float delta, const ViewP &vp)
+{
+    float ad = fabsf(delta);
+    if (vp.flags & kViewAxis)
+        return ad < vp.E ? vp.P : (ad == vp.E ? 0.5f * vp.P : 0.0f);
+    float t = __fmul_rn(__fsub_rn(vp.E, ad), vp.S);
+    return fminf(vp.P, fmaxf(0.0f, t));
+}
+
+__device__ __forceinline__ float det_coord(const ViewP &vp, float Xj, float Yi)
+{
+    return __fmaf_rn(vp.cu, Xj, __fmul_rn(vp.su, Yi));
+}
+
+__device__ __forceinline__ float bin_pos(int u, float uc) { return __fsub_rn(__int2float_rn(u), uc); }
+
+// ----------------------------------------------------------------- FFT plan
+struct FFTPlan {
+    int n;
+    int nst;
+    int radix[kMaxStages];
+    const float2 *tw;   // exp(-2 pi i k / n), k = 0 .. n-1
+};
+
+// ----------------------------------------------------------------- scalars
+// Device-resident state of one problem's solve (Algorithm 3).
+struct Scal {
+    double f;          // f(x_{k+1/2}) of the most recent forward projection of x
+    double f0;         // f(x_0)
+    double pth;        // p^T h = ||R p||^2 of the current p
+    double gtp;        // g^T p
+    double zth;        // z^T h_prev
+    double alpha, beta;
+    double tv_k, tv_half;  // TV(x_k), TV(x_{k+1/2}) of the last S_TV call
+    double snorm2;     // ||s_k||^2 of the last S_TV call (accumulated in FP64)
+    double eps;
+    long long ell;     // l of Algorithm 1/3
+    long long trials;  // trials of the last S_TV call
+    int k;             // executions of the while body
+    int done;          // 1: the while condition failed (or an error stopped the loop)
+    int status;        // SUPCG_OK or an error code
+    int init;          // 1 while running steps 2-7 (beta forced to 0)
+    int pad[4];
+};
+
+// ----------------------------------------------------------------- problem
+// One problem of a batched launch (device copy lives in global memory).
+struct Prob {
+    CUtensorMap tm[4];     // TMA maps: 0 = x, 1 = x^T, 2 = p, 3 = p^T (FP32, padded pitches)
+    int nx, ny, V, U;
+    int nxp, nyp, Up;      // pitches in elements: image, transposed image, sinogram
+    int BU, BW, ntu;       // forward tiling: bins per block, box width, bin tiles per view
+    int nA, nB;            // number of class-A / class-B views
+    float cx, cy, uc;
+    const ViewP *views;    // [V]
+    const int *vlist;      // [nA + nB]: class-A views, then class-B views
+    FFTPlan fx, fy;
+    float mu, rho;
+    int precond;           // 1: M of Eq. (3.2); 0: M = I
+    int storage;           // SUPCG_F32 / SUPCG_BF16 element type of in_user / out_user
+    int stv_blocks;        // cooperative S_TV: blocks owned by this problem
+    int fft_rpb, fft_cw;   // FFT rows per block / columns per block
+    // solve buffers (images pitch nxp, transposed pitch nyp, sinograms pitch Up)
+    float *x, *xT, *p, *pT, *g, *z, *h, *tbar;
+    float *r, *q, *bpad;
+    float2 *C;             // FFT scratch [ny][nx]
+    Scal *sc;
+    double *partial;       // reduction partials (>= 2 * max blocks per kernel)
+    unsigned *counter;     // last-block tickets [8]
+    unsigned *bar;         // cooperative barrier [2]: arrivals, generation
+    double *log;           // nullable [max_iter][SUPCG_LOG_STRIDE]
+    // caller-owned I/O (unpadded): image in / out, sinogram in
+    const void *in_user;
+    void *out_user;
+    const void *in_user2;
+};
+
+// Map a block of a batched launch to (problem, block within problem).
+__device__ __forceinline__ int find_problem(const int *prefix, int count, int b, int *local)
+{
+    int lo = 0, hi = count - 1;
+    while (lo < hi) {
+        int mid = (lo + hi + 1) >> 1;
+        if (__ldg(prefix + mid) <= b) lo = mid; else hi = mid - 1;
+    }
+    *local = b - __ldg(prefix + lo);
+    return lo;
+}
+
+// ----------------------------------------------------------------- reductions
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Block sum in a fixed order (deterministic); result valid in thread 0.
+template <int NT>
+__device__ __forceinline__ double block_sum(double v, double *sh)
+{
+    v = warp_sum(v);
+    int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) sh[w] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (w == 0) {
+        r = (l < NT / 32) ? sh[l] : 0.0;
+        r = warp_sum(r);
+    }
+    __syncthreads();
+    return r;
+}
+
+// Sum partial[0..n) in a fixed order with the whole block; result in all threads.
+template <int NT>
+__device__ __forceinline__ double block_sum_array(const volatile double *partial, int n, double *sh)
+{
+    double v = 0.0;
+    for (int i = threadIdx.x; i < n; i += NT) v += partial[i];
+    v = block_sum<NT>(v, sh);
+    if (threadIdx.x == 0) sh[32] = v;
+    __syncthreads();
+    double r = sh[32];
+    __syncthreads();
+    return r;
+}
+
+// Last-block-done ticket: true in every thread of the block that finishes last.
+__device__ __forceinline__ bool last_block(unsigned *counter, unsigned nblocks, int *sh_flag)
+{
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned t = atomicAdd(counter, 1u);
+        *sh_flag = (t == nblocks - 1);
+    }
+    __syncthreads();
+    bool last = *sh_flag;
+    if (last) __threadfence();
+    return last;
+}
+
+// Bounded barrier among `nblocks` co-resident blocks (cooperative launch).
+// bar[0] counts arrivals, bar[1] is the generation.  Returns false on timeout
+// (and raises SUPCG_ERR_TIMEOUT in *status).
+__device__ __forceinline__ bool coop_barrier(unsigned *bar, unsigned nblocks, int *status, int *sh_flag)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *vgen = bar + 1;
+        unsigned gen = *vgen;
+        __threadfence();
+        unsigned arrived = atomicAdd(bar, 1u);
+        int ok = 1;
+        if (arrived == nblocks - 1) {
+            atomicExch(bar, 0u);
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            long long it = 0;
+            while (*vgen == gen) {
+                if (++it > kSpinLimit) { ok = 0; atomicExch(status, (int)SUPCG_ERR_TIMEOUT); break; }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        *sh_flag = ok && (*(volatile int *)status != (int)SUPCG_ERR_TIMEOUT);
+    }
+    __syncthreads();
+    return *sh_flag;
+}
+
+// ----------------------------------------------------------------- TMA / mbarrier
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// Bounded wait for phase `parity` of an mbarrier; false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned parity)
+{
+    uint32_t a = smem_u32(bar);
+    for (long long it = 0; it < kSpinLimit; ++it) {
+        uint32_t done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// 2-D tiled TMA load of box (x0 = innermost coordinate, y0) into shared memory.
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *tm, int x0, int y0, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(tm)), "r"(x0), "r"(y0), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// ----------------------------------------------------------------- host side
+#define SUPCG_CUDA_TRY(expr)                                   \
+    do {                                                       \
+        cudaError_t e_ = (expr);                               \
+        if (e_ != cudaSuccess) return supcg::cuda_fail(e_, #expr, __FILE__, __LINE__); \
+    } while (0)
+
+int cuda_fail(cudaError_t e, const char *what, const char *file, int line);
+
+// Launchers (defined in the kernel translation units).  Each enqueues one
+// kernel over all `count` problems of `probs` (device array) on `st`.
+enum FwdMode { FWD_RESID = 0, FWD_NORM = 1, FWD_PLAIN = 2 };
+enum BwdMode { BWD_G = 0, BWD_H = 1, BWD_PLAIN = 2 };
+
+struct Launch {
+    const Prob *probs;     // device
+    int count;
+    const int *prefix;     // device: block prefix for this kernel type, count+1 entries
+    int blocks;            // total blocks
+    cudaStream_t st;
+};
+
+int launch_forward(const Launch &L, int which, int mode);
+int launch_backward(const Launch &L, int mode);
+int launch_transpose(const Launch &L, int which);          // x -> x^T (which 0) or p -> p^T (which 1)
+int launch_stage_in(const Launch &L, int which);           // caller image -> x and x^T (0) or g (1)
+int launch_stage_sino(const Launch &L, int which);         // caller sinogram -> r (0, in_user) or bpad (1, in_user2)
+int launch_store_out(const Launch &L, int which);          // padded image (0 x, 1 g, 2 z, 3 tbar) -> caller
+int launch_fft_rows(const Launch &L, int inverse, int standalone, int smem);
+int launch_fft_cols(const Launch &L, int standalone, int smem);
+int launch_pupdate(const Launch &L);
+int launch_beta(const Launch &L);
+int launch_xupdate(const Launch &L);
+int launch_end_init(const Launch &L);
+int launch_stv(const Launch &L, int K, double a, double gamma, long long max_trials, int *trials_out,
+               int want_snorm);
+int launch_tv_tbar(const Launch &L);
+int launch_log(const Launch &L);
+int stv_max_blocks_per_sm(int *out);
+
+} // namespace supcg

@@ -1,0 +1,330 @@
+// Forward projection R x and its exact transpose R^T y (Sec. 2: R x = b + e;
+// Eq. (2.2): normal equations R^T R x = R^T b).
+//
+// Forward (ray-driven, gather over pixels).  A block owns one view and up to
+// 128 consecutive bins.  Views are split in two classes: class A
+// (|cos| >= |sin|) walks image rows, class B walks image columns, and class B
+// reads the transposed image x^T so that both classes walk contiguous rows of
+// the array they read.  Chunks of 32 rows x BW columns covering the block's
+// rays are staged in shared memory by 2-D TMA loads (double buffered, one
+// mbarrier per buffer).  For every row a ray can only cross the three columns
+// nearest to its centre; each is weighted by the shared trapezoid weight().
+//
+// Backward (pixel-driven, gather over bins, no atomics).  A block owns a
+// 16 x 32 pixel tile; for chunks of 32 views the bins that the tile projects
+// onto are staged in shared memory with 16-byte vector loads; every pixel
+// gathers the three bins nearest to its projected centre with the same
+// weight() evaluated on the same FP32 operands as the forward kernel.
+#include "internal.cuh"
+
+namespace supcg {
+
+// ============================================================ forward
+template <bool CLASS_B>
+__device__ __forceinline__ float fwd_rows(const Prob &P, const ViewP &vp, float tau, float base_u, int o0,
+                                          int rows, int qs, const float *patch, int *bad)
+{
+    float acc = 0.0f;
+    const int BW = P.BW;
+    for (int r = 0; r < rows; ++r) {
+        const int o = o0 + r;
+        const float of = __int2float_rn(o);
+        const float qm = __fmaf_rn(vp.b_o, of, base_u);
+        const int qc = __float2int_rn(qm);
+        const float *row = patch + r * BW - qs;
+        if (!CLASS_B) {
+            // class A: outer = image row i = o, inner = column j = q
+            const float Yo = __fsub_rn(P.cy, of);
+            const float suY = __fmul_rn(vp.su, Yo);
+#pragma unroll
+            for (int k = -1; k <= 1; ++k) {
+                const int q = qc + k;
+                const float Xq = __fsub_rn(__int2float_rn(q), P.cx);
+                const float w = weight(__fsub_rn(tau, __fmaf_rn(vp.cu, Xq, suY)), vp);
+                const int idx = q - qs;
+                if ((unsigned)idx < (unsigned)BW) acc = __fmaf_rn(w, row[q], acc);
+                else *bad = 1;
+            }
+        } else {
+            // class B: outer = image column j = o, inner = row i = q (patch from x^T)
+            const float Xo = __fsub_rn(of, P.cx);
+#pragma unroll
+            for (int k = -1; k <= 1; ++k) {
+                const int q = qc + k;
+                const float Yq = __fsub_rn(P.cy, __int2float_rn(q));
+                const float w = weight(__fsub_rn(tau, det_coord(vp, Xo, Yq)), vp);
+                const int idx = q - qs;
+                if ((unsigned)idx < (unsigned)BW) acc = __fmaf_rn(w, row[q], acc);
+                else *bad = 1;
+            }
+        }
+    }
+    return acc;
+}
+
+// Lower end (multiple of 4) of the inner range that chunk [o0, o0+RC) of the
+// block's rays [u_first, u_last] can touch.
+__device__ __forceinline__ int fwd_box_start(const ViewP &vp, float tf, float tl, float uc, int o0)
+{
+    const float bf = __fmaf_rn(vp.a_tau, tf, vp.g0);
+    const float bl = __fmaf_rn(vp.a_tau, tl, vp.g0);
+    const float o_a = __int2float_rn(o0), o_b = __int2float_rn(o0 + kRowsPerChunk - 1);
+    float m = fminf(fminf(__fmaf_rn(vp.b_o, o_a, bf), __fmaf_rn(vp.b_o, o_b, bf)),
+                    fminf(__fmaf_rn(vp.b_o, o_a, bl), __fmaf_rn(vp.b_o, o_b, bl)));
+    int lo = __float2int_rd(m) - 3;
+    return lo & ~3;   // round down to a multiple of 4 floats (16-byte TMA rule)
+}
+
+__global__ void __launch_bounds__(128) k_forward(const Prob *__restrict__ probs, const int *__restrict__ prefix,
+                                                 int count, int which, int mode)
+{
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t bars[2];
+    __shared__ double red[40];
+    __shared__ int flag;
+    __shared__ int bad_sh;
+
+    int local;
+    const int pi = find_problem(prefix, count, blockIdx.x, &local);
+    const Prob &P = probs[pi];
+    if (mode != FWD_PLAIN && P.sc->done) return;
+
+    const int vidx = local / P.ntu, tile = local - vidx * P.ntu;
+    const bool classB = vidx >= P.nA;
+    const int v = P.vlist[vidx];
+    const ViewP vp = P.views[v];
+    const int n_outer = classB ? P.nx : P.ny;
+    const CUtensorMap *tm = &P.tm[which * 2 + (classB ? 1 : 0)];
+    float *patch0 = reinterpret_cast<float *>(smem_raw);
+    const int RC = kRowsPerChunk, BW = P.BW;
+    const int box_elems = RC * BW;
+
+    const int t = threadIdx.x;
+    const int u_first = tile * P.BU;
+    const int u_last = min(P.U, u_first + P.BU) - 1;
+    const int u = u_first + t;
+    const float tau = bin_pos(u, P.uc);
+    const float base_u = __fmaf_rn(vp.a_tau, tau, vp.g0);
+    const float tf = bin_pos(u_first, P.uc), tl = bin_pos(u_last, P.uc);
+    const int nchunks = (n_outer + RC - 1) / RC;
+
+    if (t == 0) {
+        bad_sh = 0;
+        mbar_init(&bars[0], 1);
+        mbar_init(&bars[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (t == 0) {
+        for (int c = 0; c < 2 && c < nchunks; ++c) {
+            mbar_expect_tx(&bars[c], box_elems * 4);
+            tma_load_2d(patch0 + c * box_elems, tm, fwd_box_start(vp, tf, tl, P.uc, c * RC), c * RC, &bars[c]);
+        }
+    }
+
+    float acc = 0.0f;
+    int bad = 0;
+    bool timed_out = false;
+    for (int c = 0; c < nchunks; ++c) {
+        const int buf = c & 1;
+        if (!mbar_wait(&bars[buf], (c >> 1) & 1)) { timed_out = true; break; }
+        const int o0 = c * RC;
+        const int rows = min(RC, n_outer - o0);
+        const int qs = fwd_box_start(vp, tf, tl, P.uc, o0);
+        if (u <= u_last) {
+            if (classB) acc += fwd_rows<true>(P, vp, tau, base_u, o0, rows, qs, patch0 + buf * box_elems, &bad);
+            else acc += fwd_rows<false>(P, vp, tau, base_u, o0, rows, qs, patch0 + buf * box_elems, &bad);
+        }
+        __syncthreads();   // every thread is done with this buffer
+        if (t == 0 && c + 2 < nchunks) {
+            mbar_expect_tx(&bars[buf], box_elems * 4);
+            tma_load_2d(patch0 + buf * box_elems, tm, fwd_box_start(vp, tf, tl, P.uc, (c + 2) * RC), (c + 2) * RC,
+                        &bars[buf]);
+        }
+    }
+    if (timed_out) {
+        // wait (bounded) for any copy still in flight before leaving
+        if (t == 0) {
+            atomicExch(&P.sc->status, (int)SUPCG_ERR_TIMEOUT);
+            for (int b = 0; b < 2; ++b) (void)mbar_wait(&bars[b], 0);
+        }
+        return;
+    }
+    if (bad) atomicExch(&bad_sh, 1);
+
+    // epilogue: store, fused residual / norm reduction
+    double s = 0.0;
+    if (u <= u_last) {
+        if (mode == FWD_PLAIN) {
+            const size_t o = (size_t)v * P.U + u;
+            if (P.storage == SUPCG_BF16) reinterpret_cast<__nv_bfloat16 *>(P.out_user)[o] = __float2bfloat16_rn(acc);
+            else reinterpret_cast<float *>(P.out_user)[o] = acc;
+        } else if (mode == FWD_RESID) {
+            const size_t o = (size_t)v * P.Up + u;
+            const float rr = acc - P.bpad[o];
+            P.r[o] = rr;
+            s = (double)rr * (double)rr;
+        } else {
+            const size_t o = (size_t)v * P.Up + u;
+            P.q[o] = acc;
+            s = (double)acc * (double)acc;
+        }
+    }
+    __syncthreads();
+    if (t == 0 && bad_sh) atomicExch(&P.sc->status, (int)SUPCG_ERR_UNSUPPORTED);
+    if (mode == FWD_PLAIN) return;
+
+    const double bs = block_sum<128>(s, red);
+    if (t == 0) P.partial[local] = bs;
+    const int nblk = prefix[pi + 1] - prefix[pi];
+    if (last_block(&P.counter[0], nblk, &flag)) {
+        const double tot = block_sum_array<128>(P.partial, nblk, red);
+        if (t == 0) {
+            Scal *sc = P.sc;
+            if (mode == FWD_RESID) {
+                sc->f = tot;
+                if (sc->init) sc->f0 = tot;
+            } else {
+                sc->pth = tot;
+                const double al = -sc->gtp / tot;
+                if (!(tot > 0.0) || !isfinite(al)) {
+                    atomicExch(&sc->status, (int)SUPCG_ERR_BREAKDOWN);
+                    sc->alpha = 0.0;
+                } else {
+                    sc->alpha = al;
+                }
+            }
+            P.counter[0] = 0;
+        }
+    }
+}
+
+int launch_forward(const Launch &L, int which, int mode)
+{
+    static int max_smem_set = 0;
+    // every problem's BW <= 256, so the box buffers never exceed this size
+    const int smem = 2 * kRowsPerChunk * 256 * 4;
+    if (!max_smem_set) {
+        SUPCG_CUDA_TRY(cudaFuncSetAttribute(k_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        max_smem_set = 1;
+    }
+    k_forward<<<L.blocks, 128, smem, L.st>>>(L.probs, L.prefix, L.count, which, mode);
+    SUPCG_CUDA_TRY(cudaGetLastError());
+    return SUPCG_OK;
+}
+
+// ============================================================ backward
+constexpr int kBwdThreads = 256;
+constexpr int kBwdPixPerThread = kBwdTileI * kBwdTileJ / kBwdThreads;   // 2
+
+__global__ void __launch_bounds__(kBwdThreads) k_backward(const Prob *__restrict__ probs,
+                                                          const int *__restrict__ prefix, int count, int mode)
+{
+    __shared__ __align__(16) float win[2][kBwdViewChunk][kBwdWin];
+    __shared__ ViewP vsh[2][kBwdViewChunk];
+    __shared__ int ulo_sh[2][kBwdViewChunk];
+    __shared__ int bad_sh;
+
+    int local;
+    const int pi = find_problem(prefix, count, blockIdx.x, &local);
+    const Prob &P = probs[pi];
+    if (mode != BWD_PLAIN && P.sc->done) return;
+
+    const int tiles_j = (P.nx + kBwdTileJ - 1) / kBwdTileJ;
+    const int ti = local / tiles_j, tj = local - ti * tiles_j;
+    const int i0 = ti * kBwdTileI, j0 = tj * kBwdTileJ;
+    const int t = threadIdx.x;
+    const int lx = t % kBwdTileJ, ly = t / kBwdTileJ;   // ly in [0, 8)
+    const int j = j0 + lx;
+    const float Xj = __fsub_rn(__int2float_rn(j), P.cx);
+    float Yi[kBwdPixPerThread];
+#pragma unroll
+    for (int e = 0; e < kBwdPixPerThread; ++e) Yi[e] = __fsub_rn(P.cy, __int2float_rn(i0 + ly + 8 * e));
+    float acc[kBwdPixPerThread];
+#pragma unroll
+    for (int e = 0; e < kBwdPixPerThread; ++e) acc[e] = 0.0f;
+
+    const float *sino = (mode == BWD_G) ? P.r : (mode == BWD_H ? P.q : P.r);
+    const int Up = P.Up;
+    // tile corners in pixel-centre coordinates
+    const float Xa = __fsub_rn(__int2float_rn(j0), P.cx), Xb = __fsub_rn(__int2float_rn(j0 + kBwdTileJ - 1), P.cx);
+    const float Ya = __fsub_rn(P.cy, __int2float_rn(i0)), Yb = __fsub_rn(P.cy, __int2float_rn(i0 + kBwdTileI - 1));
+    if (t == 0) bad_sh = 0;
+
+    const int nchunks = (P.V + kBwdViewChunk - 1) / kBwdViewChunk;
+    // stage chunk c into buffer c&1
+    auto stage = [&](int c) {
+        const int buf = c & 1;
+        const int v0 = c * kBwdViewChunk;
+        if (t < kBwdViewChunk) {
+            const int v = v0 + t;
+            int lo = 0;
+            if (v < P.V) {
+                const ViewP vp = P.views[v];
+                vsh[buf][t] = vp;
+                float m = fminf(fminf(det_coord(vp, Xa, Ya), det_coord(vp, Xa, Yb)),
+                                fminf(det_coord(vp, Xb, Ya), det_coord(vp, Xb, Yb)));
+                lo = (__float2int_rd(__fadd_rn(m, P.uc)) - 3) & ~3;
+            }
+            ulo_sh[buf][t] = lo;
+        }
+        __syncthreads();
+        constexpr int V4 = kBwdWin / 4;
+        for (int e = t; e < kBwdViewChunk * V4; e += kBwdThreads) {
+            const int vv = e / V4, k4 = e - vv * V4;
+            const int v = v0 + vv;
+            float4 val = make_float4(0.f, 0.f, 0.f, 0.f);
+            const int ub = ulo_sh[buf][vv] + 4 * k4;
+            if (v < P.V && ub >= 0 && ub + 3 < Up)
+                val = __ldg(reinterpret_cast<const float4 *>(sino + (size_t)v * Up + ub));
+            *reinterpret_cast<float4 *>(&win[buf][vv][4 * k4]) = val;
+        }
+    };
+
+    stage(0);
+    __syncthreads();
+    int bad = 0;
+    for (int c = 0; c < nchunks; ++c) {
+        const int buf = c & 1;
+        if (c + 1 < nchunks) stage(c + 1);   // other buffer; its previous readers finished at the last barrier
+        const int nv = min(kBwdViewChunk, P.V - c * kBwdViewChunk);
+        for (int vv = 0; vv < nv; ++vv) {
+            const ViewP &vp = vsh[buf][vv];
+            const int lo = ulo_sh[buf][vv];
+            const float *w_row = win[buf][vv];
+#pragma unroll
+            for (int e = 0; e < kBwdPixPerThread; ++e) {
+                const float tc = det_coord(vp, Xj, Yi[e]);
+                const int ur = __float2int_rn(__fadd_rn(tc, P.uc));
+#pragma unroll
+                for (int k = -1; k <= 1; ++k) {
+                    const int uu = ur + k;
+                    const float w = weight(__fsub_rn(bin_pos(uu, P.uc), tc), vp);
+                    const int idx = uu - lo;
+                    if ((unsigned)idx < (unsigned)kBwdWin) acc[e] = __fmaf_rn(w, w_row[idx], acc[e]);
+                    else bad = 1;
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (bad) atomicExch(&bad_sh, 1);
+    __syncthreads();
+
+    float *out = (mode == BWD_G) ? P.g : (mode == BWD_H ? P.h : P.g);
+#pragma unroll
+    for (int e = 0; e < kBwdPixPerThread; ++e) {
+        const int i = i0 + ly + 8 * e;
+        if (i < P.ny && j < P.nx) out[(size_t)i * P.nxp + j] = acc[e];
+    }
+    if (t == 0 && bad_sh && P.sc) atomicExch(&P.sc->status, (int)SUPCG_ERR_UNSUPPORTED);
+}
+
+int launch_backward(const Launch &L, int mode)
+{
+    k_backward<<<L.blocks, kBwdThreads, 0, L.st>>>(L.probs, L.prefix, L.count, mode);
+    SUPCG_CUDA_TRY(cudaGetLastError());
+    return SUPCG_OK;
+}
+
+} // namespace supcg

@@ -1,0 +1,260 @@
+// Total variation, its nonascending vector and S_TV (Sec. 3.1, Algorithm 1).
+//
+//   TV(y) = sum_{i<ny-1, j<nx-1} sqrt((y_ij - y_i+1,j)^2 + (y_ij - y_i,j+1)^2)
+//   tbar_p = -dTV/dy_p where the partial exists (every TV term containing y_p
+//            has a nonzero root, i.e. not both of its differences are 0), else 0
+//   t = tbar / ||tbar||  (0 when tbar = 0)
+//
+// S_TV runs as one cooperative launch per call: each problem owns a fixed set
+// of co-resident blocks that meet at bounded device barriers, so the
+// data-dependent backtracking loop (repeat ... until TV(y~) <= TV(y)) runs
+// on the device without returning to the host.  Every block sums the
+// per-block FP64 partials in the same order, so all blocks take the same
+// accept / reject decision.
+#include "internal.cuh"
+
+namespace supcg {
+
+constexpr int kTvThreads = 256;
+
+// tbar at pixel (i, j) of y (pitch ld); *Tb receives the root of the TV term
+// whose base is (i, j) (0 if that term does not exist).
+__device__ __forceinline__ float tbar_at(const float *__restrict__ y, int ld, int ny, int nx, int i, int j,
+                                         float *Tb)
+{
+    float g = 0.0f;
+    bool undef = false;
+    float tb = 0.0f;
+    const float yc = y[(size_t)i * ld + j];
+    if (i + 1 < ny && j + 1 < nx) {
+        const float a = yc - y[(size_t)(i + 1) * ld + j], b = yc - y[(size_t)i * ld + j + 1];
+        if (a == 0.0f && b == 0.0f) undef = true;
+        else {
+            const float T = sqrtf(a * a + b * b);
+            tb = T;
+            g += (a + b) / T;
+        }
+    }
+    if (i >= 1 && j + 1 < nx) {
+        const float yu = y[(size_t)(i - 1) * ld + j];
+        const float a = yu - yc, b = yu - y[(size_t)(i - 1) * ld + j + 1];
+        if (a == 0.0f && b == 0.0f) undef = true;
+        else g -= a / sqrtf(a * a + b * b);
+    }
+    if (j >= 1 && i + 1 < ny) {
+        const float yl = y[(size_t)i * ld + j - 1];
+        const float a = yl - y[(size_t)(i + 1) * ld + j - 1], b = yl - yc;
+        if (a == 0.0f && b == 0.0f) undef = true;
+        else g -= b / sqrtf(a * a + b * b);
+    }
+    *Tb = tb;
+    return undef ? 0.0f : -g;
+}
+
+// Root of the TV term based at (i, j) of y~ = y + c tbar (term must exist).
+__device__ __forceinline__ float trial_term(const float *__restrict__ y, const float *__restrict__ t, int ld,
+                                            int i, int j, float c)
+{
+    const size_t p = (size_t)i * ld + j;
+    const float yc = __fmaf_rn(c, t[p], y[p]);
+    const float yd = __fmaf_rn(c, t[p + ld], y[p + ld]);
+    const float yr = __fmaf_rn(c, t[p + 1], y[p + 1]);
+    const float a = yc - yd, b = yc - yr;
+    return sqrtf(a * a + b * b);
+}
+
+// Standalone TV and tbar of P.x (one image per problem): writes P.tbar and
+// sc->tv_k = TV, sc->snorm2 = ||tbar||^2.
+__global__ void __launch_bounds__(kTvThreads) k_tv_tbar(const Prob *__restrict__ probs, const int *__restrict__ prefix,
+                                                        int count)
+{
+    __shared__ double red[40];
+    __shared__ int flag;
+    int local;
+    const int pi = find_problem(prefix, count, blockIdx.x, &local);
+    const Prob &P = probs[pi];
+    const int nblk = prefix[pi + 1] - prefix[pi];
+    const long long n = (long long)P.ny * P.nx;
+    double s_tv = 0.0, s_nn = 0.0;
+    for (long long e = (long long)local * kTvThreads + threadIdx.x; e < n; e += (long long)nblk * kTvThreads) {
+        const int i = (int)(e / P.nx), j = (int)(e - (long long)i * P.nx);
+        float Tb;
+        const float tb = tbar_at(P.x, P.nxp, P.ny, P.nx, i, j, &Tb);
+        P.tbar[(size_t)i * P.nxp + j] = tb;
+        s_tv += (double)Tb;
+        s_nn += (double)tb * (double)tb;
+    }
+    const double btv = block_sum<kTvThreads>(s_tv, red);
+    const double bnn = block_sum<kTvThreads>(s_nn, red);
+    if (threadIdx.x == 0) {
+        P.partial[local] = btv;
+        P.partial[nblk + local] = bnn;
+    }
+    if (last_block(&P.counter[3], nblk, &flag)) {
+        const double tv = block_sum_array<kTvThreads>(P.partial, nblk, red);
+        const double nn = block_sum_array<kTvThreads>(P.partial + nblk, nblk, red);
+        if (threadIdx.x == 0) {
+            P.sc->tv_k = tv;
+            P.sc->snorm2 = nn;
+            P.counter[3] = 0;
+        }
+    }
+}
+
+int launch_tv_tbar(const Launch &L)
+{
+    k_tv_tbar<<<L.blocks, kTvThreads, 0, L.st>>>(L.probs, L.prefix, L.count);
+    SUPCG_CUDA_TRY(cudaGetLastError());
+    return SUPCG_OK;
+}
+
+// Sum of the block partials of one phase, identical in every block.
+__device__ __forceinline__ double phase_sum(const Prob &P, int nb, int slot, int local, double v, double *red,
+                                            int *flag, bool *ok)
+{
+    const double bs = block_sum<kTvThreads>(v, red);
+    if (threadIdx.x == 0) P.partial[(size_t)slot * nb + local] = bs;
+    *ok = coop_barrier(P.bar, nb, &P.sc->status, flag);
+    if (!*ok) return 0.0;
+    return block_sum_array<kTvThreads>(P.partial + (size_t)slot * nb, nb, red);
+}
+
+// S_TV(x, l, a, gamma, K), Algorithm 1, in place on P.x (one cooperative launch).
+// trials_out (nullable): [count][K] trials of every nonascending step.
+__global__ void __launch_bounds__(kTvThreads) k_stv(const Prob *__restrict__ probs, const int *__restrict__ prefix,
+                                                    int count, int K, double a, double gamma, long long max_trials,
+                                                    int *trials_out, int want_snorm)
+{
+    __shared__ double red[40];
+    __shared__ int flag;
+    int local;
+    const int pi = find_problem(prefix, count, blockIdx.x, &local);
+    const Prob &P = probs[pi];
+    Scal *sc = P.sc;
+    if (sc->done) return;
+    const int nb = prefix[pi + 1] - prefix[pi];
+    const int nx = P.nx, ny = P.ny, ld = P.nxp;
+    const long long n = (long long)ny * nx;
+    const long long stride = (long long)nb * kTvThreads;
+    const long long e0 = (long long)local * kTvThreads + threadIdx.x;
+    float *x = P.x;
+    float *tb = P.tbar;
+    long long ell = sc->ell;
+    long long total_trials = 0;
+    double tv_first = 0.0, tv_last = 0.0;
+    int slot = 0;   // partial buffers alternate between two slots (pairs of slots for 2-value phases)
+    bool ok = true;
+
+    if (want_snorm)
+        for (long long e = e0; e < n; e += stride) {
+            const int i = (int)(e / nx), j = (int)(e - (long long)i * nx);
+            P.z[(size_t)i * ld + j] = x[(size_t)i * ld + j];
+        }
+
+    for (int step = 0; step < K && ok; ++step) {
+        // t in the nonascending set at y (Sec. 3.1)
+        double s_tv = 0.0, s_nn = 0.0;
+        for (long long e = e0; e < n; e += stride) {
+            const int i = (int)(e / nx), j = (int)(e - (long long)i * nx);
+            float Tb;
+            const float t = tbar_at(x, ld, ny, nx, i, j, &Tb);
+            tb[(size_t)i * ld + j] = t;
+            s_tv += (double)Tb;
+            s_nn += (double)t * (double)t;
+        }
+        // two sums through one barrier: slots 2*slot and 2*slot+1
+        {
+            const double b1 = block_sum<kTvThreads>(s_tv, red);
+            const double b2 = block_sum<kTvThreads>(s_nn, red);
+            if (threadIdx.x == 0) {
+                P.partial[(size_t)(4 + 2 * slot) * nb + local] = b1;
+                P.partial[(size_t)(5 + 2 * slot) * nb + local] = b2;
+            }
+            ok = coop_barrier(P.bar, nb, &sc->status, &flag);
+            if (!ok) break;
+            s_tv = block_sum_array<kTvThreads>(P.partial + (size_t)(4 + 2 * slot) * nb, nb, red);
+            s_nn = block_sum_array<kTvThreads>(P.partial + (size_t)(5 + 2 * slot) * nb, nb, red);
+            slot ^= 1;
+        }
+        const double tv_y = s_tv;
+        if (step == 0) tv_first = tv_y;
+        const double inv_norm = (s_nn > 0.0) ? 1.0 / sqrt(s_nn) : 0.0;
+        long long trials = 0;
+        float c = 0.0f;
+        double tv_t = 0.0;
+        for (;;) {
+            if (trials >= max_trials) {
+                if (local == 0 && threadIdx.x == 0) atomicExch(&sc->status, (int)SUPCG_ERR_BACKTRACK);
+                ok = false;
+                break;
+            }
+            const double gt = gamma * pow(a, (double)ell);   // gamma~ = gamma a^l
+            c = (float)(gt * inv_norm);                      // y~ = y + gamma~ tbar/||tbar||
+            ++ell;
+            ++trials;
+            double s = 0.0;
+            for (long long e = e0; e < n; e += stride) {
+                const int i = (int)(e / nx), j = (int)(e - (long long)i * nx);
+                if (i + 1 < ny && j + 1 < nx) s += (double)trial_term(x, tb, ld, i, j, c);
+            }
+            tv_t = phase_sum(P, nb, slot, local, s, red, &flag, &ok);
+            slot ^= 1;
+            if (!ok) break;
+            if (tv_t <= tv_y) break;   // until TV(y~) <= TV(y)
+        }
+        total_trials += trials;
+        if (!ok) break;
+        if (trials_out && local == 0 && threadIdx.x == 0) trials_out[(size_t)pi * K + step] = (int)trials;
+        for (long long e = e0; e < n; e += stride) {   // y <- y~
+            const int i = (int)(e / nx), j = (int)(e - (long long)i * nx);
+            const size_t p = (size_t)i * ld + j;
+            x[p] = __fmaf_rn(c, tb[p], x[p]);
+        }
+        ok = coop_barrier(P.bar, nb, &sc->status, &flag);
+        tv_last = tv_t;
+    }
+    double sn = 0.0;
+    if (ok && want_snorm) {
+        double s = 0.0;
+        for (long long e = e0; e < n; e += stride) {
+            const int i = (int)(e / nx), j = (int)(e - (long long)i * nx);
+            const size_t p = (size_t)i * ld + j;
+            const double dlt = (double)x[p] - (double)P.z[p];
+            s += dlt * dlt;
+        }
+        sn = phase_sum(P, nb, slot, local, s, red, &flag, &ok);
+    }
+    if (local == 0 && threadIdx.x == 0) {
+        sc->ell = ell;
+        sc->trials = total_trials;
+        sc->tv_k = tv_first;
+        sc->tv_half = (K > 0) ? tv_last : tv_first;
+        sc->snorm2 = sn;
+    }
+}
+
+int stv_max_blocks_per_sm(int *out)
+{
+    SUPCG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(out, k_stv, kTvThreads, 0));
+    return SUPCG_OK;
+}
+
+int launch_stv(const Launch &L, int K, double a, double gamma, long long max_trials, int *trials_out,
+               int want_snorm)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(L.blocks);
+    cfg.blockDim = dim3(kTvThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = L.st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    SUPCG_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_stv, L.probs, L.prefix, L.count, K, a, gamma, max_trials,
+                                      trials_out, want_snorm));
+    return SUPCG_OK;
+}
+
+} // namespace supcg

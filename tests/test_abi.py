@@ -1,0 +1,52 @@
+"""The C-ABI library builds, loads and exports every entry point that
+include/supcg.h declares; argument errors come back as status codes without
+touching a GPU."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+import paper_1807_10151_gb300 as S
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    src = open(os.path.join(ROOT, "include", "supcg.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(supcg_\w+)\s*\(", src)))
+
+
+def test_header_declares_the_binding_names():
+    assert declared_symbols() == sorted(S.EXPORTED)
+
+
+def test_library_exports_every_declared_symbol():
+    L = S.load()
+    for name in declared_symbols():
+        assert hasattr(L, name), name
+    out = os.popen(f"nm -D --defined-only {S.lib_path()}").read()
+    for name in declared_symbols():
+        assert re.search(rf"\bT {name}\b", out), name
+
+
+def test_argument_errors_are_status_codes():
+    L = S.load()
+    assert L.supcg_project(None, None, None, 1, None) == -1
+    assert L.supcg_backproject(None, None, None, 1, None) == -1
+    assert L.supcg_destroy_geometry(None) == -1
+    h = C.c_void_p()
+    # invalid sizes are rejected before any CUDA call
+    assert L.supcg_create_geometry(0, 4, 0.25, 4, None, 5, 0.0, 0.0, 0, C.byref(h)) == -1
+    assert L.supcg_create_geometry(4, 4, -1.0, 4, None, 5, 0.0, 0.0, 0, C.byref(h)) == -1
+    assert L.supcg_create_geometry(4, 4, 0.25, 4, None, 5, 0.0, 0.0, 7, C.byref(h)) == -1
+    assert S.supcg_status_string(-5).startswith("S_TV")
+    assert S.supcg_status_string(0) == "ok"
+
+
+def test_param_struct_layout_matches_header():
+    # offsets follow the C layout of supcg_params / supcg_report on LP64
+    assert S.Params.a.offset == 8 and S.Params.max_iter.offset == 48 and S.Params.max_trials.offset == 56
+    assert C.sizeof(S.Params) == 80
+    assert S.Report.ell.offset == 8 and C.sizeof(S.Report) == 48
