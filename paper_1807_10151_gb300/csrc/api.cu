@@ -84,6 +84,7 @@ struct Workspace {
     int *dprefix = nullptr;     // KT_COUNT x (count + 1)
     int blocks[KT_COUNT] = {};
     int smem_rows = 0, smem_cols = 0;
+    int bwin = 0;
     std::vector<void *> allocs;
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t body_exec = nullptr;
@@ -123,11 +124,12 @@ struct supcg_geometry_s {
     int nA, nB;
     int BU, BW, ntu;
     int nxp, nyp, Up;
-    float cx, cy, uc;
+    float cx, cy, uc, uc_hi, uc_lo;
+    int bwin;
     FFTPlan fx, fy;
     ViewP *dviews = nullptr;
     int *dvlist = nullptr;
-    float2 *dtwx = nullptr, *dtwy = nullptr;
+    double2 *dtwx = nullptr, *dtwy = nullptr;
     Workspace *ws_ops = nullptr;    // standalone operators, `ops_batch` images
     int ops_batch = 0;
     Workspace *ws_solve = nullptr;  // single-problem solve
@@ -157,15 +159,15 @@ static void exact_cos_sin(double th, double *c, double *s)
     }
 }
 
-static int upload_twiddles(int n, float2 **out)
+static int upload_twiddles(int n, double2 **out)
 {
-    std::vector<float2> tw(n);
+    std::vector<double2> tw(n);
     for (int k = 0; k < n; ++k) {
         const double a = -2.0 * M_PI * (double)k / (double)n;
-        tw[k] = make_float2((float)cos(a), (float)sin(a));
+        tw[k] = make_double2(cos(a), sin(a));
     }
-    SUPCG_CUDA_TRY(cudaMalloc(out, sizeof(float2) * n));
-    SUPCG_CUDA_TRY(cudaMemcpy(*out, tw.data(), sizeof(float2) * n, cudaMemcpyHostToDevice));
+    SUPCG_CUDA_TRY(cudaMalloc(out, sizeof(double2) * n));
+    SUPCG_CUDA_TRY(cudaMemcpy(*out, tw.data(), sizeof(double2) * n, cudaMemcpyHostToDevice));
     return SUPCG_OK;
 }
 
@@ -191,31 +193,47 @@ extern "C" int supcg_create_geometry(int nx, int ny, double pixel_size, int n_vi
     }
     const double r = g->d / g->ds;
     const double cx = 0.5 * (nx - 1), cy = 0.5 * (ny - 1);
+    const double uc = 0.5 * (n_bins - 1) - g->off / g->ds;
     g->cx = (float)cx; g->cy = (float)cy;
-    g->uc = (float)(0.5 * (n_bins - 1) - g->off / g->ds);
+    g->uc = (float)uc;
+    // exact split: every partial sum of u - uc_hi - cu_hi X - su_hi Y stays a
+    // multiple of 2^-Q below 2^(24-Q) in magnitude
+    const double mbound = (double)n_bins + 256.0 + fabs(uc) + r * (cx + cy + 4.0) + 8.0;
+    const int Q = (int)floor(24.0 - log2(mbound)) - 1;
+    if (Q < 4) { delete g; return SUPCG_ERR_UNSUPPORTED; }
+    auto split = [](double v, int q, float *hi, float *lo) {
+        const double h = ldexp(nearbyint(ldexp(v, q)), -q);
+        *hi = (float)h;
+        *lo = (float)(v - h);
+    };
+    split(uc, Q, &g->uc_hi, &g->uc_lo);
     g->views.resize(n_views);
     std::vector<int> A, B;
-    double maxE = 0.0, span_bwd = 0.0;
+    double maxE = 0.0, span_bwd = 0.0, max_small = fabs((double)g->uc_lo);
+    double mcl = 0.0, msl = 0.0;
     for (int v = 0; v < n_views; ++v) {
         double c, s;
         exact_cos_sin(g->theta[v], &c, &s);
         const double ac = fabs(c), as = fabs(s);
         const double a = std::max(ac, as), b = std::min(ac, as);
         ViewP vp = {};
-        vp.cu = (float)(c * r);
-        vp.su = (float)(s * r);
+        const double cu = c * r, su = s * r;
+        vp.cu = (float)cu;
+        vp.su = (float)su;
+        split(cu, Q - 1, &vp.cu_hi, &vp.cu_lo);
+        split(su, Q - 1, &vp.su_hi, &vp.su_lo);
+        mcl = std::max(mcl, fabs((double)vp.cu_lo));
+        msl = std::max(msl, fabs((double)vp.su_lo));
         vp.E = (float)(r * (a + b) / 2.0);
         vp.S = (b > 0.0) ? (float)(g->ds / (a * b)) : 0.0f;
         vp.P = (float)(g->d / a);
         const bool classB = as > ac;
         if (!classB) {
-            const double cu = c * r, su = s * r;
             vp.a_tau = (float)(1.0 / cu);
             vp.b_o = (float)(su / cu);
             vp.g0 = (float)(cx - (su / cu) * cy);
             A.push_back(v);
         } else {
-            const double cu = c * r, su = s * r;
             vp.a_tau = (float)(-1.0 / su);
             vp.b_o = (float)(cu / su);
             vp.g0 = (float)(cy - (cu / su) * cx);
@@ -226,9 +244,11 @@ extern "C" int supcg_create_geometry(int nx, int ny, double pixel_size, int n_vi
         maxE = std::max(maxE, (double)vp.E);
         span_bwd = std::max(span_bwd, (kBwdTileJ - 1) * fabs((double)vp.cu) + (kBwdTileI - 1) * fabs((double)vp.su));
     }
+    max_small += mcl * (cx + 1.0) + msl * (cy + 1.0);
     // the three bins nearest a pixel's centre must cover its footprint, and a
-    // backprojector tile must fit its shared-memory window
-    if (maxE > 1.45 || span_bwd + 9.0 > kBwdWin) { delete g; return SUPCG_ERR_UNSUPPORTED; }
+    // backprojector tile's bins must fit its shared-memory window
+    g->bwin = std::max(64, round_up((int)ceil(span_bwd + 9.0), 4));
+    if (maxE + max_small + 0.51 >= 2.0 || g->bwin > 256) { delete g; return SUPCG_ERR_UNSUPPORTED; }
     g->nA = (int)A.size();
     g->nB = (int)B.size();
     g->vlist = A;
@@ -316,11 +336,11 @@ static int ws_create(const std::vector<supcg_geometry> &gs, Workspace **out)
         nb[KT_VEC][c] = (int)(((long long)g->ny * g->nxp + 1023) / 1024);
         nb[KT_TR][c] = ((g->ny + 31) / 32) * ((g->nx + 31) / 32);
         const int rpb = std::max(1, std::min(16, 4096 / g->nx));
-        const int cw = std::max(1, std::min(16, 8192 / g->ny));
+        const int cw = std::max(1, std::min(16, 4096 / g->ny));
         nb[KT_ROWS][c] = (g->ny + rpb - 1) / rpb;
         nb[KT_COLS][c] = (g->nx + cw - 1) / cw;
-        w->smem_rows = std::max(w->smem_rows, 2 * rpb * g->nx * 8);
-        w->smem_cols = std::max(w->smem_cols, 2 * cw * g->ny * 8);
+        w->smem_rows = std::max(w->smem_rows, 2 * rpb * g->nx * 16);
+        w->smem_cols = std::max(w->smem_cols, 2 * cw * g->ny * 16);
         nb[KT_SINO][c] = (int)(((long long)g->V * g->Up + 1023) / 1024);
         npx[c] = (long long)g->nx * g->ny;
         nb[KT_STV][c] = (int)std::max(1LL, std::min<long long>((npx[c] + 1023) / 1024, stv_cap));
@@ -329,7 +349,7 @@ static int ws_create(const std::vector<supcg_geometry> &gs, Workspace **out)
         w->hp[c].fft_rpb = rpb;
         w->hp[c].fft_cw = cw;
     }
-    if (w->smem_rows > 160 * 1024 || w->smem_cols > 160 * 1024) { delete w; return SUPCG_ERR_UNSUPPORTED; }
+    if (w->smem_rows > 200 * 1024 || w->smem_cols > 200 * 1024) { delete w; return SUPCG_ERR_UNSUPPORTED; }
     // co-residency of the cooperative S_TV launch: scale down to the device capacity
     if (stv_want > stv_cap) {
         long long tot = 0;
@@ -365,7 +385,7 @@ static int ws_create(const std::vector<supcg_geometry> &gs, Workspace **out)
         const size_t npart = std::max<size_t>(8 * (size_t)nb[KT_STV][c], 2 * (size_t)maxblk) + 64;
         auto al = [](size_t b) { return (b + 255) / 256 * 256; };
         const size_t sizes[] = {img * 4, imgT * 4, img * 4, imgT * 4, img * 4, img * 4, img * 4, img * 4,
-                                sino * 4, sino * 4, sino * 4, (size_t)g->ny * g->nx * 8, sizeof(Scal),
+                                sino * 4, sino * 4, sino * 4, (size_t)g->ny * g->nx * 16, sizeof(Scal),
                                 npart * 8, 16 * 4, 4 * 4};
         size_t total = 0;
         for (size_t s : sizes) total += al(s);
@@ -379,17 +399,19 @@ static int ws_create(const std::vector<supcg_geometry> &gs, Workspace **out)
         P.x = (float *)ptrs[0]; P.xT = (float *)ptrs[1]; P.p = (float *)ptrs[2]; P.pT = (float *)ptrs[3];
         P.g = (float *)ptrs[4]; P.z = (float *)ptrs[5]; P.h = (float *)ptrs[6]; P.tbar = (float *)ptrs[7];
         P.r = (float *)ptrs[8]; P.q = (float *)ptrs[9]; P.bpad = (float *)ptrs[10];
-        P.C = (float2 *)ptrs[11]; P.sc = (Scal *)ptrs[12]; P.partial = (double *)ptrs[13];
+        P.C = (double2 *)ptrs[11]; P.sc = (Scal *)ptrs[12]; P.partial = (double *)ptrs[13];
         P.counter = (unsigned *)ptrs[14]; P.bar = (unsigned *)ptrs[15];
         P.nx = g->nx; P.ny = g->ny; P.V = g->V; P.U = g->U;
         P.nxp = g->nxp; P.nyp = g->nyp; P.Up = g->Up;
         P.BU = g->BU; P.BW = g->BW; P.ntu = g->ntu; P.nA = g->nA; P.nB = g->nB;
-        P.cx = g->cx; P.cy = g->cy; P.uc = g->uc;
+        P.cx = g->cx; P.cy = g->cy; P.uc = g->uc; P.uc_hi = g->uc_hi; P.uc_lo = g->uc_lo;
+        P.bwin = g->bwin;
+        w->bwin = std::max(w->bwin, g->bwin);
         P.views = g->dviews; P.vlist = g->dvlist;
         P.fx = g->fx; P.fy = g->fy;
         P.storage = g->storage;
         P.stv_blocks = nb[KT_STV][c];
-        P.mu = 1e-5f; P.rho = 0.8f; P.precond = 1;
+        P.mu = 1e-5; P.rho = 0.8; P.precond = 1;
         int e = 0;
         e |= encode_map(&P.tm[0], P.x, g->nx, g->ny, g->nxp, g->BW, kRowsPerChunk);
         e |= encode_map(&P.tm[1], P.xT, g->ny, g->nx, g->nyp, g->BW, kRowsPerChunk);
@@ -458,7 +480,7 @@ extern "C" int supcg_backproject(supcg_geometry g, const void *d_y, void *d_x, i
     }
     if ((rc = ws_upload(w, st))) return rc;
     if ((rc = launch_stage_sino(w->L(KT_SINO, st), 0))) return rc;
-    if ((rc = launch_backward(w->L(KT_BWD, st), BWD_PLAIN))) return rc;
+    if ((rc = launch_backward(w->L(KT_BWD, st), BWD_PLAIN, w->bwin))) return rc;
     return launch_store_out(w->L(KT_VEC, st), 1);
 }
 
@@ -488,8 +510,8 @@ extern "C" int supcg_precondition(supcg_geometry g, double mu, double rho, const
         Prob &P = w->hp[b];
         P.in_user = d_g + (size_t)b * g->nx * g->ny;
         P.out_user = d_z + (size_t)b * g->nx * g->ny;
-        P.mu = (float)mu;
-        P.rho = (float)rho;
+        P.mu = mu;
+        P.rho = rho;
         P.storage = SUPCG_F32;
     }
     rc = ws_upload(w, st);
@@ -639,13 +661,13 @@ static int enqueue_body(Workspace *w, const supcg_params *p, cudaStream_t st, in
                                               want_snorm));
     LAUNCH(SUPCG_KIND_VECTOR, st, launch_transpose(w->L(KT_TR, st), 0));
     LAUNCH(SUPCG_KIND_FORWARD, st, launch_forward(w->L(KT_FWD, st), 0, FWD_RESID));   // r = R x - b, f
-    LAUNCH(SUPCG_KIND_BACKWARD, st, launch_backward(w->L(KT_BWD, st), BWD_G));         // g = R^T r
+    LAUNCH(SUPCG_KIND_BACKWARD, st, launch_backward(w->L(KT_BWD, st), BWD_G, w->bwin));         // g = R^T r
     if (p->precondition && (rc = enqueue_precond_k(w, st))) return rc;                  // z = M g
     LAUNCH(SUPCG_KIND_VECTOR, st, launch_beta(w->L(KT_VEC, st)));               // beta = z^T h / p^T h
     LAUNCH(SUPCG_KIND_VECTOR, st, launch_pupdate(w->L(KT_VEC, st)));            // p = -z + beta p, g^T p
     LAUNCH(SUPCG_KIND_VECTOR, st, launch_transpose(w->L(KT_TR, st), 1));
     LAUNCH(SUPCG_KIND_FORWARD, st, launch_forward(w->L(KT_FWD, st), 1, FWD_NORM));    // q = R p, p^T h, alpha
-    LAUNCH(SUPCG_KIND_BACKWARD, st, launch_backward(w->L(KT_BWD, st), BWD_H));         // h = R^T q
+    LAUNCH(SUPCG_KIND_BACKWARD, st, launch_backward(w->L(KT_BWD, st), BWD_H, w->bwin));         // h = R^T q
     LAUNCH(SUPCG_KIND_VECTOR, st, launch_log(w->L(KT_VEC, st)));                // k <- k + 1
     return SUPCG_OK;
 }
@@ -655,13 +677,13 @@ static int enqueue_init(Workspace *w, const supcg_params *p, cudaStream_t st)
 {
     int rc;
     LAUNCH(SUPCG_KIND_FORWARD, st, launch_forward(w->L(KT_FWD, st), 0, FWD_RESID));
-    LAUNCH(SUPCG_KIND_BACKWARD, st, launch_backward(w->L(KT_BWD, st), BWD_G));
+    LAUNCH(SUPCG_KIND_BACKWARD, st, launch_backward(w->L(KT_BWD, st), BWD_G, w->bwin));
     if (p->precondition && (rc = enqueue_precond_k(w, st))) return rc;
     LAUNCH(SUPCG_KIND_VECTOR, st, launch_beta(w->L(KT_VEC, st)));
     LAUNCH(SUPCG_KIND_VECTOR, st, launch_pupdate(w->L(KT_VEC, st)));
     LAUNCH(SUPCG_KIND_VECTOR, st, launch_transpose(w->L(KT_TR, st), 1));
     LAUNCH(SUPCG_KIND_FORWARD, st, launch_forward(w->L(KT_FWD, st), 1, FWD_NORM));
-    LAUNCH(SUPCG_KIND_BACKWARD, st, launch_backward(w->L(KT_BWD, st), BWD_H));
+    LAUNCH(SUPCG_KIND_BACKWARD, st, launch_backward(w->L(KT_BWD, st), BWD_H, w->bwin));
     LAUNCH(SUPCG_KIND_VECTOR, st, launch_end_init(w->L(KT_VEC, st)));
     return SUPCG_OK;
 }
@@ -675,8 +697,8 @@ static int run_solve(Workspace *w, const float *const *d_b, float *const *d_x, c
         P.in_user = d_x[c];
         P.out_user = d_x[c];
         P.in_user2 = d_b[c];
-        P.mu = (float)p->mu;
-        P.rho = (float)p->rho;
+        P.mu = p->mu;
+        P.rho = p->rho;
         P.precond = p->precondition ? 1 : 0;
         P.storage = SUPCG_F32;
         P.log = (c == 0) ? d_log : nullptr;

@@ -1,34 +1,36 @@
 // Preconditioner z = M g, M = F^-1 D F (Eq. (3.2)), on the ny x nx grid.
 //
-// Three passes over a complex FP32 scratch array C [ny][nx]:
+// Three passes over a complex FP64 scratch array C [ny][nx] (FP32 vectors in
+// and out, FP64 arithmetic inside: the operator spans five decades, from
+// h(0) = mu to about pi, and an FP32 transform of a gradient dominated by its
+// low frequencies loses several digits of M g):
 //   rows:  C[i, :] = FFT(g[i, :])                    (k_fft_rows, forward)
 //   cols:  C[:, k2] = IFFT(D[:, k2] * FFT(C[:, k2]))  (k_fft_cols)
 //   rows:  z[i, :] = Re IFFT(C[i, :]) / (nx ny)        (k_fft_rows, inverse)
 // Each length is transformed in shared memory by a mixed-radix Stockham
 // (autosort) FFT: radix 4 and 2 butterflies written out, any other prime
-// factor by its defining sum.  Twiddles exp(-2 pi i k/n) come from a table
-// built on the host in FP64.  D = h(w_r), h(w) = (|w| + mu)(rho + (1-rho) cos w),
+// factor by its defining sum.  Twiddles exp(-2 pi i k/n) come from an FP64
+// table built on the host.  D = h(w_r), h(w) = (|w| + mu)(rho + (1-rho) cos w),
 // w_r the radial frequency clamped to pi, is evaluated on the fly.
 #include "internal.cuh"
 
 namespace supcg {
 
-__device__ __forceinline__ float2 cmul(float2 a, float2 b)
+__device__ __forceinline__ double2 cmul(double2 a, double2 b)
 {
-    return make_float2(__fsub_rn(__fmul_rn(a.x, b.x), __fmul_rn(a.y, b.y)),
-                       __fadd_rn(__fmul_rn(a.x, b.y), __fmul_rn(a.y, b.x)));
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
-__device__ __forceinline__ float2 twid(const float2 *tw, int e, bool inv)
+__device__ __forceinline__ double2 cadd(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 csub(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 twid(const double2 *tw, int e, bool inv)
 {
-    float2 w = __ldg(tw + e);
-    return inv ? make_float2(w.x, -w.y) : w;
+    double2 w = __ldg(tw + e);
+    return inv ? make_double2(w.x, -w.y) : w;
 }
 
 // Transforms `nvec` contiguous vectors of length pl.n held in a (b is scratch
 // of the same size).  Returns the buffer that holds the result.
-__device__ float2 *fft_smem(float2 *a, float2 *b, int nvec, const FFTPlan &pl, bool inv)
+__device__ double2 *fft_smem(double2 *a, double2 *b, int nvec, const FFTPlan &pl, bool inv)
 {
     const int n = pl.n;
     int Ns = 1;
@@ -39,20 +41,20 @@ __device__ float2 *fft_smem(float2 *a, float2 *b, int nvec, const FFTPlan &pl, b
         for (int idx = threadIdx.x; idx < nvec * m; idx += blockDim.x) {
             const int vec = idx / m, j = idx - vec * m;
             const int k = j % Ns;
-            const float2 *src = a + vec * n;
-            float2 *dst = b + vec * n + (j / Ns) * Ns * R + k;
+            const double2 *src = a + vec * n;
+            double2 *dst = b + vec * n + (j / Ns) * Ns * R + k;
             if (R == 2) {
-                float2 v0 = src[j], v1 = cmul(src[j + m], twid(pl.tw, k * stride, inv));
+                double2 v0 = src[j], v1 = cmul(src[j + m], twid(pl.tw, k * stride, inv));
                 dst[0] = cadd(v0, v1);
                 dst[Ns] = csub(v0, v1);
             } else if (R == 4) {
-                float2 v0 = src[j];
-                float2 v1 = cmul(src[j + m], twid(pl.tw, k * stride, inv));
-                float2 v2 = cmul(src[j + 2 * m], twid(pl.tw, 2 * k * stride, inv));
-                float2 v3 = cmul(src[j + 3 * m], twid(pl.tw, 3 * k * stride, inv));
-                float2 t0 = cadd(v0, v2), t1 = csub(v0, v2), t2 = cadd(v1, v3), d = csub(v1, v3);
+                double2 v0 = src[j];
+                double2 v1 = cmul(src[j + m], twid(pl.tw, k * stride, inv));
+                double2 v2 = cmul(src[j + 2 * m], twid(pl.tw, 2 * k * stride, inv));
+                double2 v3 = cmul(src[j + 3 * m], twid(pl.tw, 3 * k * stride, inv));
+                double2 t0 = cadd(v0, v2), t1 = csub(v0, v2), t2 = cadd(v1, v3), d = csub(v1, v3);
                 // multiply (v1 - v3) by the fourth root of unity -i (forward) or +i (inverse)
-                float2 t3 = inv ? make_float2(-d.y, d.x) : make_float2(d.y, -d.x);
+                double2 t3 = inv ? make_double2(-d.y, d.x) : make_double2(d.y, -d.x);
                 dst[0] = cadd(t0, t2);
                 dst[Ns] = cadd(t1, t3);
                 dst[2 * Ns] = csub(t0, t2);
@@ -61,9 +63,9 @@ __device__ float2 *fft_smem(float2 *a, float2 *b, int nvec, const FFTPlan &pl, b
                 // any radix: V_s = sum_r (src_r w^{rk}) w_R^{rs}
                 const int nR = n / R;
                 for (int so = 0; so < R; ++so) {
-                    float2 acc = make_float2(0.f, 0.f);
+                    double2 acc = make_double2(0.0, 0.0);
                     for (int r = 0; r < R; ++r) {
-                        float2 v = cmul(src[j + r * m], twid(pl.tw, r * k * stride, inv));
+                        double2 v = cmul(src[j + r * m], twid(pl.tw, r * k * stride, inv));
                         acc = cadd(acc, cmul(v, twid(pl.tw, ((r * so) % R) * nR, inv)));
                     }
                     dst[so * Ns] = acc;
@@ -71,7 +73,7 @@ __device__ float2 *fft_smem(float2 *a, float2 *b, int nvec, const FFTPlan &pl, b
             }
         }
         __syncthreads();
-        float2 *t = a;
+        double2 *t = a;
         a = b;
         b = t;
         Ns *= R;
@@ -88,22 +90,22 @@ __global__ void __launch_bounds__(256) k_fft_rows(const Prob *__restrict__ probs
     const Prob &P = probs[find_problem(prefix, count, blockIdx.x, &local)];
     if (!standalone && P.sc->done) return;
     const int nx = P.nx, rpb = P.fft_rpb;
-    float2 *a = reinterpret_cast<float2 *>(smem_raw);
-    float2 *b = a + rpb * nx;
+    double2 *a = reinterpret_cast<double2 *>(smem_raw);
+    double2 *b = a + rpb * nx;
     const int i0 = local * rpb;
     const int nr = min(rpb, P.ny - i0);
     for (int e = threadIdx.x; e < nr * nx; e += blockDim.x) {
         const int r = e / nx, q = e - r * nx;
         const size_t gi = (size_t)(i0 + r);
-        a[e] = inverse ? P.C[gi * nx + q] : make_float2(P.g[gi * P.nxp + q], 0.0f);
+        a[e] = inverse ? P.C[gi * nx + q] : make_double2((double)P.g[gi * P.nxp + q], 0.0);
     }
     __syncthreads();
-    float2 *res = fft_smem(a, b, nr, P.fx, inverse != 0);
-    const float scale = (float)(1.0 / ((double)P.nx * (double)P.ny));
+    double2 *res = fft_smem(a, b, nr, P.fx, inverse != 0);
+    const double scale = 1.0 / ((double)P.nx * (double)P.ny);
     for (int e = threadIdx.x; e < nr * nx; e += blockDim.x) {
         const int r = e / nx, q = e - r * nx;
         const size_t gi = (size_t)(i0 + r);
-        if (inverse) P.z[gi * P.nxp + q] = res[e].x * scale;
+        if (inverse) P.z[gi * P.nxp + q] = (float)(res[e].x * scale);
         else P.C[gi * nx + q] = res[e];
     }
 }
@@ -117,8 +119,8 @@ __global__ void __launch_bounds__(256) k_fft_cols(const Prob *__restrict__ probs
     const Prob &P = probs[find_problem(prefix, count, blockIdx.x, &local)];
     if (!standalone && P.sc->done) return;
     const int nx = P.nx, ny = P.ny, cw = P.fft_cw;
-    float2 *a = reinterpret_cast<float2 *>(smem_raw);
-    float2 *b = a + cw * ny;
+    double2 *a = reinterpret_cast<double2 *>(smem_raw);
+    double2 *b = a + cw * ny;
     const int c0 = local * cw;
     const int nc = min(cw, nx - c0);
     for (int e = threadIdx.x; e < nc * ny; e += blockDim.x) {
@@ -126,21 +128,21 @@ __global__ void __launch_bounds__(256) k_fft_cols(const Prob *__restrict__ probs
         a[c * ny + k1] = P.C[(size_t)k1 * nx + c0 + c];
     }
     __syncthreads();
-    float2 *res = fft_smem(a, b, nc, P.fy, false);
-    float2 *oth = (res == a) ? b : a;
-    const float two_pi = 6.28318530717958647692f;
-    const float pi_f = 3.14159265358979323846f;
+    double2 *res = fft_smem(a, b, nc, P.fy, false);
+    double2 *oth = (res == a) ? b : a;
+    const double two_pi = 6.28318530717958647692;
+    const double pi_d = 3.14159265358979323846;
     for (int e = threadIdx.x; e < nc * ny; e += blockDim.x) {
         const int c = e / ny, k1 = e - c * ny;
         const int k2 = c0 + c;
         const int m1 = min(k1, ny - k1), m2 = min(k2, nx - k2);
-        const float w1 = two_pi * (float)m1 / (float)ny, w2 = two_pi * (float)m2 / (float)nx;
-        const float wr = fminf(sqrtf(w1 * w1 + w2 * w2), pi_f);
-        const float hD = (wr + P.mu) * (P.rho + (1.0f - P.rho) * cosf(wr));
-        res[e] = make_float2(res[e].x * hD, res[e].y * hD);
+        const double w1 = two_pi * m1 / ny, w2 = two_pi * m2 / nx;
+        const double wr = fmin(sqrt(w1 * w1 + w2 * w2), pi_d);
+        const double hD = (wr + P.mu) * (P.rho + (1.0 - P.rho) * cos(wr));
+        res[e] = make_double2(res[e].x * hD, res[e].y * hD);
     }
     __syncthreads();
-    float2 *fin = fft_smem(res, oth, nc, P.fy, true);
+    double2 *fin = fft_smem(res, oth, nc, P.fy, true);
     for (int e = threadIdx.x; e < nc * ny; e += blockDim.x) {
         const int k1 = e / nc, c = e - k1 * nc;
         P.C[(size_t)k1 * nx + c0 + c] = fin[c * ny + k1];
@@ -151,7 +153,7 @@ int launch_fft_rows(const Launch &L, int inverse, int standalone, int smem)
 {
     static int set = 0;
     if (!set) {
-        SUPCG_CUDA_TRY(cudaFuncSetAttribute(k_fft_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
+        SUPCG_CUDA_TRY(cudaFuncSetAttribute(k_fft_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
         set = 1;
     }
     k_fft_rows<<<L.blocks, 256, smem, L.st>>>(L.probs, L.prefix, L.count, inverse, standalone);
@@ -163,7 +165,7 @@ int launch_fft_cols(const Launch &L, int standalone, int smem)
 {
     static int set = 0;
     if (!set) {
-        SUPCG_CUDA_TRY(cudaFuncSetAttribute(k_fft_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024));
+        SUPCG_CUDA_TRY(cudaFuncSetAttribute(k_fft_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
         set = 1;
     }
     k_fft_cols<<<L.blocks, 256, smem, L.st>>>(L.probs, L.prefix, L.count, standalone);

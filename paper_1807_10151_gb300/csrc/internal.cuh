@@ -19,25 +19,33 @@ constexpr int kRowsPerChunk = 32;    // forward projector: image rows staged per
 constexpr int kBwdTileI = 16;        // backprojector pixel tile (rows)
 constexpr int kBwdTileJ = 32;        // backprojector pixel tile (columns)
 constexpr int kBwdViewChunk = 32;    // backprojector: views staged per shared-memory chunk
-constexpr int kBwdWin = 64;          // backprojector: bins per staged window (floats)
 constexpr int kRedThreads = 256;     // block size of the reduction / vector kernels
 constexpr long long kSpinLimit = 1ll << 24;  // bounded waits (iterations of a ~100 ns poll)
 
 // ----------------------------------------------------------------- views
-// Per-view constants.  The detector coordinate of pixel (i, j) in bins is
-//   t_c(i, j) = fmaf(cu, X_j, su * Y_i),   X_j = j - (nx-1)/2,  Y_i = (ny-1)/2 - i
-// and ray (v, u) sits at tau_u = u - uc.  The intersection length of ray u with
-// pixel (i, j) is the trapezoid W(tau_u - t_c) (see weight()).  Both
-// projector kernels evaluate exactly this expression, so the backprojector
-// applies the exact transpose of the forward matrix.
+// Per-view constants.  Detector coordinates are in bins.  Pixel (i, j) has
+// centre X_j = j - (nx-1)/2, Y_i = (ny-1)/2 - i (pixel units) and ray (v, u)
+// sits at signed distance
+//   delta = u - uc - cu X_j - su Y_i            (cu = cos d/ds, su = sin d/ds)
+// from it.  delta is evaluated as big - small with cu = cu_hi + cu_lo,
+// su = su_hi + su_lo, uc = uc_hi + uc_lo, where the _hi parts are multiples
+// of 2^-(Q-1) chosen per geometry so that every partial sum of
+//   big = u - uc_hi - cu_hi X - su_hi Y
+// is a multiple of 2^-Q below 2^(24-Q) in magnitude: big is exact in FP32 in
+// any order of evaluation, and only `small` (|small| << 1) and the final
+// subtraction round.  Both projector kernels evaluate small in the same order
+// (fixed per view class), so they produce identical bits for every
+// (ray, pixel) pair: the backprojector applies the exact transpose of the
+// forward matrix.  The length is then the trapezoid weight(delta).
 struct ViewP {
-    float cu, su;   // cos(theta) d/ds, sin(theta) d/ds
+    float cu, su;   // cos(theta) d/ds, sin(theta) d/ds (approximate uses: candidate centres, boxes)
     float E;        // footprint half-width in bins: (d/ds) (|cos|+|sin|) / 2
     float S;        // ds / (|cos| |sin|): length per bin on the trapezoid's sides
     float P;        // plateau length d / max(|cos|, |sin|)
     float a_tau;    // forward: inner index of the ray centre = a_tau*tau + b_o*outer + g0
     float b_o;
     float g0;
+    float cu_hi, su_hi, cu_lo, su_lo;
     int flags;      // bit 0: axis-aligned view (cos or sin exactly 0); bit 1: class B
     int pad[3];
 };
@@ -57,9 +65,17 @@ __device__ __forceinline__ float weight(float delta, const ViewP &vp)
     return fminf(vp.P, fmaxf(0.0f, t));
 }
 
+// Approximate detector coordinate of a pixel centre (candidate selection only).
 __device__ __forceinline__ float det_coord(const ViewP &vp, float Xj, float Yi)
 {
     return __fmaf_rn(vp.cu, Xj, __fmul_rn(vp.su, Yi));
+}
+
+// The rounded part of delta: uc_lo + cu_lo X + su_lo Y, in the view class's order.
+__device__ __forceinline__ float delta_small(const ViewP &vp, float X, float Y, float uc_lo)
+{
+    return (vp.flags & kViewClassB) ? __fmaf_rn(vp.su_lo, Y, __fmaf_rn(vp.cu_lo, X, uc_lo))
+                                    : __fmaf_rn(vp.cu_lo, X, __fmaf_rn(vp.su_lo, Y, uc_lo));
 }
 
 __device__ __forceinline__ float bin_pos(int u, float uc) { return __fsub_rn(__int2float_rn(u), uc); }
@@ -69,7 +85,7 @@ struct FFTPlan {
     int n;
     int nst;
     int radix[kMaxStages];
-    const float2 *tw;   // exp(-2 pi i k / n), k = 0 .. n-1
+    const double2 *tw;  // exp(-2 pi i k / n), k = 0 .. n-1 (FP64)
 };
 
 // ----------------------------------------------------------------- scalars
@@ -101,11 +117,13 @@ struct Prob {
     int nxp, nyp, Up;      // pitches in elements: image, transposed image, sinogram
     int BU, BW, ntu;       // forward tiling: bins per block, box width, bin tiles per view
     int nA, nB;            // number of class-A / class-B views
-    float cx, cy, uc;
+    float cx, cy, uc;      // uc = (U-1)/2 - off/ds (approximate uses)
+    float uc_hi, uc_lo;    // exact split of uc (see ViewP)
+    int bwin;              // backprojector: bins staged per view and tile (multiple of 4)
     const ViewP *views;    // [V]
     const int *vlist;      // [nA + nB]: class-A views, then class-B views
     FFTPlan fx, fy;
-    float mu, rho;
+    double mu, rho;
     int precond;           // 1: M of Eq. (3.2); 0: M = I
     int storage;           // SUPCG_F32 / SUPCG_BF16 element type of in_user / out_user
     int stv_blocks;        // cooperative S_TV: blocks owned by this problem
@@ -113,7 +131,7 @@ struct Prob {
     // solve buffers (images pitch nxp, transposed pitch nyp, sinograms pitch Up)
     float *x, *xT, *p, *pT, *g, *z, *h, *tbar;
     float *r, *q, *bpad;
-    float2 *C;             // FFT scratch [ny][nx]
+    double2 *C;            // FFT scratch [ny][nx] (FP64 complex)
     Scal *sc;
     double *partial;       // reduction partials (>= 2 * max blocks per kernel)
     unsigned *counter;     // last-block tickets [8]
@@ -294,7 +312,7 @@ struct Launch {
 };
 
 int launch_forward(const Launch &L, int which, int mode);
-int launch_backward(const Launch &L, int mode);
+int launch_backward(const Launch &L, int mode, int bwin);
 int launch_transpose(const Launch &L, int which);          // x -> x^T (which 0) or p -> p^T (which 1)
 int launch_stage_in(const Launch &L, int which);           // caller image -> x and x^T (0) or g (1)
 int launch_stage_sino(const Launch &L, int which);         // caller sinogram -> r (0, in_user) or bpad (1, in_user2)

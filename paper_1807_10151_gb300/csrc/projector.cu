@@ -21,7 +21,7 @@ namespace supcg {
 
 // ============================================================ forward
 template <bool CLASS_B>
-__device__ __forceinline__ float fwd_rows(const Prob &P, const ViewP &vp, float tau, float base_u, int o0,
+__device__ __forceinline__ float fwd_rows(const Prob &P, const ViewP &vp, float tau_hi, float base_u, int o0,
                                           int rows, int qs, const float *patch, int *bad)
 {
     float acc = 0.0f;
@@ -34,25 +34,30 @@ __device__ __forceinline__ float fwd_rows(const Prob &P, const ViewP &vp, float 
         const float *row = patch + r * BW - qs;
         if (!CLASS_B) {
             // class A: outer = image row i = o, inner = column j = q
-            const float Yo = __fsub_rn(P.cy, of);
-            const float suY = __fmul_rn(vp.su, Yo);
+            const float Y = __fsub_rn(P.cy, of);
+            const float rbig = __fmaf_rn(-vp.su_hi, Y, tau_hi);      // exact
+            const float rsmall = __fmaf_rn(vp.su_lo, Y, P.uc_lo);
 #pragma unroll
             for (int k = -1; k <= 1; ++k) {
                 const int q = qc + k;
-                const float Xq = __fsub_rn(__int2float_rn(q), P.cx);
-                const float w = weight(__fsub_rn(tau, __fmaf_rn(vp.cu, Xq, suY)), vp);
+                const float X = __fsub_rn(__int2float_rn(q), P.cx);
+                const float big = __fmaf_rn(-vp.cu_hi, X, rbig);       // exact
+                const float w = weight(__fsub_rn(big, __fmaf_rn(vp.cu_lo, X, rsmall)), vp);
                 const int idx = q - qs;
                 if ((unsigned)idx < (unsigned)BW) acc = __fmaf_rn(w, row[q], acc);
                 else *bad = 1;
             }
         } else {
             // class B: outer = image column j = o, inner = row i = q (patch from x^T)
-            const float Xo = __fsub_rn(of, P.cx);
+            const float X = __fsub_rn(of, P.cx);
+            const float rbig = __fmaf_rn(-vp.cu_hi, X, tau_hi);      // exact
+            const float rsmall = __fmaf_rn(vp.cu_lo, X, P.uc_lo);
 #pragma unroll
             for (int k = -1; k <= 1; ++k) {
                 const int q = qc + k;
-                const float Yq = __fsub_rn(P.cy, __int2float_rn(q));
-                const float w = weight(__fsub_rn(tau, det_coord(vp, Xo, Yq)), vp);
+                const float Y = __fsub_rn(P.cy, __int2float_rn(q));
+                const float big = __fmaf_rn(-vp.su_hi, Y, rbig);       // exact
+                const float w = weight(__fsub_rn(big, __fmaf_rn(vp.su_lo, Y, rsmall)), vp);
                 const int idx = q - qs;
                 if ((unsigned)idx < (unsigned)BW) acc = __fmaf_rn(w, row[q], acc);
                 else *bad = 1;
@@ -104,6 +109,7 @@ __global__ void __launch_bounds__(128) k_forward(const Prob *__restrict__ probs,
     const int u_last = min(P.U, u_first + P.BU) - 1;
     const int u = u_first + t;
     const float tau = bin_pos(u, P.uc);
+    const float tau_hi = bin_pos(u, P.uc_hi);   // exact
     const float base_u = __fmaf_rn(vp.a_tau, tau, vp.g0);
     const float tf = bin_pos(u_first, P.uc), tl = bin_pos(u_last, P.uc);
     const int nchunks = (n_outer + RC - 1) / RC;
@@ -122,7 +128,7 @@ __global__ void __launch_bounds__(128) k_forward(const Prob *__restrict__ probs,
         }
     }
 
-    float acc = 0.0f;
+    double acc = 0.0;   // FP64 sum of the FP32 partial sums of each 32-row chunk
     int bad = 0;
     bool timed_out = false;
     for (int c = 0; c < nchunks; ++c) {
@@ -132,8 +138,8 @@ __global__ void __launch_bounds__(128) k_forward(const Prob *__restrict__ probs,
         const int rows = min(RC, n_outer - o0);
         const int qs = fwd_box_start(vp, tf, tl, P.uc, o0);
         if (u <= u_last) {
-            if (classB) acc += fwd_rows<true>(P, vp, tau, base_u, o0, rows, qs, patch0 + buf * box_elems, &bad);
-            else acc += fwd_rows<false>(P, vp, tau, base_u, o0, rows, qs, patch0 + buf * box_elems, &bad);
+            if (classB) acc += (double)fwd_rows<true>(P, vp, tau_hi, base_u, o0, rows, qs, patch0 + buf * box_elems, &bad);
+            else acc += (double)fwd_rows<false>(P, vp, tau_hi, base_u, o0, rows, qs, patch0 + buf * box_elems, &bad);
         }
         __syncthreads();   // every thread is done with this buffer
         if (t == 0 && c + 2 < nchunks) {
@@ -157,17 +163,18 @@ __global__ void __launch_bounds__(128) k_forward(const Prob *__restrict__ probs,
     if (u <= u_last) {
         if (mode == FWD_PLAIN) {
             const size_t o = (size_t)v * P.U + u;
-            if (P.storage == SUPCG_BF16) reinterpret_cast<__nv_bfloat16 *>(P.out_user)[o] = __float2bfloat16_rn(acc);
-            else reinterpret_cast<float *>(P.out_user)[o] = acc;
+            if (P.storage == SUPCG_BF16) reinterpret_cast<__nv_bfloat16 *>(P.out_user)[o] = __double2bfloat16(acc);
+            else reinterpret_cast<float *>(P.out_user)[o] = (float)acc;
         } else if (mode == FWD_RESID) {
             const size_t o = (size_t)v * P.Up + u;
-            const float rr = acc - P.bpad[o];
+            const float rr = (float)(acc - (double)P.bpad[o]);   // r = R x - b, cancellation taken in FP64
             P.r[o] = rr;
             s = (double)rr * (double)rr;
         } else {
             const size_t o = (size_t)v * P.Up + u;
-            P.q[o] = acc;
-            s = (double)acc * (double)acc;
+            const float qq = (float)acc;
+            P.q[o] = qq;
+            s = (double)qq * (double)qq;
         }
     }
     __syncthreads();
@@ -220,7 +227,7 @@ constexpr int kBwdPixPerThread = kBwdTileI * kBwdTileJ / kBwdThreads;   // 2
 __global__ void __launch_bounds__(kBwdThreads) k_backward(const Prob *__restrict__ probs,
                                                           const int *__restrict__ prefix, int count, int mode)
 {
-    __shared__ __align__(16) float win[2][kBwdViewChunk][kBwdWin];
+    extern __shared__ __align__(16) float win_raw[];   // [2][kBwdViewChunk][bwin]
     __shared__ ViewP vsh[2][kBwdViewChunk];
     __shared__ int ulo_sh[2][kBwdViewChunk];
     __shared__ int bad_sh;
@@ -230,19 +237,20 @@ __global__ void __launch_bounds__(kBwdThreads) k_backward(const Prob *__restrict
     const Prob &P = probs[pi];
     if (mode != BWD_PLAIN && P.sc->done) return;
 
+    const int bwin = P.bwin;
     const int tiles_j = (P.nx + kBwdTileJ - 1) / kBwdTileJ;
     const int ti = local / tiles_j, tj = local - ti * tiles_j;
     const int i0 = ti * kBwdTileI, j0 = tj * kBwdTileJ;
     const int t = threadIdx.x;
     const int lx = t % kBwdTileJ, ly = t / kBwdTileJ;   // ly in [0, 8)
     const int j = j0 + lx;
-    const float Xj = __fsub_rn(__int2float_rn(j), P.cx);
-    float Yi[kBwdPixPerThread];
+    const float X = __fsub_rn(__int2float_rn(j), P.cx);
+    float Y[kBwdPixPerThread];
 #pragma unroll
-    for (int e = 0; e < kBwdPixPerThread; ++e) Yi[e] = __fsub_rn(P.cy, __int2float_rn(i0 + ly + 8 * e));
-    float acc[kBwdPixPerThread];
+    for (int e = 0; e < kBwdPixPerThread; ++e) Y[e] = __fsub_rn(P.cy, __int2float_rn(i0 + ly + 8 * e));
+    double acc[kBwdPixPerThread];   // FP64 sum of the FP32 partial sums of each 32-view chunk
 #pragma unroll
-    for (int e = 0; e < kBwdPixPerThread; ++e) acc[e] = 0.0f;
+    for (int e = 0; e < kBwdPixPerThread; ++e) acc[e] = 0.0;
 
     const float *sino = (mode == BWD_G) ? P.r : (mode == BWD_H ? P.q : P.r);
     const int Up = P.Up;
@@ -269,7 +277,8 @@ __global__ void __launch_bounds__(kBwdThreads) k_backward(const Prob *__restrict
             ulo_sh[buf][t] = lo;
         }
         __syncthreads();
-        constexpr int V4 = kBwdWin / 4;
+        const int V4 = bwin >> 2;
+        float *wb = win_raw + (size_t)buf * kBwdViewChunk * bwin;
         for (int e = t; e < kBwdViewChunk * V4; e += kBwdThreads) {
             const int vv = e / V4, k4 = e - vv * V4;
             const int v = v0 + vv;
@@ -277,7 +286,7 @@ __global__ void __launch_bounds__(kBwdThreads) k_backward(const Prob *__restrict
             const int ub = ulo_sh[buf][vv] + 4 * k4;
             if (v < P.V && ub >= 0 && ub + 3 < Up)
                 val = __ldg(reinterpret_cast<const float4 *>(sino + (size_t)v * Up + ub));
-            *reinterpret_cast<float4 *>(&win[buf][vv][4 * k4]) = val;
+            *reinterpret_cast<float4 *>(wb + vv * bwin + 4 * k4) = val;
         }
     };
 
@@ -288,24 +297,32 @@ __global__ void __launch_bounds__(kBwdThreads) k_backward(const Prob *__restrict
         const int buf = c & 1;
         if (c + 1 < nchunks) stage(c + 1);   // other buffer; its previous readers finished at the last barrier
         const int nv = min(kBwdViewChunk, P.V - c * kBwdViewChunk);
+        const float *wb = win_raw + (size_t)buf * kBwdViewChunk * bwin;
+        float part[kBwdPixPerThread];
+#pragma unroll
+        for (int e = 0; e < kBwdPixPerThread; ++e) part[e] = 0.0f;
         for (int vv = 0; vv < nv; ++vv) {
             const ViewP &vp = vsh[buf][vv];
             const int lo = ulo_sh[buf][vv];
-            const float *w_row = win[buf][vv];
+            const float *w_row = wb + vv * bwin;
 #pragma unroll
             for (int e = 0; e < kBwdPixPerThread; ++e) {
-                const float tc = det_coord(vp, Xj, Yi[e]);
-                const int ur = __float2int_rn(__fadd_rn(tc, P.uc));
+                // delta = (u + pb) - small, pb = -uc_hi - cu_hi X - su_hi Y (exact)
+                const float pb = __fmaf_rn(-vp.cu_hi, X, __fmaf_rn(-vp.su_hi, Y[e], -P.uc_hi));
+                const float sm = delta_small(vp, X, Y[e], P.uc_lo);
+                const int ur = __float2int_rn(-pb);
 #pragma unroll
                 for (int k = -1; k <= 1; ++k) {
                     const int uu = ur + k;
-                    const float w = weight(__fsub_rn(bin_pos(uu, P.uc), tc), vp);
+                    const float w = weight(__fsub_rn(__fadd_rn(__int2float_rn(uu), pb), sm), vp);
                     const int idx = uu - lo;
-                    if ((unsigned)idx < (unsigned)kBwdWin) acc[e] = __fmaf_rn(w, w_row[idx], acc[e]);
+                    if ((unsigned)idx < (unsigned)bwin) part[e] = __fmaf_rn(w, w_row[idx], part[e]);
                     else bad = 1;
                 }
             }
         }
+#pragma unroll
+        for (int e = 0; e < kBwdPixPerThread; ++e) acc[e] += (double)part[e];
         __syncthreads();
     }
     if (bad) atomicExch(&bad_sh, 1);
@@ -315,14 +332,20 @@ __global__ void __launch_bounds__(kBwdThreads) k_backward(const Prob *__restrict
 #pragma unroll
     for (int e = 0; e < kBwdPixPerThread; ++e) {
         const int i = i0 + ly + 8 * e;
-        if (i < P.ny && j < P.nx) out[(size_t)i * P.nxp + j] = acc[e];
+        if (i < P.ny && j < P.nx) out[(size_t)i * P.nxp + j] = (float)acc[e];
     }
     if (t == 0 && bad_sh && P.sc) atomicExch(&P.sc->status, (int)SUPCG_ERR_UNSUPPORTED);
 }
 
-int launch_backward(const Launch &L, int mode)
+int launch_backward(const Launch &L, int mode, int bwin)
 {
-    k_backward<<<L.blocks, kBwdThreads, 0, L.st>>>(L.probs, L.prefix, L.count, mode);
+    static int set = 0;
+    if (!set) {
+        SUPCG_CUDA_TRY(cudaFuncSetAttribute(k_backward, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            2 * kBwdViewChunk * 256 * 4));
+        set = 1;
+    }
+    k_backward<<<L.blocks, kBwdThreads, 2 * kBwdViewChunk * bwin * 4, L.st>>>(L.probs, L.prefix, L.count, mode);
     SUPCG_CUDA_TRY(cudaGetLastError());
     return SUPCG_OK;
 }
