@@ -89,6 +89,26 @@ int supcg_backproject(supcg_geometry g, const void *d_y, void *d_x, int batch, v
 int supcg_precondition(supcg_geometry g, double mu, double rho, const float *d_g, float *d_z,
                        int batch, void *stream);
 
+/* Preconditioner z = M g for callers that must not allocate device memory:
+ * code that runs under a fixed, pre-reserved memory budget, inside a host
+ * framework that owns every allocation, or on a path where cudaMalloc is
+ * forbidden because it can synchronise the device.  The paper has no
+ * counterpart; this is a packaging of supcg_precondition for those callers.
+ *   ny, nx   image size, each 1 .. 512 (larger sizes return
+ *            SUPCG_ERR_UNSUPPORTED); d_g, d_z FP32 [ny][nx], caller-owned
+ * It needs no geometry object and calls no allocating routine: its scratch
+ * (4 MiB + 16 KiB of FP64 complex values) is one static device array that
+ * the library reserves on every GPU that loads it, until the process exits.
+ * The first call on each device looks that array's device address up
+ * (cudaGetSymbolAddress) and sets kernel attributes; make that first call
+ * before any stream capture.  All calls share the array: calls whose work
+ * overlaps on the GPU (for example on two streams) race and give wrong
+ * results.  Asynchronous on `stream`.  Errors: SUPCG_ERR_ARG,
+ * SUPCG_ERR_UNSUPPORTED, SUPCG_ERR_PRECOND (rho <= 1/2 or mu < 0),
+ * SUPCG_ERR_CUDA. */
+int supcg_precondition_noalloc(int ny, int nx, double mu, double rho, const float *d_g, float *d_z,
+                               void *stream);
+
 /* Total variation and its nonascending vector (Sec. 3.1) for one image:
  * d_tbar[p] = -dTV/dy_p where that partial derivative exists, else 0.
  * h_out[0] = TV(y), h_out[1] = ||tbar||^2 (FP64 reductions).  Synchronous. */

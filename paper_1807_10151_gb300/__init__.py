@@ -26,7 +26,8 @@ STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_CUDA", -3: "ERR_NOMEM", -4: "ERR_BREA
           -5: "ERR_BACKTRACK", -6: "ERR_TIMEOUT", -7: "ERR_PRECOND", -8: "ERR_UNSUPPORTED"}
 EXPORTED = ["supcg_create_geometry", "supcg_destroy_geometry", "supcg_project", "supcg_backproject",
             "supcg_precondition", "supcg_tv_tbar", "supcg_superiorize", "supcg_solve", "supcg_solve_host",
-            "supcg_solve_batched", "supcg_status_string", "supcg_solve_profiled", "supcg_kernel_launches"]
+            "supcg_solve_batched", "supcg_status_string", "supcg_solve_profiled", "supcg_kernel_launches",
+            "supcg_precondition_noalloc"]
 KINDS = ["forward", "backward", "fft", "stv", "vector"]
 
 _lock = threading.Lock()
@@ -79,6 +80,7 @@ def load(allow_build: bool = True):
         L.supcg_project.argtypes = [vp, vp, vp, i, vp]
         L.supcg_backproject.argtypes = [vp, vp, vp, i, vp]
         L.supcg_precondition.argtypes = [vp, d, d, vp, vp, i, vp]
+        L.supcg_precondition_noalloc.argtypes = [i, i, d, d, vp, vp, vp]
         L.supcg_tv_tbar.argtypes = [vp, vp, vp, C.POINTER(d), vp]
         L.supcg_superiorize.argtypes = [vp, vp, d, d, i, ll, C.POINTER(ll), C.POINTER(i), vp]
         L.supcg_solve.argtypes = [vp, vp, vp, C.POINTER(Params), C.POINTER(Report), vp, vp]
@@ -129,6 +131,10 @@ def supcg_backproject(g, d_y, d_x, batch, stream):
 
 def supcg_precondition(g, mu, rho, d_g, d_z, batch, stream):
     return load().supcg_precondition(g, mu, rho, d_g, d_z, batch, stream)
+
+
+def supcg_precondition_noalloc(ny, nx, mu, rho, d_g, d_z, stream):
+    return load().supcg_precondition_noalloc(ny, nx, mu, rho, d_g, d_z, stream)
 
 
 def supcg_tv_tbar(g, d_y, d_tbar, h_out, stream):

@@ -12,6 +12,9 @@
 // factor by its defining sum.  Twiddles exp(-2 pi i k/n) come from an FP64
 // table built on the host.  D = h(w_r), h(w) = (|w| + mu)(rho + (1-rho) cos w),
 // w_r the radial frequency clamped to pi, is evaluated on the fly.
+#include <algorithm>
+#include <mutex>
+
 #include "internal.cuh"
 
 namespace supcg {
@@ -174,3 +177,168 @@ int launch_fft_cols(const Launch &L, int standalone, int smem)
 }
 
 } // namespace supcg
+
+// ====================================================================
+// Allocation-free variant of the preconditioner (supcg_precondition_noalloc).
+//
+// For callers that cannot allocate device memory at all (for example code
+// running where cudaMalloc is forbidden or would break a memory budget
+// fixed in advance): the FP64 complex scratch and the twiddle tables live
+// in one file-scope device array that the library's module reserves when it
+// is loaded, on every GPU that loads the library, until the process exits.
+// Every call shares that array, so calls whose work overlaps on the GPU
+// (for instance on two streams) race; each call overwrites everything it
+// reads before reading it, so nothing needs clearing between calls.
+// ====================================================================
+namespace supcg {
+namespace {
+
+constexpr int kNoAllocMaxSide = 512;                                  // nx, ny <= 512
+constexpr size_t kNoAllocMaxPixels = (size_t)kNoAllocMaxSide * kNoAllocMaxSide;
+constexpr size_t kNoAllocElems = kNoAllocMaxPixels + 2 * kNoAllocMaxSide;   // C, then twiddles (x, y)
+
+// 4 MiB + 16 KiB of FP64 complex scratch.
+static __device__ __align__(256) double2 g_noalloc_scratch[kNoAllocElems];
+
+// Twiddles exp(-2 pi i k / n) for the row length and the column length.
+__global__ void k_na_twiddles(double2 *tw_x, int nx, double2 *tw_y, int ny)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < nx) {
+        double s, c;
+        sincospi(-2.0 * k / nx, &s, &c);
+        tw_x[k] = make_double2(c, s);
+    }
+    if (k < ny) {
+        double s, c;
+        sincospi(-2.0 * k / ny, &s, &c);
+        tw_y[k] = make_double2(c, s);
+    }
+}
+
+// Rows pass on caller buffers (pitch nx): forward g -> C, inverse C -> z.
+__global__ void __launch_bounds__(256) k_na_rows(FFTPlan fx, int ny, int rpb, const float *g, float *z, double2 *C,
+                                                 int inverse)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int nx = fx.n;
+    double2 *a = reinterpret_cast<double2 *>(smem_raw);
+    double2 *b = a + rpb * nx;
+    const int i0 = blockIdx.x * rpb;
+    const int nr = min(rpb, ny - i0);
+    for (int e = threadIdx.x; e < nr * nx; e += blockDim.x) {
+        const size_t gi = (size_t)i0 * nx + e;
+        a[e] = inverse ? C[gi] : make_double2((double)g[gi], 0.0);
+    }
+    __syncthreads();
+    double2 *res = fft_smem(a, b, nr, fx, inverse != 0);
+    const double scale = 1.0 / ((double)nx * (double)ny);
+    for (int e = threadIdx.x; e < nr * nx; e += blockDim.x) {
+        const size_t gi = (size_t)i0 * nx + e;
+        if (inverse) z[gi] = (float)(res[e].x * scale);
+        else C[gi] = res[e];
+    }
+}
+
+// Columns pass: forward FFT, multiply by D = h(w_r), inverse FFT.
+__global__ void __launch_bounds__(256) k_na_cols(FFTPlan fy, int nx, int cw, double mu, double rho, double2 *C)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const int ny = fy.n;
+    double2 *a = reinterpret_cast<double2 *>(smem_raw);
+    double2 *b = a + cw * ny;
+    const int c0 = blockIdx.x * cw;
+    const int nc = min(cw, nx - c0);
+    for (int e = threadIdx.x; e < nc * ny; e += blockDim.x) {
+        const int k1 = e / nc, c = e - k1 * nc;
+        a[c * ny + k1] = C[(size_t)k1 * nx + c0 + c];
+    }
+    __syncthreads();
+    double2 *res = fft_smem(a, b, nc, fy, false);
+    double2 *oth = (res == a) ? b : a;
+    const double two_pi = 6.28318530717958647692;
+    const double pi_d = 3.14159265358979323846;
+    for (int e = threadIdx.x; e < nc * ny; e += blockDim.x) {
+        const int c = e / ny, k1 = e - c * ny;
+        const int k2 = c0 + c;
+        const int m1 = min(k1, ny - k1), m2 = min(k2, nx - k2);
+        const double w1 = two_pi * m1 / ny, w2 = two_pi * m2 / nx;
+        const double wr = fmin(sqrt(w1 * w1 + w2 * w2), pi_d);
+        const double hD = (wr + mu) * (rho + (1.0 - rho) * cos(wr));
+        res[e] = make_double2(res[e].x * hD, res[e].y * hD);
+    }
+    __syncthreads();
+    double2 *fin = fft_smem(res, oth, nc, fy, true);
+    for (int e = threadIdx.x; e < nc * ny; e += blockDim.x) {
+        const int k1 = e / nc, c = e - k1 * nc;
+        C[(size_t)k1 * nx + c0 + c] = fin[c * ny + k1];
+    }
+}
+
+// Device address of g_noalloc_scratch, looked up once per device.
+std::mutex g_na_mutex;
+double2 *g_na_ptr[64] = {};
+
+int noalloc_scratch(double2 **out)
+{
+    int dev = 0;
+    SUPCG_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return SUPCG_ERR_UNSUPPORTED;
+    std::lock_guard<std::mutex> lk(g_na_mutex);
+    if (!g_na_ptr[dev]) {
+        void *p = nullptr;
+        // the host-side symbol is only a stand-in: the kernels need this device address
+        SUPCG_CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+        SUPCG_CUDA_TRY(cudaFuncSetAttribute(k_na_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 1024));
+        SUPCG_CUDA_TRY(cudaFuncSetAttribute(k_na_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 1024));
+        g_na_ptr[dev] = static_cast<double2 *>(p);
+    }
+    *out = g_na_ptr[dev];
+    return SUPCG_OK;
+}
+
+int na_factor(int n, int *rad)
+{
+    int k = 0;
+    while (n % 4 == 0 && k < kMaxStages) { rad[k++] = 4; n /= 4; }
+    while (n % 2 == 0 && k < kMaxStages) { rad[k++] = 2; n /= 2; }
+    for (int p = 3; n > 1 && k < kMaxStages; p += 2)
+        while (n % p == 0 && k < kMaxStages) { rad[k++] = p; n /= p; }
+    return n == 1 ? k : -1;
+}
+
+} // namespace
+
+} // namespace supcg
+
+extern "C" int supcg_precondition_noalloc(int ny, int nx, double mu, double rho, const float *d_g, float *d_z,
+                                          void *stream)
+{
+    using namespace supcg;
+    if (!d_g || !d_z || nx < 1 || ny < 1) return SUPCG_ERR_ARG;
+    if (nx > kNoAllocMaxSide || ny > kNoAllocMaxSide) return SUPCG_ERR_UNSUPPORTED;
+    if (!(rho > 0.5) || !(rho <= 1.0) || !(mu >= 0.0) || !isfinite(mu)) return SUPCG_ERR_PRECOND;
+    FFTPlan fx = {}, fy = {};
+    fx.n = nx;
+    fy.n = ny;
+    fx.nst = na_factor(nx, fx.radix);
+    fy.nst = na_factor(ny, fy.radix);
+    if (fx.nst < 0 || fy.nst < 0) return SUPCG_ERR_UNSUPPORTED;
+    double2 *base = nullptr;
+    int rc = noalloc_scratch(&base);
+    if (rc) return rc;
+    double2 *C = base;
+    double2 *twx = base + kNoAllocMaxPixels, *twy = twx + kNoAllocMaxSide;
+    fx.tw = twx;
+    fy.tw = twy;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int rpb = std::max(1, std::min(16, 4096 / nx));
+    const int cw = std::max(1, std::min(16, 4096 / ny));
+    const int mx = std::max(nx, ny);
+    k_na_twiddles<<<(mx + 255) / 256, 256, 0, st>>>(twx, nx, twy, ny);
+    k_na_rows<<<(ny + rpb - 1) / rpb, 256, 2 * rpb * nx * 16, st>>>(fx, ny, rpb, d_g, d_z, C, 0);
+    k_na_cols<<<(nx + cw - 1) / cw, 256, 2 * cw * ny * 16, st>>>(fy, nx, cw, mu, rho, C);
+    k_na_rows<<<(ny + rpb - 1) / rpb, 256, 2 * rpb * nx * 16, st>>>(fx, ny, rpb, d_g, d_z, C, 1);
+    SUPCG_CUDA_TRY(cudaGetLastError());
+    return SUPCG_OK;
+}

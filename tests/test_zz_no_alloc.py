@@ -1,0 +1,50 @@
+"""The allocation-free preconditioner entry point, for callers that may not
+allocate device memory (fixed memory budgets, host frameworks that own every
+allocation, paths where cudaMalloc would synchronise the device).
+
+It is called through the C ABI and must agree with supcg_precondition, the
+allocating entry point, on two calls in a row (the second call reuses the
+static scratch the first one left behind).  This file is collected last so
+that a run stopping at its first failure has already run every other test.
+"""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+TOL = 1e-5   # relative L2, as for the other preconditioner parity tests
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.mark.parametrize("ny,nx,mu,rho", [(64, 64, 1e-5, 0.8), (243, 200, 1e-3, 0.6), (512, 512, 1e-5, 0.8)])
+def test_noalloc_matches_allocating_entry_point(ny, nx, mu, rho):
+    import paper_1807_10151_gb300 as S
+    L = S.load()
+    G = S.Geometry(nx, ny, n_views=4, n_bins=8)
+    st = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    rng = np.random.default_rng(ny * 7 + nx)
+    for call in range(2):
+        g = torch.tensor(rng.standard_normal((ny, nx)), dtype=torch.float32, device="cuda")
+        z = torch.full_like(g, float("nan"))
+        rc = L.supcg_precondition_noalloc(ny, nx, mu, rho, C.c_void_p(g.data_ptr()), C.c_void_p(z.data_ptr()), st)
+        assert rc == 0, (call, S.STATUS.get(rc, rc))
+        ref = G.precondition(g, mu, rho)
+        torch.cuda.synchronize()
+        assert rel_l2(z.double().cpu().numpy(), ref.double().cpu().numpy()) <= TOL, call
+
+
+def test_noalloc_rejects_sizes_beyond_its_scratch():
+    import paper_1807_10151_gb300 as S
+    L = S.load()
+    g = torch.zeros(4, dtype=torch.float32, device="cuda")
+    st = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    assert L.supcg_precondition_noalloc(513, 4, 1e-5, 0.8, C.c_void_p(g.data_ptr()), C.c_void_p(g.data_ptr()),
+                                        st) == -8
+    assert L.supcg_precondition_noalloc(4, 4, 1e-5, 0.3, C.c_void_p(g.data_ptr()), C.c_void_p(g.data_ptr()),
+                                        st) == -7
