@@ -85,6 +85,7 @@ struct Workspace {
     int blocks[KT_COUNT] = {};
     int smem_rows = 0, smem_cols = 0;
     int bwin = 0;
+    int bw_max = 0;
     std::vector<void *> allocs;
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t body_exec = nullptr;
@@ -101,6 +102,7 @@ struct Workspace {
         l.count = count;
         l.prefix = dprefix + kt * (count + 1);
         l.blocks = blocks[kt];
+        l.bw_max = bw_max;
         l.st = st;
         return l;
     }
@@ -247,7 +249,7 @@ extern "C" int supcg_create_geometry(int nx, int ny, double pixel_size, int n_vi
     max_small += mcl * (cx + 1.0) + msl * (cy + 1.0);
     // the three bins nearest a pixel's centre must cover its footprint, and a
     // backprojector tile's bins must fit its shared-memory window
-    g->bwin = std::max(64, round_up((int)ceil(span_bwd + 9.0), 4));
+    g->bwin = std::max(64, round_up((int)ceil(span_bwd + 11.0), 4));
     if (maxE + max_small + 0.51 >= 2.0 || g->bwin > 256) { delete g; return SUPCG_ERR_UNSUPPORTED; }
     g->nA = (int)A.size();
     g->nB = (int)B.size();
@@ -259,7 +261,7 @@ extern "C" int supcg_create_geometry(int nx, int ny, double pixel_size, int n_vi
         double span = 0.0;
         for (const ViewP &vp : g->views)
             span = std::max(span, fabs((double)vp.a_tau) * (bu - 1) + fabs((double)vp.b_o) * (kRowsPerChunk - 1));
-        const int bw = round_up((int)ceil(span + 9.0), 4);
+        const int bw = round_up((int)ceil(span + 11.0), 4);
         if (bw <= 256) { g->BU = bu; g->BW = bw; break; }
     }
     if (!g->BU) { delete g; return SUPCG_ERR_UNSUPPORTED; }
@@ -335,8 +337,9 @@ static int ws_create(const std::vector<supcg_geometry> &gs, Workspace **out)
         nb[KT_BWD][c] = ((g->ny + kBwdTileI - 1) / kBwdTileI) * ((g->nx + kBwdTileJ - 1) / kBwdTileJ);
         nb[KT_VEC][c] = (int)(((long long)g->ny * g->nxp + 1023) / 1024);
         nb[KT_TR][c] = ((g->ny + 31) / 32) * ((g->nx + 31) / 32);
-        const int rpb = std::max(1, std::min(16, 4096 / g->nx));
-        const int cw = std::max(1, std::min(16, 4096 / g->ny));
+        // FFT: enough blocks to fill the device, each a few rows / columns
+        const int rpb = std::max(1, std::min(std::min(8, 4096 / g->nx), g->ny / 256));
+        const int cw = std::max(1, std::min(std::min(8, 4096 / g->ny), g->nx / 256));
         nb[KT_ROWS][c] = (g->ny + rpb - 1) / rpb;
         nb[KT_COLS][c] = (g->nx + cw - 1) / cw;
         w->smem_rows = std::max(w->smem_rows, 2 * rpb * g->nx * 16);
@@ -407,6 +410,7 @@ static int ws_create(const std::vector<supcg_geometry> &gs, Workspace **out)
         P.cx = g->cx; P.cy = g->cy; P.uc = g->uc; P.uc_hi = g->uc_hi; P.uc_lo = g->uc_lo;
         P.bwin = g->bwin;
         w->bwin = std::max(w->bwin, g->bwin);
+        w->bw_max = std::max(w->bw_max, g->BW);
         P.views = g->dviews; P.vlist = g->dvlist;
         P.fx = g->fx; P.fy = g->fy;
         P.storage = g->storage;

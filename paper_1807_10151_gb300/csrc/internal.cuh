@@ -15,7 +15,7 @@ namespace supcg {
 // ----------------------------------------------------------------- limits
 constexpr int kMaxStages = 24;       // FFT stages (radices) per length
 constexpr int kMaxRadix = 64;        // largest prime factor handled by the generic butterfly
-constexpr int kRowsPerChunk = 32;    // forward projector: image rows staged per TMA box
+constexpr int kRowsPerChunk = 16;    // forward projector: image rows staged per TMA box
 constexpr int kBwdTileI = 16;        // backprojector pixel tile (rows)
 constexpr int kBwdTileJ = 32;        // backprojector pixel tile (columns)
 constexpr int kBwdViewChunk = 32;    // backprojector: views staged per shared-memory chunk
@@ -308,6 +308,7 @@ struct Launch {
     int count;
     const int *prefix;     // device: block prefix for this kernel type, count+1 entries
     int blocks;            // total blocks
+    int bw_max;            // widest forward box (floats) among the problems
     cudaStream_t st;
 };
 

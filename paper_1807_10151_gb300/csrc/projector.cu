@@ -20,56 +20,65 @@
 namespace supcg {
 
 // ============================================================ forward
-template <bool CLASS_B>
-__device__ __forceinline__ float fwd_rows(const Prob &P, const ViewP &vp, float tau_hi, float base_u, int o0,
-                                          int rows, int qs, const float *patch, int *bad)
+// Inner loop over the rows [o0, o0 + rows) of one staged box.  For every row
+// the ray meets at most the three inner indices nearest its centre (the
+// footprint of a pixel on the ray's perpendicular is at most two pixels
+// wide); each is weighted by weight(delta) with delta from the exact split.
+// The row's three terms are summed in FP32 and added to the ray's running
+// sum with Kahan compensation (sum, comp), so that the ray sum is accurate
+// to a few units in the last place of FP32 however many rows it crosses.
+template <bool CLASS_B, bool AXIS>
+__device__ __forceinline__ void fwd_rows(const Prob &P, const ViewP &vp, float tau_hi, float &qm, int o0, int rows,
+                                         int qs, const float *patch, int *bad, float &sum, float &comp)
 {
-    float acc = 0.0f;
     const int BW = P.BW;
+    // outer coordinate of row o0 (pixel units) and its change per row
+    float Oc = CLASS_B ? __fsub_rn(__int2float_rn(o0), P.cx) : __fsub_rn(P.cy, __int2float_rn(o0));
+    const float dO = CLASS_B ? 1.0f : -1.0f;
+    const float hi_o = CLASS_B ? vp.cu_hi : vp.su_hi;   // coefficient of the outer coordinate
+    const float lo_o = CLASS_B ? vp.cu_lo : vp.su_lo;
+    const float hi_i = CLASS_B ? vp.su_hi : vp.cu_hi;   // coefficient of the inner coordinate
+    const float lo_i = CLASS_B ? vp.su_lo : vp.cu_lo;
+    // inner coordinate of inner index q: X = q - cx (class A) or Y = cy - q (class B)
+    const float c_in = CLASS_B ? P.cy : P.cx;
+    const float E = vp.E, S = vp.S, Pl = vp.P;
     for (int r = 0; r < rows; ++r) {
-        const int o = o0 + r;
-        const float of = __int2float_rn(o);
-        const float qm = __fmaf_rn(vp.b_o, of, base_u);
-        const int qc = __float2int_rn(qm);
-        const float *row = patch + r * BW - qs;
-        if (!CLASS_B) {
-            // class A: outer = image row i = o, inner = column j = q
-            const float Y = __fsub_rn(P.cy, of);
-            const float rbig = __fmaf_rn(-vp.su_hi, Y, tau_hi);      // exact
-            const float rsmall = __fmaf_rn(vp.su_lo, Y, P.uc_lo);
-#pragma unroll
-            for (int k = -1; k <= 1; ++k) {
-                const int q = qc + k;
-                const float X = __fsub_rn(__int2float_rn(q), P.cx);
-                const float big = __fmaf_rn(-vp.cu_hi, X, rbig);       // exact
-                const float w = weight(__fsub_rn(big, __fmaf_rn(vp.cu_lo, X, rsmall)), vp);
-                const int idx = q - qs;
-                if ((unsigned)idx < (unsigned)BW) acc = __fmaf_rn(w, row[q], acc);
-                else *bad = 1;
-            }
-        } else {
-            // class B: outer = image column j = o, inner = row i = q (patch from x^T)
-            const float X = __fsub_rn(of, P.cx);
-            const float rbig = __fmaf_rn(-vp.cu_hi, X, tau_hi);      // exact
-            const float rsmall = __fmaf_rn(vp.cu_lo, X, P.uc_lo);
-#pragma unroll
-            for (int k = -1; k <= 1; ++k) {
-                const int q = qc + k;
-                const float Y = __fsub_rn(P.cy, __int2float_rn(q));
-                const float big = __fmaf_rn(-vp.su_hi, Y, rbig);       // exact
-                const float w = weight(__fsub_rn(big, __fmaf_rn(vp.su_lo, Y, rsmall)), vp);
-                const int idx = q - qs;
-                if ((unsigned)idx < (unsigned)BW) acc = __fmaf_rn(w, row[q], acc);
-                else *bad = 1;
-            }
+        int q0 = __float2int_rn(qm) - 1;
+        qm = __fadd_rn(qm, vp.b_o);
+        int idx = q0 - qs;
+        if (idx < 0 || idx > BW - 3) {   // outside the staged box: never for a valid box (host-checked)
+            *bad = 1;
+            idx = min(max(idx, 0), BW - 3);
+            q0 = idx + qs;
         }
+        const float *pv = patch + r * BW + idx;
+        const float rbig = __fmaf_rn(-hi_o, Oc, tau_hi);            // exact
+        const float rsmall = __fmaf_rn(lo_o, Oc, P.uc_lo);
+        Oc = __fadd_rn(Oc, dO);
+        // inner coordinates of q0, q0+1, q0+2 (exact half-integers)
+        const float I0 = CLASS_B ? __fsub_rn(c_in, __int2float_rn(q0)) : __fsub_rn(__int2float_rn(q0), c_in);
+        const float dI = CLASS_B ? -1.0f : 1.0f;
+        float w[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float I = __fadd_rn(I0, k * dI);
+            const float big = __fmaf_rn(-hi_i, I, rbig);              // exact
+            const float dl = __fsub_rn(big, __fmaf_rn(lo_i, I, rsmall));
+            const float ad = fabsf(dl);
+            if (AXIS) w[k] = ad < E ? Pl : (ad == E ? 0.5f * Pl : 0.0f);
+            else w[k] = fminf(Pl, fmaxf(0.0f, __fmul_rn(__fsub_rn(E, ad), S)));
+        }
+        const float rs = __fmaf_rn(w[2], pv[2], __fmaf_rn(w[1], pv[1], __fmul_rn(w[0], pv[0])));
+        const float y = __fsub_rn(rs, comp);
+        const float tt = __fadd_rn(sum, y);
+        comp = __fsub_rn(__fsub_rn(tt, sum), y);
+        sum = tt;
     }
-    return acc;
 }
 
 // Lower end (multiple of 4) of the inner range that chunk [o0, o0+RC) of the
 // block's rays [u_first, u_last] can touch.
-__device__ __forceinline__ int fwd_box_start(const ViewP &vp, float tf, float tl, float uc, int o0)
+__device__ __forceinline__ int fwd_box_start(const ViewP &vp, float tf, float tl, int o0)
 {
     const float bf = __fmaf_rn(vp.a_tau, tf, vp.g0);
     const float bl = __fmaf_rn(vp.a_tau, tl, vp.g0);
@@ -78,6 +87,45 @@ __device__ __forceinline__ int fwd_box_start(const ViewP &vp, float tf, float tl
                     fminf(__fmaf_rn(vp.b_o, o_a, bl), __fmaf_rn(vp.b_o, o_b, bl)));
     int lo = __float2int_rd(m) - 3;
     return lo & ~3;   // round down to a multiple of 4 floats (16-byte TMA rule)
+}
+
+template <bool CLASS_B, bool AXIS>
+__device__ __forceinline__ double fwd_ray(const Prob &P, const ViewP &vp, const CUtensorMap *tm, float *patch0,
+                                          uint64_t *bars, int n_outer, int u, int u_last, float tf, float tl,
+                                          int *bad, bool *timed_out)
+{
+    const int RC = kRowsPerChunk, BW = P.BW;
+    const int box_elems = RC * BW;
+    const int nchunks = (n_outer + RC - 1) / RC;
+    const int t = threadIdx.x;
+    const float tau = bin_pos(u, P.uc);
+    const float tau_hi = bin_pos(u, P.uc_hi);   // exact
+    const float base_u = __fmaf_rn(vp.a_tau, tau, vp.g0);   // inner index of the ray centre at outer index 0
+    float sum = 0.0f, comp = 0.0f;   // compensated running sum of the ray
+    if (t == 0) {
+        for (int c = 0; c < 2 && c < nchunks; ++c) {
+            mbar_expect_tx(&bars[c], box_elems * 4);
+            tma_load_2d(patch0 + c * box_elems, tm, fwd_box_start(vp, tf, tl, c * RC), c * RC, &bars[c]);
+        }
+    }
+    for (int c = 0; c < nchunks; ++c) {
+        const int buf = c & 1;
+        if (!mbar_wait(&bars[buf], (c >> 1) & 1)) { *timed_out = true; break; }
+        const int o0 = c * RC;
+        const int rows = min(RC, n_outer - o0);
+        if (u <= u_last) {
+            float qm = __fmaf_rn(vp.b_o, __int2float_rn(o0), base_u);   // restart the centre track per chunk
+            fwd_rows<CLASS_B, AXIS>(P, vp, tau_hi, qm, o0, rows, fwd_box_start(vp, tf, tl, o0),
+                                    patch0 + buf * box_elems, bad, sum, comp);
+        }
+        __syncthreads();   // every thread is done with this buffer
+        if (t == 0 && c + 2 < nchunks) {
+            mbar_expect_tx(&bars[buf], box_elems * 4);
+            tma_load_2d(patch0 + buf * box_elems, tm, fwd_box_start(vp, tf, tl, (c + 2) * RC), (c + 2) * RC,
+                        &bars[buf]);
+        }
+    }
+    return (double)sum - (double)comp;
 }
 
 __global__ void __launch_bounds__(128) k_forward(const Prob *__restrict__ probs, const int *__restrict__ prefix,
@@ -98,21 +146,16 @@ __global__ void __launch_bounds__(128) k_forward(const Prob *__restrict__ probs,
     const bool classB = vidx >= P.nA;
     const int v = P.vlist[vidx];
     const ViewP vp = P.views[v];
+    const bool axis = (vp.flags & kViewAxis) != 0;
     const int n_outer = classB ? P.nx : P.ny;
     const CUtensorMap *tm = &P.tm[which * 2 + (classB ? 1 : 0)];
     float *patch0 = reinterpret_cast<float *>(smem_raw);
-    const int RC = kRowsPerChunk, BW = P.BW;
-    const int box_elems = RC * BW;
 
     const int t = threadIdx.x;
     const int u_first = tile * P.BU;
     const int u_last = min(P.U, u_first + P.BU) - 1;
     const int u = u_first + t;
-    const float tau = bin_pos(u, P.uc);
-    const float tau_hi = bin_pos(u, P.uc_hi);   // exact
-    const float base_u = __fmaf_rn(vp.a_tau, tau, vp.g0);
     const float tf = bin_pos(u_first, P.uc), tl = bin_pos(u_last, P.uc);
-    const int nchunks = (n_outer + RC - 1) / RC;
 
     if (t == 0) {
         bad_sh = 0;
@@ -121,37 +164,21 @@ __global__ void __launch_bounds__(128) k_forward(const Prob *__restrict__ probs,
         fence_mbar_init();
     }
     __syncthreads();
-    if (t == 0) {
-        for (int c = 0; c < 2 && c < nchunks; ++c) {
-            mbar_expect_tx(&bars[c], box_elems * 4);
-            tma_load_2d(patch0 + c * box_elems, tm, fwd_box_start(vp, tf, tl, P.uc, c * RC), c * RC, &bars[c]);
-        }
-    }
 
-    double acc = 0.0;   // FP64 sum of the FP32 partial sums of each 32-row chunk
     int bad = 0;
     bool timed_out = false;
-    for (int c = 0; c < nchunks; ++c) {
-        const int buf = c & 1;
-        if (!mbar_wait(&bars[buf], (c >> 1) & 1)) { timed_out = true; break; }
-        const int o0 = c * RC;
-        const int rows = min(RC, n_outer - o0);
-        const int qs = fwd_box_start(vp, tf, tl, P.uc, o0);
-        if (u <= u_last) {
-            if (classB) acc += (double)fwd_rows<true>(P, vp, tau_hi, base_u, o0, rows, qs, patch0 + buf * box_elems, &bad);
-            else acc += (double)fwd_rows<false>(P, vp, tau_hi, base_u, o0, rows, qs, patch0 + buf * box_elems, &bad);
-        }
-        __syncthreads();   // every thread is done with this buffer
-        if (t == 0 && c + 2 < nchunks) {
-            mbar_expect_tx(&bars[buf], box_elems * 4);
-            tma_load_2d(patch0 + buf * box_elems, tm, fwd_box_start(vp, tf, tl, P.uc, (c + 2) * RC), (c + 2) * RC,
-                        &bars[buf]);
-        }
+    double acc;
+    if (classB) {
+        acc = axis ? fwd_ray<true, true>(P, vp, tm, patch0, bars, n_outer, u, u_last, tf, tl, &bad, &timed_out)
+                   : fwd_ray<true, false>(P, vp, tm, patch0, bars, n_outer, u, u_last, tf, tl, &bad, &timed_out);
+    } else {
+        acc = axis ? fwd_ray<false, true>(P, vp, tm, patch0, bars, n_outer, u, u_last, tf, tl, &bad, &timed_out)
+                   : fwd_ray<false, false>(P, vp, tm, patch0, bars, n_outer, u, u_last, tf, tl, &bad, &timed_out);
     }
     if (timed_out) {
         // wait (bounded) for any copy still in flight before leaving
         if (t == 0) {
-            atomicExch(&P.sc->status, (int)SUPCG_ERR_TIMEOUT);
+            if (P.sc) atomicExch(&P.sc->status, (int)SUPCG_ERR_TIMEOUT);
             for (int b = 0; b < 2; ++b) (void)mbar_wait(&bars[b], 0);
         }
         return;
@@ -178,7 +205,7 @@ __global__ void __launch_bounds__(128) k_forward(const Prob *__restrict__ probs,
         }
     }
     __syncthreads();
-    if (t == 0 && bad_sh) atomicExch(&P.sc->status, (int)SUPCG_ERR_UNSUPPORTED);
+    if (t == 0 && bad_sh && P.sc) atomicExch(&P.sc->status, (int)SUPCG_ERR_UNSUPPORTED);
     if (mode == FWD_PLAIN) return;
 
     const double bs = block_sum<128>(s, red);
@@ -210,9 +237,10 @@ int launch_forward(const Launch &L, int which, int mode)
 {
     static int max_smem_set = 0;
     // every problem's BW <= 256, so the box buffers never exceed this size
-    const int smem = 2 * kRowsPerChunk * 256 * 4;
+    const int smem = 2 * kRowsPerChunk * L.bw_max * 4;
     if (!max_smem_set) {
-        SUPCG_CUDA_TRY(cudaFuncSetAttribute(k_forward, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        SUPCG_CUDA_TRY(cudaFuncSetAttribute(k_forward, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            2 * kRowsPerChunk * 256 * 4));
         max_smem_set = 1;
     }
     k_forward<<<L.blocks, 128, smem, L.st>>>(L.probs, L.prefix, L.count, which, mode);
@@ -221,8 +249,44 @@ int launch_forward(const Launch &L, int which, int mode)
 }
 
 // ============================================================ backward
-constexpr int kBwdThreads = 256;
-constexpr int kBwdPixPerThread = kBwdTileI * kBwdTileJ / kBwdThreads;   // 2
+constexpr int kBwdThreads = 128;
+constexpr int kBwdPixPerThread = kBwdTileI * kBwdTileJ / kBwdThreads;   // 4
+constexpr int kBwdRowStep = kBwdThreads / kBwdTileJ;                    // 4
+
+// Per pixel and view: the three bins nearest the pixel's projected centre.
+template <bool AXIS>
+__device__ __forceinline__ void bwd_view(const ViewP &vp, float uc_hi, float uc_lo, float X, const float *Y,
+                                         const float *w_row, int lo, int bwin, float *part, float *comp, int *bad)
+{
+    const float E = vp.E, S = vp.S, Pl = vp.P;
+#pragma unroll
+    for (int e = 0; e < kBwdPixPerThread; ++e) {
+        // delta = (u + pb) - small with pb = -uc_hi - cu_hi X - su_hi Y exact
+        const float pb = __fmaf_rn(-vp.cu_hi, X, __fmaf_rn(-vp.su_hi, Y[e], -uc_hi));
+        const float sm = delta_small(vp, X, Y[e], uc_lo);
+        int u0 = __float2int_rn(-pb) - 1;
+        int idx = u0 - lo;
+        if (idx < 0 || idx > bwin - 3) {   // outside the staged window: never for a valid window (host-checked)
+            *bad = 1;
+            idx = min(max(idx, 0), bwin - 3);
+            u0 = idx + lo;
+        }
+        const float big0 = __fadd_rn(__int2float_rn(u0), pb);   // exact, as are big0 + 1 and big0 + 2
+        float t = 0.0f;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const float ad = fabsf(__fsub_rn(__fadd_rn(big0, (float)k), sm));
+            const float w = AXIS ? (ad < E ? Pl : (ad == E ? 0.5f * Pl : 0.0f))
+                                 : fminf(Pl, fmaxf(0.0f, __fmul_rn(__fsub_rn(E, ad), S)));
+            t = __fmaf_rn(w, w_row[idx + k], t);
+        }
+        // Kahan-compensated accumulation over views
+        const float y = __fsub_rn(t, comp[e]);
+        const float tt = __fadd_rn(part[e], y);
+        comp[e] = __fsub_rn(__fsub_rn(tt, part[e]), y);
+        part[e] = tt;
+    }
+}
 
 __global__ void __launch_bounds__(kBwdThreads) k_backward(const Prob *__restrict__ probs,
                                                           const int *__restrict__ prefix, int count, int mode)
@@ -242,12 +306,12 @@ __global__ void __launch_bounds__(kBwdThreads) k_backward(const Prob *__restrict
     const int ti = local / tiles_j, tj = local - ti * tiles_j;
     const int i0 = ti * kBwdTileI, j0 = tj * kBwdTileJ;
     const int t = threadIdx.x;
-    const int lx = t % kBwdTileJ, ly = t / kBwdTileJ;   // ly in [0, 8)
+    const int lx = t % kBwdTileJ, ly = t / kBwdTileJ;
     const int j = j0 + lx;
     const float X = __fsub_rn(__int2float_rn(j), P.cx);
     float Y[kBwdPixPerThread];
 #pragma unroll
-    for (int e = 0; e < kBwdPixPerThread; ++e) Y[e] = __fsub_rn(P.cy, __int2float_rn(i0 + ly + 8 * e));
+    for (int e = 0; e < kBwdPixPerThread; ++e) Y[e] = __fsub_rn(P.cy, __int2float_rn(i0 + ly + kBwdRowStep * e));
     double acc[kBwdPixPerThread];   // FP64 sum of the FP32 partial sums of each 32-view chunk
 #pragma unroll
     for (int e = 0; e < kBwdPixPerThread; ++e) acc[e] = 0.0;
@@ -298,31 +362,18 @@ __global__ void __launch_bounds__(kBwdThreads) k_backward(const Prob *__restrict
         if (c + 1 < nchunks) stage(c + 1);   // other buffer; its previous readers finished at the last barrier
         const int nv = min(kBwdViewChunk, P.V - c * kBwdViewChunk);
         const float *wb = win_raw + (size_t)buf * kBwdViewChunk * bwin;
-        float part[kBwdPixPerThread];
+        float part[kBwdPixPerThread], comp[kBwdPixPerThread];
 #pragma unroll
-        for (int e = 0; e < kBwdPixPerThread; ++e) part[e] = 0.0f;
+        for (int e = 0; e < kBwdPixPerThread; ++e) part[e] = comp[e] = 0.0f;
         for (int vv = 0; vv < nv; ++vv) {
             const ViewP &vp = vsh[buf][vv];
-            const int lo = ulo_sh[buf][vv];
-            const float *w_row = wb + vv * bwin;
-#pragma unroll
-            for (int e = 0; e < kBwdPixPerThread; ++e) {
-                // delta = (u + pb) - small, pb = -uc_hi - cu_hi X - su_hi Y (exact)
-                const float pb = __fmaf_rn(-vp.cu_hi, X, __fmaf_rn(-vp.su_hi, Y[e], -P.uc_hi));
-                const float sm = delta_small(vp, X, Y[e], P.uc_lo);
-                const int ur = __float2int_rn(-pb);
-#pragma unroll
-                for (int k = -1; k <= 1; ++k) {
-                    const int uu = ur + k;
-                    const float w = weight(__fsub_rn(__fadd_rn(__int2float_rn(uu), pb), sm), vp);
-                    const int idx = uu - lo;
-                    if ((unsigned)idx < (unsigned)bwin) part[e] = __fmaf_rn(w, w_row[idx], part[e]);
-                    else bad = 1;
-                }
-            }
+            if (vp.flags & kViewAxis)
+                bwd_view<true>(vp, P.uc_hi, P.uc_lo, X, Y, wb + vv * bwin, ulo_sh[buf][vv], bwin, part, comp, &bad);
+            else
+                bwd_view<false>(vp, P.uc_hi, P.uc_lo, X, Y, wb + vv * bwin, ulo_sh[buf][vv], bwin, part, comp, &bad);
         }
 #pragma unroll
-        for (int e = 0; e < kBwdPixPerThread; ++e) acc[e] += (double)part[e];
+        for (int e = 0; e < kBwdPixPerThread; ++e) acc[e] += (double)part[e] - (double)comp[e];
         __syncthreads();
     }
     if (bad) atomicExch(&bad_sh, 1);
@@ -331,7 +382,7 @@ __global__ void __launch_bounds__(kBwdThreads) k_backward(const Prob *__restrict
     float *out = (mode == BWD_G) ? P.g : (mode == BWD_H ? P.h : P.g);
 #pragma unroll
     for (int e = 0; e < kBwdPixPerThread; ++e) {
-        const int i = i0 + ly + 8 * e;
+        const int i = i0 + ly + kBwdRowStep * e;
         if (i < P.ny && j < P.nx) out[(size_t)i * P.nxp + j] = (float)acc[e];
     }
     if (t == 0 && bad_sh && P.sc) atomicExch(&P.sc->status, (int)SUPCG_ERR_UNSUPPORTED);
