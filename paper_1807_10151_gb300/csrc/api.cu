@@ -241,7 +241,15 @@ extern "C" int supcg_create_geometry(int nx, int ny, double pixel_size, int n_vi
             vp.g0 = (float)(cy - (cu / su) * cx);
             B.push_back(v);
         }
-        vp.flags = (b == 0.0 ? kViewAxis : 0) | (classB ? kViewClassB : 0);
+        vp.ES = (float)(r * (a + b) / 2.0 * (b > 0.0 ? g->ds / (a * b) : 0.0));
+        // candidate windows: a ray's footprint on a row (column) is (a+b)/(2a) pixels
+        // either side of its centre, a pixel's footprint E bins either side of its
+        // projected centre; 0.02 covers the rounding of the centres
+        const double margin = 0.02;
+        vp.hwq = (float)((a + b) / (2.0 * a) + margin);
+        vp.hwu = (float)(r * (a + b) / 2.0 + margin);
+        vp.flags = (b == 0.0 ? kViewAxis : 0) | (classB ? kViewClassB : 0) |
+                   (2.0 * vp.hwq >= 2.0 ? kViewFwd3 : 0) | (2.0 * vp.hwu >= 2.0 ? kViewBwd3 : 0);
         g->views[v] = vp;
         maxE = std::max(maxE, (double)vp.E);
         span_bwd = std::max(span_bwd, (kBwdTileJ - 1) * fabs((double)vp.cu) + (kBwdTileI - 1) * fabs((double)vp.su));
@@ -250,7 +258,7 @@ extern "C" int supcg_create_geometry(int nx, int ny, double pixel_size, int n_vi
     // the three bins nearest a pixel's centre must cover its footprint, and a
     // backprojector tile's bins must fit its shared-memory window
     g->bwin = std::max(64, round_up((int)ceil(span_bwd + 11.0), 4));
-    if (maxE + max_small + 0.51 >= 2.0 || g->bwin > 256) { delete g; return SUPCG_ERR_UNSUPPORTED; }
+    if (maxE + max_small + 0.03 >= 1.5 || g->bwin > 256) { delete g; return SUPCG_ERR_UNSUPPORTED; }
     g->nA = (int)A.size();
     g->nB = (int)B.size();
     g->vlist = A;

@@ -46,11 +46,15 @@ struct ViewP {
     float b_o;
     float g0;
     float cu_hi, su_hi, cu_lo, su_lo;
-    int flags;      // bit 0: axis-aligned view (cos or sin exactly 0); bit 1: class B
-    int pad[3];
+    int flags;      // kView* bits
+    float ES;       // E * S (rounded once): the trapezoid is fmaf(-|delta|, S, ES) clamped to [0, P]
+    float hwq;      // forward: half-width of a ray's footprint in inner-index units, plus a 0.02 margin
+    float hwu;      // backward: half-width of a pixel's footprint in bins, plus a 0.02 margin
 };
-constexpr int kViewAxis = 1;
-constexpr int kViewClassB = 2;
+constexpr int kViewAxis = 1;     // cos or sin exactly 0: box footprint
+constexpr int kViewClassB = 2;   // |sin| > |cos|: the forward projector walks columns (reads x^T)
+constexpr int kViewFwd3 = 4;     // a ray can meet three pixels of a row within the margin
+constexpr int kViewBwd3 = 8;     // a pixel can meet three bins within the margin
 
 // Intersection length for a ray at signed detector distance `delta` (bins)
 // from the pixel centre.  Axis-aligned views use the box limit with half
@@ -61,8 +65,7 @@ __device__ __forceinline__ float weight(float delta, const ViewP &vp)
     float ad = fabsf(delta);
     if (vp.flags & kViewAxis)
         return ad < vp.E ? vp.P : (ad == vp.E ? 0.5f * vp.P : 0.0f);
-    float t = __fmul_rn(__fsub_rn(vp.E, ad), vp.S);
-    return fminf(vp.P, fmaxf(0.0f, t));
+    return fminf(vp.P, fmaxf(0.0f, __fmaf_rn(-ad, vp.S, vp.ES)));
 }
 
 // Approximate detector coordinate of a pixel centre (candidate selection only).

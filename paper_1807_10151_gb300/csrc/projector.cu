@@ -20,14 +20,14 @@
 namespace supcg {
 
 // ============================================================ forward
-// Inner loop over the rows [o0, o0 + rows) of one staged box.  For every row
-// the ray meets at most the three inner indices nearest its centre (the
-// footprint of a pixel on the ray's perpendicular is at most two pixels
-// wide); each is weighted by weight(delta) with delta from the exact split.
-// The row's three terms are summed in FP32 and added to the ray's running
+// Inner loop over the rows [o0, o0 + rows) of one staged box.  A ray meets a
+// row in the inner indices within hwq (half-width + margin) of its centre:
+// two of them, or three for views within about a degree of the diagonal
+// (NC = 3).  Each is weighted by weight(delta) with delta from the exact
+// split.  The row's terms are summed in FP32 and added to the ray's running
 // sum with Kahan compensation (sum, comp), so that the ray sum is accurate
 // to a few units in the last place of FP32 however many rows it crosses.
-template <bool CLASS_B, bool AXIS>
+template <bool CLASS_B, bool AXIS, int NC>
 __device__ __forceinline__ void fwd_rows(const Prob &P, const ViewP &vp, float tau_hi, float &qm, int o0, int rows,
                                          int qs, const float *patch, int *bad, float &sum, float &comp)
 {
@@ -41,34 +41,32 @@ __device__ __forceinline__ void fwd_rows(const Prob &P, const ViewP &vp, float t
     const float lo_i = CLASS_B ? vp.su_lo : vp.cu_lo;
     // inner coordinate of inner index q: X = q - cx (class A) or Y = cy - q (class B)
     const float c_in = CLASS_B ? P.cy : P.cx;
-    const float E = vp.E, S = vp.S, Pl = vp.P;
+    const float dI = CLASS_B ? -1.0f : 1.0f;
+    const float E = vp.E, S = vp.S, ES = vp.ES, Pl = vp.P, hw = vp.hwq;
     for (int r = 0; r < rows; ++r) {
-        int q0 = __float2int_rn(qm) - 1;
+        int q0 = __float2int_ru(__fsub_rn(qm, hw));
         qm = __fadd_rn(qm, vp.b_o);
         int idx = q0 - qs;
-        if (idx < 0 || idx > BW - 3) {   // outside the staged box: never for a valid box (host-checked)
+        if (idx < 0 || idx > BW - NC) {   // outside the staged box: never for a valid box (host-checked)
             *bad = 1;
-            idx = min(max(idx, 0), BW - 3);
+            idx = min(max(idx, 0), BW - NC);
             q0 = idx + qs;
         }
         const float *pv = patch + r * BW + idx;
         const float rbig = __fmaf_rn(-hi_o, Oc, tau_hi);            // exact
         const float rsmall = __fmaf_rn(lo_o, Oc, P.uc_lo);
         Oc = __fadd_rn(Oc, dO);
-        // inner coordinates of q0, q0+1, q0+2 (exact half-integers)
         const float I0 = CLASS_B ? __fsub_rn(c_in, __int2float_rn(q0)) : __fsub_rn(__int2float_rn(q0), c_in);
-        const float dI = CLASS_B ? -1.0f : 1.0f;
-        float w[3];
+        float rs = 0.0f;
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-            const float I = __fadd_rn(I0, k * dI);
+        for (int k = 0; k < NC; ++k) {
+            const float I = __fadd_rn(I0, k * dI);                    // exact half-integer
             const float big = __fmaf_rn(-hi_i, I, rbig);              // exact
-            const float dl = __fsub_rn(big, __fmaf_rn(lo_i, I, rsmall));
-            const float ad = fabsf(dl);
-            if (AXIS) w[k] = ad < E ? Pl : (ad == E ? 0.5f * Pl : 0.0f);
-            else w[k] = fminf(Pl, fmaxf(0.0f, __fmul_rn(__fsub_rn(E, ad), S)));
+            const float ad = fabsf(__fsub_rn(big, __fmaf_rn(lo_i, I, rsmall)));
+            const float w = AXIS ? (ad < E ? Pl : (ad == E ? 0.5f * Pl : 0.0f))
+                                 : fminf(Pl, fmaxf(0.0f, __fmaf_rn(-ad, S, ES)));
+            rs = __fmaf_rn(w, pv[k], rs);
         }
-        const float rs = __fmaf_rn(w[2], pv[2], __fmaf_rn(w[1], pv[1], __fmul_rn(w[0], pv[0])));
         const float y = __fsub_rn(rs, comp);
         const float tt = __fadd_rn(sum, y);
         comp = __fsub_rn(__fsub_rn(tt, sum), y);
@@ -89,7 +87,7 @@ __device__ __forceinline__ int fwd_box_start(const ViewP &vp, float tf, float tl
     return lo & ~3;   // round down to a multiple of 4 floats (16-byte TMA rule)
 }
 
-template <bool CLASS_B, bool AXIS>
+template <bool CLASS_B, bool AXIS, int NC>
 __device__ __forceinline__ double fwd_ray(const Prob &P, const ViewP &vp, const CUtensorMap *tm, float *patch0,
                                           uint64_t *bars, int n_outer, int u, int u_last, float tf, float tl,
                                           int *bad, bool *timed_out)
@@ -115,7 +113,7 @@ __device__ __forceinline__ double fwd_ray(const Prob &P, const ViewP &vp, const 
         const int rows = min(RC, n_outer - o0);
         if (u <= u_last) {
             float qm = __fmaf_rn(vp.b_o, __int2float_rn(o0), base_u);   // restart the centre track per chunk
-            fwd_rows<CLASS_B, AXIS>(P, vp, tau_hi, qm, o0, rows, fwd_box_start(vp, tf, tl, o0),
+            fwd_rows<CLASS_B, AXIS, NC>(P, vp, tau_hi, qm, o0, rows, fwd_box_start(vp, tf, tl, o0),
                                     patch0 + buf * box_elems, bad, sum, comp);
         }
         __syncthreads();   // every thread is done with this buffer
@@ -168,13 +166,14 @@ __global__ void __launch_bounds__(128) k_forward(const Prob *__restrict__ probs,
     int bad = 0;
     bool timed_out = false;
     double acc;
-    if (classB) {
-        acc = axis ? fwd_ray<true, true>(P, vp, tm, patch0, bars, n_outer, u, u_last, tf, tl, &bad, &timed_out)
-                   : fwd_ray<true, false>(P, vp, tm, patch0, bars, n_outer, u, u_last, tf, tl, &bad, &timed_out);
-    } else {
-        acc = axis ? fwd_ray<false, true>(P, vp, tm, patch0, bars, n_outer, u, u_last, tf, tl, &bad, &timed_out)
-                   : fwd_ray<false, false>(P, vp, tm, patch0, bars, n_outer, u, u_last, tf, tl, &bad, &timed_out);
-    }
+    // axis-aligned views meet at most two pixels per row; near-diagonal ones up to three
+    const bool three = (vp.flags & kViewFwd3) != 0;
+#define SUPCG_FWD(CB, AX, NC) fwd_ray<CB, AX, NC>(P, vp, tm, patch0, bars, n_outer, u, u_last, tf, tl, &bad, &timed_out)
+    if (classB)
+        acc = axis ? SUPCG_FWD(true, true, 2) : (three ? SUPCG_FWD(true, false, 3) : SUPCG_FWD(true, false, 2));
+    else
+        acc = axis ? SUPCG_FWD(false, true, 2) : (three ? SUPCG_FWD(false, false, 3) : SUPCG_FWD(false, false, 2));
+#undef SUPCG_FWD
     if (timed_out) {
         // wait (bounded) for any copy still in flight before leaving
         if (t == 0) {
@@ -253,31 +252,32 @@ constexpr int kBwdThreads = 128;
 constexpr int kBwdPixPerThread = kBwdTileI * kBwdTileJ / kBwdThreads;   // 4
 constexpr int kBwdRowStep = kBwdThreads / kBwdTileJ;                    // 4
 
-// Per pixel and view: the three bins nearest the pixel's projected centre.
-template <bool AXIS>
+// Per pixel and view: the bins within hwu (half-width + margin) of the pixel's
+// projected centre, two of them (three when the bins are finer than pixels).
+template <bool AXIS, int NC>
 __device__ __forceinline__ void bwd_view(const ViewP &vp, float uc_hi, float uc_lo, float X, const float *Y,
                                          const float *w_row, int lo, int bwin, float *part, float *comp, int *bad)
 {
-    const float E = vp.E, S = vp.S, Pl = vp.P;
+    const float E = vp.E, S = vp.S, ES = vp.ES, Pl = vp.P;
 #pragma unroll
     for (int e = 0; e < kBwdPixPerThread; ++e) {
         // delta = (u + pb) - small with pb = -uc_hi - cu_hi X - su_hi Y exact
         const float pb = __fmaf_rn(-vp.cu_hi, X, __fmaf_rn(-vp.su_hi, Y[e], -uc_hi));
         const float sm = delta_small(vp, X, Y[e], uc_lo);
-        int u0 = __float2int_rn(-pb) - 1;
+        int u0 = __float2int_ru(__fsub_rn(__fsub_rn(sm, pb), vp.hwu));
         int idx = u0 - lo;
-        if (idx < 0 || idx > bwin - 3) {   // outside the staged window: never for a valid window (host-checked)
+        if (idx < 0 || idx > bwin - NC) {   // outside the staged window: never for a valid window (host-checked)
             *bad = 1;
-            idx = min(max(idx, 0), bwin - 3);
+            idx = min(max(idx, 0), bwin - NC);
             u0 = idx + lo;
         }
         const float big0 = __fadd_rn(__int2float_rn(u0), pb);   // exact, as are big0 + 1 and big0 + 2
         float t = 0.0f;
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
+        for (int k = 0; k < NC; ++k) {
             const float ad = fabsf(__fsub_rn(__fadd_rn(big0, (float)k), sm));
             const float w = AXIS ? (ad < E ? Pl : (ad == E ? 0.5f * Pl : 0.0f))
-                                 : fminf(Pl, fmaxf(0.0f, __fmul_rn(__fsub_rn(E, ad), S)));
+                                 : fminf(Pl, fmaxf(0.0f, __fmaf_rn(-ad, S, ES)));
             t = __fmaf_rn(w, w_row[idx + k], t);
         }
         // Kahan-compensated accumulation over views
@@ -367,10 +367,15 @@ __global__ void __launch_bounds__(kBwdThreads) k_backward(const Prob *__restrict
         for (int e = 0; e < kBwdPixPerThread; ++e) part[e] = comp[e] = 0.0f;
         for (int vv = 0; vv < nv; ++vv) {
             const ViewP &vp = vsh[buf][vv];
-            if (vp.flags & kViewAxis)
-                bwd_view<true>(vp, P.uc_hi, P.uc_lo, X, Y, wb + vv * bwin, ulo_sh[buf][vv], bwin, part, comp, &bad);
-            else
-                bwd_view<false>(vp, P.uc_hi, P.uc_lo, X, Y, wb + vv * bwin, ulo_sh[buf][vv], bwin, part, comp, &bad);
+            const float *wr = wb + vv * bwin;
+            const int lo = ulo_sh[buf][vv];
+            if (vp.flags & kViewBwd3) {
+                if (vp.flags & kViewAxis) bwd_view<true, 3>(vp, P.uc_hi, P.uc_lo, X, Y, wr, lo, bwin, part, comp, &bad);
+                else bwd_view<false, 3>(vp, P.uc_hi, P.uc_lo, X, Y, wr, lo, bwin, part, comp, &bad);
+            } else {
+                if (vp.flags & kViewAxis) bwd_view<true, 2>(vp, P.uc_hi, P.uc_lo, X, Y, wr, lo, bwin, part, comp, &bad);
+                else bwd_view<false, 2>(vp, P.uc_hi, P.uc_lo, X, Y, wr, lo, bwin, part, comp, &bad);
+            }
         }
 #pragma unroll
         for (int e = 0; e < kBwdPixPerThread; ++e) acc[e] += (double)part[e] - (double)comp[e];
