@@ -9,9 +9,19 @@ Algorithm 3 (S_TV, forward projection with residual, backprojection,
 preconditioner, CG scalars and axpys, forward and back projection of p).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload plain512|batched64|large2048]
 
 --impl reference times the FP64 CPU oracle on the host cores on the same
 workload (it is the only other implementation of the method here).
+--workload batched64: 64 independent problems of uneven sizes (images
+256^2-1024^2 with 2^a 3^b 5^c sides, 180-1440 views, ceil(1.42 N) bins,
+ellipse phantoms, 1 % Gaussian noise) solved by one batched schedule, timed
+against solving them one after another (same iterates, so the time ratio is
+the time-to-equal ratio).
+--workload large2048: 8 slices of 2048^2, 2880 views, 2900 bins (40 ellipses
+on a textured background, Poisson 1e4 photons): FP32- and BF16-stored
+projector pair timed on the batch, errors of both against the FP64 oracle on
+a 256^2 / 360-view / 364-bin crop geometry.
 """
 from __future__ import annotations
 
@@ -143,6 +153,153 @@ def oracle_sample(iters):
     return {"t_build_s": t_build, "t_solve_s": t_solve, "iters": iters, "cores": O.num_threads(), "nnz": R.nnz}
 
 
+def smooth_sides(lo=256, hi=1024):
+    """Image sides in [lo, hi] of the form 2^a 3^b 5^c."""
+    out = []
+    for n in range(lo, hi + 1):
+        m = n
+        for p in (2, 3, 5):
+            while m % p == 0:
+                m //= p
+        if m == 1:
+            out.append(n)
+    return out
+
+
+def run_batched(args, dev):
+    """64 uneven problems in one batched schedule vs one at a time."""
+    import numpy as np
+    import torch
+    import paper_1807_10151_gb300 as S
+    from paper_1807_10151_gb300 import synth
+    rng = np.random.default_rng(3000)
+    sides = smooth_sides()
+    geoms, bs = [], []
+    nnz = 0.0
+    for c in range(64):
+        N = int(rng.choice(sides))
+        V = int(rng.integers(180, 1441))
+        U = int(math.ceil(1.42 * N))
+        G = S.Geometry(N, n_views=V, n_bins=U)
+        x = synth.ellipse_phantom(N, 15, 3000 + c)
+        clean = G.project(torch.tensor(x, dtype=torch.float32, device=dev)).double().cpu().numpy()
+        bs.append(torch.tensor(synth.gaussian_noise(clean, 0.01, 3500 + c), dtype=torch.float32, device=dev))
+        geoms.append(G)
+        nnz += nnz_per_projection(N, V, U)
+    kw = dict(K=WL["K"], a=WL["a"], gamma=WL["gamma"], mu=WL["mu"], rho=WL["rho"])
+    st = torch.cuda.current_stream()
+    xs = [torch.zeros(g.ny, g.nx, device=dev) for g in geoms]
+    S.solve_batched(geoms, bs, xs, max_iter=args.warmup, **kw)
+    for x in xs:
+        x.zero_()
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    l0 = S.supcg_kernel_launches()
+    with ClockSampler(dev.index or 0) as clk:
+        ev[0].record(st)
+        reps = S.solve_batched(geoms, bs, xs, max_iter=args.steps, **kw)
+        ev[1].record(st)
+        torch.cuda.synchronize()
+    launches = S.supcg_kernel_launches() - l0
+    assert all(r["status"] == 0 for r in reps), reps
+    t_batch = ev[0].elapsed_time(ev[1]) / 1000.0
+    # the same problems one after another (warm each geometry's workspace first)
+    for g, b in zip(geoms, bs):
+        g.solve(b, max_iter=1, **kw)
+    torch.cuda.synchronize()
+    ev[2].record(st)
+    for g, b in zip(geoms, bs):
+        g.solve(b, max_iter=args.steps, **kw)
+    ev[3].record(st)
+    torch.cuda.synchronize()
+    t_seq = ev[2].elapsed_time(ev[3]) / 1000.0
+    value = 64 * args.steps / t_batch
+    line = {
+        "metric": "SupPCG problem-iterations/s (batched)", "value": value, "unit": "problem-iterations/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * t_batch / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "suppcg_batched_64_uneven", "problems": 64,
+                   "sides": sorted({g.nx for g in geoms}), "views": [min(g.V for g in geoms), max(g.V for g in geoms)],
+                   "K": WL["K"], "gamma": WL["gamma"], "a": WL["a"], "mu": WL["mu"], "rho": WL["rho"],
+                   "l2": "working set of the batch (several GB) exceeds L2"},
+        "sequential": {"seconds": t_seq, "problem_iterations_per_s": 64 * args.steps / t_seq,
+                       "time_to_equal_ratio": t_seq / t_batch},
+        "intersections_per_s": 4.0 * nnz * args.steps / t_batch,
+        "gpu_launches": int(launches), "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_large(args, dev):
+    """8 slices of 2048^2: FP32 vs BF16 storage of the projector pair."""
+    import numpy as np
+    import torch
+    import paper_1807_10151_gb300 as S
+    from paper_1807_10151_gb300 import synth
+    from oracle import oracle as O
+    N, V, U, B = 2048, 2880, 2900, 8
+    st = torch.cuda.current_stream()
+    xs = []
+    for c in range(B):
+        x = synth.ellipse_phantom(N, 40, 5000 + c) + synth.textured_background(N, 5100 + c)
+        xs.append(x)
+    X = torch.tensor(np.stack(xs), dtype=torch.float32, device=dev)
+    res = {}
+    for storage, dt in (("f32", torch.float32), ("bf16", torch.bfloat16)):
+        G = S.Geometry(N, n_views=V, n_bins=U, storage=storage)
+        Xs = X.to(dt)
+        Y = G.project(Xs)
+        Z = G.backproject(Y)
+        torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ev[0].record(st)
+        for _ in range(args.steps):
+            G.project(Xs, out=Y)
+        ev[1].record(st)
+        for _ in range(args.steps):
+            G.backproject(Y, out=Z)
+        ev[2].record(st)
+        torch.cuda.synchronize()
+        res[storage] = {"project_ms": ev[0].elapsed_time(ev[1]) / args.steps,
+                        "backproject_ms": ev[1].elapsed_time(ev[2]) / args.steps}
+        G.close()
+        del Y, Z, Xs
+    # errors on the 256^2 crop geometry against the FP64 oracle
+    og = O.Geometry(256, V=360, U=364)
+    R = O.CSR(og)
+    crop = xs[0][N // 2 - 128:N // 2 + 128, N // 2 - 128:N // 2 + 128]
+    ref_p = R.project(crop.astype(np.float32).astype(np.float64))
+    yr = np.random.default_rng(9).standard_normal((og.V, og.U)).astype(np.float32)
+    ref_b = R.backproject(yr.astype(np.float64))
+    err = {}
+    for storage, dt in (("f32", torch.float32), ("bf16", torch.bfloat16)):
+        G = S.Geometry(256, n_views=360, n_bins=364, storage=storage)
+        gp = G.project(torch.tensor(crop, dtype=torch.float32, device=dev).to(dt)).double().cpu().numpy()
+        gb = G.backproject(torch.tensor(yr, device=dev).to(dt)).double().cpu().numpy()
+        # BF16 inputs are themselves rounded: compare with the oracle on the same rounded inputs
+        xin = torch.tensor(crop, dtype=torch.float32).to(dt).double().numpy()
+        yin = torch.tensor(yr).to(dt).double().numpy()
+        e_p = np.linalg.norm(gp - R.project(xin)) / np.linalg.norm(R.project(xin))
+        e_b = np.linalg.norm(gb - R.backproject(yin)) / np.linalg.norm(R.backproject(yin))
+        e_p0 = np.linalg.norm(gp - ref_p) / np.linalg.norm(ref_p)
+        e_b0 = np.linalg.norm(gb - ref_b) / np.linalg.norm(ref_b)
+        err[storage] = {"project_rel_l2_same_input": e_p, "backproject_rel_l2_same_input": e_b,
+                        "project_rel_l2_vs_fp32_input": e_p0, "backproject_rel_l2_vs_fp32_input": e_b0}
+    nnz = nnz_per_projection(N, V, U) * B
+    line = {
+        "metric": "projector pair intersections/s (2048^2 x 8 slices)",
+        "value": 2 * nnz / ((res["f32"]["project_ms"] + res["f32"]["backproject_ms"]) / 1000.0),
+        "unit": "intersections/s", "n_gpus": 1, "steps": args.steps, "warmup": 1, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "projector_2048x2048_2880views_2900bins_x8", "slices": B,
+                   "l2": "inputs (8 x 16 MB images, 8 x 33 MB sinograms) exceed L2"},
+        "timing_ms": res, "crop_errors_vs_fp64_oracle": err,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
@@ -173,6 +330,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-iters", type=int, default=3)
+    ap.add_argument("--workload", default="plain512", choices=["plain512", "batched64", "large2048"])
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world = env_int("WORLD_SIZE", 1)
@@ -195,6 +353,10 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     st = torch.cuda.current_stream()
+    if args.workload == "batched64":
+        return run_batched(args, dev)
+    if args.workload == "large2048":
+        return run_large(args, dev)
     G, b_host = make_problem(rank, dev)
     b = torch.tensor(b_host, device=dev)
 

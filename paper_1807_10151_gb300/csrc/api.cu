@@ -737,7 +737,7 @@ static int run_solve(Workspace *w, const float *const *d_b, float *const *d_x, c
     const int want_snorm = d_log != nullptr;
     const bool eps_mode = p->eps >= 0.0;
     int *hdone = nullptr;
-    if (eps_mode) SUPCG_CUDA_TRY(cudaMallocHost(&hdone, sizeof(int)));
+    if (eps_mode) SUPCG_CUDA_TRY(cudaMallocHost(&hdone, sizeof(int) * w->count));
     bool use_graph = p->graph != 0 && t_prof == nullptr;
     if (use_graph) {
         const double key[6] = {p->a, p->gamma, (double)p->max_trials, (double)p->K, (double)p->perturb,
@@ -772,10 +772,13 @@ static int run_solve(Workspace *w, const float *const *d_b, float *const *d_x, c
             SUPCG_CUDA_TRY(cudaGraphLaunch(w->body_exec, st));
             g_launches += w->body_nodes;
         } else if ((rc = enqueue_body(w, p, st, want_snorm))) return rc;
-        if (eps_mode && w->count == 1 && (it % 8 == 7)) {
-            SUPCG_CUDA_TRY(cudaMemcpyAsync(hdone, &w->hp[0].sc->done, sizeof(int), cudaMemcpyDeviceToHost, st));
+        if (eps_mode && (it % 8 == 7)) {   // stop launching once every problem has stopped
+            for (int c = 0; c < w->count; ++c)
+                SUPCG_CUDA_TRY(cudaMemcpyAsync(hdone + c, &w->hp[c].sc->done, sizeof(int), cudaMemcpyDeviceToHost, st));
             SUPCG_CUDA_TRY(cudaStreamSynchronize(st));
-            if (*hdone) break;
+            bool all = true;
+            for (int c = 0; c < w->count; ++c) all = all && hdone[c];
+            if (all) break;
         }
     }
     if (hdone) cudaFreeHost(hdone);

@@ -37,7 +37,7 @@ constexpr long long kSpinLimit = 1ll << 24;  // bounded waits (iterations of a ~
 // (fixed per view class), so they produce identical bits for every
 // (ray, pixel) pair: the backprojector applies the exact transpose of the
 // forward matrix.  The length is then the trapezoid weight(delta).
-struct ViewP {
+struct __align__(16) ViewP {
     float cu, su;   // cos(theta) d/ds, sin(theta) d/ds (approximate uses: candidate centres, boxes)
     float E;        // footprint half-width in bins: (d/ds) (|cos|+|sin|) / 2
     float S;        // ds / (|cos| |sin|): length per bin on the trapezoid's sides

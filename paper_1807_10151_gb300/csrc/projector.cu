@@ -27,8 +27,8 @@ namespace supcg {
 // split.  The row's terms are summed in FP32 and added to the ray's running
 // sum with Kahan compensation (sum, comp), so that the ray sum is accurate
 // to a few units in the last place of FP32 however many rows it crosses.
-template <bool CLASS_B, bool AXIS, int NC>
-__device__ __forceinline__ void fwd_rows(const Prob &P, const ViewP &vp, float tau_hi, float &qm, int o0, int rows,
+template <bool CLASS_B, bool AXIS, int NC, bool CHECKED>
+__device__ __forceinline__ void fwd_rows(const Prob &P, const ViewP &vp, float tau_hi, float qm, int o0, int rows,
                                          int qs, const float *patch, int *bad, float &sum, float &comp)
 {
     const int BW = P.BW;
@@ -42,22 +42,25 @@ __device__ __forceinline__ void fwd_rows(const Prob &P, const ViewP &vp, float t
     // inner coordinate of inner index q: X = q - cx (class A) or Y = cy - q (class B)
     const float c_in = CLASS_B ? P.cy : P.cx;
     const float dI = CLASS_B ? -1.0f : 1.0f;
-    const float E = vp.E, S = vp.S, ES = vp.ES, Pl = vp.P, hw = vp.hwq;
+    const float E = vp.E, S = vp.S, ES = vp.ES, Pl = vp.P;
+    const float qh = __fsub_rn(qm, vp.hwq);
+    const float *prow = patch - qs;
+    float rs = 0.0f;   // FP32 sum of up to 8 rows, then folded into (sum, comp)
+#pragma unroll 4
     for (int r = 0; r < rows; ++r) {
-        int q0 = __float2int_ru(__fsub_rn(qm, hw));
-        qm = __fadd_rn(qm, vp.b_o);
-        int idx = q0 - qs;
-        if (idx < 0 || idx > BW - NC) {   // outside the staged box: never for a valid box (host-checked)
-            *bad = 1;
-            idx = min(max(idx, 0), BW - NC);
-            q0 = idx + qs;
+        int q0 = __float2int_ru(__fmaf_rn((float)r, vp.b_o, qh));
+        if (CHECKED) {
+            const int idx = q0 - qs;
+            if (idx < 0 || idx > BW - NC) {   // outside the staged box: never for a valid box (host-checked)
+                *bad = 1;
+                q0 = min(max(idx, 0), BW - NC) + qs;
+            }
         }
-        const float *pv = patch + r * BW + idx;
+        const float *pv = prow + r * BW + q0;
         const float rbig = __fmaf_rn(-hi_o, Oc, tau_hi);            // exact
         const float rsmall = __fmaf_rn(lo_o, Oc, P.uc_lo);
         Oc = __fadd_rn(Oc, dO);
         const float I0 = CLASS_B ? __fsub_rn(c_in, __int2float_rn(q0)) : __fsub_rn(__int2float_rn(q0), c_in);
-        float rs = 0.0f;
 #pragma unroll
         for (int k = 0; k < NC; ++k) {
             const float I = __fadd_rn(I0, k * dI);                    // exact half-integer
@@ -67,10 +70,13 @@ __device__ __forceinline__ void fwd_rows(const Prob &P, const ViewP &vp, float t
                                  : fminf(Pl, fmaxf(0.0f, __fmaf_rn(-ad, S, ES)));
             rs = __fmaf_rn(w, pv[k], rs);
         }
-        const float y = __fsub_rn(rs, comp);
-        const float tt = __fadd_rn(sum, y);
-        comp = __fsub_rn(__fsub_rn(tt, sum), y);
-        sum = tt;
+        if ((r & 7) == 7 || r == rows - 1) {   // Kahan-compensated fold
+            const float y = __fsub_rn(rs, comp);
+            const float tt = __fadd_rn(sum, y);
+            comp = __fsub_rn(__fsub_rn(tt, sum), y);
+            sum = tt;
+            rs = 0.0f;
+        }
     }
 }
 
@@ -112,9 +118,20 @@ __device__ __forceinline__ double fwd_ray(const Prob &P, const ViewP &vp, const 
         const int o0 = c * RC;
         const int rows = min(RC, n_outer - o0);
         if (u <= u_last) {
-            float qm = __fmaf_rn(vp.b_o, __int2float_rn(o0), base_u);   // restart the centre track per chunk
-            fwd_rows<CLASS_B, AXIS, NC>(P, vp, tau_hi, qm, o0, rows, fwd_box_start(vp, tf, tl, o0),
-                                    patch0 + buf * box_elems, bad, sum, comp);
+            const float qm = __fmaf_rn(vp.b_o, __int2float_rn(o0), base_u);   // ray centre at row o0
+            const int qs = fwd_box_start(vp, tf, tl, o0);
+            // the first candidate is monotone in the row: its end values (with one index
+            // of slack for rounding) bound every row of the chunk
+            const float qh = __fsub_rn(qm, vp.hwq);
+            const int qa = __float2int_ru(qh) - qs;
+            const int qb = __float2int_ru(__fmaf_rn((float)(rows - 1), vp.b_o, qh)) - qs;
+            const bool inside = min(qa, qb) >= 1 && max(qa, qb) <= P.BW - NC - 1;
+            if (inside)
+                fwd_rows<CLASS_B, AXIS, NC, false>(P, vp, tau_hi, qm, o0, rows, qs, patch0 + buf * box_elems, bad,
+                                                   sum, comp);
+            else
+                fwd_rows<CLASS_B, AXIS, NC, true>(P, vp, tau_hi, qm, o0, rows, qs, patch0 + buf * box_elems, bad,
+                                                  sum, comp);
         }
         __syncthreads();   // every thread is done with this buffer
         if (t == 0 && c + 2 < nchunks) {
@@ -248,43 +265,41 @@ int launch_forward(const Launch &L, int which, int mode)
 }
 
 // ============================================================ backward
-constexpr int kBwdThreads = 128;
-constexpr int kBwdPixPerThread = kBwdTileI * kBwdTileJ / kBwdThreads;   // 4
-constexpr int kBwdRowStep = kBwdThreads / kBwdTileJ;                    // 4
+constexpr int kBwdSplit = 2;                                             // thread groups splitting the views
+constexpr int kBwdGroup = 128;                                           // threads per group
+constexpr int kBwdThreads = kBwdSplit * kBwdGroup;
+constexpr int kBwdPixPerThread = kBwdTileI * kBwdTileJ / kBwdGroup;      // 4
+constexpr int kBwdRowStep = kBwdGroup / kBwdTileJ;                       // 4
 
 // Per pixel and view: the bins within hwu (half-width + margin) of the pixel's
 // projected centre, two of them (three when the bins are finer than pixels).
-template <bool AXIS, int NC>
-__device__ __forceinline__ void bwd_view(const ViewP &vp, float uc_hi, float uc_lo, float X, const float *Y,
-                                         const float *w_row, int lo, int bwin, float *part, float *comp, int *bad)
+template <bool AXIS, int NC, bool CHECKED>
+__device__ __forceinline__ void bwd_view(const ViewP &vp, float pb0, const float *sm, const float *w_row, int lo,
+                                         int bwin, float *t, int *bad)
 {
     const float E = vp.E, S = vp.S, ES = vp.ES, Pl = vp.P;
 #pragma unroll
     for (int e = 0; e < kBwdPixPerThread; ++e) {
-        // delta = (u + pb) - small with pb = -uc_hi - cu_hi X - su_hi Y exact
-        const float pb = __fmaf_rn(-vp.cu_hi, X, __fmaf_rn(-vp.su_hi, Y[e], -uc_hi));
-        const float sm = delta_small(vp, X, Y[e], uc_lo);
-        int u0 = __float2int_ru(__fsub_rn(__fsub_rn(sm, pb), vp.hwu));
-        int idx = u0 - lo;
-        if (idx < 0 || idx > bwin - NC) {   // outside the staged window: never for a valid window (host-checked)
-            *bad = 1;
-            idx = min(max(idx, 0), bwin - NC);
-            u0 = idx + lo;
+        // delta = (u + pb) - small; pb = -uc_hi - cu_hi X - su_hi Y is exact, and so is
+        // stepping it by su_hi per pixel row
+        const float pb = __fmaf_rn((float)(kBwdRowStep * e), vp.su_hi, pb0);
+        int u0 = __float2int_ru(__fsub_rn(__fsub_rn(sm[e], pb), vp.hwu));
+        if (CHECKED) {
+            const int idx = u0 - lo;
+            if (idx < 0 || idx > bwin - NC) {   // outside the staged window: never for a valid window
+                *bad = 1;
+                u0 = min(max(idx, 0), bwin - NC) + lo;
+            }
         }
         const float big0 = __fadd_rn(__int2float_rn(u0), pb);   // exact, as are big0 + 1 and big0 + 2
-        float t = 0.0f;
+        const float *wv = w_row + (u0 - lo);
 #pragma unroll
         for (int k = 0; k < NC; ++k) {
-            const float ad = fabsf(__fsub_rn(__fadd_rn(big0, (float)k), sm));
+            const float ad = fabsf(__fsub_rn(__fadd_rn(big0, (float)k), sm[e]));
             const float w = AXIS ? (ad < E ? Pl : (ad == E ? 0.5f * Pl : 0.0f))
                                  : fminf(Pl, fmaxf(0.0f, __fmaf_rn(-ad, S, ES)));
-            t = __fmaf_rn(w, w_row[idx + k], t);
+            t[e] = __fmaf_rn(w, wv[k], t[e]);
         }
-        // Kahan-compensated accumulation over views
-        const float y = __fsub_rn(t, comp[e]);
-        const float tt = __fadd_rn(part[e], y);
-        comp[e] = __fsub_rn(__fsub_rn(tt, part[e]), y);
-        part[e] = tt;
     }
 }
 
@@ -294,6 +309,7 @@ __global__ void __launch_bounds__(kBwdThreads) k_backward(const Prob *__restrict
     extern __shared__ __align__(16) float win_raw[];   // [2][kBwdViewChunk][bwin]
     __shared__ ViewP vsh[2][kBwdViewChunk];
     __shared__ int ulo_sh[2][kBwdViewChunk];
+    __shared__ double comb[kBwdGroup * kBwdPixPerThread];   // second group's sums, combined by the first
     __shared__ int bad_sh;
 
     int local;
@@ -306,7 +322,8 @@ __global__ void __launch_bounds__(kBwdThreads) k_backward(const Prob *__restrict
     const int ti = local / tiles_j, tj = local - ti * tiles_j;
     const int i0 = ti * kBwdTileI, j0 = tj * kBwdTileJ;
     const int t = threadIdx.x;
-    const int lx = t % kBwdTileJ, ly = t / kBwdTileJ;
+    const int grp = t / kBwdGroup, tg = t - grp * kBwdGroup;   // group grp takes views vv = grp (mod kBwdSplit)
+    const int lx = tg % kBwdTileJ, ly = tg / kBwdTileJ;
     const int j = j0 + lx;
     const float X = __fsub_rn(__int2float_rn(j), P.cx);
     float Y[kBwdPixPerThread];
@@ -362,19 +379,42 @@ __global__ void __launch_bounds__(kBwdThreads) k_backward(const Prob *__restrict
         if (c + 1 < nchunks) stage(c + 1);   // other buffer; its previous readers finished at the last barrier
         const int nv = min(kBwdViewChunk, P.V - c * kBwdViewChunk);
         const float *wb = win_raw + (size_t)buf * kBwdViewChunk * bwin;
-        float part[kBwdPixPerThread], comp[kBwdPixPerThread];
+        float part[kBwdPixPerThread], comp[kBwdPixPerThread], t[kBwdPixPerThread];
 #pragma unroll
-        for (int e = 0; e < kBwdPixPerThread; ++e) part[e] = comp[e] = 0.0f;
-        for (int vv = 0; vv < nv; ++vv) {
-            const ViewP &vp = vsh[buf][vv];
+        for (int e = 0; e < kBwdPixPerThread; ++e) part[e] = comp[e] = t[e] = 0.0f;
+        for (int vv = grp; vv < nv; vv += kBwdSplit) {
+            const ViewP vp = vsh[buf][vv];
             const float *wr = wb + vv * bwin;
             const int lo = ulo_sh[buf][vv];
-            if (vp.flags & kViewBwd3) {
-                if (vp.flags & kViewAxis) bwd_view<true, 3>(vp, P.uc_hi, P.uc_lo, X, Y, wr, lo, bwin, part, comp, &bad);
-                else bwd_view<false, 3>(vp, P.uc_hi, P.uc_lo, X, Y, wr, lo, bwin, part, comp, &bad);
+            const float pb0 = __fmaf_rn(-vp.cu_hi, X, __fmaf_rn(-vp.su_hi, Y[0], -P.uc_hi));
+            float sm[kBwdPixPerThread];
+#pragma unroll
+            for (int e = 0; e < kBwdPixPerThread; ++e) sm[e] = delta_small(vp, X, Y[e], P.uc_lo);
+            // the first candidate is monotone along the thread's pixel column: its end values
+            // (with one bin of slack) bound all four pixels
+            const int NCv = (vp.flags & kViewBwd3) ? 3 : 2;
+            const float pbl = __fmaf_rn((float)(kBwdRowStep * (kBwdPixPerThread - 1)), vp.su_hi, pb0);
+            const int ia = __float2int_ru(__fsub_rn(__fsub_rn(sm[0], pb0), vp.hwu)) - lo;
+            const int ib = __float2int_ru(__fsub_rn(__fsub_rn(sm[kBwdPixPerThread - 1], pbl), vp.hwu)) - lo;
+            const bool inside = min(ia, ib) >= 1 && max(ia, ib) <= bwin - NCv - 1;
+#define SUPCG_BWD(AX, NC, CK) bwd_view<AX, NC, CK>(vp, pb0, sm, wr, lo, bwin, t, &bad)
+            if (vp.flags & kViewAxis) {
+                if (inside) SUPCG_BWD(true, 2, false); else SUPCG_BWD(true, 2, true);
+            } else if (NCv == 3) {
+                if (inside) SUPCG_BWD(false, 3, false); else SUPCG_BWD(false, 3, true);
             } else {
-                if (vp.flags & kViewAxis) bwd_view<true, 2>(vp, P.uc_hi, P.uc_lo, X, Y, wr, lo, bwin, part, comp, &bad);
-                else bwd_view<false, 2>(vp, P.uc_hi, P.uc_lo, X, Y, wr, lo, bwin, part, comp, &bad);
+                if (inside) SUPCG_BWD(false, 2, false); else SUPCG_BWD(false, 2, true);
+            }
+#undef SUPCG_BWD
+            if (((vv / kBwdSplit) & 3) == 3 || vv + kBwdSplit >= nv) {   // Kahan-compensated fold every four views
+#pragma unroll
+                for (int e = 0; e < kBwdPixPerThread; ++e) {
+                    const float y = __fsub_rn(t[e], comp[e]);
+                    const float tt = __fadd_rn(part[e], y);
+                    comp[e] = __fsub_rn(__fsub_rn(tt, part[e]), y);
+                    part[e] = tt;
+                    t[e] = 0.0f;
+                }
             }
         }
 #pragma unroll
@@ -384,12 +424,18 @@ __global__ void __launch_bounds__(kBwdThreads) k_backward(const Prob *__restrict
     if (bad) atomicExch(&bad_sh, 1);
     __syncthreads();
 
-    float *out = (mode == BWD_G) ? P.g : (mode == BWD_H ? P.h : P.g);
+    // combine the groups' sums in a fixed order
+    if (grp == 1)
 #pragma unroll
-    for (int e = 0; e < kBwdPixPerThread; ++e) {
-        const int i = i0 + ly + kBwdRowStep * e;
-        if (i < P.ny && j < P.nx) out[(size_t)i * P.nxp + j] = (float)acc[e];
-    }
+        for (int e = 0; e < kBwdPixPerThread; ++e) comb[e * kBwdGroup + tg] = acc[e];
+    __syncthreads();
+    float *out = (mode == BWD_G) ? P.g : (mode == BWD_H ? P.h : P.g);
+    if (grp == 0)
+#pragma unroll
+        for (int e = 0; e < kBwdPixPerThread; ++e) {
+            const int i = i0 + ly + kBwdRowStep * e;
+            if (i < P.ny && j < P.nx) out[(size_t)i * P.nxp + j] = (float)(acc[e] + comb[e * kBwdGroup + tg]);
+        }
     if (t == 0 && bad_sh && P.sc) atomicExch(&P.sc->status, (int)SUPCG_ERR_UNSUPPORTED);
 }
 
