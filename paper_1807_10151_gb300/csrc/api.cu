@@ -258,7 +258,9 @@ extern "C" int supcg_create_geometry(int nx, int ny, double pixel_size, int n_vi
     // the three bins nearest a pixel's centre must cover its footprint, and a
     // backprojector tile's bins must fit its shared-memory window
     g->bwin = std::max(64, round_up((int)ceil(span_bwd + 11.0), 4));
-    if (maxE + max_small + 0.03 >= 1.5 || g->bwin > 256) { delete g; return SUPCG_ERR_UNSUPPORTED; }
+    // (the centres include the small correction, so only the margin pads the windows)
+    (void)max_small;
+    if (maxE + 0.03 >= 1.5 || g->bwin > 256) { delete g; return SUPCG_ERR_UNSUPPORTED; }
     g->nA = (int)A.size();
     g->nB = (int)B.size();
     g->vlist = A;
