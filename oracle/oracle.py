@@ -71,6 +71,8 @@ def _L():
                                         C.c_long, C.c_int,
                                         dp, dp, ip, ip, lp] + [dp, dp, dp, lp, dp, dp, dp, dp])
             lib.orc_num_threads.restype = C.c_int
+            lib.orc_conv3x3.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, dp, dp, dp, C.c_int, dp]
+            lib.orc_conv3x3_backward.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, dp, dp, dp, dp, dp, dp]
             _lib = lib
     return _lib
 
@@ -284,3 +286,36 @@ def suppcg(R: CSR, b, x0=None, a=0.995, gamma=0.5, K=1, eps=-1.0, max_iter=50,
     for k, v in logs.items():
         out[k] = v[:it].copy()
     return out
+
+
+# ------------------------------------------------------------------ learned perturbation layers
+def conv3x3(x, W, bias=None, relu=False):
+    """3x3 convolution with zero padding: x [cin][ny][nx], W [cout][cin][3][3]."""
+    x, W = _f64(x), _f64(W)
+    cin, ny, nx = x.shape
+    cout = W.shape[0]
+    assert W.shape == (cout, cin, 3, 3)
+    y = np.empty((cout, ny, nx))
+    b = _f64(bias) if bias is not None else None
+    _L().orc_conv3x3(ny, nx, cin, cout, _d(x), _d(W), _d(b) if b is not None else None, int(relu), _d(y))
+    return y
+
+
+def conv3x3_backward(x, W, dy, want_dx=True):
+    """(dL/dx, dL/dW, dL/dbias) of conv3x3 (no activation) for dL/dy."""
+    x, W, dy = _f64(x), _f64(W), _f64(dy)
+    cin, ny, nx = x.shape
+    cout = W.shape[0]
+    dx = np.empty_like(x) if want_dx else None
+    dW = np.empty_like(W)
+    db = np.empty(cout)
+    _L().orc_conv3x3_backward(ny, nx, cin, cout, _d(x), _d(W), _d(dy), _d(dx) if want_dx else None, _d(dW), _d(db))
+    return dx, dW, db
+
+
+def cnn_forward(x, layers):
+    """Network of 3x3 layers [(W, b), ...], ReLU after every layer but the last."""
+    a = _f64(x)
+    for li, (W, b) in enumerate(layers):
+        a = conv3x3(a, W, b, relu=li + 1 < len(layers))
+    return a

@@ -604,3 +604,72 @@ int orc_num_threads(void)
     return 1;
 #endif
 }
+
+/* ------------------------------------------------------------------ */
+/* Learned perturbation: 3x3 convolution layers (test reference)        */
+/* ------------------------------------------------------------------ */
+/* The paper has no learned part; this is the plain definition of the
+ * layers the GPU network uses, for parity and gradient checks:
+ *   y[co][i][j] = bias[co] + sum_{ci, dy, dx} W[co][ci][dy][dx] x[ci][i+dy-1][j+dx-1]
+ * (zero outside the image), optionally followed by max(0, .). */
+void orc_conv3x3(int ny, int nx, int cin, int cout, const double *x, const double *W, const double *bias,
+                 int relu, double *y)
+{
+    long n = (long)ny * nx;
+#pragma omp parallel for schedule(static)
+    for (int co = 0; co < cout; ++co)
+        for (int i = 0; i < ny; ++i)
+            for (int j = 0; j < nx; ++j) {
+                double s = bias ? bias[co] : 0.0;
+                for (int ci = 0; ci < cin; ++ci)
+                    for (int dy = 0; dy < 3; ++dy)
+                        for (int dx = 0; dx < 3; ++dx) {
+                            int ii = i + dy - 1, jj = j + dx - 1;
+                            if (ii < 0 || ii >= ny || jj < 0 || jj >= nx) continue;
+                            s += W[((co * cin + ci) * 3 + dy) * 3 + dx] * x[ci * n + (long)ii * nx + jj];
+                        }
+                y[co * n + (long)i * nx + j] = (relu && s < 0.0) ? 0.0 : s;
+            }
+}
+
+/* Gradients of a layer without activation: given dL/dy, write dL/dx (nullable),
+ * dL/dW and dL/dbias (nullable) by the definition of the layer above. */
+void orc_conv3x3_backward(int ny, int nx, int cin, int cout, const double *x, const double *W, const double *dy_,
+                          double *dx_, double *dW, double *db)
+{
+    long n = (long)ny * nx;
+    if (dx_) {
+        for (long e = 0; e < (long)cin * n; ++e) dx_[e] = 0.0;
+        for (int co = 0; co < cout; ++co)
+            for (int i = 0; i < ny; ++i)
+                for (int j = 0; j < nx; ++j) {
+                    double g = dy_[co * n + (long)i * nx + j];
+                    for (int ci = 0; ci < cin; ++ci)
+                        for (int dy = 0; dy < 3; ++dy)
+                            for (int dx = 0; dx < 3; ++dx) {
+                                int ii = i + dy - 1, jj = j + dx - 1;
+                                if (ii < 0 || ii >= ny || jj < 0 || jj >= nx) continue;
+                                dx_[ci * n + (long)ii * nx + jj] += W[((co * cin + ci) * 3 + dy) * 3 + dx] * g;
+                            }
+                }
+    }
+    for (int co = 0; co < cout; ++co) {
+        if (db) {
+            double s = 0.0;
+            for (long p = 0; p < n; ++p) s += dy_[co * n + p];
+            db[co] = s;
+        }
+        for (int ci = 0; ci < cin; ++ci)
+            for (int dy = 0; dy < 3; ++dy)
+                for (int dx = 0; dx < 3; ++dx) {
+                    double s = 0.0;
+                    for (int i = 0; i < ny; ++i)
+                        for (int j = 0; j < nx; ++j) {
+                            int ii = i + dy - 1, jj = j + dx - 1;
+                            if (ii < 0 || ii >= ny || jj < 0 || jj >= nx) continue;
+                            s += dy_[co * n + (long)i * nx + j] * x[ci * n + (long)ii * nx + jj];
+                        }
+                    dW[((co * cin + ci) * 3 + dy) * 3 + dx] = s;
+                }
+    }
+}
