@@ -178,6 +178,44 @@ int supcg_solve_host(supcg_geometry g, const float *h_b, float *h_x, const supcg
 int supcg_solve_batched(const supcg_geometry *gs, const float *const *d_b, float *const *d_x,
                         int count, const supcg_params *p, supcg_report *reps, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Learned perturbation network (an addition to the paper's method: the paper
+ * perturbs along the normalised negative TV gradient, Sec. 3.1; this network
+ * proposes a direction from the iterate and that gradient, and the solver
+ * accepts it only when it is nonascending for TV).
+ *
+ * Five 3x3 convolutions (zero padding), channels 2 -> 32 -> 32 -> 32 -> 32 -> 1,
+ * ReLU after the first four, output added to the scaled input direction.
+ * Input: the image x scaled to unit RMS and tbar (Sec. 3.1) scaled to unit
+ * RMS; output: the proposed direction at unit-RMS scale.  BF16 weights and
+ * activations, FP32 accumulation (tensor cores), FP32 master weights (Adam).
+ * Parameters, as a flat FP32 array: for each layer W[cout][cin][3][3] then
+ * b[cout].  A network is created for images of ny x nx and up to max_batch
+ * images per call; it owns its device memory.
+ * ------------------------------------------------------------------------ */
+typedef struct supcg_cnn_s *supcg_cnn;
+
+/* Create a network with seeded initial weights (last layer zero: the untrained
+ * network returns the plain direction).  Errors: SUPCG_ERR_ARG, _NOMEM, _CUDA. */
+int supcg_cnn_create(int ny, int nx, int max_batch, unsigned long long seed, supcg_cnn *out);
+int supcg_cnn_destroy(supcg_cnn net);
+/* Number of FP32 parameters (length of the flat array). */
+int supcg_cnn_num_params(supcg_cnn net);
+int supcg_cnn_get_params(supcg_cnn net, float *h_params);
+int supcg_cnn_set_params(supcg_cnn net, const float *h_params);
+/* Forward pass for `count` images: d_x, d_tbar, d_out FP32 [count][ny][nx]. */
+int supcg_cnn_forward(supcg_cnn net, const float *d_x, const float *d_tbar, int count, float *d_out,
+                      void *stream);
+/* Gradients of the mean squared error between the output and d_target
+ * (unit-RMS scale) with respect to all parameters (host array, flat layout);
+ * *h_loss receives the loss.  Synchronous. */
+int supcg_cnn_gradients(supcg_cnn net, const float *d_x, const float *d_tbar, const float *d_target, int count,
+                        float *h_grads, double *h_loss, void *stream);
+/* One Adam step (lr, beta1 0.9, beta2 0.999) on the same loss.  h_loss nullable
+ * (when given, the call synchronises to read it). */
+int supcg_cnn_train_step(supcg_cnn net, const float *d_x, const float *d_tbar, const float *d_target, int count,
+                         double lr, double *h_loss, void *stream);
+
 /* Kernel kinds of supcg_solve_profiled. */
 typedef enum {
     SUPCG_KIND_FORWARD = 0,  /* forward projector (R x with residual, R p with ||R p||^2)   */

@@ -27,7 +27,9 @@ STATUS = {0: "OK", -1: "ERR_ARG", -2: "ERR_CUDA", -3: "ERR_NOMEM", -4: "ERR_BREA
 EXPORTED = ["supcg_create_geometry", "supcg_destroy_geometry", "supcg_project", "supcg_backproject",
             "supcg_precondition", "supcg_tv_tbar", "supcg_superiorize", "supcg_solve", "supcg_solve_host",
             "supcg_solve_batched", "supcg_status_string", "supcg_solve_profiled", "supcg_kernel_launches",
-            "supcg_precondition_noalloc"]
+            "supcg_precondition_noalloc", "supcg_cnn_create", "supcg_cnn_destroy", "supcg_cnn_num_params",
+            "supcg_cnn_get_params", "supcg_cnn_set_params", "supcg_cnn_forward", "supcg_cnn_gradients",
+            "supcg_cnn_train_step"]
 KINDS = ["forward", "backward", "fft", "stv", "vector"]
 
 _lock = threading.Lock()
@@ -91,6 +93,15 @@ def load(allow_build: bool = True):
                                            C.POINTER(d), C.POINTER(ll), vp]
         L.supcg_kernel_launches.argtypes = []
         L.supcg_kernel_launches.restype = ll
+        fp = C.POINTER(C.c_float)
+        L.supcg_cnn_create.argtypes = [i, i, i, C.c_ulonglong, C.POINTER(vp)]
+        L.supcg_cnn_destroy.argtypes = [vp]
+        L.supcg_cnn_num_params.argtypes = [vp]
+        L.supcg_cnn_get_params.argtypes = [vp, fp]
+        L.supcg_cnn_set_params.argtypes = [vp, fp]
+        L.supcg_cnn_forward.argtypes = [vp, vp, vp, i, vp, vp]
+        L.supcg_cnn_gradients.argtypes = [vp, vp, vp, vp, i, fp, C.POINTER(d), vp]
+        L.supcg_cnn_train_step.argtypes = [vp, vp, vp, vp, i, d, C.POINTER(d), vp]
         L.supcg_status_string.argtypes = [i]
         L.supcg_status_string.restype = C.c_char_p
         for name in EXPORTED:
@@ -336,3 +347,83 @@ def solve_batched(geoms, bs, xs, stream=None, **kw):
     if rc not in (0,) and rc > -4:
         raise SupcgError(rc, "supcg_solve_batched")
     return [r.as_dict() for r in reps]
+
+
+# ---------------------------------------------------------------- learned perturbation network
+CNN_SHAPES = [(32, 2), (32, 32), (32, 32), (32, 32), (1, 32)]   # (cout, cin) of the five 3x3 layers
+
+
+class CNN:
+    """The learned-direction network (supcg_cnn_*): 2 -> 32 -> 32 -> 32 -> 32 -> 1
+    channels of 3x3 convolutions on the tensor cores."""
+
+    def __init__(self, ny, nx, max_batch=1, seed=1):
+        self.ny, self.nx, self.cap = int(ny), int(nx), int(max_batch)
+        h = C.c_void_p()
+        _check(load().supcg_cnn_create(self.ny, self.nx, self.cap, int(seed), C.byref(h)), "supcg_cnn_create")
+        self.handle = h
+        self.nparam = load().supcg_cnn_num_params(h)
+
+    def close(self):
+        if getattr(self, "handle", None) is not None and _lib is not None:
+            _lib.supcg_cnn_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get_params(self):
+        import numpy as np
+        a = np.empty(self.nparam, dtype=np.float32)
+        _check(load().supcg_cnn_get_params(self.handle, a.ctypes.data_as(C.POINTER(C.c_float))), "get_params")
+        return a
+
+    def set_params(self, a):
+        import numpy as np
+        a = np.ascontiguousarray(a, dtype=np.float32)
+        assert a.size == self.nparam
+        _check(load().supcg_cnn_set_params(self.handle, a.ctypes.data_as(C.POINTER(C.c_float))), "set_params")
+
+    @staticmethod
+    def unflatten(a):
+        """Flat parameters -> [(W [cout][cin][3][3], b [cout]), ...]."""
+        out, off = [], 0
+        for co, ci in CNN_SHAPES:
+            W = a[off:off + co * ci * 9].reshape(co, ci, 3, 3)
+            off += co * ci * 9
+            b = a[off:off + co]
+            off += co
+            out.append((W, b))
+        return out
+
+    def forward(self, x, tbar, stream=None):
+        import torch
+        count = x.numel() // (self.ny * self.nx)
+        out = torch.empty_like(x)
+        _check(load().supcg_cnn_forward(self.handle, _ptr(x, torch.float32), _ptr(tbar, torch.float32), count,
+                                        _ptr(out, torch.float32), _stream(stream)), "supcg_cnn_forward")
+        return out
+
+    def gradients(self, x, tbar, target, stream=None):
+        import numpy as np
+        import torch
+        count = x.numel() // (self.ny * self.nx)
+        g = np.empty(self.nparam, dtype=np.float32)
+        loss = C.c_double()
+        _check(load().supcg_cnn_gradients(self.handle, _ptr(x, torch.float32), _ptr(tbar, torch.float32),
+                                          _ptr(target, torch.float32), count, g.ctypes.data_as(C.POINTER(C.c_float)),
+                                          C.byref(loss), _stream(stream)), "supcg_cnn_gradients")
+        return g, loss.value
+
+    def train_step(self, x, tbar, target, lr=1e-3, want_loss=True, stream=None):
+        import torch
+        count = x.numel() // (self.ny * self.nx)
+        loss = C.c_double()
+        _check(load().supcg_cnn_train_step(self.handle, _ptr(x, torch.float32), _ptr(tbar, torch.float32),
+                                           _ptr(target, torch.float32), count, float(lr),
+                                           C.byref(loss) if want_loss else None, _stream(stream)),
+               "supcg_cnn_train_step")
+        return loss.value if want_loss else None

@@ -1,0 +1,125 @@
+"""Learned-direction network on the tensor cores vs the oracle's FP64 layers.
+
+The GPU stores weights and activations in BF16 and accumulates in FP32; the
+reference here applies the same BF16 roundings (weights, the input tensor,
+every hidden activation and every stored gradient) around the oracle's FP64
+convolutions, so the remaining differences are FP32-vs-FP64 accumulation and
+rare one-ulp BF16 flips."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+def bf16(a):
+    return torch.tensor(np.asarray(a, dtype=np.float32)).to(torch.bfloat16).to(torch.float32).double().numpy()
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / max(np.linalg.norm(np.ravel(b)), 1e-300))
+
+
+def random_params(net, rng, scale=1.0):
+    import paper_1807_10151_gb300 as S
+    flat = []
+    for co, ci in S.CNN_SHAPES:
+        flat.append(rng.standard_normal(co * ci * 9) * scale * np.sqrt(2.0 / (9 * ci)))
+        flat.append(0.1 * rng.standard_normal(co))
+    p = np.concatenate(flat).astype(np.float32)
+    net.set_params(p)
+    return p
+
+
+def reference_forward(params, x, tb):
+    """Oracle layers with the GPU's BF16 roundings; returns (out, [a0..a4], resid)."""
+    import paper_1807_10151_gb300 as S
+    layers = S.CNN.unflatten(params.astype(np.float64))
+    outs, acts, resids = [], [], []
+    n = x.shape[1] * x.shape[2]
+    for xi, ti in zip(x, tb):
+        fx = np.float32(np.sqrt(n / np.sum(xi.astype(np.float64) ** 2)))
+        ft = np.float32(np.sqrt(n / np.sum(ti.astype(np.float64) ** 2)))
+        v0 = (xi * fx).astype(np.float32)
+        v1 = (ti * ft).astype(np.float32)
+        a = np.stack([bf16(v0), bf16(v1)])
+        al = [a]
+        for li, (W, b) in enumerate(layers):
+            z = O.conv3x3(a, bf16(W), b, relu=li < 4)
+            if li < 4:
+                a = bf16(z)
+                al.append(a)
+            else:
+                outs.append(z[0] + v1)
+        acts.append(al)
+        resids.append(v1)
+    return np.stack(outs), acts, resids
+
+
+def test_forward_matches_oracle_layers():
+    import paper_1807_10151_gb300 as S
+    ny, nx, count = 20, 24, 3          # 1440 pixels: 11 full 128-pixel tiles and a ragged one
+    rng = np.random.default_rng(0)
+    net = S.CNN(ny, nx, max_batch=4, seed=5)
+    p = random_params(net, rng)
+    x = rng.uniform(size=(count, ny, nx)).astype(np.float32)
+    tb = rng.standard_normal((count, ny, nx)).astype(np.float32)
+    out = net.forward(torch.tensor(x, device="cuda"), torch.tensor(tb, device="cuda")).cpu().numpy()
+    ref, _, _ = reference_forward(p, x, tb)
+    assert rel_l2(out, ref) <= 5e-3
+    # an untrained network (last layer zero) returns the scaled input direction
+    net2 = S.CNN(ny, nx, max_batch=4, seed=5)
+    out2 = net2.forward(torch.tensor(x, device="cuda"), torch.tensor(tb, device="cuda")).cpu().numpy()
+    n = ny * nx
+    for k in range(count):
+        np.testing.assert_allclose(out2[k], tb[k] * np.sqrt(n / np.sum(tb[k].astype(np.float64) ** 2)), rtol=1e-6)
+
+
+def test_gradients_match_oracle_backward():
+    import paper_1807_10151_gb300 as S
+    ny, nx, count = 16, 18, 2
+    rng = np.random.default_rng(1)
+    net = S.CNN(ny, nx, max_batch=2, seed=3)
+    p = random_params(net, rng)
+    x = rng.uniform(size=(count, ny, nx)).astype(np.float32)
+    tb = rng.standard_normal((count, ny, nx)).astype(np.float32)
+    tg = rng.standard_normal((count, ny, nx)).astype(np.float32)
+    g, loss = net.gradients(torch.tensor(x, device="cuda"), torch.tensor(tb, device="cuda"),
+                            torch.tensor(tg, device="cuda"))
+    out, acts, _ = reference_forward(p, x, tb)
+    total = out.size
+    assert loss == pytest.approx(np.mean((out - tg) ** 2), rel=1e-2)
+    layers = S.CNN.unflatten(p.astype(np.float64))
+    ref = [np.zeros_like(W) for W, _ in layers], [np.zeros_like(b) for _, b in layers]
+    for k in range(count):
+        G = bf16(2.0 * (out[k] - tg[k]) / total)[None]      # dL/dout, stored in BF16
+        for li in range(4, -1, -1):
+            W = bf16(layers[li][0])
+            dx, dW, db = O.conv3x3_backward(acts[k][li], W, G, want_dx=li > 0)
+            ref[0][li] += dW
+            ref[1][li] += db
+            if li > 0:
+                G = bf16(dx * (acts[k][li] > 0))                # dL/dz of the layer below, stored in BF16
+    gl = S.CNN.unflatten(g.astype(np.float64))
+    for li in range(5):
+        assert rel_l2(gl[li][0], ref[0][li]) <= 3e-2, li
+        assert rel_l2(gl[li][1], ref[1][li]) <= 3e-2, li
+
+
+def test_training_reduces_the_loss():
+    import paper_1807_10151_gb300 as S
+    ny, nx, count = 32, 32, 4
+    rng = np.random.default_rng(2)
+    net = S.CNN(ny, nx, max_batch=count, seed=7)
+    x = torch.tensor(rng.uniform(size=(count, ny, nx)), dtype=torch.float32, device="cuda")
+    tb = torch.tensor(rng.standard_normal((count, ny, nx)), dtype=torch.float32, device="cuda")
+    n = ny * nx
+    scale = torch.sqrt(n / (tb.double() ** 2).sum(dim=(1, 2), keepdim=True)).float()
+    target = 0.5 * tb * scale          # half the input direction (unit-RMS scale)
+    l0 = net.train_step(x, tb, target, lr=3e-3)
+    for _ in range(150):
+        net.train_step(x, tb, target, lr=3e-3, want_loss=False)
+    l1 = net.train_step(x, tb, target, lr=3e-3)
+    assert l1 < 0.3 * l0, (l0, l1)
