@@ -146,6 +146,8 @@ typedef struct {
     double f0;          /* f(x_0)                                                        */
     double tv_last;     /* TV(x_{k-1/2})  (0 unless perturb = 1 and iters > 0)            */
     int status;         /* SUPCG_OK or the error that stopped the iteration              */
+    int n_fallback;     /* supcg_solve_learned: proposals rejected by the nonascent test  */
+    int n_learned;      /* supcg_solve_learned: proposals accepted                        */
 } supcg_report;
 
 /* Number of doubles per iteration written to the optional log of supcg_solve:
@@ -207,7 +209,8 @@ int supcg_cnn_set_params(supcg_cnn net, const float *h_params);
 int supcg_cnn_forward(supcg_cnn net, const float *d_x, const float *d_tbar, int count, float *d_out,
                       void *stream);
 /* Gradients of the mean squared error between the output and d_target
- * (unit-RMS scale) with respect to all parameters (host array, flat layout);
+ * (scaled per image to unit RMS inside the call) with respect to all
+ * parameters (host array, flat layout);
  * *h_loss receives the loss.  Synchronous. */
 int supcg_cnn_gradients(supcg_cnn net, const float *d_x, const float *d_tbar, const float *d_target, int count,
                         float *h_grads, double *h_loss, void *stream);
@@ -216,6 +219,24 @@ int supcg_cnn_gradients(supcg_cnn net, const float *d_x, const float *d_tbar, co
 int supcg_cnn_train_step(supcg_cnn net, const float *d_x, const float *d_tbar, const float *d_target, int count,
                          double lr, double *h_loss, void *stream);
 
+/* supcg_solve that also records x_k (the iterate S_TV receives) of every while
+ * body into d_trace [max_iter][ny][nx] (FP32, caller-owned): training data for
+ * the learned direction.  Synchronous. */
+int supcg_solve_trace(supcg_geometry g, const float *d_b, float *d_x, const supcg_params *p,
+                      supcg_report *rep, double *d_log, float *d_trace, void *stream);
+
+/* SupPCG with the learned direction: every while body computes tbar at x_k
+ * (Sec. 3.1), runs the network on (x_k, tbar), and tests the proposal t with
+ * the exact one-sided directional derivative D_TV(x_k; t).  If D_TV < 0 (t is
+ * nonascending for TV at x_k), one step along t/||t|| of length
+ * 2^-j gamma * sum_{i<K} a^(l+i) is taken, j = 0, 1, ... until TV does not
+ * increase (the test of Algorithm 1), and l advances by K + j, which keeps the
+ * bound of Theorem 1; otherwise the plain K steps of Algorithm 1 run.  The network must
+ * have been created for this geometry's image size; nx must be a multiple of
+ * 4.  rep->n_learned / n_fallback count the two outcomes.  Synchronous. */
+int supcg_solve_learned(supcg_geometry g, supcg_cnn net, const float *d_b, float *d_x,
+                        const supcg_params *p, supcg_report *rep, double *d_log, void *stream);
+
 /* Kernel kinds of supcg_solve_profiled. */
 typedef enum {
     SUPCG_KIND_FORWARD = 0,  /* forward projector (R x with residual, R p with ||R p||^2)   */
@@ -223,7 +244,8 @@ typedef enum {
     SUPCG_KIND_FFT = 2,      /* preconditioner passes                                      */
     SUPCG_KIND_STV = 3,      /* S_TV (Algorithm 1)                                         */
     SUPCG_KIND_VECTOR = 4,   /* axpys, inner products, transposes, staging, bookkeeping    */
-    SUPCG_KIND_COUNT = 5
+    SUPCG_KIND_CNN = 5,      /* learned-direction network (supcg_solve_learned)            */
+    SUPCG_KIND_COUNT = 6
 } supcg_kernel_kind;
 
 /* supcg_solve without graph replay and with a CUDA event pair around every

@@ -29,8 +29,8 @@ EXPORTED = ["supcg_create_geometry", "supcg_destroy_geometry", "supcg_project", 
             "supcg_solve_batched", "supcg_status_string", "supcg_solve_profiled", "supcg_kernel_launches",
             "supcg_precondition_noalloc", "supcg_cnn_create", "supcg_cnn_destroy", "supcg_cnn_num_params",
             "supcg_cnn_get_params", "supcg_cnn_set_params", "supcg_cnn_forward", "supcg_cnn_gradients",
-            "supcg_cnn_train_step"]
-KINDS = ["forward", "backward", "fft", "stv", "vector"]
+            "supcg_cnn_train_step", "supcg_solve_trace", "supcg_solve_learned"]
+KINDS = ["forward", "backward", "fft", "stv", "vector", "cnn"]
 
 _lock = threading.Lock()
 _lib = None
@@ -53,7 +53,8 @@ class Params(C.Structure):
 class Report(C.Structure):
     """supcg_report (include/supcg.h)."""
     _fields_ = [("iters", C.c_int), ("k", C.c_int), ("ell", C.c_longlong), ("f_last", C.c_double),
-                ("f0", C.c_double), ("tv_last", C.c_double), ("status", C.c_int)]
+                ("f0", C.c_double), ("tv_last", C.c_double), ("status", C.c_int), ("n_fallback", C.c_int),
+                ("n_learned", C.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -102,6 +103,8 @@ def load(allow_build: bool = True):
         L.supcg_cnn_forward.argtypes = [vp, vp, vp, i, vp, vp]
         L.supcg_cnn_gradients.argtypes = [vp, vp, vp, vp, i, fp, C.POINTER(d), vp]
         L.supcg_cnn_train_step.argtypes = [vp, vp, vp, vp, i, d, C.POINTER(d), vp]
+        L.supcg_solve_trace.argtypes = [vp, vp, vp, C.POINTER(Params), C.POINTER(Report), vp, vp, vp]
+        L.supcg_solve_learned.argtypes = [vp, vp, vp, vp, C.POINTER(Params), C.POINTER(Report), vp, vp]
         L.supcg_status_string.argtypes = [i]
         L.supcg_status_string.restype = C.c_char_p
         for name in EXPORTED:
@@ -308,8 +311,8 @@ class Geometry:
         x = torch.zeros(self.ny, self.nx, device=b.device, dtype=torch.float32) if x0 is None else x0.clone()
         p = make_params(**kw)
         rep = Report()
-        ms = (C.c_double * 5)()
-        cnt = (C.c_longlong * 5)()
+        ms = (C.c_double * len(KINDS))()
+        cnt = (C.c_longlong * len(KINDS))()
         rc = supcg_solve_profiled(self.handle, _ptr(b, torch.float32), _ptr(x, torch.float32), p, rep, ms, cnt,
                                   _stream(stream))
         if rc not in (0,) and rc > -4:
@@ -317,6 +320,37 @@ class Geometry:
         out = rep.as_dict()
         out["rc"] = rc
         return x, out, {k: (ms[i], cnt[i]) for i, k in enumerate(KINDS)}
+
+    def solve_trace(self, b, x0=None, stream=None, **kw):
+        """SupPCG recording x_k of every while body: (x, report, log, trace [max_iter][ny][nx])."""
+        import torch
+        x = torch.zeros(self.ny, self.nx, device=b.device, dtype=torch.float32) if x0 is None else x0.clone()
+        p = make_params(**kw)
+        rep = Report()
+        lg = torch.zeros(max(p.max_iter, 1), LOG_STRIDE, device=b.device, dtype=torch.float64)
+        tr = torch.zeros(max(p.max_iter, 1), self.ny, self.nx, device=b.device, dtype=torch.float32)
+        rc = load().supcg_solve_trace(self.handle, _ptr(b, torch.float32), _ptr(x, torch.float32), C.byref(p),
+                                      C.byref(rep), _ptr(lg), _ptr(tr), _stream(stream))
+        if rc not in (0,) and rc > -4:
+            raise SupcgError(rc, "supcg_solve_trace")
+        out = rep.as_dict()
+        out["rc"] = rc
+        return x, out, lg, tr
+
+    def solve_learned(self, net, b, x0=None, log=False, stream=None, **kw):
+        """SupPCG with the learned direction (supcg_solve_learned)."""
+        import torch
+        x = torch.zeros(self.ny, self.nx, device=b.device, dtype=torch.float32) if x0 is None else x0.clone()
+        p = make_params(**kw)
+        rep = Report()
+        lg = torch.zeros(max(p.max_iter, 1), LOG_STRIDE, device=b.device, dtype=torch.float64) if log else None
+        rc = load().supcg_solve_learned(self.handle, net.handle, _ptr(b, torch.float32), _ptr(x, torch.float32),
+                                        C.byref(p), C.byref(rep), _ptr(lg) if log else None, _stream(stream))
+        if rc not in (0,) and rc > -4:
+            raise SupcgError(rc, "supcg_solve_learned")
+        out = rep.as_dict()
+        out["rc"] = rc
+        return x, out, lg
 
     def solve_host(self, b_host, x_host, stream=None, **kw):
         """SupPCG through host buffers (numpy / CPU tensors, float32); x_host is overwritten."""

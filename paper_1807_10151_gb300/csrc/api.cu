@@ -395,7 +395,7 @@ static int ws_create(const std::vector<supcg_geometry> &gs, Workspace **out)
         const size_t img = (size_t)g->ny * g->nxp, imgT = (size_t)g->nx * g->nyp, sino = (size_t)g->V * g->Up;
         int maxblk = 0;
         for (int kt = 0; kt < KT_COUNT; ++kt) maxblk = std::max(maxblk, nb[kt][c]);
-        const size_t npart = std::max<size_t>(8 * (size_t)nb[KT_STV][c], 2 * (size_t)maxblk) + 64;
+        const size_t npart = std::max<size_t>(12 * (size_t)nb[KT_STV][c], 2 * (size_t)maxblk) + 64;
         auto al = [](size_t b) { return (b + 255) / 256 * 256; };
         const size_t sizes[] = {img * 4, imgT * 4, img * 4, imgT * 4, img * 4, img * 4, img * 4, img * 4,
                                 sino * 4, sino * 4, sino * 4, (size_t)g->ny * g->nx * 16, sizeof(Scal),
@@ -666,13 +666,20 @@ static int enqueue_precond_k(Workspace *w, cudaStream_t st)
     return SUPCG_OK;
 }
 
-static int enqueue_body(Workspace *w, const supcg_params *p, cudaStream_t st, int want_snorm)
+static int enqueue_body(Workspace *w, const supcg_params *p, cudaStream_t st, int want_snorm,
+                        supcg_cnn_s *net = nullptr)
 {
     int rc;
     LAUNCH(SUPCG_KIND_VECTOR, st, launch_xupdate(w->L(KT_VEC, st)));            // step 10 + deferred step 7
+    const float *dir = nullptr;
+    if (net && p->perturb && p->K > 0) {                                         // proposal of the network
+        LAUNCH(SUPCG_KIND_STV, st, launch_tv_tbar(w->L(KT_TV, st)));
+        LAUNCH(SUPCG_KIND_CNN, st, cnn_forward(net, w->hp[0].x, w->hp[0].tbar, 1, st));
+        dir = cnn_output(net);
+    }
     if (p->perturb && p->K > 0)                                                 // steps 11-12
         LAUNCH(SUPCG_KIND_STV, st, launch_stv(w->L(KT_STV, st), p->K, p->a, p->gamma, p->max_trials, nullptr,
-                                              want_snorm));
+                                              want_snorm, dir));
     LAUNCH(SUPCG_KIND_VECTOR, st, launch_transpose(w->L(KT_TR, st), 0));
     LAUNCH(SUPCG_KIND_FORWARD, st, launch_forward(w->L(KT_FWD, st), 0, FWD_RESID));   // r = R x - b, f
     LAUNCH(SUPCG_KIND_BACKWARD, st, launch_backward(w->L(KT_BWD, st), BWD_G, w->bwin));         // g = R^T r
@@ -703,7 +710,8 @@ static int enqueue_init(Workspace *w, const supcg_params *p, cudaStream_t st)
 }
 
 static int run_solve(Workspace *w, const float *const *d_b, float *const *d_x, const supcg_params *p,
-                     supcg_report *reps, double *d_log, cudaStream_t st)
+                     supcg_report *reps, double *d_log, cudaStream_t st, float *d_trace = nullptr,
+                     supcg_cnn_s *net = nullptr)
 {
     int rc;
     for (int c = 0; c < w->count; ++c) {
@@ -716,6 +724,7 @@ static int run_solve(Workspace *w, const float *const *d_b, float *const *d_x, c
         P.precond = p->precondition ? 1 : 0;
         P.storage = SUPCG_F32;
         P.log = (c == 0) ? d_log : nullptr;
+        P.trace = (c == 0) ? d_trace : nullptr;
     }
     rc = ws_upload(w, st);
     for (int c = 0; c < w->count; ++c) w->hp[c].storage = w->geoms[c]->storage;
@@ -744,7 +753,7 @@ static int run_solve(Workspace *w, const float *const *d_b, float *const *d_x, c
     if (use_graph) {
         const double key[6] = {p->a, p->gamma, (double)p->max_trials, (double)p->K, (double)p->perturb,
                                (double)p->precondition};
-        const int key_i[4] = {want_snorm, 1, 0, 0};
+        const int key_i[4] = {want_snorm, 1, (int)((uintptr_t)d_trace & 0x7fffffff), (int)((uintptr_t)net & 0x7fffffff)};
         if (!w->body_exec || memcmp(key, w->key, sizeof(key)) || memcmp(key_i, w->key_i, sizeof(key_i))) {
             if (w->body_exec) cudaGraphExecDestroy(w->body_exec);
             w->body_exec = nullptr;
@@ -753,7 +762,7 @@ static int run_solve(Workspace *w, const float *const *d_b, float *const *d_x, c
                 use_graph = false;
             } else {
                 t_capture_count = 0;
-                int brc = enqueue_body(w, p, w->cap_stream, want_snorm);
+                int brc = enqueue_body(w, p, w->cap_stream, want_snorm, net);
                 w->body_nodes = t_capture_count;
                 cudaError_t e = cudaStreamEndCapture(w->cap_stream, &graph);
                 if (brc || e != cudaSuccess || cudaGraphInstantiate(&w->body_exec, graph, 0) != cudaSuccess) {
@@ -773,7 +782,7 @@ static int run_solve(Workspace *w, const float *const *d_b, float *const *d_x, c
         if (use_graph) {
             SUPCG_CUDA_TRY(cudaGraphLaunch(w->body_exec, st));
             g_launches += w->body_nodes;
-        } else if ((rc = enqueue_body(w, p, st, want_snorm))) return rc;
+        } else if ((rc = enqueue_body(w, p, st, want_snorm, net))) return rc;
         if (eps_mode && (it % 8 == 7)) {   // stop launching once every problem has stopped
             for (int c = 0; c < w->count; ++c)
                 SUPCG_CUDA_TRY(cudaMemcpyAsync(hdone + c, &w->hp[c].sc->done, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -799,6 +808,8 @@ static int run_solve(Workspace *w, const float *const *d_b, float *const *d_x, c
         r.f0 = hs[c].f0;
         r.tv_last = hs[c].tv_half;
         r.status = hs[c].status;
+        r.n_fallback = hs[c].n_fallback;
+        r.n_learned = hs[c].n_learned;
         if (hs[c].status && !worst) worst = hs[c].status;
     }
     return worst;
@@ -815,6 +826,39 @@ extern "C" int supcg_solve(supcg_geometry g, const float *d_b, float *d_x, const
         if ((rc = ws_create(gs, &g->ws_solve))) return rc;
     }
     return run_solve(g->ws_solve, &d_b, &d_x, p, rep, d_log, (cudaStream_t)stream);
+}
+
+extern "C" int supcg_solve_trace(supcg_geometry g, const float *d_b, float *d_x, const supcg_params *p,
+                                 supcg_report *rep, double *d_log, float *d_trace, void *stream)
+{
+    if (!g || !d_b || !d_x || !rep || !d_trace) return SUPCG_ERR_ARG;
+    int rc = check_params(p);
+    if (rc) return rc;
+    if (!g->ws_solve) {
+        std::vector<supcg_geometry> gs(1, g);
+        if ((rc = ws_create(gs, &g->ws_solve))) return rc;
+    }
+    return run_solve(g->ws_solve, &d_b, &d_x, p, rep, d_log, (cudaStream_t)stream, d_trace);
+}
+
+extern "C" int supcg_solve_learned(supcg_geometry g, supcg_cnn_s *net, const float *d_b, float *d_x,
+                                   const supcg_params *p, supcg_report *rep, double *d_log, void *stream)
+{
+    if (!g || !net || !d_b || !d_x || !rep) return SUPCG_ERR_ARG;
+    int rc = check_params(p);
+    if (rc) return rc;
+    int ny = 0, nx = 0;
+    cnn_shape(net, &ny, &nx);
+    if (ny != g->ny || nx != g->nx || g->nxp != g->nx) return SUPCG_ERR_UNSUPPORTED;
+    if (!g->ws_solve) {
+        std::vector<supcg_geometry> gs(1, g);
+        if ((rc = ws_create(gs, &g->ws_solve))) return rc;
+    }
+    // run the network once outside any capture (kernel attributes are set on first use)
+    Workspace *w = g->ws_solve;
+    if ((rc = cnn_forward(net, w->hp[0].x, w->hp[0].tbar, 1, (cudaStream_t)stream))) return rc;
+    SUPCG_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    return run_solve(w, &d_b, &d_x, p, rep, d_log, (cudaStream_t)stream, nullptr, net);
 }
 
 extern "C" int supcg_solve_profiled(supcg_geometry g, const float *d_b, float *d_x, const supcg_params *p,

@@ -242,9 +242,16 @@ __global__ void __launch_bounds__(kRedThreads) k_xupdate(const Prob *__restrict_
     }
     const float al = (float)sc->alpha;
     const size_t tot = (size_t)P.ny * P.nxp;
+    float *tr = P.trace ? P.trace + (size_t)sc->k * P.ny * P.nx : nullptr;
     for (size_t e = (size_t)local * kVecPerBlock + threadIdx.x; e < tot && e < (size_t)(local + 1) * kVecPerBlock;
-         e += kRedThreads)
-        P.x[e] = __fmaf_rn(al, P.p[e], P.x[e]);
+         e += kRedThreads) {
+        const float xv = __fmaf_rn(al, P.p[e], P.x[e]);
+        P.x[e] = xv;
+        if (tr) {
+            const int i = (int)(e / P.nxp), j = (int)(e - (size_t)i * P.nxp);
+            if (j < P.nx) tr[(size_t)i * P.nx + j] = xv;
+        }
+    }
 }
 
 int launch_xupdate(const Launch &L)

@@ -285,16 +285,19 @@ __global__ void k_pack_input(const float *x, const float *tb, const double *norm
     resid[p] = v1;
 }
 
-// Loss L = mean (out - target)^2; G5 = dL/dout as an 8-channel BF16 tensor (channel 0).
-__global__ void __launch_bounds__(256) k_loss(const float *out, const float *target, long long total,
-                                              __nv_bfloat16 *G5, double *partial)
+// Loss L = mean (out - target~)^2 with target~ the target scaled per image to unit
+// RMS; G5 = dL/dout as an 8-channel BF16 tensor (channel 0).
+__global__ void __launch_bounds__(256) k_loss(const float *out, const float *target, const double *tnorms,
+                                              long long n, long long total, __nv_bfloat16 *G5, double *partial)
 {
     __shared__ double red[40];
     double s = 0.0;
     const float scale = (float)(2.0 / (double)total);
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < total;
          p += (long long)gridDim.x * blockDim.x) {
-        const float d = out[p] - target[p];
+        const double tn = tnorms[2 * (p / n)];
+        const float ft = tn > 0.0 ? (float)sqrt((double)n / tn) : 0.0f;
+        const float d = out[p] - target[p] * ft;
         s += (double)d * (double)d;
         __align__(16) __nv_bfloat16 o[8];
         o[0] = __float2bfloat16_rn(scale * d);
@@ -357,7 +360,7 @@ struct supcg_cnn_s {
     __nv_bfloat16 *act[kCnnLayers] = {};   // act[0] input (8 ch), act[1..4] hidden (32 ch)
     __nv_bfloat16 *gbuf[kCnnLayers] = {};  // gbuf[4] = dL/dout (8 ch); gbuf[l] = dL/dz_l (32 ch), l = 1..3; gbuf[0] for layer 1
     float *resid = nullptr, *out = nullptr, *partial = nullptr;
-    double *norms = nullptr, *lpart = nullptr;
+    double *norms = nullptr, *tnorms = nullptr, *lpart = nullptr;
     int *status = nullptr;
     size_t partial_len = 0;
     long long step = 0;
@@ -439,6 +442,7 @@ extern "C" int supcg_cnn_create(int ny, int nx, int max_batch, unsigned long lon
     rc = rc ? rc : cnn_alloc(net, (void **)&net->resid, sizeof(float) * npix);
     rc = rc ? rc : cnn_alloc(net, (void **)&net->out, sizeof(float) * npix);
     rc = rc ? rc : cnn_alloc(net, (void **)&net->norms, sizeof(double) * 2 * max_batch);
+    rc = rc ? rc : cnn_alloc(net, (void **)&net->tnorms, sizeof(double) * 2 * max_batch);
     rc = rc ? rc : cnn_alloc(net, (void **)&net->lpart, sizeof(double) * 1024);
     rc = rc ? rc : cnn_alloc(net, (void **)&net->status, sizeof(int));
     if (!rc && cudaMemcpy(net->params, h.data(), sizeof(float) * off, cudaMemcpyHostToDevice) != cudaSuccess)
@@ -556,9 +560,11 @@ static int cnn_backward(supcg_cnn net, int count, cudaStream_t st)
 
 static int cnn_loss(supcg_cnn net, const float *d_target, int count, cudaStream_t st, double *h_loss)
 {
-    const long long total = (long long)net->ny * net->nx * count;
+    const long long n = (long long)net->ny * net->nx;
+    const long long total = n * count;
     const int blocks = (int)std::min<long long>(1024, (total + 255) / 256);
-    k_loss<<<blocks, 256, 0, st>>>(net->out, d_target, total, net->gbuf[kCnnLayers - 1], net->lpart);
+    k_norms<<<count, 1024, 0, st>>>(d_target, d_target, n, net->tnorms);
+    k_loss<<<blocks, 256, 0, st>>>(net->out, d_target, net->tnorms, n, total, net->gbuf[kCnnLayers - 1], net->lpart);
     SUPCG_CUDA_TRY(cudaGetLastError());
     if (h_loss) {
         std::vector<double> hp(blocks);
@@ -571,6 +577,16 @@ static int cnn_loss(supcg_cnn net, const float *d_target, int count, cudaStream_
     return SUPCG_OK;
 }
 
+} // namespace supcg
+
+namespace supcg {
+float *cnn_output(supcg_cnn net) { return net->out; }
+int cnn_shape(supcg_cnn net, int *ny, int *nx)
+{
+    *ny = net->ny;
+    *nx = net->nx;
+    return SUPCG_OK;
+}
 } // namespace supcg
 
 static int cnn_check(supcg_cnn net, int count)

@@ -109,7 +109,9 @@ struct Scal {
     int done;          // 1: the while condition failed (or an error stopped the loop)
     int status;        // SUPCG_OK or an error code
     int init;          // 1 while running steps 2-7 (beta forced to 0)
-    int pad[4];
+    int n_fallback;    // learned perturbation: proposals rejected by the nonascent test
+    int n_learned;     // learned perturbation: proposals accepted
+    int pad[2];
 };
 
 // ----------------------------------------------------------------- problem
@@ -140,6 +142,7 @@ struct Prob {
     unsigned *counter;     // last-block tickets [8]
     unsigned *bar;         // cooperative barrier [2]: arrivals, generation
     double *log;           // nullable [max_iter][SUPCG_LOG_STRIDE]
+    float *trace;          // nullable [max_iter][ny][nx]: x_k at the start of every while body
     // caller-owned I/O (unpadded): image in / out, sinogram in
     const void *in_user;
     void *out_user;
@@ -328,9 +331,12 @@ int launch_beta(const Launch &L);
 int launch_xupdate(const Launch &L);
 int launch_end_init(const Launch &L);
 int launch_stv(const Launch &L, int K, double a, double gamma, long long max_trials, int *trials_out,
-               int want_snorm);
+               int want_snorm, const float *dir = nullptr);
 int launch_tv_tbar(const Launch &L);
 int launch_log(const Launch &L);
 int stv_max_blocks_per_sm(int *out);
+int cnn_forward(struct supcg_cnn_s *net, const float *d_x, const float *d_tbar, int count, cudaStream_t st);
+float *cnn_output(struct supcg_cnn_s *net);
+int cnn_shape(struct supcg_cnn_s *net, int *ny, int *nx);
 
 } // namespace supcg

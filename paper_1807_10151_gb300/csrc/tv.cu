@@ -123,7 +123,7 @@ __device__ __forceinline__ double phase_sum(const Prob &P, int nb, int slot, int
 // trials_out (nullable): [count][K] trials of every nonascending step.
 __global__ void __launch_bounds__(kTvThreads) k_stv(const Prob *__restrict__ probs, const int *__restrict__ prefix,
                                                     int count, int K, double a, double gamma, long long max_trials,
-                                                    int *trials_out, int want_snorm)
+                                                    int *trials_out, int want_snorm, const float *__restrict__ dir)
 {
     __shared__ double red[40];
     __shared__ int flag;
@@ -151,7 +151,100 @@ __global__ void __launch_bounds__(kTvThreads) k_stv(const Prob *__restrict__ pro
             P.z[(size_t)i * ld + j] = x[(size_t)i * ld + j];
         }
 
-    for (int step = 0; step < K && ok; ++step) {
+    // Learned direction (dir != null, pitch nx): accepted only when nonascending for TV,
+    // i.e. when the one-sided directional derivative D_TV(x; dir) is negative; then one
+    // step of length 2^-j gamma sum_{i<K} a^(l+i) (j = rejected trials so far; halving,
+    // since a long step shrinks too slowly by factors of a near 1) replaces the K steps of
+    // Algorithm 1, and l advances by K + j, so ||s_k|| <= K gamma a^(l_k) as in Theorem 1.
+    // Otherwise the K plain steps run.
+    bool plain = true;
+    if (dir) {
+        double s_nn = 0.0, s_dd = 0.0, s_tv = 0.0;
+        for (long long e = e0; e < n; e += stride) {
+            const int i = (int)(e / nx), j = (int)(e - (long long)i * nx);
+            const size_t p = (size_t)i * ld + j;
+            const size_t q = (size_t)i * nx + j;
+            const float tp = dir[q];
+            s_nn += (double)tp * (double)tp;
+            if (i + 1 < ny && j + 1 < nx) {
+                const float a1 = x[p] - x[p + ld], b1 = x[p] - x[p + 1];
+                const float ta = tp - dir[q + nx], tb = tp - dir[q + 1];
+                if (a1 == 0.0f && b1 == 0.0f) {
+                    s_dd += (double)sqrtf(ta * ta + tb * tb);
+                } else {
+                    const double T = (double)sqrtf(a1 * a1 + b1 * b1);
+                    s_tv += T;
+                    s_dd += ((double)a1 * ta + (double)b1 * tb) / T;
+                }
+            }
+        }
+        {
+            const double v1 = block_sum<kTvThreads>(s_nn, red);
+            const double v2 = block_sum<kTvThreads>(s_dd, red);
+            const double v3 = block_sum<kTvThreads>(s_tv, red);
+            if (threadIdx.x == 0) {
+                P.partial[(size_t)8 * nb + local] = v1;
+                P.partial[(size_t)9 * nb + local] = v2;
+                P.partial[(size_t)10 * nb + local] = v3;
+            }
+            ok = coop_barrier(P.bar, nb, &sc->status, &flag);
+            if (ok) {
+                s_nn = block_sum_array<kTvThreads>(P.partial + (size_t)8 * nb, nb, red);
+                s_dd = block_sum_array<kTvThreads>(P.partial + (size_t)9 * nb, nb, red);
+                s_tv = block_sum_array<kTvThreads>(P.partial + (size_t)10 * nb, nb, red);
+            }
+        }
+        if (ok && s_dd < 0.0 && s_nn > 0.0) {
+            plain = false;
+            const double inv_norm = 1.0 / sqrt(s_nn);
+            const double geo = (a == 1.0) ? (double)K : (1.0 - pow(a, (double)K)) / (1.0 - a);
+            long long j = 0;
+            float c = 0.0f;
+            double tv_t = 0.0;
+            for (;;) {
+                if (j >= max_trials) {
+                    if (local == 0 && threadIdx.x == 0) atomicExch(&sc->status, (int)SUPCG_ERR_BACKTRACK);
+                    ok = false;
+                    break;
+                }
+                c = (float)(ldexp(gamma * pow(a, (double)ell) * geo, -(int)min(j, 2000ll)) * inv_norm);
+                ++j;
+                double sacc = 0.0;
+                for (long long e = e0; e < n; e += stride) {
+                    const int i = (int)(e / nx), jj = (int)(e - (long long)i * nx);
+                    if (i + 1 < ny && jj + 1 < nx) {
+                        const size_t p = (size_t)i * ld + jj, q = (size_t)i * nx + jj;
+                        const float yc = __fmaf_rn(c, dir[q], x[p]);
+                        const float yd = __fmaf_rn(c, dir[q + nx], x[p + ld]);
+                        const float yr = __fmaf_rn(c, dir[q + 1], x[p + 1]);
+                        const float a1 = yc - yd, b1 = yc - yr;
+                        sacc += (double)sqrtf(a1 * a1 + b1 * b1);
+                    }
+                }
+                tv_t = phase_sum(P, nb, slot, local, sacc, red, &flag, &ok);
+                slot ^= 1;
+                if (!ok) break;
+                if (tv_t <= s_tv) break;
+            }
+            if (ok) {
+                for (long long e = e0; e < n; e += stride) {
+                    const int i = (int)(e / nx), jj = (int)(e - (long long)i * nx);
+                    const size_t p = (size_t)i * ld + jj;
+                    x[p] = __fmaf_rn(c, dir[(size_t)i * nx + jj], x[p]);
+                }
+                ok = coop_barrier(P.bar, nb, &sc->status, &flag);
+                ell += (long long)K + (j - 1);
+                total_trials = j;
+                tv_first = s_tv;
+                tv_last = tv_t;
+                if (local == 0 && threadIdx.x == 0) sc->n_learned += 1;
+            }
+        } else if (local == 0 && threadIdx.x == 0) {
+            sc->n_fallback += 1;
+        }
+    }
+
+    for (int step = 0; plain && step < K && ok; ++step) {
         // t in the nonascending set at y (Sec. 3.1)
         double s_tv = 0.0, s_nn = 0.0;
         for (long long e = e0; e < n; e += stride) {
@@ -240,7 +333,7 @@ int stv_max_blocks_per_sm(int *out)
 }
 
 int launch_stv(const Launch &L, int K, double a, double gamma, long long max_trials, int *trials_out,
-               int want_snorm)
+               int want_snorm, const float *dir)
 {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(L.blocks);
@@ -253,7 +346,7 @@ int launch_stv(const Launch &L, int K, double a, double gamma, long long max_tri
     cfg.attrs = attr;
     cfg.numAttrs = 1;
     SUPCG_CUDA_TRY(cudaLaunchKernelEx(&cfg, k_stv, L.probs, L.prefix, L.count, K, a, gamma, max_trials,
-                                      trials_out, want_snorm));
+                                      trials_out, want_snorm, dir));
     return SUPCG_OK;
 }
 

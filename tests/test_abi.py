@@ -49,4 +49,4 @@ def test_param_struct_layout_matches_header():
     # offsets follow the C layout of supcg_params / supcg_report on LP64
     assert S.Params.a.offset == 8 and S.Params.max_iter.offset == 48 and S.Params.max_trials.offset == 56
     assert C.sizeof(S.Params) == 80
-    assert S.Report.ell.offset == 8 and C.sizeof(S.Report) == 48
+    assert S.Report.ell.offset == 8 and S.Report.n_learned.offset == 48 and C.sizeof(S.Report) == 56

@@ -89,6 +89,8 @@ def test_gradients_match_oracle_backward():
     g, loss = net.gradients(torch.tensor(x, device="cuda"), torch.tensor(tb, device="cuda"),
                             torch.tensor(tg, device="cuda"))
     out, acts, _ = reference_forward(p, x, tb)
+    n = ny * nx
+    tg = np.stack([t * np.float32(np.sqrt(n / np.sum(t.astype(np.float64) ** 2))) for t in tg])
     total = out.size
     assert loss == pytest.approx(np.mean((out - tg) ** 2), rel=1e-2)
     layers = S.CNN.unflatten(p.astype(np.float64))
@@ -115,11 +117,10 @@ def test_training_reduces_the_loss():
     net = S.CNN(ny, nx, max_batch=count, seed=7)
     x = torch.tensor(rng.uniform(size=(count, ny, nx)), dtype=torch.float32, device="cuda")
     tb = torch.tensor(rng.standard_normal((count, ny, nx)), dtype=torch.float32, device="cuda")
-    n = ny * nx
-    scale = torch.sqrt(n / (tb.double() ** 2).sum(dim=(1, 2), keepdim=True)).float()
-    target = 0.5 * tb * scale          # half the input direction (unit-RMS scale)
+    target = -tb                       # the reversed input direction (the loss rescales it to unit RMS)
     l0 = net.train_step(x, tb, target, lr=3e-3)
     for _ in range(150):
         net.train_step(x, tb, target, lr=3e-3, want_loss=False)
     l1 = net.train_step(x, tb, target, lr=3e-3)
+    assert l0 == pytest.approx(4.0, rel=1e-2)   # untrained: out = t~, target = -t~
     assert l1 < 0.3 * l0, (l0, l1)
