@@ -18,6 +18,12 @@ workload (it is the only other implementation of the method here).
 ellipse phantoms, 1 % Gaussian noise) solved by one batched schedule, timed
 against solving them one after another (same iterates, so the time ratio is
 the time-to-equal ratio).
+--workload learned512: the learned direction.  Training pairs (x_k, tbar,
+K-step S_TV displacement) from plain SupPCG runs (Table 1: K=40,
+a=1-1e-5, gamma=1e-2, mu=1e-5, rho=0.8) on 400 random 128^2 problems x 50
+iterations (20k pairs), network trained on the GPU, then plain vs learned
+SupPCG on the 512^2 / 720-view Poisson workload: wall time for the learned
+solve to reach the plain solve's final residual and TV.
 --workload large2048: 8 slices of 2048^2, 2880 views, 2900 bins (40 ellipses
 on a textured background, Poisson 1e4 photons): FP32- and BF16-stored
 projector pair timed on the batch, errors of both against the FP64 oracle on
@@ -300,6 +306,54 @@ def run_large(args, dev):
     return 0
 
 
+def run_learned(args, dev):
+    import numpy as np
+    import torch
+    import paper_1807_10151_gb300 as S
+    from paper_1807_10151_gb300 import learned as Lr
+    t0 = time.perf_counter()
+    X, T, D = Lr.make_training_set(400, N=128, V=180, iters=50, seed0=4000, device=dev)
+    t_data = time.perf_counter() - t0
+    net = S.CNN(128, 128, max_batch=32, seed=11)
+    Xh, Th, Dh = Lr.make_training_set(4, N=128, V=180, iters=8, seed0=4900, device=dev)
+    _, loss_untrained = net.gradients(Xh, Th, Dh)
+    t0 = time.perf_counter()
+    hist = Lr.train(net, X, T, D, epochs=2, batch=32, lr=1e-3, log_every=200)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    _, loss_trained = net.gradients(Xh, Th, Dh)
+    params = net.get_params()
+    del X, T, D
+    torch.cuda.empty_cache()
+    # evaluation on the 512^2 / 720-view Poisson workload
+    G, b_host = make_problem(0, dev)
+    b = torch.tensor(b_host, device=dev)
+    net512 = S.CNN(WL["N"], WL["N"], max_batch=1, seed=11)
+    net512.set_params(params)
+    untrained512 = S.CNN(WL["N"], WL["N"], max_batch=1, seed=11)
+    res = Lr.time_to_equal(G, b, net512, iters=args.steps, device=dev)
+    res_u = Lr.time_to_equal(G, b, untrained512, iters=args.steps, device=dev)
+    line = {
+        "metric": "time-to-equal (residual, TV): learned vs plain SupPCG", "value": res["speedup"],
+        "unit": "x (plain time / learned time)", "n_gpus": 1, "steps": args.steps, "warmup": 2,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 (network bf16)",
+        "data": "synthetic",
+        "config": {"workload": "learned_512x512_720views_725bins_poisson1e5", "K": 40, "a": 1 - 1e-5,
+                   "gamma": 1e-2, "mu": 1e-5, "rho": 0.8, "train_pairs": 20000, "train_images": "128x128",
+                   "epochs": 2, "batch": 32},
+        "trained": res, "untrained_network": res_u,
+        "training": {"data_s": t_data, "train_s": t_train, "heldout_loss_untrained": loss_untrained,
+                     "heldout_loss_trained": loss_trained, "loss_history": hist},
+    }
+    print(json.dumps(line), flush=True)
+    try:
+        os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
+        np.save(os.path.join(ROOT, "gpurun_out", "cnn_params.npy"), params)
+    except OSError:
+        pass
+    return 0
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
@@ -330,7 +384,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-iters", type=int, default=3)
-    ap.add_argument("--workload", default="plain512", choices=["plain512", "batched64", "large2048"])
+    ap.add_argument("--workload", default="plain512", choices=["plain512", "batched64", "large2048", "learned512"])
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world = env_int("WORLD_SIZE", 1)
@@ -357,6 +411,8 @@ def main():
         return run_batched(args, dev)
     if args.workload == "large2048":
         return run_large(args, dev)
+    if args.workload == "learned512":
+        return run_learned(args, dev)
     G, b_host = make_problem(rank, dev)
     b = torch.tensor(b_host, device=dev)
 

@@ -89,17 +89,19 @@ def test_learned_solve_keeps_theorem1_and_nonascent():
 
 
 def test_training_on_method_pairs_beats_the_untrained_direction():
-    """Pairs from plain SupPCG runs (x_k, tbar, K-step displacement): after training,
-    the held-out error of the proposed direction is below that of the untrained
-    network, which proposes tbar itself."""
+    """Pairs from plain SupPCG runs (x_k, tbar, K-step displacement) with steps long
+    enough for the K-step path to bend (gamma = 0.5): after training, the held-out
+    error of the proposed direction is below that of the untrained network, which
+    proposes tbar itself.  (With Table 1's short steps the path is nearly straight
+    and tbar is already within about 1 % of the K-step direction.)"""
     import paper_1807_10151_gb300 as S
     from paper_1807_10151_gb300 import learned as Lr
-    params = dict(K=10, a=1 - 1e-4, gamma=2e-2, mu=1e-5, rho=0.8)
+    params = dict(K=10, a=0.99, gamma=0.5, mu=1e-5, rho=0.8)
     X, T, D = Lr.make_training_set(10, N=64, V=90, iters=12, seed0=4100, params=params)
     Xh, Th, Dh = Lr.make_training_set(2, N=64, V=90, iters=12, seed0=4900, params=params)
     net = S.CNN(64, 64, max_batch=24, seed=3)
-    base, _ = net.gradients(Xh, Th, Dh)
     _, base_loss = net.gradients(Xh, Th, Dh)
-    Lr.train(net, X, T, D, epochs=12, batch=24, lr=2e-3)
+    Lr.train(net, X, T, D, epochs=30, batch=24, lr=1e-3)
     _, trained_loss = net.gradients(Xh, Th, Dh)
-    assert trained_loss < 0.9 * base_loss, (base_loss, trained_loss)
+    assert base_loss > 1e-3                     # the path bends: tbar alone is not the answer
+    assert trained_loss < 0.8 * base_loss, (base_loss, trained_loss)
