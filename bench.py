@@ -415,6 +415,8 @@ def main():
         return run_learned(args, dev)
     G, b_host = make_problem(rank, dev)
     b = torch.tensor(b_host, device=dev)
+    from paper_1807_10151_gb300 import autotune
+    tiling = autotune.tune(G)          # forward-projector tile for this geometry (cached per bucket)
 
     def barrier():
         torch.cuda.synchronize()
@@ -498,6 +500,7 @@ def main():
             "config": {"workload": WORKLOAD, "image": [WL["N"], WL["N"]], "views": WL["V"], "bins": WL["U"],
                        "iterations": args.steps, "K": WL["K"], "gamma": WL["gamma"], "a": WL["a"],
                        "mu": WL["mu"], "rho": WL["rho"], "graph": True, "parallelism": f"replicas{world}",
+                       "fwd_tile": tiling["tile"],
                        "l2": "flushed (256 MB write) before the timed solve; the ~14 MB working set of one "
                              "512^2 problem then stays L2-resident across its iterations"},
             "roofline": {"bound": "alu", "kernel": "k_forward", "achieved": achieved, "peak": peak_alu,

@@ -69,6 +69,14 @@ int supcg_create_geometry(int nx, int ny, double pixel_size, int n_views, const 
                           int n_bins, double bin_spacing, double det_center_offset,
                           int storage, supcg_geometry *out);
 
+/* Tiling of the forward projector: rays (bins) per thread block, one of 32,
+ * 64, 96, 128 (default: the largest whose staged box fits).  Results do not
+ * depend on it (every ray sums its row terms in the same order).  Setting it
+ * frees the geometry's scratch (rebuilt on next use).  Used by the autotuner.
+ * Errors: SUPCG_ERR_ARG, SUPCG_ERR_UNSUPPORTED (box wider than 256 columns). */
+int supcg_set_tiling(supcg_geometry g, int fwd_bins_per_block);
+int supcg_get_tiling(supcg_geometry g, int *fwd_bins_per_block);
+
 /* Free the geometry and all scratch it owns (synchronises the device first). */
 int supcg_destroy_geometry(supcg_geometry g);
 

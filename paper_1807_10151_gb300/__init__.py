@@ -29,7 +29,8 @@ EXPORTED = ["supcg_create_geometry", "supcg_destroy_geometry", "supcg_project", 
             "supcg_solve_batched", "supcg_status_string", "supcg_solve_profiled", "supcg_kernel_launches",
             "supcg_precondition_noalloc", "supcg_cnn_create", "supcg_cnn_destroy", "supcg_cnn_num_params",
             "supcg_cnn_get_params", "supcg_cnn_set_params", "supcg_cnn_forward", "supcg_cnn_gradients",
-            "supcg_cnn_train_step", "supcg_solve_trace", "supcg_solve_learned"]
+            "supcg_cnn_train_step", "supcg_solve_trace", "supcg_solve_learned", "supcg_set_tiling",
+            "supcg_get_tiling"]
 KINDS = ["forward", "backward", "fft", "stv", "vector", "cnn"]
 
 _lock = threading.Lock()
@@ -105,6 +106,8 @@ def load(allow_build: bool = True):
         L.supcg_cnn_train_step.argtypes = [vp, vp, vp, vp, i, d, C.POINTER(d), vp]
         L.supcg_solve_trace.argtypes = [vp, vp, vp, C.POINTER(Params), C.POINTER(Report), vp, vp, vp]
         L.supcg_solve_learned.argtypes = [vp, vp, vp, vp, C.POINTER(Params), C.POINTER(Report), vp, vp]
+        L.supcg_set_tiling.argtypes = [vp, i]
+        L.supcg_get_tiling.argtypes = [vp, C.POINTER(i)]
         L.supcg_status_string.argtypes = [i]
         L.supcg_status_string.restype = C.c_char_p
         for name in EXPORTED:
@@ -234,6 +237,15 @@ class Geometry:
             self.close()
         except Exception:
             pass
+
+    def set_tiling(self, fwd_bins_per_block):
+        """Forward-projector rays per block (supcg_set_tiling); returns the status."""
+        return load().supcg_set_tiling(self.handle, int(fwd_bins_per_block))
+
+    def get_tiling(self):
+        v = C.c_int()
+        _check(load().supcg_get_tiling(self.handle, C.byref(v)), "supcg_get_tiling")
+        return v.value
 
     @property
     def _dt(self):

@@ -306,6 +306,34 @@ extern "C" int supcg_create_geometry(int nx, int ny, double pixel_size, int n_vi
     return SUPCG_OK;
 }
 
+extern "C" int supcg_set_tiling(supcg_geometry g, int fwd_bins_per_block)
+{
+    if (!g || fwd_bins_per_block < 32 || fwd_bins_per_block > 128 || fwd_bins_per_block % 32) return SUPCG_ERR_ARG;
+    double span = 0.0;
+    for (const ViewP &vp : g->views)
+        span = std::max(span, fabs((double)vp.a_tau) * (fwd_bins_per_block - 1) +
+                                  fabs((double)vp.b_o) * (kRowsPerChunk - 1));
+    const int bw = round_up((int)ceil(span + 11.0), 4);
+    if (bw > 256) return SUPCG_ERR_UNSUPPORTED;
+    cudaDeviceSynchronize();
+    g->BU = fwd_bins_per_block;
+    g->BW = bw;
+    g->ntu = (g->U + g->BU - 1) / g->BU;
+    // workspaces hold launch shapes and TMA boxes of the old tiling
+    free_ws(g->ws_ops);
+    free_ws(g->ws_solve);
+    free_ws(g->ws_batch);
+    g->ops_batch = 0;
+    return SUPCG_OK;
+}
+
+extern "C" int supcg_get_tiling(supcg_geometry g, int *fwd_bins_per_block)
+{
+    if (!g || !fwd_bins_per_block) return SUPCG_ERR_ARG;
+    *fwd_bins_per_block = g->BU;
+    return SUPCG_OK;
+}
+
 extern "C" int supcg_destroy_geometry(supcg_geometry g)
 {
     if (!g) return SUPCG_ERR_ARG;

@@ -284,3 +284,19 @@ def test_solve_large_config_properties():
     # sampled residual energy is consistent with the reported f (unbiased estimate)
     est = np.sum(r_s ** 2) * og.m / rays.size
     assert est == pytest.approx(rep["f_last"], rel=0.15)
+
+
+def test_forward_tiles_give_identical_results_and_autotuner_picks_one(tmp_path):
+    from paper_1807_10151_gb300 import autotune
+    og = O.Geometry(160, V=120, U=228)
+    G = gpu_geometry(og)
+    x = to_dev(np.random.default_rng(12).uniform(size=(og.ny, og.nx)))
+    outs = []
+    for t in (128, 96, 64, 32):
+        assert G.set_tiling(t) == 0 and G.get_tiling() == t
+        outs.append(G.project(x).cpu().numpy())
+    for o in outs[1:]:
+        np.testing.assert_array_equal(o, outs[0])
+    rec = autotune.tune(G, reps=2, cache=str(tmp_path / "tiling.json"))
+    assert rec["tile"] in (128, 96, 64, 32) and G.get_tiling() == rec["tile"]
+    assert autotune.tune(G, cache=str(tmp_path / "tiling.json")) == rec      # cached
