@@ -2,19 +2,20 @@
 // proposes the TV-nonascending direction of the superiorization step).
 //
 // Network: five 3x3 convolutions (zero padding), channels
-//   8 (x / rms(x), tbar scaled to unit RMS, six zeros) -> 32 -> 32 -> 32 -> 32 -> 1,
+//   16 (x / rms(x), tbar scaled to unit RMS, fourteen zeros) -> 32 -> 32 -> 32 -> 32 -> 1,
 // ReLU after the first four; the output is added to the scaled tbar input
 // (a residual around the plain direction).  Activations are BF16 NHWC,
 // weights BF16, accumulation FP32.
 //
 // Every convolution (forward, and the input-gradient pass of training, which
 // is a convolution with the flipped, transposed kernel) is an implicit GEMM on
-// the 5th-generation tensor cores: a CTA gathers the im2col tile of 128 pixels
-// (M = 128, K = 9 * Cin rounded up to 16) and the packed weights (N = Cout)
-// into shared memory in the no-swizzle K-major core-matrix layout, one thread
-// issues the K/16 tcgen05.mma instructions into an FP32 tensor-memory
-// accumulator, and the four warps read their 32 lanes back with tcgen05.ld for
-// the epilogue (bias, ReLU or ReLU-mask, BF16 store).  The weight gradient is
+// the 5th-generation tensor cores: a CTA stages the three input rows around
+// 128 output pixels (M = 128) and the packed weights (N = Cout, K = 9 * Cin)
+// in shared memory, one thread issues one tcgen05.mma per tap and 16 channels,
+// each reading the staged rows through a descriptor shifted by the tap's
+// column offset (no im2col copy), into an FP32 tensor-memory accumulator, and
+// the four warps read their 32 lanes back with tcgen05.ld for the epilogue
+// (bias, ReLU or ReLU-mask, BF16 store).  The weight gradient is
 // a reduction over pixels on the CUDA cores with FP32 accumulation and a
 // deterministic two-level sum.  Adam keeps FP32 master weights.
 #include <math.h>
@@ -28,10 +29,10 @@ namespace supcg {
 
 constexpr int kCnnLayers = 5;
 constexpr int kCh = 32;     // hidden channels
-constexpr int kInCh = 8;    // stored input channels (2 used)
+constexpr int kInCh = 16;   // stored input channels (2 used; 16 so that one tap fills one K = 16 step)
 constexpr int kTile = 128;  // pixels per MMA tile
 
-__host__ __device__ constexpr int kpad(int cin) { return (9 * cin + 15) / 16 * 16; }
+__host__ __device__ constexpr int kpad(int cin) { return 9 * cin; }   // cin is 16 or 32
 
 // layer l (0-based): storage channels of its input, real input channels, output channels
 __host__ __device__ constexpr int l_cin(int l) { return l == 0 ? kInCh : kCh; }
@@ -53,40 +54,41 @@ struct ConvArgs {
     int *status;
 };
 
+// One CTA: the 128 pixels (i, j0 .. j0+127) of one image row.  Shared memory
+// holds the three input rows i-1, i, i+1 over columns j0-1 .. j0+128 (zero
+// outside the image), 8-channel chunk by chunk, 16 bytes per pixel, pixels
+// contiguous: [dy][chunk][kPixRows].  The A operand of tap (dy, dx) is that
+// block started dx pixels in: 8-pixel row groups 128 bytes apart (SBO), channel
+// chunks kPixRows * 16 bytes apart (LBO), so the nine taps need no im2col copy.
+constexpr int kPixRows = 136;   // staged pixels per row and chunk (>= 130, multiple of 8)
+
 template <int CIN, int NOUT, int EPI>
 __global__ void __launch_bounds__(128) k_conv(ConvArgs a)
 {
-    constexpr int KP = kpad(CIN);
-    constexpr int KG = KP / 8;       // core-matrix columns along K
-    constexpr int CH8 = CIN / 8;     // 16-byte chunks per pixel
+    constexpr int CH8 = CIN / 8;            // 16-byte chunks per pixel
+    constexpr int KP = 9 * CIN;             // GEMM K (multiple of 16: CIN is 16 or 32)
+    constexpr int KG = KP / 8;
     extern __shared__ __align__(1024) unsigned char sm_raw[];
-    __nv_bfloat16 *sa = reinterpret_cast<__nv_bfloat16 *>(sm_raw);   // 128 x KP
-    __nv_bfloat16 *sb = sa + kTile * KP;                              // NOUT x KP
+    __nv_bfloat16 *sa = reinterpret_cast<__nv_bfloat16 *>(sm_raw);   // [3][CH8][kPixRows][8]
+    __nv_bfloat16 *sb = sa + 3 * CH8 * kPixRows * 8;                  // NOUT x KP, core-matrix layout
     __shared__ __align__(8) uint64_t bar;
     __shared__ uint32_t tbase;
     const int t = threadIdx.x, warp = t >> 5;
+    const int tiles_row = (a.nx + kTile - 1) / kTile;
+    const long long rowid = blockIdx.x / tiles_row;      // img * ny + i
+    const int jb = blockIdx.x - (int)(rowid * tiles_row);
+    const int img = (int)(rowid / a.ny), i = (int)(rowid - (long long)img * a.ny);
+    const int j0 = jb * kTile;
     const long long n = (long long)a.ny * a.nx;
-    const long long total = n * a.count;
-    const long long p0 = (long long)blockIdx.x * kTile;
 
-    // A: for tap, pixel r, chunk c8: channels 8*c8.. of the tap's neighbour of pixel r
-    for (int e = t; e < 9 * kTile * CH8; e += kTile) {
-        const int c8 = e % CH8, r = (e / CH8) % kTile, tap = e / (CH8 * kTile);
-        const long long p = p0 + r;
+    // stage: consecutive threads take consecutive chunks of a pixel, then the next pixel
+    for (int e = t; e < 3 * 130 * CH8; e += kTile) {
+        const int c8 = e % CH8, q = (e / CH8) % 130, dy = e / (CH8 * 130);
+        const int ii = i + dy - 1, jj = j0 + q - 1;
         uint4 v = make_uint4(0u, 0u, 0u, 0u);
-        if (p < total) {
-            const long long img = p / n, pi = p - img * n;
-            const int i = (int)(pi / a.nx), j = (int)(pi - (long long)i * a.nx);
-            const int ii = i + tap / 3 - 1, jj = j + tap % 3 - 1;
-            if (ii >= 0 && ii < a.ny && jj >= 0 && jj < a.nx)
-                v = __ldg(reinterpret_cast<const uint4 *>(a.in + ((img * n + (long long)ii * a.nx + jj) * CIN + c8 * 8)));
-        }
-        const int kg = tap * CH8 + c8;
-        *reinterpret_cast<uint4 *>(sa + ((r >> 3) * KG + kg) * 64 + (r & 7) * 8) = v;
-    }
-    for (int e = t; e < kTile * (KG - 9 * CH8); e += kTile) {   // K padding
-        const int r = e % kTile, kg = 9 * CH8 + e / kTile;
-        *reinterpret_cast<uint4 *>(sa + ((r >> 3) * KG + kg) * 64 + (r & 7) * 8) = make_uint4(0u, 0u, 0u, 0u);
+        if (ii >= 0 && ii < a.ny && jj >= 0 && jj < a.nx)
+            v = __ldg(reinterpret_cast<const uint4 *>(a.in + (((long long)img * n + (long long)ii * a.nx + jj) * CIN + c8 * 8)));
+        *reinterpret_cast<uint4 *>(sa + ((dy * CH8 + c8) * kPixRows + q) * 8) = v;
     }
     for (int e = t; e < NOUT * KG; e += kTile) {   // B: packed weights
         const int row = e / KG, kg = e % KG;
@@ -106,22 +108,31 @@ __global__ void __launch_bounds__(128) k_conv(ConvArgs a)
     if (t == 0) {
         constexpr uint32_t idesc = tc_idesc_bf16(128, NOUT);
         const uint32_t sa_u = smem_u32(sa), sb_u = smem_u32(sb);
+        int step = 0;
 #pragma unroll 1
-        for (int ks = 0; ks < KP / 16; ++ks)
-            tc_mma_bf16(tmem, tc_sdesc(sa_u + ks * 256, 128, KG * 128), tc_sdesc(sb_u + ks * 256, 128, KG * 128),
-                        idesc, ks > 0);
+        for (int tap = 0; tap < 9; ++tap) {
+            const int dy = tap / 3, dx = tap % 3;
+#pragma unroll
+            for (int cp = 0; cp < CH8 / 2; ++cp, ++step) {
+                const uint32_t a_addr = sa_u + (uint32_t)(((dy * CH8 + 2 * cp) * kPixRows + dx) * 16);
+                const uint32_t b_addr = sb_u + (uint32_t)((tap * CH8 + 2 * cp) * 128);
+                tc_mma_bf16(tmem, tc_sdesc(a_addr, kPixRows * 16, 128), tc_sdesc(b_addr, 128, KG * 128), idesc,
+                            step > 0);
+            }
+        }
         tc_commit(&bar);
     }
     bool ok = mbar_wait(&bar, 0);
     tc_fence_after();
     const int r = warp * 32 + (t & 31);
-    const long long p = p0 + r;
+    const int j = j0 + r;
+    const long long p = (long long)img * n + (long long)i * a.nx + j;
     if (ok) {
         float acc[32];
         const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
         tc_ld16(lane_addr, acc);
         if (NOUT == 32) tc_ld16(lane_addr + 16, acc + 16);
-        if (p < total) {
+        if (j < a.nx) {
             if (EPI == EPI_LAST) {
                 a.out_f[p] = acc[0] + a.bias[0] + a.resid[p];
             } else {
@@ -155,16 +166,15 @@ __global__ void __launch_bounds__(128) k_conv(ConvArgs a)
 template <int CIN, int NOUT, int EPI>
 static int launch_conv(const ConvArgs &a, cudaStream_t st)
 {
-    constexpr int KP = kpad(CIN);
-    constexpr int smem = (kTile + NOUT) * KP * 2;
+    constexpr int KP = 9 * CIN;
+    constexpr int smem = (3 * (CIN / 8) * kPixRows * 8 + NOUT * KP) * 2;
     static int set = 0;
     if (!set) {
         SUPCG_CUDA_TRY(cudaFuncSetAttribute(k_conv<CIN, NOUT, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
         set = 1;
     }
-    const long long total = (long long)a.ny * a.nx * a.count;
-    const int blocks = (int)((total + kTile - 1) / kTile);
-    k_conv<CIN, NOUT, EPI><<<blocks, kTile, smem, st>>>(a);
+    const long long blocks = (long long)a.count * a.ny * ((a.nx + kTile - 1) / kTile);
+    k_conv<CIN, NOUT, EPI><<<(unsigned)blocks, kTile, smem, st>>>(a);
     SUPCG_CUDA_TRY(cudaGetLastError());
     return SUPCG_OK;
 }
@@ -265,7 +275,7 @@ __global__ void __launch_bounds__(1024) k_norms(const float *x, const float *tb,
 }
 
 // Input tensor: channel 0 = x / rms(x), channel 1 = tbar scaled to unit RMS,
-// channels 2..7 = 0; resid = channel 1 in FP32.
+// channels 2..15 = 0; resid = channel 1 in FP32.
 __global__ void k_pack_input(const float *x, const float *tb, const double *norms, long long n, int count,
                              __nv_bfloat16 *act0, float *resid)
 {
@@ -276,17 +286,18 @@ __global__ void k_pack_input(const float *x, const float *tb, const double *norm
     const float fx = sx > 0.0 ? (float)sqrt((double)n / sx) : 0.0f;
     const float ft = st > 0.0 ? (float)sqrt((double)n / st) : 0.0f;
     const float v0 = x[p] * fx, v1 = tb[p] * ft;
-    __align__(16) __nv_bfloat16 o[8];
+    __align__(16) __nv_bfloat16 o[16];
     o[0] = __float2bfloat16_rn(v0);
     o[1] = __float2bfloat16_rn(v1);
 #pragma unroll
-    for (int c = 2; c < 8; ++c) o[c] = __float2bfloat16_rn(0.0f);
-    reinterpret_cast<uint4 *>(act0)[p] = *reinterpret_cast<const uint4 *>(o);
+    for (int c = 2; c < 16; ++c) o[c] = __float2bfloat16_rn(0.0f);
+    reinterpret_cast<uint4 *>(act0)[2 * p] = reinterpret_cast<const uint4 *>(o)[0];
+    reinterpret_cast<uint4 *>(act0)[2 * p + 1] = reinterpret_cast<const uint4 *>(o)[1];
     resid[p] = v1;
 }
 
 // Loss L = mean (out - target~)^2 with target~ the target scaled per image to unit
-// RMS; G5 = dL/dout as an 8-channel BF16 tensor (channel 0).
+// RMS; G5 = dL/dout as a 16-channel BF16 tensor (channel 0).
 __global__ void __launch_bounds__(256) k_loss(const float *out, const float *target, const double *tnorms,
                                               long long n, long long total, __nv_bfloat16 *G5, double *partial)
 {
@@ -299,11 +310,12 @@ __global__ void __launch_bounds__(256) k_loss(const float *out, const float *tar
         const float ft = tn > 0.0 ? (float)sqrt((double)n / tn) : 0.0f;
         const float d = out[p] - target[p] * ft;
         s += (double)d * (double)d;
-        __align__(16) __nv_bfloat16 o[8];
+        __align__(16) __nv_bfloat16 o[16];
         o[0] = __float2bfloat16_rn(scale * d);
 #pragma unroll
-        for (int c = 1; c < 8; ++c) o[c] = __float2bfloat16_rn(0.0f);
-        reinterpret_cast<uint4 *>(G5)[p] = *reinterpret_cast<const uint4 *>(o);
+        for (int c = 1; c < 16; ++c) o[c] = __float2bfloat16_rn(0.0f);
+        reinterpret_cast<uint4 *>(G5)[2 * p] = reinterpret_cast<const uint4 *>(o)[0];
+        reinterpret_cast<uint4 *>(G5)[2 * p + 1] = reinterpret_cast<const uint4 *>(o)[1];
     }
     s = block_sum<256>(s, red);
     if (threadIdx.x == 0) partial[blockIdx.x] = s;
