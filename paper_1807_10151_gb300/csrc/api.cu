@@ -45,19 +45,25 @@ static EncodeTiledFn encode_fn()
     return fn;
 }
 
+// Tiled map of `rank` dimensions (innermost first), no swizzle, zero fill outside the tensor.
+int encode_tiled(CUtensorMap *m, CUtensorMapDataType type, int rank, void *base, const cuuint64_t *dims,
+                 const cuuint64_t *strides_bytes, const cuuint32_t *box)
+{
+    EncodeTiledFn fn = encode_fn();
+    if (!fn || rank < 1 || rank > 5) return SUPCG_ERR_CUDA;
+    const cuuint32_t es[5] = {1, 1, 1, 1, 1};
+    CUresult r = fn(m, type, (cuuint32_t)rank, base, dims, strides_bytes, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                    CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? SUPCG_OK : SUPCG_ERR_CUDA;
+}
+
 // 2-D FP32 map over [outer][pitch] with logical extent inner x outer, box BW x rows.
 static int encode_map(CUtensorMap *m, float *base, int inner, int outer, int pitch, int BW, int rows)
 {
-    EncodeTiledFn fn = encode_fn();
-    if (!fn) return SUPCG_ERR_CUDA;
-    cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)outer};
-    cuuint64_t strides[1] = {(cuuint64_t)pitch * 4};
-    cuuint32_t box[2] = {(cuuint32_t)BW, (cuuint32_t)rows};
-    cuuint32_t es[2] = {1, 1};
-    CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, es,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    return r == CUDA_SUCCESS ? SUPCG_OK : SUPCG_ERR_CUDA;
+    const cuuint64_t dims[2] = {(cuuint64_t)inner, (cuuint64_t)outer};
+    const cuuint64_t strides[1] = {(cuuint64_t)pitch * 4};
+    const cuuint32_t box[2] = {(cuuint32_t)BW, (cuuint32_t)rows};
+    return encode_tiled(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box);
 }
 
 // ------------------------------------------------------------------ FFT plan

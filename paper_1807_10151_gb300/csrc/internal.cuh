@@ -320,6 +320,8 @@ struct Launch {
 
 int launch_forward(const Launch &L, int which, int mode);
 int launch_backward(const Launch &L, int mode, int bwin);
+int encode_tiled(CUtensorMap *m, CUtensorMapDataType type, int rank, void *base, const cuuint64_t *dims,
+                 const cuuint64_t *strides_bytes, const cuuint32_t *box);
 int launch_transpose(const Launch &L, int which);          // x -> x^T (which 0) or p -> p^T (which 1)
 int launch_stage_in(const Launch &L, int which);           // caller image -> x and x^T (0) or g (1)
 int launch_stage_sino(const Launch &L, int which);         // caller sinogram -> r (0, in_user) or bpad (1, in_user2)
