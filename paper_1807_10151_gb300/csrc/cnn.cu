@@ -271,10 +271,16 @@ static int launch_conv(const ConvArgs &a, cudaStream_t st)
     static int set = 0, ctas = 1;
     if (!set) {
         SUPCG_CUDA_TRY(cudaFuncSetAttribute(k_conv<CIN, NOUT, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        SUPCG_CUDA_TRY(cudaFuncSetAttribute(k_conv<CIN, NOUT, EPI>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                            (int)cudaSharedmemCarveoutMaxShared));
         int per_sm = 1, dev = 0, nsm = 1;
         SUPCG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_conv<CIN, NOUT, EPI>, kTile, smem));
         SUPCG_CUDA_TRY(cudaGetDevice(&dev));
         SUPCG_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        int smem_sm = 0;
+        SUPCG_CUDA_TRY(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+        const int by_smem = smem_sm / (smem + 2048);   // dynamic + static shared memory and the per-CTA reserve
+        per_sm = std::max(per_sm, std::min(by_smem, 512 / 64));   // 64 tensor-memory columns per CTA
         ctas = nsm * std::max(1, per_sm);
         set = 1;
     }
@@ -456,6 +462,8 @@ static int launch_wgrad(const __nv_bfloat16 *in, const __nv_bfloat16 *G, int cin
     static int set = 0;
     if (!set) {
         SUPCG_CUDA_TRY(cudaFuncSetAttribute(k_wgrad<CIN, GCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        SUPCG_CUDA_TRY(cudaFuncSetAttribute(k_wgrad<CIN, GCH>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                            (int)cudaSharedmemCarveoutMaxShared));
         set = 1;
     }
     CUtensorMap tin, tg;
@@ -469,30 +477,43 @@ static int launch_wgrad(const __nv_bfloat16 *in, const __nv_bfloat16 *G, int cin
     return grid;
 }
 
-// out[e] = sum_b partial[b][e] in a fixed order.
-__global__ void k_reduce(const float *partial, int nb, int len, float *out)
+// out[e] = sum_b partial[b][e] in a fixed order: warp w of a block adds the
+// partials b = w, w + 8, ... for 32 consecutive e (lane = e), then warp 0 adds
+// the eight warp sums in warp order.
+__global__ void __launch_bounds__(256) k_reduce(const float *partial, int nb, int len, float *out)
 {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= len) return;
+    __shared__ double sh[8][33];
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    const int e = blockIdx.x * 32 + l;
     double s = 0.0;
-    for (int b = 0; b < nb; ++b) s += (double)partial[(size_t)b * len + e];
-    out[e] = (float)s;
+    if (e < len)
+        for (int b = w; b < nb; b += 8) s += (double)partial[(size_t)b * len + e];
+    sh[w][l] = s;
+    __syncthreads();
+    if (w == 0 && e < len) {
+        double tot = 0.0;
+#pragma unroll
+        for (int k = 0; k < 8; ++k) tot += sh[k][l];
+        out[e] = (float)tot;
+    }
 }
 
 // ------------------------------------------------------------------ input, loss, optimiser
 // Per-image unit-RMS scale factors sqrt(n / sum x^2) and sqrt(n / sum tbar^2)
-// (0 for an all-zero image).  Grid (kNormBlocks, count): each block sums a
-// contiguous part of one image in FP64; the image's last block adds the
-// partials in block order (deterministic) and writes the two FP32 factors.
+// (0 for an all-zero image).  Grid (nblk, count), nblk = norm_blocks(n) <= kNormBlocks:
+// each block sums a contiguous part of one image in FP64; the image's last block
+// adds the partials in block order (deterministic) and writes the two FP32 factors.
 constexpr int kNormBlocks = 64;
+
+static int norm_blocks(long long n) { return (int)std::max(1ll, std::min<long long>(kNormBlocks, n / 4096)); }
 
 __global__ void __launch_bounds__(256) k_norms(const float *x, const float *tb, long long n, double *part,
                                                unsigned *counter, float *scale)
 {
     __shared__ double red[40];
     __shared__ int sh_last;
-    const int img = blockIdx.y, blk = blockIdx.x;
-    const long long per = (n + kNormBlocks - 1) / kNormBlocks;
+    const int img = blockIdx.y, blk = blockIdx.x, nblk = gridDim.x;
+    const long long per = (n + nblk - 1) / nblk;
     const long long e0 = blk * per, e1 = e0 + per < n ? e0 + per : n;
     const float *xi = x + img * n, *ti = tb + img * n;
     double sx = 0.0, st = 0.0;
@@ -507,11 +528,11 @@ __global__ void __launch_bounds__(256) k_norms(const float *x, const float *tb, 
         part[(2 * img) * kNormBlocks + blk] = sx;
         part[(2 * img + 1) * kNormBlocks + blk] = st;
     }
-    if (!last_block(&counter[img], kNormBlocks, &sh_last)) return;
+    if (!last_block(&counter[img], nblk, &sh_last)) return;
     if (threadIdx.x < 2) {
         const volatile double *pp = part + (2 * img + threadIdx.x) * kNormBlocks;
         double s = 0.0;
-        for (int k = 0; k < kNormBlocks; ++k) s += pp[k];
+        for (int k = 0; k < nblk; ++k) s += pp[k];
         scale[2 * img + threadIdx.x] = s > 0.0 ? (float)sqrt((double)n / s) : 0.0f;
     }
     if (threadIdx.x == 0) counter[img] = 0;   // ready for the next launch
@@ -763,7 +784,7 @@ namespace supcg {
 int cnn_forward(supcg_cnn net, const float *d_x, const float *d_tbar, int count, cudaStream_t st)
 {
     const long long n = (long long)net->ny * net->nx;
-    k_norms<<<dim3(kNormBlocks, count), 256, 0, st>>>(d_x, d_tbar, n, net->npart, net->ncount, net->scales);
+    k_norms<<<dim3(norm_blocks(n), count), 256, 0, st>>>(d_x, d_tbar, n, net->npart, net->ncount, net->scales);
     k_pack_input<<<(unsigned)((n * count + 255) / 256), 256, 0, st>>>(d_x, d_tbar, net->scales, n, count, net->act[0],
                                                                      net->resid);
     SUPCG_CUDA_TRY(cudaGetLastError());
@@ -813,7 +834,7 @@ static int cnn_backward(supcg_cnn net, int count, cudaStream_t st)
                                         net->wg_ctas, net->partial, net->status, st);
         if (nb < 0) return nb;
         const int len = cout * cin_real * 9 + cout;
-        k_reduce<<<(len + 255) / 256, 256, 0, st>>>(net->partial, nb, len, net->grads + net->off_w[l]);
+        k_reduce<<<(len + 31) / 32, 256, 0, st>>>(net->partial, nb, len, net->grads + net->off_w[l]);
         SUPCG_CUDA_TRY(cudaGetLastError());
         if (l == 0) break;
         // input gradient: dL/dz_{l-1} = conv(gbuf[l], flipped W_l) masked by act[l] > 0
@@ -832,7 +853,7 @@ static int cnn_loss(supcg_cnn net, const float *d_target, int count, cudaStream_
     const long long n = (long long)net->ny * net->nx;
     const long long total = n * count;
     const int blocks = (int)std::min<long long>(1024, (total + 255) / 256);
-    k_norms<<<dim3(kNormBlocks, count), 256, 0, st>>>(d_target, d_target, n, net->npart, net->ncount, net->tscales);
+    k_norms<<<dim3(norm_blocks(n), count), 256, 0, st>>>(d_target, d_target, n, net->npart, net->ncount, net->tscales);
     k_loss<<<blocks, 256, 0, st>>>(net->out, d_target, net->tscales, n, total, net->gbuf[kCnnLayers - 1], net->lpart);
     SUPCG_CUDA_TRY(cudaGetLastError());
     if (h_loss) {
