@@ -233,8 +233,9 @@ extern "C" int supcg_create_geometry(int nx, int ny, double pixel_size, int n_vi
         mcl = std::max(mcl, fabs((double)vp.cu_lo));
         msl = std::max(msl, fabs((double)vp.su_lo));
         vp.E = (float)(r * (a + b) / 2.0);
-        vp.S = (b > 0.0) ? (float)(g->ds / (a * b)) : 0.0f;
-        vp.P = (float)(g->d / a);
+        const double Sd = (b > 0.0) ? g->ds / (a * b) : 0.0, Pd = g->d / a;
+        vp.Sn = (float)(Sd / Pd);
+        vp.P = (float)Pd;
         const bool classB = as > ac;
         if (!classB) {
             vp.a_tau = (float)(1.0 / cu);
@@ -247,7 +248,7 @@ extern "C" int supcg_create_geometry(int nx, int ny, double pixel_size, int n_vi
             vp.g0 = (float)(cy - (cu / su) * cx);
             B.push_back(v);
         }
-        vp.ES = (float)(r * (a + b) / 2.0 * (b > 0.0 ? g->ds / (a * b) : 0.0));
+        vp.ESn = (float)(r * (a + b) / 2.0 * Sd / Pd);
         // candidate windows: a ray's footprint on a row (column) is (a+b)/(2a) pixels
         // either side of its centre, a pixel's footprint E bins either side of its
         // projected centre; 0.02 covers the rounding of the centres

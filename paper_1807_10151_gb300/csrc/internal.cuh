@@ -40,14 +40,14 @@ constexpr long long kSpinLimit = 1ll << 24;  // bounded waits (iterations of a ~
 struct __align__(16) ViewP {
     float cu, su;   // cos(theta) d/ds, sin(theta) d/ds (approximate uses: candidate centres, boxes)
     float E;        // footprint half-width in bins: (d/ds) (|cos|+|sin|) / 2
-    float S;        // ds / (|cos| |sin|): length per bin on the trapezoid's sides
+    float Sn;       // S / P, S = ds / (|cos| |sin|) the length per bin on the trapezoid's sides
     float P;        // plateau length d / max(|cos|, |sin|)
     float a_tau;    // forward: inner index of the ray centre = a_tau*tau + b_o*outer + g0
     float b_o;
     float g0;
     float cu_hi, su_hi, cu_lo, su_lo;
     int flags;      // kView* bits
-    float ES;       // E * S (rounded once): the trapezoid is fmaf(-|delta|, S, ES) clamped to [0, P]
+    float ESn;      // E * S / P (rounded once): the trapezoid is P * sat(fmaf(-|delta|, Sn, ESn))
     float hwq;      // forward: half-width of a ray's footprint in inner-index units, plus a 0.02 margin
     float hwu;      // backward: half-width of a pixel's footprint in bins, plus a 0.02 margin
 };
@@ -57,16 +57,29 @@ constexpr int kViewFwd3 = 4;     // a ray can meet three pixels of a row within 
 constexpr int kViewBwd3 = 8;     // a pixel can meet three bins within the margin
 
 // Intersection length for a ray at signed detector distance `delta` (bins)
-// from the pixel centre.  Axis-aligned views use the box limit with half
-// weight exactly on the edge; others the trapezoid.  Explicit _rn intrinsics
-// pin the rounding so that every call site produces identical bits.
-__device__ __forceinline__ float weight(float delta, const ViewP &vp)
+// from the pixel centre, in units of the view's plateau length P: axis-aligned
+// views use the box limit (1 inside, 1/2 exactly on the edge, 0 outside), the
+// others the trapezoid clamped to [0, 1] by one saturating FMA.  Both
+// projectors evaluate it from the same FP32 operands with pinned rounding, so
+// they produce identical bits; the factor P is applied once per ray (forward)
+// or to the staged sinogram values (backward).
+__device__ __forceinline__ float weight_unit(float ad, float E, float Sn, float ESn, bool axis)
 {
-    float ad = fabsf(delta);
-    if (vp.flags & kViewAxis)
-        return ad < vp.E ? vp.P : (ad == vp.E ? 0.5f * vp.P : 0.0f);
-    return fminf(vp.P, fmaxf(0.0f, __fmaf_rn(-ad, vp.S, vp.ES)));
+    if (axis) return ad < E ? 1.0f : (ad == E ? 0.5f : 0.0f);
+    float w;
+    asm("fma.rn.sat.f32 %0, %1, %2, %3;" : "=f"(w) : "f"(-ad), "f"(Sn), "f"(ESn));
+    return w;
 }
+
+// ceil(x) for |x| < 2^22 by one FP32 addition rounded upward: x + 1.5 * 2^23
+// lies where FP32 numbers are the integers, so that sum's bits minus those of
+// 1.5 * 2^23 give ceil(x) as an integer, and its value minus 1.5 * 2^23 gives it
+// as a float (both exact).  Replaces a float-to-int and an int-to-float conversion.
+constexpr float kCeilMagic = 12582912.0f;
+constexpr int kCeilMagicBits = 0x4B400000;
+__device__ __forceinline__ float ceil_magic(float x) { return __fadd_ru(x, kCeilMagic); }
+__device__ __forceinline__ int magic_int(float m) { return __float_as_int(m) - kCeilMagicBits; }
+__device__ __forceinline__ float magic_float(float m) { return __fsub_rn(m, kCeilMagic); }
 
 // Approximate detector coordinate of a pixel centre (candidate selection only).
 __device__ __forceinline__ float det_coord(const ViewP &vp, float Xj, float Yi)

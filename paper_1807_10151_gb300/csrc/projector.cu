@@ -42,13 +42,14 @@ __device__ __forceinline__ void fwd_rows(const Prob &P, const ViewP &vp, float t
     // inner coordinate of inner index q: X = q - cx (class A) or Y = cy - q (class B)
     const float c_in = CLASS_B ? P.cy : P.cx;
     const float dI = CLASS_B ? -1.0f : 1.0f;
-    const float E = vp.E, S = vp.S, ES = vp.ES, Pl = vp.P;
+    const float E = vp.E, Sn = vp.Sn, ESn = vp.ESn;
     const float qh = __fsub_rn(qm, vp.hwq);
     const float *prow = patch - qs;
     float rs = 0.0f;   // FP32 sum of up to 8 rows, then folded into (sum, comp)
 #pragma unroll 4
     for (int r = 0; r < rows; ++r) {
-        int q0 = __float2int_ru(__fmaf_rn((float)r, vp.b_o, qh));
+        const float qc = ceil_magic(__fmaf_rn((float)r, vp.b_o, qh));
+        int q0 = magic_int(qc);
         if (CHECKED) {
             const int idx = q0 - qs;
             if (idx < 0 || idx > BW - NC) {   // outside the staged box: never for a valid box (host-checked)
@@ -60,15 +61,14 @@ __device__ __forceinline__ void fwd_rows(const Prob &P, const ViewP &vp, float t
         const float rbig = __fmaf_rn(-hi_o, Oc, tau_hi);            // exact
         const float rsmall = __fmaf_rn(lo_o, Oc, P.uc_lo);
         Oc = __fadd_rn(Oc, dO);
-        const float I0 = CLASS_B ? __fsub_rn(c_in, __int2float_rn(q0)) : __fsub_rn(__int2float_rn(q0), c_in);
+        const float q0f = CHECKED ? __int2float_rn(q0) : magic_float(qc);   // the clamped index when checked
+        const float I0 = CLASS_B ? __fsub_rn(c_in, q0f) : __fsub_rn(q0f, c_in);
 #pragma unroll
         for (int k = 0; k < NC; ++k) {
             const float I = __fadd_rn(I0, k * dI);                    // exact half-integer
             const float big = __fmaf_rn(-hi_i, I, rbig);              // exact
             const float ad = fabsf(__fsub_rn(big, __fmaf_rn(lo_i, I, rsmall)));
-            const float w = AXIS ? (ad < E ? Pl : (ad == E ? 0.5f * Pl : 0.0f))
-                                 : fminf(Pl, fmaxf(0.0f, __fmaf_rn(-ad, S, ES)));
-            rs = __fmaf_rn(w, pv[k], rs);
+            rs = __fmaf_rn(weight_unit(ad, E, Sn, ESn, AXIS), pv[k], rs);
         }
         if ((r & 7) == 7 || r == rows - 1) {   // Kahan-compensated fold
             const float y = __fsub_rn(rs, comp);
@@ -140,7 +140,7 @@ __device__ __forceinline__ double fwd_ray(const Prob &P, const ViewP &vp, const 
                         &bars[buf]);
         }
     }
-    return (double)sum - (double)comp;
+    return ((double)sum - (double)comp) * (double)vp.P;   // weights were in units of P
 }
 
 __global__ void __launch_bounds__(128) k_forward(const Prob *__restrict__ probs, const int *__restrict__ prefix,
@@ -277,13 +277,14 @@ template <bool AXIS, int NC, bool CHECKED>
 __device__ __forceinline__ void bwd_view(const ViewP &vp, float pb0, const float *sm, const float *w_row, int lo,
                                          int bwin, float *t, int *bad)
 {
-    const float E = vp.E, S = vp.S, ES = vp.ES, Pl = vp.P;
+    const float E = vp.E, Sn = vp.Sn, ESn = vp.ESn;
 #pragma unroll
     for (int e = 0; e < kBwdPixPerThread; ++e) {
         // delta = (u + pb) - small; pb = -uc_hi - cu_hi X - su_hi Y is exact, and so is
         // stepping it by su_hi per pixel row
         const float pb = __fmaf_rn((float)(kBwdRowStep * e), vp.su_hi, pb0);
-        int u0 = __float2int_ru(__fsub_rn(__fsub_rn(sm[e], pb), vp.hwu));
+        const float uc = ceil_magic(__fsub_rn(__fsub_rn(sm[e], pb), vp.hwu));
+        int u0 = magic_int(uc);
         if (CHECKED) {
             const int idx = u0 - lo;
             if (idx < 0 || idx > bwin - NC) {   // outside the staged window: never for a valid window
@@ -291,14 +292,13 @@ __device__ __forceinline__ void bwd_view(const ViewP &vp, float pb0, const float
                 u0 = min(max(idx, 0), bwin - NC) + lo;
             }
         }
-        const float big0 = __fadd_rn(__int2float_rn(u0), pb);   // exact, as are big0 + 1 and big0 + 2
+        const float u0f = CHECKED ? __int2float_rn(u0) : magic_float(uc);
+        const float big0 = __fadd_rn(u0f, pb);   // exact, as are big0 + 1 and big0 + 2
         const float *wv = w_row + (u0 - lo);
 #pragma unroll
         for (int k = 0; k < NC; ++k) {
             const float ad = fabsf(__fsub_rn(__fadd_rn(big0, (float)k), sm[e]));
-            const float w = AXIS ? (ad < E ? Pl : (ad == E ? 0.5f * Pl : 0.0f))
-                                 : fminf(Pl, fmaxf(0.0f, __fmaf_rn(-ad, S, ES)));
-            t[e] = __fmaf_rn(w, wv[k], t[e]);
+            t[e] = __fmaf_rn(weight_unit(ad, E, Sn, ESn, AXIS), wv[k], t[e]);   // wv holds P * y
         }
     }
 }
@@ -365,8 +365,14 @@ __global__ void __launch_bounds__(kBwdThreads) k_backward(const Prob *__restrict
             const int v = v0 + vv;
             float4 val = make_float4(0.f, 0.f, 0.f, 0.f);
             const int ub = ulo_sh[buf][vv] + 4 * k4;
-            if (v < P.V && ub >= 0 && ub + 3 < Up)
+            if (v < P.V && ub >= 0 && ub + 3 < Up) {
                 val = __ldg(reinterpret_cast<const float4 *>(sino + (size_t)v * Up + ub));
+                const float pl = vsh[buf][vv].P;   // the weights are in units of the view's plateau length
+                val.x = __fmul_rn(val.x, pl);
+                val.y = __fmul_rn(val.y, pl);
+                val.z = __fmul_rn(val.z, pl);
+                val.w = __fmul_rn(val.w, pl);
+            }
             *reinterpret_cast<float4 *>(wb + vv * bwin + 4 * k4) = val;
         }
     };

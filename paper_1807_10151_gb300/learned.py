@@ -84,17 +84,18 @@ def train(net, X, T, D, epochs=3, batch=32, lr=1e-3, seed=0, log_every=0):
     return hist
 
 
-def time_to_equal(G, b, net, iters=100, params=TABLE1, device="cuda"):
+def time_to_equal(G, b, net, iters=100, params=TABLE1, device="cuda", warmup=3):
     """Plain SupPCG for `iters` iterations sets the target (f*, TV*); the learned
     variant's wall time to reach f <= f* and TV <= TV* is compared with the plain
-    run's.  Returns a dict of the measurements."""
+    run's (both after untimed `warmup`-iteration solves).  Returns a dict of the
+    measurements."""
     import torch
     import paper_1807_10151_gb300 as S
     kw = dict(params)
     st = torch.cuda.current_stream()
     # warm both graph paths
-    G.solve(b, max_iter=2, **kw)
-    G.solve_learned(net, b, max_iter=2, **kw)
+    G.solve(b, max_iter=warmup, **kw)
+    G.solve_learned(net, b, max_iter=warmup, **kw)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(st)
