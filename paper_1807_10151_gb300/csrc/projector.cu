@@ -28,12 +28,12 @@ namespace supcg {
 // sum with Kahan compensation (sum, comp), so that the ray sum is accurate
 // to a few units in the last place of FP32 however many rows it crosses.
 template <bool CLASS_B, bool AXIS, int NC, bool CHECKED>
-__device__ __forceinline__ void fwd_rows(const Prob &P, const ViewP &vp, float tau_hi, float qm, int o0, int rows,
-                                         int qs, const float *patch, int *bad, float &sum, float &comp)
+__device__ __forceinline__ void fwd_rows(const Prob &P, const ViewP &vp, float tau_hi, float qm, int o0, int rb,
+                                         int re, int qs, const float *patch, int *bad, float &sum, float &comp)
 {
     const int BW = P.BW;
-    // outer coordinate of row o0 (pixel units) and its change per row
-    float Oc = CLASS_B ? __fsub_rn(__int2float_rn(o0), P.cx) : __fsub_rn(P.cy, __int2float_rn(o0));
+    // outer coordinate of row o0 + rb (pixel units) and its change per row
+    float Oc = CLASS_B ? __fsub_rn(__int2float_rn(o0 + rb), P.cx) : __fsub_rn(P.cy, __int2float_rn(o0 + rb));
     const float dO = CLASS_B ? 1.0f : -1.0f;
     const float hi_o = CLASS_B ? vp.cu_hi : vp.su_hi;   // coefficient of the outer coordinate
     const float lo_o = CLASS_B ? vp.cu_lo : vp.su_lo;
@@ -46,9 +46,10 @@ __device__ __forceinline__ void fwd_rows(const Prob &P, const ViewP &vp, float t
     const float qh = __fsub_rn(qm, vp.hwq);
     const float *prow = patch - qs;
     float rs = 0.0f;   // FP32 sum of up to 8 rows, then folded into (sum, comp)
+    float rf = __int2float_rn(rb);
 #pragma unroll 4
-    for (int r = 0; r < rows; ++r) {
-        const float qc = ceil_magic(__fmaf_rn((float)r, vp.b_o, qh));
+    for (int r = rb; r < re; ++r, rf = __fadd_rn(rf, 1.0f)) {
+        const float qc = ceil_magic(__fmaf_rn(rf, vp.b_o, qh));
         int q0 = magic_int(qc);
         if (CHECKED) {
             const int idx = q0 - qs;
@@ -70,7 +71,7 @@ __device__ __forceinline__ void fwd_rows(const Prob &P, const ViewP &vp, float t
             const float ad = fabsf(__fsub_rn(big, __fmaf_rn(lo_i, I, rsmall)));
             rs = __fmaf_rn(weight_unit(ad, E, Sn, ESn, AXIS), pv[k], rs);
         }
-        if ((r & 7) == 7 || r == rows - 1) {   // Kahan-compensated fold
+        if (((r - rb) & 7) == 7 || r == re - 1) {   // Kahan-compensated fold
             const float y = __fsub_rn(rs, comp);
             const float tt = __fadd_rn(sum, y);
             comp = __fsub_rn(__fsub_rn(tt, sum), y);
@@ -93,31 +94,64 @@ __device__ __forceinline__ int fwd_box_start(const ViewP &vp, float tf, float tl
     return lo & ~3;   // round down to a multiple of 4 floats (16-byte TMA rule)
 }
 
+// Outer indices [*lo, *hi] at which a ray whose centre sits at inner index
+// base + b_o * o can meet the inner range [0, n_inner): the centre within the
+// footprint half-width hwq plus one index of slack of either end.  Rows outside
+// it contribute nothing (their candidates fall on the zero fill).
+__device__ __forceinline__ void fwd_row_range(const ViewP &vp, float base, int n_inner, int n_outer, int *lo, int *hi)
+{
+    const float L = -vp.hwq - 1.0f, H = __int2float_rn(n_inner) + vp.hwq;
+    if (fabsf(vp.b_o) < 1e-20f) {
+        const bool in = base >= L && base <= H;
+        *lo = in ? 0 : n_outer;
+        *hi = in ? n_outer - 1 : -1;
+        return;
+    }
+    const float ra = __fdiv_rn(__fsub_rn(L, base), vp.b_o), rb = __fdiv_rn(__fsub_rn(H, base), vp.b_o);
+    const float fo = __int2float_rn(n_outer);
+    const float a = fminf(fmaxf(fminf(ra, rb) - 1.0f, -1.0f), fo), b = fminf(fmaxf(fmaxf(ra, rb) + 1.0f, -1.0f), fo);
+    *lo = max(0, __float2int_rd(a));
+    *hi = min(n_outer - 1, __float2int_ru(b));
+}
+
 template <bool CLASS_B, bool AXIS, int NC>
 __device__ __forceinline__ double fwd_ray(const Prob &P, const ViewP &vp, const CUtensorMap *tm, float *patch0,
-                                          uint64_t *bars, int n_outer, int u, int u_last, float tf, float tl,
-                                          int *bad, bool *timed_out)
+                                          uint64_t *bars, int *range_sh, int n_outer, int n_inner, int u, int u_last,
+                                          float tf, float tl, int *bad, int *timed_out)
 {
     const int RC = kRowsPerChunk, BW = P.BW;
     const int box_elems = RC * BW;
-    const int nchunks = (n_outer + RC - 1) / RC;
     const int t = threadIdx.x;
     const float tau = bin_pos(u, P.uc);
     const float tau_hi = bin_pos(u, P.uc_hi);   // exact
     const float base_u = __fmaf_rn(vp.a_tau, tau, vp.g0);   // inner index of the ray centre at outer index 0
     float sum = 0.0f, comp = 0.0f;   // compensated running sum of the ray
+    // rows this ray can meet; their union over the warp (uniform loop bounds) and over the block (chunks)
+    int r_lo = n_outer, r_hi = -1;
+    if (u <= u_last) fwd_row_range(vp, base_u, n_inner, n_outer, &r_lo, &r_hi);
+    const int w_lo = __reduce_min_sync(0xffffffffu, r_lo), w_hi = __reduce_max_sync(0xffffffffu, r_hi);
+    if ((t & 31) == 0) {
+        atomicMin(&range_sh[0], w_lo);
+        atomicMax(&range_sh[1], w_hi);
+    }
+    __syncthreads();
+    const int b_lo = range_sh[0], b_hi = range_sh[1];
+    const int c_first = b_hi >= b_lo ? b_lo / RC : 0;
+    const int nch = b_hi >= b_lo ? b_hi / RC - c_first + 1 : 0;   // chunks with at least one of the block's rows
     if (t == 0) {
-        for (int c = 0; c < 2 && c < nchunks; ++c) {
-            mbar_expect_tx(&bars[c], box_elems * 4);
-            tma_load_2d(patch0 + c * box_elems, tm, fwd_box_start(vp, tf, tl, c * RC), c * RC, &bars[c]);
+        for (int ci = 0; ci < 2 && ci < nch; ++ci) {
+            const int c = c_first + ci;
+            mbar_expect_tx(&bars[ci], box_elems * 4);
+            tma_load_2d(patch0 + ci * box_elems, tm, fwd_box_start(vp, tf, tl, c * RC), c * RC, &bars[ci]);
         }
     }
-    for (int c = 0; c < nchunks; ++c) {
-        const int buf = c & 1;
-        if (!mbar_wait(&bars[buf], (c >> 1) & 1)) { *timed_out = true; break; }
+    for (int ci = 0; ci < nch; ++ci) {
+        const int buf = ci & 1, c = c_first + ci;
+        const bool ok = mbar_wait(&bars[buf], (ci >> 1) & 1);
         const int o0 = c * RC;
         const int rows = min(RC, n_outer - o0);
-        if (u <= u_last) {
+        const int rb = max(0, w_lo - o0), re = min(rows, w_hi - o0 + 1);
+        if (ok && u <= u_last && rb < re) {
             const float qm = __fmaf_rn(vp.b_o, __int2float_rn(o0), base_u);   // ray centre at row o0
             const int qs = fwd_box_start(vp, tf, tl, o0);
             // the first candidate is monotone in the row: its end values (with one index
@@ -127,14 +161,22 @@ __device__ __forceinline__ double fwd_ray(const Prob &P, const ViewP &vp, const 
             const int qb = __float2int_ru(__fmaf_rn((float)(rows - 1), vp.b_o, qh)) - qs;
             const bool inside = min(qa, qb) >= 1 && max(qa, qb) <= P.BW - NC - 1;
             if (inside)
-                fwd_rows<CLASS_B, AXIS, NC, false>(P, vp, tau_hi, qm, o0, rows, qs, patch0 + buf * box_elems, bad,
+                fwd_rows<CLASS_B, AXIS, NC, false>(P, vp, tau_hi, qm, o0, rb, re, qs, patch0 + buf * box_elems, bad,
                                                    sum, comp);
             else
-                fwd_rows<CLASS_B, AXIS, NC, true>(P, vp, tau_hi, qm, o0, rows, qs, patch0 + buf * box_elems, bad,
+                fwd_rows<CLASS_B, AXIS, NC, true>(P, vp, tau_hi, qm, o0, rb, re, qs, patch0 + buf * box_elems, bad,
                                                   sum, comp);
         }
-        __syncthreads();   // every thread is done with this buffer
-        if (t == 0 && c + 2 < nchunks) {
+        // every thread is done with this buffer; a timeout anywhere ends the loop in every thread
+        if (__syncthreads_or(!ok)) {
+            *timed_out = 1;
+            if (t == 0) {   // bounded waits for the copies still in flight: chunk ci's and, if issued, ci + 1's
+                (void)mbar_wait(&bars[buf], (ci >> 1) & 1);
+                if (ci + 1 < nch) (void)mbar_wait(&bars[buf ^ 1], ((ci + 1) >> 1) & 1);
+            }
+            break;
+        }
+        if (t == 0 && ci + 2 < nch) {
             mbar_expect_tx(&bars[buf], box_elems * 4);
             tma_load_2d(patch0 + buf * box_elems, tm, fwd_box_start(vp, tf, tl, (c + 2) * RC), (c + 2) * RC,
                         &bars[buf]);
@@ -151,6 +193,7 @@ __global__ void __launch_bounds__(128) k_forward(const Prob *__restrict__ probs,
     __shared__ double red[40];
     __shared__ int flag;
     __shared__ int bad_sh;
+    __shared__ int range_sh[2];
 
     int local;
     const int pi = find_problem(prefix, count, blockIdx.x, &local);
@@ -162,7 +205,7 @@ __global__ void __launch_bounds__(128) k_forward(const Prob *__restrict__ probs,
     const int v = P.vlist[vidx];
     const ViewP vp = P.views[v];
     const bool axis = (vp.flags & kViewAxis) != 0;
-    const int n_outer = classB ? P.nx : P.ny;
+    const int n_outer = classB ? P.nx : P.ny, n_inner = classB ? P.ny : P.nx;
     const CUtensorMap *tm = &P.tm[which * 2 + (classB ? 1 : 0)];
     float *patch0 = reinterpret_cast<float *>(smem_raw);
 
@@ -174,6 +217,8 @@ __global__ void __launch_bounds__(128) k_forward(const Prob *__restrict__ probs,
 
     if (t == 0) {
         bad_sh = 0;
+        range_sh[0] = n_outer;
+        range_sh[1] = -1;
         mbar_init(&bars[0], 1);
         mbar_init(&bars[1], 1);
         fence_mbar_init();
@@ -181,22 +226,19 @@ __global__ void __launch_bounds__(128) k_forward(const Prob *__restrict__ probs,
     __syncthreads();
 
     int bad = 0;
-    bool timed_out = false;
+    int timed_out = 0;   // a copy did not arrive (every thread sees it)
     double acc;
     // axis-aligned views meet at most two pixels per row; near-diagonal ones up to three
     const bool three = (vp.flags & kViewFwd3) != 0;
-#define SUPCG_FWD(CB, AX, NC) fwd_ray<CB, AX, NC>(P, vp, tm, patch0, bars, n_outer, u, u_last, tf, tl, &bad, &timed_out)
+#define SUPCG_FWD(CB, AX, NC) \
+    fwd_ray<CB, AX, NC>(P, vp, tm, patch0, bars, range_sh, n_outer, n_inner, u, u_last, tf, tl, &bad, &timed_out)
     if (classB)
         acc = axis ? SUPCG_FWD(true, true, 2) : (three ? SUPCG_FWD(true, false, 3) : SUPCG_FWD(true, false, 2));
     else
         acc = axis ? SUPCG_FWD(false, true, 2) : (three ? SUPCG_FWD(false, false, 3) : SUPCG_FWD(false, false, 2));
 #undef SUPCG_FWD
     if (timed_out) {
-        // wait (bounded) for any copy still in flight before leaving
-        if (t == 0) {
-            if (P.sc) atomicExch(&P.sc->status, (int)SUPCG_ERR_TIMEOUT);
-            for (int b = 0; b < 2; ++b) (void)mbar_wait(&bars[b], 0);
-        }
+        if (t == 0 && P.sc) atomicExch(&P.sc->status, (int)SUPCG_ERR_TIMEOUT);
         return;
     }
     if (bad) atomicExch(&bad_sh, 1);
