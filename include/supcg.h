@@ -53,10 +53,11 @@ typedef enum { SUPCG_F32 = 0, SUPCG_BF16 = 1 } supcg_storage;
 /* Create a 2-D parallel-beam geometry (Sec. 2, Sec. 4.1).
  *   nx, ny          image size in pixels (1 .. 16384 each)
  *   pixel_size      d > 0 (the unit-square convention is d = 1/max(nx, ny))
- *   n_views         V >= 1
+ *   n_views         1 <= V <= 2^20
  *   angles          host array of V angles in radians, or NULL for v*pi/V
  *                   (V equally spaced angles in [0, pi), as in Sec. 4.1)
- *   n_bins          U >= 1
+ *   n_bins          1 <= U <= 2^21 (bin indices stay below 2^22, where one FP32
+ *                   addition rounded upward gives their ceiling exactly)
  *   bin_spacing     ds; <= 0 selects ds = d (ray spacing = pixel size, Sec. 4.1)
  *   det_center_offset  off, added to every s_u
  *   storage         SUPCG_F32 or SUPCG_BF16: element type of the images and

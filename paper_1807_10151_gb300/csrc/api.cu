@@ -184,7 +184,7 @@ extern "C" int supcg_create_geometry(int nx, int ny, double pixel_size, int n_vi
 {
     if (!out) return SUPCG_ERR_ARG;
     *out = nullptr;
-    if (nx < 1 || ny < 1 || nx > 16384 || ny > 16384 || n_views < 1 || n_bins < 1 || n_bins > (1 << 24) ||
+    if (nx < 1 || ny < 1 || nx > 16384 || ny > 16384 || n_views < 1 || n_bins < 1 || n_bins > (1 << 21) ||
         n_views > (1 << 20) || !(pixel_size > 0.0) || !isfinite(pixel_size) || !isfinite(det_center_offset) ||
         (storage != SUPCG_F32 && storage != SUPCG_BF16))
         return SUPCG_ERR_ARG;

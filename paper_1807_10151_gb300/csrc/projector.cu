@@ -345,7 +345,7 @@ __device__ __forceinline__ void bwd_view(const ViewP &vp, float pb0, const float
     }
 }
 
-__global__ void __launch_bounds__(kBwdThreads) k_backward(const Prob *__restrict__ probs,
+__global__ void __launch_bounds__(kBwdThreads, 4) k_backward(const Prob *__restrict__ probs,
                                                           const int *__restrict__ prefix, int count, int mode)
 {
     extern __shared__ __align__(16) float win_raw[];   // [2][kBwdViewChunk][bwin]
@@ -442,8 +442,8 @@ __global__ void __launch_bounds__(kBwdThreads) k_backward(const Prob *__restrict
             // (with one bin of slack) bound all four pixels
             const int NCv = (vp.flags & kViewBwd3) ? 3 : 2;
             const float pbl = __fmaf_rn((float)(kBwdRowStep * (kBwdPixPerThread - 1)), vp.su_hi, pb0);
-            const int ia = __float2int_ru(__fsub_rn(__fsub_rn(sm[0], pb0), vp.hwu)) - lo;
-            const int ib = __float2int_ru(__fsub_rn(__fsub_rn(sm[kBwdPixPerThread - 1], pbl), vp.hwu)) - lo;
+            const int ia = magic_int(ceil_magic(__fsub_rn(__fsub_rn(sm[0], pb0), vp.hwu))) - lo;
+            const int ib = magic_int(ceil_magic(__fsub_rn(__fsub_rn(sm[kBwdPixPerThread - 1], pbl), vp.hwu))) - lo;
             const bool inside = min(ia, ib) >= 1 && max(ia, ib) <= bwin - NCv - 1;
 #define SUPCG_BWD(AX, NC, CK) bwd_view<AX, NC, CK>(vp, pb0, sm, wr, lo, bwin, t, &bad)
             if (vp.flags & kViewAxis) {
