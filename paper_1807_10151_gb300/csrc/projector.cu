@@ -46,9 +46,7 @@ __device__ __forceinline__ void fwd_rows(const Prob &P, const ViewP &vp, float t
     const float qh = __fsub_rn(qm, vp.hwq);
     const float *prow = patch - qs;
     float rs = 0.0f;   // FP32 sum of up to 8 rows, then folded into (sum, comp)
-    float rf = __int2float_rn(rb);
-#pragma unroll 4
-    for (int r = rb; r < re; ++r, rf = __fadd_rn(rf, 1.0f)) {
+    auto row = [&](int r, float rf) {
         const float qc = ceil_magic(__fmaf_rn(rf, vp.b_o, qh));
         int q0 = magic_int(qc);
         if (CHECKED) {
@@ -71,13 +69,25 @@ __device__ __forceinline__ void fwd_rows(const Prob &P, const ViewP &vp, float t
             const float ad = fabsf(__fsub_rn(big, __fmaf_rn(lo_i, I, rsmall)));
             rs = __fmaf_rn(weight_unit(ad, E, Sn, ESn, AXIS), pv[k], rs);
         }
-        if (((r - rb) & 7) == 7 || r == re - 1) {   // Kahan-compensated fold
-            const float y = __fsub_rn(rs, comp);
-            const float tt = __fadd_rn(sum, y);
-            comp = __fsub_rn(__fsub_rn(tt, sum), y);
-            sum = tt;
-            rs = 0.0f;
-        }
+    };
+    auto fold = [&]() {   // Kahan-compensated fold of the group's sum
+        const float y = __fsub_rn(rs, comp);
+        const float tt = __fadd_rn(sum, y);
+        comp = __fsub_rn(__fsub_rn(tt, sum), y);
+        sum = tt;
+        rs = 0.0f;
+    };
+    // groups of eight rows from rb, the last one possibly shorter
+    int r = rb;
+    float rf = __int2float_rn(rb);
+    for (; r + 8 <= re; r += 8) {
+#pragma unroll
+        for (int k = 0; k < 8; ++k, rf = __fadd_rn(rf, 1.0f)) row(r + k, rf);
+        fold();
+    }
+    if (r < re) {
+        for (; r < re; ++r, rf = __fadd_rn(rf, 1.0f)) row(r, rf);
+        fold();
     }
 }
 
@@ -371,9 +381,11 @@ __global__ void __launch_bounds__(kBwdThreads, 4) k_backward(const Prob *__restr
     float Y[kBwdPixPerThread];
 #pragma unroll
     for (int e = 0; e < kBwdPixPerThread; ++e) Y[e] = __fsub_rn(P.cy, __int2float_rn(i0 + ly + kBwdRowStep * e));
-    double acc[kBwdPixPerThread];   // FP64 sum of the FP32 partial sums of each 32-view chunk
+    // per pixel: FP32 sum of up to four views (t4), folded into a Kahan-compensated pair (part, comp)
+    // that runs over all views; FP64 only for the final value (the FP64 pipe is narrow)
+    float part[kBwdPixPerThread], comp[kBwdPixPerThread], t4[kBwdPixPerThread];
 #pragma unroll
-    for (int e = 0; e < kBwdPixPerThread; ++e) acc[e] = 0.0;
+    for (int e = 0; e < kBwdPixPerThread; ++e) part[e] = comp[e] = t4[e] = 0.0f;
 
     const float *sino = (mode == BWD_G) ? P.r : (mode == BWD_H ? P.q : P.r);
     const int Up = P.Up;
@@ -427,9 +439,6 @@ __global__ void __launch_bounds__(kBwdThreads, 4) k_backward(const Prob *__restr
         if (c + 1 < nchunks) stage(c + 1);   // other buffer; its previous readers finished at the last barrier
         const int nv = min(kBwdViewChunk, P.V - c * kBwdViewChunk);
         const float *wb = win_raw + (size_t)buf * kBwdViewChunk * bwin;
-        float part[kBwdPixPerThread], comp[kBwdPixPerThread], t[kBwdPixPerThread];
-#pragma unroll
-        for (int e = 0; e < kBwdPixPerThread; ++e) part[e] = comp[e] = t[e] = 0.0f;
         for (int vv = grp; vv < nv; vv += kBwdSplit) {
             const ViewP vp = vsh[buf][vv];
             const float *wr = wb + vv * bwin;
@@ -445,7 +454,7 @@ __global__ void __launch_bounds__(kBwdThreads, 4) k_backward(const Prob *__restr
             const int ia = magic_int(ceil_magic(__fsub_rn(__fsub_rn(sm[0], pb0), vp.hwu))) - lo;
             const int ib = magic_int(ceil_magic(__fsub_rn(__fsub_rn(sm[kBwdPixPerThread - 1], pbl), vp.hwu))) - lo;
             const bool inside = min(ia, ib) >= 1 && max(ia, ib) <= bwin - NCv - 1;
-#define SUPCG_BWD(AX, NC, CK) bwd_view<AX, NC, CK>(vp, pb0, sm, wr, lo, bwin, t, &bad)
+#define SUPCG_BWD(AX, NC, CK) bwd_view<AX, NC, CK>(vp, pb0, sm, wr, lo, bwin, t4, &bad)
             if (vp.flags & kViewAxis) {
                 if (inside) SUPCG_BWD(true, 2, false); else SUPCG_BWD(true, 2, true);
             } else if (NCv == 3) {
@@ -457,18 +466,19 @@ __global__ void __launch_bounds__(kBwdThreads, 4) k_backward(const Prob *__restr
             if (((vv / kBwdSplit) & 3) == 3 || vv + kBwdSplit >= nv) {   // Kahan-compensated fold every four views
 #pragma unroll
                 for (int e = 0; e < kBwdPixPerThread; ++e) {
-                    const float y = __fsub_rn(t[e], comp[e]);
+                    const float y = __fsub_rn(t4[e], comp[e]);
                     const float tt = __fadd_rn(part[e], y);
                     comp[e] = __fsub_rn(__fsub_rn(tt, part[e]), y);
                     part[e] = tt;
-                    t[e] = 0.0f;
+                    t4[e] = 0.0f;
                 }
             }
         }
-#pragma unroll
-        for (int e = 0; e < kBwdPixPerThread; ++e) acc[e] += (double)part[e] - (double)comp[e];
         __syncthreads();
     }
+    double acc[kBwdPixPerThread];
+#pragma unroll
+    for (int e = 0; e < kBwdPixPerThread; ++e) acc[e] = (double)part[e] - (double)comp[e];
     if (bad) atomicExch(&bad_sh, 1);
     __syncthreads();
 
