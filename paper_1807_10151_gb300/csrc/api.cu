@@ -145,6 +145,16 @@ struct supcg_geometry_s {
     std::vector<supcg_geometry> batch_key;
 };
 
+// Forward projector box width: the inner indices that one warp's 32 rays can
+// touch over one chunk of rows, plus slack, rounded up to a multiple of 4 floats.
+static int fwd_box_width(const supcg_geometry_s *g)
+{
+    double span = 0.0;
+    for (const ViewP &vp : g->views)
+        span = std::max(span, fabs((double)vp.a_tau) * 31.0 + fabs((double)vp.b_o) * (kRowsPerChunk - 1));
+    return round_up((int)ceil(span + 11.0), 4);
+}
+
 static void free_ws(Workspace *&w)
 {
     delete w;
@@ -275,10 +285,7 @@ extern "C" int supcg_create_geometry(int nx, int ny, double pixel_size, int n_vi
     // forward tiling: the widest box any view needs must fit 256 columns
     g->BU = 0;
     for (int bu : {128, 96, 64, 32}) {
-        double span = 0.0;
-        for (const ViewP &vp : g->views)
-            span = std::max(span, fabs((double)vp.a_tau) * (bu - 1) + fabs((double)vp.b_o) * (kRowsPerChunk - 1));
-        const int bw = round_up((int)ceil(span + 11.0), 4);
+        const int bw = fwd_box_width(g);
         if (bw <= 256) { g->BU = bu; g->BW = bw; break; }
     }
     if (!g->BU) { delete g; return SUPCG_ERR_UNSUPPORTED; }
@@ -316,11 +323,7 @@ extern "C" int supcg_create_geometry(int nx, int ny, double pixel_size, int n_vi
 extern "C" int supcg_set_tiling(supcg_geometry g, int fwd_bins_per_block)
 {
     if (!g || fwd_bins_per_block < 32 || fwd_bins_per_block > 128 || fwd_bins_per_block % 32) return SUPCG_ERR_ARG;
-    double span = 0.0;
-    for (const ViewP &vp : g->views)
-        span = std::max(span, fabs((double)vp.a_tau) * (fwd_bins_per_block - 1) +
-                                  fabs((double)vp.b_o) * (kRowsPerChunk - 1));
-    const int bw = round_up((int)ceil(span + 11.0), 4);
+    const int bw = fwd_box_width(g);
     if (bw > 256) return SUPCG_ERR_UNSUPPORTED;
     cudaDeviceSynchronize();
     g->BU = fwd_bins_per_block;

@@ -124,31 +124,29 @@ __device__ __forceinline__ void fwd_row_range(const ViewP &vp, float base, int n
     *hi = min(n_outer - 1, __float2int_ru(b));
 }
 
+// One ray per lane; each warp runs its own double-buffered pipeline of
+// kRowsPerChunk-row boxes (BW columns covering its 32 rays), so warps never
+// wait for one another.  The warp walks only the chunks holding rows that one
+// of its rays can meet, and within them only those rows.
 template <bool CLASS_B, bool AXIS, int NC>
 __device__ __forceinline__ double fwd_ray(const Prob &P, const ViewP &vp, const CUtensorMap *tm, float *patch0,
-                                          uint64_t *bars, int *range_sh, int n_outer, int n_inner, int u, int u_last,
-                                          float tf, float tl, int *bad, int *timed_out)
+                                          uint64_t *bars, int n_outer, int n_inner, int u, int u_last, float tf,
+                                          float tl, int *bad, int *timed_out)
 {
     const int RC = kRowsPerChunk, BW = P.BW;
     const int box_elems = RC * BW;
-    const int t = threadIdx.x;
+    const int lane = threadIdx.x & 31;
     const float tau = bin_pos(u, P.uc);
     const float tau_hi = bin_pos(u, P.uc_hi);   // exact
     const float base_u = __fmaf_rn(vp.a_tau, tau, vp.g0);   // inner index of the ray centre at outer index 0
     float sum = 0.0f, comp = 0.0f;   // compensated running sum of the ray
-    // rows this ray can meet; their union over the warp (uniform loop bounds) and over the block (chunks)
+    // rows this ray can meet, and their union over the warp (uniform loop bounds)
     int r_lo = n_outer, r_hi = -1;
     if (u <= u_last) fwd_row_range(vp, base_u, n_inner, n_outer, &r_lo, &r_hi);
     const int w_lo = __reduce_min_sync(0xffffffffu, r_lo), w_hi = __reduce_max_sync(0xffffffffu, r_hi);
-    if ((t & 31) == 0) {
-        atomicMin(&range_sh[0], w_lo);
-        atomicMax(&range_sh[1], w_hi);
-    }
-    __syncthreads();
-    const int b_lo = range_sh[0], b_hi = range_sh[1];
-    const int c_first = b_hi >= b_lo ? b_lo / RC : 0;
-    const int nch = b_hi >= b_lo ? b_hi / RC - c_first + 1 : 0;   // chunks with at least one of the block's rows
-    if (t == 0) {
+    const int c_first = w_hi >= w_lo ? w_lo / RC : 0;
+    const int nch = w_hi >= w_lo ? w_hi / RC - c_first + 1 : 0;   // chunks with at least one of the warp's rows
+    if (lane == 0) {
         for (int ci = 0; ci < 2 && ci < nch; ++ci) {
             const int c = c_first + ci;
             mbar_expect_tx(&bars[ci], box_elems * 4);
@@ -177,16 +175,17 @@ __device__ __forceinline__ double fwd_ray(const Prob &P, const ViewP &vp, const 
                 fwd_rows<CLASS_B, AXIS, NC, true>(P, vp, tau_hi, qm, o0, rb, re, qs, patch0 + buf * box_elems, bad,
                                                   sum, comp);
         }
-        // every thread is done with this buffer; a timeout anywhere ends the loop in every thread
-        if (__syncthreads_or(!ok)) {
+        // every lane is done with this buffer; a timeout in any lane ends the warp's loop
+        if (__any_sync(0xffffffffu, !ok)) {
             *timed_out = 1;
-            if (t == 0) {   // bounded waits for the copies still in flight: chunk ci's and, if issued, ci + 1's
+            if (lane == 0) {   // bounded waits for the copies still in flight: chunk ci's and, if issued, ci + 1's
                 (void)mbar_wait(&bars[buf], (ci >> 1) & 1);
                 if (ci + 1 < nch) (void)mbar_wait(&bars[buf ^ 1], ((ci + 1) >> 1) & 1);
             }
             break;
         }
-        if (t == 0 && ci + 2 < nch) {
+        __syncwarp();
+        if (lane == 0 && ci + 2 < nch) {
             mbar_expect_tx(&bars[buf], box_elems * 4);
             tma_load_2d(patch0 + buf * box_elems, tm, fwd_box_start(vp, tf, tl, (c + 2) * RC), (c + 2) * RC,
                         &bars[buf]);
@@ -195,15 +194,14 @@ __device__ __forceinline__ double fwd_ray(const Prob &P, const ViewP &vp, const 
     return ((double)sum - (double)comp) * (double)vp.P;   // weights were in units of P
 }
 
-__global__ void __launch_bounds__(128) k_forward(const Prob *__restrict__ probs, const int *__restrict__ prefix,
+__global__ void __launch_bounds__(128, 6) k_forward(const Prob *__restrict__ probs, const int *__restrict__ prefix,
                                                  int count, int which, int mode)
 {
-    extern __shared__ __align__(128) unsigned char smem_raw[];
-    __shared__ __align__(8) uint64_t bars[2];
+    extern __shared__ __align__(128) unsigned char smem_raw[];   // [warp][2][kRowsPerChunk][BW]
+    __shared__ __align__(8) uint64_t bars[2 * 4];                 // two per warp
     __shared__ double red[40];
     __shared__ int flag;
     __shared__ int bad_sh;
-    __shared__ int range_sh[2];
 
     int local;
     const int pi = find_problem(prefix, count, blockIdx.x, &local);
@@ -217,37 +215,37 @@ __global__ void __launch_bounds__(128) k_forward(const Prob *__restrict__ probs,
     const bool axis = (vp.flags & kViewAxis) != 0;
     const int n_outer = classB ? P.nx : P.ny, n_inner = classB ? P.ny : P.nx;
     const CUtensorMap *tm = &P.tm[which * 2 + (classB ? 1 : 0)];
-    float *patch0 = reinterpret_cast<float *>(smem_raw);
+    const int t = threadIdx.x, warp = t >> 5;
+    float *patch0 = reinterpret_cast<float *>(smem_raw) + warp * 2 * kRowsPerChunk * P.BW;
+    uint64_t *wbars = bars + 2 * warp;
 
-    const int t = threadIdx.x;
     const int u_first = tile * P.BU;
     const int u_last = min(P.U, u_first + P.BU) - 1;
     const int u = u_first + t;
-    const float tf = bin_pos(u_first, P.uc), tl = bin_pos(u_last, P.uc);
+    // the warp's rays: u_first + 32 warp .. (its box spans their bin positions)
+    const int uw0 = u_first + 32 * warp, uw1 = min(u_last, uw0 + 31);
+    const float tf = bin_pos(min(uw0, u_last), P.uc), tl = bin_pos(uw1, P.uc);
 
-    if (t == 0) {
-        bad_sh = 0;
-        range_sh[0] = n_outer;
-        range_sh[1] = -1;
-        mbar_init(&bars[0], 1);
-        mbar_init(&bars[1], 1);
-        fence_mbar_init();
-    }
+    if (t == 0) bad_sh = 0;
+    if (t < 8) mbar_init(&bars[t], 1);
+    if (t == 0) fence_mbar_init();
     __syncthreads();
 
     int bad = 0;
-    int timed_out = 0;   // a copy did not arrive (every thread sees it)
+    int timed_out = 0;   // a copy did not arrive (every lane of the warp sees it)
     double acc;
     // axis-aligned views meet at most two pixels per row; near-diagonal ones up to three
     const bool three = (vp.flags & kViewFwd3) != 0;
 #define SUPCG_FWD(CB, AX, NC) \
-    fwd_ray<CB, AX, NC>(P, vp, tm, patch0, bars, range_sh, n_outer, n_inner, u, u_last, tf, tl, &bad, &timed_out)
-    if (classB)
+    fwd_ray<CB, AX, NC>(P, vp, tm, patch0, wbars, n_outer, n_inner, u, u_last, tf, tl, &bad, &timed_out)
+    if (uw0 > u_last)
+        acc = 0.0;   // a warp past the block's last bin
+    else if (classB)
         acc = axis ? SUPCG_FWD(true, true, 2) : (three ? SUPCG_FWD(true, false, 3) : SUPCG_FWD(true, false, 2));
     else
         acc = axis ? SUPCG_FWD(false, true, 2) : (three ? SUPCG_FWD(false, false, 3) : SUPCG_FWD(false, false, 2));
 #undef SUPCG_FWD
-    if (timed_out) {
+    if (__syncthreads_or(timed_out)) {   // a warp's copy did not arrive: the whole block leaves
         if (t == 0 && P.sc) atomicExch(&P.sc->status, (int)SUPCG_ERR_TIMEOUT);
         return;
     }
@@ -304,11 +302,11 @@ __global__ void __launch_bounds__(128) k_forward(const Prob *__restrict__ probs,
 int launch_forward(const Launch &L, int which, int mode)
 {
     static int max_smem_set = 0;
-    // every problem's BW <= 256, so the box buffers never exceed this size
-    const int smem = 2 * kRowsPerChunk * L.bw_max * 4;
+    // every problem's BW <= 256, so the four warps' box buffers never exceed this size
+    const int smem = 4 * 2 * kRowsPerChunk * L.bw_max * 4;
     if (!max_smem_set) {
         SUPCG_CUDA_TRY(cudaFuncSetAttribute(k_forward, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            2 * kRowsPerChunk * 256 * 4));
+                                            4 * 2 * kRowsPerChunk * 256 * 4));
         max_smem_set = 1;
     }
     k_forward<<<L.blocks, 128, smem, L.st>>>(L.probs, L.prefix, L.count, which, mode);
@@ -361,6 +359,7 @@ __global__ void __launch_bounds__(kBwdThreads, 4) k_backward(const Prob *__restr
     extern __shared__ __align__(16) float win_raw[];   // [2][kBwdViewChunk][bwin]
     __shared__ ViewP vsh[2][kBwdViewChunk];
     __shared__ int ulo_sh[2][kBwdViewChunk];
+    __shared__ int kind_sh[2][kBwdViewChunk];   // variant: axis / three bins / two bins, + 3 if a window check is needed
     __shared__ double comb[kBwdGroup * kBwdPixPerThread];   // second group's sums, combined by the first
     __shared__ int bad_sh;
 
@@ -402,14 +401,30 @@ __global__ void __launch_bounds__(kBwdThreads, 4) k_backward(const Prob *__restr
         if (t < kBwdViewChunk) {
             const int v = v0 + t;
             int lo = 0;
+            int kind = 0;
             if (v < P.V) {
                 const ViewP vp = P.views[v];
                 vsh[buf][t] = vp;
                 float m = fminf(fminf(det_coord(vp, Xa, Ya), det_coord(vp, Xa, Yb)),
                                 fminf(det_coord(vp, Xb, Ya), det_coord(vp, Xb, Yb)));
                 lo = (__float2int_rd(__fadd_rn(m, P.uc)) - 3) & ~3;
+                // a pixel's first candidate is (up to rounding) linear in X and Y, so its values at
+                // the tile's corners, with one bin of slack, bound it for every pixel of the tile;
+                // they are computed exactly as each pixel's own
+                const int nc = (vp.flags & kViewBwd3) ? 3 : 2;
+                bool inside = true;
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const float Xc = (k & 1) ? Xb : Xa, Yc = (k & 2) ? Yb : Ya;
+                    const float pbc = __fmaf_rn(-vp.cu_hi, Xc, __fmaf_rn(-vp.su_hi, Yc, -P.uc_hi));
+                    const float smc = delta_small(vp, Xc, Yc, P.uc_lo);
+                    const int q = magic_int(ceil_magic(__fsub_rn(__fsub_rn(smc, pbc), vp.hwu))) - lo;
+                    inside = inside && q >= 1 && q <= bwin - nc - 1;
+                }
+                kind = ((vp.flags & kViewAxis) ? 0 : (nc == 3 ? 1 : 2)) + (inside ? 0 : 3);
             }
             ulo_sh[buf][t] = lo;
+            kind_sh[buf][t] = kind;
         }
         __syncthreads();
         const int V4 = bwin >> 2;
@@ -439,39 +454,38 @@ __global__ void __launch_bounds__(kBwdThreads, 4) k_backward(const Prob *__restr
         if (c + 1 < nchunks) stage(c + 1);   // other buffer; its previous readers finished at the last barrier
         const int nv = min(kBwdViewChunk, P.V - c * kBwdViewChunk);
         const float *wb = win_raw + (size_t)buf * kBwdViewChunk * bwin;
-        for (int vv = grp; vv < nv; vv += kBwdSplit) {
-            const ViewP vp = vsh[buf][vv];
-            const float *wr = wb + vv * bwin;
-            const int lo = ulo_sh[buf][vv];
-            const float pb0 = __fmaf_rn(-vp.cu_hi, X, __fmaf_rn(-vp.su_hi, Y[0], -P.uc_hi));
-            float sm[kBwdPixPerThread];
+        // groups of four of this thread group's views, then one Kahan-compensated fold
+        for (int g0 = grp; g0 < nv; g0 += 4 * kBwdSplit) {
 #pragma unroll
-            for (int e = 0; e < kBwdPixPerThread; ++e) sm[e] = delta_small(vp, X, Y[e], P.uc_lo);
-            // the first candidate is monotone along the thread's pixel column: its end values
-            // (with one bin of slack) bound all four pixels
-            const int NCv = (vp.flags & kViewBwd3) ? 3 : 2;
-            const float pbl = __fmaf_rn((float)(kBwdRowStep * (kBwdPixPerThread - 1)), vp.su_hi, pb0);
-            const int ia = magic_int(ceil_magic(__fsub_rn(__fsub_rn(sm[0], pb0), vp.hwu))) - lo;
-            const int ib = magic_int(ceil_magic(__fsub_rn(__fsub_rn(sm[kBwdPixPerThread - 1], pbl), vp.hwu))) - lo;
-            const bool inside = min(ia, ib) >= 1 && max(ia, ib) <= bwin - NCv - 1;
+            for (int q = 0; q < 4; ++q) {
+                const int vv = g0 + q * kBwdSplit;
+                if (vv < nv) {
+                    const ViewP vp = vsh[buf][vv];
+                    const float *wr = wb + vv * bwin;
+                    const int lo = ulo_sh[buf][vv];
+                    const float pb0 = __fmaf_rn(-vp.cu_hi, X, __fmaf_rn(-vp.su_hi, Y[0], -P.uc_hi));
+                    float sm[kBwdPixPerThread];
+#pragma unroll
+                    for (int e = 0; e < kBwdPixPerThread; ++e) sm[e] = delta_small(vp, X, Y[e], P.uc_lo);
 #define SUPCG_BWD(AX, NC, CK) bwd_view<AX, NC, CK>(vp, pb0, sm, wr, lo, bwin, t4, &bad)
-            if (vp.flags & kViewAxis) {
-                if (inside) SUPCG_BWD(true, 2, false); else SUPCG_BWD(true, 2, true);
-            } else if (NCv == 3) {
-                if (inside) SUPCG_BWD(false, 3, false); else SUPCG_BWD(false, 3, true);
-            } else {
-                if (inside) SUPCG_BWD(false, 2, false); else SUPCG_BWD(false, 2, true);
-            }
+                    switch (kind_sh[buf][vv]) {
+                    case 0: SUPCG_BWD(true, 2, false); break;
+                    case 1: SUPCG_BWD(false, 3, false); break;
+                    case 2: SUPCG_BWD(false, 2, false); break;
+                    case 3: SUPCG_BWD(true, 2, true); break;
+                    case 4: SUPCG_BWD(false, 3, true); break;
+                    default: SUPCG_BWD(false, 2, true); break;
+                    }
 #undef SUPCG_BWD
-            if (((vv / kBwdSplit) & 3) == 3 || vv + kBwdSplit >= nv) {   // Kahan-compensated fold every four views
-#pragma unroll
-                for (int e = 0; e < kBwdPixPerThread; ++e) {
-                    const float y = __fsub_rn(t4[e], comp[e]);
-                    const float tt = __fadd_rn(part[e], y);
-                    comp[e] = __fsub_rn(__fsub_rn(tt, part[e]), y);
-                    part[e] = tt;
-                    t4[e] = 0.0f;
                 }
+            }
+#pragma unroll
+            for (int e = 0; e < kBwdPixPerThread; ++e) {
+                const float y = __fsub_rn(t4[e], comp[e]);
+                const float tt = __fadd_rn(part[e], y);
+                comp[e] = __fsub_rn(__fsub_rn(tt, part[e]), y);
+                part[e] = tt;
+                t4[e] = 0.0f;
             }
         }
         __syncthreads();
