@@ -327,7 +327,27 @@ def run_learned(args, dev):
     t_train = time.perf_counter() - t0
     _, loss_trained = net.gradients(Xh, Th, Dh)
     params = net.get_params()
-    del X, T, D
+    # network kernel timings: one training step on a batch of 32 pairs, one 512^2 inference
+    st = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    xb, tb, db = X[:32].contiguous(), T[:32].contiguous(), D[:32].contiguous()
+    for _ in range(3):
+        net.train_step(xb, tb, db, lr=1e-12, want_loss=False)
+    ev0.record(st)
+    for _ in range(20):
+        net.train_step(xb, tb, db, lr=1e-12, want_loss=False)
+    ev1.record(st)
+    torch.cuda.synchronize()
+    t_step_ms = ev0.elapsed_time(ev1) / 20
+    for _ in range(3):
+        net.forward(xb, tb)
+    ev0.record(st)
+    for _ in range(20):
+        net.forward(xb, tb)
+    ev1.record(st)
+    torch.cuda.synchronize()
+    t_fwd32_ms = ev0.elapsed_time(ev1) / 20
+    del X, T, D, xb, tb, db
     torch.cuda.empty_cache()
     # evaluation on the 512^2 / 720-view Poisson workload
     G, b_host = make_problem(0, dev)
@@ -335,6 +355,16 @@ def run_learned(args, dev):
     net512 = S.CNN(WL["N"], WL["N"], max_batch=1, seed=11)
     net512.set_params(params)
     untrained512 = S.CNN(WL["N"], WL["N"], max_batch=1, seed=11)
+    xi = torch.rand(WL["N"], WL["N"], device=dev)
+    ti = torch.randn(WL["N"], WL["N"], device=dev)
+    for _ in range(3):
+        net512.forward(xi, ti)
+    ev0.record(st)
+    for _ in range(20):
+        net512.forward(xi, ti)
+    ev1.record(st)
+    torch.cuda.synchronize()
+    t_fwd512_ms = ev0.elapsed_time(ev1) / 20
     warm = max(3, args.warmup)
     res = Lr.time_to_equal(G, b, net512, iters=args.steps, device=dev, warmup=warm)
     res_u = Lr.time_to_equal(G, b, untrained512, iters=args.steps, device=dev, warmup=warm)
@@ -349,6 +379,8 @@ def run_learned(args, dev):
         "trained": res, "untrained_network": res_u,
         "training": {"data_s": t_data, "train_s": t_train, "heldout_loss_untrained": loss_untrained,
                      "heldout_loss_trained": loss_trained, "loss_history": hist},
+        "network_ms": {"inference_1x512x512": t_fwd512_ms, "inference_32x128x128": t_fwd32_ms,
+                       "train_step_32x128x128": t_step_ms},
     }
     print(json.dumps(line), flush=True)
     try:
