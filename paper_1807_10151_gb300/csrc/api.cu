@@ -385,11 +385,12 @@ static int ws_create(const std::vector<supcg_geometry> &gs, Workspace **out)
         nb[KT_BWD][c] = ((g->ny + kBwdTileI - 1) / kBwdTileI) * ((g->nx + kBwdTileJ - 1) / kBwdTileJ);
         nb[KT_VEC][c] = (int)(((long long)g->ny * g->nxp + 1023) / 1024);
         nb[KT_TR][c] = ((g->ny + 31) / 32) * ((g->nx + 31) / 32);
-        // FFT: enough blocks to fill the device, each a few rows / columns
-        const int rpb = std::max(1, std::min(std::min(8, 4096 / g->nx), g->ny / 256));
-        const int cw = std::max(1, std::min(std::min(8, 4096 / g->ny), g->nx / 256));
-        nb[KT_ROWS][c] = (g->ny + rpb - 1) / rpb;
-        nb[KT_COLS][c] = (g->nx + cw - 1) / cw;
+        // FFT: enough blocks to fill the device, each a few row pairs / stored columns
+        const int npairs = (g->ny + 1) / 2, hx = g->nx / 2 + 1;
+        const int rpb = std::max(1, std::min(std::min(8, 4096 / g->nx), npairs / 256));
+        const int cw = std::max(1, std::min(std::min(8, 4096 / g->ny), hx / 256));
+        nb[KT_ROWS][c] = (npairs + rpb - 1) / rpb;
+        nb[KT_COLS][c] = (hx + cw - 1) / cw;
         w->smem_rows = std::max(w->smem_rows, 2 * rpb * g->nx * 16);
         w->smem_cols = std::max(w->smem_cols, 2 * cw * g->ny * 16);
         nb[KT_SINO][c] = (int)(((long long)g->V * g->Up + 1023) / 1024);
@@ -437,21 +438,21 @@ static int ws_create(const std::vector<supcg_geometry> &gs, Workspace **out)
         auto al = [](size_t b) { return (b + 255) / 256 * 256; };
         const size_t sizes[] = {img * 4, imgT * 4, img * 4, imgT * 4, img * 4, img * 4, img * 4, img * 4,
                                 sino * 4, sino * 4, sino * 4, (size_t)g->ny * g->nx * 16, sizeof(Scal),
-                                npart * 8, 16 * 4, 4 * 4};
+                                npart * 8, 16 * 4, 4 * 4, (size_t)(g->ny / 2 + 1) * (g->nx / 2 + 1) * 8};
         size_t total = 0;
         for (size_t s : sizes) total += al(s);
         char *base = nullptr;
         if (cudaMalloc(&base, total) != cudaSuccess) { delete w; return SUPCG_ERR_NOMEM; }
         w->allocs.push_back(base);
         if (cudaMemset(base, 0, total) != cudaSuccess) { delete w; return SUPCG_ERR_CUDA; }
-        char *ptrs[16];
+        char *ptrs[17];
         size_t off = 0;
-        for (int k = 0; k < 16; ++k) { ptrs[k] = base + off; off += al(sizes[k]); }
+        for (int k = 0; k < 17; ++k) { ptrs[k] = base + off; off += al(sizes[k]); }
         P.x = (float *)ptrs[0]; P.xT = (float *)ptrs[1]; P.p = (float *)ptrs[2]; P.pT = (float *)ptrs[3];
         P.g = (float *)ptrs[4]; P.z = (float *)ptrs[5]; P.h = (float *)ptrs[6]; P.tbar = (float *)ptrs[7];
         P.r = (float *)ptrs[8]; P.q = (float *)ptrs[9]; P.bpad = (float *)ptrs[10];
         P.C = (double2 *)ptrs[11]; P.sc = (Scal *)ptrs[12]; P.partial = (double *)ptrs[13];
-        P.counter = (unsigned *)ptrs[14]; P.bar = (unsigned *)ptrs[15];
+        P.counter = (unsigned *)ptrs[14]; P.bar = (unsigned *)ptrs[15]; P.Dtab = (double *)ptrs[16];
         P.nx = g->nx; P.ny = g->ny; P.V = g->V; P.U = g->U;
         P.nxp = g->nxp; P.nyp = g->nyp; P.Up = g->Up;
         P.BU = g->BU; P.BW = g->BW; P.ntu = g->ntu; P.nA = g->nA; P.nB = g->nB;
@@ -570,6 +571,7 @@ extern "C" int supcg_precondition(supcg_geometry g, double mu, double rho, const
     for (int b = 0; b < batch; ++b) w->hp[b].storage = g->storage;
     if (rc) return rc;
     if ((rc = launch_stage_in(w->L(KT_TR, st), 1))) return rc;
+    if ((rc = launch_fft_dtab(w->L(KT_VEC, st)))) return rc;
     if ((rc = enqueue_precond(w, st, 1))) return rc;
     return launch_store_out(w->L(KT_VEC, st), 2);
 }
@@ -781,6 +783,7 @@ static int run_solve(Workspace *w, const float *const *d_b, float *const *d_x, c
     }
     LAUNCH(SUPCG_KIND_VECTOR, st, launch_stage_in(w->L(KT_TR, st), 0));
     LAUNCH(SUPCG_KIND_VECTOR, st, launch_stage_sino(w->L(KT_SINO, st), 1));
+    if (p->precondition) LAUNCH(SUPCG_KIND_VECTOR, st, launch_fft_dtab(w->L(KT_VEC, st)));
     if ((rc = enqueue_init(w, p, st))) return rc;
 
     const int want_snorm = d_log != nullptr;

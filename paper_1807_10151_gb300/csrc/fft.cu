@@ -1,12 +1,14 @@
 // Preconditioner z = M g, M = F^-1 D F (Eq. (3.2)), on the ny x nx grid.
 //
-// Three passes over a complex FP64 scratch array C [ny][nx] (FP32 vectors in
-// and out, FP64 arithmetic inside: the operator spans five decades, from
-// h(0) = mu to about pi, and an FP32 transform of a gradient dominated by its
-// low frequencies loses several digits of M g):
-//   rows:  C[i, :] = FFT(g[i, :])                    (k_fft_rows, forward)
-//   cols:  C[:, k2] = IFFT(D[:, k2] * FFT(C[:, k2]))  (k_fft_cols)
-//   rows:  z[i, :] = Re IFFT(C[i, :]) / (nx ny)        (k_fft_rows, inverse)
+// Three passes over a complex FP64 scratch array S [ny][nx/2 + 1] (FP32
+// vectors in and out, FP64 arithmetic inside: the operator spans five decades,
+// from h(0) = mu to about pi, and an FP32 transform of a gradient dominated by
+// its low frequencies loses several digits of M g).  g and z are real and D is
+// real and even, so every row spectrum is Hermitian: only k2 = 0 .. nx/2 is
+// kept, and two real rows share one complex transform.
+//   rows:  S[i, k2] = FFT(g[i, :])(k2), k2 <= nx/2     (k_fft_rows, forward, row pairs)
+//   cols:  S[:, k2] = IFFT(D[:, k2] * FFT(S[:, k2]))   (k_fft_cols)
+//   rows:  z[i, :] = IFFT(Hermitian S[i, :]) / (nx ny)  (k_fft_rows, inverse, row pairs)
 // Each length is transformed in shared memory by a mixed-radix Stockham
 // (autosort) FFT: radix 4 and 2 butterflies written out, any other prime
 // factor by its defining sum.  Twiddles exp(-2 pi i k/n) come from an FP64
@@ -84,7 +86,16 @@ __device__ double2 *fft_smem(double2 *a, double2 *b, int nvec, const FFTPlan &pl
     return a;
 }
 
-// Rows pass.  inverse = 0: g (real) -> C;  inverse = 1: C -> z = Re(.)/(nx ny).
+// Rows pass on pairs of rows (g and z are real).  Block `local` takes the row
+// pairs 2i, 2i+1 for i in [local * rpb, (local + 1) * rpb) (a missing last
+// partner is a zero row).
+//   inverse = 0:  c = g[2i] + i g[2i+1];  C = FFT(c);  the two rows' spectra
+//                 A(k) = (C(k) + conj C(-k)) / 2,  B(k) = (C(k) - conj C(-k)) / (2i)
+//                 for k = 0 .. nx/2 (the rest follows by Hermitian symmetry) go to
+//                 S[2i][k] and S[2i+1][k], S = C viewed as [ny][nx/2 + 1].
+//   inverse = 1:  c(k) = Y(2i, k) + i Y(2i+1, k) with Y(r, k) = conj Y(r, nx - k)
+//                 beyond nx/2 (the filtered rows are real);  z[2i] + i z[2i+1] =
+//                 IFFT(c) / (nx ny).
 __global__ void __launch_bounds__(256) k_fft_rows(const Prob *__restrict__ probs, const int *__restrict__ prefix,
                                                   int count, int inverse, int standalone)
 {
@@ -92,28 +103,55 @@ __global__ void __launch_bounds__(256) k_fft_rows(const Prob *__restrict__ probs
     int local;
     const Prob &P = probs[find_problem(prefix, count, blockIdx.x, &local)];
     if (!standalone && P.sc->done) return;
-    const int nx = P.nx, rpb = P.fft_rpb;
+    const int nx = P.nx, ny = P.ny, rpb = P.fft_rpb, hx = nx / 2 + 1;
+    const int npairs = (ny + 1) / 2;
     double2 *a = reinterpret_cast<double2 *>(smem_raw);
     double2 *b = a + rpb * nx;
-    const int i0 = local * rpb;
-    const int nr = min(rpb, P.ny - i0);
-    for (int e = threadIdx.x; e < nr * nx; e += blockDim.x) {
-        const int r = e / nx, q = e - r * nx;
-        const size_t gi = (size_t)(i0 + r);
-        a[e] = inverse ? P.C[gi * nx + q] : make_double2((double)P.g[gi * P.nxp + q], 0.0);
+    const int p0 = local * rpb;
+    const int np = min(rpb, npairs - p0);
+    double2 *S = P.C;
+    for (int e = threadIdx.x; e < np * nx; e += blockDim.x) {
+        const int pr = e / nx, q = e - pr * nx;
+        const int ra = 2 * (p0 + pr), rb = ra + 1;
+        if (!inverse) {
+            const double va = (double)P.g[(size_t)ra * P.nxp + q];
+            const double vb = rb < ny ? (double)P.g[(size_t)rb * P.nxp + q] : 0.0;
+            a[e] = make_double2(va, vb);
+        } else {
+            const bool lo = q <= nx / 2;
+            const int kk = lo ? q : nx - q;
+            double2 ya = S[(size_t)ra * hx + kk];
+            double2 yb = rb < ny ? S[(size_t)rb * hx + kk] : make_double2(0.0, 0.0);
+            if (!lo) {
+                ya.y = -ya.y;
+                yb.y = -yb.y;
+            }
+            a[e] = make_double2(ya.x - yb.y, ya.y + yb.x);   // ya + i yb
+        }
     }
     __syncthreads();
-    double2 *res = fft_smem(a, b, nr, P.fx, inverse != 0);
-    const double scale = 1.0 / ((double)P.nx * (double)P.ny);
-    for (int e = threadIdx.x; e < nr * nx; e += blockDim.x) {
-        const int r = e / nx, q = e - r * nx;
-        const size_t gi = (size_t)(i0 + r);
-        if (inverse) P.z[gi * P.nxp + q] = (float)(res[e].x * scale);
-        else P.C[gi * nx + q] = res[e];
+    double2 *res = fft_smem(a, b, np, P.fx, inverse != 0);
+    if (!inverse) {
+        for (int e = threadIdx.x; e < np * hx; e += blockDim.x) {
+            const int pr = e / hx, k = e - pr * hx;
+            const int ra = 2 * (p0 + pr), rb = ra + 1;
+            const double2 c1 = res[pr * nx + k], c2 = res[pr * nx + (k == 0 ? 0 : nx - k)];
+            S[(size_t)ra * hx + k] = make_double2(0.5 * (c1.x + c2.x), 0.5 * (c1.y - c2.y));
+            if (rb < ny) S[(size_t)rb * hx + k] = make_double2(0.5 * (c1.y + c2.y), 0.5 * (c2.x - c1.x));
+        }
+    } else {
+        const double scale = 1.0 / ((double)nx * (double)ny);
+        for (int e = threadIdx.x; e < np * nx; e += blockDim.x) {
+            const int pr = e / nx, q = e - pr * nx;
+            const int ra = 2 * (p0 + pr), rb = ra + 1;
+            P.z[(size_t)ra * P.nxp + q] = (float)(res[e].x * scale);
+            if (rb < ny) P.z[(size_t)rb * P.nxp + q] = (float)(res[e].y * scale);
+        }
     }
 }
 
-// Columns pass: forward FFT, multiply by D = h(w_r), inverse FFT.
+// Columns pass over the nx/2 + 1 stored frequencies k2: forward FFT along
+// the columns, multiply by D = h(w_r), inverse FFT.
 __global__ void __launch_bounds__(256) k_fft_cols(const Prob *__restrict__ probs, const int *__restrict__ prefix,
                                                   int count, int standalone)
 {
@@ -121,35 +159,57 @@ __global__ void __launch_bounds__(256) k_fft_cols(const Prob *__restrict__ probs
     int local;
     const Prob &P = probs[find_problem(prefix, count, blockIdx.x, &local)];
     if (!standalone && P.sc->done) return;
-    const int nx = P.nx, ny = P.ny, cw = P.fft_cw;
+    const int nx = P.nx, ny = P.ny, cw = P.fft_cw, hx = nx / 2 + 1;
     double2 *a = reinterpret_cast<double2 *>(smem_raw);
     double2 *b = a + cw * ny;
     const int c0 = local * cw;
-    const int nc = min(cw, nx - c0);
+    const int nc = min(cw, hx - c0);
+    double2 *S = P.C;
     for (int e = threadIdx.x; e < nc * ny; e += blockDim.x) {
         const int k1 = e / nc, c = e - k1 * nc;   // consecutive threads read consecutive columns
-        a[c * ny + k1] = P.C[(size_t)k1 * nx + c0 + c];
+        a[c * ny + k1] = S[(size_t)k1 * hx + c0 + c];
     }
     __syncthreads();
     double2 *res = fft_smem(a, b, nc, P.fy, false);
     double2 *oth = (res == a) ? b : a;
-    const double two_pi = 6.28318530717958647692;
-    const double pi_d = 3.14159265358979323846;
     for (int e = threadIdx.x; e < nc * ny; e += blockDim.x) {
         const int c = e / ny, k1 = e - c * ny;
-        const int k2 = c0 + c;
-        const int m1 = min(k1, ny - k1), m2 = min(k2, nx - k2);
-        const double w1 = two_pi * m1 / ny, w2 = two_pi * m2 / nx;
-        const double wr = fmin(sqrt(w1 * w1 + w2 * w2), pi_d);
-        const double hD = (wr + P.mu) * (P.rho + (1.0 - P.rho) * cos(wr));
+        const double hD = __ldg(P.Dtab + (size_t)min(k1, ny - k1) * hx + c0 + c);   // k2 <= nx/2
         res[e] = make_double2(res[e].x * hD, res[e].y * hD);
     }
     __syncthreads();
     double2 *fin = fft_smem(res, oth, nc, P.fy, true);
     for (int e = threadIdx.x; e < nc * ny; e += blockDim.x) {
         const int k1 = e / nc, c = e - k1 * nc;
-        P.C[(size_t)k1 * nx + c0 + c] = fin[c * ny + k1];
+        S[(size_t)k1 * hx + c0 + c] = fin[c * ny + k1];
     }
+}
+
+// D = h(w_r) on the quarter spectrum (D is even in both frequencies):
+// Dtab[m1][m2], w_i = 2 pi m_i / N_i, w_r = min(sqrt(w1^2 + w2^2), pi).
+__global__ void __launch_bounds__(256) k_fft_dtab(const Prob *__restrict__ probs, const int *__restrict__ prefix,
+                                                  int count)
+{
+    int local;
+    const Prob &P = probs[find_problem(prefix, count, blockIdx.x, &local)];
+    const int nx = P.nx, ny = P.ny, hx = nx / 2 + 1, hy = ny / 2 + 1;
+    const double two_pi = 6.28318530717958647692;
+    const double pi_d = 3.14159265358979323846;
+    for (int k = 0; k < 4; ++k) {
+        const long long e = (long long)local * 1024 + k * 256 + threadIdx.x;
+        if (e >= (long long)hx * hy) break;
+        const int m1 = (int)(e / hx), m2 = (int)(e - (long long)m1 * hx);
+        const double w1 = two_pi * m1 / ny, w2 = two_pi * m2 / nx;
+        const double wr = fmin(sqrt(w1 * w1 + w2 * w2), pi_d);
+        P.Dtab[e] = (wr + P.mu) * (P.rho + (1.0 - P.rho) * cos(wr));
+    }
+}
+
+int launch_fft_dtab(const Launch &L)
+{
+    k_fft_dtab<<<L.blocks, 256, 0, L.st>>>(L.probs, L.prefix, L.count);
+    SUPCG_CUDA_TRY(cudaGetLastError());
+    return SUPCG_OK;
 }
 
 int launch_fft_rows(const Launch &L, int inverse, int standalone, int smem)

@@ -150,6 +150,7 @@ struct Prob {
     float *x, *xT, *p, *pT, *g, *z, *h, *tbar;
     float *r, *q, *bpad;
     double2 *C;            // FFT scratch [ny][nx] (FP64 complex)
+    double *Dtab;          // preconditioner diagonal h(w_r) at (min(k1, ny-k1), min(k2, nx-k2)): [ny/2+1][nx/2+1]
     Scal *sc;
     double *partial;       // reduction partials (>= 2 * max blocks per kernel)
     unsigned *counter;     // last-block tickets [8]
@@ -341,6 +342,7 @@ int launch_stage_sino(const Launch &L, int which);         // caller sinogram ->
 int launch_store_out(const Launch &L, int which);          // padded image (0 x, 1 g, 2 z, 3 tbar) -> caller
 int launch_fft_rows(const Launch &L, int inverse, int standalone, int smem);
 int launch_fft_cols(const Launch &L, int standalone, int smem);
+int launch_fft_dtab(const Launch &L);                       // fills Dtab from mu, rho (once per solve or call)
 int launch_pupdate(const Launch &L);
 int launch_beta(const Launch &L);
 int launch_xupdate(const Launch &L);
