@@ -127,6 +127,8 @@ __global__ void __launch_bounds__(kTvThreads) k_stv(const Prob *__restrict__ pro
 {
     __shared__ double red[40];
     __shared__ int flag;
+    __shared__ double sh_inv;   // grid-uniform FP64 scalars: computed by thread 0, read by all
+    __shared__ float sh_c;
     int local;
     const int pi = find_problem(prefix, count, blockIdx.x, &local);
     const Prob &P = probs[pi];
@@ -134,9 +136,9 @@ __global__ void __launch_bounds__(kTvThreads) k_stv(const Prob *__restrict__ pro
     if (sc->done) return;
     const int nb = prefix[pi + 1] - prefix[pi];
     const int nx = P.nx, ny = P.ny, ld = P.nxp;
-    const long long n = (long long)ny * nx;
-    const long long stride = (long long)nb * kTvThreads;
-    const long long e0 = (long long)local * kTvThreads + threadIdx.x;
+    const int n = ny * nx;   // < 2^31 (each side <= 16384)
+    const int stride = nb * kTvThreads;
+    const int e0 = local * kTvThreads + threadIdx.x;
     float *x = P.x;
     float *tb = P.tbar;
     long long ell = sc->ell;
@@ -146,8 +148,8 @@ __global__ void __launch_bounds__(kTvThreads) k_stv(const Prob *__restrict__ pro
     bool ok = true;
 
     if (want_snorm)
-        for (long long e = e0; e < n; e += stride) {
-            const int i = (int)(e / nx), j = (int)(e - (long long)i * nx);
+        for (int e = e0; e < n; e += stride) {
+            const int i = e / nx, j = e - i * nx;
             P.z[(size_t)i * ld + j] = x[(size_t)i * ld + j];
         }
 
@@ -160,8 +162,8 @@ __global__ void __launch_bounds__(kTvThreads) k_stv(const Prob *__restrict__ pro
     bool plain = true;
     if (dir) {
         double s_nn = 0.0, s_dd = 0.0, s_tv = 0.0;
-        for (long long e = e0; e < n; e += stride) {
-            const int i = (int)(e / nx), j = (int)(e - (long long)i * nx);
+        for (int e = e0; e < n; e += stride) {
+            const int i = e / nx, j = e - i * nx;
             const size_t p = (size_t)i * ld + j;
             const size_t q = (size_t)i * nx + j;
             const float tp = dir[q];
@@ -196,8 +198,9 @@ __global__ void __launch_bounds__(kTvThreads) k_stv(const Prob *__restrict__ pro
         }
         if (ok && s_dd < 0.0 && s_nn > 0.0) {
             plain = false;
-            const double inv_norm = 1.0 / sqrt(s_nn);
-            const double geo = (a == 1.0) ? (double)K : (1.0 - pow(a, (double)K)) / (1.0 - a);
+            // the step scalars are the same in every thread: thread 0 evaluates the FP64
+            // functions and the block reads the result (the FP64 pipe is narrow)
+            if (threadIdx.x == 0) sh_inv = 1.0 / sqrt(s_nn);
             long long j = 0;
             float c = 0.0f;
             double tv_t = 0.0;
@@ -207,11 +210,16 @@ __global__ void __launch_bounds__(kTvThreads) k_stv(const Prob *__restrict__ pro
                     ok = false;
                     break;
                 }
-                c = (float)(ldexp(gamma * pow(a, (double)ell) * geo, -(int)min(j, 2000ll)) * inv_norm);
+                if (threadIdx.x == 0) {
+                    const double geo = (a == 1.0) ? (double)K : (1.0 - pow(a, (double)K)) / (1.0 - a);
+                    sh_c = (float)(ldexp(gamma * pow(a, (double)ell) * geo, -(int)min(j, 2000ll)) * sh_inv);
+                }
+                __syncthreads();
+                c = sh_c;
                 ++j;
                 double sacc = 0.0;
-                for (long long e = e0; e < n; e += stride) {
-                    const int i = (int)(e / nx), jj = (int)(e - (long long)i * nx);
+                for (int e = e0; e < n; e += stride) {
+                    const int i = e / nx, jj = e - i * nx;
                     if (i + 1 < ny && jj + 1 < nx) {
                         const size_t p = (size_t)i * ld + jj, q = (size_t)i * nx + jj;
                         const float yc = __fmaf_rn(c, dir[q], x[p]);
@@ -227,8 +235,8 @@ __global__ void __launch_bounds__(kTvThreads) k_stv(const Prob *__restrict__ pro
                 if (tv_t <= s_tv) break;
             }
             if (ok) {
-                for (long long e = e0; e < n; e += stride) {
-                    const int i = (int)(e / nx), jj = (int)(e - (long long)i * nx);
+                for (int e = e0; e < n; e += stride) {
+                    const int i = e / nx, jj = e - i * nx;
                     const size_t p = (size_t)i * ld + jj;
                     x[p] = __fmaf_rn(c, dir[(size_t)i * nx + jj], x[p]);
                 }
@@ -247,8 +255,8 @@ __global__ void __launch_bounds__(kTvThreads) k_stv(const Prob *__restrict__ pro
     for (int step = 0; plain && step < K && ok; ++step) {
         // t in the nonascending set at y (Sec. 3.1)
         double s_tv = 0.0, s_nn = 0.0;
-        for (long long e = e0; e < n; e += stride) {
-            const int i = (int)(e / nx), j = (int)(e - (long long)i * nx);
+        for (int e = e0; e < n; e += stride) {
+            const int i = e / nx, j = e - i * nx;
             float Tb;
             const float t = tbar_at(x, ld, ny, nx, i, j, &Tb);
             tb[(size_t)i * ld + j] = t;
@@ -271,7 +279,9 @@ __global__ void __launch_bounds__(kTvThreads) k_stv(const Prob *__restrict__ pro
         }
         const double tv_y = s_tv;
         if (step == 0) tv_first = tv_y;
-        const double inv_norm = (s_nn > 0.0) ? 1.0 / sqrt(s_nn) : 0.0;
+        // the step scalars are the same in every thread: thread 0 evaluates the FP64
+        // functions and the block reads the result (the FP64 pipe is narrow)
+        if (threadIdx.x == 0) sh_inv = (s_nn > 0.0) ? 1.0 / sqrt(s_nn) : 0.0;
         long long trials = 0;
         float c = 0.0f;
         double tv_t = 0.0;
@@ -281,13 +291,14 @@ __global__ void __launch_bounds__(kTvThreads) k_stv(const Prob *__restrict__ pro
                 ok = false;
                 break;
             }
-            const double gt = gamma * pow(a, (double)ell);   // gamma~ = gamma a^l
-            c = (float)(gt * inv_norm);                      // y~ = y + gamma~ tbar/||tbar||
+            if (threadIdx.x == 0) sh_c = (float)(gamma * pow(a, (double)ell) * sh_inv);   // gamma a^l / ||tbar||
+            __syncthreads();
+            c = sh_c;                                                                     // y~ = y + c tbar
             ++ell;
             ++trials;
             double s = 0.0;
-            for (long long e = e0; e < n; e += stride) {
-                const int i = (int)(e / nx), j = (int)(e - (long long)i * nx);
+            for (int e = e0; e < n; e += stride) {
+                const int i = e / nx, j = e - i * nx;
                 if (i + 1 < ny && j + 1 < nx) s += (double)trial_term(x, tb, ld, i, j, c);
             }
             tv_t = phase_sum(P, nb, slot, local, s, red, &flag, &ok);
@@ -298,8 +309,8 @@ __global__ void __launch_bounds__(kTvThreads) k_stv(const Prob *__restrict__ pro
         total_trials += trials;
         if (!ok) break;
         if (trials_out && local == 0 && threadIdx.x == 0) trials_out[(size_t)pi * K + step] = (int)trials;
-        for (long long e = e0; e < n; e += stride) {   // y <- y~
-            const int i = (int)(e / nx), j = (int)(e - (long long)i * nx);
+        for (int e = e0; e < n; e += stride) {   // y <- y~
+            const int i = e / nx, j = e - i * nx;
             const size_t p = (size_t)i * ld + j;
             x[p] = __fmaf_rn(c, tb[p], x[p]);
         }
@@ -309,8 +320,8 @@ __global__ void __launch_bounds__(kTvThreads) k_stv(const Prob *__restrict__ pro
     double sn = 0.0;
     if (ok && want_snorm) {
         double s = 0.0;
-        for (long long e = e0; e < n; e += stride) {
-            const int i = (int)(e / nx), j = (int)(e - (long long)i * nx);
+        for (int e = e0; e < n; e += stride) {
+            const int i = e / nx, j = e - i * nx;
             const size_t p = (size_t)i * ld + j;
             const double dlt = (double)x[p] - (double)P.z[p];
             s += dlt * dlt;
