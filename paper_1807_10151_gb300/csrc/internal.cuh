@@ -71,6 +71,40 @@ __device__ __forceinline__ float weight_unit(float ad, float E, float Sn, float 
     return w;
 }
 
+// Packed pairs of FP32 values (f32x2: one instruction, two IEEE operations with
+// the stated rounding, lane by lane identical to the scalar operation).
+__device__ __forceinline__ uint64_t pk2(float a, float b)
+{
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void upk2(uint64_t p, float &a, float &b) { asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(p)); }
+__device__ __forceinline__ uint64_t add2_rn(uint64_t a, uint64_t b)
+{
+    uint64_t r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ uint64_t add2_rp(uint64_t a, uint64_t b)
+{
+    uint64_t r;
+    asm("add.rp.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ uint64_t sub2_rn(uint64_t a, uint64_t b)
+{
+    uint64_t r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+    return r;
+}
+__device__ __forceinline__ uint64_t fma2_rn(uint64_t a, uint64_t b, uint64_t c)
+{
+    uint64_t r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+    return r;
+}
+
 // ceil(x) for |x| < 2^22 by one FP32 addition rounded upward: x + 1.5 * 2^23
 // lies where FP32 numbers are the integers, so that sum's bits minus those of
 // 1.5 * 2^23 give ceil(x) as an integer, and its value minus 1.5 * 2^23 gives it

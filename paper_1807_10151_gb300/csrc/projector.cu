@@ -353,6 +353,36 @@ __device__ __forceinline__ void bwd_view(const ViewP &vp, float pb0, const float
     }
 }
 
+// The same for the thread's pixels in pairs (2h, 2h + 1), every FP32 step as one
+// f32x2 instruction; only for windows that hold every candidate (no checks).
+// sm2[h] = (small of pixel 2h, of pixel 2h + 1); t2[h] the pairs' running sums.
+template <bool AXIS, int NC>
+__device__ __forceinline__ void bwd_view_x2(const ViewP &vp, float pb0, const uint64_t *sm2, const float *w_row,
+                                            int lo, uint64_t *t2)
+{
+    const float E = vp.E, Sn = vp.Sn, ESn = vp.ESn;
+    const uint64_t su2 = pk2(vp.su_hi, vp.su_hi), hwu2 = pk2(vp.hwu, vp.hwu), pbb = pk2(pb0, pb0);
+    const uint64_t mag2 = pk2(kCeilMagic, kCeilMagic);
+#pragma unroll
+    for (int h = 0; h < kBwdPixPerThread / 2; ++h) {
+        const uint64_t st = pk2((float)(kBwdRowStep * 2 * h), (float)(kBwdRowStep * (2 * h + 1)));
+        const uint64_t pb = fma2_rn(st, su2, pbb);                          // exact
+        const uint64_t uc = add2_rp(sub2_rn(sub2_rn(sm2[h], pb), hwu2), mag2);
+        float uca, ucb;
+        upk2(uc, uca, ucb);
+        const float *wa = w_row + (magic_int(uca) - lo), *wb = w_row + (magic_int(ucb) - lo);
+        const uint64_t big0 = add2_rn(sub2_rn(uc, mag2), pb);              // exact, as are big0 + 1, + 2
+#pragma unroll
+        for (int k = 0; k < NC; ++k) {
+            const uint64_t bk = k ? add2_rn(big0, pk2((float)k, (float)k)) : big0;
+            float da, db;
+            upk2(sub2_rn(bk, sm2[h]), da, db);
+            const uint64_t w = pk2(weight_unit(fabsf(da), E, Sn, ESn, AXIS), weight_unit(fabsf(db), E, Sn, ESn, AXIS));
+            t2[h] = fma2_rn(w, pk2(wa[k], wb[k]), t2[h]);                 // w_row holds P * y
+        }
+    }
+}
+
 __global__ void __launch_bounds__(kBwdThreads, 4) k_backward(const Prob *__restrict__ probs,
                                                           const int *__restrict__ prefix, int count, int mode)
 {
@@ -380,11 +410,18 @@ __global__ void __launch_bounds__(kBwdThreads, 4) k_backward(const Prob *__restr
     float Y[kBwdPixPerThread];
 #pragma unroll
     for (int e = 0; e < kBwdPixPerThread; ++e) Y[e] = __fsub_rn(P.cy, __int2float_rn(i0 + ly + kBwdRowStep * e));
-    // per pixel: FP32 sum of up to four views (t4), folded into a Kahan-compensated pair (part, comp)
-    // that runs over all views; FP64 only for the final value (the FP64 pipe is narrow)
-    float part[kBwdPixPerThread], comp[kBwdPixPerThread], t4[kBwdPixPerThread];
+    // per pixel: FP32 sum of up to four views (t2, pixels in pairs), folded into a Kahan-compensated
+    // pair (part, comp) that runs over all views; FP64 only for the final value (the FP64 pipe is narrow)
+    float part[kBwdPixPerThread], comp[kBwdPixPerThread];
+    uint64_t t2[kBwdPixPerThread / 2];
 #pragma unroll
-    for (int e = 0; e < kBwdPixPerThread; ++e) part[e] = comp[e] = t4[e] = 0.0f;
+    for (int e = 0; e < kBwdPixPerThread; ++e) part[e] = comp[e] = 0.0f;
+#pragma unroll
+    for (int h = 0; h < kBwdPixPerThread / 2; ++h) t2[h] = pk2(0.0f, 0.0f);
+    uint64_t Y2[kBwdPixPerThread / 2];
+#pragma unroll
+    for (int h = 0; h < kBwdPixPerThread / 2; ++h) Y2[h] = pk2(Y[2 * h], Y[2 * h + 1]);
+    const uint64_t X2 = pk2(X, X);
 
     const float *sino = (mode == BWD_G) ? P.r : (mode == BWD_H ? P.q : P.r);
     const int Up = P.Up;
@@ -464,20 +501,44 @@ __global__ void __launch_bounds__(kBwdThreads, 4) k_backward(const Prob *__restr
                     const float *wr = wb + vv * bwin;
                     const int lo = ulo_sh[buf][vv];
                     const float pb0 = __fmaf_rn(-vp.cu_hi, X, __fmaf_rn(-vp.su_hi, Y[0], -P.uc_hi));
-                    float sm[kBwdPixPerThread];
+                    // small = uc_lo + cu_lo X + su_lo Y in the view class's order (delta_small), in pairs
+                    uint64_t sm2[kBwdPixPerThread / 2];
+                    if (vp.flags & kViewClassB) {
+                        const float in = __fmaf_rn(vp.cu_lo, X, P.uc_lo);
+                        const uint64_t s2 = pk2(vp.su_lo, vp.su_lo), in2 = pk2(in, in);
 #pragma unroll
-                    for (int e = 0; e < kBwdPixPerThread; ++e) sm[e] = delta_small(vp, X, Y[e], P.uc_lo);
-#define SUPCG_BWD(AX, NC, CK) bwd_view<AX, NC, CK>(vp, pb0, sm, wr, lo, bwin, t4, &bad)
-                    switch (kind_sh[buf][vv]) {
-                    case 0: SUPCG_BWD(true, 2, false); break;
-                    case 1: SUPCG_BWD(false, 3, false); break;
-                    case 2: SUPCG_BWD(false, 2, false); break;
-                    case 3: SUPCG_BWD(true, 2, true); break;
-                    case 4: SUPCG_BWD(false, 3, true); break;
-                    default: SUPCG_BWD(false, 2, true); break;
+                        for (int h = 0; h < kBwdPixPerThread / 2; ++h) sm2[h] = fma2_rn(s2, Y2[h], in2);
+                    } else {
+                        const uint64_t s2 = pk2(vp.su_lo, vp.su_lo), c2 = pk2(vp.cu_lo, vp.cu_lo),
+                                       u2 = pk2(P.uc_lo, P.uc_lo);
+#pragma unroll
+                        for (int h = 0; h < kBwdPixPerThread / 2; ++h) sm2[h] = fma2_rn(c2, X2, fma2_rn(s2, Y2[h], u2));
                     }
-#undef SUPCG_BWD
+                    const int kind = kind_sh[buf][vv];
+                    if (kind < 3) {
+                        if (kind == 0) bwd_view_x2<true, 2>(vp, pb0, sm2, wr, lo, t2);
+                        else if (kind == 1) bwd_view_x2<false, 3>(vp, pb0, sm2, wr, lo, t2);
+                        else bwd_view_x2<false, 2>(vp, pb0, sm2, wr, lo, t2);
+                    } else {   // a window check is needed: the scalar path
+                        float sm[kBwdPixPerThread], t4[kBwdPixPerThread];
+#pragma unroll
+                        for (int h = 0; h < kBwdPixPerThread / 2; ++h) {
+                            upk2(sm2[h], sm[2 * h], sm[2 * h + 1]);
+                            upk2(t2[h], t4[2 * h], t4[2 * h + 1]);
+                        }
+                        if (kind == 3) bwd_view<true, 2, true>(vp, pb0, sm, wr, lo, bwin, t4, &bad);
+                        else if (kind == 4) bwd_view<false, 3, true>(vp, pb0, sm, wr, lo, bwin, t4, &bad);
+                        else bwd_view<false, 2, true>(vp, pb0, sm, wr, lo, bwin, t4, &bad);
+#pragma unroll
+                        for (int h = 0; h < kBwdPixPerThread / 2; ++h) t2[h] = pk2(t4[2 * h], t4[2 * h + 1]);
+                    }
                 }
+            }
+            float t4[kBwdPixPerThread];
+#pragma unroll
+            for (int h = 0; h < kBwdPixPerThread / 2; ++h) {
+                upk2(t2[h], t4[2 * h], t4[2 * h + 1]);
+                t2[h] = pk2(0.0f, 0.0f);
             }
 #pragma unroll
             for (int e = 0; e < kBwdPixPerThread; ++e) {
@@ -485,7 +546,6 @@ __global__ void __launch_bounds__(kBwdThreads, 4) k_backward(const Prob *__restr
                 const float tt = __fadd_rn(part[e], y);
                 comp[e] = __fsub_rn(__fsub_rn(tt, part[e]), y);
                 part[e] = tt;
-                t4[e] = 0.0f;
             }
         }
         __syncthreads();
