@@ -46,36 +46,68 @@ __device__ __forceinline__ void fwd_rows(const Prob &P, const ViewP &vp, float t
     const float qh = __fsub_rn(qm, vp.hwq);
     const float *prow = patch - qs;
     float rs = 0.0f;   // FP32 sum of up to 8 rows, then folded into (sum, comp)
+    // without checks the first two candidates run as packed f32x2 steps (lane for lane the
+    // scalar IEEE operations): rs2 holds their separate sums, rs the third candidate's
+    uint64_t rs2 = pk2(0.0f, 0.0f), Oc2 = pk2(Oc, Oc);
+    const uint64_t hio2 = pk2(-hi_o, -hi_o), loo2 = pk2(lo_o, lo_o), tau2 = pk2(tau_hi, tau_hi);
+    const uint64_t ucl2 = pk2(P.uc_lo, P.uc_lo), hii2 = pk2(-hi_i, -hi_i), loi2 = pk2(lo_i, lo_i), dO2 = pk2(dO, dO);
     auto row = [&](int r, float rf) {
         const float qc = ceil_magic(__fmaf_rn(rf, vp.b_o, qh));
         int q0 = magic_int(qc);
-        if (CHECKED) {
+        if constexpr (CHECKED) {
             const int idx = q0 - qs;
             if (idx < 0 || idx > BW - NC) {   // outside the staged box: never for a valid box (host-checked)
                 *bad = 1;
                 q0 = min(max(idx, 0), BW - NC) + qs;
             }
-        }
-        const float *pv = prow + r * BW + q0;
-        const float rbig = __fmaf_rn(-hi_o, Oc, tau_hi);            // exact
-        const float rsmall = __fmaf_rn(lo_o, Oc, P.uc_lo);
-        Oc = __fadd_rn(Oc, dO);
-        const float q0f = CHECKED ? __int2float_rn(q0) : magic_float(qc);   // the clamped index when checked
-        const float I0 = CLASS_B ? __fsub_rn(c_in, q0f) : __fsub_rn(q0f, c_in);
+            const float *pv = prow + r * BW + q0;
+            const float rbig = __fmaf_rn(-hi_o, Oc, tau_hi);            // exact
+            const float rsmall = __fmaf_rn(lo_o, Oc, P.uc_lo);
+            Oc = __fadd_rn(Oc, dO);
+            const float q0f = __int2float_rn(q0);                      // the clamped index
+            const float I0 = CLASS_B ? __fsub_rn(c_in, q0f) : __fsub_rn(q0f, c_in);
 #pragma unroll
-        for (int k = 0; k < NC; ++k) {
-            const float I = __fadd_rn(I0, k * dI);                    // exact half-integer
-            const float big = __fmaf_rn(-hi_i, I, rbig);              // exact
-            const float ad = fabsf(__fsub_rn(big, __fmaf_rn(lo_i, I, rsmall)));
-            rs = __fmaf_rn(weight_unit(ad, E, Sn, ESn, AXIS), pv[k], rs);
+            for (int k = 0; k < NC; ++k) {
+                const float I = __fadd_rn(I0, k * dI);                    // exact half-integer
+                const float big = __fmaf_rn(-hi_i, I, rbig);              // exact
+                const float ad = fabsf(__fsub_rn(big, __fmaf_rn(lo_i, I, rsmall)));
+                rs = __fmaf_rn(weight_unit(ad, E, Sn, ESn, AXIS), pv[k], rs);
+            }
+        } else {
+            const float *pv = prow + r * BW + q0;
+            const uint64_t rbig2 = fma2_rn(hio2, Oc2, tau2);             // exact
+            const uint64_t rsmall2 = fma2_rn(loo2, Oc2, ucl2);
+            Oc2 = add2_rn(Oc2, dO2);
+            const float q0f = magic_float(qc);
+            const float I0 = CLASS_B ? __fsub_rn(c_in, q0f) : __fsub_rn(q0f, c_in);
+            const float I1 = __fadd_rn(I0, dI);                           // exact half-integers
+            const uint64_t I2 = pk2(I0, I1);
+            const uint64_t big2 = fma2_rn(hii2, I2, rbig2);              // exact
+            float d0, d1;
+            upk2(sub2_rn(big2, fma2_rn(loi2, I2, rsmall2)), d0, d1);
+            const uint64_t w2 = pk2(weight_unit(fabsf(d0), E, Sn, ESn, AXIS), weight_unit(fabsf(d1), E, Sn, ESn, AXIS));
+            rs2 = fma2_rn(w2, pk2(pv[0], pv[1]), rs2);
+            if constexpr (NC == 3) {
+                float rbig, rbig_b, rsmall, rsmall_b;
+                upk2(rbig2, rbig, rbig_b);
+                upk2(rsmall2, rsmall, rsmall_b);
+                const float I = __fadd_rn(I1, dI);
+                const float big = __fmaf_rn(-hi_i, I, rbig);
+                const float ad = fabsf(__fsub_rn(big, __fmaf_rn(lo_i, I, rsmall)));
+                rs = __fmaf_rn(weight_unit(ad, E, Sn, ESn, AXIS), pv[2], rs);
+            }
         }
     };
     auto fold = [&]() {   // Kahan-compensated fold of the group's sum
-        const float y = __fsub_rn(rs, comp);
+        float ra, rb2;
+        upk2(rs2, ra, rb2);
+        const float g = __fadd_rn(__fadd_rn(ra, rb2), rs);
+        const float y = __fsub_rn(g, comp);
         const float tt = __fadd_rn(sum, y);
         comp = __fsub_rn(__fsub_rn(tt, sum), y);
         sum = tt;
         rs = 0.0f;
+        rs2 = pk2(0.0f, 0.0f);
     };
     // groups of eight rows from rb, the last one possibly shorter
     int r = rb;
