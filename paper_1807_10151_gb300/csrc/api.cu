@@ -720,13 +720,16 @@ static int enqueue_body(Workspace *w, const supcg_params *p, cudaStream_t st, in
     if (p->perturb && p->K > 0)                                                 // steps 11-12
         LAUNCH(SUPCG_KIND_STV, st, launch_stv(w->L(KT_STV, st), p->K, p->a, p->gamma, p->max_trials, nullptr,
                                               want_snorm, dir));
-    LAUNCH(SUPCG_KIND_VECTOR, st, launch_transpose(w->L(KT_TR, st), 0));
+    else                                                                        // (S_TV writes x^T itself)
+        LAUNCH(SUPCG_KIND_VECTOR, st, launch_transpose(w->L(KT_TR, st), 0));
     LAUNCH(SUPCG_KIND_FORWARD, st, launch_forward(w->L(KT_FWD, st), 0, FWD_RESID));   // r = R x - b, f
     LAUNCH(SUPCG_KIND_BACKWARD, st, launch_backward(w->L(KT_BWD, st), BWD_G, w->bwin));         // g = R^T r
-    if (p->precondition && (rc = enqueue_precond_k(w, st))) return rc;                  // z = M g
-    LAUNCH(SUPCG_KIND_VECTOR, st, launch_beta(w->L(KT_VEC, st)));               // beta = z^T h / p^T h
-    LAUNCH(SUPCG_KIND_VECTOR, st, launch_pupdate(w->L(KT_VEC, st)));            // p = -z + beta p, g^T p
-    LAUNCH(SUPCG_KIND_VECTOR, st, launch_transpose(w->L(KT_TR, st), 1));
+    if (p->precondition) {                                                      // z = M g; its last pass
+        if ((rc = enqueue_precond_k(w, st))) return rc;                         // also forms beta
+    } else {
+        LAUNCH(SUPCG_KIND_VECTOR, st, launch_beta(w->L(KT_VEC, st)));           // beta = z^T h / p^T h
+    }
+    LAUNCH(SUPCG_KIND_VECTOR, st, launch_pupdate(w->L(KT_TR, st)));             // p = -z + beta p, g^T p, p^T
     LAUNCH(SUPCG_KIND_FORWARD, st, launch_forward(w->L(KT_FWD, st), 1, FWD_NORM));    // q = R p, p^T h, alpha
     LAUNCH(SUPCG_KIND_BACKWARD, st, launch_backward(w->L(KT_BWD, st), BWD_H, w->bwin));         // h = R^T q
     LAUNCH(SUPCG_KIND_VECTOR, st, launch_log(w->L(KT_VEC, st)));                // k <- k + 1
@@ -739,10 +742,12 @@ static int enqueue_init(Workspace *w, const supcg_params *p, cudaStream_t st)
     int rc;
     LAUNCH(SUPCG_KIND_FORWARD, st, launch_forward(w->L(KT_FWD, st), 0, FWD_RESID));
     LAUNCH(SUPCG_KIND_BACKWARD, st, launch_backward(w->L(KT_BWD, st), BWD_G, w->bwin));
-    if (p->precondition && (rc = enqueue_precond_k(w, st))) return rc;
-    LAUNCH(SUPCG_KIND_VECTOR, st, launch_beta(w->L(KT_VEC, st)));
-    LAUNCH(SUPCG_KIND_VECTOR, st, launch_pupdate(w->L(KT_VEC, st)));
-    LAUNCH(SUPCG_KIND_VECTOR, st, launch_transpose(w->L(KT_TR, st), 1));
+    if (p->precondition) {
+        if ((rc = enqueue_precond_k(w, st))) return rc;
+    } else {
+        LAUNCH(SUPCG_KIND_VECTOR, st, launch_beta(w->L(KT_VEC, st)));
+    }
+    LAUNCH(SUPCG_KIND_VECTOR, st, launch_pupdate(w->L(KT_TR, st)));
     LAUNCH(SUPCG_KIND_FORWARD, st, launch_forward(w->L(KT_FWD, st), 1, FWD_NORM));
     LAUNCH(SUPCG_KIND_BACKWARD, st, launch_backward(w->L(KT_BWD, st), BWD_H, w->bwin));
     LAUNCH(SUPCG_KIND_VECTOR, st, launch_end_init(w->L(KT_VEC, st)));

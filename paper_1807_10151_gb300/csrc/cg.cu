@@ -10,24 +10,6 @@ constexpr int kVecPerThread = 4;
 constexpr int kVecPerBlock = kRedThreads * kVecPerThread;   // elements per block of the vector kernels
 
 // ------------------------------------------------------------ layout staging
-// 32 x 32 tile transpose through shared memory.  src [ny][sp] -> dst [nx][dp].
-__device__ __forceinline__ void transpose_tile(const float *src, int sp, float *dst, int dp, int ny, int nx,
-                                               int tile, float (*sh)[33])
-{
-    const int tiles_j = (nx + 31) / 32;
-    const int ti = tile / tiles_j, tj = tile - ti * tiles_j;
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 256 threads: 32 x 8
-    for (int r = ty; r < 32; r += 8) {
-        const int i = ti * 32 + r, j = tj * 32 + tx;
-        sh[r][tx] = (i < ny && j < nx) ? src[(size_t)i * sp + j] : 0.0f;
-    }
-    __syncthreads();
-    for (int r = ty; r < 32; r += 8) {
-        const int j = tj * 32 + r, i = ti * 32 + tx;
-        if (j < nx && i < ny) dst[(size_t)j * dp + i] = sh[tx][r];
-    }
-}
-
 __global__ void __launch_bounds__(256) k_transpose(const Prob *__restrict__ probs, const int *__restrict__ prefix,
                                                    int count, int which)
 {
@@ -138,9 +120,13 @@ int launch_store_out(const Launch &L, int which)
 // ------------------------------------------------------------ Algorithm 2 steps
 // Steps 3-4 (beta from z^T h computed earlier) and the g^T p half of step 6:
 //   p <- -z + beta p ;  partial g^T p.   In steps 2-7 of Algorithm 3 beta = 0.
-__global__ void __launch_bounds__(kRedThreads) k_pupdate(const Prob *__restrict__ probs,
-                                                         const int *__restrict__ prefix, int count)
+// p = -z + beta p (Algorithm 2 step 4; z = g when M = I) and g^T p (step 6), on
+// 32 x 32 tiles so that the same pass writes p^T for the projector; the last
+// block stores g^T p and beta.  Launched with the transpose's tile grid.
+__global__ void __launch_bounds__(256) k_pupdate(const Prob *__restrict__ probs, const int *__restrict__ prefix,
+                                                 int count)
 {
+    __shared__ float sh[32][33];
     __shared__ double red[40];
     __shared__ int flag;
     int local;
@@ -150,19 +136,31 @@ __global__ void __launch_bounds__(kRedThreads) k_pupdate(const Prob *__restrict_
     const double beta_d = P.sc->init ? 0.0 : P.sc->beta;
     const float beta = (float)beta_d;
     const float *z = P.precond ? P.z : P.g;   // M = I: z = g
-    const size_t tot = (size_t)P.ny * P.nxp;
+    const int tiles_j = (P.nx + 31) / 32;
+    const int ti = local / tiles_j, tj = local - ti * tiles_j;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     double s = 0.0;
-    for (size_t e = (size_t)local * kVecPerBlock + threadIdx.x; e < tot && e < (size_t)(local + 1) * kVecPerBlock;
-         e += kRedThreads) {
-        const float pn = __fmaf_rn(beta, P.p[e], -z[e]);
-        P.p[e] = pn;
-        s += (double)P.g[e] * (double)pn;
+    for (int r = ty; r < 32; r += 8) {
+        const int i = ti * 32 + r, j = tj * 32 + tx;
+        float pn = 0.0f;
+        if (i < P.ny && j < P.nx) {   // the padding of p stays 0
+            const size_t e = (size_t)i * P.nxp + j;
+            pn = __fmaf_rn(beta, P.p[e], -z[e]);
+            P.p[e] = pn;
+            s += (double)P.g[e] * (double)pn;
+        }
+        sh[r][tx] = pn;
     }
-    const double bs = block_sum<kRedThreads>(s, red);
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+        const int j = tj * 32 + r, i = ti * 32 + tx;
+        if (j < P.nx && i < P.ny) P.pT[(size_t)j * P.nyp + i] = sh[tx][r];
+    }
+    const double bs = block_sum<256>(s, red);
     if (threadIdx.x == 0) P.partial[local] = bs;
     const int nblk = prefix[pi + 1] - prefix[pi];
     if (last_block(&P.counter[1], nblk, &flag)) {
-        const double tot_s = block_sum_array<kRedThreads>(P.partial, nblk, red);
+        const double tot_s = block_sum_array<256>(P.partial, nblk, red);
         if (threadIdx.x == 0) {
             P.sc->gtp = tot_s;
             P.sc->beta = beta_d;
@@ -173,7 +171,7 @@ __global__ void __launch_bounds__(kRedThreads) k_pupdate(const Prob *__restrict_
 
 int launch_pupdate(const Launch &L)
 {
-    k_pupdate<<<L.blocks, kRedThreads, 0, L.st>>>(L.probs, L.prefix, L.count);
+    k_pupdate<<<L.blocks, 256, 0, L.st>>>(L.probs, L.prefix, L.count);
     SUPCG_CUDA_TRY(cudaGetLastError());
     return SUPCG_OK;
 }

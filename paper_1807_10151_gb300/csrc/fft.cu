@@ -140,12 +140,44 @@ __global__ void __launch_bounds__(256) k_fft_rows(const Prob *__restrict__ probs
             if (rb < ny) S[(size_t)rb * hx + k] = make_double2(0.5 * (c1.y + c2.y), 0.5 * (c2.x - c1.x));
         }
     } else {
+        // z, and inside a solve also z^T h for beta = z^T h / p^T h (Algorithm 2 step 3)
         const double scale = 1.0 / ((double)nx * (double)ny);
+        double s = 0.0;
         for (int e = threadIdx.x; e < np * nx; e += blockDim.x) {
             const int pr = e / nx, q = e - pr * nx;
             const int ra = 2 * (p0 + pr), rb = ra + 1;
-            P.z[(size_t)ra * P.nxp + q] = (float)(res[e].x * scale);
-            if (rb < ny) P.z[(size_t)rb * P.nxp + q] = (float)(res[e].y * scale);
+            const size_t ia = (size_t)ra * P.nxp + q, ib = (size_t)rb * P.nxp + q;
+            const float za = (float)(res[e].x * scale);
+            P.z[ia] = za;
+            if (!standalone) s += (double)za * (double)P.h[ia];
+            if (rb < ny) {
+                const float zb = (float)(res[e].y * scale);
+                P.z[ib] = zb;
+                if (!standalone) s += (double)zb * (double)P.h[ib];
+            }
+        }
+        if (!standalone) {
+            __shared__ double red[40];
+            __shared__ int flag;
+            const int pi = find_problem(prefix, count, blockIdx.x, &local);
+            const double bs = block_sum<256>(s, red);
+            if (threadIdx.x == 0) P.partial[local] = bs;
+            const int nblk = prefix[pi + 1] - prefix[pi];
+            if (last_block(&P.counter[2], nblk, &flag)) {
+                const double tot_s = block_sum_array<256>(P.partial, nblk, red);
+                if (threadIdx.x == 0) {
+                    Scal *sc = P.sc;
+                    sc->zth = tot_s;
+                    if (sc->init) {
+                        sc->beta = 0.0;
+                    } else {
+                        const double b = tot_s / sc->pth;
+                        if (!isfinite(b)) atomicExch(&sc->status, (int)SUPCG_ERR_BREAKDOWN);
+                        sc->beta = isfinite(b) ? b : 0.0;
+                    }
+                    P.counter[2] = 0;
+                }
+            }
         }
     }
 }

@@ -293,6 +293,25 @@ __device__ __forceinline__ bool coop_barrier(unsigned *bar, unsigned nblocks, in
     return *sh_flag;
 }
 
+// 32 x 32 tile transpose through shared memory (256 threads).  src [ny][sp] ->
+// dst [nx][dp].  A caller looping over tiles syncs before reusing sh.
+__device__ __forceinline__ void transpose_tile(const float *src, int sp, float *dst, int dp, int ny, int nx,
+                                               int tile, float (*sh)[33])
+{
+    const int tiles_j = (nx + 31) / 32;
+    const int ti = tile / tiles_j, tj = tile - ti * tiles_j;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 256 threads: 32 x 8
+    for (int r = ty; r < 32; r += 8) {
+        const int i = ti * 32 + r, j = tj * 32 + tx;
+        sh[r][tx] = (i < ny && j < nx) ? src[(size_t)i * sp + j] : 0.0f;
+    }
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+        const int j = tj * 32 + r, i = ti * 32 + tx;
+        if (j < nx && i < ny) dst[(size_t)j * dp + i] = sh[tx][r];
+    }
+}
+
 // ----------------------------------------------------------------- TMA / mbarrier
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {

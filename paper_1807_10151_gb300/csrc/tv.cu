@@ -335,6 +335,16 @@ __global__ void __launch_bounds__(kTvThreads) k_stv(const Prob *__restrict__ pro
         sc->tv_half = (K > 0) ? tv_last : tv_first;
         sc->snorm2 = sn;
     }
+    // x^T of x_{k+1/2} for the forward projector's column-walking views (after the last
+    // barrier every block sees the final x)
+    if (ok) {
+        __shared__ float sh[32][33];
+        const int tiles = ((ny + 31) / 32) * ((nx + 31) / 32);
+        for (int tile = local; tile < tiles; tile += nb) {
+            transpose_tile(x, ld, P.xT, P.nyp, ny, nx, tile, sh);
+            __syncthreads();
+        }
+    }
 }
 
 int stv_max_blocks_per_sm(int *out)
