@@ -382,7 +382,7 @@ static int ws_create(const std::vector<supcg_geometry> &gs, Workspace **out)
     for (int c = 0; c < w->count; ++c) {
         const supcg_geometry g = gs[c];
         nb[KT_FWD][c] = g->V * g->ntu;
-        nb[KT_BWD][c] = ((g->ny + kBwdTileI - 1) / kBwdTileI) * ((g->nx + kBwdTileJ - 1) / kBwdTileJ);
+        nb[KT_BWD][c] = kBwdHalves * ((g->ny + kBwdTileI - 1) / kBwdTileI) * ((g->nx + kBwdTileJ - 1) / kBwdTileJ);
         nb[KT_VEC][c] = (int)(((long long)g->ny * g->nxp + 1023) / 1024);
         nb[KT_TR][c] = ((g->ny + 31) / 32) * ((g->nx + 31) / 32);
         // FFT: enough blocks to fill the device, each a few row pairs / stored columns
@@ -438,21 +438,23 @@ static int ws_create(const std::vector<supcg_geometry> &gs, Workspace **out)
         auto al = [](size_t b) { return (b + 255) / 256 * 256; };
         const size_t sizes[] = {img * 4, imgT * 4, img * 4, imgT * 4, img * 4, img * 4, img * 4, img * 4,
                                 sino * 4, sino * 4, sino * 4, (size_t)g->ny * g->nx * 16, sizeof(Scal),
-                                npart * 8, 16 * 4, 4 * 4, (size_t)(g->ny / 2 + 1) * (g->nx / 2 + 1) * 8};
+                                npart * 8, 16 * 4, 4 * 4, (size_t)(g->ny / 2 + 1) * (g->nx / 2 + 1) * 8,
+                                (size_t)kBwdHalves * img * 8, (size_t)nb[KT_BWD][c] * 4};
         size_t total = 0;
         for (size_t s : sizes) total += al(s);
         char *base = nullptr;
         if (cudaMalloc(&base, total) != cudaSuccess) { delete w; return SUPCG_ERR_NOMEM; }
         w->allocs.push_back(base);
         if (cudaMemset(base, 0, total) != cudaSuccess) { delete w; return SUPCG_ERR_CUDA; }
-        char *ptrs[17];
+        char *ptrs[19];
         size_t off = 0;
-        for (int k = 0; k < 17; ++k) { ptrs[k] = base + off; off += al(sizes[k]); }
+        for (int k = 0; k < 19; ++k) { ptrs[k] = base + off; off += al(sizes[k]); }
         P.x = (float *)ptrs[0]; P.xT = (float *)ptrs[1]; P.p = (float *)ptrs[2]; P.pT = (float *)ptrs[3];
         P.g = (float *)ptrs[4]; P.z = (float *)ptrs[5]; P.h = (float *)ptrs[6]; P.tbar = (float *)ptrs[7];
         P.r = (float *)ptrs[8]; P.q = (float *)ptrs[9]; P.bpad = (float *)ptrs[10];
         P.C = (double2 *)ptrs[11]; P.sc = (Scal *)ptrs[12]; P.partial = (double *)ptrs[13];
         P.counter = (unsigned *)ptrs[14]; P.bar = (unsigned *)ptrs[15]; P.Dtab = (double *)ptrs[16];
+        P.bsplit = (double *)ptrs[17]; P.tilecnt = (unsigned *)ptrs[18];
         P.nx = g->nx; P.ny = g->ny; P.V = g->V; P.U = g->U;
         P.nxp = g->nxp; P.nyp = g->nyp; P.Up = g->Up;
         P.BU = g->BU; P.BW = g->BW; P.ntu = g->ntu; P.nA = g->nA; P.nB = g->nB;

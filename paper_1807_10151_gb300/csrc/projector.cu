@@ -415,7 +415,7 @@ __device__ __forceinline__ void bwd_view_x2(const ViewP &vp, float pb0, const ui
     }
 }
 
-__global__ void __launch_bounds__(kBwdThreads, 4) k_backward(const Prob *__restrict__ probs,
+__global__ void __launch_bounds__(kBwdThreads, 3) k_backward(const Prob *__restrict__ probs,
                                                           const int *__restrict__ prefix, int count, int mode)
 {
     extern __shared__ __align__(16) float win_raw[];   // [2][kBwdViewChunk][bwin]
@@ -432,7 +432,8 @@ __global__ void __launch_bounds__(kBwdThreads, 4) k_backward(const Prob *__restr
 
     const int bwin = P.bwin;
     const int tiles_j = (P.nx + kBwdTileJ - 1) / kBwdTileJ;
-    const int ti = local / tiles_j, tj = local - ti * tiles_j;
+    const int tile = local / kBwdHalves, half = local - tile * kBwdHalves;   // this block's half of the views
+    const int ti = tile / tiles_j, tj = tile - ti * tiles_j;
     const int i0 = ti * kBwdTileI, j0 = tj * kBwdTileJ;
     const int t = threadIdx.x;
     const int grp = t / kBwdGroup, tg = t - grp * kBwdGroup;   // group grp takes views vv = grp (mod kBwdSplit)
@@ -515,12 +516,14 @@ __global__ void __launch_bounds__(kBwdThreads, 4) k_backward(const Prob *__restr
         }
     };
 
-    stage(0);
+    const int per_half = (nchunks + kBwdHalves - 1) / kBwdHalves;
+    const int c_begin = min(nchunks, half * per_half), c_end = min(nchunks, c_begin + per_half);
+    if (c_begin < c_end) stage(c_begin);
     __syncthreads();
     int bad = 0;
-    for (int c = 0; c < nchunks; ++c) {
+    for (int c = c_begin; c < c_end; ++c) {
         const int buf = c & 1;
-        if (c + 1 < nchunks) stage(c + 1);   // other buffer; its previous readers finished at the last barrier
+        if (c + 1 < c_end) stage(c + 1);   // other buffer; its previous readers finished at the last barrier
         const int nv = min(kBwdViewChunk, P.V - c * kBwdViewChunk);
         const float *wb = win_raw + (size_t)buf * kBwdViewChunk * bwin;
         // groups of four of this thread group's views, then one Kahan-compensated fold
@@ -593,14 +596,30 @@ __global__ void __launch_bounds__(kBwdThreads, 4) k_backward(const Prob *__restr
 #pragma unroll
         for (int e = 0; e < kBwdPixPerThread; ++e) comb[e * kBwdGroup + tg] = acc[e];
     __syncthreads();
+    // this half's sums; the tile's second half to finish adds the two in half order
+    const size_t img = (size_t)P.ny * P.nxp;
+    if (grp == 0)
+#pragma unroll
+        for (int e = 0; e < kBwdPixPerThread; ++e) {
+            const int i = i0 + ly + kBwdRowStep * e;
+            if (i < P.ny && j < P.nx) P.bsplit[half * img + (size_t)i * P.nxp + j] = acc[e] + comb[e * kBwdGroup + tg];
+        }
+    if (t == 0 && bad_sh && P.sc) atomicExch(&P.sc->status, (int)SUPCG_ERR_UNSUPPORTED);
+    __shared__ int last_sh;
+    if (!last_block(&P.tilecnt[tile], kBwdHalves, &last_sh)) return;
     float *out = (mode == BWD_G) ? P.g : (mode == BWD_H ? P.h : P.g);
     if (grp == 0)
 #pragma unroll
         for (int e = 0; e < kBwdPixPerThread; ++e) {
             const int i = i0 + ly + kBwdRowStep * e;
-            if (i < P.ny && j < P.nx) out[(size_t)i * P.nxp + j] = (float)(acc[e] + comb[e * kBwdGroup + tg]);
+            if (i < P.ny && j < P.nx) {
+                const size_t o = (size_t)i * P.nxp + j;
+                double v = 0.0;
+                for (int h = 0; h < kBwdHalves; ++h) v += *(volatile const double *)(P.bsplit + h * img + o);
+                out[o] = (float)v;
+            }
         }
-    if (t == 0 && bad_sh && P.sc) atomicExch(&P.sc->status, (int)SUPCG_ERR_UNSUPPORTED);
+    if (t == 0) P.tilecnt[tile] = 0;   // ready for the next launch
 }
 
 int launch_backward(const Launch &L, int mode, int bwin)
