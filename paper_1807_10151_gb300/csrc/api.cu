@@ -382,7 +382,7 @@ static int ws_create(const std::vector<supcg_geometry> &gs, Workspace **out)
     for (int c = 0; c < w->count; ++c) {
         const supcg_geometry g = gs[c];
         nb[KT_FWD][c] = g->V * g->ntu;
-        nb[KT_BWD][c] = kBwdHalves * ((g->ny + kBwdTileI - 1) / kBwdTileI) * ((g->nx + kBwdTileJ - 1) / kBwdTileJ);
+        nb[KT_BWD][c] = kBwdViewParts * ((g->ny + kBwdTileI - 1) / kBwdTileI) * ((g->nx + kBwdTileJ - 1) / kBwdTileJ);
         nb[KT_VEC][c] = (int)(((long long)g->ny * g->nxp + 1023) / 1024);
         nb[KT_TR][c] = ((g->ny + 31) / 32) * ((g->nx + 31) / 32);
         // FFT: enough blocks to fill the device, each a few row pairs / stored columns
@@ -439,7 +439,7 @@ static int ws_create(const std::vector<supcg_geometry> &gs, Workspace **out)
         const size_t sizes[] = {img * 4, imgT * 4, img * 4, imgT * 4, img * 4, img * 4, img * 4, img * 4,
                                 sino * 4, sino * 4, sino * 4, (size_t)g->ny * g->nx * 16, sizeof(Scal),
                                 npart * 8, 16 * 4, 4 * 4, (size_t)(g->ny / 2 + 1) * (g->nx / 2 + 1) * 8,
-                                (size_t)kBwdHalves * img * 8, (size_t)nb[KT_BWD][c] * 4};
+                                (size_t)kBwdViewParts * img * 8, (size_t)nb[KT_BWD][c] * 4};
         size_t total = 0;
         for (size_t s : sizes) total += al(s);
         char *base = nullptr;

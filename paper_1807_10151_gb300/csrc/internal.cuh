@@ -17,7 +17,7 @@ constexpr int kMaxStages = 24;       // FFT stages (radices) per length
 constexpr int kMaxRadix = 64;        // largest prime factor handled by the generic butterfly
 constexpr int kRowsPerChunk = 16;    // forward projector: image rows staged per TMA box
 constexpr int kBwdTileI = 32;        // backprojector pixel tile (rows)
-constexpr int kBwdHalves = 2;        // backprojector: blocks per tile, each taking half of the view chunks
+constexpr int kBwdViewParts = 4;     // backprojector: blocks per tile, each taking a quarter of the view chunks
 constexpr int kBwdTileJ = 32;        // backprojector pixel tile (columns)
 constexpr int kBwdViewChunk = 32;    // backprojector: views staged per shared-memory chunk
 constexpr int kRedThreads = 256;     // block size of the reduction / vector kernels
@@ -186,8 +186,8 @@ struct Prob {
     float *r, *q, *bpad;
     double2 *C;            // FFT scratch [ny][nx] (FP64 complex)
     double *Dtab;          // preconditioner diagonal h(w_r) at (min(k1, ny-k1), min(k2, nx-k2)): [ny/2+1][nx/2+1]
-    double *bsplit;        // backprojector: each view half's pixel sums [kBwdHalves][ny][nxp]
-    unsigned *tilecnt;     // backprojector: halves finished per tile (reset by the last one)
+    double *bsplit;        // backprojector: each view part's pixel sums [kBwdViewParts][ny][nxp]
+    unsigned *tilecnt;     // backprojector: parts finished per tile (reset by the last one)
     Scal *sc;
     double *partial;       // reduction partials (>= 2 * max blocks per kernel)
     unsigned *counter;     // last-block tickets [8]

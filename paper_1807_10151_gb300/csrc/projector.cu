@@ -2,19 +2,22 @@
 // Eq. (2.2): normal equations R^T R x = R^T b).
 //
 // Forward (ray-driven, gather over pixels).  A block owns one view and up to
-// 128 consecutive bins.  Views are split in two classes: class A
-// (|cos| >= |sin|) walks image rows, class B walks image columns, and class B
-// reads the transposed image x^T so that both classes walk contiguous rows of
-// the array they read.  Chunks of 32 rows x BW columns covering the block's
-// rays are staged in shared memory by 2-D TMA loads (double buffered, one
-// mbarrier per buffer).  For every row a ray can only cross the three columns
-// nearest to its centre; each is weighted by the shared trapezoid weight().
+// 128 consecutive bins, one ray per thread.  Views are split in two classes:
+// class A (|cos| >= |sin|) walks image rows, class B walks image columns, and
+// class B reads the transposed image x^T so that both classes walk contiguous
+// rows of the array they read.  Each warp stages chunks of kRowsPerChunk rows
+// x BW columns covering its 32 rays in shared memory by 2-D TMA loads (its own
+// double buffer, one mbarrier per buffer), and only the rows its rays can
+// meet.  For every row a ray can only cross the two (three near the diagonal)
+// columns nearest to its centre; each is weighted by the shared trapezoid.
 //
-// Backward (pixel-driven, gather over bins, no atomics).  A block owns a
-// 16 x 32 pixel tile; for chunks of 32 views the bins that the tile projects
+// Backward (pixel-driven, gather over bins, no atomics).  A tile of 32 x 32
+// pixels is shared by kBwdViewParts blocks, each taking a contiguous part of
+// the view chunks; for chunks of 32 views the bins that the tile projects
 // onto are staged in shared memory with 16-byte vector loads; every pixel
-// gathers the three bins nearest to its projected centre with the same
-// weight() evaluated on the same FP32 operands as the forward kernel.
+// gathers the two (three) bins nearest to its projected centre with the same
+// weight evaluated on the same FP32 operands as the forward kernel.  The last
+// block of a tile to finish adds the parts' FP64 sums in part order.
 #include "internal.cuh"
 
 namespace supcg {
@@ -432,7 +435,7 @@ __global__ void __launch_bounds__(kBwdThreads, 3) k_backward(const Prob *__restr
 
     const int bwin = P.bwin;
     const int tiles_j = (P.nx + kBwdTileJ - 1) / kBwdTileJ;
-    const int tile = local / kBwdHalves, half = local - tile * kBwdHalves;   // this block's half of the views
+    const int tile = local / kBwdViewParts, vpart = local - tile * kBwdViewParts;   // this block's part of the views
     const int ti = tile / tiles_j, tj = tile - ti * tiles_j;
     const int i0 = ti * kBwdTileI, j0 = tj * kBwdTileJ;
     const int t = threadIdx.x;
@@ -516,8 +519,8 @@ __global__ void __launch_bounds__(kBwdThreads, 3) k_backward(const Prob *__restr
         }
     };
 
-    const int per_half = (nchunks + kBwdHalves - 1) / kBwdHalves;
-    const int c_begin = min(nchunks, half * per_half), c_end = min(nchunks, c_begin + per_half);
+    const int per_part = (nchunks + kBwdViewParts - 1) / kBwdViewParts;
+    const int c_begin = min(nchunks, vpart * per_part), c_end = min(nchunks, c_begin + per_part);
     if (c_begin < c_end) stage(c_begin);
     __syncthreads();
     int bad = 0;
@@ -596,17 +599,17 @@ __global__ void __launch_bounds__(kBwdThreads, 3) k_backward(const Prob *__restr
 #pragma unroll
         for (int e = 0; e < kBwdPixPerThread; ++e) comb[e * kBwdGroup + tg] = acc[e];
     __syncthreads();
-    // this half's sums; the tile's second half to finish adds the two in half order
+    // this part's sums; the tile's last part to finish adds them in part order
     const size_t img = (size_t)P.ny * P.nxp;
     if (grp == 0)
 #pragma unroll
         for (int e = 0; e < kBwdPixPerThread; ++e) {
             const int i = i0 + ly + kBwdRowStep * e;
-            if (i < P.ny && j < P.nx) P.bsplit[half * img + (size_t)i * P.nxp + j] = acc[e] + comb[e * kBwdGroup + tg];
+            if (i < P.ny && j < P.nx) P.bsplit[vpart * img + (size_t)i * P.nxp + j] = acc[e] + comb[e * kBwdGroup + tg];
         }
     if (t == 0 && bad_sh && P.sc) atomicExch(&P.sc->status, (int)SUPCG_ERR_UNSUPPORTED);
     __shared__ int last_sh;
-    if (!last_block(&P.tilecnt[tile], kBwdHalves, &last_sh)) return;
+    if (!last_block(&P.tilecnt[tile], kBwdViewParts, &last_sh)) return;
     float *out = (mode == BWD_G) ? P.g : (mode == BWD_H ? P.h : P.g);
     if (grp == 0)
 #pragma unroll
@@ -615,7 +618,7 @@ __global__ void __launch_bounds__(kBwdThreads, 3) k_backward(const Prob *__restr
             if (i < P.ny && j < P.nx) {
                 const size_t o = (size_t)i * P.nxp + j;
                 double v = 0.0;
-                for (int h = 0; h < kBwdHalves; ++h) v += *(volatile const double *)(P.bsplit + h * img + o);
+                for (int h = 0; h < kBwdViewParts; ++h) v += *(volatile const double *)(P.bsplit + h * img + o);
                 out[o] = (float)v;
             }
         }
