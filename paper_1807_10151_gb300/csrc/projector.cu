@@ -22,6 +22,10 @@
 
 namespace supcg {
 
+// The kernels' dynamic shared memory, indexed by 32-bit float offsets so that
+// operand loads are plain shared-memory loads with 32-bit addresses.
+extern __shared__ __align__(128) float proj_dyn[];
+
 // ============================================================ forward
 // Inner loop over the rows [o0, o0 + rows) of one staged box.  A ray meets a
 // row in the inner indices within hwq (half-width + margin) of its centre:
@@ -32,7 +36,7 @@ namespace supcg {
 // to a few units in the last place of FP32 however many rows it crosses.
 template <bool CLASS_B, bool AXIS, int NC, bool CHECKED>
 __device__ __forceinline__ void fwd_rows(const Prob &P, const ViewP &vp, float tau_hi, float qm, int o0, int rb,
-                                         int re, int qs, const float *patch, int *bad, float &sum, float &comp)
+                                         int re, int qs, int pbase, int *bad, float &sum, float &comp)
 {
     const int BW = P.BW;
     // outer coordinate of row o0 + rb (pixel units) and its change per row
@@ -47,7 +51,7 @@ __device__ __forceinline__ void fwd_rows(const Prob &P, const ViewP &vp, float t
     const float dI = CLASS_B ? -1.0f : 1.0f;
     const float E = vp.E, Sn = vp.Sn, ESn = vp.ESn;
     const float qh = __fsub_rn(qm, vp.hwq);
-    const float *prow = patch - qs;
+    const int prow = pbase - qs;   // proj_dyn index of inner index 0 of the box's first row
     float rs = 0.0f;   // FP32 sum of up to 8 rows, then folded into (sum, comp)
     // without checks the first two candidates run as packed f32x2 steps (lane for lane the
     // scalar IEEE operations): rs2 holds their separate sums, rs the third candidate's
@@ -63,7 +67,7 @@ __device__ __forceinline__ void fwd_rows(const Prob &P, const ViewP &vp, float t
                 *bad = 1;
                 q0 = min(max(idx, 0), BW - NC) + qs;
             }
-            const float *pv = prow + r * BW + q0;
+            const float *pv = proj_dyn + (prow + r * BW + q0);
             const float rbig = __fmaf_rn(-hi_o, Oc, tau_hi);            // exact
             const float rsmall = __fmaf_rn(lo_o, Oc, P.uc_lo);
             Oc = __fadd_rn(Oc, dO);
@@ -77,7 +81,7 @@ __device__ __forceinline__ void fwd_rows(const Prob &P, const ViewP &vp, float t
                 rs = __fmaf_rn(weight_unit(ad, E, Sn, ESn, AXIS), pv[k], rs);
             }
         } else {
-            const float *pv = prow + r * BW + q0;
+            const int pv = prow + r * BW + q0;
             const uint64_t rbig2 = fma2_rn(hio2, Oc2, tau2);             // exact
             const uint64_t rsmall2 = fma2_rn(loo2, Oc2, ucl2);
             Oc2 = add2_rn(Oc2, dO2);
@@ -89,7 +93,7 @@ __device__ __forceinline__ void fwd_rows(const Prob &P, const ViewP &vp, float t
             float d0, d1;
             upk2(sub2_rn(big2, fma2_rn(loi2, I2, rsmall2)), d0, d1);
             const uint64_t w2 = pk2(weight_unit(fabsf(d0), E, Sn, ESn, AXIS), weight_unit(fabsf(d1), E, Sn, ESn, AXIS));
-            rs2 = fma2_rn(w2, pk2(pv[0], pv[1]), rs2);
+            rs2 = fma2_rn(w2, pk2(proj_dyn[pv], proj_dyn[pv + 1]), rs2);
             if constexpr (NC == 3) {
                 float rbig, rbig_b, rsmall, rsmall_b;
                 upk2(rbig2, rbig, rbig_b);
@@ -97,7 +101,7 @@ __device__ __forceinline__ void fwd_rows(const Prob &P, const ViewP &vp, float t
                 const float I = __fadd_rn(I1, dI);
                 const float big = __fmaf_rn(-hi_i, I, rbig);
                 const float ad = fabsf(__fsub_rn(big, __fmaf_rn(lo_i, I, rsmall)));
-                rs = __fmaf_rn(weight_unit(ad, E, Sn, ESn, AXIS), pv[2], rs);
+                rs = __fmaf_rn(weight_unit(ad, E, Sn, ESn, AXIS), proj_dyn[pv + 2], rs);
             }
         }
     };
@@ -164,7 +168,7 @@ __device__ __forceinline__ void fwd_row_range(const ViewP &vp, float base, int n
 // wait for one another.  The warp walks only the chunks holding rows that one
 // of its rays can meet, and within them only those rows.
 template <bool CLASS_B, bool AXIS, int NC>
-__device__ __forceinline__ double fwd_ray(const Prob &P, const ViewP &vp, const CUtensorMap *tm, float *patch0,
+__device__ __forceinline__ double fwd_ray(const Prob &P, const ViewP &vp, const CUtensorMap *tm, int patch0,
                                           uint64_t *bars, int n_outer, int n_inner, int u, int u_last, float tf,
                                           float tl, int *bad, int *timed_out)
 {
@@ -185,7 +189,7 @@ __device__ __forceinline__ double fwd_ray(const Prob &P, const ViewP &vp, const 
         for (int ci = 0; ci < 2 && ci < nch; ++ci) {
             const int c = c_first + ci;
             mbar_expect_tx(&bars[ci], box_elems * 4);
-            tma_load_2d(patch0 + ci * box_elems, tm, fwd_box_start(vp, tf, tl, c * RC), c * RC, &bars[ci]);
+            tma_load_2d(proj_dyn + patch0 + ci * box_elems, tm, fwd_box_start(vp, tf, tl, c * RC), c * RC, &bars[ci]);
         }
     }
     for (int ci = 0; ci < nch; ++ci) {
@@ -222,7 +226,7 @@ __device__ __forceinline__ double fwd_ray(const Prob &P, const ViewP &vp, const 
         __syncwarp();
         if (lane == 0 && ci + 2 < nch) {
             mbar_expect_tx(&bars[buf], box_elems * 4);
-            tma_load_2d(patch0 + buf * box_elems, tm, fwd_box_start(vp, tf, tl, (c + 2) * RC), (c + 2) * RC,
+            tma_load_2d(proj_dyn + patch0 + buf * box_elems, tm, fwd_box_start(vp, tf, tl, (c + 2) * RC), (c + 2) * RC,
                         &bars[buf]);
         }
     }
@@ -232,7 +236,7 @@ __device__ __forceinline__ double fwd_ray(const Prob &P, const ViewP &vp, const 
 __global__ void __launch_bounds__(128, 6) k_forward(const Prob *__restrict__ probs, const int *__restrict__ prefix,
                                                  int count, int which, int mode)
 {
-    extern __shared__ __align__(128) unsigned char smem_raw[];   // [warp][2][kRowsPerChunk][BW]
+    // proj_dyn: [warp][2][kRowsPerChunk][BW]
     __shared__ __align__(8) uint64_t bars[2 * 4];                 // two per warp
     __shared__ double red[40];
     __shared__ int flag;
@@ -251,7 +255,7 @@ __global__ void __launch_bounds__(128, 6) k_forward(const Prob *__restrict__ pro
     const int n_outer = classB ? P.nx : P.ny, n_inner = classB ? P.ny : P.nx;
     const CUtensorMap *tm = &P.tm[which * 2 + (classB ? 1 : 0)];
     const int t = threadIdx.x, warp = t >> 5;
-    float *patch0 = reinterpret_cast<float *>(smem_raw) + warp * 2 * kRowsPerChunk * P.BW;
+    const int patch0 = warp * 2 * kRowsPerChunk * P.BW;   // this warp's two boxes in proj_dyn
     uint64_t *wbars = bars + 2 * warp;
 
     const int u_first = tile * P.BU;
@@ -359,7 +363,7 @@ constexpr int kBwdRowStep = kBwdGroup / kBwdTileJ;                       // 4
 // Per pixel and view: the bins within hwu (half-width + margin) of the pixel's
 // projected centre, two of them (three when the bins are finer than pixels).
 template <bool AXIS, int NC, bool CHECKED>
-__device__ __forceinline__ void bwd_view(const ViewP &vp, float pb0, const float *sm, const float *w_row, int lo,
+__device__ __forceinline__ void bwd_view(const ViewP &vp, float pb0, const float *sm, int w_row, int lo,
                                          int bwin, float *t, int *bad)
 {
     const float E = vp.E, Sn = vp.Sn, ESn = vp.ESn;
@@ -379,11 +383,11 @@ __device__ __forceinline__ void bwd_view(const ViewP &vp, float pb0, const float
         }
         const float u0f = CHECKED ? __int2float_rn(u0) : magic_float(uc);
         const float big0 = __fadd_rn(u0f, pb);   // exact, as are big0 + 1 and big0 + 2
-        const float *wv = w_row + (u0 - lo);
+        const int wv = w_row + (u0 - lo);
 #pragma unroll
         for (int k = 0; k < NC; ++k) {
             const float ad = fabsf(__fsub_rn(__fadd_rn(big0, (float)k), sm[e]));
-            t[e] = __fmaf_rn(weight_unit(ad, E, Sn, ESn, AXIS), wv[k], t[e]);   // wv holds P * y
+            t[e] = __fmaf_rn(weight_unit(ad, E, Sn, ESn, AXIS), proj_dyn[wv + k], t[e]);   // the window holds P * y
         }
     }
 }
@@ -392,7 +396,7 @@ __device__ __forceinline__ void bwd_view(const ViewP &vp, float pb0, const float
 // f32x2 instruction; only for windows that hold every candidate (no checks).
 // sm2[h] = (small of pixel 2h, of pixel 2h + 1); t2[h] the pairs' running sums.
 template <bool AXIS, int NC>
-__device__ __forceinline__ void bwd_view_x2(const ViewP &vp, float pb0, const uint64_t *sm2, const float *w_row,
+__device__ __forceinline__ void bwd_view_x2(const ViewP &vp, float pb0, const uint64_t *sm2, int w_row,
                                             int lo, uint64_t *t2)
 {
     const float E = vp.E, Sn = vp.Sn, ESn = vp.ESn;
@@ -405,7 +409,7 @@ __device__ __forceinline__ void bwd_view_x2(const ViewP &vp, float pb0, const ui
         const uint64_t uc = add2_rp(sub2_rn(sub2_rn(sm2[h], pb), hwu2), mag2);
         float uca, ucb;
         upk2(uc, uca, ucb);
-        const float *wa = w_row + (magic_int(uca) - lo), *wb = w_row + (magic_int(ucb) - lo);
+        const int wa = w_row + (magic_int(uca) - lo), wb = w_row + (magic_int(ucb) - lo);
         const uint64_t big0 = add2_rn(sub2_rn(uc, mag2), pb);              // exact, as are big0 + 1, + 2
 #pragma unroll
         for (int k = 0; k < NC; ++k) {
@@ -413,7 +417,7 @@ __device__ __forceinline__ void bwd_view_x2(const ViewP &vp, float pb0, const ui
             float da, db;
             upk2(sub2_rn(bk, sm2[h]), da, db);
             const uint64_t w = pk2(weight_unit(fabsf(da), E, Sn, ESn, AXIS), weight_unit(fabsf(db), E, Sn, ESn, AXIS));
-            t2[h] = fma2_rn(w, pk2(wa[k], wb[k]), t2[h]);                 // w_row holds P * y
+            t2[h] = fma2_rn(w, pk2(proj_dyn[wa + k], proj_dyn[wb + k]), t2[h]);   // the window holds P * y
         }
     }
 }
@@ -421,7 +425,7 @@ __device__ __forceinline__ void bwd_view_x2(const ViewP &vp, float pb0, const ui
 __global__ void __launch_bounds__(kBwdThreads, 3) k_backward(const Prob *__restrict__ probs,
                                                           const int *__restrict__ prefix, int count, int mode)
 {
-    extern __shared__ __align__(16) float win_raw[];   // [2][kBwdViewChunk][bwin]
+    // proj_dyn: [2][kBwdViewChunk][bwin] sinogram windows
     __shared__ ViewP vsh[2][kBwdViewChunk];
     __shared__ int ulo_sh[2][kBwdViewChunk];
     __shared__ int kind_sh[2][kBwdViewChunk];   // variant: axis / three bins / two bins, + 3 if a window check is needed
@@ -501,7 +505,7 @@ __global__ void __launch_bounds__(kBwdThreads, 3) k_backward(const Prob *__restr
         }
         __syncthreads();
         const int V4 = bwin >> 2;
-        float *wb = win_raw + (size_t)buf * kBwdViewChunk * bwin;
+        float *wb = proj_dyn + buf * kBwdViewChunk * bwin;
         for (int e = t; e < kBwdViewChunk * V4; e += kBwdThreads) {
             const int vv = e / V4, k4 = e - vv * V4;
             const int v = v0 + vv;
@@ -528,7 +532,7 @@ __global__ void __launch_bounds__(kBwdThreads, 3) k_backward(const Prob *__restr
         const int buf = c & 1;
         if (c + 1 < c_end) stage(c + 1);   // other buffer; its previous readers finished at the last barrier
         const int nv = min(kBwdViewChunk, P.V - c * kBwdViewChunk);
-        const float *wb = win_raw + (size_t)buf * kBwdViewChunk * bwin;
+        const int wb = buf * kBwdViewChunk * bwin;
         // groups of four of this thread group's views, then one Kahan-compensated fold
         for (int g0 = grp; g0 < nv; g0 += 4 * kBwdSplit) {
 #pragma unroll
@@ -536,7 +540,7 @@ __global__ void __launch_bounds__(kBwdThreads, 3) k_backward(const Prob *__restr
                 const int vv = g0 + q * kBwdSplit;
                 if (vv < nv) {
                     const ViewP vp = vsh[buf][vv];
-                    const float *wr = wb + vv * bwin;
+                    const int wr = wb + vv * bwin;
                     const int lo = ulo_sh[buf][vv];
                     const float pb0 = __fmaf_rn(-vp.cu_hi, X, __fmaf_rn(-vp.su_hi, Y[0], -P.uc_hi));
                     // small = uc_lo + cu_lo X + su_lo Y in the view class's order (delta_small), in pairs
