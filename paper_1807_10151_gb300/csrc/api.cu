@@ -145,13 +145,13 @@ struct supcg_geometry_s {
     std::vector<supcg_geometry> batch_key;
 };
 
-// Forward projector box width: the inner indices that one warp's 32 rays can
+// Forward projector box width: the inner indices that one warp's 64 rays can
 // touch over one chunk of rows, plus slack, rounded up to a multiple of 4 floats.
 static int fwd_box_width(const supcg_geometry_s *g)
 {
     double span = 0.0;
     for (const ViewP &vp : g->views)
-        span = std::max(span, fabs((double)vp.a_tau) * 31.0 + fabs((double)vp.b_o) * (kRowsPerChunk - 1));
+        span = std::max(span, fabs((double)vp.a_tau) * 63.0 + fabs((double)vp.b_o) * (kRowsPerChunk - 1));
     return round_up((int)ceil(span + 11.0), 4);
 }
 

@@ -26,6 +26,8 @@ namespace supcg {
 // operand loads are plain shared-memory loads with 32-bit addresses.
 extern __shared__ __align__(128) float proj_dyn[];
 
+static_assert(kRowsPerChunk % 8 == 0, "chunks start at multiples of the 8-row fold groups");
+
 // ============================================================ forward
 // Inner loop over the rows [o0, o0 + rows) of one staged box.  A ray meets a
 // row in the inner indices within hwq (half-width + margin) of its centre:
@@ -52,81 +54,133 @@ __device__ __forceinline__ void fwd_rows(const Prob &P, const ViewP &vp, float t
     const float E = vp.E, Sn = vp.Sn, ESn = vp.ESn;
     const float qh = __fsub_rn(qm, vp.hwq);
     const int prow = pbase - qs;   // proj_dyn index of inner index 0 of the box's first row
-    float rs = 0.0f;   // FP32 sum of up to 8 rows, then folded into (sum, comp)
-    // without checks the first two candidates run as packed f32x2 steps (lane for lane the
-    // scalar IEEE operations): rs2 holds their separate sums, rs the third candidate's
-    uint64_t rs2 = pk2(0.0f, 0.0f), Oc2 = pk2(Oc, Oc);
-    const uint64_t hio2 = pk2(-hi_o, -hi_o), loo2 = pk2(lo_o, lo_o), tau2 = pk2(tau_hi, tau_hi);
-    const uint64_t ucl2 = pk2(P.uc_lo, P.uc_lo), hii2 = pk2(-hi_i, -hi_i), loi2 = pk2(lo_i, lo_i), dO2 = pk2(dO, dO);
+    float rs = 0.0f;   // FP32 sum of the rows of one 8-row group, then folded into (sum, comp)
     auto row = [&](int r, float rf) {
         const float qc = ceil_magic(__fmaf_rn(rf, vp.b_o, qh));
         int q0 = magic_int(qc);
-        if constexpr (CHECKED) {
+        if (CHECKED) {
             const int idx = q0 - qs;
             if (idx < 0 || idx > BW - NC) {   // outside the staged box: never for a valid box (host-checked)
                 *bad = 1;
                 q0 = min(max(idx, 0), BW - NC) + qs;
             }
-            const float *pv = proj_dyn + (prow + r * BW + q0);
-            const float rbig = __fmaf_rn(-hi_o, Oc, tau_hi);            // exact
-            const float rsmall = __fmaf_rn(lo_o, Oc, P.uc_lo);
-            Oc = __fadd_rn(Oc, dO);
-            const float q0f = __int2float_rn(q0);                      // the clamped index
-            const float I0 = CLASS_B ? __fsub_rn(c_in, q0f) : __fsub_rn(q0f, c_in);
+        }
+        const float *pv = proj_dyn + (prow + r * BW + q0);
+        const float rbig = __fmaf_rn(-hi_o, Oc, tau_hi);            // exact
+        const float rsmall = __fmaf_rn(lo_o, Oc, P.uc_lo);
+        Oc = __fadd_rn(Oc, dO);
+        const float q0f = CHECKED ? __int2float_rn(q0) : magic_float(qc);   // the clamped index when checked
+        const float I0 = CLASS_B ? __fsub_rn(c_in, q0f) : __fsub_rn(q0f, c_in);
+        float I = I0;
 #pragma unroll
-            for (int k = 0; k < NC; ++k) {
-                const float I = __fadd_rn(I0, k * dI);                    // exact half-integer
-                const float big = __fmaf_rn(-hi_i, I, rbig);              // exact
-                const float ad = fabsf(__fsub_rn(big, __fmaf_rn(lo_i, I, rsmall)));
-                rs = __fmaf_rn(weight_unit(ad, E, Sn, ESn, AXIS), pv[k], rs);
-            }
-        } else {
-            const int pv = prow + r * BW + q0;
-            const uint64_t rbig2 = fma2_rn(hio2, Oc2, tau2);             // exact
-            const uint64_t rsmall2 = fma2_rn(loo2, Oc2, ucl2);
-            Oc2 = add2_rn(Oc2, dO2);
-            const float q0f = magic_float(qc);
-            const float I0 = CLASS_B ? __fsub_rn(c_in, q0f) : __fsub_rn(q0f, c_in);
-            const float I1 = __fadd_rn(I0, dI);                           // exact half-integers
-            const uint64_t I2 = pk2(I0, I1);
-            const uint64_t big2 = fma2_rn(hii2, I2, rbig2);              // exact
-            float d0, d1;
-            upk2(sub2_rn(big2, fma2_rn(loi2, I2, rsmall2)), d0, d1);
-            const uint64_t w2 = pk2(weight_unit(fabsf(d0), E, Sn, ESn, AXIS), weight_unit(fabsf(d1), E, Sn, ESn, AXIS));
-            rs2 = fma2_rn(w2, pk2(proj_dyn[pv], proj_dyn[pv + 1]), rs2);
-            if constexpr (NC == 3) {
-                float rbig, rbig_b, rsmall, rsmall_b;
-                upk2(rbig2, rbig, rbig_b);
-                upk2(rsmall2, rsmall, rsmall_b);
-                const float I = __fadd_rn(I1, dI);
-                const float big = __fmaf_rn(-hi_i, I, rbig);
-                const float ad = fabsf(__fsub_rn(big, __fmaf_rn(lo_i, I, rsmall)));
-                rs = __fmaf_rn(weight_unit(ad, E, Sn, ESn, AXIS), proj_dyn[pv + 2], rs);
-            }
+        for (int k = 0; k < NC; ++k) {
+            if (k) I = __fadd_rn(I, dI);                                // exact half-integer
+            const float big = __fmaf_rn(-hi_i, I, rbig);              // exact
+            const float ad = fabsf(__fsub_rn(big, __fmaf_rn(lo_i, I, rsmall)));
+            rs = __fmaf_rn(weight_unit(ad, E, Sn, ESn, AXIS), pv[k], rs);
         }
     };
-    auto fold = [&]() {   // Kahan-compensated fold of the group's sum
-        float ra, rb2;
-        upk2(rs2, ra, rb2);
-        const float g = __fadd_rn(__fadd_rn(ra, rb2), rs);
-        const float y = __fsub_rn(g, comp);
-        const float tt = __fadd_rn(sum, y);
-        comp = __fsub_rn(__fsub_rn(tt, sum), y);
-        sum = tt;
+    // Kahan-compensated fold of a group's sum; a group that summed to exactly 0 is
+    // skipped, so rows that only met the zero fill leave the ray's sum untouched
+    auto fold = [&]() {
+        if (rs != 0.0f) {
+            const float y = __fsub_rn(rs, comp);
+            const float tt = __fadd_rn(sum, y);
+            comp = __fsub_rn(__fsub_rn(tt, sum), y);
+            sum = tt;
+        }
         rs = 0.0f;
-        rs2 = pk2(0.0f, 0.0f);
     };
-    // groups of eight rows from rb, the last one possibly shorter
+    // groups of eight rows aligned to multiples of 8 of the outer index (o0 is one), so
+    // that a ray's sum does not depend on the rows its warp walks beyond its own
     int r = rb;
     float rf = __int2float_rn(rb);
-    for (; r + 8 <= re; r += 8) {
+    while (r < re) {
+        const int gend = min(re, (r & ~7) + 8);
+        if (gend - r == 8) {
 #pragma unroll
-        for (int k = 0; k < 8; ++k, rf = __fadd_rn(rf, 1.0f)) row(r + k, rf);
+            for (int k = 0; k < 8; ++k, rf = __fadd_rn(rf, 1.0f)) row(r + k, rf);
+        } else {
+            for (int q = r; q < gend; ++q, rf = __fadd_rn(rf, 1.0f)) row(q, rf);
+        }
         fold();
+        r = gend;
     }
-    if (r < re) {
-        for (; r < re; ++r, rf = __fadd_rn(rf, 1.0f)) row(r, rf);
+}
+
+// Two rays per lane (A, B), every per-ray FP32 step as one f32x2 instruction
+// for both: the candidate index, the exact-split coordinates and each
+// candidate's weight (lane for lane the scalar IEEE steps of fwd_rows, so
+// the weights are the same bits).  Only for boxes that hold every candidate.
+template <bool CLASS_B, bool AXIS, int NC>
+__device__ __forceinline__ void fwd_rows2(const Prob &P, const ViewP &vp, uint64_t tau2, uint64_t qm2, int o0, int rb,
+                                          int re, int qs, int pbase, float *sum, float *comp)
+{
+    const int BW = P.BW;
+    const float Oc0 = CLASS_B ? __fsub_rn(__int2float_rn(o0 + rb), P.cx) : __fsub_rn(P.cy, __int2float_rn(o0 + rb));
+    const float dO = CLASS_B ? 1.0f : -1.0f;
+    const float hi_o = CLASS_B ? vp.cu_hi : vp.su_hi;   // coefficient of the outer coordinate
+    const float lo_o = CLASS_B ? vp.cu_lo : vp.su_lo;
+    const float hi_i = CLASS_B ? vp.su_hi : vp.cu_hi;   // coefficient of the inner coordinate
+    const float lo_i = CLASS_B ? vp.su_lo : vp.cu_lo;
+    const float c_in = CLASS_B ? P.cy : P.cx;           // inner coordinate = q - cx (A) or cy - q (B)
+    const float dI = CLASS_B ? -1.0f : 1.0f;
+    const float E = vp.E, Sn = vp.Sn, ESn = vp.ESn;
+    uint64_t Oc2 = pk2(Oc0, Oc0);
+    const uint64_t dO2 = pk2(dO, dO), hio2 = pk2(-hi_o, -hi_o), loo2 = pk2(lo_o, lo_o), ucl2 = pk2(P.uc_lo, P.uc_lo);
+    const uint64_t hii2 = pk2(-hi_i, -hi_i), loi2 = pk2(lo_i, lo_i), cin2 = pk2(c_in, c_in), dI2 = pk2(dI, dI);
+    const uint64_t bo2 = pk2(vp.b_o, vp.b_o), mag2 = pk2(kCeilMagic, kCeilMagic), one2 = pk2(1.0f, 1.0f);
+    const uint64_t qh2 = sub2_rn(qm2, pk2(vp.hwq, vp.hwq));
+    const int prow = pbase - qs;   // proj_dyn index of inner index 0 of the box's first row
+    uint64_t acc2 = pk2(0.0f, 0.0f);   // FP32 sums of up to 8 rows of A and B, then folded
+    auto row = [&](int r, uint64_t rf2) {
+        const uint64_t qc2 = add2_rp(fma2_rn(rf2, bo2, qh2), mag2);   // first candidates, as magic floats
+        float qcA, qcB;
+        upk2(qc2, qcA, qcB);
+        const int rowi = prow + r * BW;
+        const int pA = rowi + magic_int(qcA), pB = rowi + magic_int(qcB);
+        const uint64_t rbig2 = fma2_rn(hio2, Oc2, tau2);             // exact
+        const uint64_t rsmall2 = fma2_rn(loo2, Oc2, ucl2);
+        Oc2 = add2_rn(Oc2, dO2);
+        const uint64_t q0f2 = sub2_rn(qc2, mag2);
+        uint64_t I2 = CLASS_B ? sub2_rn(cin2, q0f2) : sub2_rn(q0f2, cin2);   // exact half-integers
+#pragma unroll
+        for (int k = 0; k < NC; ++k) {
+            if (k) I2 = add2_rn(I2, dI2);
+            const uint64_t big2 = fma2_rn(hii2, I2, rbig2);          // exact
+            float dA, dB;
+            upk2(sub2_rn(big2, fma2_rn(loi2, I2, rsmall2)), dA, dB);
+            const uint64_t w2 = pk2(weight_unit(fabsf(dA), E, Sn, ESn, AXIS), weight_unit(fabsf(dB), E, Sn, ESn, AXIS));
+            acc2 = fma2_rn(w2, pk2(proj_dyn[pA + k], proj_dyn[pB + k]), acc2);
+        }
+    };
+    auto fold = [&]() {   // Kahan-compensated folds of the group's sums, as in fwd_rows
+        float g[2];
+        upk2(acc2, g[0], g[1]);
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            if (g[q] != 0.0f) {
+                const float y = __fsub_rn(g[q], comp[q]);
+                const float tt = __fadd_rn(sum[q], y);
+                comp[q] = __fsub_rn(__fsub_rn(tt, sum[q]), y);
+                sum[q] = tt;
+            }
+        }
+        acc2 = pk2(0.0f, 0.0f);
+    };
+    int r = rb;
+    const float rbf = __int2float_rn(rb);
+    uint64_t rf2 = pk2(rbf, rbf);
+    while (r < re) {   // groups aligned to multiples of 8 of the outer index, as in fwd_rows
+        const int gend = min(re, (r & ~7) + 8);
+        if (gend - r == 8) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k, rf2 = add2_rn(rf2, one2)) row(r + k, rf2);
+        } else {
+            for (int q = r; q < gend; ++q, rf2 = add2_rn(rf2, one2)) row(q, rf2);
+        }
         fold();
+        r = gend;
     }
 }
 
@@ -163,25 +217,35 @@ __device__ __forceinline__ void fwd_row_range(const ViewP &vp, float base, int n
     *hi = min(n_outer - 1, __float2int_ru(b));
 }
 
-// One ray per lane; each warp runs its own double-buffered pipeline of
-// kRowsPerChunk-row boxes (BW columns covering its 32 rays), so warps never
-// wait for one another.  The warp walks only the chunks holding rows that one
-// of its rays can meet, and within them only those rows.
+// Two rays per lane (u and u + 32: 64 consecutive bins per warp); each warp
+// runs its own double-buffered pipeline of kRowsPerChunk-row boxes (BW columns
+// covering its 64 rays), so warps never wait for one another.  The warp walks
+// only the chunks holding rows that one of its rays can meet, and within them
+// only those rows.  Rays past the block's last bin follow the last ray (inside
+// the box) and are dropped by the caller.
 template <bool CLASS_B, bool AXIS, int NC>
-__device__ __forceinline__ double fwd_ray(const Prob &P, const ViewP &vp, const CUtensorMap *tm, int patch0,
-                                          uint64_t *bars, int n_outer, int n_inner, int u, int u_last, float tf,
-                                          float tl, int *bad, int *timed_out)
+__device__ __forceinline__ void fwd_ray2(const Prob &P, const ViewP &vp, const CUtensorMap *tm, int patch0,
+                                         uint64_t *bars, int n_outer, int n_inner, int uA, int uB, int u_last, float tf,
+                                         float tl, int *bad, int *timed_out, double *acc)
 {
     const int RC = kRowsPerChunk, BW = P.BW;
     const int box_elems = RC * BW;
     const int lane = threadIdx.x & 31;
-    const float tau = bin_pos(u, P.uc);
-    const float tau_hi = bin_pos(u, P.uc_hi);   // exact
-    const float base_u = __fmaf_rn(vp.a_tau, tau, vp.g0);   // inner index of the ray centre at outer index 0
-    float sum = 0.0f, comp = 0.0f;   // compensated running sum of the ray
-    // rows this ray can meet, and their union over the warp (uniform loop bounds)
+    const int uc[2] = {min(uA, u_last), min(uB, u_last)};
+    float tau_hi[2], base[2], sum[2] = {0.0f, 0.0f}, comp[2] = {0.0f, 0.0f};
     int r_lo = n_outer, r_hi = -1;
-    if (u <= u_last) fwd_row_range(vp, base_u, n_inner, n_outer, &r_lo, &r_hi);
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        tau_hi[q] = bin_pos(uc[q], P.uc_hi);                            // exact
+        base[q] = __fmaf_rn(vp.a_tau, bin_pos(uc[q], P.uc), vp.g0);     // ray centre at outer index 0
+        int lo, hi;
+        fwd_row_range(vp, base[q], n_inner, n_outer, &lo, &hi);
+        if ((q ? uB : uA) <= u_last) {
+            r_lo = min(r_lo, lo);
+            r_hi = max(r_hi, hi);
+        }
+    }
+    const uint64_t tau2 = pk2(tau_hi[0], tau_hi[1]);
     const int w_lo = __reduce_min_sync(0xffffffffu, r_lo), w_hi = __reduce_max_sync(0xffffffffu, r_hi);
     const int c_first = w_hi >= w_lo ? w_lo / RC : 0;
     const int nch = w_hi >= w_lo ? w_hi / RC - c_first + 1 : 0;   // chunks with at least one of the warp's rows
@@ -198,21 +262,28 @@ __device__ __forceinline__ double fwd_ray(const Prob &P, const ViewP &vp, const 
         const int o0 = c * RC;
         const int rows = min(RC, n_outer - o0);
         const int rb = max(0, w_lo - o0), re = min(rows, w_hi - o0 + 1);
-        if (ok && u <= u_last && rb < re) {
-            const float qm = __fmaf_rn(vp.b_o, __int2float_rn(o0), base_u);   // ray centre at row o0
+        if (ok && rb < re) {
             const int qs = fwd_box_start(vp, tf, tl, o0);
-            // the first candidate is monotone in the row: its end values (with one index
-            // of slack for rounding) bound every row of the chunk
-            const float qh = __fsub_rn(qm, vp.hwq);
-            const int qa = __float2int_ru(qh) - qs;
-            const int qb = __float2int_ru(__fmaf_rn((float)(rows - 1), vp.b_o, qh)) - qs;
-            const bool inside = min(qa, qb) >= 1 && max(qa, qb) <= P.BW - NC - 1;
-            if (inside)
-                fwd_rows<CLASS_B, AXIS, NC, false>(P, vp, tau_hi, qm, o0, rb, re, qs, patch0 + buf * box_elems, bad,
-                                                   sum, comp);
-            else
-                fwd_rows<CLASS_B, AXIS, NC, true>(P, vp, tau_hi, qm, o0, rb, re, qs, patch0 + buf * box_elems, bad,
-                                                  sum, comp);
+            float qm[2];
+            bool inside = true;
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                qm[q] = __fmaf_rn(vp.b_o, __int2float_rn(o0), base[q]);   // ray centre at row o0
+                // the first candidate is monotone in the row: its end values (with one index
+                // of slack for rounding) bound every row of the chunk
+                const float qh = __fsub_rn(qm[q], vp.hwq);
+                const int qa = __float2int_ru(qh) - qs;
+                const int qb = __float2int_ru(__fmaf_rn((float)(rows - 1), vp.b_o, qh)) - qs;
+                inside = inside && min(qa, qb) >= 1 && max(qa, qb) <= BW - NC - 1;
+            }
+            const int pb = patch0 + buf * box_elems;
+            if (inside) {
+                fwd_rows2<CLASS_B, AXIS, NC>(P, vp, tau2, pk2(qm[0], qm[1]), o0, rb, re, qs, pb, sum, comp);
+            } else {
+#pragma unroll
+                for (int q = 0; q < 2; ++q)
+                    fwd_rows<CLASS_B, AXIS, NC, true>(P, vp, tau_hi[q], qm[q], o0, rb, re, qs, pb, bad, sum[q], comp[q]);
+            }
         }
         // every lane is done with this buffer; a timeout in any lane ends the warp's loop
         if (__any_sync(0xffffffffu, !ok)) {
@@ -230,14 +301,17 @@ __device__ __forceinline__ double fwd_ray(const Prob &P, const ViewP &vp, const 
                         &bars[buf]);
         }
     }
-    return ((double)sum - (double)comp) * (double)vp.P;   // weights were in units of P
+#pragma unroll
+    for (int q = 0; q < 2; ++q) acc[q] = ((double)sum[q] - (double)comp[q]) * (double)vp.P;   // weights in units of P
 }
 
-__global__ void __launch_bounds__(128, 6) k_forward(const Prob *__restrict__ probs, const int *__restrict__ prefix,
-                                                 int count, int which, int mode)
+constexpr int kFwdThreads = 64;   // two warps of 64 rays: 128 bins per block at most
+
+__global__ void __launch_bounds__(kFwdThreads, 8) k_forward(const Prob *__restrict__ probs, const int *__restrict__ prefix,
+                                                         int count, int which, int mode)
 {
     // proj_dyn: [warp][2][kRowsPerChunk][BW]
-    __shared__ __align__(8) uint64_t bars[2 * 4];                 // two per warp
+    __shared__ __align__(8) uint64_t bars[2 * (kFwdThreads / 32)];   // two per warp
     __shared__ double red[40];
     __shared__ int flag;
     __shared__ int bad_sh;
@@ -254,35 +328,36 @@ __global__ void __launch_bounds__(128, 6) k_forward(const Prob *__restrict__ pro
     const bool axis = (vp.flags & kViewAxis) != 0;
     const int n_outer = classB ? P.nx : P.ny, n_inner = classB ? P.ny : P.nx;
     const CUtensorMap *tm = &P.tm[which * 2 + (classB ? 1 : 0)];
-    const int t = threadIdx.x, warp = t >> 5;
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
     const int patch0 = warp * 2 * kRowsPerChunk * P.BW;   // this warp's two boxes in proj_dyn
     uint64_t *wbars = bars + 2 * warp;
 
     const int u_first = tile * P.BU;
     const int u_last = min(P.U, u_first + P.BU) - 1;
-    const int u = u_first + t;
-    // the warp's rays: u_first + 32 warp .. (its box spans their bin positions)
-    const int uw0 = u_first + 32 * warp, uw1 = min(u_last, uw0 + 31);
+    // the warp's rays: uw0 .. uw0 + 63, lane l takes uw0 + l and uw0 + 32 + l
+    const int uw0 = u_first + 64 * warp, uw1 = min(u_last, uw0 + 63);
+    const int uA = uw0 + lane, uB = uw0 + 32 + lane;
     const float tf = bin_pos(min(uw0, u_last), P.uc), tl = bin_pos(uw1, P.uc);
 
     if (t == 0) bad_sh = 0;
-    if (t < 8) mbar_init(&bars[t], 1);
+    if (t < 2 * (kFwdThreads / 32)) mbar_init(&bars[t], 1);
     if (t == 0) fence_mbar_init();
     __syncthreads();
 
     int bad = 0;
     int timed_out = 0;   // a copy did not arrive (every lane of the warp sees it)
-    double acc;
+    double acc[2] = {0.0, 0.0};
     // axis-aligned views meet at most two pixels per row; near-diagonal ones up to three
     const bool three = (vp.flags & kViewFwd3) != 0;
 #define SUPCG_FWD(CB, AX, NC) \
-    fwd_ray<CB, AX, NC>(P, vp, tm, patch0, wbars, n_outer, n_inner, u, u_last, tf, tl, &bad, &timed_out)
-    if (uw0 > u_last)
-        acc = 0.0;   // a warp past the block's last bin
-    else if (classB)
-        acc = axis ? SUPCG_FWD(true, true, 2) : (three ? SUPCG_FWD(true, false, 3) : SUPCG_FWD(true, false, 2));
-    else
-        acc = axis ? SUPCG_FWD(false, true, 2) : (three ? SUPCG_FWD(false, false, 3) : SUPCG_FWD(false, false, 2));
+    fwd_ray2<CB, AX, NC>(P, vp, tm, patch0, wbars, n_outer, n_inner, uA, uB, u_last, tf, tl, &bad, &timed_out, acc)
+    if (uw0 > u_last) {
+        // a warp past the block's last bin
+    } else if (classB) {
+        if (axis) SUPCG_FWD(true, true, 2); else if (three) SUPCG_FWD(true, false, 3); else SUPCG_FWD(true, false, 2);
+    } else {
+        if (axis) SUPCG_FWD(false, true, 2); else if (three) SUPCG_FWD(false, false, 3); else SUPCG_FWD(false, false, 2);
+    }
 #undef SUPCG_FWD
     if (__syncthreads_or(timed_out)) {   // a warp's copy did not arrive: the whole block leaves
         if (t == 0 && P.sc) atomicExch(&P.sc->status, (int)SUPCG_ERR_TIMEOUT);
@@ -292,32 +367,35 @@ __global__ void __launch_bounds__(128, 6) k_forward(const Prob *__restrict__ pro
 
     // epilogue: store, fused residual / norm reduction
     double s = 0.0;
-    if (u <= u_last) {
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+        const int u = q ? uB : uA;
+        if (u > u_last) continue;
         if (mode == FWD_PLAIN) {
             const size_t o = (size_t)v * P.U + u;
-            if (P.storage == SUPCG_BF16) reinterpret_cast<__nv_bfloat16 *>(P.out_user)[o] = __double2bfloat16(acc);
-            else reinterpret_cast<float *>(P.out_user)[o] = (float)acc;
+            if (P.storage == SUPCG_BF16) reinterpret_cast<__nv_bfloat16 *>(P.out_user)[o] = __double2bfloat16(acc[q]);
+            else reinterpret_cast<float *>(P.out_user)[o] = (float)acc[q];
         } else if (mode == FWD_RESID) {
             const size_t o = (size_t)v * P.Up + u;
-            const float rr = (float)(acc - (double)P.bpad[o]);   // r = R x - b, cancellation taken in FP64
+            const float rr = (float)(acc[q] - (double)P.bpad[o]);   // r = R x - b, cancellation taken in FP64
             P.r[o] = rr;
-            s = (double)rr * (double)rr;
+            s += (double)rr * (double)rr;
         } else {
             const size_t o = (size_t)v * P.Up + u;
-            const float qq = (float)acc;
+            const float qq = (float)acc[q];
             P.q[o] = qq;
-            s = (double)qq * (double)qq;
+            s += (double)qq * (double)qq;
         }
     }
     __syncthreads();
     if (t == 0 && bad_sh && P.sc) atomicExch(&P.sc->status, (int)SUPCG_ERR_UNSUPPORTED);
     if (mode == FWD_PLAIN) return;
 
-    const double bs = block_sum<128>(s, red);
+    const double bs = block_sum<kFwdThreads>(s, red);
     if (t == 0) P.partial[local] = bs;
     const int nblk = prefix[pi + 1] - prefix[pi];
     if (last_block(&P.counter[0], nblk, &flag)) {
-        const double tot = block_sum_array<128>(P.partial, nblk, red);
+        const double tot = block_sum_array<kFwdThreads>(P.partial, nblk, red);
         if (t == 0) {
             Scal *sc = P.sc;
             if (mode == FWD_RESID) {
@@ -341,14 +419,14 @@ __global__ void __launch_bounds__(128, 6) k_forward(const Prob *__restrict__ pro
 int launch_forward(const Launch &L, int which, int mode)
 {
     static int max_smem_set = 0;
-    // every problem's BW <= 256, so the four warps' box buffers never exceed this size
-    const int smem = 4 * 2 * kRowsPerChunk * L.bw_max * 4;
+    // every problem's BW <= 256, so the warps' box buffers never exceed this size
+    const int smem = (kFwdThreads / 32) * 2 * kRowsPerChunk * L.bw_max * 4;
     if (!max_smem_set) {
         SUPCG_CUDA_TRY(cudaFuncSetAttribute(k_forward, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            4 * 2 * kRowsPerChunk * 256 * 4));
+                                            (kFwdThreads / 32) * 2 * kRowsPerChunk * 256 * 4));
         max_smem_set = 1;
     }
-    k_forward<<<L.blocks, 128, smem, L.st>>>(L.probs, L.prefix, L.count, which, mode);
+    k_forward<<<L.blocks, kFwdThreads, smem, L.st>>>(L.probs, L.prefix, L.count, which, mode);
     SUPCG_CUDA_TRY(cudaGetLastError());
     return SUPCG_OK;
 }
