@@ -64,8 +64,9 @@ typedef enum { SUPCG_F32 = 0, SUPCG_BF16 = 1 } supcg_storage;
  *                   sinograms passed to supcg_project / supcg_backproject
  * The host copies everything it needs; `angles` may be freed afterwards.
  * cos/sin are evaluated in FP64 on the host and are exact at multiples of pi/2.
- * Errors: SUPCG_ERR_ARG, SUPCG_ERR_UNSUPPORTED (bins much coarser than pixels),
- * SUPCG_ERR_CUDA, SUPCG_ERR_NOMEM. */
+ * Errors: SUPCG_ERR_ARG, SUPCG_ERR_UNSUPPORTED (bins more than about 2.5 times
+ * coarser or about 2 times finer than pixels: the projectors' shared-memory
+ * windows have fixed maxima), SUPCG_ERR_CUDA, SUPCG_ERR_NOMEM. */
 int supcg_create_geometry(int nx, int ny, double pixel_size, int n_views, const double *angles,
                           int n_bins, double bin_spacing, double det_center_offset,
                           int storage, supcg_geometry *out);
