@@ -59,6 +59,27 @@ def test_project_and_backproject_match_oracle(nx, ny, V, U, off, dsf):
         assert abs(lhs - rhs) <= 1e-6 * np.linalg.norm(gx) * np.linalg.norm(yy)
 
 
+def test_bin_size_limits():
+    """Bins up to about 2.5 times coarser than pixels are projected with oracle parity;
+    much coarser or much finer bins are refused (SUPCG_ERR_UNSUPPORTED), not computed wrongly.
+    (2.3: with 2.4 or 1.6 some axis-view rays lie on pixel edges up to the FP64 rounding
+    of the spacing, and the tie rule then sees a boundary edge on one side only.)"""
+    import paper_1807_10151_gb300 as S
+    d = 1.0 / 48
+    og = O.Geometry(48, V=40, U=31, ds=2.3 * d)
+    R = O.CSR(og)
+    G = gpu_geometry(og)
+    rng = np.random.default_rng(48)
+    x = f32(rng.uniform(size=(og.ny, og.nx)))
+    y = f32(rng.standard_normal((og.V, og.U)))
+    assert rel_l2(G.project(to_dev(x)).double().cpu().numpy(), R.project(x)) <= 1e-5
+    assert rel_l2(G.backproject(to_dev(y)).double().cpu().numpy(), R.backproject(y)) <= 1e-5
+    for dsf in (3.0, 0.45):
+        with pytest.raises(S.SupcgError) as e:
+            S.Geometry(48, n_views=40, n_bins=int(1.5 * 48 / dsf) + 2, pixel_size=d, bin_spacing=dsf * d)
+        assert e.value.code == -8
+
+
 def test_backprojector_is_exact_transpose_bitwise():
     """Entries of R read from forward columns equal entries read from backward rows, bit for bit."""
     og = O.Geometry(24, ny=20, V=13, U=33, off=0.004)
