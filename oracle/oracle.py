@@ -69,7 +69,8 @@ def _L():
                                         C.c_int, C.c_int, dp, dp, dp,
                                         C.c_double, C.c_double, C.c_int, C.c_double, C.c_int,
                                         C.c_long, C.c_int,
-                                        dp, dp, ip, ip, lp] + [dp, dp, dp, lp, dp, dp, dp, dp])
+                                        dp, dp, ip, ip, lp] + [dp, dp, dp, lp, dp, dp, dp, dp]
+                                       + [C.c_double, C.c_double])
             lib.orc_num_threads.restype = C.c_int
             lib.orc_conv3x3.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, dp, dp, dp, C.c_int, dp]
             lib.orc_conv3x3_backward.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, dp, dp, dp, dp, dp, dp]
@@ -249,12 +250,24 @@ def precondition(g, mu, rho):
     return fourier_diag(precond_D(g.shape[0], g.shape[1], mu, rho), g)
 
 
+def gray_level(g: Geometry, b):
+    """mu_X of Eq. (2.3): the image's average value estimated from the data
+    (Sec. 2).  Each view's sum b_u ds approximates the integral of the image
+    (every ray of a view crosses it, spaced ds apart); the mean over views,
+    divided by the image area nx ny d^2, is the gray level."""
+    b = _f64(b).reshape(g.V, g.U)
+    return float(np.mean(b.sum(axis=1)) * g.ds / (g.nx * g.ny * g.d * g.d))
+
+
 def suppcg(R: CSR, b, x0=None, a=0.995, gamma=0.5, K=1, eps=-1.0, max_iter=50,
-           max_trials=10_000, perturb=True, mu=1e-5, rho=0.8, D=None):
+           max_trials=10_000, perturb=True, mu=1e-5, rho=0.8, D=None, bayes_r=0.0, bayes_mu=None):
     """SupPCG(x0, a, gamma, K, eps), Algorithm 3 (perturb=False: PCG).
 
-    Returns a dict with the returned image x_{k-1/2} ("x_half"), x_k ("x_last"),
-    the count of while-body executions, the returned k, l_k and per-body logs.
+    bayes_r > 0 minimises the Bayesian criterion of Eq. (2.3),
+    r^2 ||Rx - b||^2 + ||x - mu_X||^2, instead of ||Rx - b||^2 (mu_X = bayes_mu,
+    or gray_level(b) when None).  Returns a dict with the returned image
+    x_{k-1/2} ("x_half"), x_k ("x_last"), the count of while-body executions,
+    the returned k, l_k and per-body logs.
     """
     g = R.geom
     n, m = g.n, g.m
@@ -277,7 +290,9 @@ def suppcg(R: CSR, b, x0=None, a=0.995, gamma=0.5, K=1, eps=-1.0, max_iter=50,
                          float(eps), int(max_iter), int(max_trials), int(bool(perturb)),
                          _d(x_half), _d(x_last), _i(iters), _i(k_out), _l(ell),
                          _d(logs["f"]), _d(logs["tv_k"]), _d(logs["tv_half"]), _l(log_ell),
-                         _d(logs["alpha"]), _d(logs["beta"]), _d(logs["snorm"]), _d(init))
+                         _d(logs["alpha"]), _d(logs["beta"]), _d(logs["snorm"]), _d(init),
+                         float(bayes_r) ** 2 if bayes_r > 0 else 0.0,
+                         float(gray_level(g, b) if (bayes_r > 0 and bayes_mu is None) else (bayes_mu or 0.0)))
     it = int(iters[0])
     out = {"status": int(rc), "x_half": x_half.reshape(g.ny, g.nx),
            "x_last": x_last.reshape(g.ny, g.nx), "iters": it, "k": int(k_out[0]),

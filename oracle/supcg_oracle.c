@@ -12,6 +12,7 @@
  *   - data model R x = b + e, R the projection (Radon) matrix ........ Sec. 2
  *   - least squares f(x) = ||Rx - b||^2, normal equations R^T R x = R^T b
  *                                                         Eq. (2.1), (2.2)
+ *   - Bayesian criterion f(x) = r^2 ||Rx - b||^2 + ||x - mu_X||^2 ... Eq. (2.3)
  *   - acquisition shape (parallel rays, equally spaced angles in [0,pi),
  *     ray spacing = pixel size) ............................. Sec. 4.1
  *   - total variation TV(y) and the nonascending vector t ...... Sec. 3.1
@@ -486,6 +487,7 @@ typedef struct {
     long m, n;
     const long *rp; const int *ci; const double *va;    /* R    (CSR) */
     const long *rpt; const int *cit; const double *vat; /* R^T  (CSR) */
+    double r2, muX;   /* r2 > 0: Bayesian criterion of Eq. (2.3) with r^2 = r2, gray level muX */
 } orc_op;
 
 static double dotv(long n, const double *a, const double *b)
@@ -495,7 +497,9 @@ static double dotv(long n, const double *a, const double *b)
     return s;
 }
 
-/* g = A x - y = R^T (R x - b); returns f(x) = ||R x - b||^2. */
+/* g = A x - y and f(x).  Least squares (Eq. (2.1), (2.2)): A = R^T R,
+ * y = R^T b, f = ||R x - b||^2.  Bayesian (Eq. (2.3); half its gradient):
+ * A = r^2 R^T R + I, y = r^2 R^T b + mu_X, f = r^2 ||R x - b||^2 + ||x - mu_X||^2. */
 static double grad_ls(const orc_op *op, const double *x, const double *b,
                       double *r, double *g)
 {
@@ -503,14 +507,25 @@ static double grad_ls(const orc_op *op, const double *x, const double *b,
     double f = 0.0;
     for (long i = 0; i < op->m; ++i) { r[i] -= b[i]; f += r[i] * r[i]; }
     orc_spmv(op->n, op->rpt, op->cit, op->vat, r, g);
+    if (op->r2 > 0.0) {
+        double fx = 0.0;
+        for (long j = 0; j < op->n; ++j) {
+            const double dx = x[j] - op->muX;
+            g[j] = op->r2 * g[j] + dx;
+            fx += dx * dx;
+        }
+        f = op->r2 * f + fx;
+    }
     return f;
 }
 
-/* h = A p = R^T R p. */
+/* h = A p: R^T R p, or r^2 R^T R p + p for the Bayesian criterion. */
 static void apply_A(const orc_op *op, const double *p, double *q, double *h)
 {
     orc_spmv(op->m, op->rp, op->ci, op->va, p, q);
     orc_spmv(op->n, op->rpt, op->cit, op->vat, q, h);
+    if (op->r2 > 0.0)
+        for (long j = 0; j < op->n; ++j) h[j] = op->r2 * h[j] + p[j];
 }
 
 /*
@@ -524,6 +539,8 @@ static void apply_A(const orc_op *op, const double *p, double *q, double *h)
  * Logs (nullable, max_iter entries, entry k-1 for body k):
  *   f(x_{k+1/2}), TV(x_k), TV(x_{k+1/2}), l_{k+1}, alpha, beta, ||s_k||.
  * init_log (nullable, 3 entries): f(x_0), alpha of step 6, ||p_0||.
+ * r2 > 0 selects the Bayesian criterion of Eq. (2.3) (r^2 = r2, gray level muX)
+ * in place of least squares: A, y and f as in grad_ls.
  */
 int orc_suppcg(long m, long n,
                const long *rp, const int *ci, const double *va,
@@ -533,10 +550,11 @@ int orc_suppcg(long m, long n,
                long max_trials, int perturb,
                double *x_half, double *x_last, int *iters, int *k_out, long *ell_out,
                double *log_f, double *log_tv_k, double *log_tv_half, long *log_ell,
-               double *log_alpha, double *log_beta, double *log_snorm, double *init_log)
+               double *log_alpha, double *log_beta, double *log_snorm, double *init_log,
+               double r2, double muX)
 {
     if ((long)ny * nx != n) return ORC_ERR_ARG;
-    orc_op op = {m, n, rp, ci, va, rpt, cit, vat};
+    orc_op op = {m, n, rp, ci, va, rpt, cit, vat, r2, muX};
     size_t nb = sizeof(double) * (size_t)n, mb = sizeof(double) * (size_t)m;
     double *x = malloc(nb), *g = malloc(nb), *z = malloc(nb), *p = malloc(nb);
     double *h = malloc(nb), *s = malloc(nb), *r = malloc(mb), *q = malloc(mb);
