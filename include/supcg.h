@@ -145,6 +145,13 @@ typedef struct {
     int perturb;           /* 1: SupPCG; 0: skip S_TV (plain PCG)                         */
     int precondition;      /* 1: M of Eq. (3.2); 0: M = I (SupCG / CG)                     */
     int graph;             /* 1: replay each iteration as a captured CUDA graph            */
+    double bayes_r;        /* > 0: minimise the Bayesian criterion of Eq. (2.3),
+                            *   r^2 ||R x - b||^2 + ||x - mu_X||^2 (r = bayes_r, the
+                            *   signal-to-noise ratio), instead of ||R x - b||^2; every f
+                            *   (eps test, report, log) is then that criterion.  <= 0: least squares */
+    double bayes_mu;       /* mu_X, the gray level of Eq. (2.3); NaN: estimated from b on the
+                            *   device as the image average the data imply (mean over views of
+                            *   sum_u b ds, over the image area)                              */
 } supcg_params;
 
 /* Outcome of a solve. */

@@ -48,7 +48,7 @@ class Params(C.Structure):
     _fields_ = [("K", C.c_int), ("a", C.c_double), ("gamma", C.c_double), ("mu", C.c_double),
                 ("rho", C.c_double), ("eps", C.c_double), ("max_iter", C.c_int),
                 ("max_trials", C.c_longlong), ("perturb", C.c_int), ("precondition", C.c_int),
-                ("graph", C.c_int)]
+                ("graph", C.c_int), ("bayes_r", C.c_double), ("bayes_mu", C.c_double)]
 
 
 class Report(C.Structure):
@@ -203,9 +203,11 @@ def _ptr(t, dtype=None):
 
 
 def make_params(K=1, a=0.995, gamma=0.5, mu=1e-5, rho=0.8, eps=-1.0, max_iter=50, max_trials=10_000,
-                perturb=True, precondition=True, graph=True) -> Params:
+                perturb=True, precondition=True, graph=True, bayes_r=0.0, bayes_mu=None) -> Params:
+    """supcg_params; bayes_r > 0 selects the Bayesian criterion (bayes_mu None: mu_X from the data)."""
     return Params(int(K), float(a), float(gamma), float(mu), float(rho), float(eps), int(max_iter),
-                  int(max_trials), int(bool(perturb)), int(bool(precondition)), int(bool(graph)))
+                  int(max_trials), int(bool(perturb)), int(bool(precondition)), int(bool(graph)),
+                  float(bayes_r), float("nan") if bayes_mu is None else float(bayes_mu))
 
 
 class Geometry:

@@ -467,6 +467,8 @@ static int ws_create(const std::vector<supcg_geometry> &gs, Workspace **out)
         P.storage = g->storage;
         P.stv_blocks = nb[KT_STV][c];
         P.mu = 1e-5; P.rho = 0.8; P.precond = 1;
+        P.r2 = 0.0;
+        P.gray_scale = g->ds / ((double)g->V * g->nx * g->ny * g->d * g->d);
         int e = 0;
         e |= encode_map(&P.tm[0], P.x, g->nx, g->ny, g->nxp, g->BW, kRowsPerChunk);
         e |= encode_map(&P.tm[1], P.xT, g->ny, g->nx, g->nyp, g->BW, kRowsPerChunk);
@@ -691,6 +693,7 @@ extern "C" long long supcg_kernel_launches(void) { return g_launches.load(); }
 static int check_params(const supcg_params *p)
 {
     if (!p || p->max_iter < 0 || p->K < 0) return SUPCG_ERR_ARG;
+    if (!isfinite(p->bayes_r) || (p->bayes_r > 0.0 && isinf(p->bayes_mu))) return SUPCG_ERR_ARG;
     if (p->perturb) {
         int rc = check_stv(p->a, p->gamma, p->K, p->max_trials);
         if (rc) return rc;
@@ -769,6 +772,7 @@ static int run_solve(Workspace *w, const float *const *d_b, float *const *d_x, c
         P.mu = p->mu;
         P.rho = p->rho;
         P.precond = p->precondition ? 1 : 0;
+        P.r2 = p->bayes_r > 0.0 ? p->bayes_r * p->bayes_r : 0.0;
         P.storage = SUPCG_F32;
         P.log = (c == 0) ? d_log : nullptr;
         P.trace = (c == 0) ? d_trace : nullptr;
@@ -782,6 +786,7 @@ static int run_solve(Workspace *w, const float *const *d_b, float *const *d_x, c
         s0[c] = Scal();
         s0[c].eps = p->eps;
         s0[c].init = 1;
+        s0[c].muX = isnan(p->bayes_mu) ? 0.0 : p->bayes_mu;   // NaN: estimated from b below
         SUPCG_CUDA_TRY(cudaMemcpyAsync(P.sc, &s0[c], sizeof(Scal), cudaMemcpyHostToDevice, st));
         SUPCG_CUDA_TRY(cudaMemsetAsync(P.counter, 0, 16 * sizeof(unsigned), st));
         SUPCG_CUDA_TRY(cudaMemsetAsync(P.bar, 0, 2 * sizeof(unsigned), st));
@@ -790,6 +795,7 @@ static int run_solve(Workspace *w, const float *const *d_b, float *const *d_x, c
     }
     LAUNCH(SUPCG_KIND_VECTOR, st, launch_stage_in(w->L(KT_TR, st), 0));
     LAUNCH(SUPCG_KIND_VECTOR, st, launch_stage_sino(w->L(KT_SINO, st), 1));
+    if (p->bayes_r > 0.0 && isnan(p->bayes_mu)) LAUNCH(SUPCG_KIND_VECTOR, st, launch_gray(w->L(KT_SINO, st)));
     if (p->precondition) LAUNCH(SUPCG_KIND_VECTOR, st, launch_fft_dtab(w->L(KT_VEC, st)));
     if ((rc = enqueue_init(w, p, st))) return rc;
 

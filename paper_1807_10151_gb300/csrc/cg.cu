@@ -120,9 +120,10 @@ int launch_store_out(const Launch &L, int which)
 // ------------------------------------------------------------ Algorithm 2 steps
 // Steps 3-4 (beta from z^T h computed earlier) and the g^T p half of step 6:
 //   p <- -z + beta p ;  partial g^T p.   In steps 2-7 of Algorithm 3 beta = 0.
-// p = -z + beta p (Algorithm 2 step 4; z = g when M = I) and g^T p (step 6), on
-// 32 x 32 tiles so that the same pass writes p^T for the projector; the last
-// block stores g^T p and beta.  Launched with the transpose's tile grid.
+// p = -z + beta p (Algorithm 2 step 4; z = g when M = I), g^T p (step 6) and
+// ||p||^2 (for h = A p under the Bayesian criterion), on 32 x 32 tiles so that
+// the same pass writes p^T for the projector; the last block stores the sums
+// and beta.  Launched with the transpose's tile grid.
 __global__ void __launch_bounds__(256) k_pupdate(const Prob *__restrict__ probs, const int *__restrict__ prefix,
                                                  int count)
 {
@@ -139,7 +140,7 @@ __global__ void __launch_bounds__(256) k_pupdate(const Prob *__restrict__ probs,
     const int tiles_j = (P.nx + 31) / 32;
     const int ti = local / tiles_j, tj = local - ti * tiles_j;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    double s = 0.0;
+    double s = 0.0, spp = 0.0;   // g^T p and ||p||^2
     for (int r = ty; r < 32; r += 8) {
         const int i = ti * 32 + r, j = tj * 32 + tx;
         float pn = 0.0f;
@@ -148,6 +149,7 @@ __global__ void __launch_bounds__(256) k_pupdate(const Prob *__restrict__ probs,
             pn = __fmaf_rn(beta, P.p[e], -z[e]);
             P.p[e] = pn;
             s += (double)P.g[e] * (double)pn;
+            spp += (double)pn * (double)pn;
         }
         sh[r][tx] = pn;
     }
@@ -157,16 +159,57 @@ __global__ void __launch_bounds__(256) k_pupdate(const Prob *__restrict__ probs,
         if (j < P.nx && i < P.ny) P.pT[(size_t)j * P.nyp + i] = sh[tx][r];
     }
     const double bs = block_sum<256>(s, red);
-    if (threadIdx.x == 0) P.partial[local] = bs;
+    const double bp = block_sum<256>(spp, red);
     const int nblk = prefix[pi + 1] - prefix[pi];
+    if (threadIdx.x == 0) {
+        P.partial[local] = bs;
+        P.partial[nblk + local] = bp;
+    }
     if (last_block(&P.counter[1], nblk, &flag)) {
         const double tot_s = block_sum_array<256>(P.partial, nblk, red);
+        const double tot_p = block_sum_array<256>(P.partial + nblk, nblk, red);
         if (threadIdx.x == 0) {
             P.sc->gtp = tot_s;
+            P.sc->pp = tot_p;
             P.sc->beta = beta_d;
             P.counter[1] = 0;
         }
     }
+}
+
+// Gray level mu_X of the Bayesian criterion (Eq. (2.3)) estimated from the data:
+// every view's sum_u b ds approximates the image integral, so the mean over views
+// divided by the image area is the image average (sc->muX = gray_scale sum b).
+__global__ void __launch_bounds__(kRedThreads) k_gray(const Prob *__restrict__ probs, const int *__restrict__ prefix,
+                                                      int count)
+{
+    __shared__ double red[40];
+    __shared__ int flag;
+    int local;
+    const int pi = find_problem(prefix, count, blockIdx.x, &local);
+    const Prob &P = probs[pi];
+    const size_t tot = (size_t)P.V * P.Up;   // bpad: zero padding beyond U
+    double s = 0.0;
+    for (size_t e = (size_t)local * kVecPerBlock + threadIdx.x; e < tot && e < (size_t)(local + 1) * kVecPerBlock;
+         e += kRedThreads)
+        s += (double)P.bpad[e];
+    const double bs = block_sum<kRedThreads>(s, red);
+    if (threadIdx.x == 0) P.partial[local] = bs;
+    const int nblk = prefix[pi + 1] - prefix[pi];
+    if (last_block(&P.counter[5], nblk, &flag)) {
+        const double sum = block_sum_array<kRedThreads>(P.partial, nblk, red);
+        if (threadIdx.x == 0) {
+            P.sc->muX = sum * P.gray_scale;
+            P.counter[5] = 0;
+        }
+    }
+}
+
+int launch_gray(const Launch &L)
+{
+    k_gray<<<L.blocks, kRedThreads, 0, L.st>>>(L.probs, L.prefix, L.count);
+    SUPCG_CUDA_TRY(cudaGetLastError());
+    return SUPCG_OK;
 }
 
 int launch_pupdate(const Launch &L)

@@ -151,6 +151,9 @@ struct Scal {
     double tv_k, tv_half;  // TV(x_k), TV(x_{k+1/2}) of the last S_TV call
     double snorm2;     // ||s_k||^2 of the last S_TV call (accumulated in FP64)
     double eps;
+    double f_ls;       // Bayesian criterion: ||R x - b||^2 of the most recent residual projection
+    double muX;        // Bayesian criterion: the gray level mu_X of Eq. (2.3)
+    double pp;         // ||p||^2 of the current p (h = r^2 R^T R p + p for the Bayesian criterion)
     long long ell;     // l of Algorithm 1/3
     long long trials;  // trials of the last S_TV call
     int k;             // executions of the while body
@@ -177,6 +180,8 @@ struct Prob {
     const int *vlist;      // [nA + nB]: class-A views, then class-B views
     FFTPlan fx, fy;
     double mu, rho;
+    double r2;             // r^2 of the Bayesian criterion (Eq. (2.3)); 0: least squares
+    double gray_scale;     // ds / (V nx ny d^2): sum of b times this is the gray-level estimate
     int precond;           // 1: M of Eq. (3.2); 0: M = I
     int storage;           // SUPCG_F32 / SUPCG_BF16 element type of in_user / out_user
     int stv_blocks;        // cooperative S_TV: blocks owned by this problem
@@ -399,6 +404,7 @@ int launch_store_out(const Launch &L, int which);          // padded image (0 x,
 int launch_fft_rows(const Launch &L, int inverse, int standalone, int smem);
 int launch_fft_cols(const Launch &L, int standalone, int smem);
 int launch_fft_dtab(const Launch &L);                       // fills Dtab from mu, rho (once per solve or call)
+int launch_gray(const Launch &L);                           // sc->muX from bpad (Bayesian criterion)
 int launch_pupdate(const Launch &L);
 int launch_beta(const Launch &L);
 int launch_xupdate(const Launch &L);

@@ -399,12 +399,17 @@ __global__ void __launch_bounds__(kFwdThreads, 8) k_forward(const Prob *__restri
         if (t == 0) {
             Scal *sc = P.sc;
             if (mode == FWD_RESID) {
-                sc->f = tot;
-                if (sc->init) sc->f0 = tot;
+                if (P.r2 > 0.0) {
+                    sc->f_ls = tot;   // f = r^2 ||r||^2 + ||x - mu_X||^2 is completed by the backprojector
+                } else {
+                    sc->f = tot;
+                    if (sc->init) sc->f0 = tot;
+                }
             } else {
-                sc->pth = tot;
-                const double al = -sc->gtp / tot;
-                if (!(tot > 0.0) || !isfinite(al)) {
+                const double pth = (P.r2 > 0.0) ? P.r2 * tot + sc->pp : tot;   // p^T h, h = A p
+                sc->pth = pth;
+                const double al = -sc->gtp / pth;
+                if (!(pth > 0.0) || !isfinite(al)) {
                     atomicExch(&sc->status, (int)SUPCG_ERR_BREAKDOWN);
                     sc->alpha = 0.0;
                 } else {
@@ -693,6 +698,11 @@ __global__ void __launch_bounds__(kBwdThreads, 3) k_backward(const Prob *__restr
     __shared__ int last_sh;
     if (!last_block(&P.tilecnt[tile], kBwdViewParts, &last_sh)) return;
     float *out = (mode == BWD_G) ? P.g : (mode == BWD_H ? P.h : P.g);
+    // Bayesian criterion (Eq. (2.3)): g = r^2 R^T r + (x - mu_X), h = r^2 R^T q + p, and
+    // ||x - mu_X||^2 for f
+    const bool bayes = mode != BWD_PLAIN && P.r2 > 0.0;
+    const double muX = bayes ? P.sc->muX : 0.0;
+    double sx = 0.0;
     if (grp == 0)
 #pragma unroll
         for (int e = 0; e < kBwdPixPerThread; ++e) {
@@ -701,10 +711,33 @@ __global__ void __launch_bounds__(kBwdThreads, 3) k_backward(const Prob *__restr
                 const size_t o = (size_t)i * P.nxp + j;
                 double v = 0.0;
                 for (int h = 0; h < kBwdViewParts; ++h) v += *(volatile const double *)(P.bsplit + h * img + o);
+                if (bayes) {
+                    if (mode == BWD_G) {
+                        const double dx = (double)P.x[o] - muX;
+                        v = P.r2 * v + dx;
+                        sx += dx * dx;
+                    } else {
+                        v = P.r2 * v + (double)P.p[o];
+                    }
+                }
                 out[o] = (float)v;
             }
         }
     if (t == 0) P.tilecnt[tile] = 0;   // ready for the next launch
+    if (!bayes || mode != BWD_G) return;
+    // f = r^2 ||R x - b||^2 + ||x - mu_X||^2: the tiles' sums, added by the last tile to finish
+    const double bs = block_sum<kBwdThreads>(sx, comb);
+    const int ntiles = (prefix[pi + 1] - prefix[pi]) / kBwdViewParts;
+    if (t == 0) P.partial[tile] = bs;
+    if (last_block(&P.counter[4], ntiles, &last_sh)) {
+        const double tot = block_sum_array<kBwdThreads>(P.partial, ntiles, comb);
+        if (t == 0) {
+            Scal *sc = P.sc;
+            sc->f = P.r2 * sc->f_ls + tot;
+            if (sc->init) sc->f0 = sc->f;
+            P.counter[4] = 0;
+        }
+    }
 }
 
 int launch_backward(const Launch &L, int mode, int bwin)

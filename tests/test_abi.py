@@ -48,5 +48,6 @@ def test_argument_errors_are_status_codes():
 def test_param_struct_layout_matches_header():
     # offsets follow the C layout of supcg_params / supcg_report on LP64
     assert S.Params.a.offset == 8 and S.Params.max_iter.offset == 48 and S.Params.max_trials.offset == 56
-    assert C.sizeof(S.Params) == 80
+    assert S.Params.bayes_r.offset == 80 and S.Params.bayes_mu.offset == 88
+    assert C.sizeof(S.Params) == 96
     assert S.Report.ell.offset == 8 and S.Report.n_learned.offset == 48 and C.sizeof(S.Report) == 56
