@@ -250,6 +250,23 @@ def precondition(g, mu, rho):
     return fourier_diag(precond_D(g.shape[0], g.shape[1], mu, rho), g)
 
 
+def selective_error(x, ref, ax, ay):
+    """SE of Eq. (4.1) with C = 1: sqrt of the sum over the pixels S whose centres
+    lie in the centred ellipse of horizontal semi-axis ax * nx and vertical
+    semi-axis ay * ny pixels of (x - ref)^2 (Sec. 4.2 uses semi-axes of 5 and
+    7 cm, just inside the skull)."""
+    x, ref = _f64(x), _f64(ref)
+    ny, nx = ref.shape
+    s = 0.0
+    for i in range(ny):
+        for j in range(nx):
+            ex = (j - 0.5 * (nx - 1)) / (ax * nx)
+            ey = (i - 0.5 * (ny - 1)) / (ay * ny)
+            if ex * ex + ey * ey <= 1.0:
+                s += (x[i, j] - ref[i, j]) ** 2
+    return float(np.sqrt(s))
+
+
 def gray_level(g: Geometry, b):
     """mu_X of Eq. (2.3): the image's average value estimated from the data
     (Sec. 2).  Each view's sum b_u ds approximates the integral of the image
