@@ -9,7 +9,7 @@ Algorithm 3 (S_TV, forward projection with residual, backprojection,
 preconditioner, CG scalars and axpys, forward and back projection of p).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload plain512|batched64|large2048]
+                  [--workload plain512|batched64|large2048|learned512|sweep243]
 
 --impl reference times the FP64 CPU oracle on the host cores on the same
 workload (it is the only other implementation of the method here).
@@ -24,6 +24,11 @@ a=1-1e-5, gamma=1e-2, mu=1e-5, rho=0.8) on 400 random 128^2 problems x 50
 iterations (20k pairs), network trained on the GPU, then plain vs learned
 SupPCG on the 512^2 / 720-view Poisson workload: wall time for the learned
 solve to reach the plain solve's final residual and TV.
+--workload sweep243: the paper's parameter selection (Sec. 4.2) for SupPCG as
+one batched sweep: 180 grid points (K, a, gamma, mu, rho; rho = 0.4 excluded)
+x 15 iterations on a 243^2 / 360-view / 345-bin head stand-in (Poisson 1e5),
+scored by the selective error of Eq. (4.1), timed against the same solves one
+after another.
 --workload large2048: 8 slices of 2048^2, 2880 views, 2900 bins (40 ellipses
 on a textured background, Poisson 1e4 photons): FP32- and BF16-stored
 projector pair timed on the batch, errors of both against the FP64 oracle on
@@ -237,6 +242,73 @@ def run_batched(args, dev):
     return 0
 
 
+SWEEP_GRID = [dict(K=K, a=a, gamma=g, mu=mu, rho=rho)
+              for K in (10, 20, 40) for a in (1 - 1e-5, 1 - 1e-4, 1 - 1e-3, 1 - 1e-2, 1 - 1e-1)
+              for g in (1e-2, 5e-2) for mu in (1e-5, 1e-4, 1e-3) for rho in (0.6, 0.8)]
+
+
+def run_sweep(args, dev):
+    """Sec. 4.2's parameter selection for SupPCG as one batched sweep: the grid
+    K x a x gamma x mu x rho of the paper (rho = 0.4 excluded: h(pi) <= 0), 15
+    iterations each, scored by the selective error SE of Eq. (4.1) against the
+    phantom; timed against the same 180 solves one after another."""
+    import numpy as np
+    import torch
+    import paper_1807_10151_gb300 as S
+    from paper_1807_10151_gb300 import synth
+    N, V, U, its = 243, 360, 345, 15
+    x = synth.head_standin(N, 6001)
+    G = S.Geometry(N, n_views=V, n_bins=U)
+    clean = G.project(torch.tensor(x, dtype=torch.float32, device=dev)).double().cpu().numpy()
+    b = torch.tensor(synth.poisson_log(clean, 1e5, 6002), dtype=torch.float32, device=dev)
+    ref = torch.tensor(x, dtype=torch.float32, device=dev)
+    params = [dict(q, max_iter=its) for q in SWEEP_GRID]
+    st = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        S.solve_sweep(G, b, [dict(q, max_iter=3) for q in SWEEP_GRID], ref=ref)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    l0 = S.supcg_kernel_launches()
+    with ClockSampler(dev.index or 0) as clk:
+        ev[0].record(st)
+        xs, reps, se = S.solve_sweep(G, b, params, ref=ref)
+        ev[1].record(st)
+        torch.cuda.synchronize()
+    launches = S.supcg_kernel_launches() - l0
+    assert all(r["status"] == 0 for r in reps), [r for r in reps if r["status"]]
+    t_batch = ev[0].elapsed_time(ev[1]) / 1000.0
+    se = se.cpu().numpy()
+    best = int(np.argmin(se.min(axis=1)))
+    best_it = int(np.argmin(se[best])) + 1
+    # the same solves one after another
+    G.solve(b, **params[0])
+    torch.cuda.synchronize()
+    ev[2].record(st)
+    for q in params:
+        G.solve(b, **q)
+    ev[3].record(st)
+    torch.cuda.synchronize()
+    t_seq = ev[2].elapsed_time(ev[3]) / 1000.0
+    n = len(params)
+    line = {
+        "metric": "SupPCG problem-iterations/s (parameter sweep)", "value": n * its / t_batch,
+        "unit": "problem-iterations/s", "n_gpus": 1, "steps": its, "warmup": args.warmup,
+        "ms_per_step": 1000.0 * t_batch / its, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "sweep_243x243_360views_345bins_head_standin_poisson1e5", "solves": n,
+                   "grid": {"K": [10, 20, 40], "a": "1 - 1e-5 .. 1 - 1e-1", "gamma": [1e-2, 5e-2],
+                            "mu": [1e-5, 1e-4, 1e-3], "rho": [0.6, 0.8]},
+                   "se_axes": list(S.SE_AXES), "l2": "180 working sets of ~6 MB: the batch exceeds L2"},
+        "sequential": {"seconds": t_seq, "problem_iterations_per_s": n * its / t_seq,
+                       "time_to_equal_ratio": t_seq / t_batch},
+        "best": {"params": SWEEP_GRID[best], "iteration": best_it, "se": float(se[best, best_it - 1]),
+                 "se_plain_first_iteration_median": float(np.median(se[:, 0]))},
+        "gpu_launches": int(launches), "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_large(args, dev):
     """8 slices of 2048^2: FP32 vs BF16 storage of the projector pair."""
     import numpy as np
@@ -421,7 +493,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-iters", type=int, default=3)
-    ap.add_argument("--workload", default="plain512", choices=["plain512", "batched64", "large2048", "learned512"])
+    ap.add_argument("--workload", default="plain512",
+                    choices=["plain512", "batched64", "large2048", "learned512", "sweep243"])
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world = env_int("WORLD_SIZE", 1)
@@ -450,6 +523,8 @@ def main():
         return run_large(args, dev)
     if args.workload == "learned512":
         return run_learned(args, dev)
+    if args.workload == "sweep243":
+        return run_sweep(args, dev)
     G, b_host = make_problem(rank, dev)
     b = torch.tensor(b_host, device=dev)
     from paper_1807_10151_gb300 import autotune

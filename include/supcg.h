@@ -197,6 +197,25 @@ int supcg_solve_host(supcg_geometry g, const float *h_b, float *h_x, const supcg
 int supcg_solve_batched(const supcg_geometry *gs, const float *const *d_b, float *const *d_x,
                         int count, const supcg_params *p, supcg_report *reps, void *stream);
 
+/* Parameter sweep (Sec. 4.2, algorithmic parameter selection): `count` solves of
+ * the same problem (geometry g, data d_b) in one set of batched launches, solve c
+ * with the S_TV parameters K, a, gamma and the preconditioner parameters mu, rho
+ * of ps[c]; every other field must equal ps[0]'s (the shared loop control), else
+ * SUPCG_ERR_ARG.
+ *   d_x[c]   FP32 [ny][nx] image of solve c (in x_0, out x_{k-1/2}), caller-owned
+ *   d_ref    nullable FP32 [ny][nx] reference image (the phantom x-dagger): with it,
+ *            the selective error of Eq. (4.1) with C = 1,
+ *              SE(x) = sqrt(sum over (i,j) in S of (x_ij - ref_ij)^2),
+ *            S = the pixels whose centres lie in the centred ellipse of horizontal
+ *            semi-axis se_ax * nx and vertical semi-axis se_ay * ny pixels, is
+ *            written for x_{k+1/2} of every while-body k (1-based) of solve c to
+ *            d_se[c * max_iter + k - 1] (FP64, device, caller-owned, count * max_iter)
+ *   reps     host array of `count` reports
+ * The scratch lives in g (one workspace per solve).  Synchronous. */
+int supcg_solve_sweep(supcg_geometry g, const float *d_b, float *const *d_x, int count,
+                      const supcg_params *ps, const float *d_ref, double se_ax, double se_ay,
+                      double *d_se, supcg_report *reps, void *stream);
+
 /* ------------------------------------------------------------------------
  * Learned perturbation network (an addition to the paper's method: the paper
  * perturbs along the normalised negative TV gradient, Sec. 3.1; this network

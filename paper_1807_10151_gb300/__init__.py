@@ -17,7 +17,7 @@ __all__ = [
     "load", "lib_path", "SupcgError", "Geometry", "Params", "Report", "solve_batched",
     "supcg_create_geometry", "supcg_destroy_geometry", "supcg_project", "supcg_backproject",
     "supcg_precondition", "supcg_tv_tbar", "supcg_superiorize", "supcg_solve", "supcg_solve_host",
-    "supcg_solve_batched", "supcg_status_string", "LOG_STRIDE", "EXPORTED",
+    "supcg_solve_batched", "supcg_status_string", "LOG_STRIDE", "EXPORTED", "solve_sweep", "SE_AXES",
 ]
 
 LOG_STRIDE = 8
@@ -30,7 +30,7 @@ EXPORTED = ["supcg_create_geometry", "supcg_destroy_geometry", "supcg_project", 
             "supcg_precondition_noalloc", "supcg_cnn_create", "supcg_cnn_destroy", "supcg_cnn_num_params",
             "supcg_cnn_get_params", "supcg_cnn_set_params", "supcg_cnn_forward", "supcg_cnn_gradients",
             "supcg_cnn_train_step", "supcg_solve_trace", "supcg_solve_learned", "supcg_set_tiling",
-            "supcg_get_tiling"]
+            "supcg_get_tiling", "supcg_solve_sweep"]
 KINDS = ["forward", "backward", "fft", "stv", "vector", "cnn"]
 
 _lock = threading.Lock()
@@ -91,6 +91,8 @@ def load(allow_build: bool = True):
         L.supcg_solve_host.argtypes = [vp, vp, vp, C.POINTER(Params), C.POINTER(Report), vp]
         L.supcg_solve_batched.argtypes = [C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), i,
                                           C.POINTER(Params), C.POINTER(Report), vp]
+        L.supcg_solve_sweep.argtypes = [vp, vp, C.POINTER(vp), i, C.POINTER(Params), vp, d, d, vp,
+                                        C.POINTER(Report), vp]
         L.supcg_solve_profiled.argtypes = [vp, vp, vp, C.POINTER(Params), C.POINTER(Report),
                                            C.POINTER(d), C.POINTER(ll), vp]
         L.supcg_kernel_launches.argtypes = []
@@ -395,6 +397,34 @@ def solve_batched(geoms, bs, xs, stream=None, **kw):
     if rc not in (0,) and rc > -4:
         raise SupcgError(rc, "supcg_solve_batched")
     return [r.as_dict() for r in reps]
+
+
+# Semi-axes of the selective-error ellipse as fractions of the image side: 5 cm and
+# 7 cm in the paper's 243 x 0.0752 cm field (Sec. 4.2, Eq. (4.1)).
+SE_AXES = (5.0 / (243 * 0.0752), 7.0 / (243 * 0.0752))
+
+
+def solve_sweep(G, b, params, ref=None, se_axes=SE_AXES, stream=None):
+    """Parameter sweep (supcg_solve_sweep): one solve of (G, b) per dict of
+    parameters in `params` (K, a, gamma, mu, rho differ; the rest shared), all in
+    one batched schedule.  Returns (images [count][ny][nx], reports, SE) with SE
+    [count][max_iter] the selective error of every iteration against `ref`
+    (None without a reference)."""
+    import torch
+    n = len(params)
+    ps = (Params * n)(*[make_params(**q) for q in params])
+    xs = torch.zeros(n, G.ny, G.nx, device=b.device, dtype=torch.float32)
+    X = (C.c_void_p * n)(*[xs[c].data_ptr() for c in range(n)])
+    mi = max(int(ps[0].max_iter), 1)
+    se = torch.zeros(n, mi, device=b.device, dtype=torch.float64) if ref is not None else None
+    reps = (Report * n)()
+    rc = load().supcg_solve_sweep(G.handle, _ptr(b, torch.float32), X, n, ps,
+                                  _ptr(ref, torch.float32) if ref is not None else None,
+                                  float(se_axes[0]), float(se_axes[1]), _ptr(se) if se is not None else None,
+                                  reps, _stream(stream))
+    if rc not in (0,) and rc > -4:
+        raise SupcgError(rc, "supcg_solve_sweep")
+    return xs, [r.as_dict() for r in reps], se
 
 
 # ---------------------------------------------------------------- learned perturbation network

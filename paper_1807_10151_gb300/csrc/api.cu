@@ -759,23 +759,41 @@ static int enqueue_init(Workspace *w, const supcg_params *p, cudaStream_t st)
     return SUPCG_OK;
 }
 
+// Selective-error logging of a sweep (Eq. (4.1)): reference image, per-problem logs, semi-axes in pixels.
+struct SeLog {
+    const float *ref = nullptr;
+    double *logs = nullptr;   // [count][max_iter]
+    double ax = 0.0, ay = 0.0;
+};
+
+// per (nullable): per-problem parameters of a sweep; each problem then takes its S_TV (K, a,
+// gamma) and preconditioner (mu, rho) parameters from per[c] and everything else from p.
 static int run_solve(Workspace *w, const float *const *d_b, float *const *d_x, const supcg_params *p,
                      supcg_report *reps, double *d_log, cudaStream_t st, float *d_trace = nullptr,
-                     supcg_cnn_s *net = nullptr)
+                     supcg_cnn_s *net = nullptr, const supcg_params *per = nullptr, const SeLog *se = nullptr)
 {
     int rc;
     for (int c = 0; c < w->count; ++c) {
         Prob &P = w->hp[c];
+        const supcg_params &q = per ? per[c] : *p;
         P.in_user = d_x[c];
         P.out_user = d_x[c];
         P.in_user2 = d_b[c];
-        P.mu = p->mu;
-        P.rho = p->rho;
+        P.mu = q.mu;
+        P.rho = q.rho;
+        P.stv_own = per ? 1 : 0;
+        P.stv_K = q.K;
+        P.stv_a = q.a;
+        P.stv_gamma = q.gamma;
         P.precond = p->precondition ? 1 : 0;
         P.r2 = p->bayes_r > 0.0 ? p->bayes_r * p->bayes_r : 0.0;
         P.storage = SUPCG_F32;
         P.log = (c == 0) ? d_log : nullptr;
         P.trace = (c == 0) ? d_trace : nullptr;
+        P.se_ref = (se && se->ref) ? se->ref : nullptr;
+        P.se_log = P.se_ref ? se->logs + (size_t)c * std::max(1, p->max_iter) : nullptr;
+        P.se_ax = se ? se->ax * P.nx : 0.0;
+        P.se_ay = se ? se->ay * P.ny : 0.0;
     }
     rc = ws_upload(w, st);
     for (int c = 0; c < w->count; ++c) w->hp[c].storage = w->geoms[c]->storage;
@@ -975,6 +993,42 @@ extern "C" int supcg_solve_batched(const supcg_geometry *gs, const float *const 
         owner->batch_key = key;
     }
     return run_solve(owner->ws_batch, d_b, d_x, p, reps, nullptr, (cudaStream_t)stream);
+}
+
+extern "C" int supcg_solve_sweep(supcg_geometry g, const float *d_b, float *const *d_x, int count,
+                                 const supcg_params *ps, const float *d_ref, double se_ax, double se_ay,
+                                 double *d_se, supcg_report *reps, void *stream)
+{
+    if (!g || !d_b || !d_x || !ps || !reps || count < 1) return SUPCG_ERR_ARG;
+    if (d_ref && (!d_se || !(se_ax > 0.0) || !(se_ay > 0.0))) return SUPCG_ERR_ARG;
+    const supcg_params &p0 = ps[0];
+    auto same_mu = [](double u, double v) { return (isnan(u) && isnan(v)) || u == v; };
+    for (int c = 0; c < count; ++c) {
+        if (!d_x[c]) return SUPCG_ERR_ARG;
+        const supcg_params &q = ps[c];
+        int rc = check_params(&q);
+        if (rc) return rc;
+        // what is not swept is shared: the launch schedule and the loop control
+        if (q.perturb != p0.perturb || q.precondition != p0.precondition || q.eps != p0.eps ||
+            q.max_iter != p0.max_iter || q.max_trials != p0.max_trials || q.graph != p0.graph ||
+            q.bayes_r != p0.bayes_r || !same_mu(q.bayes_mu, p0.bayes_mu) || (p0.perturb && q.K < 1))
+            return SUPCG_ERR_ARG;
+    }
+    std::vector<supcg_geometry> key(count, g);
+    if (!g->ws_batch || g->batch_key != key) {
+        free_ws(g->ws_batch);
+        int rc = ws_create(key, &g->ws_batch);
+        if (rc) return rc;
+        g->batch_key = key;
+    }
+    std::vector<const float *> bs(count, d_b);
+    SeLog se;
+    se.ref = d_ref;
+    se.logs = d_se;
+    se.ax = se_ax;
+    se.ay = se_ay;
+    return run_solve(g->ws_batch, bs.data(), d_x, &p0, reps, nullptr, (cudaStream_t)stream, nullptr, nullptr, ps,
+                     d_ref ? &se : nullptr);
 }
 
 extern "C" const char *supcg_status_string(int status)

@@ -181,6 +181,12 @@ struct Prob {
     FFTPlan fx, fy;
     double mu, rho;
     double r2;             // r^2 of the Bayesian criterion (Eq. (2.3)); 0: least squares
+    int stv_own;           // 1: S_TV uses stv_K, stv_a, stv_gamma below (a parameter sweep), else its arguments
+    int stv_K;
+    double stv_a, stv_gamma;
+    const float *se_ref;   // nullable: reference image [ny][nx] of the selective error of Eq. (4.1)
+    double *se_log;        // SE of x_{k+1/2} of while-body k (1-based) at se_log[k - 1] (with se_ref)
+    double se_ax, se_ay;   // semi-axes of the SE ellipse, in pixels (horizontal, vertical)
     double gray_scale;     // ds / (V nx ny d^2): sum of b times this is the gray-level estimate
     int precond;           // 1: M of Eq. (3.2); 0: M = I
     int storage;           // SUPCG_F32 / SUPCG_BF16 element type of in_user / out_user

@@ -699,10 +699,12 @@ __global__ void __launch_bounds__(kBwdThreads, 3) k_backward(const Prob *__restr
     if (!last_block(&P.tilecnt[tile], kBwdViewParts, &last_sh)) return;
     float *out = (mode == BWD_G) ? P.g : (mode == BWD_H ? P.h : P.g);
     // Bayesian criterion (Eq. (2.3)): g = r^2 R^T r + (x - mu_X), h = r^2 R^T q + p, and
-    // ||x - mu_X||^2 for f
+    // ||x - mu_X||^2 for f.  With a reference image, the selective error of Eq. (4.1) of
+    // x = x_{k+1/2} over the centred ellipse S (this pass reads x anyway).
     const bool bayes = mode != BWD_PLAIN && P.r2 > 0.0;
+    const bool want_se = mode == BWD_G && P.se_ref != nullptr && !P.sc->init;
     const double muX = bayes ? P.sc->muX : 0.0;
-    double sx = 0.0;
+    double sx = 0.0, sse = 0.0;
     if (grp == 0)
 #pragma unroll
         for (int e = 0; e < kBwdPixPerThread; ++e) {
@@ -721,20 +723,37 @@ __global__ void __launch_bounds__(kBwdThreads, 3) k_backward(const Prob *__restr
                     }
                 }
                 out[o] = (float)v;
+                if (want_se) {   // pixel centre inside the ellipse (FP64, as the definition)
+                    const double ex = ((double)j - 0.5 * (P.nx - 1)) / P.se_ax;
+                    const double ey = ((double)i - 0.5 * (P.ny - 1)) / P.se_ay;
+                    if (ex * ex + ey * ey <= 1.0) {
+                        const double dr = (double)P.x[o] - (double)P.se_ref[(size_t)i * P.nx + j];
+                        sse += dr * dr;
+                    }
+                }
             }
         }
     if (t == 0) P.tilecnt[tile] = 0;   // ready for the next launch
-    if (!bayes || mode != BWD_G) return;
-    // f = r^2 ||R x - b||^2 + ||x - mu_X||^2: the tiles' sums, added by the last tile to finish
+    if (!(bayes && mode == BWD_G) && !want_se) return;
+    // the tiles' sums, added in tile order by the last tile to finish: f = r^2 ||R x - b||^2 +
+    // ||x - mu_X||^2, and SE = sqrt(sum over S)
     const double bs = block_sum<kBwdThreads>(sx, comb);
+    const double be = block_sum<kBwdThreads>(sse, comb);
     const int ntiles = (prefix[pi + 1] - prefix[pi]) / kBwdViewParts;
-    if (t == 0) P.partial[tile] = bs;
+    if (t == 0) {
+        P.partial[tile] = bs;
+        P.partial[ntiles + tile] = be;
+    }
     if (last_block(&P.counter[4], ntiles, &last_sh)) {
         const double tot = block_sum_array<kBwdThreads>(P.partial, ntiles, comb);
+        const double tse = block_sum_array<kBwdThreads>(P.partial + ntiles, ntiles, comb);
         if (t == 0) {
             Scal *sc = P.sc;
-            sc->f = P.r2 * sc->f_ls + tot;
-            if (sc->init) sc->f0 = sc->f;
+            if (bayes) {
+                sc->f = P.r2 * sc->f_ls + tot;
+                if (sc->init) sc->f0 = sc->f;
+            }
+            if (want_se) P.se_log[sc->k] = sqrt(tse);   // body sc->k + 1 (k counts finished bodies)
             P.counter[4] = 0;
         }
     }

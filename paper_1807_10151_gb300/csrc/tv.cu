@@ -122,8 +122,9 @@ __device__ __forceinline__ double phase_sum(const Prob &P, int nb, int slot, int
 // S_TV(x, l, a, gamma, K), Algorithm 1, in place on P.x (one cooperative launch).
 // trials_out (nullable): [count][K] trials of every nonascending step.
 __global__ void __launch_bounds__(kTvThreads) k_stv(const Prob *__restrict__ probs, const int *__restrict__ prefix,
-                                                    int count, int K, double a, double gamma, long long max_trials,
-                                                    int *trials_out, int want_snorm, const float *__restrict__ dir)
+                                                    int count, int K_arg, double a_arg, double gamma_arg,
+                                                    long long max_trials, int *trials_out, int want_snorm,
+                                                    const float *__restrict__ dir)
 {
     __shared__ double red[40];
     __shared__ int flag;
@@ -134,6 +135,9 @@ __global__ void __launch_bounds__(kTvThreads) k_stv(const Prob *__restrict__ pro
     const Prob &P = probs[pi];
     Scal *sc = P.sc;
     if (sc->done) return;
+    // a parameter sweep gives every problem its own K, a, gamma
+    const int K = P.stv_own ? P.stv_K : K_arg;
+    const double a = P.stv_own ? P.stv_a : a_arg, gamma = P.stv_own ? P.stv_gamma : gamma_arg;
     const int nb = prefix[pi + 1] - prefix[pi];
     const int nx = P.nx, ny = P.ny, ld = P.nxp;
     const int n = ny * nx;   // < 2^31 (each side <= 16384)

@@ -54,6 +54,32 @@ def ellipse_phantom(N: int, n_ellipses: int, seed: int, nx: int | None = None, n
     return img.astype(dtype)
 
 
+def head_standin(N: int, seed: int, n_inner: int = 8) -> np.ndarray:
+    """Stand-in for the head phantom of Sec. 4.1 (not available): a dense
+    elliptical annulus ("skull", value 1.0, outer semi-axes 0.44 x 0.48 of the
+    unit square, 0.035 thick) around a soft-tissue interior (0.2) holding
+    n_inner small low-contrast ellipses (0.2 +- 0.01 .. 0.05), values at pixel
+    centres."""
+    rng = np.random.default_rng(seed)
+    xj, yi = pixel_centres(N, N, 1.0 / N)
+    X, Y = np.meshgrid(xj, yi)
+    img = np.zeros((N, N))
+    outer = (X / 0.44) ** 2 + (Y / 0.48) ** 2 <= 1.0
+    inner = (X / 0.405) ** 2 + (Y / 0.445) ** 2 <= 1.0
+    img[outer] = 1.0
+    img[inner] = 0.2
+    for _ in range(n_inner):
+        r, t = 0.25 * np.sqrt(rng.uniform()), rng.uniform(0.0, 2.0 * np.pi)
+        cx, cy = r * np.cos(t), r * np.sin(t)
+        ax, ay, ang = rng.uniform(0.02, 0.08), rng.uniform(0.02, 0.08), rng.uniform(0.0, np.pi)
+        val = 0.2 + rng.choice([-1.0, 1.0]) * rng.uniform(0.01, 0.05)
+        ca, sa = np.cos(ang), np.sin(ang)
+        u = (X - cx) * ca + (Y - cy) * sa
+        v = -(X - cx) * sa + (Y - cy) * ca
+        img[((u / ax) ** 2 + (v / ay) ** 2 <= 1.0) & inner] = val
+    return img
+
+
 def textured_background(N: int, seed: int, sigma_px: float = 8.0, amplitude: float = 0.05,
                         support_radius: float = 0.45) -> np.ndarray:
     """Seeded white noise blurred by a Gaussian of sigma_px pixels (FFT
