@@ -134,10 +134,12 @@ def make_problem(rank, device):
     import torch
     import paper_1807_10151_gb300 as S
     from paper_1807_10151_gb300 import synth
+    from paper_1807_10151_gb300 import replicas
     G = S.Geometry(WL["N"], n_views=WL["V"], n_bins=WL["U"])
-    x_true = synth.ellipse_phantom(WL["N"], WL["n_ell"], WL["seed"] + rank)
+    seed, noise_seed = replicas.rank_seeds(rank, WL["seed"], WL["noise_seed"])   # each replica its own problem
+    x_true = synth.ellipse_phantom(WL["N"], WL["n_ell"], seed)
     clean = G.project(torch.tensor(x_true, dtype=torch.float32, device=device)).double().cpu().numpy()
-    b = synth.poisson_log(clean, WL["I0"], WL["noise_seed"] + rank).astype(np.float32)
+    b = synth.poisson_log(clean, WL["I0"], noise_seed).astype(np.float32)
     return G, b
 
 
@@ -550,12 +552,9 @@ def main():
         barrier()
     launches = S.supcg_kernel_launches() - launches0
     assert rep["status"] == 0 and rep["iters"] == args.steps, rep
-    ms = ev0.elapsed_time(ev1)
-    t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    if dist:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = args.steps * world / (ms_max / 1000.0)
+    from paper_1807_10151_gb300 import replicas
+    ms_max = 1000.0 * replicas.slowest(ev0.elapsed_time(ev1) / 1000.0, dist, dev)   # slowest rank
+    value = replicas.job_rate(args.steps, world, ms_max / 1000.0)
 
     # end to end through the host-buffer entry point (copies in the timed region)
     b_pin = torch.tensor(b_host).pin_memory()
@@ -565,10 +564,7 @@ def main():
     rep_h = G.solve_host(b_pin.numpy(), x_pin.numpy(), **solve_kw(args.steps))
     t_e2e = time.perf_counter() - t0
     assert rep_h["status"] == 0, rep_h
-    te = torch.tensor([t_e2e], dtype=torch.float64, device=dev)
-    if dist:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_value = args.steps * world / float(te.item())
+    e2e_value = replicas.job_rate(args.steps, world, replicas.slowest(t_e2e, dist, dev))
 
     # per-kernel breakdown of the same solve (events around every launch)
     _, rep_p, kinds = G.solve_profiled(b, **solve_kw(args.steps, graph=False))
