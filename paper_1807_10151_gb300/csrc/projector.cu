@@ -28,6 +28,8 @@ extern __shared__ __align__(128) float proj_dyn[];
 
 static_assert(kRowsPerChunk % 8 == 0, "chunks start at multiples of the 8-row fold groups");
 
+constexpr int kFwdBufs = 1;   // forward projector: staged boxes per warp (1: more resident warps hide the copies)
+
 // ============================================================ forward
 // Inner loop over the rows [o0, o0 + rows) of one staged box.  A ray meets a
 // row in the inner indices within hwq (half-width + margin) of its centre:
@@ -250,15 +252,15 @@ __device__ __forceinline__ void fwd_ray2(const Prob &P, const ViewP &vp, const C
     const int c_first = w_hi >= w_lo ? w_lo / RC : 0;
     const int nch = w_hi >= w_lo ? w_hi / RC - c_first + 1 : 0;   // chunks with at least one of the warp's rows
     if (lane == 0) {
-        for (int ci = 0; ci < 2 && ci < nch; ++ci) {
+        for (int ci = 0; ci < kFwdBufs && ci < nch; ++ci) {
             const int c = c_first + ci;
             mbar_expect_tx(&bars[ci], box_elems * 4);
             tma_load_2d(proj_dyn + patch0 + ci * box_elems, tm, fwd_box_start(vp, tf, tl, c * RC), c * RC, &bars[ci]);
         }
     }
     for (int ci = 0; ci < nch; ++ci) {
-        const int buf = ci & 1, c = c_first + ci;
-        const bool ok = mbar_wait(&bars[buf], (ci >> 1) & 1);
+        const int buf = ci % kFwdBufs, c = c_first + ci;
+        const bool ok = mbar_wait(&bars[buf], (ci / kFwdBufs) & 1);
         const int o0 = c * RC;
         const int rows = min(RC, n_outer - o0);
         const int rb = max(0, w_lo - o0), re = min(rows, w_hi - o0 + 1);
@@ -289,16 +291,16 @@ __device__ __forceinline__ void fwd_ray2(const Prob &P, const ViewP &vp, const C
         if (__any_sync(0xffffffffu, !ok)) {
             *timed_out = 1;
             if (lane == 0) {   // bounded waits for the copies still in flight: chunk ci's and, if issued, ci + 1's
-                (void)mbar_wait(&bars[buf], (ci >> 1) & 1);
-                if (ci + 1 < nch) (void)mbar_wait(&bars[buf ^ 1], ((ci + 1) >> 1) & 1);
+                for (int cj = ci; cj < ci + kFwdBufs && cj < nch; ++cj)   // this chunk and those issued after it
+                    (void)mbar_wait(&bars[cj % kFwdBufs], (cj / kFwdBufs) & 1);
             }
             break;
         }
         __syncwarp();
-        if (lane == 0 && ci + 2 < nch) {
+        if (lane == 0 && ci + kFwdBufs < nch) {
             mbar_expect_tx(&bars[buf], box_elems * 4);
-            tma_load_2d(proj_dyn + patch0 + buf * box_elems, tm, fwd_box_start(vp, tf, tl, (c + 2) * RC), (c + 2) * RC,
-                        &bars[buf]);
+            tma_load_2d(proj_dyn + patch0 + buf * box_elems, tm, fwd_box_start(vp, tf, tl, (c + kFwdBufs) * RC),
+                        (c + kFwdBufs) * RC, &bars[buf]);
         }
     }
 #pragma unroll
@@ -307,11 +309,11 @@ __device__ __forceinline__ void fwd_ray2(const Prob &P, const ViewP &vp, const C
 
 constexpr int kFwdThreads = 64;   // two warps of 64 rays: 128 bins per block at most
 
-__global__ void __launch_bounds__(kFwdThreads, 8) k_forward(const Prob *__restrict__ probs, const int *__restrict__ prefix,
+__global__ void __launch_bounds__(kFwdThreads, 10) k_forward(const Prob *__restrict__ probs, const int *__restrict__ prefix,
                                                          int count, int which, int mode)
 {
-    // proj_dyn: [warp][2][kRowsPerChunk][BW]
-    __shared__ __align__(8) uint64_t bars[2 * (kFwdThreads / 32)];   // two per warp
+    // proj_dyn: [warp][kFwdBufs][kRowsPerChunk][BW]
+    __shared__ __align__(8) uint64_t bars[kFwdBufs * (kFwdThreads / 32)];   // one per staged box
     __shared__ double red[40];
     __shared__ int flag;
     __shared__ int bad_sh;
@@ -329,8 +331,8 @@ __global__ void __launch_bounds__(kFwdThreads, 8) k_forward(const Prob *__restri
     const int n_outer = classB ? P.nx : P.ny, n_inner = classB ? P.ny : P.nx;
     const CUtensorMap *tm = &P.tm[which * 2 + (classB ? 1 : 0)];
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
-    const int patch0 = warp * 2 * kRowsPerChunk * P.BW;   // this warp's two boxes in proj_dyn
-    uint64_t *wbars = bars + 2 * warp;
+    const int patch0 = warp * kFwdBufs * kRowsPerChunk * P.BW;   // this warp's boxes in proj_dyn
+    uint64_t *wbars = bars + kFwdBufs * warp;
 
     const int u_first = tile * P.BU;
     const int u_last = min(P.U, u_first + P.BU) - 1;
@@ -340,7 +342,7 @@ __global__ void __launch_bounds__(kFwdThreads, 8) k_forward(const Prob *__restri
     const float tf = bin_pos(min(uw0, u_last), P.uc), tl = bin_pos(uw1, P.uc);
 
     if (t == 0) bad_sh = 0;
-    if (t < 2 * (kFwdThreads / 32)) mbar_init(&bars[t], 1);
+    if (t < kFwdBufs * (kFwdThreads / 32)) mbar_init(&bars[t], 1);
     if (t == 0) fence_mbar_init();
     __syncthreads();
 
@@ -425,10 +427,10 @@ int launch_forward(const Launch &L, int which, int mode)
 {
     static int max_smem_set = 0;
     // every problem's BW <= 256, so the warps' box buffers never exceed this size
-    const int smem = (kFwdThreads / 32) * 2 * kRowsPerChunk * L.bw_max * 4;
+    const int smem = (kFwdThreads / 32) * kFwdBufs * kRowsPerChunk * L.bw_max * 4;
     if (!max_smem_set) {
         SUPCG_CUDA_TRY(cudaFuncSetAttribute(k_forward, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            (kFwdThreads / 32) * 2 * kRowsPerChunk * 256 * 4));
+                                            (kFwdThreads / 32) * kFwdBufs * kRowsPerChunk * 256 * 4));
         max_smem_set = 1;
     }
     k_forward<<<L.blocks, kFwdThreads, smem, L.st>>>(L.probs, L.prefix, L.count, which, mode);
