@@ -2,13 +2,13 @@
 // Eq. (2.2): normal equations R^T R x = R^T b).
 //
 // Forward (ray-driven, gather over pixels).  A block owns one view and up to
-// 128 consecutive bins, one ray per thread.  Views are split in two classes:
+// 128 consecutive bins, two rays per thread.  Views are split in two classes:
 // class A (|cos| >= |sin|) walks image rows, class B walks image columns, and
 // class B reads the transposed image x^T so that both classes walk contiguous
 // rows of the array they read.  Each warp stages chunks of kRowsPerChunk rows
-// x BW columns covering its 32 rays in shared memory by 2-D TMA loads (its own
-// double buffer, one mbarrier per buffer), and only the rows its rays can
-// meet.  For every row a ray can only cross the two (three near the diagonal)
+// x BW columns covering its 64 rays in shared memory by 2-D TMA loads (its own
+// kFwdBufs boxes, one mbarrier each), and only the rows its rays can meet.
+// For every row a ray can only cross the two (three near the diagonal)
 // columns nearest to its centre; each is weighted by the shared trapezoid.
 //
 // Backward (pixel-driven, gather over bins, no atomics).  A tile of 32 x 32
@@ -220,7 +220,7 @@ __device__ __forceinline__ void fwd_row_range(const ViewP &vp, float base, int n
 }
 
 // Two rays per lane (u and u + 32: 64 consecutive bins per warp); each warp
-// runs its own double-buffered pipeline of kRowsPerChunk-row boxes (BW columns
+// runs its own pipeline of kFwdBufs kRowsPerChunk-row boxes (BW columns
 // covering its 64 rays), so warps never wait for one another.  The warp walks
 // only the chunks holding rows that one of its rays can meet, and within them
 // only those rows.  Rays past the block's last bin follow the last ray (inside
