@@ -403,13 +403,21 @@ static int ws_create(const std::vector<supcg_geometry> &gs, Workspace **out)
     }
     if (w->smem_rows > 200 * 1024 || w->smem_cols > 200 * 1024) { delete w; return SUPCG_ERR_UNSUPPORTED; }
     // co-residency of the cooperative S_TV launch: scale down to the device capacity
+    // (proportional shares, at least one block each; the rounding-up of the minimum is
+    // taken back from the largest shares)
     if (stv_want > stv_cap) {
         long long tot = 0;
         for (int c = 0; c < w->count; ++c) {
-            nb[KT_STV][c] = (int)std::max(1LL, (long long)nb[KT_STV][c] * (stv_cap - w->count) / stv_want);
+            nb[KT_STV][c] = (int)std::max(1LL, (long long)nb[KT_STV][c] * stv_cap / stv_want);
             tot += nb[KT_STV][c];
         }
-        if (tot > stv_cap) { delete w; return SUPCG_ERR_UNSUPPORTED; }
+        while (tot > stv_cap) {
+            int big = 0;
+            for (int c = 1; c < w->count; ++c)
+                if (nb[KT_STV][c] > nb[KT_STV][big]) big = c;
+            --nb[KT_STV][big];
+            --tot;
+        }
     }
     std::vector<int> hprefix(KT_COUNT * (w->count + 1));
     for (int kt = 0; kt < KT_COUNT; ++kt) {

@@ -121,7 +121,7 @@ __device__ __forceinline__ double phase_sum(const Prob &P, int nb, int slot, int
 
 // S_TV(x, l, a, gamma, K), Algorithm 1, in place on P.x (one cooperative launch).
 // trials_out (nullable): [count][K] trials of every nonascending step.
-__global__ void __launch_bounds__(kTvThreads) k_stv(const Prob *__restrict__ probs, const int *__restrict__ prefix,
+__global__ void __launch_bounds__(kTvThreads, 3) k_stv(const Prob *__restrict__ probs, const int *__restrict__ prefix,
                                                     int count, int K_arg, double a_arg, double gamma_arg,
                                                     long long max_trials, int *trials_out, int want_snorm,
                                                     const float *__restrict__ dir)
@@ -130,6 +130,8 @@ __global__ void __launch_bounds__(kTvThreads) k_stv(const Prob *__restrict__ pro
     __shared__ int flag;
     __shared__ double sh_inv;   // grid-uniform FP64 scalars: computed by thread 0, read by all
     __shared__ float sh_c;
+    __shared__ float sh_t[32][33];   // tile transposes of x
+    bool xt_done = false;            // the last step wrote x^T
     int local;
     const int pi = find_problem(prefix, count, blockIdx.x, &local);
     const Prob &P = probs[pi];
@@ -313,12 +315,40 @@ __global__ void __launch_bounds__(kTvThreads) k_stv(const Prob *__restrict__ pro
         total_trials += trials;
         if (!ok) break;
         if (trials_out && local == 0 && threadIdx.x == 0) trials_out[(size_t)pi * K + step] = (int)trials;
-        for (int e = e0; e < n; e += stride) {   // y <- y~
-            const int i = e / nx, j = e - i * nx;
-            const size_t p = (size_t)i * ld + j;
-            x[p] = __fmaf_rn(c, tb[p], x[p]);
+        if (step == K - 1 && !want_snorm) {
+            // the last step: y <- y~ on 32 x 32 tiles this block owns, written in both layouts
+            // (x^T for the forward projector); no block reads another's pixels after it, so no
+            // grid barrier follows
+            const int tiles_j = (nx + 31) / 32, tiles = ((ny + 31) / 32) * tiles_j;
+            const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 256 threads: 32 x 8
+            for (int tile = local; tile < tiles; tile += nb) {
+                const int ti = tile / tiles_j, tj = tile - ti * tiles_j;
+                for (int r = ty; r < 32; r += 8) {
+                    const int i = ti * 32 + r, j = tj * 32 + tx;
+                    float v = 0.0f;
+                    if (i < ny && j < nx) {
+                        const size_t p = (size_t)i * ld + j;
+                        v = __fmaf_rn(c, tb[p], x[p]);
+                        x[p] = v;
+                    }
+                    sh_t[r][tx] = v;
+                }
+                __syncthreads();
+                for (int r = ty; r < 32; r += 8) {
+                    const int j = tj * 32 + r, i = ti * 32 + tx;
+                    if (j < nx && i < ny) P.xT[(size_t)j * P.nyp + i] = sh_t[tx][r];
+                }
+                __syncthreads();
+            }
+            xt_done = true;
+        } else {
+            for (int e = e0; e < n; e += stride) {   // y <- y~
+                const int i = e / nx, j = e - i * nx;
+                const size_t p = (size_t)i * ld + j;
+                x[p] = __fmaf_rn(c, tb[p], x[p]);
+            }
+            ok = coop_barrier(P.bar, nb, &sc->status, &flag);
         }
-        ok = coop_barrier(P.bar, nb, &sc->status, &flag);
         tv_last = tv_t;
     }
     double sn = 0.0;
@@ -339,13 +369,12 @@ __global__ void __launch_bounds__(kTvThreads) k_stv(const Prob *__restrict__ pro
         sc->tv_half = (K > 0) ? tv_last : tv_first;
         sc->snorm2 = sn;
     }
-    // x^T of x_{k+1/2} for the forward projector's column-walking views (after the last
-    // barrier every block sees the final x)
-    if (ok) {
-        __shared__ float sh[32][33];
+    // x^T of x_{k+1/2} for the forward projector's column-walking views, unless the last
+    // step wrote it (after the last barrier every block sees the final x)
+    if (ok && !xt_done) {
         const int tiles = ((ny + 31) / 32) * ((nx + 31) / 32);
         for (int tile = local; tile < tiles; tile += nb) {
-            transpose_tile(x, ld, P.xT, P.nyp, ny, nx, tile, sh);
+            transpose_tile(x, ld, P.xT, P.nyp, ny, nx, tile, sh_t);
             __syncthreads();
         }
     }
