@@ -137,6 +137,7 @@ struct supcg_geometry_s {
     FFTPlan fx, fy;
     ViewP *dviews = nullptr;
     int *dvlist = nullptr;
+    int *dtorder = nullptr;         // forward tile order, ceil(U / 32) entries
     double2 *dtwx = nullptr, *dtwy = nullptr;
     Workspace *ws_ops = nullptr;    // standalone operators, `ops_batch` images
     int ops_batch = 0;
@@ -153,6 +154,23 @@ static int fwd_box_width(const supcg_geometry_s *g)
     for (const ViewP &vp : g->views)
         span = std::max(span, fabs((double)vp.a_tau) * 63.0 + fabs((double)vp.b_o) * (kRowsPerChunk - 1));
     return round_up((int)ceil(span + 11.0), 4);
+}
+
+// Forward tiles in launch order: by the distance of the tile's middle bin from
+// the detector centre, so that the tiles whose rays cross the most rows start
+// first and the grid ends on short blocks.
+static int upload_tile_order(supcg_geometry_s *g)
+{
+    std::vector<int> ord(g->ntu);
+    std::vector<double> dist(g->ntu);
+    const double uc = 0.5 * (g->U - 1) - g->off / g->ds;
+    for (int t = 0; t < g->ntu; ++t) {
+        ord[t] = t;
+        dist[t] = fabs(0.5 * (t * g->BU + std::min(g->U, (t + 1) * g->BU) - 1) - uc);
+    }
+    std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return dist[a] < dist[b]; });
+    SUPCG_CUDA_TRY(cudaMemcpy(g->dtorder, ord.data(), sizeof(int) * g->ntu, cudaMemcpyHostToDevice));
+    return SUPCG_OK;
 }
 
 static void free_ws(Workspace *&w)
@@ -307,7 +325,8 @@ extern "C" int supcg_create_geometry(int nx, int ny, double pixel_size, int n_vi
     g->fx.tw = g->dtwx;
     g->fy.tw = g->dtwy;
     if (cudaMalloc(&g->dviews, sizeof(ViewP) * n_views) != cudaSuccess ||
-        cudaMalloc(&g->dvlist, sizeof(int) * n_views) != cudaSuccess) {
+        cudaMalloc(&g->dvlist, sizeof(int) * n_views) != cudaSuccess ||
+        cudaMalloc(&g->dtorder, sizeof(int) * ((n_bins + 31) / 32)) != cudaSuccess) {
         supcg_destroy_geometry(g);
         return SUPCG_ERR_NOMEM;
     }
@@ -315,6 +334,10 @@ extern "C" int supcg_create_geometry(int nx, int ny, double pixel_size, int n_vi
         cudaMemcpy(g->dvlist, g->vlist.data(), sizeof(int) * n_views, cudaMemcpyHostToDevice) != cudaSuccess) {
         supcg_destroy_geometry(g);
         return SUPCG_ERR_CUDA;
+    }
+    if ((rc = upload_tile_order(g))) {
+        supcg_destroy_geometry(g);
+        return rc;
     }
     *out = g;
     return SUPCG_OK;
@@ -329,6 +352,8 @@ extern "C" int supcg_set_tiling(supcg_geometry g, int fwd_bins_per_block)
     g->BU = fwd_bins_per_block;
     g->BW = bw;
     g->ntu = (g->U + g->BU - 1) / g->BU;
+    int rc = upload_tile_order(g);
+    if (rc) return rc;
     // workspaces hold launch shapes and TMA boxes of the old tiling
     free_ws(g->ws_ops);
     free_ws(g->ws_solve);
@@ -353,6 +378,7 @@ extern "C" int supcg_destroy_geometry(supcg_geometry g)
     free_ws(g->ws_batch);
     if (g->dviews) cudaFree(g->dviews);
     if (g->dvlist) cudaFree(g->dvlist);
+    if (g->dtorder) cudaFree(g->dtorder);
     if (g->dtwx) cudaFree(g->dtwx);
     if (g->dtwy) cudaFree(g->dtwy);
     delete g;
@@ -463,6 +489,7 @@ static int ws_create(const std::vector<supcg_geometry> &gs, Workspace **out)
         P.C = (double2 *)ptrs[11]; P.sc = (Scal *)ptrs[12]; P.partial = (double *)ptrs[13];
         P.counter = (unsigned *)ptrs[14]; P.bar = (unsigned *)ptrs[15]; P.Dtab = (double *)ptrs[16];
         P.bsplit = (double *)ptrs[17]; P.tilecnt = (unsigned *)ptrs[18];
+        P.torder = g->dtorder;
         P.nx = g->nx; P.ny = g->ny; P.V = g->V; P.U = g->U;
         P.nxp = g->nxp; P.nyp = g->nyp; P.Up = g->Up;
         P.BU = g->BU; P.BW = g->BW; P.ntu = g->ntu; P.nA = g->nA; P.nB = g->nB;
