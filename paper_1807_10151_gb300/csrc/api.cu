@@ -80,7 +80,7 @@ static int fft_factor(int n, int *rad)
 } // namespace supcg
 
 // ------------------------------------------------------------------ objects
-enum { KT_FWD, KT_BWD, KT_VEC, KT_TR, KT_ROWS, KT_COLS, KT_SINO, KT_STV, KT_TV, KT_COUNT };
+enum { KT_FWD, KT_BWD, KT_BWD2, KT_VEC, KT_TR, KT_ROWS, KT_COLS, KT_SINO, KT_STV, KT_TV, KT_COUNT };
 
 struct Workspace {
     int count = 0;
@@ -408,7 +408,8 @@ static int ws_create(const std::vector<supcg_geometry> &gs, Workspace **out)
     for (int c = 0; c < w->count; ++c) {
         const supcg_geometry g = gs[c];
         nb[KT_FWD][c] = g->V * g->ntu;
-        nb[KT_BWD][c] = kBwdViewParts * ((g->ny + kBwdTileI - 1) / kBwdTileI) * ((g->nx + kBwdTileJ - 1) / kBwdTileJ);
+        nb[KT_BWD][c] = backward_blocks(g->nx, g->ny, 0);
+        nb[KT_BWD2][c] = backward_blocks(g->nx, g->ny, 1);
         nb[KT_VEC][c] = (int)(((long long)g->ny * g->nxp + 1023) / 1024);
         nb[KT_TR][c] = ((g->ny + 31) / 32) * ((g->nx + 31) / 32);
         // FFT: enough blocks to fill the device, each a few row pairs / stored columns
@@ -473,7 +474,8 @@ static int ws_create(const std::vector<supcg_geometry> &gs, Workspace **out)
         const size_t sizes[] = {img * 4, imgT * 4, img * 4, imgT * 4, img * 4, img * 4, img * 4, img * 4,
                                 sino * 4, sino * 4, sino * 4, (size_t)g->ny * g->nx * 16, sizeof(Scal),
                                 npart * 8, 16 * 4, 4 * 4, (size_t)(g->ny / 2 + 1) * (g->nx / 2 + 1) * 8,
-                                (size_t)kBwdViewParts * img * 8, (size_t)nb[KT_BWD][c] * 4};
+                                2 * (size_t)kBwdViewParts * img * 8,
+                                (size_t)std::max(nb[KT_BWD][c], nb[KT_BWD2][c]) * 4};
         size_t total = 0;
         for (size_t s : sizes) total += al(s);
         char *base = nullptr;
@@ -763,7 +765,9 @@ static int enqueue_body(Workspace *w, const supcg_params *p, cudaStream_t st, in
     else                                                                        // (S_TV writes x^T itself)
         LAUNCH(SUPCG_KIND_VECTOR, st, launch_transpose(w->L(KT_TR, st), 0));
     LAUNCH(SUPCG_KIND_FORWARD, st, launch_forward(w->L(KT_FWD, st), 0, FWD_RESID));   // r = R x - b, f
-    LAUNCH(SUPCG_KIND_BACKWARD, st, launch_backward(w->L(KT_BWD, st), BWD_G, w->bwin));         // g = R^T r
+    // g = R^T r, and h = R^T q of the previous step (A p for this step's beta; the previous alpha
+    // took p^T A p from ||q||^2), one pass over the views for both
+    LAUNCH(SUPCG_KIND_BACKWARD, st, launch_backward2(w->L(KT_BWD2, st), w->bwin));
     if (p->precondition) {                                                      // z = M g; its last pass
         if ((rc = enqueue_precond_k(w, st))) return rc;                         // also forms beta
     } else {
@@ -771,7 +775,6 @@ static int enqueue_body(Workspace *w, const supcg_params *p, cudaStream_t st, in
     }
     LAUNCH(SUPCG_KIND_VECTOR, st, launch_pupdate(w->L(KT_TR, st)));             // p = -z + beta p, g^T p, p^T
     LAUNCH(SUPCG_KIND_FORWARD, st, launch_forward(w->L(KT_FWD, st), 1, FWD_NORM));    // q = R p, p^T h, alpha
-    LAUNCH(SUPCG_KIND_BACKWARD, st, launch_backward(w->L(KT_BWD, st), BWD_H, w->bwin));         // h = R^T q
     LAUNCH(SUPCG_KIND_VECTOR, st, launch_log(w->L(KT_VEC, st)));                // k <- k + 1
     return SUPCG_OK;
 }
@@ -788,8 +791,7 @@ static int enqueue_init(Workspace *w, const supcg_params *p, cudaStream_t st)
         LAUNCH(SUPCG_KIND_VECTOR, st, launch_beta(w->L(KT_VEC, st)));
     }
     LAUNCH(SUPCG_KIND_VECTOR, st, launch_pupdate(w->L(KT_TR, st)));
-    LAUNCH(SUPCG_KIND_FORWARD, st, launch_forward(w->L(KT_FWD, st), 1, FWD_NORM));
-    LAUNCH(SUPCG_KIND_BACKWARD, st, launch_backward(w->L(KT_BWD, st), BWD_H, w->bwin));
+    LAUNCH(SUPCG_KIND_FORWARD, st, launch_forward(w->L(KT_FWD, st), 1, FWD_NORM));   // (h = A p: next pass)
     LAUNCH(SUPCG_KIND_VECTOR, st, launch_end_init(w->L(KT_VEC, st)));
     return SUPCG_OK;
 }

@@ -198,7 +198,7 @@ struct Prob {
     float *r, *q, *bpad;
     double2 *C;            // FFT scratch [ny][nx] (FP64 complex)
     double *Dtab;          // preconditioner diagonal h(w_r) at (min(k1, ny-k1), min(k2, nx-k2)): [ny/2+1][nx/2+1]
-    double *bsplit;        // backprojector: each view part's pixel sums [kBwdViewParts][ny][nxp]
+    double *bsplit;        // backprojector: each sinogram's and view part's pixel sums [2][kBwdViewParts][ny][nxp]
     unsigned *tilecnt;     // backprojector: parts finished per tile (reset by the last one)
     Scal *sc;
     double *partial;       // reduction partials (>= 2 * max blocks per kernel)
@@ -402,6 +402,8 @@ struct Launch {
 
 int launch_forward(const Launch &L, int which, int mode);
 int launch_backward(const Launch &L, int mode, int bwin);
+int launch_backward2(const Launch &L, int bwin);   // g from r and h from q in one pass
+int backward_blocks(int nx, int ny, int dual);
 int encode_tiled(CUtensorMap *m, CUtensorMapDataType type, int rank, void *base, const cuuint64_t *dims,
                  const cuuint64_t *strides_bytes, const cuuint32_t *box);
 int launch_transpose(const Launch &L, int which);          // x -> x^T (which 0) or p -> p^T (which 1)

@@ -446,53 +446,67 @@ int launch_forward(const Launch &L, int which, int mode)
 constexpr int kBwdSplit = 2;                                             // thread groups splitting the views
 constexpr int kBwdGroup = 128;                                           // threads per group
 constexpr int kBwdThreads = kBwdSplit * kBwdGroup;
-constexpr int kBwdPixPerThread = kBwdTileI * kBwdTileJ / kBwdGroup;      // 4
 constexpr int kBwdRowStep = kBwdGroup / kBwdTileJ;                       // 4
 
+// One sinogram: 32 x 32 pixel tiles, 8 pixels per thread.  Two sinograms (the
+// solver's R^T r and R^T q, one pass): 16 x 32 tiles, 4 pixels per thread, each
+// pixel's weights evaluated once and applied to both.  Either way a pixel sums
+// its views in the same order (same groups, folds and parts), so each output
+// has the same bits as from the one-sinogram kernel.
+template <bool DUAL>
+struct BwdShape {
+    static constexpr int NS = DUAL ? 2 : 1;                        // sinograms
+    static constexpr int TI = DUAL ? kBwdTileI / 2 : kBwdTileI;    // tile rows
+    static constexpr int PX = TI * kBwdTileJ / kBwdGroup;          // pixels per thread
+};
+
 // Per pixel and view: the bins within hwu (half-width + margin) of the pixel's
-// projected centre, two of them (three when the bins are finer than pixels).
-template <bool AXIS, int NC, bool CHECKED>
+// projected centre, two of them (three when the bins are finer than pixels),
+// with a check of the staged window.  t[s * PX + e]: sinogram s, pixel e; the
+// window of sinogram s starts qoff floats after that of sinogram 0.
+template <bool AXIS, int NC, int PX, int NS>
 __device__ __forceinline__ void bwd_view(const ViewP &vp, float pb0, const float *sm, int w_row, int lo,
-                                         int bwin, float *t, int *bad)
+                                         int bwin, int qoff, float *t, int *bad)
 {
     const float E = vp.E, Sn = vp.Sn, ESn = vp.ESn;
 #pragma unroll
-    for (int e = 0; e < kBwdPixPerThread; ++e) {
+    for (int e = 0; e < PX; ++e) {
         // delta = (u + pb) - small; pb = -uc_hi - cu_hi X - su_hi Y is exact, and so is
         // stepping it by su_hi per pixel row
         const float pb = __fmaf_rn((float)(kBwdRowStep * e), vp.su_hi, pb0);
         const float uc = ceil_magic(__fsub_rn(__fsub_rn(sm[e], pb), vp.hwu));
         int u0 = magic_int(uc);
-        if (CHECKED) {
-            const int idx = u0 - lo;
-            if (idx < 0 || idx > bwin - NC) {   // outside the staged window: never for a valid window
-                *bad = 1;
-                u0 = min(max(idx, 0), bwin - NC) + lo;
-            }
+        const int idx = u0 - lo;
+        if (idx < 0 || idx > bwin - NC) {   // outside the staged window: never for a valid window
+            *bad = 1;
+            u0 = min(max(idx, 0), bwin - NC) + lo;
         }
-        const float u0f = CHECKED ? __int2float_rn(u0) : magic_float(uc);
-        const float big0 = __fadd_rn(u0f, pb);   // exact, as are big0 + 1 and big0 + 2
+        const float big0 = __fadd_rn(__int2float_rn(u0), pb);   // exact, as are big0 + 1 and big0 + 2
         const int wv = w_row + (u0 - lo);
 #pragma unroll
         for (int k = 0; k < NC; ++k) {
             const float ad = fabsf(__fsub_rn(__fadd_rn(big0, (float)k), sm[e]));
-            t[e] = __fmaf_rn(weight_unit(ad, E, Sn, ESn, AXIS), proj_dyn[wv + k], t[e]);   // the window holds P * y
+            const float w = weight_unit(ad, E, Sn, ESn, AXIS);
+#pragma unroll
+            for (int s = 0; s < NS; ++s)   // the window holds P * y
+                t[s * PX + e] = __fmaf_rn(w, proj_dyn[wv + s * qoff + k], t[s * PX + e]);
         }
     }
 }
 
 // The same for the thread's pixels in pairs (2h, 2h + 1), every FP32 step as one
 // f32x2 instruction; only for windows that hold every candidate (no checks).
-// sm2[h] = (small of pixel 2h, of pixel 2h + 1); t2[h] the pairs' running sums.
-template <bool AXIS, int NC>
-__device__ __forceinline__ void bwd_view_x2(const ViewP &vp, float pb0, const uint64_t *sm2, int w_row,
-                                            int lo, uint64_t *t2)
+// sm2[h] = (small of pixel 2h, of pixel 2h + 1); t2[s * PX / 2 + h] the pairs'
+// running sums for sinogram s.
+template <bool AXIS, int NC, int PX, int NS>
+__device__ __forceinline__ void bwd_view_x2(const ViewP &vp, float pb0, const uint64_t *sm2, int w_row, int lo,
+                                            int qoff, uint64_t *t2)
 {
     const float E = vp.E, Sn = vp.Sn, ESn = vp.ESn;
     const uint64_t su2 = pk2(vp.su_hi, vp.su_hi), hwu2 = pk2(vp.hwu, vp.hwu), pbb = pk2(pb0, pb0);
     const uint64_t mag2 = pk2(kCeilMagic, kCeilMagic);
 #pragma unroll
-    for (int h = 0; h < kBwdPixPerThread / 2; ++h) {
+    for (int h = 0; h < PX / 2; ++h) {
         const uint64_t st = pk2((float)(kBwdRowStep * 2 * h), (float)(kBwdRowStep * (2 * h + 1)));
         const uint64_t pb = fma2_rn(st, su2, pbb);                          // exact
         const uint64_t uc = add2_rp(sub2_rn(sub2_rn(sm2[h], pb), hwu2), mag2);
@@ -506,57 +520,68 @@ __device__ __forceinline__ void bwd_view_x2(const ViewP &vp, float pb0, const ui
             float da, db;
             upk2(sub2_rn(bk, sm2[h]), da, db);
             const uint64_t w = pk2(weight_unit(fabsf(da), E, Sn, ESn, AXIS), weight_unit(fabsf(db), E, Sn, ESn, AXIS));
-            t2[h] = fma2_rn(w, pk2(proj_dyn[wa + k], proj_dyn[wb + k]), t2[h]);   // the window holds P * y
+#pragma unroll
+            for (int s = 0; s < NS; ++s)   // the window holds P * y
+                t2[s * PX / 2 + h] =
+                    fma2_rn(w, pk2(proj_dyn[wa + s * qoff + k], proj_dyn[wb + s * qoff + k]), t2[s * PX / 2 + h]);
         }
     }
 }
 
+// R^T y over one sinogram (mode BWD_G: y = r into g, BWD_H: y = q into h,
+// BWD_PLAIN: y = the staged input into g), or, DUAL, over two in one pass:
+// g from r and h from q (h = A p for the beta of the next step of Algorithm 2,
+// deferred to this pass: alpha takes p^T A p from the forward projector's ||q||^2).
+template <bool DUAL>
 __global__ void __launch_bounds__(kBwdThreads, 3) k_backward(const Prob *__restrict__ probs,
                                                           const int *__restrict__ prefix, int count, int mode)
 {
-    // proj_dyn: [2][kBwdViewChunk][bwin] sinogram windows
+    constexpr int NS = BwdShape<DUAL>::NS, TI = BwdShape<DUAL>::TI, PX = BwdShape<DUAL>::PX;
+    // proj_dyn: [2][NS][kBwdViewChunk][bwin] sinogram windows
     __shared__ ViewP vsh[2][kBwdViewChunk];
     __shared__ int ulo_sh[2][kBwdViewChunk];
     __shared__ int kind_sh[2][kBwdViewChunk];   // variant: axis / three bins / two bins, + 3 if a window check is needed
-    __shared__ double comb[kBwdGroup * kBwdPixPerThread];   // second group's sums, combined by the first
+    __shared__ double comb[kBwdGroup * NS * PX];   // second group's sums, combined by the first
     __shared__ int bad_sh;
 
     int local;
     const int pi = find_problem(prefix, count, blockIdx.x, &local);
     const Prob &P = probs[pi];
-    if (mode != BWD_PLAIN && P.sc->done) return;
+    if ((DUAL || mode != BWD_PLAIN) && P.sc->done) return;
 
     const int bwin = P.bwin;
+    const int qoff = kBwdViewChunk * bwin;   // second sinogram's windows after the first's
     const int tiles_j = (P.nx + kBwdTileJ - 1) / kBwdTileJ;
     const int tile = local / kBwdViewParts, vpart = local - tile * kBwdViewParts;   // this block's part of the views
     const int ti = tile / tiles_j, tj = tile - ti * tiles_j;
-    const int i0 = ti * kBwdTileI, j0 = tj * kBwdTileJ;
+    const int i0 = ti * TI, j0 = tj * kBwdTileJ;
     const int t = threadIdx.x;
     const int grp = t / kBwdGroup, tg = t - grp * kBwdGroup;   // group grp takes views vv = grp (mod kBwdSplit)
     const int lx = tg % kBwdTileJ, ly = tg / kBwdTileJ;
     const int j = j0 + lx;
     const float X = __fsub_rn(__int2float_rn(j), P.cx);
-    float Y[kBwdPixPerThread];
+    float Y[PX];
 #pragma unroll
-    for (int e = 0; e < kBwdPixPerThread; ++e) Y[e] = __fsub_rn(P.cy, __int2float_rn(i0 + ly + kBwdRowStep * e));
+    for (int e = 0; e < PX; ++e) Y[e] = __fsub_rn(P.cy, __int2float_rn(i0 + ly + kBwdRowStep * e));
     // per pixel: FP32 sum of up to four views (t2, pixels in pairs), folded into a Kahan-compensated
     // pair (part, comp) that runs over all views; FP64 only for the final value (the FP64 pipe is narrow)
-    float part[kBwdPixPerThread], comp[kBwdPixPerThread];
-    uint64_t t2[kBwdPixPerThread / 2];
+    float part[NS * PX], comp[NS * PX];
+    uint64_t t2[NS * PX / 2];
 #pragma unroll
-    for (int e = 0; e < kBwdPixPerThread; ++e) part[e] = comp[e] = 0.0f;
+    for (int e = 0; e < NS * PX; ++e) part[e] = comp[e] = 0.0f;
 #pragma unroll
-    for (int h = 0; h < kBwdPixPerThread / 2; ++h) t2[h] = pk2(0.0f, 0.0f);
-    uint64_t Y2[kBwdPixPerThread / 2];
+    for (int h = 0; h < NS * PX / 2; ++h) t2[h] = pk2(0.0f, 0.0f);
+    uint64_t Y2[PX / 2];
 #pragma unroll
-    for (int h = 0; h < kBwdPixPerThread / 2; ++h) Y2[h] = pk2(Y[2 * h], Y[2 * h + 1]);
+    for (int h = 0; h < PX / 2; ++h) Y2[h] = pk2(Y[2 * h], Y[2 * h + 1]);
     const uint64_t X2 = pk2(X, X);
 
-    const float *sino = (mode == BWD_G) ? P.r : (mode == BWD_H ? P.q : P.r);
+    const float *sino0 = (!DUAL && mode == BWD_H) ? P.q : P.r;
+    const float *sino1 = P.q;
     const int Up = P.Up;
     // tile corners in pixel-centre coordinates
     const float Xa = __fsub_rn(__int2float_rn(j0), P.cx), Xb = __fsub_rn(__int2float_rn(j0 + kBwdTileJ - 1), P.cx);
-    const float Ya = __fsub_rn(P.cy, __int2float_rn(i0)), Yb = __fsub_rn(P.cy, __int2float_rn(i0 + kBwdTileI - 1));
+    const float Ya = __fsub_rn(P.cy, __int2float_rn(i0)), Yb = __fsub_rn(P.cy, __int2float_rn(i0 + TI - 1));
     if (t == 0) bad_sh = 0;
 
     const int nchunks = (P.V + kBwdViewChunk - 1) / kBwdViewChunk;
@@ -594,21 +619,23 @@ __global__ void __launch_bounds__(kBwdThreads, 3) k_backward(const Prob *__restr
         }
         __syncthreads();
         const int V4 = bwin >> 2;
-        float *wb = proj_dyn + buf * kBwdViewChunk * bwin;
-        for (int e = t; e < kBwdViewChunk * V4; e += kBwdThreads) {
-            const int vv = e / V4, k4 = e - vv * V4;
+        float *wb = proj_dyn + buf * NS * qoff;
+        for (int e = t; e < NS * kBwdViewChunk * V4; e += kBwdThreads) {
+            const int s = (NS == 2 && e >= kBwdViewChunk * V4) ? 1 : 0;
+            const int es = e - s * kBwdViewChunk * V4;
+            const int vv = es / V4, k4 = es - vv * V4;
             const int v = v0 + vv;
             float4 val = make_float4(0.f, 0.f, 0.f, 0.f);
             const int ub = ulo_sh[buf][vv] + 4 * k4;
             if (v < P.V && ub >= 0 && ub + 3 < Up) {
-                val = __ldg(reinterpret_cast<const float4 *>(sino + (size_t)v * Up + ub));
+                val = __ldg(reinterpret_cast<const float4 *>((s ? sino1 : sino0) + (size_t)v * Up + ub));
                 const float pl = vsh[buf][vv].P;   // the weights are in units of the view's plateau length
                 val.x = __fmul_rn(val.x, pl);
                 val.y = __fmul_rn(val.y, pl);
                 val.z = __fmul_rn(val.z, pl);
                 val.w = __fmul_rn(val.w, pl);
             }
-            *reinterpret_cast<float4 *>(wb + vv * bwin + 4 * k4) = val;
+            *reinterpret_cast<float4 *>(wb + s * qoff + vv * bwin + 4 * k4) = val;
         }
     };
 
@@ -621,7 +648,7 @@ __global__ void __launch_bounds__(kBwdThreads, 3) k_backward(const Prob *__restr
         const int buf = c & 1;
         if (c + 1 < c_end) stage(c + 1);   // other buffer; its previous readers finished at the last barrier
         const int nv = min(kBwdViewChunk, P.V - c * kBwdViewChunk);
-        const int wb = buf * kBwdViewChunk * bwin;
+        const int wb = buf * NS * qoff;
         // groups of four of this thread group's views, then one Kahan-compensated fold
         for (int g0 = grp; g0 < nv; g0 += 4 * kBwdSplit) {
 #pragma unroll
@@ -633,46 +660,45 @@ __global__ void __launch_bounds__(kBwdThreads, 3) k_backward(const Prob *__restr
                     const int lo = ulo_sh[buf][vv];
                     const float pb0 = __fmaf_rn(-vp.cu_hi, X, __fmaf_rn(-vp.su_hi, Y[0], -P.uc_hi));
                     // small = uc_lo + cu_lo X + su_lo Y in the view class's order (delta_small), in pairs
-                    uint64_t sm2[kBwdPixPerThread / 2];
+                    uint64_t sm2[PX / 2];
                     if (vp.flags & kViewClassB) {
                         const float in = __fmaf_rn(vp.cu_lo, X, P.uc_lo);
                         const uint64_t s2 = pk2(vp.su_lo, vp.su_lo), in2 = pk2(in, in);
 #pragma unroll
-                        for (int h = 0; h < kBwdPixPerThread / 2; ++h) sm2[h] = fma2_rn(s2, Y2[h], in2);
+                        for (int h = 0; h < PX / 2; ++h) sm2[h] = fma2_rn(s2, Y2[h], in2);
                     } else {
                         const uint64_t s2 = pk2(vp.su_lo, vp.su_lo), c2 = pk2(vp.cu_lo, vp.cu_lo),
                                        u2 = pk2(P.uc_lo, P.uc_lo);
 #pragma unroll
-                        for (int h = 0; h < kBwdPixPerThread / 2; ++h) sm2[h] = fma2_rn(c2, X2, fma2_rn(s2, Y2[h], u2));
+                        for (int h = 0; h < PX / 2; ++h) sm2[h] = fma2_rn(c2, X2, fma2_rn(s2, Y2[h], u2));
                     }
                     const int kind = kind_sh[buf][vv];
                     if (kind < 3) {
-                        if (kind == 0) bwd_view_x2<true, 2>(vp, pb0, sm2, wr, lo, t2);
-                        else if (kind == 1) bwd_view_x2<false, 3>(vp, pb0, sm2, wr, lo, t2);
-                        else bwd_view_x2<false, 2>(vp, pb0, sm2, wr, lo, t2);
+                        if (kind == 0) bwd_view_x2<true, 2, PX, NS>(vp, pb0, sm2, wr, lo, qoff, t2);
+                        else if (kind == 1) bwd_view_x2<false, 3, PX, NS>(vp, pb0, sm2, wr, lo, qoff, t2);
+                        else bwd_view_x2<false, 2, PX, NS>(vp, pb0, sm2, wr, lo, qoff, t2);
                     } else {   // a window check is needed: the scalar path
-                        float sm[kBwdPixPerThread], t4[kBwdPixPerThread];
+                        float sm[PX], t4[NS * PX];
 #pragma unroll
-                        for (int h = 0; h < kBwdPixPerThread / 2; ++h) {
-                            upk2(sm2[h], sm[2 * h], sm[2 * h + 1]);
-                            upk2(t2[h], t4[2 * h], t4[2 * h + 1]);
-                        }
-                        if (kind == 3) bwd_view<true, 2, true>(vp, pb0, sm, wr, lo, bwin, t4, &bad);
-                        else if (kind == 4) bwd_view<false, 3, true>(vp, pb0, sm, wr, lo, bwin, t4, &bad);
-                        else bwd_view<false, 2, true>(vp, pb0, sm, wr, lo, bwin, t4, &bad);
+                        for (int h = 0; h < PX / 2; ++h) upk2(sm2[h], sm[2 * h], sm[2 * h + 1]);
 #pragma unroll
-                        for (int h = 0; h < kBwdPixPerThread / 2; ++h) t2[h] = pk2(t4[2 * h], t4[2 * h + 1]);
+                        for (int h = 0; h < NS * PX / 2; ++h) upk2(t2[h], t4[2 * h], t4[2 * h + 1]);
+                        if (kind == 3) bwd_view<true, 2, PX, NS>(vp, pb0, sm, wr, lo, bwin, qoff, t4, &bad);
+                        else if (kind == 4) bwd_view<false, 3, PX, NS>(vp, pb0, sm, wr, lo, bwin, qoff, t4, &bad);
+                        else bwd_view<false, 2, PX, NS>(vp, pb0, sm, wr, lo, bwin, qoff, t4, &bad);
+#pragma unroll
+                        for (int h = 0; h < NS * PX / 2; ++h) t2[h] = pk2(t4[2 * h], t4[2 * h + 1]);
                     }
                 }
             }
-            float t4[kBwdPixPerThread];
+            float t4[NS * PX];
 #pragma unroll
-            for (int h = 0; h < kBwdPixPerThread / 2; ++h) {
+            for (int h = 0; h < NS * PX / 2; ++h) {
                 upk2(t2[h], t4[2 * h], t4[2 * h + 1]);
                 t2[h] = pk2(0.0f, 0.0f);
             }
 #pragma unroll
-            for (int e = 0; e < kBwdPixPerThread; ++e) {
+            for (int e = 0; e < NS * PX; ++e) {
                 const float y = __fsub_rn(t4[e], comp[e]);
                 const float tt = __fadd_rn(part[e], y);
                 comp[e] = __fsub_rn(__fsub_rn(tt, part[e]), y);
@@ -681,66 +707,77 @@ __global__ void __launch_bounds__(kBwdThreads, 3) k_backward(const Prob *__restr
         }
         __syncthreads();
     }
-    double acc[kBwdPixPerThread];
+    double acc[NS * PX];
 #pragma unroll
-    for (int e = 0; e < kBwdPixPerThread; ++e) acc[e] = (double)part[e] - (double)comp[e];
+    for (int e = 0; e < NS * PX; ++e) acc[e] = (double)part[e] - (double)comp[e];
     if (bad) atomicExch(&bad_sh, 1);
     __syncthreads();
 
     // combine the groups' sums in a fixed order
     if (grp == 1)
 #pragma unroll
-        for (int e = 0; e < kBwdPixPerThread; ++e) comb[e * kBwdGroup + tg] = acc[e];
+        for (int e = 0; e < NS * PX; ++e) comb[e * kBwdGroup + tg] = acc[e];
     __syncthreads();
     // this part's sums; the tile's last part to finish adds them in part order
     const size_t img = (size_t)P.ny * P.nxp;
     if (grp == 0)
 #pragma unroll
-        for (int e = 0; e < kBwdPixPerThread; ++e) {
-            const int i = i0 + ly + kBwdRowStep * e;
-            if (i < P.ny && j < P.nx) P.bsplit[vpart * img + (size_t)i * P.nxp + j] = acc[e] + comb[e * kBwdGroup + tg];
-        }
+        for (int s = 0; s < NS; ++s)
+#pragma unroll
+            for (int e = 0; e < PX; ++e) {
+                const int i = i0 + ly + kBwdRowStep * e;
+                if (i < P.ny && j < P.nx)
+                    P.bsplit[(size_t)(s * kBwdViewParts + vpart) * img + (size_t)i * P.nxp + j] =
+                        acc[s * PX + e] + comb[(s * PX + e) * kBwdGroup + tg];
+            }
     if (t == 0 && bad_sh && P.sc) atomicExch(&P.sc->status, (int)SUPCG_ERR_UNSUPPORTED);
     __shared__ int last_sh;
     if (!last_block(&P.tilecnt[tile], kBwdViewParts, &last_sh)) return;
-    float *out = (mode == BWD_G) ? P.g : (mode == BWD_H ? P.h : P.g);
+    // output s: the gradient (g from r) or h from q
+    const bool is_g[2] = {DUAL || mode != BWD_H, false};
+    float *outs[2] = {(!DUAL && mode == BWD_H) ? P.h : P.g, P.h};
     // Bayesian criterion (Eq. (2.3)): g = r^2 R^T r + (x - mu_X), h = r^2 R^T q + p, and
     // ||x - mu_X||^2 for f.  With a reference image, the selective error of Eq. (4.1) of
     // x = x_{k+1/2} over the centred ellipse S (this pass reads x anyway).
-    const bool bayes = mode != BWD_PLAIN && P.r2 > 0.0;
-    const bool want_se = mode == BWD_G && P.se_ref != nullptr && !P.sc->init;
+    const bool solve = DUAL || mode != BWD_PLAIN;
+    const bool bayes = solve && P.r2 > 0.0;
+    const bool want_se = (DUAL || mode == BWD_G) && P.se_ref != nullptr && !P.sc->init;
     const double muX = bayes ? P.sc->muX : 0.0;
     double sx = 0.0, sse = 0.0;
     if (grp == 0)
 #pragma unroll
-        for (int e = 0; e < kBwdPixPerThread; ++e) {
-            const int i = i0 + ly + kBwdRowStep * e;
-            if (i < P.ny && j < P.nx) {
-                const size_t o = (size_t)i * P.nxp + j;
-                double v = 0.0;
-                for (int h = 0; h < kBwdViewParts; ++h) v += *(volatile const double *)(P.bsplit + h * img + o);
-                if (bayes) {
-                    if (mode == BWD_G) {
-                        const double dx = (double)P.x[o] - muX;
-                        v = P.r2 * v + dx;
-                        sx += dx * dx;
-                    } else {
-                        v = P.r2 * v + (double)P.p[o];
+        for (int s = 0; s < NS; ++s)
+#pragma unroll
+            for (int e = 0; e < PX; ++e) {
+                const int i = i0 + ly + kBwdRowStep * e;
+                if (i < P.ny && j < P.nx) {
+                    const size_t o = (size_t)i * P.nxp + j;
+                    double v = 0.0;
+#pragma unroll
+                    for (int h = 0; h < kBwdViewParts; ++h)
+                        v += *(volatile const double *)(P.bsplit + (size_t)(s * kBwdViewParts + h) * img + o);
+                    if (bayes) {
+                        if (is_g[s]) {
+                            const double dx = (double)P.x[o] - muX;
+                            v = P.r2 * v + dx;
+                            sx += dx * dx;
+                        } else {
+                            v = P.r2 * v + (double)P.p[o];
+                        }
                     }
-                }
-                out[o] = (float)v;
-                if (want_se) {   // pixel centre inside the ellipse (FP64, as the definition)
-                    const double ex = ((double)j - 0.5 * (P.nx - 1)) / P.se_ax;
-                    const double ey = ((double)i - 0.5 * (P.ny - 1)) / P.se_ay;
-                    if (ex * ex + ey * ey <= 1.0) {
-                        const double dr = (double)P.x[o] - (double)P.se_ref[(size_t)i * P.nx + j];
-                        sse += dr * dr;
+                    outs[s][o] = (float)v;
+                    if (want_se && s == 0) {   // pixel centre inside the ellipse (FP64, as the definition)
+                        const double ex = ((double)j - 0.5 * (P.nx - 1)) / P.se_ax;
+                        const double ey = ((double)i - 0.5 * (P.ny - 1)) / P.se_ay;
+                        if (ex * ex + ey * ey <= 1.0) {
+                            const double dr = (double)P.x[o] - (double)P.se_ref[(size_t)i * P.nx + j];
+                            sse += dr * dr;
+                        }
                     }
                 }
             }
-        }
     if (t == 0) P.tilecnt[tile] = 0;   // ready for the next launch
-    if (!(bayes && mode == BWD_G) && !want_se) return;
+    if (!(bayes && is_g[0]) && !want_se) return;
     // the tiles' sums, added in tile order by the last tile to finish: f = r^2 ||R x - b||^2 +
     // ||x - mu_X||^2, and SE = sqrt(sum over S)
     const double bs = block_sum<kBwdThreads>(sx, comb);
@@ -765,15 +802,37 @@ __global__ void __launch_bounds__(kBwdThreads, 3) k_backward(const Prob *__restr
     }
 }
 
+// Blocks per problem: kBwdViewParts per pixel tile.
+int backward_blocks(int nx, int ny, int dual)
+{
+    const int ti = dual ? BwdShape<true>::TI : BwdShape<false>::TI;
+    return kBwdViewParts * ((ny + ti - 1) / ti) * ((nx + kBwdTileJ - 1) / kBwdTileJ);
+}
+
 int launch_backward(const Launch &L, int mode, int bwin)
 {
     static int set = 0;
     if (!set) {
-        SUPCG_CUDA_TRY(cudaFuncSetAttribute(k_backward, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        SUPCG_CUDA_TRY(cudaFuncSetAttribute(k_backward<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                             2 * kBwdViewChunk * 256 * 4));
         set = 1;
     }
-    k_backward<<<L.blocks, kBwdThreads, 2 * kBwdViewChunk * bwin * 4, L.st>>>(L.probs, L.prefix, L.count, mode);
+    k_backward<false><<<L.blocks, kBwdThreads, 2 * kBwdViewChunk * bwin * 4, L.st>>>(L.probs, L.prefix, L.count,
+                                                                                     mode);
+    SUPCG_CUDA_TRY(cudaGetLastError());
+    return SUPCG_OK;
+}
+
+int launch_backward2(const Launch &L, int bwin)
+{
+    static int set = 0;
+    if (!set) {
+        SUPCG_CUDA_TRY(cudaFuncSetAttribute(k_backward<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                            2 * 2 * kBwdViewChunk * 256 * 4));
+        set = 1;
+    }
+    k_backward<true><<<L.blocks, kBwdThreads, 2 * 2 * kBwdViewChunk * bwin * 4, L.st>>>(L.probs, L.prefix, L.count,
+                                                                                       BWD_G);
     SUPCG_CUDA_TRY(cudaGetLastError());
     return SUPCG_OK;
 }
