@@ -138,7 +138,7 @@ struct supcg_geometry_s {
     ViewP *dviews = nullptr;
     int *dvlist = nullptr;
     int *dtorder = nullptr;         // forward tile order, ceil(U / 32) entries
-    double2 *dtwx = nullptr, *dtwy = nullptr;
+    float4 *dtwx = nullptr, *dtwy = nullptr;   // double-float twiddles
     Workspace *ws_ops = nullptr;    // standalone operators, `ops_batch` images
     int ops_batch = 0;
     Workspace *ws_solve = nullptr;  // single-problem solve
@@ -195,15 +195,18 @@ static void exact_cos_sin(double th, double *c, double *s)
     }
 }
 
-static int upload_twiddles(int n, double2 **out)
+// exp(-2 pi i k / n), k < n, as double-float pairs (cos h, cos l, sin h, sin l) of the FP64 values
+static int upload_twiddles(int n, float4 **out)
 {
-    std::vector<double2> tw(n);
+    std::vector<float4> tw(n);
     for (int k = 0; k < n; ++k) {
         const double a = -2.0 * M_PI * (double)k / (double)n;
-        tw[k] = make_double2(cos(a), sin(a));
+        const double c = cos(a), s = sin(a);
+        const float ch = (float)c, sh = (float)s;
+        tw[k] = make_float4(ch, (float)(c - (double)ch), sh, (float)(s - (double)sh));
     }
-    SUPCG_CUDA_TRY(cudaMalloc(out, sizeof(double2) * n));
-    SUPCG_CUDA_TRY(cudaMemcpy(*out, tw.data(), sizeof(double2) * n, cudaMemcpyHostToDevice));
+    SUPCG_CUDA_TRY(cudaMalloc(out, sizeof(float4) * n));
+    SUPCG_CUDA_TRY(cudaMemcpy(*out, tw.data(), sizeof(float4) * n, cudaMemcpyHostToDevice));
     return SUPCG_OK;
 }
 
@@ -322,8 +325,10 @@ extern "C" int supcg_create_geometry(int nx, int ny, double pixel_size, int n_vi
         supcg_destroy_geometry(g);
         return rc;
     }
-    g->fx.tw = g->dtwx;
-    g->fy.tw = g->dtwy;
+    g->fx.tw = nullptr;
+    g->fy.tw = nullptr;
+    g->fx.twf = g->dtwx;
+    g->fy.twf = g->dtwy;
     if (cudaMalloc(&g->dviews, sizeof(ViewP) * n_views) != cudaSuccess ||
         cudaMalloc(&g->dvlist, sizeof(int) * n_views) != cudaSuccess ||
         cudaMalloc(&g->dtorder, sizeof(int) * ((n_bins + 31) / 32)) != cudaSuccess) {
@@ -489,7 +494,7 @@ static int ws_create(const std::vector<supcg_geometry> &gs, Workspace **out)
         P.g = (float *)ptrs[4]; P.z = (float *)ptrs[5]; P.h = (float *)ptrs[6]; P.tbar = (float *)ptrs[7];
         P.r = (float *)ptrs[8]; P.q = (float *)ptrs[9]; P.bpad = (float *)ptrs[10];
         P.C = (double2 *)ptrs[11]; P.sc = (Scal *)ptrs[12]; P.partial = (double *)ptrs[13];
-        P.counter = (unsigned *)ptrs[14]; P.bar = (unsigned *)ptrs[15]; P.Dtab = (double *)ptrs[16];
+        P.counter = (unsigned *)ptrs[14]; P.bar = (unsigned *)ptrs[15]; P.Dtab = (float2 *)ptrs[16];
         P.bsplit = (double *)ptrs[17]; P.tilecnt = (unsigned *)ptrs[18];
         P.torder = g->dtorder;
         P.nx = g->nx; P.ny = g->ny; P.V = g->V; P.U = g->U;

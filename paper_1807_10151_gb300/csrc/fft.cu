@@ -1,19 +1,23 @@
 // Preconditioner z = M g, M = F^-1 D F (Eq. (3.2)), on the ny x nx grid.
 //
-// Three passes over a complex FP64 scratch array S [ny][nx/2 + 1] (FP32
-// vectors in and out, FP64 arithmetic inside: the operator spans five decades,
-// from h(0) = mu to about pi, and an FP32 transform of a gradient dominated by
-// its low frequencies loses several digits of M g).  g and z are real and D is
-// real and even, so every row spectrum is Hermitian: only k2 = 0 .. nx/2 is
-// kept, and two real rows share one complex transform.
+// Three passes over a complex scratch array S [ny][nx/2 + 1] (FP32 vectors in
+// and out; inside, double-float arithmetic: pairs of FP32 numbers carrying
+// about 48 bits, on the FP32 pipe, since this part's FP64 pipe is narrow.  The
+// operator spans five decades, from h(0) = mu to about pi, and a plain FP32
+// transform of a gradient dominated by its low frequencies loses several
+// digits of M g).  g and z are real and D is real and even, so every row
+// spectrum is Hermitian: only k2 = 0 .. nx/2 is kept, and two real rows share
+// one complex transform.
 //   rows:  S[i, k2] = FFT(g[i, :])(k2), k2 <= nx/2     (k_fft_rows, forward, row pairs)
 //   cols:  S[:, k2] = IFFT(D[:, k2] * FFT(S[:, k2]))   (k_fft_cols)
-//   rows:  z[i, :] = IFFT(Hermitian S[i, :]) / (nx ny)  (k_fft_rows, inverse, row pairs)
-// Each length is transformed in shared memory by a mixed-radix Stockham
-// (autosort) FFT: radix 4 and 2 butterflies written out, any other prime
-// factor by its defining sum.  Twiddles exp(-2 pi i k/n) come from an FP64
-// table built on the host.  D = h(w_r), h(w) = (|w| + mu)(rho + (1-rho) cos w),
-// w_r the radial frequency clamped to pi, is evaluated on the fly.
+//   rows:  z[i, :] = IFFT(Hermitian S[i, :])            (k_fft_rows, inverse, row pairs)
+// with D = h(w_r) / (nx ny), h(w) = (|w| + mu)(rho + (1-rho) cos w), w_r the
+// radial frequency clamped to pi, tabulated once per call or solve in FP64 and
+// stored as pairs.  Each length is transformed in shared memory by a
+// mixed-radix Stockham (autosort) FFT: radix 4 and 2 butterflies written out,
+// any other prime factor by its defining sum.  Twiddles exp(-2 pi i k/n) come
+// from FP64 tables built on the host (stored as pairs for the solver's
+// transforms; the allocation-free variant at the end of this file keeps FP64).
 #include <algorithm>
 #include <mutex>
 
@@ -86,16 +90,125 @@ __device__ double2 *fft_smem(double2 *a, double2 *b, int nvec, const FFTPlan &pl
     return a;
 }
 
+// ------------------------------------------------------------ double-float arithmetic
+// The solver's transforms run on the FP32 pipe (the FP64 pipe of this part is
+// narrow): a real value is the unevaluated sum h + l of two FP32 numbers with
+// |l| <= ulp(h) / 2, about 48 significant bits.  Sums use Knuth's TwoSum (the
+// exact rounding error of a + b for any magnitudes), products the FMA form of
+// Dekker's TwoProduct (the exact rounding error of a * b); the low parts are
+// then added and the pair renormalised.  Each operation's error is a few units
+// of 2^-48 relative to its operands, as a rounded FP64 operation's is of 2^-53,
+// so the transforms keep the FP64 design's accuracy (the five decades of D).
+struct df {
+    float h, l;
+};
+
+__device__ __forceinline__ df df_make(float v) { return {v, 0.0f}; }
+__device__ __forceinline__ df df_neg(df a) { return {-a.h, -a.l}; }
+__device__ __forceinline__ df df_half(df a) { return {0.5f * a.h, 0.5f * a.l}; }   // exact
+
+__device__ __forceinline__ df df_add(df a, df b)
+{
+    const float s = __fadd_rn(a.h, b.h);
+    const float bv = __fsub_rn(s, a.h);
+    const float e = __fadd_rn(__fsub_rn(a.h, __fsub_rn(s, bv)), __fsub_rn(b.h, bv));   // TwoSum error
+    const float t = __fadd_rn(__fadd_rn(a.l, b.l), e);
+    const float h = __fadd_rn(s, t);
+    return {h, __fsub_rn(t, __fsub_rn(h, s))};
+}
+__device__ __forceinline__ df df_sub(df a, df b) { return df_add(a, df_neg(b)); }
+
+__device__ __forceinline__ df df_mul(df a, df b)
+{
+    const float p = __fmul_rn(a.h, b.h);
+    float e = __fmaf_rn(a.h, b.h, -p);                               // TwoProduct error
+    e = __fmaf_rn(a.h, b.l, __fmaf_rn(a.l, b.h, e));
+    const float h = __fadd_rn(p, e);
+    return {h, __fsub_rn(e, __fsub_rn(h, p))};
+}
+
+// complex double-float, stored as float4 (re.h, re.l, im.h, im.l)
+struct dfc {
+    df r, i;
+};
+__device__ __forceinline__ dfc dfc_ld(const float4 &v) { return {{v.x, v.y}, {v.z, v.w}}; }
+__device__ __forceinline__ float4 dfc_st(const dfc &a) { return make_float4(a.r.h, a.r.l, a.i.h, a.i.l); }
+__device__ __forceinline__ dfc dfc_add(dfc a, dfc b) { return {df_add(a.r, b.r), df_add(a.i, b.i)}; }
+__device__ __forceinline__ dfc dfc_sub(dfc a, dfc b) { return {df_sub(a.r, b.r), df_sub(a.i, b.i)}; }
+__device__ __forceinline__ dfc dfc_mul(dfc a, dfc b)
+{
+    return {df_sub(df_mul(a.r, b.r), df_mul(a.i, b.i)), df_add(df_mul(a.r, b.i), df_mul(a.i, b.r))};
+}
+__device__ __forceinline__ dfc twid_df(const float4 *tw, int e, bool inv)
+{
+    const float4 w = __ldg(tw + e);
+    return inv ? dfc{{w.x, w.y}, {-w.z, -w.w}} : dfc{{w.x, w.y}, {w.z, w.w}};
+}
+
+// Transforms `nvec` contiguous vectors of length pl.n held in a (b is scratch
+// of the same size), in double-float; returns the buffer that holds the result.
+// The same mixed-radix Stockham schedule as fft_smem.
+__device__ float4 *fft_smem_df(float4 *a, float4 *b, int nvec, const FFTPlan &pl, bool inv)
+{
+    const int n = pl.n;
+    int Ns = 1;
+    for (int s = 0; s < pl.nst; ++s) {
+        const int R = pl.radix[s];
+        const int m = n / R;
+        const int stride = n / (Ns * R);
+        for (int idx = threadIdx.x; idx < nvec * m; idx += blockDim.x) {
+            const int vec = idx / m, j = idx - vec * m;
+            const int k = j % Ns;
+            const float4 *src = a + vec * n;
+            float4 *dst = b + vec * n + (j / Ns) * Ns * R + k;
+            if (R == 2) {
+                const dfc v0 = dfc_ld(src[j]), v1 = dfc_mul(dfc_ld(src[j + m]), twid_df(pl.twf, k * stride, inv));
+                dst[0] = dfc_st(dfc_add(v0, v1));
+                dst[Ns] = dfc_st(dfc_sub(v0, v1));
+            } else if (R == 4) {
+                const dfc v0 = dfc_ld(src[j]);
+                const dfc v1 = dfc_mul(dfc_ld(src[j + m]), twid_df(pl.twf, k * stride, inv));
+                const dfc v2 = dfc_mul(dfc_ld(src[j + 2 * m]), twid_df(pl.twf, 2 * k * stride, inv));
+                const dfc v3 = dfc_mul(dfc_ld(src[j + 3 * m]), twid_df(pl.twf, 3 * k * stride, inv));
+                const dfc t0 = dfc_add(v0, v2), t1 = dfc_sub(v0, v2), t2 = dfc_add(v1, v3), d = dfc_sub(v1, v3);
+                // (v1 - v3) times the fourth root of unity -i (forward) or +i (inverse)
+                const dfc t3 = inv ? dfc{df_neg(d.i), d.r} : dfc{d.i, df_neg(d.r)};
+                dst[0] = dfc_st(dfc_add(t0, t2));
+                dst[Ns] = dfc_st(dfc_add(t1, t3));
+                dst[2 * Ns] = dfc_st(dfc_sub(t0, t2));
+                dst[3 * Ns] = dfc_st(dfc_sub(t1, t3));
+            } else {
+                // any radix: V_s = sum_r (src_r w^{rk}) w_R^{rs}
+                const int nR = n / R;
+                for (int so = 0; so < R; ++so) {
+                    dfc acc = {{0.0f, 0.0f}, {0.0f, 0.0f}};
+                    for (int r = 0; r < R; ++r) {
+                        const dfc v = dfc_mul(dfc_ld(src[j + r * m]), twid_df(pl.twf, r * k * stride, inv));
+                        acc = dfc_add(acc, dfc_mul(v, twid_df(pl.twf, ((r * so) % R) * nR, inv)));
+                    }
+                    dst[so * Ns] = dfc_st(acc);
+                }
+            }
+        }
+        __syncthreads();
+        float4 *t = a;
+        a = b;
+        b = t;
+        Ns *= R;
+    }
+    return a;
+}
+
 // Rows pass on pairs of rows (g and z are real).  Block `local` takes the row
 // pairs 2i, 2i+1 for i in [local * rpb, (local + 1) * rpb) (a missing last
 // partner is a zero row).
 //   inverse = 0:  c = g[2i] + i g[2i+1];  C = FFT(c);  the two rows' spectra
 //                 A(k) = (C(k) + conj C(-k)) / 2,  B(k) = (C(k) - conj C(-k)) / (2i)
 //                 for k = 0 .. nx/2 (the rest follows by Hermitian symmetry) go to
-//                 S[2i][k] and S[2i+1][k], S = C viewed as [ny][nx/2 + 1].
+//                 S[2i][k] and S[2i+1][k], S viewed as [ny][nx/2 + 1].
 //   inverse = 1:  c(k) = Y(2i, k) + i Y(2i+1, k) with Y(r, k) = conj Y(r, nx - k)
 //                 beyond nx/2 (the filtered rows are real);  z[2i] + i z[2i+1] =
-//                 IFFT(c) / (nx ny).
+//                 IFFT(c) (the 1 / (nx ny) is folded into D).
 __global__ void __launch_bounds__(256) k_fft_rows(const Prob *__restrict__ probs, const int *__restrict__ prefix,
                                                   int count, int inverse, int standalone)
 {
@@ -105,53 +218,53 @@ __global__ void __launch_bounds__(256) k_fft_rows(const Prob *__restrict__ probs
     if (!standalone && P.sc->done) return;
     const int nx = P.nx, ny = P.ny, rpb = P.fft_rpb, hx = nx / 2 + 1;
     const int npairs = (ny + 1) / 2;
-    double2 *a = reinterpret_cast<double2 *>(smem_raw);
-    double2 *b = a + rpb * nx;
+    float4 *a = reinterpret_cast<float4 *>(smem_raw);
+    float4 *b = a + rpb * nx;
     const int p0 = local * rpb;
     const int np = min(rpb, npairs - p0);
-    double2 *S = P.C;
+    float4 *S = reinterpret_cast<float4 *>(P.C);
     for (int e = threadIdx.x; e < np * nx; e += blockDim.x) {
         const int pr = e / nx, q = e - pr * nx;
         const int ra = 2 * (p0 + pr), rb = ra + 1;
         if (!inverse) {
-            const double va = (double)P.g[(size_t)ra * P.nxp + q];
-            const double vb = rb < ny ? (double)P.g[(size_t)rb * P.nxp + q] : 0.0;
-            a[e] = make_double2(va, vb);
+            const float va = P.g[(size_t)ra * P.nxp + q];
+            const float vb = rb < ny ? P.g[(size_t)rb * P.nxp + q] : 0.0f;
+            a[e] = make_float4(va, 0.0f, vb, 0.0f);
         } else {
             const bool lo = q <= nx / 2;
             const int kk = lo ? q : nx - q;
-            double2 ya = S[(size_t)ra * hx + kk];
-            double2 yb = rb < ny ? S[(size_t)rb * hx + kk] : make_double2(0.0, 0.0);
+            dfc ya = dfc_ld(S[(size_t)ra * hx + kk]);
+            dfc yb = rb < ny ? dfc_ld(S[(size_t)rb * hx + kk]) : dfc{{0.0f, 0.0f}, {0.0f, 0.0f}};
             if (!lo) {
-                ya.y = -ya.y;
-                yb.y = -yb.y;
+                ya.i = df_neg(ya.i);
+                yb.i = df_neg(yb.i);
             }
-            a[e] = make_double2(ya.x - yb.y, ya.y + yb.x);   // ya + i yb
+            a[e] = dfc_st(dfc{df_sub(ya.r, yb.i), df_add(ya.i, yb.r)});   // ya + i yb
         }
     }
     __syncthreads();
-    double2 *res = fft_smem(a, b, np, P.fx, inverse != 0);
+    float4 *res = fft_smem_df(a, b, np, P.fx, inverse != 0);
     if (!inverse) {
         for (int e = threadIdx.x; e < np * hx; e += blockDim.x) {
             const int pr = e / hx, k = e - pr * hx;
             const int ra = 2 * (p0 + pr), rb = ra + 1;
-            const double2 c1 = res[pr * nx + k], c2 = res[pr * nx + (k == 0 ? 0 : nx - k)];
-            S[(size_t)ra * hx + k] = make_double2(0.5 * (c1.x + c2.x), 0.5 * (c1.y - c2.y));
-            if (rb < ny) S[(size_t)rb * hx + k] = make_double2(0.5 * (c1.y + c2.y), 0.5 * (c2.x - c1.x));
+            const dfc c1 = dfc_ld(res[pr * nx + k]), c2 = dfc_ld(res[pr * nx + (k == 0 ? 0 : nx - k)]);
+            S[(size_t)ra * hx + k] = dfc_st(dfc{df_half(df_add(c1.r, c2.r)), df_half(df_sub(c1.i, c2.i))});
+            if (rb < ny) S[(size_t)rb * hx + k] = dfc_st(dfc{df_half(df_add(c1.i, c2.i)), df_half(df_sub(c2.r, c1.r))});
         }
     } else {
         // z, and inside a solve also z^T h for beta = z^T h / p^T h (Algorithm 2 step 3)
-        const double scale = 1.0 / ((double)nx * (double)ny);
         double s = 0.0;
         for (int e = threadIdx.x; e < np * nx; e += blockDim.x) {
             const int pr = e / nx, q = e - pr * nx;
             const int ra = 2 * (p0 + pr), rb = ra + 1;
             const size_t ia = (size_t)ra * P.nxp + q, ib = (size_t)rb * P.nxp + q;
-            const float za = (float)(res[e].x * scale);
+            const float4 v = res[e];
+            const float za = __fadd_rn(v.x, v.y);   // the pair rounded to FP32
             P.z[ia] = za;
             if (!standalone) s += (double)za * (double)P.h[ia];
             if (rb < ny) {
-                const float zb = (float)(res[e].y * scale);
+                const float zb = __fadd_rn(v.z, v.w);
                 P.z[ib] = zb;
                 if (!standalone) s += (double)zb * (double)P.h[ib];
             }
@@ -183,7 +296,7 @@ __global__ void __launch_bounds__(256) k_fft_rows(const Prob *__restrict__ probs
 }
 
 // Columns pass over the nx/2 + 1 stored frequencies k2: forward FFT along
-// the columns, multiply by D = h(w_r), inverse FFT.
+// the columns, multiply by D = h(w_r) / (nx ny), inverse FFT.
 __global__ void __launch_bounds__(256) k_fft_cols(const Prob *__restrict__ probs, const int *__restrict__ prefix,
                                                   int count, int standalone)
 {
@@ -192,33 +305,35 @@ __global__ void __launch_bounds__(256) k_fft_cols(const Prob *__restrict__ probs
     const Prob &P = probs[find_problem(prefix, count, blockIdx.x, &local)];
     if (!standalone && P.sc->done) return;
     const int nx = P.nx, ny = P.ny, cw = P.fft_cw, hx = nx / 2 + 1;
-    double2 *a = reinterpret_cast<double2 *>(smem_raw);
-    double2 *b = a + cw * ny;
+    float4 *a = reinterpret_cast<float4 *>(smem_raw);
+    float4 *b = a + cw * ny;
     const int c0 = local * cw;
     const int nc = min(cw, hx - c0);
-    double2 *S = P.C;
+    float4 *S = reinterpret_cast<float4 *>(P.C);
     for (int e = threadIdx.x; e < nc * ny; e += blockDim.x) {
         const int k1 = e / nc, c = e - k1 * nc;   // consecutive threads read consecutive columns
         a[c * ny + k1] = S[(size_t)k1 * hx + c0 + c];
     }
     __syncthreads();
-    double2 *res = fft_smem(a, b, nc, P.fy, false);
-    double2 *oth = (res == a) ? b : a;
+    float4 *res = fft_smem_df(a, b, nc, P.fy, false);
+    float4 *oth = (res == a) ? b : a;
     for (int e = threadIdx.x; e < nc * ny; e += blockDim.x) {
         const int c = e / ny, k1 = e - c * ny;
-        const double hD = __ldg(P.Dtab + (size_t)min(k1, ny - k1) * hx + c0 + c);   // k2 <= nx/2
-        res[e] = make_double2(res[e].x * hD, res[e].y * hD);
+        const float2 hd = __ldg(P.Dtab + (size_t)min(k1, ny - k1) * hx + c0 + c);   // k2 <= nx/2
+        const df D = {hd.x, hd.y};
+        const dfc v = dfc_ld(res[e]);
+        res[e] = dfc_st(dfc{df_mul(v.r, D), df_mul(v.i, D)});
     }
     __syncthreads();
-    double2 *fin = fft_smem(res, oth, nc, P.fy, true);
+    float4 *fin = fft_smem_df(res, oth, nc, P.fy, true);
     for (int e = threadIdx.x; e < nc * ny; e += blockDim.x) {
         const int k1 = e / nc, c = e - k1 * nc;
         S[(size_t)k1 * hx + c0 + c] = fin[c * ny + k1];
     }
 }
 
-// D = h(w_r) on the quarter spectrum (D is even in both frequencies):
-// Dtab[m1][m2], w_i = 2 pi m_i / N_i, w_r = min(sqrt(w1^2 + w2^2), pi).
+// D = h(w_r) / (nx ny) on the quarter spectrum (D is even in both frequencies),
+// as a double-float pair: Dtab[m1][m2], w_i = 2 pi m_i / N_i, w_r = min(sqrt(w1^2 + w2^2), pi).
 __global__ void __launch_bounds__(256) k_fft_dtab(const Prob *__restrict__ probs, const int *__restrict__ prefix,
                                                   int count)
 {
@@ -227,13 +342,16 @@ __global__ void __launch_bounds__(256) k_fft_dtab(const Prob *__restrict__ probs
     const int nx = P.nx, ny = P.ny, hx = nx / 2 + 1, hy = ny / 2 + 1;
     const double two_pi = 6.28318530717958647692;
     const double pi_d = 3.14159265358979323846;
+    const double scale = 1.0 / ((double)nx * (double)ny);
     for (int k = 0; k < 4; ++k) {
         const long long e = (long long)local * 1024 + k * 256 + threadIdx.x;
         if (e >= (long long)hx * hy) break;
         const int m1 = (int)(e / hx), m2 = (int)(e - (long long)m1 * hx);
         const double w1 = two_pi * m1 / ny, w2 = two_pi * m2 / nx;
         const double wr = fmin(sqrt(w1 * w1 + w2 * w2), pi_d);
-        P.Dtab[e] = (wr + P.mu) * (P.rho + (1.0 - P.rho) * cos(wr));
+        const double v = (wr + P.mu) * (P.rho + (1.0 - P.rho) * cos(wr)) * scale;
+        const float vh = (float)v;
+        P.Dtab[e] = make_float2(vh, (float)(v - (double)vh));
     }
 }
 

@@ -137,6 +137,7 @@ struct FFTPlan {
     int nst;
     int radix[kMaxStages];
     const double2 *tw;  // exp(-2 pi i k / n), k = 0 .. n-1 (FP64)
+    const float4 *twf;  // the same as double-float pairs (cos h, cos l, sin h, sin l)
 };
 
 // ----------------------------------------------------------------- scalars
@@ -197,7 +198,7 @@ struct Prob {
     float *x, *xT, *p, *pT, *g, *z, *h, *tbar;
     float *r, *q, *bpad;
     double2 *C;            // FFT scratch [ny][nx] (FP64 complex)
-    double *Dtab;          // preconditioner diagonal h(w_r) at (min(k1, ny-k1), min(k2, nx-k2)): [ny/2+1][nx/2+1]
+    float2 *Dtab;          // h(w_r) / (nx ny) at (min(k1, ny-k1), min(k2, nx-k2)), double-float: [ny/2+1][nx/2+1]
     double *bsplit;        // backprojector: each sinogram's and view part's pixel sums [2][kBwdViewParts][ny][nxp]
     unsigned *tilecnt;     // backprojector: parts finished per tile (reset by the last one)
     Scal *sc;

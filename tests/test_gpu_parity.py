@@ -141,6 +141,24 @@ def test_preconditioner_matches_oracle(ny, nx, mu, rho):
     assert rel_l2(z, ref) <= 1e-5
 
 
+@pytest.mark.parametrize("ny,nx", [(512, 512), (300, 257), (96, 128)])
+def test_preconditioner_keeps_digits_of_damped_low_frequencies(ny, nx):
+    """A gradient dominated by its lowest frequencies (as R^T b is): M damps them
+    by mu = 1e-5, so z = M g is far smaller than g there.  Each transform step in
+    FP32 arithmetic leaves errors of about 2^-24 |g| at every frequency, which
+    then dominate z (an FP32 FFT lands 4e-6 from the FP64 one on this input);
+    the result must stay near the level of z's own FP32 rounding (2.4e-8)."""
+    og = O.Geometry(nx, ny=ny, V=4, U=8)
+    G = gpu_geometry(og)
+    yy, xx = np.mgrid[0:ny, 0:nx]
+    smooth = 1e3 * (2.0 + np.cos(2 * np.pi * xx / nx) + np.sin(2 * np.pi * yy / ny)
+                    + 0.5 * np.cos(2 * np.pi * (xx / nx + 2 * yy / ny)))
+    g = f32(smooth + np.random.default_rng(7).standard_normal((ny, nx)))
+    z = G.precondition(to_dev(g), 1e-5, 0.8).double().cpu().numpy()
+    ref = np.real(np.fft.ifft2(O.precond_D(ny, nx, 1e-5, 0.8) * np.fft.fft2(g)))
+    assert rel_l2(z, ref) <= 1e-7
+
+
 def test_preconditioner_rejects_indefinite():
     import paper_1807_10151_gb300 as S
     og = O.Geometry(8, V=4, U=8)
