@@ -495,7 +495,7 @@ static int ws_create(const std::vector<supcg_geometry> &gs, Workspace **out)
         P.r = (float *)ptrs[8]; P.q = (float *)ptrs[9]; P.bpad = (float *)ptrs[10];
         P.C = (double2 *)ptrs[11]; P.sc = (Scal *)ptrs[12]; P.partial = (double *)ptrs[13];
         P.counter = (unsigned *)ptrs[14]; P.bar = (unsigned *)ptrs[15]; P.Dtab = (float2 *)ptrs[16];
-        P.bsplit = (double *)ptrs[17]; P.tilecnt = (unsigned *)ptrs[18];
+        P.bsplit = (float2 *)ptrs[17]; P.tilecnt = (unsigned *)ptrs[18];
         P.torder = g->dtorder;
         P.nx = g->nx; P.ny = g->ny; P.V = g->V; P.U = g->U;
         P.nxp = g->nxp; P.nyp = g->nyp; P.Up = g->Up;

@@ -90,43 +90,6 @@ __device__ double2 *fft_smem(double2 *a, double2 *b, int nvec, const FFTPlan &pl
     return a;
 }
 
-// ------------------------------------------------------------ double-float arithmetic
-// The solver's transforms run on the FP32 pipe (the FP64 pipe of this part is
-// narrow): a real value is the unevaluated sum h + l of two FP32 numbers with
-// |l| <= ulp(h) / 2, about 48 significant bits.  Sums use Knuth's TwoSum (the
-// exact rounding error of a + b for any magnitudes), products the FMA form of
-// Dekker's TwoProduct (the exact rounding error of a * b); the low parts are
-// then added and the pair renormalised.  Each operation's error is a few units
-// of 2^-48 relative to its operands, as a rounded FP64 operation's is of 2^-53,
-// so the transforms keep the FP64 design's accuracy (the five decades of D).
-struct df {
-    float h, l;
-};
-
-__device__ __forceinline__ df df_make(float v) { return {v, 0.0f}; }
-__device__ __forceinline__ df df_neg(df a) { return {-a.h, -a.l}; }
-__device__ __forceinline__ df df_half(df a) { return {0.5f * a.h, 0.5f * a.l}; }   // exact
-
-__device__ __forceinline__ df df_add(df a, df b)
-{
-    const float s = __fadd_rn(a.h, b.h);
-    const float bv = __fsub_rn(s, a.h);
-    const float e = __fadd_rn(__fsub_rn(a.h, __fsub_rn(s, bv)), __fsub_rn(b.h, bv));   // TwoSum error
-    const float t = __fadd_rn(__fadd_rn(a.l, b.l), e);
-    const float h = __fadd_rn(s, t);
-    return {h, __fsub_rn(t, __fsub_rn(h, s))};
-}
-__device__ __forceinline__ df df_sub(df a, df b) { return df_add(a, df_neg(b)); }
-
-__device__ __forceinline__ df df_mul(df a, df b)
-{
-    const float p = __fmul_rn(a.h, b.h);
-    float e = __fmaf_rn(a.h, b.h, -p);                               // TwoProduct error
-    e = __fmaf_rn(a.h, b.l, __fmaf_rn(a.l, b.h, e));
-    const float h = __fadd_rn(p, e);
-    return {h, __fsub_rn(e, __fsub_rn(h, p))};
-}
-
 // complex double-float, stored as float4 (re.h, re.l, im.h, im.l)
 struct dfc {
     df r, i;

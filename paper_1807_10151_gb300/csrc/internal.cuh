@@ -199,7 +199,7 @@ struct Prob {
     float *r, *q, *bpad;
     double2 *C;            // FFT scratch [ny][nx] (FP64 complex)
     float2 *Dtab;          // h(w_r) / (nx ny) at (min(k1, ny-k1), min(k2, nx-k2)), double-float: [ny/2+1][nx/2+1]
-    double *bsplit;        // backprojector: each sinogram's and view part's pixel sums [2][kBwdViewParts][ny][nxp]
+    float2 *bsplit;        // backprojector: each sinogram's and view part's pixel sums, double-float [2][kBwdViewParts][ny][nxp]
     unsigned *tilecnt;     // backprojector: parts finished per tile (reset by the last one)
     Scal *sc;
     double *partial;       // reduction partials (>= 2 * max blocks per kernel)
@@ -223,6 +223,43 @@ __device__ __forceinline__ int find_problem(const int *prefix, int count, int b,
     }
     *local = b - __ldg(prefix + lo);
     return lo;
+}
+
+// ----------------------------------------------------------------- double-float arithmetic
+// For work that needs more than FP32 but should not run on this part's narrow
+// FP64 pipe (the preconditioner's transforms, the projectors' final sums): a
+// real value is the unevaluated sum h + l of two FP32 numbers with |l| <=
+// ulp(h) / 2, about 48 significant bits.  Sums use Knuth's TwoSum (the
+// exact rounding error of a + b for any magnitudes), products the FMA form of
+// Dekker's TwoProduct (the exact rounding error of a * b); the low parts are
+// then added and the pair renormalised.  Each operation's error is a few units
+// of 2^-48 relative to its operands, as a rounded FP64 operation's is of 2^-53.
+struct df {
+    float h, l;
+};
+
+__device__ __forceinline__ df df_make(float v) { return {v, 0.0f}; }
+__device__ __forceinline__ df df_neg(df a) { return {-a.h, -a.l}; }
+__device__ __forceinline__ df df_half(df a) { return {0.5f * a.h, 0.5f * a.l}; }   // exact
+
+__device__ __forceinline__ df df_add(df a, df b)
+{
+    const float s = __fadd_rn(a.h, b.h);
+    const float bv = __fsub_rn(s, a.h);
+    const float e = __fadd_rn(__fsub_rn(a.h, __fsub_rn(s, bv)), __fsub_rn(b.h, bv));   // TwoSum error
+    const float t = __fadd_rn(__fadd_rn(a.l, b.l), e);
+    const float h = __fadd_rn(s, t);
+    return {h, __fsub_rn(t, __fsub_rn(h, s))};
+}
+__device__ __forceinline__ df df_sub(df a, df b) { return df_add(a, df_neg(b)); }
+
+__device__ __forceinline__ df df_mul(df a, df b)
+{
+    const float p = __fmul_rn(a.h, b.h);
+    float e = __fmaf_rn(a.h, b.h, -p);                               // TwoProduct error
+    e = __fmaf_rn(a.h, b.l, __fmaf_rn(a.l, b.h, e));
+    const float h = __fadd_rn(p, e);
+    return {h, __fsub_rn(e, __fsub_rn(h, p))};
 }
 
 // ----------------------------------------------------------------- reductions

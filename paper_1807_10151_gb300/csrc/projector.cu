@@ -541,7 +541,8 @@ __global__ void __launch_bounds__(kBwdThreads, 3) k_backward(const Prob *__restr
     __shared__ ViewP vsh[2][kBwdViewChunk];
     __shared__ int ulo_sh[2][kBwdViewChunk];
     __shared__ int kind_sh[2][kBwdViewChunk];   // variant: axis / three bins / two bins, + 3 if a window check is needed
-    __shared__ double comb[kBwdGroup * NS * PX];   // second group's sums, combined by the first
+    __shared__ float2 comb[kBwdGroup * NS * PX];   // second group's sums, combined by the first
+    __shared__ double red[40];
     __shared__ int bad_sh;
 
     int local;
@@ -707,16 +708,13 @@ __global__ void __launch_bounds__(kBwdThreads, 3) k_backward(const Prob *__restr
         }
         __syncthreads();
     }
-    double acc[NS * PX];
-#pragma unroll
-    for (int e = 0; e < NS * PX; ++e) acc[e] = (double)part[e] - (double)comp[e];
+    // the Kahan pair as a double-float value part - comp (|comp| <= ulp(part) / 2); the
+    // groups' and the parts' sums are added in double-float arithmetic, in a fixed order
     if (bad) atomicExch(&bad_sh, 1);
     __syncthreads();
-
-    // combine the groups' sums in a fixed order
     if (grp == 1)
 #pragma unroll
-        for (int e = 0; e < NS * PX; ++e) comb[e * kBwdGroup + tg] = acc[e];
+        for (int e = 0; e < NS * PX; ++e) comb[e * kBwdGroup + tg] = make_float2(part[e], -comp[e]);
     __syncthreads();
     // this part's sums; the tile's last part to finish adds them in part order
     const size_t img = (size_t)P.ny * P.nxp;
@@ -726,9 +724,11 @@ __global__ void __launch_bounds__(kBwdThreads, 3) k_backward(const Prob *__restr
 #pragma unroll
             for (int e = 0; e < PX; ++e) {
                 const int i = i0 + ly + kBwdRowStep * e;
-                if (i < P.ny && j < P.nx)
-                    P.bsplit[(size_t)(s * kBwdViewParts + vpart) * img + (size_t)i * P.nxp + j] =
-                        acc[s * PX + e] + comb[(s * PX + e) * kBwdGroup + tg];
+                if (i < P.ny && j < P.nx) {
+                    const float2 o2 = comb[(s * PX + e) * kBwdGroup + tg];
+                    const df v = df_add(df{part[s * PX + e], -comp[s * PX + e]}, df{o2.x, o2.y});
+                    P.bsplit[(size_t)(s * kBwdViewParts + vpart) * img + (size_t)i * P.nxp + j] = make_float2(v.h, v.l);
+                }
             }
     if (t == 0 && bad_sh && P.sc) atomicExch(&P.sc->status, (int)SUPCG_ERR_UNSUPPORTED);
     __shared__ int last_sh;
@@ -752,11 +752,14 @@ __global__ void __launch_bounds__(kBwdThreads, 3) k_backward(const Prob *__restr
                 const int i = i0 + ly + kBwdRowStep * e;
                 if (i < P.ny && j < P.nx) {
                     const size_t o = (size_t)i * P.nxp + j;
-                    double v = 0.0;
+                    float2 pv[kBwdViewParts];   // the other blocks' sums: read past L1
 #pragma unroll
-                    for (int h = 0; h < kBwdViewParts; ++h)
-                        v += *(volatile const double *)(P.bsplit + (size_t)(s * kBwdViewParts + h) * img + o);
+                    for (int h = 0; h < kBwdViewParts; ++h) pv[h] = __ldcg(P.bsplit + (size_t)(s * kBwdViewParts + h) * img + o);
+                    df vs = {0.0f, 0.0f};
+#pragma unroll
+                    for (int h = 0; h < kBwdViewParts; ++h) vs = df_add(vs, df{pv[h].x, pv[h].y});
                     if (bayes) {
+                        double v = (double)vs.h + (double)vs.l;
                         if (is_g[s]) {
                             const double dx = (double)P.x[o] - muX;
                             v = P.r2 * v + dx;
@@ -764,8 +767,10 @@ __global__ void __launch_bounds__(kBwdThreads, 3) k_backward(const Prob *__restr
                         } else {
                             v = P.r2 * v + (double)P.p[o];
                         }
+                        outs[s][o] = (float)v;
+                    } else {
+                        outs[s][o] = __fadd_rn(vs.h, vs.l);   // the pair rounded to FP32
                     }
-                    outs[s][o] = (float)v;
                     if (want_se && s == 0) {   // pixel centre inside the ellipse (FP64, as the definition)
                         const double ex = ((double)j - 0.5 * (P.nx - 1)) / P.se_ax;
                         const double ey = ((double)i - 0.5 * (P.ny - 1)) / P.se_ay;
@@ -780,16 +785,16 @@ __global__ void __launch_bounds__(kBwdThreads, 3) k_backward(const Prob *__restr
     if (!(bayes && is_g[0]) && !want_se) return;
     // the tiles' sums, added in tile order by the last tile to finish: f = r^2 ||R x - b||^2 +
     // ||x - mu_X||^2, and SE = sqrt(sum over S)
-    const double bs = block_sum<kBwdThreads>(sx, comb);
-    const double be = block_sum<kBwdThreads>(sse, comb);
+    const double bs = block_sum<kBwdThreads>(sx, red);
+    const double be = block_sum<kBwdThreads>(sse, red);
     const int ntiles = (prefix[pi + 1] - prefix[pi]) / kBwdViewParts;
     if (t == 0) {
         P.partial[tile] = bs;
         P.partial[ntiles + tile] = be;
     }
     if (last_block(&P.counter[4], ntiles, &last_sh)) {
-        const double tot = block_sum_array<kBwdThreads>(P.partial, ntiles, comb);
-        const double tse = block_sum_array<kBwdThreads>(P.partial + ntiles, ntiles, comb);
+        const double tot = block_sum_array<kBwdThreads>(P.partial, ntiles, red);
+        const double tse = block_sum_array<kBwdThreads>(P.partial + ntiles, ntiles, red);
         if (t == 0) {
             Scal *sc = P.sc;
             if (bayes) {
