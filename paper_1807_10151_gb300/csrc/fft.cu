@@ -104,35 +104,61 @@ __device__ __forceinline__ dfc dfc_mul(dfc a, dfc b)
 }
 __device__ __forceinline__ dfc twid_df(const float4 *tw, int e, bool inv)
 {
-    const float4 w = __ldg(tw + e);
+    const float4 w = tw[e];
     return inv ? dfc{{w.x, w.y}, {-w.z, -w.w}} : dfc{{w.x, w.y}, {w.z, w.w}};
 }
 
+// Twiddle tables of up to this many entries are copied to shared memory by each block.
+constexpr int kFftSmemTw = 2048;
+
+// The twiddles the block's transforms read: its shared copy (stw, room for
+// kFftSmemTw entries) when the length allows, else the global table.
+__device__ __forceinline__ const float4 *stage_twiddles(const FFTPlan &pl, float4 *stw)
+{
+    if (pl.n > kFftSmemTw) return pl.twf;
+    for (int e = threadIdx.x; e < pl.n; e += blockDim.x) stw[e] = __ldg(pl.twf + e);
+    __syncthreads();
+    return stw;
+}
+
 // Transforms `nvec` contiguous vectors of length pl.n held in a (b is scratch
-// of the same size), in double-float; returns the buffer that holds the result.
-// The same mixed-radix Stockham schedule as fft_smem.
-__device__ float4 *fft_smem_df(float4 *a, float4 *b, int nvec, const FFTPlan &pl, bool inv)
+// of the same size), in double-float, with the twiddles tw (shared or global);
+// returns the buffer that holds the result.  The same mixed-radix Stockham
+// schedule as fft_smem; for power-of-two lengths the index arithmetic is shifts.
+__device__ float4 *fft_smem_df(float4 *a, float4 *b, int nvec, const FFTPlan &pl, const float4 *tw, bool inv)
 {
     const int n = pl.n;
+    const bool pow2 = (n & (n - 1)) == 0;
     int Ns = 1;
     for (int s = 0; s < pl.nst; ++s) {
         const int R = pl.radix[s];
         const int m = n / R;
         const int stride = n / (Ns * R);
+        const int lm = __ffs(m) - 1, lns = __ffs(Ns) - 1;   // log2 m, log2 Ns (power-of-two lengths)
         for (int idx = threadIdx.x; idx < nvec * m; idx += blockDim.x) {
-            const int vec = idx / m, j = idx - vec * m;
-            const int k = j % Ns;
+            int vec, j, k, jq;
+            if (pow2) {
+                vec = idx >> lm;
+                j = idx & (m - 1);
+                k = j & (Ns - 1);
+                jq = j >> lns;
+            } else {
+                vec = idx / m;
+                j = idx - vec * m;
+                jq = j / Ns;
+                k = j - jq * Ns;
+            }
             const float4 *src = a + vec * n;
-            float4 *dst = b + vec * n + (j / Ns) * Ns * R + k;
+            float4 *dst = b + vec * n + jq * Ns * R + k;
             if (R == 2) {
-                const dfc v0 = dfc_ld(src[j]), v1 = dfc_mul(dfc_ld(src[j + m]), twid_df(pl.twf, k * stride, inv));
+                const dfc v0 = dfc_ld(src[j]), v1 = dfc_mul(dfc_ld(src[j + m]), twid_df(tw, k * stride, inv));
                 dst[0] = dfc_st(dfc_add(v0, v1));
                 dst[Ns] = dfc_st(dfc_sub(v0, v1));
             } else if (R == 4) {
                 const dfc v0 = dfc_ld(src[j]);
-                const dfc v1 = dfc_mul(dfc_ld(src[j + m]), twid_df(pl.twf, k * stride, inv));
-                const dfc v2 = dfc_mul(dfc_ld(src[j + 2 * m]), twid_df(pl.twf, 2 * k * stride, inv));
-                const dfc v3 = dfc_mul(dfc_ld(src[j + 3 * m]), twid_df(pl.twf, 3 * k * stride, inv));
+                const dfc v1 = dfc_mul(dfc_ld(src[j + m]), twid_df(tw, k * stride, inv));
+                const dfc v2 = dfc_mul(dfc_ld(src[j + 2 * m]), twid_df(tw, 2 * k * stride, inv));
+                const dfc v3 = dfc_mul(dfc_ld(src[j + 3 * m]), twid_df(tw, 3 * k * stride, inv));
                 const dfc t0 = dfc_add(v0, v2), t1 = dfc_sub(v0, v2), t2 = dfc_add(v1, v3), d = dfc_sub(v1, v3);
                 // (v1 - v3) times the fourth root of unity -i (forward) or +i (inverse)
                 const dfc t3 = inv ? dfc{df_neg(d.i), d.r} : dfc{d.i, df_neg(d.r)};
@@ -146,8 +172,8 @@ __device__ float4 *fft_smem_df(float4 *a, float4 *b, int nvec, const FFTPlan &pl
                 for (int so = 0; so < R; ++so) {
                     dfc acc = {{0.0f, 0.0f}, {0.0f, 0.0f}};
                     for (int r = 0; r < R; ++r) {
-                        const dfc v = dfc_mul(dfc_ld(src[j + r * m]), twid_df(pl.twf, r * k * stride, inv));
-                        acc = dfc_add(acc, dfc_mul(v, twid_df(pl.twf, ((r * so) % R) * nR, inv)));
+                        const dfc v = dfc_mul(dfc_ld(src[j + r * m]), twid_df(tw, r * k * stride, inv));
+                        acc = dfc_add(acc, dfc_mul(v, twid_df(tw, ((r * so) % R) * nR, inv)));
                     }
                     dst[so * Ns] = dfc_st(acc);
                 }
@@ -183,6 +209,7 @@ __global__ void __launch_bounds__(256) k_fft_rows(const Prob *__restrict__ probs
     const int npairs = (ny + 1) / 2;
     float4 *a = reinterpret_cast<float4 *>(smem_raw);
     float4 *b = a + rpb * nx;
+    const float4 *tw = stage_twiddles(P.fx, b + rpb * nx);
     const int p0 = local * rpb;
     const int np = min(rpb, npairs - p0);
     float4 *S = reinterpret_cast<float4 *>(P.C);
@@ -206,7 +233,7 @@ __global__ void __launch_bounds__(256) k_fft_rows(const Prob *__restrict__ probs
         }
     }
     __syncthreads();
-    float4 *res = fft_smem_df(a, b, np, P.fx, inverse != 0);
+    float4 *res = fft_smem_df(a, b, np, P.fx, tw, inverse != 0);
     if (!inverse) {
         for (int e = threadIdx.x; e < np * hx; e += blockDim.x) {
             const int pr = e / hx, k = e - pr * hx;
@@ -270,6 +297,7 @@ __global__ void __launch_bounds__(256) k_fft_cols(const Prob *__restrict__ probs
     const int nx = P.nx, ny = P.ny, cw = P.fft_cw, hx = nx / 2 + 1;
     float4 *a = reinterpret_cast<float4 *>(smem_raw);
     float4 *b = a + cw * ny;
+    const float4 *tw = stage_twiddles(P.fy, b + cw * ny);
     const int c0 = local * cw;
     const int nc = min(cw, hx - c0);
     float4 *S = reinterpret_cast<float4 *>(P.C);
@@ -278,7 +306,7 @@ __global__ void __launch_bounds__(256) k_fft_cols(const Prob *__restrict__ probs
         a[c * ny + k1] = S[(size_t)k1 * hx + c0 + c];
     }
     __syncthreads();
-    float4 *res = fft_smem_df(a, b, nc, P.fy, false);
+    float4 *res = fft_smem_df(a, b, nc, P.fy, tw, false);
     float4 *oth = (res == a) ? b : a;
     for (int e = threadIdx.x; e < nc * ny; e += blockDim.x) {
         const int c = e / ny, k1 = e - c * ny;
@@ -288,7 +316,7 @@ __global__ void __launch_bounds__(256) k_fft_cols(const Prob *__restrict__ probs
         res[e] = dfc_st(dfc{df_mul(v.r, D), df_mul(v.i, D)});
     }
     __syncthreads();
-    float4 *fin = fft_smem_df(res, oth, nc, P.fy, true);
+    float4 *fin = fft_smem_df(res, oth, nc, P.fy, tw, true);
     for (int e = threadIdx.x; e < nc * ny; e += blockDim.x) {
         const int k1 = e / nc, c = e - k1 * nc;
         S[(size_t)k1 * hx + c0 + c] = fin[c * ny + k1];
