@@ -780,8 +780,8 @@ static int enqueue_body(Workspace *w, const supcg_params *p, cudaStream_t st, in
         LAUNCH(SUPCG_KIND_VECTOR, st, launch_beta(w->L(KT_VEC, st)));           // beta = z^T h / p^T h
     }
     LAUNCH(SUPCG_KIND_VECTOR, st, launch_pupdate(w->L(KT_TR, st)));             // p = -z + beta p, g^T p, p^T
-    LAUNCH(SUPCG_KIND_FORWARD, st, launch_forward(w->L(KT_FWD, st), 1, FWD_NORM));    // q = R p, p^T h, alpha
-    LAUNCH(SUPCG_KIND_VECTOR, st, launch_log(w->L(KT_VEC, st)));                // k <- k + 1
+    // q = R p, p^T h, alpha; its last block also logs the step and sets k <- k + 1 (step 14)
+    LAUNCH(SUPCG_KIND_FORWARD, st, launch_forward(w->L(KT_FWD, st), 1, FWD_NORM));
     return SUPCG_OK;
 }
 
@@ -797,8 +797,8 @@ static int enqueue_init(Workspace *w, const supcg_params *p, cudaStream_t st)
         LAUNCH(SUPCG_KIND_VECTOR, st, launch_beta(w->L(KT_VEC, st)));
     }
     LAUNCH(SUPCG_KIND_VECTOR, st, launch_pupdate(w->L(KT_TR, st)));
-    LAUNCH(SUPCG_KIND_FORWARD, st, launch_forward(w->L(KT_FWD, st), 1, FWD_NORM));   // (h = A p: next pass)
-    LAUNCH(SUPCG_KIND_VECTOR, st, launch_end_init(w->L(KT_VEC, st)));
+    // (h = A p: in the next pass; the last block ends steps 1-9: init <- 0)
+    LAUNCH(SUPCG_KIND_FORWARD, st, launch_forward(w->L(KT_FWD, st), 1, FWD_NORM));
     return SUPCG_OK;
 }
 

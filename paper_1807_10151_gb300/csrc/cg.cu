@@ -302,54 +302,4 @@ int launch_xupdate(const Launch &L)
     return SUPCG_OK;
 }
 
-// End of steps 2-7 of Algorithm 3.
-__global__ void k_end_init(const Prob *__restrict__ probs, int count)
-{
-    const int pi = blockIdx.x * blockDim.x + threadIdx.x;
-    if (pi < count) probs[pi].sc->init = 0;
-}
-
-int launch_end_init(const Launch &L)
-{
-    k_end_init<<<(L.count + 127) / 128, 128, 0, L.st>>>(L.probs, L.count);
-    SUPCG_CUDA_TRY(cudaGetLastError());
-    return SUPCG_OK;
-}
-
-// End of a while-body: record the per-iteration metrics, k <- k + 1 (step 14).
-__global__ void k_body_end(const Prob *__restrict__ probs, int count)
-{
-    const int pi = blockIdx.x * blockDim.x + threadIdx.x;
-    if (pi >= count) return;
-    const Prob &P = probs[pi];
-    Scal *sc = P.sc;
-    if (sc->done) {
-        sc->done = 1;
-        return;
-    }
-    if (sc->status != 0) {
-        sc->done = 1;
-        return;
-    }
-    if (P.log) {
-        double *L = P.log + (size_t)sc->k * SUPCG_LOG_STRIDE;
-        L[0] = sc->f;
-        L[1] = sc->tv_k;
-        L[2] = sc->tv_half;
-        L[3] = (double)sc->ell;
-        L[4] = sc->alpha;
-        L[5] = sc->beta;
-        L[6] = sc->snorm2;
-        L[7] = (double)sc->trials;
-    }
-    sc->k += 1;
-}
-
-int launch_log(const Launch &L)
-{
-    k_body_end<<<(L.count + 127) / 128, 128, 0, L.st>>>(L.probs, L.count);
-    SUPCG_CUDA_TRY(cudaGetLastError());
-    return SUPCG_OK;
-}
-
 } // namespace supcg

@@ -132,12 +132,12 @@ __device__ __forceinline__ void fwd_rows2(const Prob &P, const ViewP &vp, uint64
     uint64_t Oc2 = pk2(Oc0, Oc0);
     const uint64_t dO2 = pk2(dO, dO), hio2 = pk2(-hi_o, -hi_o), loo2 = pk2(lo_o, lo_o), ucl2 = pk2(P.uc_lo, P.uc_lo);
     const uint64_t hii2 = pk2(-hi_i, -hi_i), loi2 = pk2(lo_i, lo_i), cin2 = pk2(c_in, c_in), dI2 = pk2(dI, dI);
-    const uint64_t bo2 = pk2(vp.b_o, vp.b_o), mag2 = pk2(kCeilMagic, kCeilMagic), one2 = pk2(1.0f, 1.0f);
+    const uint64_t bo2 = pk2(vp.b_o, vp.b_o), mag2 = pk2(kCeilMagic, kCeilMagic);
     const uint64_t qh2 = sub2_rn(qm2, pk2(vp.hwq, vp.hwq));
     const int prow = pbase - qs;   // proj_dyn index of inner index 0 of the box's first row
     uint64_t acc2 = pk2(0.0f, 0.0f);   // FP32 sums of up to 8 rows of A and B, then folded
-    auto row = [&](int r, uint64_t rf2) {
-        const uint64_t qc2 = add2_rp(fma2_rn(rf2, bo2, qh2), mag2);   // first candidates, as magic floats
+    auto row = [&](int r, uint64_t qp2) {
+        const uint64_t qc2 = add2_rp(qp2, mag2);   // first candidates, as magic floats
         float qcA, qcB;
         upk2(qc2, qcA, qcB);
         const int rowi = prow + r * BW;
@@ -172,15 +172,18 @@ __device__ __forceinline__ void fwd_rows2(const Prob &P, const ViewP &vp, uint64
         acc2 = pk2(0.0f, 0.0f);
     };
     int r = rb;
-    const float rbf = __int2float_rn(rb);
-    uint64_t rf2 = pk2(rbf, rbf);
     while (r < re) {   // groups aligned to multiples of 8 of the outer index, as in fwd_rows
         const int gend = min(re, (r & ~7) + 8);
+        // the candidates' window start (centre - hwq) of row r, then stepped by b_o per row: it only
+        // chooses the candidates (the weights decide), and eight steps stay ~1e-4 pixels from the
+        // direct value, far inside the window's margin
+        const float rf = __int2float_rn(r);
+        uint64_t qp2 = fma2_rn(pk2(rf, rf), bo2, qh2);
         if (gend - r == 8) {
 #pragma unroll
-            for (int k = 0; k < 8; ++k, rf2 = add2_rn(rf2, one2)) row(r + k, rf2);
+            for (int k = 0; k < 8; ++k, qp2 = add2_rn(qp2, bo2)) row(r + k, qp2);
         } else {
-            for (int q = r; q < gend; ++q, rf2 = add2_rn(rf2, one2)) row(q, rf2);
+            for (int q = r; q < gend; ++q, qp2 = add2_rn(qp2, bo2)) row(q, qp2);
         }
         fold();
         r = gend;
@@ -420,6 +423,26 @@ __global__ void __launch_bounds__(kFwdThreads, 10) k_forward(const Prob *__restr
                     sc->alpha = 0.0;
                 } else {
                     sc->alpha = al;
+                }
+                // the end of the pass: after steps 1-9 of Algorithm 3 the loop begins; after a
+                // while-body, unless an error stopped it, its log entry and k <- k + 1 (step 14)
+                if (sc->init) {
+                    sc->init = 0;
+                } else if (sc->status != 0) {
+                    sc->done = 1;
+                } else {
+                    if (P.log) {
+                        double *Lg = P.log + (size_t)sc->k * SUPCG_LOG_STRIDE;
+                        Lg[0] = sc->f;
+                        Lg[1] = sc->tv_k;
+                        Lg[2] = sc->tv_half;
+                        Lg[3] = (double)sc->ell;
+                        Lg[4] = sc->alpha;
+                        Lg[5] = sc->beta;
+                        Lg[6] = sc->snorm2;
+                        Lg[7] = (double)sc->trials;
+                    }
+                    sc->k += 1;
                 }
             }
             P.counter[0] = 0;
