@@ -117,20 +117,14 @@ __device__ __forceinline__ void fwd_rows(const Prob &P, const ViewP &vp, float t
 // the weights are the same bits).  Only for boxes that hold every candidate.
 template <bool CLASS_B, bool AXIS, int NC>
 __device__ __forceinline__ void fwd_rows2(const Prob &P, const ViewP &vp, uint64_t tau2, uint64_t qm2, int o0, int rb,
-                                          int re, int qs, int pbase, float *sum, float *comp)
+                                          int re, int qs, int pbase, const float4 *rtab, float *sum, float *comp)
 {
     const int BW = P.BW;
-    const float Oc0 = CLASS_B ? __fsub_rn(__int2float_rn(o0 + rb), P.cx) : __fsub_rn(P.cy, __int2float_rn(o0 + rb));
-    const float dO = CLASS_B ? 1.0f : -1.0f;
-    const float hi_o = CLASS_B ? vp.cu_hi : vp.su_hi;   // coefficient of the outer coordinate
-    const float lo_o = CLASS_B ? vp.cu_lo : vp.su_lo;
     const float hi_i = CLASS_B ? vp.su_hi : vp.cu_hi;   // coefficient of the inner coordinate
     const float lo_i = CLASS_B ? vp.su_lo : vp.cu_lo;
     const float c_in = CLASS_B ? P.cy : P.cx;           // inner coordinate = q - cx (A) or cy - q (B)
     const float dI = CLASS_B ? -1.0f : 1.0f;
     const float E = vp.E, Sn = vp.Sn, ESn = vp.ESn;
-    uint64_t Oc2 = pk2(Oc0, Oc0);
-    const uint64_t dO2 = pk2(dO, dO), hio2 = pk2(-hi_o, -hi_o), loo2 = pk2(lo_o, lo_o), ucl2 = pk2(P.uc_lo, P.uc_lo);
     const uint64_t hii2 = pk2(-hi_i, -hi_i), loi2 = pk2(lo_i, lo_i), cin2 = pk2(c_in, c_in), dI2 = pk2(dI, dI);
     const uint64_t bo2 = pk2(vp.b_o, vp.b_o), mag2 = pk2(kCeilMagic, kCeilMagic);
     const uint64_t qh2 = sub2_rn(qm2, pk2(vp.hwq, vp.hwq));
@@ -142,9 +136,9 @@ __device__ __forceinline__ void fwd_rows2(const Prob &P, const ViewP &vp, uint64
         upk2(qc2, qcA, qcB);
         const int rowi = prow + r * BW;
         const int pA = rowi + magic_int(qcA), pB = rowi + magic_int(qcB);
-        const uint64_t rbig2 = fma2_rn(hio2, Oc2, tau2);             // exact
-        const uint64_t rsmall2 = fma2_rn(loo2, Oc2, ucl2);
-        Oc2 = add2_rn(Oc2, dO2);
+        const float4 rt = rtab[r];                                   // the row's terms (fwd_row_terms)
+        const uint64_t rbig2 = add2_rn(tau2, pk2(rt.x, rt.y));       // exact
+        const uint64_t rsmall2 = pk2(rt.z, rt.w);
         const uint64_t q0f2 = sub2_rn(qc2, mag2);
         uint64_t I2 = CLASS_B ? sub2_rn(cin2, q0f2) : sub2_rn(q0f2, cin2);   // exact half-integers
 #pragma unroll
@@ -190,6 +184,23 @@ __device__ __forceinline__ void fwd_rows2(const Prob &P, const ViewP &vp, uint64
     }
 }
 
+// The outer coordinate's terms of the exact split for the rows of chunk [o0, o0 + RC),
+// the same for every ray of the view: rtab[r] = (H, H, s, s) with H = -hi_o O (exact)
+// and s = lo_o O + uc_lo (rounded once), O the outer coordinate of row o0 + r, so that
+// a ray's row needs big = tau_hi + H (exact, the value of fma(-hi_o, O, tau_hi)) and s.
+// Written by lanes 0 .. RC-1 of the warp that reads it.
+template <bool CLASS_B>
+__device__ __forceinline__ void fwd_row_terms(const Prob &P, const ViewP &vp, int o0, int lane, float4 *rtab)
+{
+    if (lane < kRowsPerChunk) {
+        const float O = CLASS_B ? __fsub_rn(__int2float_rn(o0 + lane), P.cx) : __fsub_rn(P.cy, __int2float_rn(o0 + lane));
+        const float H = __fmul_rn(CLASS_B ? -vp.cu_hi : -vp.su_hi, O);
+        const float sm = __fmaf_rn(CLASS_B ? vp.cu_lo : vp.su_lo, O, P.uc_lo);
+        rtab[lane] = make_float4(H, H, sm, sm);
+    }
+    __syncwarp();
+}
+
 // Lower end (multiple of 4) of the inner range that chunk [o0, o0+RC) of the
 // block's rays [u_first, u_last] can touch.
 __device__ __forceinline__ int fwd_box_start(const ViewP &vp, float tf, float tl, int o0)
@@ -231,8 +242,8 @@ __device__ __forceinline__ void fwd_row_range(const ViewP &vp, float base, int n
 // the box) and are dropped by the caller.
 template <bool CLASS_B, bool AXIS, int NC>
 __device__ __forceinline__ void fwd_ray2(const Prob &P, const ViewP &vp, const CUtensorMap *tm, int patch0,
-                                         uint64_t *bars, int n_outer, int n_inner, int uA, int uB, int u_last, float tf,
-                                         float tl, int *bad, int *timed_out, double *acc)
+                                         uint64_t *bars, float4 *rtab, int n_outer, int n_inner, int uA, int uB,
+                                         int u_last, float tf, float tl, int *bad, int *timed_out, double *acc)
 {
     const int RC = kRowsPerChunk, BW = P.BW;
     const int box_elems = RC * BW;
@@ -266,6 +277,7 @@ __device__ __forceinline__ void fwd_ray2(const Prob &P, const ViewP &vp, const C
         const int buf = ci % kFwdBufs, c = c_first + ci;
         const bool ok = mbar_wait(&bars[buf], (ci / kFwdBufs) & 1);
         const int o0 = c * RC;
+        fwd_row_terms<CLASS_B>(P, vp, o0, lane, rtab);
         const int rows = min(RC, n_outer - o0);
         const int rb = max(0, w_lo - o0), re = min(rows, w_hi - o0 + 1);
         if (ok && rb < re) {
@@ -284,7 +296,7 @@ __device__ __forceinline__ void fwd_ray2(const Prob &P, const ViewP &vp, const C
             }
             const int pb = patch0 + buf * box_elems;
             if (inside) {
-                fwd_rows2<CLASS_B, AXIS, NC>(P, vp, tau2, pk2(qm[0], qm[1]), o0, rb, re, qs, pb, sum, comp);
+                fwd_rows2<CLASS_B, AXIS, NC>(P, vp, tau2, pk2(qm[0], qm[1]), o0, rb, re, qs, pb, rtab, sum, comp);
             } else {
 #pragma unroll
                 for (int q = 0; q < 2; ++q)
@@ -318,6 +330,7 @@ __global__ void __launch_bounds__(kFwdThreads, 10) k_forward(const Prob *__restr
 {
     // proj_dyn: [warp][kFwdBufs][kRowsPerChunk][BW]
     __shared__ __align__(8) uint64_t bars[kFwdBufs * (kFwdThreads / 32)];   // one per staged box
+    __shared__ float4 rowtab[kFwdThreads / 32][kRowsPerChunk];             // each warp's row terms
     __shared__ double red[40];
     __shared__ int flag;
     __shared__ int bad_sh;
@@ -359,7 +372,8 @@ __global__ void __launch_bounds__(kFwdThreads, 10) k_forward(const Prob *__restr
     // axis-aligned views meet at most two pixels per row; near-diagonal ones up to three
     const bool three = (vp.flags & kViewFwd3) != 0;
 #define SUPCG_FWD(CB, AX, NC) \
-    fwd_ray2<CB, AX, NC>(P, vp, tm, patch0, wbars, n_outer, n_inner, uA, uB, u_last, tf, tl, &bad, &timed_out, acc)
+    fwd_ray2<CB, AX, NC>(P, vp, tm, patch0, wbars, rowtab[warp], n_outer, n_inner, uA, uB, u_last, tf, tl, &bad, \
+                         &timed_out, acc)
     if (uw0 > u_last) {
         // a warp past the block's last bin
     } else if (classB) {
