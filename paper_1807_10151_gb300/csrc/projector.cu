@@ -485,15 +485,15 @@ constexpr int kBwdGroup = 128;                                           // thre
 constexpr int kBwdThreads = kBwdSplit * kBwdGroup;
 constexpr int kBwdRowStep = kBwdGroup / kBwdTileJ;                       // 4
 
-// One sinogram: 32 x 32 pixel tiles, 8 pixels per thread.  Two sinograms (the
-// solver's R^T r and R^T q, one pass): 16 x 32 tiles, 4 pixels per thread, each
-// pixel's weights evaluated once and applied to both.  Either way a pixel sums
-// its views in the same order (same groups, folds and parts), so each output
-// has the same bits as from the one-sinogram kernel.
+// Tiles of 32 x 32 pixels, 8 per thread, over one sinogram or, DUAL, two (the
+// solver's R^T r and R^T q in one pass: each pixel's weights evaluated once and
+// applied to both; twice the sums per thread, so two blocks per SM instead of
+// three).  Either way a pixel sums its views in the same order (same groups,
+// folds and parts), so each output has the same bits as from the one-sinogram kernel.
 template <bool DUAL>
 struct BwdShape {
     static constexpr int NS = DUAL ? 2 : 1;                        // sinograms
-    static constexpr int TI = DUAL ? kBwdTileI / 2 : kBwdTileI;    // tile rows
+    static constexpr int TI = kBwdTileI;                           // tile rows
     static constexpr int PX = TI * kBwdTileJ / kBwdGroup;          // pixels per thread
 };
 
@@ -570,7 +570,7 @@ __device__ __forceinline__ void bwd_view_x2(const ViewP &vp, float pb0, const ui
 // g from r and h from q (h = A p for the beta of the next step of Algorithm 2,
 // deferred to this pass: alpha takes p^T A p from the forward projector's ||q||^2).
 template <bool DUAL>
-__global__ void __launch_bounds__(kBwdThreads, 3) k_backward(const Prob *__restrict__ probs,
+__global__ void __launch_bounds__(kBwdThreads, DUAL ? 2 : 3) k_backward(const Prob *__restrict__ probs,
                                                           const int *__restrict__ prefix, int count, int mode)
 {
     constexpr int NS = BwdShape<DUAL>::NS, TI = BwdShape<DUAL>::TI, PX = BwdShape<DUAL>::PX;
