@@ -137,7 +137,7 @@ struct supcg_geometry_s {
     FFTPlan fx, fy;
     ViewP *dviews = nullptr;
     int *dvlist = nullptr;
-    int *dtorder = nullptr;         // forward tile order, ceil(U / 32) entries
+    int *dborder = nullptr;         // forward block order, V x ceil(U / 32) entries
     float4 *dtwx = nullptr, *dtwy = nullptr;   // double-float twiddles
     Workspace *ws_ops = nullptr;    // standalone operators, `ops_batch` images
     int ops_batch = 0;
@@ -156,20 +156,50 @@ static int fwd_box_width(const supcg_geometry_s *g)
     return round_up((int)ceil(span + 11.0), 4);
 }
 
-// Forward tiles in launch order: by the distance of the tile's middle bin from
-// the detector centre, so that the tiles whose rays cross the most rows start
-// first and the grid ends on short blocks.
-static int upload_tile_order(supcg_geometry_s *g)
+// Forward blocks in launch order, longest first: a block (view, bin tile) lasts
+// about as long as its slowest warp walks, i.e. the rows that the union of that
+// warp's rays can meet (the row ranges of the kernel's fwd_row_range, here in FP64,
+// plus a fixed cost).  Starting the long blocks first lets the grid end on short
+// ones; with the view-major order a view's long central tiles could start last.
+// Entry i is vidx * ntu + tile, vidx indexing the class-A-then-class-B view list.
+static int upload_block_order(supcg_geometry_s *g)
 {
-    std::vector<int> ord(g->ntu);
-    std::vector<double> dist(g->ntu);
+    const int nv = g->V, ntu = g->ntu;
     const double uc = 0.5 * (g->U - 1) - g->off / g->ds;
-    for (int t = 0; t < g->ntu; ++t) {
-        ord[t] = t;
-        dist[t] = fabs(0.5 * (t * g->BU + std::min(g->U, (t + 1) * g->BU) - 1) - uc);
+    std::vector<double> cost((size_t)nv * ntu);
+    for (int vi = 0; vi < nv; ++vi) {
+        const ViewP &vp = g->views[g->vlist[vi]];
+        const bool classB = vi >= g->nA;
+        const int n_outer = classB ? g->nx : g->ny, n_inner = classB ? g->ny : g->nx;
+        const double L = -(double)vp.hwq - 1.0, H = (double)n_inner + vp.hwq;
+        for (int t = 0; t < ntu; ++t) {
+            double longest = 0.0;
+            for (int w0 = t * g->BU; w0 < std::min(g->U, (t + 1) * g->BU); w0 += 64) {
+                int lo = n_outer, hi = -1;
+                for (int u = w0; u < std::min(std::min(g->U, (t + 1) * g->BU), w0 + 64); ++u) {
+                    const double base = (double)vp.a_tau * ((double)u - uc) + vp.g0;
+                    int l, h;
+                    if (fabs((double)vp.b_o) < 1e-20) {
+                        const bool in = base >= L && base <= H;
+                        l = in ? 0 : n_outer;
+                        h = in ? n_outer - 1 : -1;
+                    } else {
+                        const double ra = (L - base) / vp.b_o, rb = (H - base) / vp.b_o;
+                        l = std::max(0, (int)floor(std::min(ra, rb) - 1.0));
+                        h = std::min(n_outer - 1, (int)ceil(std::max(ra, rb) + 1.0));
+                    }
+                    lo = std::min(lo, l);
+                    hi = std::max(hi, h);
+                }
+                longest = std::max(longest, (double)std::max(0, hi - lo + 1));
+            }
+            cost[(size_t)vi * ntu + t] = longest + 32.0;   // + the block's fixed cost, in rows
+        }
     }
-    std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return dist[a] < dist[b]; });
-    SUPCG_CUDA_TRY(cudaMemcpy(g->dtorder, ord.data(), sizeof(int) * g->ntu, cudaMemcpyHostToDevice));
+    std::vector<int> ord((size_t)nv * ntu);
+    for (size_t i = 0; i < ord.size(); ++i) ord[i] = (int)i;
+    std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+    SUPCG_CUDA_TRY(cudaMemcpy(g->dborder, ord.data(), sizeof(int) * ord.size(), cudaMemcpyHostToDevice));
     return SUPCG_OK;
 }
 
@@ -331,7 +361,7 @@ extern "C" int supcg_create_geometry(int nx, int ny, double pixel_size, int n_vi
     g->fy.twf = g->dtwy;
     if (cudaMalloc(&g->dviews, sizeof(ViewP) * n_views) != cudaSuccess ||
         cudaMalloc(&g->dvlist, sizeof(int) * n_views) != cudaSuccess ||
-        cudaMalloc(&g->dtorder, sizeof(int) * ((n_bins + 31) / 32)) != cudaSuccess) {
+        cudaMalloc(&g->dborder, sizeof(int) * (size_t)n_views * ((n_bins + 31) / 32)) != cudaSuccess) {
         supcg_destroy_geometry(g);
         return SUPCG_ERR_NOMEM;
     }
@@ -340,7 +370,7 @@ extern "C" int supcg_create_geometry(int nx, int ny, double pixel_size, int n_vi
         supcg_destroy_geometry(g);
         return SUPCG_ERR_CUDA;
     }
-    if ((rc = upload_tile_order(g))) {
+    if ((rc = upload_block_order(g))) {
         supcg_destroy_geometry(g);
         return rc;
     }
@@ -357,7 +387,7 @@ extern "C" int supcg_set_tiling(supcg_geometry g, int fwd_bins_per_block)
     g->BU = fwd_bins_per_block;
     g->BW = bw;
     g->ntu = (g->U + g->BU - 1) / g->BU;
-    int rc = upload_tile_order(g);
+    int rc = upload_block_order(g);
     if (rc) return rc;
     // workspaces hold launch shapes and TMA boxes of the old tiling
     free_ws(g->ws_ops);
@@ -383,7 +413,7 @@ extern "C" int supcg_destroy_geometry(supcg_geometry g)
     free_ws(g->ws_batch);
     if (g->dviews) cudaFree(g->dviews);
     if (g->dvlist) cudaFree(g->dvlist);
-    if (g->dtorder) cudaFree(g->dtorder);
+    if (g->dborder) cudaFree(g->dborder);
     if (g->dtwx) cudaFree(g->dtwx);
     if (g->dtwy) cudaFree(g->dtwy);
     delete g;
@@ -497,7 +527,7 @@ static int ws_create(const std::vector<supcg_geometry> &gs, Workspace **out)
         P.C = (double2 *)ptrs[11]; P.sc = (Scal *)ptrs[12]; P.partial = (double *)ptrs[13];
         P.counter = (unsigned *)ptrs[14]; P.bar = (unsigned *)ptrs[15]; P.Dtab = (float2 *)ptrs[16];
         P.bsplit = (float2 *)ptrs[17]; P.tilecnt = (unsigned *)ptrs[18];
-        P.torder = g->dtorder;
+        P.border = g->dborder;
         P.nx = g->nx; P.ny = g->ny; P.V = g->V; P.U = g->U;
         P.nxp = g->nxp; P.nyp = g->nyp; P.Up = g->Up;
         P.BU = g->BU; P.BW = g->BW; P.ntu = g->ntu; P.nA = g->nA; P.nB = g->nB;

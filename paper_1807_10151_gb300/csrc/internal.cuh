@@ -179,7 +179,7 @@ struct Prob {
     int bwin;              // backprojector: bins staged per view and tile (multiple of 4)
     const ViewP *views;    // [V]
     const int *vlist;      // [nA + nB]: class-A views, then class-B views
-    const int *torder;     // [ntu]: forward bin tiles, nearest the detector centre (most rows) first
+    const int *border;     // [V * ntu]: forward blocks (vidx * ntu + tile), longest first
     FFTPlan fx, fy;
     double mu, rho;
     double r2;             // r^2 of the Bayesian criterion (Eq. (2.3)); 0: least squares

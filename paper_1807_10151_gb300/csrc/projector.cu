@@ -2,8 +2,9 @@
 // Eq. (2.2): normal equations R^T R x = R^T b).
 //
 // Forward (ray-driven, gather over pixels).  A block owns one view and up to
-// 128 consecutive bins, two rays per thread; blocks run in tile-rank order
-// (every view's central tile first), so the grid ends on short blocks.  Views are split in two classes:
+// 128 consecutive bins, two rays per thread; blocks run longest first (an order
+// the host computes from the rows each block's warps walk), so the grid ends on
+// short blocks.  Views are split in two classes:
 // class A (|cos| >= |sin|) walks image rows, class B walks image columns, and
 // class B reads the transposed image x^T so that both classes walk contiguous
 // rows of the array they read.  Each warp stages chunks of kRowsPerChunk rows
@@ -340,10 +341,9 @@ __global__ void __launch_bounds__(kFwdThreads, 10) k_forward(const Prob *__restr
     const Prob &P = probs[pi];
     if (mode != FWD_PLAIN && P.sc->done) return;
 
-    // rank-major: every view's tile of rank 0 (the most rows), then rank 1, ...
-    const int nv = P.nA + P.nB;
-    const int rank = local / nv, vidx = local - rank * nv;
-    const int tile = P.torder[rank];
+    // blocks longest first (the host's order of (view, tile) by the rows their warps walk)
+    const int item = P.border[local];
+    const int vidx = item / P.ntu, tile = item - vidx * P.ntu;
     const bool classB = vidx >= P.nA;
     const int v = P.vlist[vidx];
     const ViewP vp = P.views[v];
