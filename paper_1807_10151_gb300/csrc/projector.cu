@@ -590,7 +590,10 @@ __global__ void __launch_bounds__(kBwdThreads, DUAL ? 2 : 3) k_backward(const Pr
     const int bwin = P.bwin;
     const int qoff = kBwdViewChunk * bwin;   // second sinogram's windows after the first's
     const int tiles_j = (P.nx + kBwdTileJ - 1) / kBwdTileJ;
-    const int tile = local / kBwdViewParts, vpart = local - tile * kBwdViewParts;   // this block's part of the views
+    // part-major: every tile's first part, then its second, ...; the last part has the
+    // fewest view chunks, so the grid's final (partial) wave holds the shortest blocks
+    const int ntiles_p = (prefix[pi + 1] - prefix[pi]) / kBwdViewParts;
+    const int vpart = local / ntiles_p, tile = local - vpart * ntiles_p;   // this block's part of the views
     const int ti = tile / tiles_j, tj = tile - ti * tiles_j;
     const int i0 = ti * TI, j0 = tj * kBwdTileJ;
     const int t = threadIdx.x;
