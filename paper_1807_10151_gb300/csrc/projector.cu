@@ -296,7 +296,9 @@ __device__ __forceinline__ void fwd_ray2(const Prob &P, const ViewP &vp, const C
                 inside = inside && min(qa, qb) >= 1 && max(qa, qb) <= BW - NC - 1;
             }
             const int pb = patch0 + buf * box_elems;
-            if (inside) {
+            // axis-aligned views (two in a uniform set) take the scalar path: no packed copy of
+            // the row loop for them, less code competing for the instruction cache
+            if (!AXIS && inside) {
                 fwd_rows2<CLASS_B, AXIS, NC>(P, vp, tau2, pk2(qm[0], qm[1]), o0, rb, re, qs, pb, rtab, sum, comp);
             } else {
 #pragma unroll
@@ -577,7 +579,7 @@ __global__ void __launch_bounds__(kBwdThreads, DUAL ? 2 : 3) k_backward(const Pr
     // proj_dyn: [2][NS][kBwdViewChunk][bwin] sinogram windows
     __shared__ ViewP vsh[2][kBwdViewChunk];
     __shared__ int ulo_sh[2][kBwdViewChunk];
-    __shared__ int kind_sh[2][kBwdViewChunk];   // variant: axis / three bins / two bins, + 3 if a window check is needed
+    __shared__ int kind_sh[2][kBwdViewChunk];   // variant: three bins (1) / two bins (2), + 3 if a window check is needed; axis 3
     __shared__ float2 comb[kBwdGroup * NS * PX];   // second group's sums, combined by the first
     __shared__ double red[40];
     __shared__ int bad_sh;
@@ -653,7 +655,8 @@ __global__ void __launch_bounds__(kBwdThreads, DUAL ? 2 : 3) k_backward(const Pr
                     const int q = magic_int(ceil_magic(__fsub_rn(__fsub_rn(smc, pbc), vp.hwu))) - lo;
                     inside = inside && q >= 1 && q <= bwin - nc - 1;
                 }
-                kind = ((vp.flags & kViewAxis) ? 0 : (nc == 3 ? 1 : 2)) + (inside ? 0 : 3);
+                // axis-aligned views (two in a uniform set) always take the checked scalar path
+                kind = ((vp.flags & kViewAxis) ? 3 : (nc == 3 ? 1 : 2) + (inside ? 0 : 3));
             }
             ulo_sh[buf][t] = lo;
             kind_sh[buf][t] = kind;
@@ -715,8 +718,7 @@ __global__ void __launch_bounds__(kBwdThreads, DUAL ? 2 : 3) k_backward(const Pr
                     }
                     const int kind = kind_sh[buf][vv];
                     if (kind < 3) {
-                        if (kind == 0) bwd_view_x2<true, 2, PX, NS>(vp, pb0, sm2, wr, lo, qoff, t2);
-                        else if (kind == 1) bwd_view_x2<false, 3, PX, NS>(vp, pb0, sm2, wr, lo, qoff, t2);
+                        if (kind == 1) bwd_view_x2<false, 3, PX, NS>(vp, pb0, sm2, wr, lo, qoff, t2);
                         else bwd_view_x2<false, 2, PX, NS>(vp, pb0, sm2, wr, lo, qoff, t2);
                     } else {   // a window check is needed: the scalar path
                         float sm[PX], t4[NS * PX];
