@@ -1,7 +1,7 @@
 // CG vector algebra of U_PCG (Algorithm 2) and the state handling of
 // SupPCG (Algorithm 3): axpys with FP64-reduced inner products, the
-// termination test, staging of caller images into the padded / transposed
-// layouts the projector reads, and per-iteration logging.
+// termination test, and staging of caller images into the padded / transposed
+// layouts the projector reads.
 #include "internal.cuh"
 
 namespace supcg {
@@ -141,14 +141,26 @@ __global__ void __launch_bounds__(256) k_pupdate(const Prob *__restrict__ probs,
     const int ti = local / tiles_j, tj = local - ti * tiles_j;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     double s = 0.0, spp = 0.0;   // g^T p and ||p||^2
-    for (int r = ty; r < 32; r += 8) {
-        const int i = ti * 32 + r, j = tj * 32 + tx;
+    // the thread's four rows: every load issued before the first store
+    float pv[4], zv[4], gv[4];
+    bool in[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int i = ti * 32 + ty + 8 * q, j = tj * 32 + tx;
+        in[q] = i < P.ny && j < P.nx;   // the padding of p stays 0
+        const size_t e = in[q] ? (size_t)i * P.nxp + j : 0;
+        pv[q] = in[q] ? P.p[e] : 0.0f;
+        zv[q] = in[q] ? z[e] : 0.0f;
+        gv[q] = in[q] ? P.g[e] : 0.0f;
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int r = ty + 8 * q;
         float pn = 0.0f;
-        if (i < P.ny && j < P.nx) {   // the padding of p stays 0
-            const size_t e = (size_t)i * P.nxp + j;
-            pn = __fmaf_rn(beta, P.p[e], -z[e]);
-            P.p[e] = pn;
-            s += (double)P.g[e] * (double)pn;
+        if (in[q]) {
+            pn = __fmaf_rn(beta, pv[q], -zv[q]);
+            P.p[(size_t)(ti * 32 + r) * P.nxp + tj * 32 + tx] = pn;
+            s += (double)gv[q] * (double)pn;
             spp += (double)pn * (double)pn;
         }
         sh[r][tx] = pn;
@@ -282,15 +294,25 @@ __global__ void __launch_bounds__(kRedThreads) k_xupdate(const Prob *__restrict_
         return;
     }
     const float al = (float)sc->alpha;
-    const size_t tot = (size_t)P.ny * P.nxp;
+    const size_t tot = (size_t)P.ny * P.nxp;   // a multiple of 4: rows are padded to 16 bytes
     float *tr = P.trace ? P.trace + (size_t)sc->k * P.ny * P.nx : nullptr;
-    for (size_t e = (size_t)local * kVecPerBlock + threadIdx.x; e < tot && e < (size_t)(local + 1) * kVecPerBlock;
-         e += kRedThreads) {
-        const float xv = __fmaf_rn(al, P.p[e], P.x[e]);
-        P.x[e] = xv;
+    // one float4 of x and of p per thread (kVecPerBlock = 4 x kRedThreads elements per block)
+    const size_t e4 = (size_t)local * kRedThreads + threadIdx.x;
+    if (4 * e4 < tot) {
+        const float4 pv = reinterpret_cast<const float4 *>(P.p)[e4];
+        float4 xv = reinterpret_cast<const float4 *>(P.x)[e4];
+        xv.x = __fmaf_rn(al, pv.x, xv.x);
+        xv.y = __fmaf_rn(al, pv.y, xv.y);
+        xv.z = __fmaf_rn(al, pv.z, xv.z);
+        xv.w = __fmaf_rn(al, pv.w, xv.w);
+        reinterpret_cast<float4 *>(P.x)[e4] = xv;
         if (tr) {
-            const int i = (int)(e / P.nxp), j = (int)(e - (size_t)i * P.nxp);
-            if (j < P.nx) tr[(size_t)i * P.nx + j] = xv;
+            const float v4[4] = {xv.x, xv.y, xv.z, xv.w};
+            for (int q = 0; q < 4; ++q) {
+                const size_t e = 4 * e4 + q;
+                const int i = (int)(e / P.nxp), j = (int)(e - (size_t)i * P.nxp);
+                if (j < P.nx) tr[(size_t)i * P.nx + j] = v4[q];
+            }
         }
     }
 }
