@@ -183,7 +183,8 @@ int supcg_solve(supcg_geometry g, const float *d_b, float *d_x, const supcg_para
 
 /* supcg_solve with HOST buffers: copies h_b and h_x (x_0) to the device,
  * solves, and copies x_{k-1/2} back into h_x.  Page-locked host memory gives
- * the fastest copies.  Synchronous. */
+ * the fastest copies.  The device copies are allocated on the first call and
+ * kept with the geometry until it is destroyed.  Synchronous. */
 int supcg_solve_host(supcg_geometry g, const float *h_b, float *h_x, const supcg_params *p,
                      supcg_report *rep, void *stream);
 

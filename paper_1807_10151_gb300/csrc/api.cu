@@ -138,6 +138,7 @@ struct supcg_geometry_s {
     ViewP *dviews = nullptr;
     int *dvlist = nullptr;
     int *dborder = nullptr;         // forward block order, V x ceil(U / 32) entries
+    float *host_db = nullptr, *host_dx = nullptr;   // supcg_solve_host's device copies of b and x (first use)
     float4 *dtwx = nullptr, *dtwy = nullptr;   // double-float twiddles
     Workspace *ws_ops = nullptr;    // standalone operators, `ops_batch` images
     int ops_batch = 0;
@@ -414,6 +415,8 @@ extern "C" int supcg_destroy_geometry(supcg_geometry g)
     if (g->dviews) cudaFree(g->dviews);
     if (g->dvlist) cudaFree(g->dvlist);
     if (g->dborder) cudaFree(g->dborder);
+    if (g->host_db) cudaFree(g->host_db);
+    if (g->host_dx) cudaFree(g->host_dx);
     if (g->dtwx) cudaFree(g->dtwx);
     if (g->dtwy) cudaFree(g->dtwy);
     delete g;
@@ -1034,18 +1037,17 @@ extern "C" int supcg_solve_host(supcg_geometry g, const float *h_b, float *h_x, 
     int rc = check_params(p);
     if (rc) return rc;
     cudaStream_t st = (cudaStream_t)stream;
-    float *db = nullptr, *dx = nullptr;
     const size_t nb = sizeof(float) * (size_t)g->V * g->U, nx = sizeof(float) * (size_t)g->nx * g->ny;
-    SUPCG_CUDA_TRY(cudaMallocAsync(&db, nb, st));
-    SUPCG_CUDA_TRY(cudaMallocAsync(&dx, nx, st));
+    // device copies kept with the geometry (like its workspace): no allocation per call
+    if (!g->host_db) SUPCG_CUDA_TRY(cudaMalloc(&g->host_db, nb));
+    if (!g->host_dx) SUPCG_CUDA_TRY(cudaMalloc(&g->host_dx, nx));
+    float *db = g->host_db, *dx = g->host_dx;
     SUPCG_CUDA_TRY(cudaMemcpyAsync(db, h_b, nb, cudaMemcpyHostToDevice, st));
     SUPCG_CUDA_TRY(cudaMemcpyAsync(dx, h_x, nx, cudaMemcpyHostToDevice, st));
     rc = supcg_solve(g, db, dx, p, rep, nullptr, stream);
     if (rc == SUPCG_OK || rc < SUPCG_ERR_NOMEM) {
         SUPCG_CUDA_TRY(cudaMemcpyAsync(h_x, dx, nx, cudaMemcpyDeviceToHost, st));
     }
-    cudaFreeAsync(db, st);
-    cudaFreeAsync(dx, st);
     SUPCG_CUDA_TRY(cudaStreamSynchronize(st));
     return rc;
 }
