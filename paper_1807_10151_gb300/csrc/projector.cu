@@ -267,11 +267,15 @@ __device__ __forceinline__ void fwd_ray2(const Prob &P, const ViewP &vp, const C
     const int w_lo = __reduce_min_sync(0xffffffffu, r_lo), w_hi = __reduce_max_sync(0xffffffffu, r_hi);
     const int c_first = w_hi >= w_lo ? w_lo / RC : 0;
     const int nch = w_hi >= w_lo ? w_hi / RC - c_first + 1 : 0;   // chunks with at least one of the warp's rows
+    // each box's first inner index, computed once (every lane: the copy and the rows use it)
+    int qs_buf[kFwdBufs];
+#pragma unroll
+    for (int ci = 0; ci < kFwdBufs; ++ci) qs_buf[ci] = fwd_box_start(vp, tf, tl, (c_first + ci) * RC);
     if (lane == 0) {
         for (int ci = 0; ci < kFwdBufs && ci < nch; ++ci) {
             const int c = c_first + ci;
             mbar_expect_tx(&bars[ci], box_elems * 4);
-            tma_load_2d(proj_dyn + patch0 + ci * box_elems, tm, fwd_box_start(vp, tf, tl, c * RC), c * RC, &bars[ci]);
+            tma_load_2d(proj_dyn + patch0 + ci * box_elems, tm, qs_buf[ci], c * RC, &bars[ci]);
         }
     }
     for (int ci = 0; ci < nch; ++ci) {
@@ -282,7 +286,7 @@ __device__ __forceinline__ void fwd_ray2(const Prob &P, const ViewP &vp, const C
         const int rows = min(RC, n_outer - o0);
         const int rb = max(0, w_lo - o0), re = min(rows, w_hi - o0 + 1);
         if (ok && rb < re) {
-            const int qs = fwd_box_start(vp, tf, tl, o0);
+            const int qs = qs_buf[buf];
             float qm[2];
             bool inside = true;
 #pragma unroll
@@ -316,10 +320,12 @@ __device__ __forceinline__ void fwd_ray2(const Prob &P, const ViewP &vp, const C
             break;
         }
         __syncwarp();
-        if (lane == 0 && ci + kFwdBufs < nch) {
-            mbar_expect_tx(&bars[buf], box_elems * 4);
-            tma_load_2d(proj_dyn + patch0 + buf * box_elems, tm, fwd_box_start(vp, tf, tl, (c + kFwdBufs) * RC),
-                        (c + kFwdBufs) * RC, &bars[buf]);
+        if (ci + kFwdBufs < nch) {
+            qs_buf[buf] = fwd_box_start(vp, tf, tl, (c + kFwdBufs) * RC);
+            if (lane == 0) {
+                mbar_expect_tx(&bars[buf], box_elems * 4);
+                tma_load_2d(proj_dyn + patch0 + buf * box_elems, tm, qs_buf[buf], (c + kFwdBufs) * RC, &bars[buf]);
+            }
         }
     }
 #pragma unroll
