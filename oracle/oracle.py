@@ -71,6 +71,7 @@ def _L():
                                         C.c_long, C.c_int,
                                         dp, dp, ip, ip, lp] + [dp, dp, dp, lp, dp, dp, dp, dp]
                                        + [C.c_double, C.c_double])
+            lib.orc_art_rays.argtypes = [lp, ip, dp, lp, C.c_long, dp, C.c_double, C.c_double, dp, dp]
             lib.orc_num_threads.restype = C.c_int
             lib.orc_conv3x3.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, dp, dp, dp, C.c_int, dp]
             lib.orc_conv3x3_backward.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, dp, dp, dp, dp, dp, dp]
@@ -321,6 +322,61 @@ def suppcg(R: CSR, b, x0=None, a=0.995, gamma=0.5, K=1, eps=-1.0, max_iter=50,
 
 
 # ------------------------------------------------------------------ learned perturbation layers
+def art_spacing(g: Geometry):
+    """Smallest bin spacing S at which two rays of one view share no pixel.
+
+    A pixel meets ray u when its centre projects within E = (d/ds)(|cos| +
+    |sin|)/2 bins of u (the footprint of a square pixel; on the boundary only
+    for axis-aligned views), so rays S >= 2E + (a little) apart touch disjoint
+    pixel sets: S = floor(2 max_v E_v) + 1."""
+    r = g.d / g.ds
+    E = 0.0
+    for th in g.theta:
+        q = th / (0.5 * np.pi)
+        if abs(q - round(q)) < 1e-12:
+            c, s = (1.0, 0.0) if int(round(q)) % 2 == 0 else (0.0, 1.0)
+        else:
+            c, s = abs(np.cos(th)), abs(np.sin(th))
+        E = max(E, r * (c + s) / 2.0)
+    return int(np.floor(2.0 * E)) + 1
+
+
+def art_order(g: Geometry, S=None):
+    """One ART cycle's ray order (the paper only says that a cycle visits every
+    equation once): views in order; within a view the residue classes u = c
+    (mod S), c = 0 .. S-1, each in increasing u.  Rays of one class touch
+    disjoint pixels, so their updates commute."""
+    S = art_spacing(g) if S is None else S
+    order = [v * g.U + u for v in range(g.V) for c in range(S) for u in range(c, g.U, S)]
+    return np.asarray(order, dtype=np.int64)
+
+
+def art(R: CSR, b, r=5.0, lam=1e-2, cycles=1, mu=None, K=0, a=1 - 1e-5, gamma=1e-2, max_trials=10_000,
+        x0=None, u0=None, order=None):
+    """ART for the Bayesian criterion of Eq. (2.3), Sec. 3.4 (Herman, Hurwitz,
+    Lent): `cycles` full cycles over the rays in art_order, from x = mu_X (the
+    prior mean; gray_level(b) when None) and u = 0.  K > 0 gives SupART: before
+    every cycle x <- S_TV(x, l, a, gamma, K) (Algorithm 1), the perturbation
+    step of superiorization.  Returns x, the auxiliary u, l and the status."""
+    g = R.geom
+    b = _f64(b).ravel()
+    if mu is None:
+        mu = gray_level(g, b)
+    x = np.full(g.n, float(mu)) if x0 is None else _f64(x0).ravel().copy()
+    u = np.zeros(g.m) if u0 is None else _f64(u0).ravel().copy()
+    order = art_order(g) if order is None else np.ascontiguousarray(order, dtype=np.int64)
+    ell, rc = 0, 0
+    for _ in range(int(cycles)):
+        if K > 0:
+            rc, s, ell, _tr = stv(x.reshape(g.ny, g.nx), ell, a, gamma, K, max_trials)
+            if rc != 0:
+                break
+            x = x + s.ravel()
+        _L().orc_art_rays(_l(R.rp), _i(R.ci), _d(R.va), _l(order), order.size, _d(b), float(r), float(lam),
+                          _d(x), _d(u))
+    return {"x": x.reshape(g.ny, g.nx), "u": u.reshape(g.V, g.U), "ell": ell, "status": rc, "mu": float(mu)}
+
+
 def conv3x3(x, W, bias=None, relu=False):
     """3x3 convolution with zero padding: x [cin][ny][nx], W [cout][cin][3][3]."""
     x, W = _f64(x), _f64(W)

@@ -20,6 +20,9 @@
  *   - U_PCG(x, p, h) ............................................ Algorithm 2
  *   - M = F^-1 D F with h(w) = (|w|+mu)(rho+(1-rho)cos w) ....... Eq. (3.2)
  *   - SupPCG(x0, a, gamma, K, eps) .............................. Algorithm 3
+ *   - ART for the Bayesian criterion (the row-action method of Herman,
+ *     Hurwitz and Lent that Sec. 3.4 uses) and its superiorization SupART
+ *                                                          Sec. 3.4, Eq. (2.3)
  *
  * The paper leaves the entries of R to its software package.  Here R_{ray,pixel}
  * is the Euclidean length of the intersection of the ray (a straight line) with
@@ -612,6 +615,35 @@ int orc_suppcg(long m, long n,
 out:
     free(x); free(g); free(z); free(p); free(h); free(s); free(r); free(q);
     return rc;
+}
+
+/* ------------------------------------------------------------------ */
+/* ART for the Bayesian criterion (Sec. 3.4, Eq. (2.3))                  */
+/* ------------------------------------------------------------------ */
+
+/* The row-action method of Herman, Hurwitz and Lent named in Sec. 3.4 (a
+ * Kaczmarz sweep over the consistent system r R y + u = r (b - R mu_X) in the
+ * unknowns y = x - mu_X and one auxiliary value u_i per ray, whose
+ * minimum-norm solution minimises r^2 ||R x - b||^2 + ||x - mu_X||^2, the
+ * criterion of Eq. (2.3)).  Starting from x = mu_X, u = 0, ray i updates
+ *     c   = lambda (r (b_i - <R_i, x>) - u_i) / (1 + r^2 ||R_i||^2),
+ *     x  <- x + r c R_i,      u_i <- u_i + c,
+ * with lambda the relaxation.  This function applies the updates for the rays
+ * order[0 .. count-1] in that order (rows of the CSR R, ids v U + u). */
+void orc_art_rays(const long *rp, const int *ci, const double *va, const long *order, long count,
+                  const double *b, double r, double lam, double *x, double *uaux)
+{
+    for (long t = 0; t < count; ++t) {
+        const long i = order[t];
+        double dot = 0.0, nn = 0.0;
+        for (long k = rp[i]; k < rp[i + 1]; ++k) {
+            dot += va[k] * x[ci[k]];
+            nn += va[k] * va[k];
+        }
+        const double c = lam * (r * (b[i] - dot) - uaux[i]) / (1.0 + r * r * nn);
+        for (long k = rp[i]; k < rp[i + 1]; ++k) x[ci[k]] += r * c * va[k];
+        uaux[i] += c;
+    }
 }
 
 int orc_num_threads(void)
