@@ -9,7 +9,7 @@ Algorithm 3 (S_TV, forward projection with residual, backprojection,
 preconditioner, CG scalars and axpys, forward and back projection of p).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload plain512|batched64|large2048|learned512|sweep243]
+                  [--workload plain512|batched64|large2048|learned512|sweep243|art512]
 
 --impl reference times the FP64 CPU oracle on the host cores on the same
 workload (it is the only other implementation of the method here).
@@ -29,6 +29,11 @@ one batched sweep: 180 grid points (K, a, gamma, mu, rho; rho = 0.4 excluded)
 x 15 iterations on a 243^2 / 360-view / 345-bin head stand-in (Poisson 1e5),
 scored by the selective error of Eq. (4.1), timed against the same solves one
 after another.
+--workload art512: ART on the Bayesian criterion and SupART (Sec. 3.4) on the
+512^2 / 720-view Poisson workload with Table 1's parameters (ART r = 5,
+lambda = 1e-2; SupART K = 10, a = 1 - 1e-5, gamma = 1e-2, r = 5,
+lambda = 5e-2): cycles/s on the GPU, and one cycle of the FP64 oracle on the
+host cores.
 --workload large2048: 8 slices of 2048^2, 2880 views, 2900 bins (40 ellipses
 on a textured background, Poisson 1e4 photons): FP32- and BF16-stored
 projector pair timed on the batch, errors of both against the FP64 oracle on
@@ -311,6 +316,63 @@ def run_sweep(args, dev):
     return 0
 
 
+def run_art(args, dev):
+    """ART and SupART (Sec. 3.4) on the 512^2 / 720-view workload: cycles per
+    second, each cycle visiting every ray once (V x S grid barriers: the rays
+    of one view and residue class run in parallel)."""
+    import numpy as np
+    import torch
+    import paper_1807_10151_gb300 as S
+    G, b_host = make_problem(0, dev)
+    b = torch.tensor(b_host, device=dev)
+    st = torch.cuda.current_stream()
+    art_kw = dict(r=5.0, lam=1e-2)
+    sup_kw = dict(r=5.0, lam=5e-2, K=10, a=1 - 1e-5, gamma=1e-2)
+    cycles = max(2, min(args.steps, 10))
+    for _ in range(args.warmup):
+        G.art(b, cycles=1, **art_kw)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    l0 = S.supcg_kernel_launches()
+    with ClockSampler(dev.index or 0) as clk:
+        ev[0].record(st)
+        x, rep = G.art(b, cycles=cycles, **art_kw)
+        ev[1].record(st)
+        ev[2].record(st)
+        xs, reps = G.art(b, cycles=cycles, **sup_kw)
+        ev[3].record(st)
+        torch.cuda.synchronize()
+    assert rep["status"] == 0 and reps["status"] == 0, (rep, reps)
+    t_art = ev[0].elapsed_time(ev[1]) / 1000.0
+    t_sup = ev[2].elapsed_time(ev[3]) / 1000.0
+    cpu = None
+    if not args.no_cpu_baseline:
+        from oracle import oracle as O
+        from paper_1807_10151_gb300 import synth
+        og = O.Geometry(WL["N"], V=WL["V"], U=WL["U"])
+        R = O.CSR(og)
+        t0 = time.perf_counter()
+        O.art(R, b_host, cycles=1, **art_kw)
+        t_cpu = time.perf_counter() - t0
+        cpu = {"value": 1.0 / t_cpu, "unit": "cycles/s", "cores": 1, "kind": "oracle",
+               "sample": "one ART cycle of the FP64 oracle (sequential over the 522000 rays of the explicit CSR R, "
+                         "built beforehand, not timed)"}
+    line = {
+        "metric": "ART cycles/s (Bayesian criterion, Sec. 3.4)", "value": cycles / t_art, "unit": "cycles/s",
+        "n_gpus": 1, "steps": cycles, "warmup": args.warmup, "ms_per_step": 1000.0 * t_art / cycles,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 (ray sums f64)",
+        "data": "synthetic",
+        "config": {"workload": "art_512x512_720views_725bins_poisson1e5", "art": art_kw, "supart": sup_kw,
+                   "class_barriers_per_cycle": WL["V"] * 2, "l2": "the 14 MB working set stays L2-resident"},
+        "supart": {"value": cycles / t_sup, "unit": "iterations/s (S_TV + one cycle)", "ell": reps["ell"]},
+        "gpu_launches": int(S.supcg_kernel_launches() - l0), "clocks": clk.summary(),
+    }
+    if cpu:
+        line["cpu_baseline"] = cpu
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_large(args, dev):
     """8 slices of 2048^2: FP32 vs BF16 storage of the projector pair."""
     import numpy as np
@@ -496,7 +558,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-iters", type=int, default=3)
     ap.add_argument("--workload", default="plain512",
-                    choices=["plain512", "batched64", "large2048", "learned512", "sweep243"])
+                    choices=["plain512", "batched64", "large2048", "learned512", "sweep243", "art512"])
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world = env_int("WORLD_SIZE", 1)
@@ -527,6 +589,8 @@ def main():
         return run_learned(args, dev)
     if args.workload == "sweep243":
         return run_sweep(args, dev)
+    if args.workload == "art512":
+        return run_art(args, dev)
     G, b_host = make_problem(rank, dev)
     b = torch.tensor(b_host, device=dev)
     from paper_1807_10151_gb300 import autotune

@@ -217,6 +217,50 @@ int supcg_solve_sweep(supcg_geometry g, const float *d_b, float *const *d_x, int
                       const supcg_params *ps, const float *d_ref, double se_ax, double se_ay,
                       double *d_se, supcg_report *reps, void *stream);
 
+/* ART for the Bayesian criterion of Eq. (2.3) and SupART (Sec. 3.4, the
+ * row-action method of Herman, Hurwitz and Lent with pixel basis functions).
+ * From x = mu_X and one auxiliary value u_i = 0 per ray, each ray i updates
+ *     c = lambda (r (b_i - <R_i, x>) - u_i) / (1 + r^2 ||R_i||^2),
+ *     x <- x + r c R_i,   u_i <- u_i + c
+ * (a sweep over r R (x - mu_X) + u = r (b - R mu_X), whose minimum-norm
+ * solution minimises r^2 ||R x - b||^2 + ||x - mu_X||^2); one iteration is a
+ * full cycle through the rays.  The paper does not fix the order of the
+ * rays: here the views in order and, within a view, the rays in the residue
+ * classes u = c (mod S), c = 0 .. S-1, with S = floor(2 max_v E_v) + 1 the
+ * smallest bin spacing at which two rays of a view share no pixel (E_v =
+ * (d/ds)(|cos|+|sin|)/2 the footprint half-width in bins); the rays of one
+ * class touch disjoint pixels, so the GPU runs each class in parallel and the
+ * result is that of any sequential order of the class.  R is the projectors'
+ * matrix (same entries).  SupART (K > 0): before every cycle x <- S_TV(x, l,
+ * a, gamma, K), Algorithm 1, from l = 0.  Table 1 of the paper lists r = 5,
+ * lambda = 1e-2 for ART and K = 10, a = 1 - 1e-5, gamma = 1e-2, r = 5,
+ * lambda = 5e-2 for SupART. */
+typedef struct {
+    double r;               /* signal-to-noise ratio of Eq. (2.3), > 0                     */
+    double lambda;          /* relaxation, 0 < lambda < 2                                  */
+    double mu;              /* prior mean mu_X, the starting image; NaN: estimated from b
+                               (the data's gray level, as for supcg_params.bayes_mu)       */
+    int cycles;             /* iterations (full cycles through the rays), >= 0             */
+    int K;                  /* SupART: S_TV steps before every cycle; 0: ART               */
+    double a, gamma;        /* SupART: S_TV parameters (Algorithm 1)                       */
+    long long max_trials;   /* SupART: bound on each S_TV `repeat` loop                    */
+} supcg_art_params;
+
+typedef struct {
+    int cycles;             /* cycles completed                                            */
+    long long ell;          /* l after the last S_TV (SupART)                              */
+    double mu;              /* the prior mean used                                         */
+    int status;             /* SUPCG_OK or the first error                                 */
+} supcg_art_report;
+
+/* ART / SupART on one problem: d_b FP32 [V][U] (caller-owned), d_x FP32 [ny][nx]
+ * out (x after `cycles` cycles).  The per-ray values u_i and 1 / (1 + r^2 ||R_i||^2)
+ * (FP64, 16 bytes per ray) are kept with the geometry.  Synchronous.  Errors:
+ * SUPCG_ERR_ARG, SUPCG_ERR_BACKTRACK (S_TV), SUPCG_ERR_TIMEOUT, SUPCG_ERR_NOMEM,
+ * SUPCG_ERR_CUDA. */
+int supcg_art(supcg_geometry g, const float *d_b, float *d_x, const supcg_art_params *p,
+              supcg_art_report *rep, void *stream);
+
 /* ------------------------------------------------------------------------
  * Learned perturbation network (an addition to the paper's method: the paper
  * perturbs along the normalised negative TV gradient, Sec. 3.1; this network

@@ -18,6 +18,7 @@ __all__ = [
     "supcg_create_geometry", "supcg_destroy_geometry", "supcg_project", "supcg_backproject",
     "supcg_precondition", "supcg_tv_tbar", "supcg_superiorize", "supcg_solve", "supcg_solve_host",
     "supcg_solve_batched", "supcg_status_string", "LOG_STRIDE", "EXPORTED", "solve_sweep", "SE_AXES",
+    "ArtParams", "ArtReport", "supcg_art",
 ]
 
 LOG_STRIDE = 8
@@ -30,7 +31,7 @@ EXPORTED = ["supcg_create_geometry", "supcg_destroy_geometry", "supcg_project", 
             "supcg_precondition_noalloc", "supcg_cnn_create", "supcg_cnn_destroy", "supcg_cnn_num_params",
             "supcg_cnn_get_params", "supcg_cnn_set_params", "supcg_cnn_forward", "supcg_cnn_gradients",
             "supcg_cnn_train_step", "supcg_solve_trace", "supcg_solve_learned", "supcg_set_tiling",
-            "supcg_get_tiling", "supcg_solve_sweep"]
+            "supcg_get_tiling", "supcg_solve_sweep", "supcg_art"]
 KINDS = ["forward", "backward", "fft", "stv", "vector", "cnn"]
 
 _lock = threading.Lock()
@@ -56,6 +57,20 @@ class Report(C.Structure):
     _fields_ = [("iters", C.c_int), ("k", C.c_int), ("ell", C.c_longlong), ("f_last", C.c_double),
                 ("f0", C.c_double), ("tv_last", C.c_double), ("status", C.c_int), ("n_fallback", C.c_int),
                 ("n_learned", C.c_int)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class ArtParams(C.Structure):
+    """supcg_art_params (include/supcg.h): ART / SupART of Sec. 3.4."""
+    _fields_ = [("r", C.c_double), ("lam", C.c_double), ("mu", C.c_double), ("cycles", C.c_int), ("K", C.c_int),
+                ("a", C.c_double), ("gamma", C.c_double), ("max_trials", C.c_longlong)]
+
+
+class ArtReport(C.Structure):
+    """supcg_art_report (include/supcg.h)."""
+    _fields_ = [("cycles", C.c_int), ("ell", C.c_longlong), ("mu", C.c_double), ("status", C.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}
@@ -88,6 +103,7 @@ def load(allow_build: bool = True):
         L.supcg_tv_tbar.argtypes = [vp, vp, vp, C.POINTER(d), vp]
         L.supcg_superiorize.argtypes = [vp, vp, d, d, i, ll, C.POINTER(ll), C.POINTER(i), vp]
         L.supcg_solve.argtypes = [vp, vp, vp, C.POINTER(Params), C.POINTER(Report), vp, vp]
+        L.supcg_art.argtypes = [vp, vp, vp, C.POINTER(ArtParams), C.POINTER(ArtReport), vp]
         L.supcg_solve_host.argtypes = [vp, vp, vp, C.POINTER(Params), C.POINTER(Report), vp]
         L.supcg_solve_batched.argtypes = [C.POINTER(vp), C.POINTER(vp), C.POINTER(vp), i,
                                           C.POINTER(Params), C.POINTER(Report), vp]
@@ -162,6 +178,10 @@ def supcg_tv_tbar(g, d_y, d_tbar, h_out, stream):
 
 def supcg_superiorize(g, d_x, a, gamma, K, max_trials, h_ell, h_trials, stream):
     return load().supcg_superiorize(g, d_x, a, gamma, K, max_trials, h_ell, h_trials, stream)
+
+
+def supcg_art(g, d_b, d_x, params, rep, stream):
+    return load().supcg_art(g, d_b, d_x, C.byref(params), C.byref(rep), stream)
 
 
 def supcg_solve(g, d_b, d_x, params, rep, d_log, stream):
@@ -305,6 +325,21 @@ class Geometry:
         if rc not in (0, -5):
             raise SupcgError(rc, "supcg_superiorize")
         return rc, int(e.value), list(tr)[:int(K)]
+
+    def art(self, b, r=5.0, lam=1e-2, cycles=1, mu=None, K=0, a=1 - 1e-5, gamma=1e-2, max_trials=10_000,
+            stream=None):
+        """ART on the Bayesian criterion of Eq. (2.3) (K = 0) or SupART (K > 0), Sec. 3.4:
+        `cycles` full cycles through the rays from x = mu_X (None: estimated from b).
+        Returns (x [ny][nx], report dict)."""
+        import torch
+        x = torch.empty(self.ny, self.nx, device=b.device, dtype=torch.float32)
+        p = ArtParams(float(r), float(lam), float("nan") if mu is None else float(mu), int(cycles), int(K),
+                      float(a), float(gamma), int(max_trials))
+        rep = ArtReport()
+        rc = supcg_art(self.handle, _ptr(b, torch.float32), _ptr(x, torch.float32), p, rep, _stream(stream))
+        if rc not in (0, -5):
+            raise SupcgError(rc, "supcg_art")
+        return x, rep.as_dict()
 
     def solve(self, b, x0=None, log=False, stream=None, **kw):
         """SupPCG (Algorithm 3).  Returns (x_{k-1/2}, report dict, log or None)."""

@@ -139,6 +139,8 @@ struct supcg_geometry_s {
     int *dvlist = nullptr;
     int *dborder = nullptr;         // forward block order, V x ceil(U / 32) entries
     float *host_db = nullptr, *host_dx = nullptr;   // supcg_solve_host's device copies of b and x (first use)
+    double *art_u = nullptr, *art_rn = nullptr;     // ART's per-ray values (first use)
+    int art_S = 1;                                  // ART: bin spacing of rays with disjoint pixels
     float4 *dtwx = nullptr, *dtwy = nullptr;   // double-float twiddles
     Workspace *ws_ops = nullptr;    // standalone operators, `ops_batch` images
     int ops_batch = 0;
@@ -330,6 +332,17 @@ extern "C" int supcg_create_geometry(int nx, int ny, double pixel_size, int n_vi
     // (the centres include the small correction, so only the margin pads the windows)
     (void)max_small;
     if (maxE + 0.03 >= 1.5 || g->bwin > 256) { delete g; return SUPCG_ERR_UNSUPPORTED; }
+    // ART's class spacing: two rays of a view S bins apart share no pixel when S > 2 E for every
+    // view's footprint half-width E = (d/ds)(|cos| + |sin|)/2 (FP64, exact cos/sin on the axes)
+    {
+        double e2 = 0.0;
+        for (int v = 0; v < n_views; ++v) {
+            double c, s2;
+            exact_cos_sin(g->theta[v], &c, &s2);
+            e2 = std::max(e2, r * (fabs(c) + fabs(s2)));
+        }
+        g->art_S = (int)floor(e2) + 1;
+    }
     g->nA = (int)A.size();
     g->nB = (int)B.size();
     g->vlist = A;
@@ -417,6 +430,8 @@ extern "C" int supcg_destroy_geometry(supcg_geometry g)
     if (g->dborder) cudaFree(g->dborder);
     if (g->host_db) cudaFree(g->host_db);
     if (g->host_dx) cudaFree(g->host_dx);
+    if (g->art_u) cudaFree(g->art_u);
+    if (g->art_rn) cudaFree(g->art_rn);
     if (g->dtwx) cudaFree(g->dtwx);
     if (g->dtwy) cudaFree(g->dtwy);
     delete g;
@@ -764,6 +779,64 @@ static thread_local long long t_capture_count = 0;
     } while (0)
 
 extern "C" long long supcg_kernel_launches(void) { return g_launches.load(); }
+
+// ------------------------------------------------------------------ ART / SupART (Sec. 3.4)
+extern "C" int supcg_art(supcg_geometry g, const float *d_b, float *d_x, const supcg_art_params *p,
+                         supcg_art_report *rep, void *stream)
+{
+    if (!g || !d_b || !d_x || !p || !rep) return SUPCG_ERR_ARG;
+    if (!(p->r > 0.0) || !isfinite(p->r) || !(p->lambda > 0.0) || !(p->lambda < 2.0) || p->cycles < 0 ||
+        p->K < 0 || (!isnan(p->mu) && !isfinite(p->mu)))
+        return SUPCG_ERR_ARG;
+    int rc;
+    if (p->K > 0 && (rc = check_stv(p->a, p->gamma, p->K, p->max_trials))) return rc;
+    Workspace *w;
+    if ((rc = ops_ws(g, 1, &w))) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t m = (size_t)g->V * g->U;
+    if (!g->art_u) SUPCG_CUDA_TRY(cudaMalloc(&g->art_u, sizeof(double) * m));
+    if (!g->art_rn) SUPCG_CUDA_TRY(cudaMalloc(&g->art_rn, sizeof(double) * m));
+    Prob &P = w->hp[0];
+    P.in_user = d_x;
+    P.out_user = d_x;
+    P.in_user2 = d_b;
+    P.art_u = g->art_u;
+    P.art_rn = g->art_rn;
+    P.storage = SUPCG_F32;
+    rc = ws_upload(w, st);
+    P.storage = g->storage;
+    if (rc) return rc;
+    Scal s0 = {};
+    s0.muX = isnan(p->mu) ? 0.0 : p->mu;
+    SUPCG_CUDA_TRY(cudaMemcpyAsync(P.sc, &s0, sizeof(Scal), cudaMemcpyHostToDevice, st));
+    SUPCG_CUDA_TRY(cudaMemsetAsync(P.bar, 0, 2 * sizeof(unsigned), st));
+    SUPCG_CUDA_TRY(cudaMemsetAsync(P.counter, 0, 16 * sizeof(unsigned), st));
+    LAUNCH(SUPCG_KIND_VECTOR, st, launch_stage_sino(w->L(KT_SINO, st), 1));   // b -> bpad
+    if (isnan(p->mu)) LAUNCH(SUPCG_KIND_VECTOR, st, launch_gray(w->L(KT_SINO, st)));
+    const int init_blocks = (int)std::min<size_t>(8192, (m + 1) / 2);
+    LAUNCH(SUPCG_KIND_VECTOR, st, launch_art_init(w->dp, p->r, init_blocks, st));   // norms, u = 0, x = mu_X
+    int cap = 0;
+    if ((rc = art_max_blocks(&cap))) return rc;
+    const int rays = (g->U + g->art_S - 1) / g->art_S;   // rays per class, one block each
+    const int blocks = std::max(1, std::min(cap, rays));
+    if (p->K == 0) {
+        if (p->cycles > 0)
+            LAUNCH(SUPCG_KIND_FORWARD, st, launch_art(w->dp, p->cycles, p->r, p->lambda, g->art_S, blocks, st));
+    } else {
+        for (int c = 0; c < p->cycles; ++c) {   // SupART: S_TV, then one cycle
+            LAUNCH(SUPCG_KIND_STV, st, launch_stv(w->L(KT_STV, st), p->K, p->a, p->gamma, p->max_trials, nullptr, 0));
+            LAUNCH(SUPCG_KIND_FORWARD, st, launch_art(w->dp, 1, p->r, p->lambda, g->art_S, blocks, st));
+        }
+    }
+    LAUNCH(SUPCG_KIND_VECTOR, st, launch_store_out(w->L(KT_VEC, st), 0));
+    Scal s;
+    if ((rc = read_scal(P, &s, st))) return rc;
+    rep->cycles = s.status ? 0 : p->cycles;
+    rep->ell = s.ell;
+    rep->mu = s.muX;
+    rep->status = s.status;
+    return s.status;
+}
 
 // ------------------------------------------------------------------ solve
 static int check_params(const supcg_params *p)

@@ -131,6 +131,26 @@ __device__ __forceinline__ float delta_small(const ViewP &vp, float X, float Y, 
 
 __device__ __forceinline__ float bin_pos(int u, float uc) { return __fsub_rn(__int2float_rn(u), uc); }
 
+// Outer indices [*lo, *hi] at which a ray whose centre sits at inner index
+// base + b_o * o can meet the inner range [0, n_inner): the centre within the
+// footprint half-width hwq plus one index of slack of either end.  Rows outside
+// it contribute nothing (their candidates fall on the zero fill).
+__device__ __forceinline__ void fwd_row_range(const ViewP &vp, float base, int n_inner, int n_outer, int *lo, int *hi)
+{
+    const float L = -vp.hwq - 1.0f, H = __int2float_rn(n_inner) + vp.hwq;
+    if (fabsf(vp.b_o) < 1e-20f) {
+        const bool in = base >= L && base <= H;
+        *lo = in ? 0 : n_outer;
+        *hi = in ? n_outer - 1 : -1;
+        return;
+    }
+    const float ra = __fdiv_rn(__fsub_rn(L, base), vp.b_o), rb = __fdiv_rn(__fsub_rn(H, base), vp.b_o);
+    const float fo = __int2float_rn(n_outer);
+    const float a = fminf(fmaxf(fminf(ra, rb) - 1.0f, -1.0f), fo), b = fminf(fmaxf(fmaxf(ra, rb) + 1.0f, -1.0f), fo);
+    *lo = max(0, __float2int_rd(a));
+    *hi = min(n_outer - 1, __float2int_ru(b));
+}
+
 // ----------------------------------------------------------------- FFT plan
 struct FFTPlan {
     int n;
@@ -200,6 +220,8 @@ struct Prob {
     double2 *C;            // FFT scratch [ny][nx] (FP64 complex)
     float2 *Dtab;          // h(w_r) / (nx ny) at (min(k1, ny-k1), min(k2, nx-k2)), double-float: [ny/2+1][nx/2+1]
     float2 *bsplit;        // backprojector: each sinogram's and view part's pixel sums, double-float [2][kBwdViewParts][ny][nxp]
+    double *art_u;         // ART: auxiliary value u_i per ray [V][U]
+    double *art_rn;        // ART: 1 / (1 + r^2 ||R_i||^2) per ray [V][U]
     unsigned *tilecnt;     // backprojector: parts finished per tile (reset by the last one)
     Scal *sc;
     double *partial;       // reduction partials (>= 2 * max blocks per kernel)
@@ -441,6 +463,9 @@ struct Launch {
 int launch_forward(const Launch &L, int which, int mode);
 int launch_backward(const Launch &L, int mode, int bwin);
 int launch_backward2(const Launch &L, int bwin);   // g from r and h from q in one pass
+int art_max_blocks(int *out);                                           // co-resident blocks of k_art
+int launch_art_init(const Prob *d_prob, double r, int blocks, cudaStream_t st);
+int launch_art(const Prob *d_prob, int cycles, double r, double lam, int S, int blocks, cudaStream_t st);
 int backward_blocks(int nx, int ny, int dual);
 int encode_tiled(CUtensorMap *m, CUtensorMapDataType type, int rank, void *base, const cuuint64_t *dims,
                  const cuuint64_t *strides_bytes, const cuuint32_t *box);

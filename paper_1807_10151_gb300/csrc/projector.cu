@@ -215,26 +215,6 @@ __device__ __forceinline__ int fwd_box_start(const ViewP &vp, float tf, float tl
     return lo & ~3;   // round down to a multiple of 4 floats (16-byte TMA rule)
 }
 
-// Outer indices [*lo, *hi] at which a ray whose centre sits at inner index
-// base + b_o * o can meet the inner range [0, n_inner): the centre within the
-// footprint half-width hwq plus one index of slack of either end.  Rows outside
-// it contribute nothing (their candidates fall on the zero fill).
-__device__ __forceinline__ void fwd_row_range(const ViewP &vp, float base, int n_inner, int n_outer, int *lo, int *hi)
-{
-    const float L = -vp.hwq - 1.0f, H = __int2float_rn(n_inner) + vp.hwq;
-    if (fabsf(vp.b_o) < 1e-20f) {
-        const bool in = base >= L && base <= H;
-        *lo = in ? 0 : n_outer;
-        *hi = in ? n_outer - 1 : -1;
-        return;
-    }
-    const float ra = __fdiv_rn(__fsub_rn(L, base), vp.b_o), rb = __fdiv_rn(__fsub_rn(H, base), vp.b_o);
-    const float fo = __int2float_rn(n_outer);
-    const float a = fminf(fmaxf(fminf(ra, rb) - 1.0f, -1.0f), fo), b = fminf(fmaxf(fmaxf(ra, rb) + 1.0f, -1.0f), fo);
-    *lo = max(0, __float2int_rd(a));
-    *hi = min(n_outer - 1, __float2int_ru(b));
-}
-
 // Two rays per lane (u and u + 32: 64 consecutive bins per warp); each warp
 // runs its own pipeline of kFwdBufs kRowsPerChunk-row boxes (BW columns
 // covering its 64 rays), so warps never wait for one another.  The warp walks

@@ -51,3 +51,35 @@ def test_param_struct_layout_matches_header():
     assert S.Params.bayes_r.offset == 80 and S.Params.bayes_mu.offset == 88
     assert C.sizeof(S.Params) == 96
     assert S.Report.ell.offset == 8 and S.Report.n_learned.offset == 48 and C.sizeof(S.Report) == 56
+
+
+def test_art_struct_layout_matches_the_compiled_header(tmp_path):
+    """supcg_art_params / supcg_art_report as the C compiler lays them out from
+    include/supcg.h, against the binding's ctypes structures."""
+    import shutil
+    import subprocess
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    inc = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+    src = tmp_path / "layout.c"
+    src.write_text(
+        "#include <stddef.h>\n#include <stdio.h>\n#include \"supcg.h\"\n"
+        "int main(void) {\n"
+        "  printf(\"%zu %zu %zu %zu %zu %zu %zu %zu %zu\\n\", offsetof(supcg_art_params, r),\n"
+        "         offsetof(supcg_art_params, lambda), offsetof(supcg_art_params, mu),\n"
+        "         offsetof(supcg_art_params, cycles), offsetof(supcg_art_params, K),\n"
+        "         offsetof(supcg_art_params, a), offsetof(supcg_art_params, gamma),\n"
+        "         offsetof(supcg_art_params, max_trials), sizeof(supcg_art_params));\n"
+        "  printf(\"%zu %zu %zu %zu %zu\\n\", offsetof(supcg_art_report, cycles), offsetof(supcg_art_report, ell),\n"
+        "         offsetof(supcg_art_report, mu), offsetof(supcg_art_report, status), sizeof(supcg_art_report));\n"
+        "  return 0;\n}\n")
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", inc, str(src), "-o", str(exe)], check=True)
+    lines = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split("\n")
+    p = [int(v) for v in lines[0].split()]
+    r = [int(v) for v in lines[1].split()]
+    A, R = S.ArtParams, S.ArtReport
+    assert p == [A.r.offset, A.lam.offset, A.mu.offset, A.cycles.offset, A.K.offset, A.a.offset, A.gamma.offset,
+                 A.max_trials.offset, C.sizeof(A)]
+    assert r == [R.cycles.offset, R.ell.offset, R.mu.offset, R.status.offset, C.sizeof(R)]
