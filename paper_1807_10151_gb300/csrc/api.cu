@@ -131,13 +131,14 @@ struct supcg_geometry_s {
     std::vector<int> vlist;
     int nA, nB;
     int BU, BW, ntu;
+    int nfw = 0;                    // forward warp items (see upload_block_order)
     int nxp, nyp, Up;
     float cx, cy, uc, uc_hi, uc_lo;
     int bwin;
     FFTPlan fx, fy;
     ViewP *dviews = nullptr;
     int *dvlist = nullptr;
-    int *dborder = nullptr;         // forward block order, V x ceil(U / 32) entries
+    int *dborder = nullptr;         // forward warp items in launch order, at most V x ceil(U / 32)
     float *host_db = nullptr, *host_dx = nullptr;   // supcg_solve_host's device copies of b and x (first use)
     double *art_u = nullptr, *art_rn = nullptr;     // ART's per-ray values (first use)
     int art_S = 1;                                  // ART: bin spacing of rays with disjoint pixels
@@ -159,27 +160,34 @@ static int fwd_box_width(const supcg_geometry_s *g)
     return round_up((int)ceil(span + 11.0), 4);
 }
 
-// Forward blocks in launch order, longest first: a block (view, bin tile) lasts
-// about as long as its slowest warp walks, i.e. the rows that the union of that
-// warp's rays can meet (the row ranges of the kernel's fwd_row_range, here in FP64,
-// plus a fixed cost).  Starting the long blocks first lets the grid end on short
-// ones; with the view-major order a view's long central tiles could start last.
-// Entry i is vidx * ntu + tile, vidx indexing the class-A-then-class-B view list.
+// Forward warp items in launch order, longest first.  An item is one warp's rays: the
+// first 64 bins of a (view, bin tile) or the rest of the tile.  It lasts about as long
+// as the rows that the union of its rays can meet (the row ranges of the kernel's
+// fwd_row_range, here in FP64).  Block b runs items 2b and 2b + 1 of the list, so a
+// block pairs items of about the same length (its warps finish together) and the
+// grid starts the long blocks first and ends on short ones; with one block per
+// (view, tile) a block lasted as long as its slower warp and a view's long central
+// tiles could start last.  Entry: (vidx * ntu + tile) * 2 + half, vidx indexing the
+// class-A-then-class-B view list.
 static int upload_block_order(supcg_geometry_s *g)
 {
     const int nv = g->V, ntu = g->ntu;
     const double uc = 0.5 * (g->U - 1) - g->off / g->ds;
-    std::vector<double> cost((size_t)nv * ntu);
+    std::vector<int> ord;
+    std::vector<double> cost;
+    ord.reserve((size_t)nv * ntu * 2);
     for (int vi = 0; vi < nv; ++vi) {
         const ViewP &vp = g->views[g->vlist[vi]];
         const bool classB = vi >= g->nA;
         const int n_outer = classB ? g->nx : g->ny, n_inner = classB ? g->ny : g->nx;
         const double L = -(double)vp.hwq - 1.0, H = (double)n_inner + vp.hwq;
         for (int t = 0; t < ntu; ++t) {
-            double longest = 0.0;
-            for (int w0 = t * g->BU; w0 < std::min(g->U, (t + 1) * g->BU); w0 += 64) {
+            const int u_end = std::min(g->U, (t + 1) * g->BU);
+            for (int half = 0; half < 2; ++half) {
+                const int w0 = t * g->BU + 64 * half;
+                if (w0 >= u_end) continue;
                 int lo = n_outer, hi = -1;
-                for (int u = w0; u < std::min(std::min(g->U, (t + 1) * g->BU), w0 + 64); ++u) {
+                for (int u = w0; u < std::min(u_end, w0 + 64); ++u) {
                     const double base = (double)vp.a_tau * ((double)u - uc) + vp.g0;
                     int l, h;
                     if (fabs((double)vp.b_o) < 1e-20) {
@@ -194,15 +202,18 @@ static int upload_block_order(supcg_geometry_s *g)
                     lo = std::min(lo, l);
                     hi = std::max(hi, h);
                 }
-                longest = std::max(longest, (double)std::max(0, hi - lo + 1));
+                ord.push_back((vi * ntu + t) * 2 + half);
+                cost.push_back((double)std::max(0, hi - lo + 1));
             }
-            cost[(size_t)vi * ntu + t] = longest + 32.0;   // + the block's fixed cost, in rows
         }
     }
-    std::vector<int> ord((size_t)nv * ntu);
-    for (size_t i = 0; i < ord.size(); ++i) ord[i] = (int)i;
-    std::stable_sort(ord.begin(), ord.end(), [&](int x, int y) { return cost[x] > cost[y]; });
-    SUPCG_CUDA_TRY(cudaMemcpy(g->dborder, ord.data(), sizeof(int) * ord.size(), cudaMemcpyHostToDevice));
+    std::vector<int> idx(ord.size());
+    for (size_t i = 0; i < idx.size(); ++i) idx[i] = (int)i;
+    std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) { return cost[x] > cost[y]; });
+    std::vector<int> sorted(ord.size());
+    for (size_t i = 0; i < idx.size(); ++i) sorted[i] = ord[idx[i]];
+    g->nfw = (int)sorted.size();
+    SUPCG_CUDA_TRY(cudaMemcpy(g->dborder, sorted.data(), sizeof(int) * sorted.size(), cudaMemcpyHostToDevice));
     return SUPCG_OK;
 }
 
@@ -460,7 +471,7 @@ static int ws_create(const std::vector<supcg_geometry> &gs, Workspace **out)
     std::vector<long long> npx(w->count);
     for (int c = 0; c < w->count; ++c) {
         const supcg_geometry g = gs[c];
-        nb[KT_FWD][c] = g->V * g->ntu;
+        nb[KT_FWD][c] = (g->nfw + 1) / 2;
         nb[KT_BWD][c] = backward_blocks(g->nx, g->ny, 0);
         nb[KT_BWD2][c] = backward_blocks(g->nx, g->ny, 1);
         nb[KT_VEC][c] = (int)(((long long)g->ny * g->nxp + 1023) / 1024);
@@ -548,7 +559,7 @@ static int ws_create(const std::vector<supcg_geometry> &gs, Workspace **out)
         P.border = g->dborder;
         P.nx = g->nx; P.ny = g->ny; P.V = g->V; P.U = g->U;
         P.nxp = g->nxp; P.nyp = g->nyp; P.Up = g->Up;
-        P.BU = g->BU; P.BW = g->BW; P.ntu = g->ntu; P.nA = g->nA; P.nB = g->nB;
+        P.BU = g->BU; P.BW = g->BW; P.ntu = g->ntu; P.nfw = g->nfw; P.nA = g->nA; P.nB = g->nB;
         P.cx = g->cx; P.cy = g->cy; P.uc = g->uc; P.uc_hi = g->uc_hi; P.uc_lo = g->uc_lo;
         P.bwin = g->bwin;
         w->bwin = std::max(w->bwin, g->bwin);

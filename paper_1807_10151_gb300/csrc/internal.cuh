@@ -192,14 +192,16 @@ struct Prob {
     CUtensorMap tm[4];     // TMA maps: 0 = x, 1 = x^T, 2 = p, 3 = p^T (FP32, padded pitches)
     int nx, ny, V, U;
     int nxp, nyp, Up;      // pitches in elements: image, transposed image, sinogram
-    int BU, BW, ntu;       // forward tiling: bins per block, box width, bin tiles per view
+    int BU, BW, ntu;       // forward tiling: bins per tile, box width, bin tiles per view
+    int nfw;               // forward warp items (a tile's first 64 bins, or the rest)
     int nA, nB;            // number of class-A / class-B views
     float cx, cy, uc;      // uc = (U-1)/2 - off/ds (approximate uses)
     float uc_hi, uc_lo;    // exact split of uc (see ViewP)
     int bwin;              // backprojector: bins staged per view and tile (multiple of 4)
     const ViewP *views;    // [V]
     const int *vlist;      // [nA + nB]: class-A views, then class-B views
-    const int *border;     // [V * ntu]: forward blocks (vidx * ntu + tile), longest first
+    const int *border;     // [nfw]: forward warp items ((vidx * ntu + tile) * 2 + half), longest
+                           // first; block b's warps take entries 2b and 2b + 1
     FFTPlan fx, fy;
     double mu, rho;
     double r2;             // r^2 of the Bayesian criterion (Eq. (2.3)); 0: least squares

@@ -329,23 +329,27 @@ __global__ void __launch_bounds__(kFwdThreads, 10) k_forward(const Prob *__restr
     const Prob &P = probs[pi];
     if (mode != FWD_PLAIN && P.sc->done) return;
 
-    // blocks longest first (the host's order of (view, tile) by the rows their warps walk)
-    const int item = P.border[local];
-    const int vidx = item / P.ntu, tile = item - vidx * P.ntu;
+    // the warp's item (longest first; the block's two are of about the same length): the
+    // first 64 bins of a (view, bin tile) or the rest of the tile
+    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
+    const int wi = 2 * local + warp;
+    const bool idle = wi >= P.nfw;   // the grid's last block may hold one item
+    const int item = idle ? 0 : P.border[wi];
+    const int half = item & 1, tv = item >> 1;
+    const int vidx = tv / P.ntu, tile = tv - vidx * P.ntu;
     const bool classB = vidx >= P.nA;
     const int v = P.vlist[vidx];
     const ViewP vp = P.views[v];
     const bool axis = (vp.flags & kViewAxis) != 0;
     const int n_outer = classB ? P.nx : P.ny, n_inner = classB ? P.ny : P.nx;
     const CUtensorMap *tm = &P.tm[which * 2 + (classB ? 1 : 0)];
-    const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
     const int patch0 = warp * kFwdBufs * kRowsPerChunk * P.BW;   // this warp's boxes in proj_dyn
     uint64_t *wbars = bars + kFwdBufs * warp;
 
     const int u_first = tile * P.BU;
     const int u_last = min(P.U, u_first + P.BU) - 1;
     // the warp's rays: uw0 .. uw0 + 63, lane l takes uw0 + l and uw0 + 32 + l
-    const int uw0 = u_first + 64 * warp, uw1 = min(u_last, uw0 + 63);
+    const int uw0 = u_first + 64 * half, uw1 = min(u_last, uw0 + 63);
     const int uA = uw0 + lane, uB = uw0 + 32 + lane;
     const float tf = bin_pos(min(uw0, u_last), P.uc), tl = bin_pos(uw1, P.uc);
 
@@ -362,8 +366,8 @@ __global__ void __launch_bounds__(kFwdThreads, 10) k_forward(const Prob *__restr
 #define SUPCG_FWD(CB, AX, NC) \
     fwd_ray2<CB, AX, NC>(P, vp, tm, patch0, wbars, rowtab[warp], n_outer, n_inner, uA, uB, u_last, tf, tl, &bad, \
                          &timed_out, acc)
-    if (uw0 > u_last) {
-        // a warp past the block's last bin
+    if (idle) {
+        // no item for this warp
     } else if (classB) {
         if (axis) SUPCG_FWD(true, true, 2); else if (three) SUPCG_FWD(true, false, 3); else SUPCG_FWD(true, false, 2);
     } else {
@@ -381,7 +385,7 @@ __global__ void __launch_bounds__(kFwdThreads, 10) k_forward(const Prob *__restr
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
         const int u = q ? uB : uA;
-        if (u > u_last) continue;
+        if (idle || u > uw1) continue;
         if (mode == FWD_PLAIN) {
             const size_t o = (size_t)v * P.U + u;
             if (P.storage == SUPCG_BF16) reinterpret_cast<__nv_bfloat16 *>(P.out_user)[o] = __double2bfloat16(acc[q]);
