@@ -373,6 +373,40 @@ def run_art(args, dev):
     return 0
 
 
+def memory_bound_legs(G, b, N, peak_gbs):
+    """Steady-state per-iteration time of the HBM-bound kernels of one SupPCG solve
+    on an N x N slice (its working set, images, spectrum and sinograms, exceeds L2):
+    the difference of two profiled solves (4 and 12 iterations) removes the one-off
+    staging and steps 1-9.  Algorithmic bytes per iteration (n = N^2):
+      vector: x update (read x, p; write x) 12n + p update (read p, z, g; write p, p^T) 20n;
+      fft: rows (read g 4n, write the half spectrum, 16 B per stored complex), columns
+           (read and write it, read the quarter table of D, 8 B per entry), inverse rows
+           (read it, write z, read h for z^T h);
+      stv (K = 1): tbar pass (read x, write tbar) 8n, every trial (read x, tbar) 8n,
+           last step (read x, tbar; write x, x^T) 16n."""
+    n = N * N
+    hx = N // 2 + 1
+    spec = 16 * hx * N
+    fft_bytes = (4 * n + spec) + (2 * spec + 8 * (N // 2 + 1) * hx) + (spec + 8 * n)
+    runs = {}
+    for it in (4, 12):
+        _, rep, kinds = G.solve_profiled(b, **solve_kw(it, graph=False))
+        assert rep["status"] == 0 and rep["iters"] == it, rep
+        runs[it] = (rep, kinds)
+    d_it = 8
+    trials = runs[12][0]["ell"] - runs[4][0]["ell"]   # K = 1: l advances once per trial
+    out = {}
+    for kind, launches, nbytes in (("vector", 2, 32 * n), ("fft", 3, fft_bytes),
+                                   ("stv", 1, 24 * n + 8 * n * trials / d_it)):
+        ms = (runs[12][1][kind][0] - runs[4][1][kind][0]) / d_it
+        nl = (runs[12][1][kind][1] - runs[4][1][kind][1]) / d_it
+        gbs = nbytes / (ms / 1000.0) / 1e9
+        out[kind] = {"ms_per_iteration": ms, "launches_per_iteration": nl, "bytes_per_iteration": nbytes,
+                     "achieved_gbs": gbs, "frac_of_hbm": gbs / peak_gbs}
+    out["stv"]["trials_per_iteration"] = trials / d_it
+    return out
+
+
 def run_large(args, dev):
     """8 slices of 2048^2: FP32 vs BF16 storage of the projector pair."""
     import numpy as np
@@ -408,6 +442,18 @@ def run_large(args, dev):
         torch.cuda.synchronize()
         res[storage] = {"project_ms": ev[0].elapsed_time(ev[1]) / args.steps,
                         "backproject_ms": ev[1].elapsed_time(ev[2]) / args.steps}
+        if storage == "f32":
+            # one slice as a SupPCG problem: Poisson data with 1e4 incident photons per ray
+            rng = np.random.default_rng(5200)
+            counts = rng.poisson(1e4 * np.exp(-Y[0].double().cpu().numpy()))
+            b0 = torch.tensor(-np.log(np.maximum(counts, 1) / 1e4), dtype=torch.float32, device=dev)
+            G1 = S.Geometry(N, n_views=V, n_bins=U)
+            peaks, peak_src = measured_peaks()
+            mem_legs = memory_bound_legs(G1, b0, N, peaks["hbm_gbs"])
+            mem_legs["hbm_peak_gbs"] = peaks["hbm_gbs"]
+            mem_legs["peak_source"] = peak_src
+            G1.close()
+            del b0
         G.close()
         del Y, Z, Xs
     # errors on the 256^2 crop geometry against the FP64 oracle
@@ -441,6 +487,7 @@ def run_large(args, dev):
         "config": {"workload": "projector_2048x2048_2880views_2900bins_x8", "slices": B,
                    "l2": "inputs (8 x 16 MB images, 8 x 33 MB sinograms) exceed L2"},
         "timing_ms": res, "crop_errors_vs_fp64_oracle": err,
+        "memory_bound_kernels_2048": mem_legs,
     }
     print(json.dumps(line), flush=True)
     return 0

@@ -140,7 +140,7 @@ __global__ void __launch_bounds__(256) k_pupdate(const Prob *__restrict__ probs,
     const int tiles_j = (P.nx + 31) / 32;
     const int ti = local / tiles_j, tj = local - ti * tiles_j;
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
-    double s = 0.0, spp = 0.0;   // g^T p and ||p||^2
+    df s = df_make(0.0f), spp = df_make(0.0f);   // g^T p and ||p||^2 (exact products, double-float sums)
     // the thread's four rows: every load issued before the first store
     float pv[4], zv[4], gv[4];
     bool in[4];
@@ -160,8 +160,8 @@ __global__ void __launch_bounds__(256) k_pupdate(const Prob *__restrict__ probs,
         if (in[q]) {
             pn = __fmaf_rn(beta, pv[q], -zv[q]);
             P.p[(size_t)(ti * 32 + r) * P.nxp + tj * 32 + tx] = pn;
-            s += (double)gv[q] * (double)pn;
-            spp += (double)pn * (double)pn;
+            df_acc_prod(s, gv[q], pn);
+            df_acc_prod(spp, pn, pn);
         }
         sh[r][tx] = pn;
     }
@@ -170,8 +170,8 @@ __global__ void __launch_bounds__(256) k_pupdate(const Prob *__restrict__ probs,
         const int j = tj * 32 + r, i = ti * 32 + tx;
         if (j < P.nx && i < P.ny) P.pT[(size_t)j * P.nyp + i] = sh[tx][r];
     }
-    const double bs = block_sum<256>(s, red);
-    const double bp = block_sum<256>(spp, red);
+    const double bs = block_sum<256>(df_to_double(s), red);
+    const double bp = block_sum<256>(df_to_double(spp), red);
     const int nblk = prefix[pi + 1] - prefix[pi];
     if (threadIdx.x == 0) {
         P.partial[local] = bs;
@@ -244,11 +244,11 @@ __global__ void __launch_bounds__(kRedThreads) k_beta(const Prob *__restrict__ p
     if (P.sc->done) return;
     const float *z = P.precond ? P.z : P.g;
     const size_t tot = (size_t)P.ny * P.nxp;
-    double s = 0.0;
+    df s = df_make(0.0f);
     for (size_t e = (size_t)local * kVecPerBlock + threadIdx.x; e < tot && e < (size_t)(local + 1) * kVecPerBlock;
          e += kRedThreads)
-        s += (double)z[e] * (double)P.h[e];
-    const double bs = block_sum<kRedThreads>(s, red);
+        df_acc_prod(s, z[e], P.h[e]);
+    const double bs = block_sum<kRedThreads>(df_to_double(s), red);
     if (threadIdx.x == 0) P.partial[local] = bs;
     const int nblk = prefix[pi + 1] - prefix[pi];
     if (last_block(&P.counter[2], nblk, &flag)) {

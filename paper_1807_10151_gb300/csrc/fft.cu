@@ -244,7 +244,7 @@ __global__ void __launch_bounds__(256) k_fft_rows(const Prob *__restrict__ probs
         }
     } else {
         // z, and inside a solve also z^T h for beta = z^T h / p^T h (Algorithm 2 step 3)
-        double s = 0.0;
+        df s = df_make(0.0f);   // z^T h: exact products, double-float sums
         for (int e = threadIdx.x; e < np * nx; e += blockDim.x) {
             const int pr = e / nx, q = e - pr * nx;
             const int ra = 2 * (p0 + pr), rb = ra + 1;
@@ -252,18 +252,18 @@ __global__ void __launch_bounds__(256) k_fft_rows(const Prob *__restrict__ probs
             const float4 v = res[e];
             const float za = __fadd_rn(v.x, v.y);   // the pair rounded to FP32
             P.z[ia] = za;
-            if (!standalone) s += (double)za * (double)P.h[ia];
+            if (!standalone) df_acc_prod(s, za, P.h[ia]);
             if (rb < ny) {
                 const float zb = __fadd_rn(v.z, v.w);
                 P.z[ib] = zb;
-                if (!standalone) s += (double)zb * (double)P.h[ib];
+                if (!standalone) df_acc_prod(s, zb, P.h[ib]);
             }
         }
         if (!standalone) {
             __shared__ double red[40];
             __shared__ int flag;
             const int pi = find_problem(prefix, count, blockIdx.x, &local);
-            const double bs = block_sum<256>(s, red);
+            const double bs = block_sum<256>(df_to_double(s), red);
             if (threadIdx.x == 0) P.partial[local] = bs;
             const int nblk = prefix[pi + 1] - prefix[pi];
             if (last_block(&P.counter[2], nblk, &flag)) {

@@ -286,6 +286,20 @@ __device__ __forceinline__ df df_mul(df a, df b)
     return {h, __fsub_rn(e, __fsub_rn(h, p))};
 }
 
+// Per-thread sums of FP32 terms and products for the FP64 reductions of the
+// streaming kernels: each term (or the exact product of two FP32 values, a
+// TwoProduct pair) is added in double-float arithmetic and the thread's sum is
+// converted to FP64 once, so that the narrow FP64 pipe does a few operations
+// per thread instead of a conversion and an add per element.
+__device__ __forceinline__ df df_prod(float a, float b)
+{
+    const float p = __fmul_rn(a, b);
+    return {p, __fmaf_rn(a, b, -p)};   // p + e = a b exactly
+}
+__device__ __forceinline__ void df_acc(df &s, float v) { s = df_add(s, df{v, 0.0f}); }
+__device__ __forceinline__ void df_acc_prod(df &s, float a, float b) { s = df_add(s, df_prod(a, b)); }
+__device__ __forceinline__ double df_to_double(df a) { return (double)a.h + (double)a.l; }
+
 // ----------------------------------------------------------------- reductions
 __device__ __forceinline__ double warp_sum(double v)
 {

@@ -75,17 +75,17 @@ __global__ void __launch_bounds__(kTvThreads) k_tv_tbar(const Prob *__restrict__
     const Prob &P = probs[pi];
     const int nblk = prefix[pi + 1] - prefix[pi];
     const long long n = (long long)P.ny * P.nx;
-    double s_tv = 0.0, s_nn = 0.0;
+    df s_tv = df_make(0.0f), s_nn = df_make(0.0f);   // double-float sums, FP64 per thread
     for (long long e = (long long)local * kTvThreads + threadIdx.x; e < n; e += (long long)nblk * kTvThreads) {
         const int i = (int)(e / P.nx), j = (int)(e - (long long)i * P.nx);
         float Tb;
         const float tb = tbar_at(P.x, P.nxp, P.ny, P.nx, i, j, &Tb);
         P.tbar[(size_t)i * P.nxp + j] = tb;
-        s_tv += (double)Tb;
-        s_nn += (double)tb * (double)tb;
+        df_acc(s_tv, Tb);
+        df_acc_prod(s_nn, tb, tb);
     }
-    const double btv = block_sum<kTvThreads>(s_tv, red);
-    const double bnn = block_sum<kTvThreads>(s_nn, red);
+    const double btv = block_sum<kTvThreads>(df_to_double(s_tv), red);
+    const double bnn = block_sum<kTvThreads>(df_to_double(s_nn), red);
     if (threadIdx.x == 0) {
         P.partial[local] = btv;
         P.partial[nblk + local] = bnn;
@@ -260,19 +260,20 @@ __global__ void __launch_bounds__(kTvThreads, 3) k_stv(const Prob *__restrict__ 
 
     for (int step = 0; plain && step < K && ok; ++step) {
         // t in the nonascending set at y (Sec. 3.1)
-        double s_tv = 0.0, s_nn = 0.0;
+        df d_tv = df_make(0.0f), d_nn = df_make(0.0f);   // double-float sums, FP64 per thread
         for (int e = e0; e < n; e += stride) {
             const int i = e / nx, j = e - i * nx;
             float Tb;
             const float t = tbar_at(x, ld, ny, nx, i, j, &Tb);
             tb[(size_t)i * ld + j] = t;
-            s_tv += (double)Tb;
-            s_nn += (double)t * (double)t;
+            df_acc(d_tv, Tb);
+            df_acc_prod(d_nn, t, t);
         }
+        double s_tv, s_nn;
         // two sums through one barrier: slots 2*slot and 2*slot+1
         {
-            const double b1 = block_sum<kTvThreads>(s_tv, red);
-            const double b2 = block_sum<kTvThreads>(s_nn, red);
+            const double b1 = block_sum<kTvThreads>(df_to_double(d_tv), red);
+            const double b2 = block_sum<kTvThreads>(df_to_double(d_nn), red);
             if (threadIdx.x == 0) {
                 P.partial[(size_t)(4 + 2 * slot) * nb + local] = b1;
                 P.partial[(size_t)(5 + 2 * slot) * nb + local] = b2;
@@ -302,12 +303,12 @@ __global__ void __launch_bounds__(kTvThreads, 3) k_stv(const Prob *__restrict__ 
             c = sh_c;                                                                     // y~ = y + c tbar
             ++ell;
             ++trials;
-            double s = 0.0;
+            df s = df_make(0.0f);
             for (int e = e0; e < n; e += stride) {
                 const int i = e / nx, j = e - i * nx;
-                if (i + 1 < ny && j + 1 < nx) s += (double)trial_term(x, tb, ld, i, j, c);
+                if (i + 1 < ny && j + 1 < nx) df_acc(s, trial_term(x, tb, ld, i, j, c));
             }
-            tv_t = phase_sum(P, nb, slot, local, s, red, &flag, &ok);
+            tv_t = phase_sum(P, nb, slot, local, df_to_double(s), red, &flag, &ok);
             slot ^= 1;
             if (!ok) break;
             if (tv_t <= tv_y) break;   // until TV(y~) <= TV(y)
