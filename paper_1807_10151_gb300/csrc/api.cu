@@ -478,8 +478,8 @@ static int ws_create(const std::vector<supcg_geometry> &gs, Workspace **out)
         nb[KT_TR][c] = ((g->ny + 31) / 32) * ((g->nx + 31) / 32);
         // FFT: enough blocks to fill the device, each a few row pairs / stored columns
         const int npairs = (g->ny + 1) / 2, hx = g->nx / 2 + 1;
-        const int rpb = std::max(1, std::min(std::min(8, 4096 / g->nx), npairs / 256));
-        const int cw = std::max(1, std::min(std::min(8, 4096 / g->ny), hx / 256));
+        const int rpb = std::max(1, std::min(std::min(8, 2048 / g->nx), npairs / 256));
+        const int cw = std::max(1, std::min(std::min(8, 2048 / g->ny), hx / 256));
         nb[KT_ROWS][c] = (npairs + rpb - 1) / rpb;
         nb[KT_COLS][c] = (hx + cw - 1) / cw;
         // (two transform buffers, then the twiddles when at most 2048 of them)
