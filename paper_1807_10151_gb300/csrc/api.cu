@@ -163,7 +163,7 @@ static int fwd_box_width(const supcg_geometry_s *g)
 // Forward warp items in launch order, longest first.  An item is one warp's rays: the
 // first 64 bins of a (view, bin tile) or the rest of the tile.  It lasts about as long
 // as the rows that the union of its rays can meet (the row ranges of the kernel's
-// fwd_row_range, here in FP64).  Block b runs items 2b and 2b + 1 of the list, so a
+// fwd_row_range, here in FP64), weighted by the cost of a row in its view.  Block b runs items 2b and 2b + 1 of the list, so a
 // block pairs items of about the same length (its warps finish together) and the
 // grid starts the long blocks first and ends on short ones; with one block per
 // (view, tile) a block lasted as long as its slower warp and a view's long central
@@ -202,8 +202,12 @@ static int upload_block_order(supcg_geometry_s *g)
                     lo = std::min(lo, l);
                     hi = std::max(hi, h);
                 }
+                // per row: the packed path with two candidates; three candidates near the
+                // diagonal cost half as much again, and axis-aligned views take the scalar path
+                // (the warp's two rays one after the other)
+                const double per_row = (vp.flags & kViewAxis) ? 2.0 : ((vp.flags & kViewFwd3) ? 1.5 : 1.0);
                 ord.push_back((vi * ntu + t) * 2 + half);
-                cost.push_back((double)std::max(0, hi - lo + 1));
+                cost.push_back(16.0 + per_row * (double)std::max(0, hi - lo + 1));
             }
         }
     }
