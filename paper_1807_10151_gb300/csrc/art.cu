@@ -149,9 +149,15 @@ __global__ void __launch_bounds__(kArtRayThreads) k_art(const Prob *__restrict__
                         rni = P.art_rn[i];
                     }
                     float ks = 0.0f, kc = 0.0f;   // Kahan pair of the thread's terms of <R_i, x>
+                    // a ray of at most kArtRows x kArtRayThreads rows: each thread's rows, weights and
+                    // pixel values are gathered once and kept for the update (the class's other rays
+                    // touch none of these pixels, so the values are still current then)
+                    const bool one_group = R.hi - R.lo < kArtRows * kArtRayThreads;
+                    int gpix[3 * kArtRows];
+                    float gw[3 * kArtRows], gx[3 * kArtRows];
                     for (int o0 = R.lo + t; o0 <= R.hi; o0 += kArtRows * kArtRayThreads) {
-                        int pix[3 * kArtRows];
-                        float w[3 * kArtRows], xv[3 * kArtRows];
+                        int *pix = gpix;
+                        float *w = gw, *xv = gx;
 #pragma unroll
                         for (int q = 0; q < kArtRows; ++q) {
                             const int o = o0 + q * kArtRayThreads;
@@ -180,6 +186,13 @@ __global__ void __launch_bounds__(kArtRayThreads) k_art(const Prob *__restrict__
                     }
                     __syncthreads();
                     const float rcf = sh_rc;
+                    if (one_group) {
+                        if (t <= R.hi - R.lo) {   // (threads past the ray's rows gathered nothing)
+#pragma unroll
+                            for (int k = 0; k < 3 * kArtRows; ++k)
+                                if (gw[k] != 0.0f) x[gpix[k]] = __fmaf_rn(rcf, gw[k], gx[k]);
+                        }
+                    } else
                     for (int o0 = R.lo + t; o0 <= R.hi; o0 += kArtRows * kArtRayThreads) {
                         int pix[3 * kArtRows];
                         float w[3 * kArtRows], xv[3 * kArtRows];
