@@ -1,10 +1,12 @@
 // Forward projection R x and its exact transpose R^T y (Sec. 2: R x = b + e;
 // Eq. (2.2): normal equations R^T R x = R^T b).
 //
-// Forward (ray-driven, gather over pixels).  A block owns one view and up to
-// 128 consecutive bins, two rays per thread; blocks run longest first (an order
-// the host computes from the rows each block's warps walk), so the grid ends on
-// short blocks.  Views are split in two classes:
+// Forward (ray-driven, gather over pixels).  A warp owns one view and up to 64
+// consecutive bins (a warp item), two rays per lane.  The host sorts the warp
+// items longest first by the rows their rays can meet, weighted by the cost of
+// a row in the item's view, and block b runs items 2b and 2b + 1: a block's
+// warps finish together and the grid ends on short items.  Views are split in
+// two classes:
 // class A (|cos| >= |sin|) walks image rows, class B walks image columns, and
 // class B reads the transposed image x^T so that both classes walk contiguous
 // rows of the array they read.  Each warp stages chunks of kRowsPerChunk rows
@@ -19,7 +21,7 @@
 // onto are staged in shared memory with 16-byte vector loads; every pixel
 // gathers the two (three) bins nearest to its projected centre with the same
 // weight evaluated on the same FP32 operands as the forward kernel.  The last
-// block of a tile to finish adds the parts' FP64 sums in part order.
+// block of a tile to finish adds the parts' double-float sums in part order.
 #include "internal.cuh"
 
 namespace supcg {
