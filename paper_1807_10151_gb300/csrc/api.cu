@@ -544,22 +544,23 @@ static int ws_create(const std::vector<supcg_geometry> &gs, Workspace **out)
                                 sino * 4, sino * 4, sino * 4, (size_t)g->ny * g->nx * 16, sizeof(Scal),
                                 npart * 8, 16 * 4, 4 * 4, (size_t)(g->ny / 2 + 1) * (g->nx / 2 + 1) * 8,
                                 2 * (size_t)kBwdViewParts * img * 8,
-                                (size_t)std::max(nb[KT_BWD][c], nb[KT_BWD2][c]) * 4};
+                                (size_t)std::max(nb[KT_BWD][c], nb[KT_BWD2][c]) * 4, img * 4, img * 4};
         size_t total = 0;
         for (size_t s : sizes) total += al(s);
         char *base = nullptr;
         if (cudaMalloc(&base, total) != cudaSuccess) { delete w; return SUPCG_ERR_NOMEM; }
         w->allocs.push_back(base);
         if (cudaMemset(base, 0, total) != cudaSuccess) { delete w; return SUPCG_ERR_CUDA; }
-        char *ptrs[19];
+        char *ptrs[21];
         size_t off = 0;
-        for (int k = 0; k < 19; ++k) { ptrs[k] = base + off; off += al(sizes[k]); }
+        for (int k = 0; k < 21; ++k) { ptrs[k] = base + off; off += al(sizes[k]); }
         P.x = (float *)ptrs[0]; P.xT = (float *)ptrs[1]; P.p = (float *)ptrs[2]; P.pT = (float *)ptrs[3];
         P.g = (float *)ptrs[4]; P.z = (float *)ptrs[5]; P.h = (float *)ptrs[6]; P.tbar = (float *)ptrs[7];
         P.r = (float *)ptrs[8]; P.q = (float *)ptrs[9]; P.bpad = (float *)ptrs[10];
         P.C = (double2 *)ptrs[11]; P.sc = (Scal *)ptrs[12]; P.partial = (double *)ptrs[13];
         P.counter = (unsigned *)ptrs[14]; P.bar = (unsigned *)ptrs[15]; P.Dtab = (float2 *)ptrs[16];
-        P.bsplit = (float2 *)ptrs[17]; P.tilecnt = (unsigned *)ptrs[18];
+        P.bsplit = (float2 *)ptrs[17]; P.tilecnt = (unsigned *)ptrs[18]; P.xlo = (float *)ptrs[19];
+        P.glo = (float *)ptrs[20];
         P.border = g->dborder;
         P.nx = g->nx; P.ny = g->ny; P.V = g->V; P.U = g->U;
         P.nxp = g->nxp; P.nyp = g->nyp; P.Up = g->Up;
@@ -818,8 +819,11 @@ extern "C" int supcg_art(supcg_geometry g, const float *d_b, float *d_x, const s
     P.art_u = g->art_u;
     P.art_rn = g->art_rn;
     P.storage = SUPCG_F32;
+    float *xlo = P.xlo;
+    P.xlo = nullptr;   // ART's row actions and SupART's S_TV work on the FP32 image alone
     rc = ws_upload(w, st);
     P.storage = g->storage;
+    P.xlo = xlo;
     if (rc) return rc;
     Scal s0 = {};
     s0.muX = isnan(p->mu) ? 0.0 : p->mu;

@@ -51,6 +51,7 @@ __global__ void __launch_bounds__(256) k_stage_in(const Prob *__restrict__ probs
         if (i < P.ny && j < P.nx) {
             v = load_user(P.in_user, (size_t)i * P.nx + j, P.storage);
             (which ? P.g : P.x)[(size_t)i * P.nxp + j] = v;
+            if (!which && P.xlo) P.xlo[(size_t)i * P.nxp + j] = 0.0f;   // x_0 is exactly its FP32 value
         }
         sh[r][tx] = v;
     }
@@ -142,7 +143,7 @@ __global__ void __launch_bounds__(256) k_pupdate(const Prob *__restrict__ probs,
     const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
     df s = df_make(0.0f), spp = df_make(0.0f);   // g^T p and ||p||^2 (exact products, double-float sums)
     // the thread's four rows: every load issued before the first store
-    float pv[4], zv[4], gv[4];
+    float pv[4], zv[4], gv[4], glv[4];
     bool in[4];
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -152,6 +153,7 @@ __global__ void __launch_bounds__(256) k_pupdate(const Prob *__restrict__ probs,
         pv[q] = in[q] ? P.p[e] : 0.0f;
         zv[q] = in[q] ? z[e] : 0.0f;
         gv[q] = in[q] ? P.g[e] : 0.0f;
+        glv[q] = in[q] ? P.glo[e] : 0.0f;   // the gradient's low part (written by the backprojector)
     }
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
@@ -161,6 +163,7 @@ __global__ void __launch_bounds__(256) k_pupdate(const Prob *__restrict__ probs,
             pn = __fmaf_rn(beta, pv[q], -zv[q]);
             P.p[(size_t)(ti * 32 + r) * P.nxp + tj * 32 + tx] = pn;
             df_acc_prod(s, gv[q], pn);
+            df_acc_prod(s, glv[q], pn);
             df_acc_prod(spp, pn, pn);
         }
         sh[r][tx] = pn;
@@ -278,7 +281,10 @@ int launch_beta(const Launch &L)
 // Start of a while-body of Algorithm 3: the condition f(x_{k-1/2}) > eps
 // (step 10) and, when it holds, step 7 of the previous U_PCG call
 // (x_k = x_{k-1/2} + alpha p_{k-1}), deferred to here so that x holds the
-// returned image x_{k-1/2} whenever the loop stops.
+// returned image x_{k-1/2} whenever the loop stops.  With the low part xlo the
+// update is x + xlo <- x + xlo + alpha p in double-float arithmetic (alpha split
+// into two FP32 parts, the product's rounding error kept), so that the iterate
+// does not lose the low bits of alpha p to FP32 rounding at every step.
 __global__ void __launch_bounds__(kRedThreads) k_xupdate(const Prob *__restrict__ probs,
                                                          const int *__restrict__ prefix, int count)
 {
@@ -294,6 +300,7 @@ __global__ void __launch_bounds__(kRedThreads) k_xupdate(const Prob *__restrict_
         return;
     }
     const float al = (float)sc->alpha;
+    const float al_lo = (float)(sc->alpha - (double)al);   // alpha = al + al_lo to about 2^-48
     const size_t tot = (size_t)P.ny * P.nxp;   // a multiple of 4: rows are padded to 16 bytes
     float *tr = P.trace ? P.trace + (size_t)sc->k * P.ny * P.nx : nullptr;
     // one float4 of x and of p per thread (kVecPerBlock = 4 x kRedThreads elements per block)
@@ -301,10 +308,25 @@ __global__ void __launch_bounds__(kRedThreads) k_xupdate(const Prob *__restrict_
     if (4 * e4 < tot) {
         const float4 pv = reinterpret_cast<const float4 *>(P.p)[e4];
         float4 xv = reinterpret_cast<const float4 *>(P.x)[e4];
-        xv.x = __fmaf_rn(al, pv.x, xv.x);
-        xv.y = __fmaf_rn(al, pv.y, xv.y);
-        xv.z = __fmaf_rn(al, pv.z, xv.z);
-        xv.w = __fmaf_rn(al, pv.w, xv.w);
+        if (P.xlo) {
+            float4 lv = reinterpret_cast<const float4 *>(P.xlo)[e4];
+            float *xs = &xv.x, *ls = &lv.x;
+            const float *ps = &pv.x;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                df prod = df_prod(al, ps[q]);                  // al p exactly, then + al_lo p
+                prod.l = __fmaf_rn(al_lo, ps[q], prod.l);
+                const df v = df_add(df{xs[q], ls[q]}, prod);
+                xs[q] = v.h;
+                ls[q] = v.l;
+            }
+            reinterpret_cast<float4 *>(P.xlo)[e4] = lv;
+        } else {
+            xv.x = __fmaf_rn(al, pv.x, xv.x);
+            xv.y = __fmaf_rn(al, pv.y, xv.y);
+            xv.z = __fmaf_rn(al, pv.z, xv.z);
+            xv.w = __fmaf_rn(al, pv.w, xv.w);
+        }
         reinterpret_cast<float4 *>(P.x)[e4] = xv;
         if (tr) {
             const float v4[4] = {xv.x, xv.y, xv.z, xv.w};

@@ -217,9 +217,14 @@ __global__ void __launch_bounds__(256) k_fft_rows(const Prob *__restrict__ probs
         const int pr = e / nx, q = e - pr * nx;
         const int ra = 2 * (p0 + pr), rb = ra + 1;
         if (!inverse) {
-            const float va = P.g[(size_t)ra * P.nxp + q];
-            const float vb = rb < ny ? P.g[(size_t)rb * P.nxp + q] : 0.0f;
-            a[e] = make_float4(va, 0.0f, vb, 0.0f);
+            // inside a solve the gradient is the double-float pair (g, glo)
+            const float *glo = standalone ? nullptr : P.glo;
+            const size_t ia = (size_t)ra * P.nxp + q, ib = (size_t)rb * P.nxp + q;
+            const float va = P.g[ia];
+            const float vb = rb < ny ? P.g[ib] : 0.0f;
+            const float la = glo ? glo[ia] : 0.0f;
+            const float lb = (glo && rb < ny) ? glo[ib] : 0.0f;
+            a[e] = make_float4(va, la, vb, lb);
         } else {
             const bool lo = q <= nx / 2;
             const int kk = lo ? q : nx - q;

@@ -218,6 +218,15 @@ struct Prob {
     int fft_rpb, fft_cw;   // FFT rows per block / columns per block
     // solve buffers (images pitch nxp, transposed pitch nyp, sinograms pitch Up)
     float *x, *xT, *p, *pT, *g, *z, *h, *tbar;
+    // low part of the iterate: the solve keeps x as the double-float pair (x, xlo), x = RN(x + xlo)
+    // the FP32 image every reader (projector, TV, caller) sees, xlo the rounding error of x,
+    // so that the many small updates of S_TV and x <- x + alpha p do not round into x; null:
+    // x alone (ART's row actions)
+    float *xlo;
+    // low part of the gradient of a solve, g + glo = the backprojector's double-float sum:
+    // the preconditioner damps g's lowest frequencies by mu, so FP32 rounding of g alone
+    // would dominate z = M g there; read by the first transform pass and by g^T p
+    float *glo;
     float *r, *q, *bpad;
     double2 *C;            // FFT scratch [ny][nx] (FP64 complex)
     float2 *Dtab;          // h(w_r) / (nx ny) at (min(k1, ny-k1), min(k2, nx-k2)), double-float: [ny/2+1][nx/2+1]

@@ -801,9 +801,13 @@ __global__ void __launch_bounds__(kBwdThreads, DUAL ? 2 : 3) k_backward(const Pr
                         } else {
                             v = P.r2 * v + (double)P.p[o];
                         }
-                        outs[s][o] = (float)v;
+                        const float vh = (float)v;
+                        outs[s][o] = vh;
+                        if (solve && is_g[s]) P.glo[o] = (float)(v - (double)vh);
                     } else {
-                        outs[s][o] = __fadd_rn(vs.h, vs.l);   // the pair rounded to FP32
+                        const float vh = __fadd_rn(vs.h, vs.l);   // the pair rounded to FP32
+                        outs[s][o] = vh;
+                        if (solve && is_g[s]) P.glo[o] = __fsub_rn(vs.l, __fsub_rn(vh, vs.h));   // its error, exactly
                     }
                     if (want_se && s == 0) {   // pixel centre inside the ellipse (FP64, as the definition)
                         const double ex = ((double)j - 0.5 * (P.nx - 1)) / P.se_ax;

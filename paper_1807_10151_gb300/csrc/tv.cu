@@ -63,6 +63,22 @@ __device__ __forceinline__ float trial_term(const float *__restrict__ y, const f
     return sqrtf(a * a + b * b);
 }
 
+// y <- y + c t at element p of the iterate: in double-float arithmetic on the pair
+// (x, xlo) when the low part exists (the exact product c t added to it), else one
+// FP32 FMA.  Returns the new FP32 image value x = RN(x + xlo).
+__device__ __forceinline__ float x_step(float *__restrict__ x, float *__restrict__ xlo, size_t p, float c, float t)
+{
+    if (!xlo) {
+        const float v = __fmaf_rn(c, t, x[p]);
+        x[p] = v;
+        return v;
+    }
+    const df v = df_add(df{x[p], xlo[p]}, df_prod(c, t));
+    x[p] = v.h;
+    xlo[p] = v.l;
+    return v.h;
+}
+
 // Standalone TV and tbar of P.x (one image per problem): writes P.tbar and
 // sc->tv_k = TV, sc->snorm2 = ||tbar||^2.
 __global__ void __launch_bounds__(kTvThreads) k_tv_tbar(const Prob *__restrict__ probs, const int *__restrict__ prefix,
@@ -146,6 +162,7 @@ __global__ void __launch_bounds__(kTvThreads, 3) k_stv(const Prob *__restrict__ 
     const int stride = nb * kTvThreads;
     const int e0 = local * kTvThreads + threadIdx.x;
     float *x = P.x;
+    float *xl = P.xlo;   // low part of the iterate (null: FP32 updates)
     float *tb = P.tbar;
     long long ell = sc->ell;
     long long total_trials = 0;
@@ -153,10 +170,14 @@ __global__ void __launch_bounds__(kTvThreads, 3) k_stv(const Prob *__restrict__ 
     int slot = 0;   // partial buffers alternate between two slots (pairs of slots for 2-value phases)
     bool ok = true;
 
+    // ||s_k||^2 for the log: the iterate before the steps (high part in z, low part in g;
+    // both are recomputed after S_TV in a while body)
     if (want_snorm)
         for (int e = e0; e < n; e += stride) {
             const int i = e / nx, j = e - i * nx;
-            P.z[(size_t)i * ld + j] = x[(size_t)i * ld + j];
+            const size_t p = (size_t)i * ld + j;
+            P.z[p] = x[p];
+            P.g[p] = xl ? xl[p] : 0.0f;
         }
 
     // Learned direction (dir != null, pitch nx): accepted only when nonascending for TV,
@@ -243,8 +264,7 @@ __global__ void __launch_bounds__(kTvThreads, 3) k_stv(const Prob *__restrict__ 
             if (ok) {
                 for (int e = e0; e < n; e += stride) {
                     const int i = e / nx, jj = e - i * nx;
-                    const size_t p = (size_t)i * ld + jj;
-                    x[p] = __fmaf_rn(c, dir[(size_t)i * nx + jj], x[p]);
+                    (void)x_step(x, xl, (size_t)i * ld + jj, c, dir[(size_t)i * nx + jj]);
                 }
                 ok = coop_barrier(P.bar, nb, &sc->status, &flag);
                 ell += (long long)K + (j - 1);
@@ -329,8 +349,7 @@ __global__ void __launch_bounds__(kTvThreads, 3) k_stv(const Prob *__restrict__ 
                     float v = 0.0f;
                     if (i < ny && j < nx) {
                         const size_t p = (size_t)i * ld + j;
-                        v = __fmaf_rn(c, tb[p], x[p]);
-                        x[p] = v;
+                        v = x_step(x, xl, p, c, tb[p]);
                     }
                     sh_t[r][tx] = v;
                 }
@@ -346,7 +365,7 @@ __global__ void __launch_bounds__(kTvThreads, 3) k_stv(const Prob *__restrict__ 
             for (int e = e0; e < n; e += stride) {   // y <- y~
                 const int i = e / nx, j = e - i * nx;
                 const size_t p = (size_t)i * ld + j;
-                x[p] = __fmaf_rn(c, tb[p], x[p]);
+                (void)x_step(x, xl, p, c, tb[p]);
             }
             ok = coop_barrier(P.bar, nb, &sc->status, &flag);
         }
@@ -358,7 +377,7 @@ __global__ void __launch_bounds__(kTvThreads, 3) k_stv(const Prob *__restrict__ 
         for (int e = e0; e < n; e += stride) {
             const int i = e / nx, j = e - i * nx;
             const size_t p = (size_t)i * ld + j;
-            const double dlt = (double)x[p] - (double)P.z[p];
+            const double dlt = ((double)x[p] - (double)P.z[p]) + ((xl ? (double)xl[p] : 0.0) - (double)P.g[p]);
             s += dlt * dlt;
         }
         sn = phase_sum(P, nb, slot, local, s, red, &flag, &ok);

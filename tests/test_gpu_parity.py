@@ -209,10 +209,9 @@ def test_superiorize_backtrack_cap():
 @pytest.mark.parametrize("seed", [1001, 1002, 1003, 1004, 1005])
 def test_solve_config1_50_iterations_match_oracle(seed):
     """64 x 64, 90 views, 95 bins, 10 ellipses, 1 % noise, K=1, gamma=0.5, a=0.995:
-    50 SupPCG iterations.  The l sequence must be identical and the iterate
-    within 1e-4 (rel. L2) of the oracle's -- or, where the FP32 trajectory is
-    itself less reproducible than that, within 4x its own sensitivity to a
-    one-ulp change of b (measured here on the GPU)."""
+    50 SupPCG iterations (Algorithm 3).  The l sequence must be identical, the
+    returned iterate within 1e-4 (rel. L2) of the oracle's, and the logged f and
+    TV of every iterate, and the reported f, within 1e-4."""
     og, R, x_true, b = config1_problem(seed=seed)
     G = gpu_geometry(og)
     b32 = f32(b)
@@ -228,13 +227,9 @@ def test_solve_config1_50_iterations_match_oracle(seed):
         errs.append(rel_l2(x.double().cpu().numpy(), ref["x_half"]))
         assert rel_l2(lg[:, 2], ref["tv_half"]) <= 1e-4
         assert rel_l2(lg[:, 0], ref["f"]) <= 1e-4
+        assert rep["f_last"] == pytest.approx(ref["f"][-1], rel=1e-4)
     assert errs[0] == errs[1]   # graph replay and direct launches are bitwise identical
-    err = errs[0]
-    if err > 1e-4:
-        bp = f32(b32 * (1 + 6e-8 * np.random.default_rng(seed).standard_normal(b32.shape)))
-        xp, _, _ = G.solve(to_dev(bp), **kw)
-        self_sens = rel_l2(xp.double().cpu().numpy(), x.double().cpu().numpy())
-        assert err <= 4 * self_sens, (err, self_sens)
+    assert errs[0] <= 1e-4, errs[0]
 
 
 @pytest.mark.parametrize("perturb,precond", [(False, True), (False, False), (True, False)])
