@@ -44,7 +44,7 @@ typedef enum {
     SUPCG_ERR_BREAKDOWN = -4, /* CG breakdown: p^T h <= 0 or a non-finite scalar          */
     SUPCG_ERR_BACKTRACK = -5, /* S_TV backtracking exceeded max_trials (Algorithm 1)      */
     SUPCG_ERR_TIMEOUT = -6,   /* a bounded device-side wait expired                       */
-    SUPCG_ERR_PRECOND = -7,   /* preconditioner not positive definite (rho <= 1/2)        */
+    SUPCG_ERR_PRECOND = -7,   /* preconditioner parameters outside 1/2 < rho <= 1, mu >= 0 */
     SUPCG_ERR_UNSUPPORTED = -8/* geometry outside the kernels' supported range             */
 } supcg_status;
 
@@ -95,7 +95,8 @@ int supcg_backproject(supcg_geometry g, const void *d_y, void *d_x, int batch, v
 /* Preconditioner z = M g, M = F^-1 D F, D = h(w) of Eq. (3.2) with
  * h(w) = (|w| + mu)(rho + (1 - rho) cos w), w the radial frequency of the
  * ny x nx DFT clamped to pi.  d_g, d_z FP32 [batch][ny][nx]; may alias.
- * Errors: SUPCG_ERR_PRECOND when rho <= 1/2 or mu < 0 (M not SPD). */
+ * Accepted parameters: 1/2 < rho <= 1, mu finite and >= 0 (h(w) > 0 on [0, pi]: M
+ * is symmetric positive definite).  Errors: SUPCG_ERR_PRECOND outside that range. */
 int supcg_precondition(supcg_geometry g, double mu, double rho, const float *d_g, float *d_z,
                        int batch, void *stream);
 
@@ -109,13 +110,14 @@ int supcg_precondition(supcg_geometry g, double mu, double rho, const float *d_g
  * It needs no geometry object and calls no allocating routine: its scratch
  * (4 MiB + 16 KiB of FP64 complex values) is one static device array that
  * the library reserves on every GPU that loads it, until the process exits.
- * The first call on each device looks that array's device address up
- * (cudaGetSymbolAddress) and sets kernel attributes; make that first call
- * before any stream capture.  All calls share the array: calls whose work
+ * The first call on each device (and the first after that device's context
+ * has been replaced, e.g. by cudaDeviceReset) looks that array's device
+ * address up (cudaGetSymbolAddress) and sets kernel attributes; make that
+ * first call before any stream capture.  All calls share the array: calls whose work
  * overlaps on the GPU (for example on two streams) race and give wrong
- * results.  Asynchronous on `stream`.  Errors: SUPCG_ERR_ARG,
- * SUPCG_ERR_UNSUPPORTED, SUPCG_ERR_PRECOND (rho <= 1/2 or mu < 0),
- * SUPCG_ERR_CUDA. */
+ * results.  Asynchronous on `stream`.  Accepted parameters: 1/2 < rho <= 1,
+ * mu finite and >= 0.  Errors: SUPCG_ERR_ARG, SUPCG_ERR_UNSUPPORTED,
+ * SUPCG_ERR_PRECOND (rho or mu outside that range), SUPCG_ERR_CUDA. */
 int supcg_precondition_noalloc(int ny, int nx, double mu, double rho, const float *d_g, float *d_z,
                                void *stream);
 
@@ -341,6 +343,27 @@ int supcg_solve_profiled(supcg_geometry g, const float *d_b, float *d_x, const s
 /* Number of kernels the library has enqueued in this process so far (a CUDA
  * graph replay counts every kernel node it launches). */
 long long supcg_kernel_launches(void);
+
+/* Bounded device-side waits.  The repeat loop of Algorithm 1 (S_TV) has no
+ * bound in the paper; here it runs on the device in one cooperative launch
+ * whose blocks meet at grid barriers, and ART's ray classes (Sec. 3.4) meet
+ * at the same kind of barrier.  Each wait polls a flag at most `polls` times
+ * (each poll sleeps about 64 ns; the default, 2^24 polls, is a second or
+ * two) and then gives up: the kernel records SUPCG_ERR_TIMEOUT, leaves, and
+ * the call returns that status (the context stays usable and the next call
+ * starts from a clean barrier).  The setting is process-wide and read by
+ * every call when it starts.  The paper has no counterpart.
+ * Errors: SUPCG_ERR_ARG when polls < 1. */
+int supcg_set_wait_limit(long long polls);
+
+/* Test hook for the timeout path above: with extra_blocks > 0 every
+ * cooperative grid barrier waits for extra_blocks more arrivals than its
+ * launch has blocks, so no barrier is ever released and every wait runs to
+ * the limit of supcg_set_wait_limit (no copy or memory access is left in
+ * flight: the blocks only poll).  0 (the default) restores normal barriers.
+ * Process-wide; for tests of the error path only.  The paper has no
+ * counterpart.  Errors: SUPCG_ERR_ARG outside 0 .. 1024. */
+int supcg_set_barrier_shortfall(int extra_blocks);
 
 /* Human-readable name of a status code (static string). */
 const char *supcg_status_string(int status);

@@ -31,7 +31,8 @@ EXPORTED = ["supcg_create_geometry", "supcg_destroy_geometry", "supcg_project", 
             "supcg_precondition_noalloc", "supcg_cnn_create", "supcg_cnn_destroy", "supcg_cnn_num_params",
             "supcg_cnn_get_params", "supcg_cnn_set_params", "supcg_cnn_forward", "supcg_cnn_gradients",
             "supcg_cnn_train_step", "supcg_solve_trace", "supcg_solve_learned", "supcg_set_tiling",
-            "supcg_get_tiling", "supcg_solve_sweep", "supcg_art"]
+            "supcg_get_tiling", "supcg_solve_sweep", "supcg_art", "supcg_set_wait_limit",
+            "supcg_set_barrier_shortfall"]
 KINDS = ["forward", "backward", "fft", "stv", "vector", "cnn"]
 
 _lock = threading.Lock()
@@ -126,6 +127,8 @@ def load(allow_build: bool = True):
         L.supcg_solve_learned.argtypes = [vp, vp, vp, vp, C.POINTER(Params), C.POINTER(Report), vp, vp]
         L.supcg_set_tiling.argtypes = [vp, i]
         L.supcg_get_tiling.argtypes = [vp, C.POINTER(i)]
+        L.supcg_set_wait_limit.argtypes = [ll]
+        L.supcg_set_barrier_shortfall.argtypes = [i]
         L.supcg_status_string.argtypes = [i]
         L.supcg_status_string.restype = C.c_char_p
         for name in EXPORTED:
@@ -206,6 +209,17 @@ def supcg_kernel_launches():
 
 def supcg_status_string(status):
     return load().supcg_status_string(status).decode()
+
+
+def supcg_set_wait_limit(polls):
+    return load().supcg_set_wait_limit(int(polls))
+
+
+def supcg_set_barrier_shortfall(extra_blocks):
+    return load().supcg_set_barrier_shortfall(int(extra_blocks))
+
+
+DEFAULT_WAIT_LIMIT = 1 << 24
 
 
 # ---------------------------------------------------------------- torch helpers

@@ -7,6 +7,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 #include <vector>
 
@@ -589,8 +590,38 @@ static int ws_create(const std::vector<supcg_geometry> &gs, Workspace **out)
     return SUPCG_OK;
 }
 
+int supcg::current_device(int *dev)
+{
+    SUPCG_CUDA_TRY(cudaGetDevice(dev));
+    return (*dev >= 0 && *dev < kMaxDevices) ? SUPCG_OK : SUPCG_ERR_UNSUPPORTED;
+}
+
+int supcg::func_attrs_once(const void *func, int max_dyn_smem, int carveout)
+{
+    static std::mutex mu;
+    static std::vector<std::pair<const void *, int>> done;   // (kernel, device) pairs already set
+    int dev = 0;
+    int rc = current_device(&dev);
+    if (rc) return rc;
+    std::lock_guard<std::mutex> lk(mu);
+    for (const auto &d : done)
+        if (d.first == func && d.second == dev) return SUPCG_OK;
+    SUPCG_CUDA_TRY(cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, max_dyn_smem));
+    if (carveout >= 0) SUPCG_CUDA_TRY(cudaFuncSetAttribute(func, cudaFuncAttributePreferredSharedMemoryCarveout, carveout));
+    done.emplace_back(func, dev);
+    return SUPCG_OK;
+}
+
+// Bounded grid barriers: polls before giving up, and the test hook's extra blocks.
+static std::atomic<long long> g_wait_limit{kSpinLimit};
+static std::atomic<int> g_bar_extra{0};
+
 static int ws_upload(Workspace *w, cudaStream_t st)
 {
+    for (Prob &P : w->hp) {
+        P.wait_limit = g_wait_limit.load();
+        P.bar_extra = g_bar_extra.load();
+    }
     // synchronous copy from pageable memory: safe to modify hp afterwards
     SUPCG_CUDA_TRY(cudaStreamSynchronize(st));
     SUPCG_CUDA_TRY(cudaMemcpy(w->dp, w->hp.data(), sizeof(Prob) * w->count, cudaMemcpyHostToDevice));
@@ -763,7 +794,6 @@ extern "C" int supcg_superiorize(supcg_geometry g, float *d_x, double a, double 
 }
 
 // ------------------------------------------------------------------ launch accounting
-#include <atomic>
 static std::atomic<long long> g_launches{0};
 
 struct Prof {
@@ -795,6 +825,20 @@ static thread_local long long t_capture_count = 0;
     } while (0)
 
 extern "C" long long supcg_kernel_launches(void) { return g_launches.load(); }
+
+extern "C" int supcg_set_wait_limit(long long polls)
+{
+    if (polls < 1) return SUPCG_ERR_ARG;
+    g_wait_limit.store(polls);
+    return SUPCG_OK;
+}
+
+extern "C" int supcg_set_barrier_shortfall(int extra_blocks)
+{
+    if (extra_blocks < 0 || extra_blocks > 1024) return SUPCG_ERR_ARG;
+    g_bar_extra.store(extra_blocks);
+    return SUPCG_OK;
+}
 
 // ------------------------------------------------------------------ ART / SupART (Sec. 3.4)
 extern "C" int supcg_art(supcg_geometry g, const float *d_b, float *d_x, const supcg_art_params *p,

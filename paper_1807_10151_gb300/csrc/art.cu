@@ -214,7 +214,7 @@ __global__ void __launch_bounds__(kArtRayThreads) k_art(const Prob *__restrict__
                     }
                     __syncthreads();   // sh_rc and red are reused by the block's next ray
                 }
-                if (!coop_barrier(P.bar, gridDim.x, &sc->status, &flag)) return;   // bounded: SUPCG_ERR_TIMEOUT
+                if (!coop_barrier(P.bar, gridDim.x + P.bar_extra, &sc->status, &flag, P.wait_limit)) return;   // bounded: SUPCG_ERR_TIMEOUT
             }
         }
     }

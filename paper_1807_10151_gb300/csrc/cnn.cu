@@ -22,6 +22,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <mutex>
 #include <vector>
 
 #include "tc.cuh"
@@ -268,21 +269,28 @@ static int launch_conv(const ConvArgs &a, cudaStream_t st)
 {
     constexpr int KP = 9 * CIN;
     constexpr int smem = 2 * 3 * (CIN / 8) * kChunkBytes + NOUT * KP * 2;
-    static int set = 0, ctas = 1;
-    if (!set) {
-        SUPCG_CUDA_TRY(cudaFuncSetAttribute(k_conv<CIN, NOUT, EPI>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        SUPCG_CUDA_TRY(cudaFuncSetAttribute(k_conv<CIN, NOUT, EPI>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                            (int)cudaSharedmemCarveoutMaxShared));
-        int per_sm = 1, dev = 0, nsm = 1;
-        SUPCG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_conv<CIN, NOUT, EPI>, kTile, smem));
-        SUPCG_CUDA_TRY(cudaGetDevice(&dev));
-        SUPCG_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-        int smem_sm = 0;
-        SUPCG_CUDA_TRY(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
-        const int by_smem = smem_sm / (smem + 2048);   // dynamic + static shared memory and the per-CTA reserve
-        per_sm = std::max(per_sm, std::min(by_smem, 512 / 64));   // 64 tensor-memory columns per CTA
-        ctas = nsm * std::max(1, per_sm);
-        set = 1;
+    // attributes and the persistent grid size are per device
+    static std::mutex mu;
+    static int ctas_dev[kMaxDevices] = {};
+    int dev = 0;
+    int rc0 = current_device(&dev);
+    if (rc0) return rc0;
+    rc0 = func_attrs_once((const void *)k_conv<CIN, NOUT, EPI>, smem, (int)cudaSharedmemCarveoutMaxShared);
+    if (rc0) return rc0;
+    int ctas;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        if (!ctas_dev[dev]) {
+            int per_sm = 1, nsm = 1;
+            SUPCG_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_conv<CIN, NOUT, EPI>, kTile, smem));
+            SUPCG_CUDA_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+            int smem_sm = 0;
+            SUPCG_CUDA_TRY(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev));
+            const int by_smem = smem_sm / (smem + 2048);   // dynamic + static shared memory and the per-CTA reserve
+            per_sm = std::max(per_sm, std::min(by_smem, 512 / 64));   // 64 tensor-memory columns per CTA
+            ctas_dev[dev] = nsm * std::max(1, per_sm);
+        }
+        ctas = ctas_dev[dev];
     }
     CUtensorMap tm;
     int rc = nhwc_map(&tm, a.in, CIN, a.ny, a.nx, a.count, kBoxPix);
@@ -459,13 +467,8 @@ static int launch_wgrad(const __nv_bfloat16 *in, const __nv_bfloat16 *G, int cin
                         int count, int max_ctas, float *partial, int *status, cudaStream_t st)
 {
     constexpr int smem = 2 * kWgStageBytes + 2 * (GCH / 8) * kChunkBytes;
-    static int set = 0;
-    if (!set) {
-        SUPCG_CUDA_TRY(cudaFuncSetAttribute(k_wgrad<CIN, GCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        SUPCG_CUDA_TRY(cudaFuncSetAttribute(k_wgrad<CIN, GCH>, cudaFuncAttributePreferredSharedMemoryCarveout,
-                                            (int)cudaSharedmemCarveoutMaxShared));
-        set = 1;
-    }
+    const int rc0 = func_attrs_once((const void *)k_wgrad<CIN, GCH>, smem, (int)cudaSharedmemCarveoutMaxShared);
+    if (rc0) return rc0;
     CUtensorMap tin, tg;
     int rc = nhwc_map(&tin, in, CIN, ny, nx, count, kBoxPix);
     if (!rc) rc = nhwc_map(&tg, G, GCH, ny, nx, count, kTile);

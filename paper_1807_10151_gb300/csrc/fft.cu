@@ -360,11 +360,8 @@ int launch_fft_dtab(const Launch &L)
 
 int launch_fft_rows(const Launch &L, int inverse, int standalone, int smem)
 {
-    static int set = 0;
-    if (!set) {
-        SUPCG_CUDA_TRY(cudaFuncSetAttribute(k_fft_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-        set = 1;
-    }
+    int rc = func_attrs_once((const void *)k_fft_rows, 200 * 1024);
+    if (rc) return rc;
     k_fft_rows<<<L.blocks, 256, smem, L.st>>>(L.probs, L.prefix, L.count, inverse, standalone);
     SUPCG_CUDA_TRY(cudaGetLastError());
     return SUPCG_OK;
@@ -372,11 +369,8 @@ int launch_fft_rows(const Launch &L, int inverse, int standalone, int smem)
 
 int launch_fft_cols(const Launch &L, int standalone, int smem)
 {
-    static int set = 0;
-    if (!set) {
-        SUPCG_CUDA_TRY(cudaFuncSetAttribute(k_fft_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-        set = 1;
-    }
+    int rc = func_attrs_once((const void *)k_fft_cols, 200 * 1024);
+    if (rc) return rc;
     k_fft_cols<<<L.blocks, 256, smem, L.st>>>(L.probs, L.prefix, L.count, standalone);
     SUPCG_CUDA_TRY(cudaGetLastError());
     return SUPCG_OK;
@@ -481,9 +475,41 @@ __global__ void __launch_bounds__(256) k_na_cols(FFTPlan fy, int nx, int cw, dou
     }
 }
 
-// Device address of g_noalloc_scratch, looked up once per device.
+// Device address of g_noalloc_scratch, looked up once per device and context: the set-up
+// runs again when the device's context has changed since (after cudaDeviceReset the module
+// is loaded anew and the array has a new address).
 std::mutex g_na_mutex;
-double2 *g_na_ptr[64] = {};
+struct NaSetup {
+    unsigned long long ctx_id;   // context the address belongs to
+    double2 *ptr;                // nullptr: not set up
+};
+NaSetup g_na[64] = {};
+
+typedef CUresult (*PfnCtxGetCurrent)(CUcontext *);
+typedef CUresult (*PfnCtxGetId)(CUcontext, unsigned long long *);
+
+// Unique ID of the calling thread's current context (the device's primary context,
+// which cudaSetDevice makes current and initialises).
+int current_ctx_id(int dev, unsigned long long *id)
+{
+    static PfnCtxGetCurrent get_cur = nullptr;
+    static PfnCtxGetId get_id = nullptr;
+    if (!get_cur || !get_id) {
+        void *p1 = nullptr, *p2 = nullptr;
+        cudaDriverEntryPointQueryResult q1, q2;
+        SUPCG_CUDA_TRY(cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p1, 12000, cudaEnableDefault, &q1));
+        SUPCG_CUDA_TRY(cudaGetDriverEntryPointByVersion("cuCtxGetId", &p2, 12000, cudaEnableDefault, &q2));
+        if (q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess || !p1 || !p2)
+            return SUPCG_ERR_CUDA;
+        get_cur = reinterpret_cast<PfnCtxGetCurrent>(p1);
+        get_id = reinterpret_cast<PfnCtxGetId>(p2);
+    }
+    SUPCG_CUDA_TRY(cudaSetDevice(dev));
+    CUcontext ctx = nullptr;
+    if (get_cur(&ctx) != CUDA_SUCCESS || !ctx) return SUPCG_ERR_CUDA;
+    if (get_id(ctx, id) != CUDA_SUCCESS) return SUPCG_ERR_CUDA;
+    return SUPCG_OK;
+}
 
 int noalloc_scratch(double2 **out)
 {
@@ -491,15 +517,19 @@ int noalloc_scratch(double2 **out)
     SUPCG_CUDA_TRY(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 64) return SUPCG_ERR_UNSUPPORTED;
     std::lock_guard<std::mutex> lk(g_na_mutex);
-    if (!g_na_ptr[dev]) {
+    unsigned long long id = 0;
+    int rc = current_ctx_id(dev, &id);
+    if (rc) return rc;
+    if (!g_na[dev].ptr || g_na[dev].ctx_id != id) {
         void *p = nullptr;
         // the host-side symbol is only a stand-in: the kernels need this device address
         SUPCG_CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
         SUPCG_CUDA_TRY(cudaFuncSetAttribute(k_na_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 1024));
         SUPCG_CUDA_TRY(cudaFuncSetAttribute(k_na_cols, cudaFuncAttributeMaxDynamicSharedMemorySize, 128 * 1024));
-        g_na_ptr[dev] = static_cast<double2 *>(p);
+        g_na[dev].ptr = static_cast<double2 *>(p);
+        g_na[dev].ctx_id = id;
     }
-    *out = g_na_ptr[dev];
+    *out = g_na[dev].ptr;
     return SUPCG_OK;
 }
 

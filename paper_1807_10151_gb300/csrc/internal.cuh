@@ -21,7 +21,8 @@ constexpr int kBwdViewParts = 4;     // backprojector: blocks per tile, each tak
 constexpr int kBwdTileJ = 32;        // backprojector pixel tile (columns)
 constexpr int kBwdViewChunk = 32;    // backprojector: views staged per shared-memory chunk
 constexpr int kRedThreads = 256;     // block size of the reduction / vector kernels
-constexpr long long kSpinLimit = 1ll << 24;  // bounded waits (iterations of a ~100 ns poll)
+constexpr long long kSpinLimit = 1ll << 24;  // bounded waits (iterations of a ~100 ns poll); grid barriers: the
+                                             // default of supcg_set_wait_limit
 
 // ----------------------------------------------------------------- views
 // Per-view constants.  Detector coordinates are in bins.  Pixel (i, j) has
@@ -238,6 +239,8 @@ struct Prob {
     double *partial;       // reduction partials (>= 2 * max blocks per kernel)
     unsigned *counter;     // last-block tickets [8]
     unsigned *bar;         // cooperative barrier [2]: arrivals, generation
+    long long wait_limit;  // polls before a cooperative barrier gives up (supcg_set_wait_limit)
+    int bar_extra;         // blocks a cooperative barrier waits for beyond its launch's (test hook, normally 0)
     double *log;           // nullable [max_iter][SUPCG_LOG_STRIDE]
     float *trace;          // nullable [max_iter][ny][nx]: x_k at the start of every while body
     // caller-owned I/O (unpadded): image in / out, sinogram in
@@ -364,9 +367,10 @@ __device__ __forceinline__ bool last_block(unsigned *counter, unsigned nblocks, 
 }
 
 // Bounded barrier among `nblocks` co-resident blocks (cooperative launch).
-// bar[0] counts arrivals, bar[1] is the generation.  Returns false on timeout
-// (and raises SUPCG_ERR_TIMEOUT in *status).
-__device__ __forceinline__ bool coop_barrier(unsigned *bar, unsigned nblocks, int *status, int *sh_flag)
+// bar[0] counts arrivals, bar[1] is the generation.  Returns false after
+// `limit` polls without a release (and raises SUPCG_ERR_TIMEOUT in *status).
+__device__ __forceinline__ bool coop_barrier(unsigned *bar, unsigned nblocks, int *status, int *sh_flag,
+                                             long long limit)
 {
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -382,7 +386,7 @@ __device__ __forceinline__ bool coop_barrier(unsigned *bar, unsigned nblocks, in
         } else {
             long long it = 0;
             while (*vgen == gen) {
-                if (++it > kSpinLimit) { ok = 0; atomicExch(status, (int)SUPCG_ERR_TIMEOUT); break; }
+                if (++it > limit) { ok = 0; atomicExch(status, (int)SUPCG_ERR_TIMEOUT); break; }
                 __nanosleep(64);
             }
         }
@@ -470,6 +474,14 @@ __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *tm, in
     } while (0)
 
 int cuda_fail(cudaError_t e, const char *what, const char *file, int line);
+
+// Kernel attributes are per device: once per (kernel, current device), raise the
+// kernel's dynamic shared-memory limit to max_dyn_smem bytes and, when carveout >= 0,
+// set its preferred shared-memory carveout.  Thread-safe.
+int func_attrs_once(const void *func, int max_dyn_smem, int carveout = -1);
+// Current device (0 .. kMaxDevices-1) for per-device host caches.
+constexpr int kMaxDevices = 64;
+int current_device(int *dev);
 
 // Launchers (defined in the kernel translation units).  Each enqueues one
 // kernel over all `count` problems of `probs` (device array) on `st`.

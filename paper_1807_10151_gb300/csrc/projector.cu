@@ -460,14 +460,10 @@ __global__ void __launch_bounds__(kFwdThreads, 10) k_forward(const Prob *__restr
 
 int launch_forward(const Launch &L, int which, int mode)
 {
-    static int max_smem_set = 0;
     // every problem's BW <= 256, so the warps' box buffers never exceed this size
     const int smem = (kFwdThreads / 32) * kFwdBufs * kRowsPerChunk * L.bw_max * 4;
-    if (!max_smem_set) {
-        SUPCG_CUDA_TRY(cudaFuncSetAttribute(k_forward, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            (kFwdThreads / 32) * kFwdBufs * kRowsPerChunk * 256 * 4));
-        max_smem_set = 1;
-    }
+    int rc = func_attrs_once((const void *)k_forward, (kFwdThreads / 32) * kFwdBufs * kRowsPerChunk * 256 * 4);
+    if (rc) return rc;
     k_forward<<<L.blocks, kFwdThreads, smem, L.st>>>(L.probs, L.prefix, L.count, which, mode);
     SUPCG_CUDA_TRY(cudaGetLastError());
     return SUPCG_OK;
@@ -854,12 +850,8 @@ int backward_blocks(int nx, int ny, int dual)
 
 int launch_backward(const Launch &L, int mode, int bwin)
 {
-    static int set = 0;
-    if (!set) {
-        SUPCG_CUDA_TRY(cudaFuncSetAttribute(k_backward<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            2 * kBwdViewChunk * 256 * 4));
-        set = 1;
-    }
+    int rc = func_attrs_once((const void *)k_backward<false>, 2 * kBwdViewChunk * 256 * 4);
+    if (rc) return rc;
     k_backward<false><<<L.blocks, kBwdThreads, 2 * kBwdViewChunk * bwin * 4, L.st>>>(L.probs, L.prefix, L.count,
                                                                                      mode);
     SUPCG_CUDA_TRY(cudaGetLastError());
@@ -868,12 +860,8 @@ int launch_backward(const Launch &L, int mode, int bwin)
 
 int launch_backward2(const Launch &L, int bwin)
 {
-    static int set = 0;
-    if (!set) {
-        SUPCG_CUDA_TRY(cudaFuncSetAttribute(k_backward<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                            2 * 2 * kBwdViewChunk * 256 * 4));
-        set = 1;
-    }
+    int rc = func_attrs_once((const void *)k_backward<true>, 2 * 2 * kBwdViewChunk * 256 * 4);
+    if (rc) return rc;
     k_backward<true><<<L.blocks, kBwdThreads, 2 * 2 * kBwdViewChunk * bwin * 4, L.st>>>(L.probs, L.prefix, L.count,
                                                                                        BWD_G);
     SUPCG_CUDA_TRY(cudaGetLastError());

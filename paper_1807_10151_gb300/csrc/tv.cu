@@ -130,7 +130,7 @@ __device__ __forceinline__ double phase_sum(const Prob &P, int nb, int slot, int
 {
     const double bs = block_sum<kTvThreads>(v, red);
     if (threadIdx.x == 0) P.partial[(size_t)slot * nb + local] = bs;
-    *ok = coop_barrier(P.bar, nb, &P.sc->status, flag);
+    *ok = coop_barrier(P.bar, nb + P.bar_extra, &P.sc->status, flag, P.wait_limit);
     if (!*ok) return 0.0;
     return block_sum_array<kTvThreads>(P.partial + (size_t)slot * nb, nb, red);
 }
@@ -216,7 +216,7 @@ __global__ void __launch_bounds__(kTvThreads, 3) k_stv(const Prob *__restrict__ 
                 P.partial[(size_t)9 * nb + local] = v2;
                 P.partial[(size_t)10 * nb + local] = v3;
             }
-            ok = coop_barrier(P.bar, nb, &sc->status, &flag);
+            ok = coop_barrier(P.bar, nb + P.bar_extra, &sc->status, &flag, P.wait_limit);
             if (ok) {
                 s_nn = block_sum_array<kTvThreads>(P.partial + (size_t)8 * nb, nb, red);
                 s_dd = block_sum_array<kTvThreads>(P.partial + (size_t)9 * nb, nb, red);
@@ -266,7 +266,7 @@ __global__ void __launch_bounds__(kTvThreads, 3) k_stv(const Prob *__restrict__ 
                     const int i = e / nx, jj = e - i * nx;
                     (void)x_step(x, xl, (size_t)i * ld + jj, c, dir[(size_t)i * nx + jj]);
                 }
-                ok = coop_barrier(P.bar, nb, &sc->status, &flag);
+                ok = coop_barrier(P.bar, nb + P.bar_extra, &sc->status, &flag, P.wait_limit);
                 ell += (long long)K + (j - 1);
                 total_trials = j;
                 tv_first = s_tv;
@@ -298,7 +298,7 @@ __global__ void __launch_bounds__(kTvThreads, 3) k_stv(const Prob *__restrict__ 
                 P.partial[(size_t)(4 + 2 * slot) * nb + local] = b1;
                 P.partial[(size_t)(5 + 2 * slot) * nb + local] = b2;
             }
-            ok = coop_barrier(P.bar, nb, &sc->status, &flag);
+            ok = coop_barrier(P.bar, nb + P.bar_extra, &sc->status, &flag, P.wait_limit);
             if (!ok) break;
             s_tv = block_sum_array<kTvThreads>(P.partial + (size_t)(4 + 2 * slot) * nb, nb, red);
             s_nn = block_sum_array<kTvThreads>(P.partial + (size_t)(5 + 2 * slot) * nb, nb, red);
@@ -367,7 +367,7 @@ __global__ void __launch_bounds__(kTvThreads, 3) k_stv(const Prob *__restrict__ 
                 const size_t p = (size_t)i * ld + j;
                 (void)x_step(x, xl, p, c, tb[p]);
             }
-            ok = coop_barrier(P.bar, nb, &sc->status, &flag);
+            ok = coop_barrier(P.bar, nb + P.bar_extra, &sc->status, &flag, P.wait_limit);
         }
         tv_last = tv_t;
     }

@@ -45,6 +45,20 @@ def test_argument_errors_are_status_codes():
     assert S.supcg_status_string(0) == "ok"
 
 
+def test_wait_limit_and_barrier_hook_check_their_arguments():
+    """Host-only settings: out-of-range values are refused, valid ones accepted."""
+    L = S.load()
+    assert L.supcg_set_wait_limit(0) == -1
+    assert L.supcg_set_barrier_shortfall(-1) == -1
+    assert L.supcg_set_barrier_shortfall(1025) == -1
+    try:
+        assert L.supcg_set_wait_limit(1 << 10) == 0
+        assert L.supcg_set_barrier_shortfall(2) == 0
+    finally:
+        assert L.supcg_set_barrier_shortfall(0) == 0
+        assert L.supcg_set_wait_limit(S.DEFAULT_WAIT_LIMIT) == 0
+
+
 def test_param_struct_layout_matches_header():
     # offsets follow the C layout of supcg_params / supcg_report on LP64
     assert S.Params.a.offset == 8 and S.Params.max_iter.offset == 48 and S.Params.max_trials.offset == 56
