@@ -134,18 +134,35 @@ def nnz_per_projection(N, V, U, d_over_ds=1.0):
     return N * N * s * d_over_ds
 
 
-def make_problem(rank, device):
+def workload_data(seed=None, noise_seed=None):
+    """b of the benchmark workload, the same array for both arms: exact line
+    integrals of the continuous 20-ellipse phantom (the paper's simulations
+    take line integrals through a continuous phantom), Poisson counts at 1e5
+    photons per ray, log-transformed, rounded to FP32."""
     import numpy as np
-    import torch
-    import paper_1807_10151_gb300 as S
     from paper_1807_10151_gb300 import synth
+    seed = WL["seed"] if seed is None else seed
+    noise_seed = WL["noise_seed"] if noise_seed is None else noise_seed
+    clean = synth.ellipse_sinogram(WL["n_ell"], seed, WL["V"], WL["U"], 1.0 / WL["N"])
+    return synth.poisson_log(clean, WL["I0"], noise_seed).astype(np.float32)
+
+
+def workload_config(iters):
+    """config of the contract line: the workload alone, identical in both arms."""
+    return {"workload": WORKLOAD, "image": [WL["N"], WL["N"]], "views": WL["V"], "bins": WL["U"],
+            "iterations": iters, "K": WL["K"], "gamma": WL["gamma"], "a": WL["a"], "mu": WL["mu"],
+            "rho": WL["rho"], "phantom": f"{WL['n_ell']} ellipses, seed {WL['seed']}",
+            "data": f"analytic line integrals, Poisson {WL['I0']:g} photons per ray, seed {WL['noise_seed']}",
+            "l2": "flushed (256 MB write) before every timed solve; one 512^2 problem's working set "
+                  "(~16 MB) then stays L2-resident across its iterations"}
+
+
+def make_problem(rank, device):
+    import paper_1807_10151_gb300 as S
     from paper_1807_10151_gb300 import replicas
     G = S.Geometry(WL["N"], n_views=WL["V"], n_bins=WL["U"])
     seed, noise_seed = replicas.rank_seeds(rank, WL["seed"], WL["noise_seed"])   # each replica its own problem
-    x_true = synth.ellipse_phantom(WL["N"], WL["n_ell"], seed)
-    clean = G.project(torch.tensor(x_true, dtype=torch.float32, device=device)).double().cpu().numpy()
-    b = synth.poisson_log(clean, WL["I0"], noise_seed).astype(np.float32)
-    return G, b
+    return G, workload_data(seed, noise_seed)
 
 
 def solve_kw(iters, graph=True):
@@ -157,13 +174,11 @@ def oracle_sample(iters):
     """The FP64 oracle on the same workload: explicit CSR R, then SupPCG."""
     import numpy as np
     from oracle import oracle as O
-    from paper_1807_10151_gb300 import synth
     og = O.Geometry(WL["N"], V=WL["V"], U=WL["U"])
     t0 = time.perf_counter()
     R = O.CSR(og)
     t_build = time.perf_counter() - t0
-    x_true = synth.ellipse_phantom(WL["N"], WL["n_ell"], WL["seed"])
-    b = synth.poisson_log(R.project(x_true), WL["I0"], WL["noise_seed"])
+    b = workload_data().astype(np.float64)   # the GPU arm's b, bit for bit
     t0 = time.perf_counter()
     out = O.suppcg(R, b, K=WL["K"], a=WL["a"], gamma=WL["gamma"], mu=WL["mu"], rho=WL["rho"], max_iter=iters)
     t_solve = time.perf_counter() - t0
@@ -184,21 +199,30 @@ def smooth_sides(lo=256, hi=1024):
     return out
 
 
-def run_batched(args, dev):
-    """64 uneven problems in one batched schedule vs one at a time."""
+def batched_comparison(steps, warmup, dev, tune=True):
+    """64 uneven problems (images 256^2-1024^2 with 2^a 3^b 5^c sides, 180-1440
+    views, ceil(1.42 N) bins, 15-ellipse phantoms, 1 % Gaussian noise) solved by
+    one batched schedule, then the same problems one after another.  Both give
+    the same iterates (bitwise), so the time ratio is the time-to-equal ratio.
+    Each geometry's forward tile is chosen by the autotuner first (cached per
+    geometry bucket).  Returns a dict with its own clock record."""
     import numpy as np
     import torch
     import paper_1807_10151_gb300 as S
-    from paper_1807_10151_gb300 import synth
+    from paper_1807_10151_gb300 import autotune, synth
     rng = np.random.default_rng(3000)
     sides = smooth_sides()
     geoms, bs = [], []
     nnz = 0.0
+    tiles = {}
     for c in range(64):
         N = int(rng.choice(sides))
         V = int(rng.integers(180, 1441))
         U = int(math.ceil(1.42 * N))
         G = S.Geometry(N, n_views=V, n_bins=U)
+        if tune:
+            t = autotune.tune(G, reps=3)["tile"]
+            tiles[t] = tiles.get(t, 0) + 1
         x = synth.ellipse_phantom(N, 15, 3000 + c)
         clean = G.project(torch.tensor(x, dtype=torch.float32, device=dev)).double().cpu().numpy()
         bs.append(torch.tensor(synth.gaussian_noise(clean, 0.01, 3500 + c), dtype=torch.float32, device=dev))
@@ -207,7 +231,9 @@ def run_batched(args, dev):
     kw = dict(K=WL["K"], a=WL["a"], gamma=WL["gamma"], mu=WL["mu"], rho=WL["rho"])
     st = torch.cuda.current_stream()
     xs = [torch.zeros(g.ny, g.nx, device=dev) for g in geoms]
-    S.solve_batched(geoms, bs, xs, max_iter=args.warmup, **kw)
+    S.solve_batched(geoms, bs, xs, max_iter=warmup, **kw)
+    for g, b in zip(geoms, bs):      # warm each geometry's own workspace for the sequential run
+        g.solve(b, max_iter=1, **kw)
     for x in xs:
         x.zero_()
     torch.cuda.synchronize()
@@ -215,35 +241,46 @@ def run_batched(args, dev):
     l0 = S.supcg_kernel_launches()
     with ClockSampler(dev.index or 0) as clk:
         ev[0].record(st)
-        reps = S.solve_batched(geoms, bs, xs, max_iter=args.steps, **kw)
+        reps = S.solve_batched(geoms, bs, xs, max_iter=steps, **kw)
         ev[1].record(st)
         torch.cuda.synchronize()
-    launches = S.supcg_kernel_launches() - l0
+        launches = S.supcg_kernel_launches() - l0
+        ev[2].record(st)
+        for g, b in zip(geoms, bs):
+            g.solve(b, max_iter=steps, **kw)
+        ev[3].record(st)
+        torch.cuda.synchronize()
     assert all(r["status"] == 0 for r in reps), reps
     t_batch = ev[0].elapsed_time(ev[1]) / 1000.0
-    # the same problems one after another (warm each geometry's workspace first)
-    for g, b in zip(geoms, bs):
-        g.solve(b, max_iter=1, **kw)
-    torch.cuda.synchronize()
-    ev[2].record(st)
-    for g, b in zip(geoms, bs):
-        g.solve(b, max_iter=args.steps, **kw)
-    ev[3].record(st)
-    torch.cuda.synchronize()
     t_seq = ev[2].elapsed_time(ev[3]) / 1000.0
-    value = 64 * args.steps / t_batch
+    out = {"problems": 64, "iterations": steps, "batched_s": t_batch, "sequential_s": t_seq,
+           "time_to_equal_ratio": t_seq / t_batch,
+           "problem_iterations_per_s": {"batched": 64 * steps / t_batch, "sequential": 64 * steps / t_seq},
+           "intersections_per_s_batched": 4.0 * nnz * steps / t_batch, "gpu_launches_batched": int(launches),
+           "sides": [min(g.nx for g in geoms), max(g.nx for g in geoms)],
+           "views": [min(g.V for g in geoms), max(g.V for g in geoms)],
+           "fwd_tiles": {str(k): v for k, v in sorted(tiles.items())}, "clocks": clk.summary(),
+           "equal_by": "identical iterates (the batched schedule runs the same kernels per problem)"}
+    for g in geoms:
+        g.close()
+    return out
+
+
+def run_batched(args, dev):
+    """64 uneven problems in one batched schedule vs one at a time."""
+    r = batched_comparison(args.steps, args.warmup, dev)
     line = {
-        "metric": "SupPCG problem-iterations/s (batched)", "value": value, "unit": "problem-iterations/s",
-        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * t_batch / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": "suppcg_batched_64_uneven", "problems": 64,
-                   "sides": sorted({g.nx for g in geoms}), "views": [min(g.V for g in geoms), max(g.V for g in geoms)],
+        "metric": "SupPCG problem-iterations/s (batched)", "value": r["problem_iterations_per_s"]["batched"],
+        "unit": "problem-iterations/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 * r["batched_s"] / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "suppcg_batched_64_uneven", "problems": 64, "sides": r["sides"], "views": r["views"],
                    "K": WL["K"], "gamma": WL["gamma"], "a": WL["a"], "mu": WL["mu"], "rho": WL["rho"],
                    "l2": "working set of the batch (several GB) exceeds L2"},
-        "sequential": {"seconds": t_seq, "problem_iterations_per_s": 64 * args.steps / t_seq,
-                       "time_to_equal_ratio": t_seq / t_batch},
-        "intersections_per_s": 4.0 * nnz * args.steps / t_batch,
-        "gpu_launches": int(launches), "clocks": clk.summary(),
+        "sequential": {"seconds": r["sequential_s"], "problem_iterations_per_s": r["problem_iterations_per_s"]["sequential"],
+                       "time_to_equal_ratio": r["time_to_equal_ratio"]},
+        "intersections_per_s": r["intersections_per_s_batched"], "fwd_tiles": r["fwd_tiles"],
+        "gpu_launches": r["gpu_launches_batched"], "clocks": r["clocks"],
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -566,11 +603,8 @@ def run_learned(args, dev):
                        "train_step_32x128x128": t_step_ms},
     }
     print(json.dumps(line), flush=True)
-    try:
-        os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
-        np.save(os.path.join(ROOT, "gpurun_out", "cnn_params.npy"), params)
-    except OSError:
-        pass
+    if args.save_params:
+        np.save(args.save_params, params)
     return 0
 
 
@@ -584,11 +618,9 @@ def run_reference(args, rank, world):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1000.0 * s["t_solve_s"] / s["iters"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "image": [WL["N"], WL["N"]], "views": WL["V"], "bins": WL["U"],
-                   "iterations": s["iters"], "K": WL["K"], "gamma": WL["gamma"], "a": WL["a"],
-                   "mu": WL["mu"], "rho": WL["rho"], "l2": "n/a (CPU)"},
+        "config": workload_config(s["iters"]),
         "cpu_baseline": {"value": val, "unit": "iterations/s", "cores": s["cores"], "kind": "oracle",
-                         "sample": f"FP64 oracle SupPCG, {s['iters']} iterations (plus steps 1-9) after building "
+                         "sample": f"FP64 oracle SupPCG on the same b, {s['iters']} iterations (plus steps 1-9) after building "
                                    f"the explicit R ({s['nnz']} nonzeros, {s['t_build_s']:.1f} s, not timed)"},
         "e2e": {"value": val, "unit": "iterations/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -604,6 +636,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-iters", type=int, default=3)
+    ap.add_argument("--repeats", type=int, default=5, help="timed solves; the line reports their median")
+    ap.add_argument("--no-time-to-equal", action="store_true",
+                    help="skip the batched-vs-sequential time-to-equal measurement of the default workload")
+    ap.add_argument("--save-params", default=None, help="learned512: write the trained network's parameters here")
     ap.add_argument("--workload", default="plain512",
                     choices=["plain512", "batched64", "large2048", "learned512", "sweep243", "art512"])
     args = ap.parse_args()
@@ -640,7 +676,7 @@ def main():
         return run_art(args, dev)
     G, b_host = make_problem(rank, dev)
     b = torch.tensor(b_host, device=dev)
-    from paper_1807_10151_gb300 import autotune
+    from paper_1807_10151_gb300 import autotune, replicas
     tiling = autotune.tune(G)          # forward-projector tile for this geometry (cached per bucket)
 
     def barrier():
@@ -652,35 +688,40 @@ def main():
     x, rep, _ = G.solve(b, **solve_kw(args.warmup))
     assert rep["status"] == 0, rep
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > L2
-    flush.fill_(1.0)
-    barrier()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    repeats = max(1, args.repeats)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(repeats)]
     launches0 = S.supcg_kernel_launches()
     with ClockSampler(local) as clk:
-        ev0.record(st)
-        x, rep, _ = G.solve(b, **solve_kw(args.steps))
-        ev1.record(st)
-        barrier()
-    launches = S.supcg_kernel_launches() - launches0
-    assert rep["status"] == 0 and rep["iters"] == args.steps, rep
-    from paper_1807_10151_gb300 import replicas
-    ms_max = 1000.0 * replicas.slowest(ev0.elapsed_time(ev1) / 1000.0, dist, dev)   # slowest rank
+        for r in range(repeats):     # one timed solve of `steps` iterations per repeat, L2 flushed before each
+            flush.fill_(float(r))
+            barrier()
+            ev[r][0].record(st)
+            x, rep, _ = G.solve(b, **solve_kw(args.steps))
+            ev[r][1].record(st)
+            barrier()
+            assert rep["status"] == 0 and rep["iters"] == args.steps, rep
+    launches = (S.supcg_kernel_launches() - launches0) // repeats
+    solve_s = [e0.elapsed_time(e1) / 1000.0 for e0, e1 in ev]
+    t_med = statistics.median(solve_s)
+    ms_max = 1000.0 * replicas.slowest(t_med, dist, dev)   # slowest rank
     value = replicas.job_rate(args.steps, world, ms_max / 1000.0)
 
-    # end to end through the host-buffer entry point (copies in the timed region)
+    # end to end through the host-buffer entry point (copies in the timed region), median of the repeats
     b_pin = torch.tensor(b_host).pin_memory()
     x_pin = torch.zeros(WL["N"], WL["N"], dtype=torch.float32).pin_memory()
-    barrier()
-    t0 = time.perf_counter()
-    rep_h = G.solve_host(b_pin.numpy(), x_pin.numpy(), **solve_kw(args.steps))
-    t_e2e = time.perf_counter() - t0
-    assert rep_h["status"] == 0, rep_h
-    e2e_value = replicas.job_rate(args.steps, world, replicas.slowest(t_e2e, dist, dev))
+    e2e_s = []
+    for r in range(repeats):
+        flush.fill_(float(r))
+        barrier()
+        t0 = time.perf_counter()
+        rep_h = G.solve_host(b_pin.numpy(), x_pin.numpy(), **solve_kw(args.steps))
+        e2e_s.append(time.perf_counter() - t0)
+        assert rep_h["status"] == 0, rep_h
+    e2e_value = replicas.job_rate(args.steps, world, replicas.slowest(statistics.median(e2e_s), dist, dev))
 
     # per-kernel breakdown of the same solve (events around every launch)
     _, rep_p, kinds = G.solve_profiled(b, **solve_kw(args.steps, graph=False))
     fwd_ms, fwd_n = kinds["forward"]
-    bwd_ms, bwd_n = kinds["backward"]
     tot_ms = sum(v[0] for v in kinds.values())
     clocks = clk.summary()
 
@@ -703,11 +744,15 @@ def main():
         except (ValueError, OSError):
             traffic = None
 
+    tte = None
+    if rank == 0 and world == 1 and not args.no_time_to_equal:
+        tte = {"batched_vs_sequential": batched_comparison(args.steps, args.warmup, dev)}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         s = oracle_sample(args.cpu_iters)
         cpu = {"value": s["iters"] / s["t_solve_s"], "unit": "iterations/s", "cores": s["cores"], "kind": "oracle",
-               "sample": f"same workload, {s['iters']} SupPCG iterations (plus steps 1-9) of the FP64 oracle "
+               "sample": f"same workload and b, {s['iters']} SupPCG iterations (plus steps 1-9) of the FP64 oracle "
                          f"after building its explicit R ({s['nnz']} nonzeros, {s['t_build_s']:.1f} s, not timed)"}
 
     if rank == 0:
@@ -716,12 +761,11 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "image": [WL["N"], WL["N"]], "views": WL["V"], "bins": WL["U"],
-                       "iterations": args.steps, "K": WL["K"], "gamma": WL["gamma"], "a": WL["a"],
-                       "mu": WL["mu"], "rho": WL["rho"], "graph": True, "parallelism": f"replicas{world}",
-                       "fwd_tile": tiling["tile"],
-                       "l2": "flushed (256 MB write) before the timed solve; the ~14 MB working set of one "
-                             "512^2 problem then stays L2-resident across its iterations"},
+            "config": workload_config(args.steps),
+            "timing": {"repeats": repeats, "statistic": "median", "solve_s": solve_s,
+                       "timed_region": "one supcg_solve of `steps` iterations (staging and steps 1-9 included) "
+                                       "per repeat, CUDA events on the launching stream"},
+            "impl": {"graph": True, "parallelism": f"replicas{world}", "fwd_tile": tiling["tile"]},
             "roofline": {"bound": "alu", "kernel": "k_forward", "achieved": achieved, "peak": peak_alu,
                          "unit": "TOP/s", "frac": achieved / peak_alu, "traffic": traffic,
                          "basis": f"{nnz:.4g} intersections x {OPS_PER_INTERSECTION} FP32 ops per launch; peak = "
@@ -732,11 +776,14 @@ def main():
             "e2e": {"value": e2e_value, "unit": "iterations/s",
                     "h2d_bytes_per_step": 4.0 * (WL["V"] * WL["U"] + WL["N"] ** 2) / args.steps,
                     "d2h_bytes_per_step": 4.0 * WL["N"] ** 2 / args.steps,
-                    "note": "one supcg_solve_host call of `steps` iterations; b and x_0 copied in, x copied out"},
+                    "note": "median of the repeats of one supcg_solve_host call of `steps` iterations; b and x_0 "
+                            "copied in, x copied out"},
             "gpu_launches": int(launches),
             "clocks": clocks,
             "report": {"f_last": rep["f_last"], "tv_last": rep["tv_last"], "ell": rep["ell"]},
         }
+        if tte:
+            line["time_to_equal"] = tte
         if cpu:
             line["cpu_baseline"] = cpu
         print(json.dumps(line), flush=True)

@@ -95,6 +95,75 @@ def textured_background(N: int, seed: int, sigma_px: float = 8.0, amplitude: flo
     return np.where(X ** 2 + Y ** 2 <= support_radius ** 2, sm, 0.0)
 
 
+def ellipse_sinogram(n_ellipses: int, seed: int, V: int, U: int, ds: float, off: float = 0.0,
+                     half_width: float = 0.5) -> np.ndarray:
+    """Exact line integrals of the continuous ellipse phantom of ellipse_params
+    (later ellipses overwrite earlier ones) restricted to the image square
+    [-half_width, half_width]^2, for the parallel-beam rays x cos(theta_v) +
+    y sin(theta_v) = s_u, theta_v = v pi / V, s_u = (u - (U-1)/2) ds + off.
+
+    This is the measurement model of the paper's simulations (the data are
+    line integrals through a continuous phantom, Sec. 4.1), not the
+    reconstruction's pixel matrix: the phantom's ellipses are not pixelated.
+    Returns [V][U] (float64)."""
+    return ellipses_sinogram(ellipse_params(n_ellipses, seed), V, U, ds, off, half_width)
+
+
+def ellipses_sinogram(ell, V: int, U: int, ds: float, off: float = 0.0, half_width: float = 0.5) -> np.ndarray:
+    """ellipse_sinogram for an explicit list of ellipses (cx, cy, ax, ay, angle, density)."""
+    th = np.arange(V) * (np.pi / V)
+    s = (np.arange(U) - 0.5 * (U - 1)) * ds + off
+    c = np.cos(th)[:, None] * np.ones((1, U))
+    sn = np.sin(th)[:, None] * np.ones((1, U))
+    q = np.pi / 2
+    axis = np.abs(th / q - np.round(th / q)) < 1e-12     # exact cos/sin on the axes
+    c[axis] = np.where(np.round(th[axis] / q) % 2 == 0, 1.0, 0.0)[:, None]
+    sn[axis] = np.where(np.round(th[axis] / q) % 2 == 0, 0.0, 1.0)[:, None]
+    S = np.broadcast_to(s[None, :], (V, U))
+    c, sn, S = c.ravel(), sn.ravel(), S.ravel()
+    # point of ray r at parameter t: S (c, sn) + t (-sn, c); the square's chord [lo, hi]
+    px, py = S * c, S * sn
+    lo, hi = np.full(S.shape, -np.inf), np.full(S.shape, np.inf)
+    for p0, dirn in ((px, -sn), (py, c)):
+        with np.errstate(divide="ignore", invalid="ignore"):
+            ta = (-half_width - p0) / dirn
+            tb = (half_width - p0) / dirn
+        par = dirn == 0.0
+        inside = np.abs(p0) <= half_width
+        lo = np.where(par, np.where(inside, lo, np.inf), np.maximum(lo, np.minimum(ta, tb)))
+        hi = np.where(par, np.where(inside, hi, -np.inf), np.minimum(hi, np.maximum(ta, tb)))
+    E = len(ell)
+    t1 = np.empty((S.size, E))
+    t2 = np.empty((S.size, E))
+    for e, (cx, cy, ax, ay, ang, _) in enumerate(ell):
+        ca, sa = np.cos(ang), np.sin(ang)
+        u0 = (px - cx) * ca + (py - cy) * sa
+        v0 = -(px - cx) * sa + (py - cy) * ca
+        u1 = -sn * ca + c * sa
+        v1 = sn * sa + c * ca
+        A = u1 * u1 / ax ** 2 + v1 * v1 / ay ** 2
+        B = 2.0 * (u0 * u1 / ax ** 2 + v0 * v1 / ay ** 2)
+        Cq = u0 * u0 / ax ** 2 + v0 * v0 / ay ** 2 - 1.0
+        disc = B * B - 4.0 * A * Cq
+        rt = np.sqrt(np.maximum(disc, 0.0))
+        a_ = np.where(disc > 0, (-B - rt) / (2.0 * A), np.inf)
+        b_ = np.where(disc > 0, (-B + rt) / (2.0 * A), -np.inf)
+        t1[:, e] = np.clip(a_, lo, hi)
+        t2[:, e] = np.clip(b_, lo, hi)
+    # segments between consecutive breakpoints; each takes the last ellipse containing its midpoint
+    bp = np.concatenate([t1, t2, lo[:, None], hi[:, None]], axis=1)
+    bp = np.where(np.isfinite(bp), bp, 0.0)
+    bp = np.clip(bp, np.where(np.isfinite(lo), lo, 0.0)[:, None], np.where(np.isfinite(hi), hi, 0.0)[:, None])
+    bp.sort(axis=1)
+    mid = 0.5 * (bp[:, 1:] + bp[:, :-1])
+    val = np.zeros_like(mid)
+    for e, (_, _, _, _, _, dens) in enumerate(ell):
+        val = np.where((mid >= t1[:, e:e + 1]) & (mid <= t2[:, e:e + 1]), dens, val)
+    out = np.sum(np.diff(bp, axis=1) * val, axis=1)
+    out[~(hi > lo)] = 0.0
+    return out.reshape(V, U)
+
+
 def gaussian_noise(clean: np.ndarray, level: float, seed: int) -> np.ndarray:
     """b = clean + e, e ~ N(0, sigma^2), sigma = level * ||clean|| / sqrt(m)."""
     rng = np.random.default_rng(seed)

@@ -44,9 +44,18 @@ def test_reference_arm_prints_the_contract_line():
     assert d["metric"] == "SupPCG iterations/s" and d["unit"] == "iterations/s" and d["higher_is_better"] is True
     assert d["steps"] == 1 and d["warmup"] == 3 and d["n_gpus"] == 1
     assert d["value"] > 0 and d["ms_per_step"] > 0
-    assert d["config"]["workload"] == "suppcg_512x512_720views_725bins_poisson1e5"
+    assert d["config"] == bench.workload_config(1)   # the GPU arm's config, key for key
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["value"] == d["value"] and cb["cores"] >= 1 and cb["sample"]
     e2e = d["e2e"]
     assert e2e["value"] == d["value"] and e2e["unit"] == d["unit"]
     assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
+
+
+def test_both_arms_take_the_same_data():
+    """b is generated once from the analytic sinogram (no projector of either arm
+    involved), rounded to FP32; the oracle arm widens the same array."""
+    b1 = bench.workload_data()
+    b2 = bench.workload_data()
+    assert b1.dtype.name == "float32" and b1.shape == (bench.WL["V"], bench.WL["U"])
+    assert (b1 == b2).all()
