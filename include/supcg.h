@@ -320,6 +320,23 @@ int supcg_solve_trace(supcg_geometry g, const float *d_b, float *d_x, const supc
 int supcg_solve_learned(supcg_geometry g, supcg_cnn net, const float *d_b, float *d_x,
                         const supcg_params *p, supcg_report *rep, double *d_log, void *stream);
 
+/* The learned direction in a batched solve: `count` independent problems of
+ * possibly different views and bins but the network's image size, solved as
+ * supcg_solve_batched does (every kernel of an iteration over all problems,
+ * one graph per iteration), with the network run once per iteration over
+ * all problems' (x_k, tbar) as one batch.  Each problem's proposal is tested
+ * and used as in supcg_solve_learned, so every problem's iterates equal those
+ * of supcg_solve_learned on it alone.
+ *   gs[c], d_b[c], d_x[c]  geometry, data and image (in x_0, out x_{k-1/2}) of problem c
+ *   reps   host array of `count` reports (n_learned / n_fallback per problem)
+ * Requires count <= the network's max_batch, every image ny x nx equal to the
+ * network's and nx a multiple of 4.  The scratch (including the network's
+ * input batch, 2 count ny nx floats) lives in gs[0].  Synchronous.  Errors:
+ * SUPCG_ERR_ARG, SUPCG_ERR_UNSUPPORTED (image size), and those of supcg_solve. */
+int supcg_solve_batched_learned(const supcg_geometry *gs, supcg_cnn net, const float *const *d_b,
+                                float *const *d_x, int count, const supcg_params *p, supcg_report *reps,
+                                void *stream);
+
 /* Kernel kinds of supcg_solve_profiled. */
 typedef enum {
     SUPCG_KIND_FORWARD = 0,  /* forward projector (R x with residual, R p with ||R p||^2)   */

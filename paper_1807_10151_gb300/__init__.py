@@ -32,7 +32,7 @@ EXPORTED = ["supcg_create_geometry", "supcg_destroy_geometry", "supcg_project", 
             "supcg_cnn_get_params", "supcg_cnn_set_params", "supcg_cnn_forward", "supcg_cnn_gradients",
             "supcg_cnn_train_step", "supcg_solve_trace", "supcg_solve_learned", "supcg_set_tiling",
             "supcg_get_tiling", "supcg_solve_sweep", "supcg_art", "supcg_set_wait_limit",
-            "supcg_set_barrier_shortfall"]
+            "supcg_set_barrier_shortfall", "supcg_solve_batched_learned"]
 KINDS = ["forward", "backward", "fft", "stv", "vector", "cnn"]
 
 _lock = threading.Lock()
@@ -125,6 +125,8 @@ def load(allow_build: bool = True):
         L.supcg_cnn_train_step.argtypes = [vp, vp, vp, vp, i, d, C.POINTER(d), vp]
         L.supcg_solve_trace.argtypes = [vp, vp, vp, C.POINTER(Params), C.POINTER(Report), vp, vp, vp]
         L.supcg_solve_learned.argtypes = [vp, vp, vp, vp, C.POINTER(Params), C.POINTER(Report), vp, vp]
+        L.supcg_solve_batched_learned.argtypes = [C.POINTER(vp), vp, C.POINTER(vp), C.POINTER(vp), i,
+                                                  C.POINTER(Params), C.POINTER(Report), vp]
         L.supcg_set_tiling.argtypes = [vp, i]
         L.supcg_get_tiling.argtypes = [vp, C.POINTER(i)]
         L.supcg_set_wait_limit.argtypes = [ll]
@@ -136,6 +138,11 @@ def load(allow_build: bool = True):
                 getattr(L, name).restype = i
         _lib = L
         return L
+
+
+# Statuses a solve reports after running its iterations (in the report as well);
+# any other code means the call did not run and raises SupcgError.
+RUN_STATUSES = (0, -4, -5, -6)
 
 
 def _check(rc, what):
@@ -364,7 +371,7 @@ class Geometry:
         lg = torch.zeros(max(p.max_iter, 1), LOG_STRIDE, device=b.device, dtype=torch.float64) if log else None
         rc = supcg_solve(self.handle, _ptr(b, torch.float32), _ptr(x, torch.float32), p, rep,
                          _ptr(lg) if log else None, _stream(stream))
-        if rc not in (0,) and rc > -4:
+        if rc not in RUN_STATUSES:
             raise SupcgError(rc, "supcg_solve")
         out = rep.as_dict()
         out["rc"] = rc
@@ -380,7 +387,7 @@ class Geometry:
         cnt = (C.c_longlong * len(KINDS))()
         rc = supcg_solve_profiled(self.handle, _ptr(b, torch.float32), _ptr(x, torch.float32), p, rep, ms, cnt,
                                   _stream(stream))
-        if rc not in (0,) and rc > -4:
+        if rc not in RUN_STATUSES:
             raise SupcgError(rc, "supcg_solve_profiled")
         out = rep.as_dict()
         out["rc"] = rc
@@ -396,7 +403,7 @@ class Geometry:
         tr = torch.zeros(max(p.max_iter, 1), self.ny, self.nx, device=b.device, dtype=torch.float32)
         rc = load().supcg_solve_trace(self.handle, _ptr(b, torch.float32), _ptr(x, torch.float32), C.byref(p),
                                       C.byref(rep), _ptr(lg), _ptr(tr), _stream(stream))
-        if rc not in (0,) and rc > -4:
+        if rc not in RUN_STATUSES:
             raise SupcgError(rc, "supcg_solve_trace")
         out = rep.as_dict()
         out["rc"] = rc
@@ -411,7 +418,7 @@ class Geometry:
         lg = torch.zeros(max(p.max_iter, 1), LOG_STRIDE, device=b.device, dtype=torch.float64) if log else None
         rc = load().supcg_solve_learned(self.handle, net.handle, _ptr(b, torch.float32), _ptr(x, torch.float32),
                                         C.byref(p), C.byref(rep), _ptr(lg) if log else None, _stream(stream))
-        if rc not in (0,) and rc > -4:
+        if rc not in RUN_STATUSES:
             raise SupcgError(rc, "supcg_solve_learned")
         out = rep.as_dict()
         out["rc"] = rc
@@ -425,7 +432,7 @@ class Geometry:
                                                       else b_host.data_ptr()),
                               C.c_void_p(x_host.ctypes.data if hasattr(x_host, "ctypes") else x_host.data_ptr()),
                               p, rep, _stream(stream))
-        if rc not in (0,) and rc > -4:
+        if rc not in RUN_STATUSES:
             raise SupcgError(rc, "supcg_solve_host")
         out = rep.as_dict()
         out["rc"] = rc
@@ -443,8 +450,25 @@ def solve_batched(geoms, bs, xs, stream=None, **kw):
     reps = (Report * n)()
     p = make_params(**kw)
     rc = supcg_solve_batched(G, B, X, n, p, reps, _stream(stream))
-    if rc not in (0,) and rc > -4:
+    if rc not in RUN_STATUSES:
         raise SupcgError(rc, "supcg_solve_batched")
+    return [r.as_dict() for r in reps]
+
+
+def solve_batched_learned(geoms, net, bs, xs, stream=None, **kw):
+    """The learned direction over independent problems of the network's image size
+    in one batched schedule (supcg_solve_batched_learned); xs updated in place.
+    Returns the reports."""
+    import torch
+    n = len(geoms)
+    G = (C.c_void_p * n)(*[g.handle.value for g in geoms])
+    B = (C.c_void_p * n)(*[_ptr(b, torch.float32).value for b in bs])
+    X = (C.c_void_p * n)(*[_ptr(x, torch.float32).value for x in xs])
+    reps = (Report * n)()
+    p = make_params(**kw)
+    rc = load().supcg_solve_batched_learned(G, net.handle, B, X, n, C.byref(p), reps, _stream(stream))
+    if rc not in RUN_STATUSES:
+        raise SupcgError(rc, "supcg_solve_batched_learned")
     return [r.as_dict() for r in reps]
 
 
@@ -471,7 +495,7 @@ def solve_sweep(G, b, params, ref=None, se_axes=SE_AXES, stream=None):
                                   _ptr(ref, torch.float32) if ref is not None else None,
                                   float(se_axes[0]), float(se_axes[1]), _ptr(se) if se is not None else None,
                                   reps, _stream(stream))
-    if rc not in (0,) and rc > -4:
+    if rc not in RUN_STATUSES:
         raise SupcgError(rc, "supcg_solve_sweep")
     return xs, [r.as_dict() for r in reps], se
 

@@ -101,6 +101,9 @@ struct Workspace {
     int *trials_dev = nullptr;
     int trials_cap = 0;
     long long body_nodes = 0;
+    float *lstage = nullptr;    // batched learned solve: the network's input batch (x, then tbar)
+    size_t lstage_elems = 0;
+    int *hdone = nullptr;       // eps mode: pinned copies of the problems' done flags
 
     Launch L(int kt, cudaStream_t st) const
     {
@@ -121,6 +124,8 @@ struct Workspace {
         if (dp) cudaFree(dp);
         if (dprefix) cudaFree(dprefix);
         if (trials_dev) cudaFree(trials_dev);
+        if (lstage) cudaFree(lstage);
+        if (hdone) cudaFreeHost(hdone);
     }
 };
 
@@ -931,7 +936,13 @@ static int enqueue_body(Workspace *w, const supcg_params *p, cudaStream_t st, in
     const float *dir = nullptr;
     if (net && p->perturb && p->K > 0) {                                         // proposal of the network
         LAUNCH(SUPCG_KIND_STV, st, launch_tv_tbar(w->L(KT_TV, st)));
-        LAUNCH(SUPCG_KIND_CNN, st, cnn_forward(net, w->hp[0].x, w->hp[0].tbar, 1, st));
+        if (w->count == 1) {
+            LAUNCH(SUPCG_KIND_CNN, st, cnn_forward(net, w->hp[0].x, w->hp[0].tbar, 1, st));
+        } else {                                                                 // one batch for all problems
+            const size_t half = w->lstage_elems / 2;
+            LAUNCH(SUPCG_KIND_VECTOR, st, launch_gather_xt(w->L(KT_VEC, st), w->lstage, w->lstage + half));
+            LAUNCH(SUPCG_KIND_CNN, st, cnn_forward(net, w->lstage, w->lstage + half, w->count, st));
+        }
         dir = cnn_output(net);
     }
     if (p->perturb && p->K > 0)                                                 // steps 11-12
@@ -1031,8 +1042,8 @@ static int run_solve(Workspace *w, const float *const *d_b, float *const *d_x, c
 
     const int want_snorm = d_log != nullptr;
     const bool eps_mode = p->eps >= 0.0;
-    int *hdone = nullptr;
-    if (eps_mode) SUPCG_CUDA_TRY(cudaMallocHost(&hdone, sizeof(int) * w->count));
+    if (eps_mode && !w->hdone) SUPCG_CUDA_TRY(cudaMallocHost(&w->hdone, sizeof(int) * w->count));   // once per workspace
+    int *hdone = w->hdone;
     bool use_graph = p->graph != 0 && t_prof == nullptr;
     if (use_graph) {
         const double key[6] = {p->a, p->gamma, (double)p->max_trials, (double)p->K, (double)p->perturb,
@@ -1076,7 +1087,6 @@ static int run_solve(Workspace *w, const float *const *d_b, float *const *d_x, c
             if (all) break;
         }
     }
-    if (hdone) cudaFreeHost(hdone);
     LAUNCH(SUPCG_KIND_VECTOR, st, launch_store_out(w->L(KT_VEC, st), 0));
     std::vector<Scal> hs(w->count);
     for (int c = 0; c < w->count; ++c)
@@ -1204,6 +1214,44 @@ extern "C" int supcg_solve_batched(const supcg_geometry *gs, const float *const 
         owner->batch_key = key;
     }
     return run_solve(owner->ws_batch, d_b, d_x, p, reps, nullptr, (cudaStream_t)stream);
+}
+
+extern "C" int supcg_solve_batched_learned(const supcg_geometry *gs, supcg_cnn_s *net, const float *const *d_b,
+                                           float *const *d_x, int count, const supcg_params *p, supcg_report *reps,
+                                           void *stream)
+{
+    if (!gs || !net || !d_b || !d_x || !reps || count < 1) return SUPCG_ERR_ARG;
+    int ny = 0, nx = 0, cap = 0;
+    cnn_shape(net, &ny, &nx);
+    cnn_capacity(net, &cap);
+    if (count > cap) return SUPCG_ERR_ARG;
+    for (int c = 0; c < count; ++c) {
+        if (!gs[c] || !d_b[c] || !d_x[c]) return SUPCG_ERR_ARG;
+        if (gs[c]->ny != ny || gs[c]->nx != nx || gs[c]->nxp != nx) return SUPCG_ERR_UNSUPPORTED;
+    }
+    int rc = check_params(p);
+    if (rc) return rc;
+    supcg_geometry owner = gs[0];
+    std::vector<supcg_geometry> key(gs, gs + count);
+    if (!owner->ws_batch || owner->batch_key != key) {
+        free_ws(owner->ws_batch);
+        if ((rc = ws_create(key, &owner->ws_batch))) return rc;
+        owner->batch_key = key;
+    }
+    Workspace *w = owner->ws_batch;
+    const size_t need = 2 * (size_t)count * ny * nx;
+    if (w->lstage_elems != need) {
+        if (w->lstage) cudaFree(w->lstage);
+        w->lstage = nullptr;
+        w->lstage_elems = 0;
+        if (cudaMalloc(&w->lstage, need * sizeof(float)) != cudaSuccess) return SUPCG_ERR_NOMEM;
+        SUPCG_CUDA_TRY(cudaMemset(w->lstage, 0, need * sizeof(float)));
+        w->lstage_elems = need;
+    }
+    // run the network once outside any capture (kernel attributes are set on first use)
+    if ((rc = cnn_forward(net, w->lstage, w->lstage + need / 2, count, (cudaStream_t)stream))) return rc;
+    SUPCG_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    return run_solve(w, d_b, d_x, p, reps, nullptr, (cudaStream_t)stream, nullptr, net);
 }
 
 extern "C" int supcg_solve_sweep(supcg_geometry g, const float *d_b, float *const *d_x, int count,

@@ -339,6 +339,32 @@ __global__ void __launch_bounds__(kRedThreads) k_xupdate(const Prob *__restrict_
     }
 }
 
+// The iterates and tbar of every problem of a batched learned solve, back to back as
+// the network's input batch: xs, ts [count][ny][nx].  Every problem has the network's
+// image size and rows padded to nothing (nx a multiple of 4), so a problem's image is
+// one contiguous block; one float4 per thread, launched on the vector kernels' grid.
+__global__ void __launch_bounds__(kRedThreads) k_gather_xt(const Prob *__restrict__ probs, const int *__restrict__ prefix,
+                                                           int count, float *__restrict__ xs, float *__restrict__ ts)
+{
+    int local;
+    const int pi = find_problem(prefix, count, blockIdx.x, &local);
+    const Prob &P = probs[pi];
+    if (P.sc->done) return;
+    const size_t n = (size_t)P.ny * P.nx;
+    const size_t e4 = (size_t)local * kRedThreads + threadIdx.x;
+    if (4 * e4 < n) {
+        reinterpret_cast<float4 *>(xs + pi * n)[e4] = reinterpret_cast<const float4 *>(P.x)[e4];
+        reinterpret_cast<float4 *>(ts + pi * n)[e4] = reinterpret_cast<const float4 *>(P.tbar)[e4];
+    }
+}
+
+int launch_gather_xt(const Launch &L, float *xs, float *ts)
+{
+    k_gather_xt<<<L.blocks, kRedThreads, 0, L.st>>>(L.probs, L.prefix, L.count, xs, ts);
+    SUPCG_CUDA_TRY(cudaGetLastError());
+    return SUPCG_OK;
+}
+
 int launch_xupdate(const Launch &L)
 {
     k_xupdate<<<L.blocks, kRedThreads, 0, L.st>>>(L.probs, L.prefix, L.count);

@@ -880,6 +880,11 @@ int cnn_shape(supcg_cnn net, int *ny, int *nx)
     *nx = net->nx;
     return SUPCG_OK;
 }
+int cnn_capacity(supcg_cnn net, int *max_batch)
+{
+    *max_batch = net->cap;
+    return SUPCG_OK;
+}
 } // namespace supcg
 
 static int cnn_check(supcg_cnn net, int count)

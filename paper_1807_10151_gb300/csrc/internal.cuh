@@ -517,6 +517,7 @@ int launch_gray(const Launch &L);                           // sc->muX from bpad
 int launch_pupdate(const Launch &L);
 int launch_beta(const Launch &L);
 int launch_xupdate(const Launch &L);
+int launch_gather_xt(const Launch &L, float *xs, float *ts);   // x, tbar of every problem -> [count][ny][nx]
 int launch_stv(const Launch &L, int K, double a, double gamma, long long max_trials, int *trials_out,
                int want_snorm, const float *dir = nullptr);
 int launch_tv_tbar(const Launch &L);
@@ -524,5 +525,6 @@ int stv_max_blocks_per_sm(int *out);
 int cnn_forward(struct supcg_cnn_s *net, const float *d_x, const float *d_tbar, int count, cudaStream_t st);
 float *cnn_output(struct supcg_cnn_s *net);
 int cnn_shape(struct supcg_cnn_s *net, int *ny, int *nx);
+int cnn_capacity(struct supcg_cnn_s *net, int *max_batch);
 
 } // namespace supcg

@@ -136,12 +136,14 @@ __device__ __forceinline__ double phase_sum(const Prob &P, int nb, int slot, int
 }
 
 // S_TV(x, l, a, gamma, K), Algorithm 1, in place on P.x (one cooperative launch).
-// trials_out (nullable): [count][K] trials of every nonascending step.
+// trials_out (nullable): [count][K] trials of every nonascending step.  dir (nullable):
+// the learned proposals, [count][ny][nx] (every problem of the launch has the same size).
 __global__ void __launch_bounds__(kTvThreads, 3) k_stv(const Prob *__restrict__ probs, const int *__restrict__ prefix,
                                                     int count, int K_arg, double a_arg, double gamma_arg,
                                                     long long max_trials, int *trials_out, int want_snorm,
-                                                    const float *__restrict__ dir)
+                                                    const float *__restrict__ dir_all)
 {
+    const float *dir = dir_all;
     __shared__ double red[40];
     __shared__ int flag;
     __shared__ double sh_inv;   // grid-uniform FP64 scalars: computed by thread 0, read by all
@@ -163,6 +165,8 @@ __global__ void __launch_bounds__(kTvThreads, 3) k_stv(const Prob *__restrict__ 
     const int e0 = local * kTvThreads + threadIdx.x;
     float *x = P.x;
     float *xl = P.xlo;   // low part of the iterate (null: FP32 updates)
+    // a batched learned solve passes the proposals of all problems back to back ([count][ny][nx])
+    if (dir) dir += (size_t)pi * ny * nx;
     float *tb = P.tbar;
     long long ell = sc->ell;
     long long total_trials = 0;

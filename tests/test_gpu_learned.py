@@ -105,3 +105,47 @@ def test_training_on_method_pairs_beats_the_untrained_direction():
     _, trained_loss = net.gradients(Xh, Th, Dh)
     assert base_loss > 1e-3                     # the path bends: tbar alone is not the answer
     assert trained_loss < 0.8 * base_loss, (base_loss, trained_loss)
+
+
+def test_batched_learned_solve_equals_the_single_learned_solves():
+    """Three problems of one image size with different views and bins, the network
+    run once per iteration over all three (supcg_solve_batched_learned): each
+    problem's image, l and counts of accepted and rejected proposals equal those
+    of supcg_solve_learned on it alone, bit for bit.  The network's last layer is
+    seeded away from zero, so its proposals differ from tbar."""
+    import paper_1807_10151_gb300 as S
+    net = S.CNN(64, 64, max_batch=4, seed=5)
+    p = net.get_params()
+    layers = S.CNN.unflatten(p)
+    layers[4][0][...] = 0.05 * np.random.default_rng(6).standard_normal(layers[4][0].shape)
+    net.set_params(p)
+    kw = dict(K=6, a=0.97, gamma=0.3, mu=1e-5, rho=0.8, max_iter=12)
+    geoms, bs = [], []
+    for c, (V, U) in enumerate(((90, 95), (61, 92), (45, 101))):
+        og, R, x_true, b = config1_problem(seed=1200 + c, N=64, V=V, U=U)
+        geoms.append(gpu_geometry(og))
+        bs.append(to_dev(f32(b)))
+    singles = [g.solve_learned(net, b, **kw) for g, b in zip(geoms, bs)]
+    xs = [torch.zeros(64, 64, device="cuda") for _ in geoms]
+    reps = S.solve_batched_learned(geoms, net, bs, xs, **kw)
+    for (xs1, r1, _), xb, rb in zip(singles, xs, reps):
+        assert r1["status"] == 0 and rb["status"] == 0
+        assert rb["iters"] == r1["iters"] == 12 and rb["ell"] == r1["ell"]
+        assert rb["n_learned"] == r1["n_learned"] and rb["n_fallback"] == r1["n_fallback"]
+        np.testing.assert_array_equal(xb.cpu().numpy(), xs1.cpu().numpy())
+    assert sum(r["n_learned"] for r in reps) > 0
+
+
+def test_batched_learned_solve_rejects_other_image_sizes():
+    import paper_1807_10151_gb300 as S
+    net = S.CNN(64, 64, max_batch=2, seed=5)
+    og1, _, _, b1 = config1_problem(seed=1210, N=64, V=30, U=95)
+    og2, _, _, b2 = config1_problem(seed=1211, N=48, V=30, U=70)
+    geoms = [gpu_geometry(og1), gpu_geometry(og2)]
+    xs = [torch.zeros(g.ny, g.nx, device="cuda") for g in geoms]
+    with pytest.raises(S.SupcgError) as e:
+        S.solve_batched_learned(geoms, net, [to_dev(f32(b1)), to_dev(f32(b2))], xs, max_iter=2)
+    assert e.value.code == -8
+    with pytest.raises(S.SupcgError) as e:   # more problems than the network's batch
+        S.solve_batched_learned([geoms[0]] * 3, net, [to_dev(f32(b1))] * 3, [xs[0]] * 3, max_iter=2)
+    assert e.value.code == -1
