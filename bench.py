@@ -20,10 +20,14 @@ against solving them one after another (same iterates, so the time ratio is
 the time-to-equal ratio).
 --workload learned512: the learned direction.  Training pairs (x_k, tbar,
 K-step S_TV displacement) from plain SupPCG runs (Table 1: K=40,
-a=1-1e-5, gamma=1e-2, mu=1e-5, rho=0.8) on 400 random 128^2 problems x 50
-iterations (20k pairs), network trained on the GPU, then plain vs learned
-SupPCG on the 512^2 / 720-view Poisson workload: wall time for the learned
-solve to reach the plain solve's final residual and TV.
+a=1-1e-5, gamma=1e-2, mu=1e-5, rho=0.8) on 400 random 512^2 / 720-view
+problems x 50 iterations (20k pairs), network trained on the GPU, then plain
+vs learned SupPCG (trained and untrained networks) on the 512^2 / 720-view
+Poisson workload: wall time for the learned solve to reach the plain solve's
+final residual and TV; and the batched learned solve over 8 held-out
+problems against plain SupPCG on them.  The default workload's line carries
+the same comparison with a small training set (1024 pairs) in its
+time_to_equal object.
 --workload sweep243: the paper's parameter selection (Sec. 4.2) for SupPCG as
 one batched sweep: 180 grid points (K, a, gamma, mu, rho; rho = 0.4 excluded)
 x 15 iterations on a 243^2 / 360-view / 345-bin head stand-in (Poisson 1e5),
@@ -530,78 +534,119 @@ def run_large(args, dev):
     return 0
 
 
-def run_learned(args, dev):
+def learned_comparison(dev, steps, warmup, n_problems, iters_train, epochs, batch_problems=8, timings=False):
+    """The learned direction (Table 1's parameters) on the 512^2 / 720-view workload.
+
+    Training pairs (x_k, tbar at x_k, K-step S_TV displacement) come from plain
+    SupPCG runs on `n_problems` random 512^2 / 720-view problems x `iters_train`
+    iterations (the evaluation's own image size); the network trains on the GPU.
+    Then, each with its own clock record:
+      - trained and untrained networks (the untrained one proposes tbar itself)
+        against plain SupPCG on the benchmark's problem: wall time to reach the
+        plain run's final f and TV after `steps` iterations;
+      - the batched learned solve over `batch_problems` held-out problems against
+        plain SupPCG on them, batched and one after another."""
     import numpy as np
     import torch
     import paper_1807_10151_gb300 as S
-    from paper_1807_10151_gb300 import learned as Lr
+    from paper_1807_10151_gb300 import learned as Lr, synth
+    N, V = WL["N"], WL["V"]
     t0 = time.perf_counter()
-    X, T, D = Lr.make_training_set(400, N=128, V=180, iters=50, seed0=4000, device=dev)
+    X, T, D = Lr.make_training_set(n_problems, N=N, V=V, iters=iters_train, seed0=4000, device=dev)
     t_data = time.perf_counter() - t0
-    net = S.CNN(128, 128, max_batch=32, seed=11)
-    Xh, Th, Dh = Lr.make_training_set(4, N=128, V=180, iters=8, seed0=4900, device=dev)
-    _, loss_untrained = net.gradients(Xh, Th, Dh)
+    Xh, Th, Dh = Lr.make_training_set(2, N=N, V=V, iters=8, seed0=4900, device=dev)
+    bt = min(16, X.shape[0])
+    net = S.CNN(N, N, max_batch=max(bt, batch_problems), seed=11)
+    _, loss_untrained = net.gradients(Xh[:bt], Th[:bt], Dh[:bt])
     t0 = time.perf_counter()
-    hist = Lr.train(net, X, T, D, epochs=2, batch=32, lr=1e-3, log_every=200)
+    hist = Lr.train(net, X, T, D, epochs=epochs, batch=bt, lr=1e-3, log_every=100)
     torch.cuda.synchronize()
     t_train = time.perf_counter() - t0
-    _, loss_trained = net.gradients(Xh, Th, Dh)
+    _, loss_trained = net.gradients(Xh[:bt], Th[:bt], Dh[:bt])
     params = net.get_params()
-    # network kernel timings: one training step on a batch of 32 pairs, one 512^2 inference
-    st = torch.cuda.current_stream()
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    xb, tb, db = X[:32].contiguous(), T[:32].contiguous(), D[:32].contiguous()
-    for _ in range(3):
-        net.train_step(xb, tb, db, lr=1e-12, want_loss=False)
-    ev0.record(st)
-    for _ in range(20):
-        net.train_step(xb, tb, db, lr=1e-12, want_loss=False)
-    ev1.record(st)
-    torch.cuda.synchronize()
-    t_step_ms = ev0.elapsed_time(ev1) / 20
-    for _ in range(3):
-        net.forward(xb, tb)
-    ev0.record(st)
-    for _ in range(20):
-        net.forward(xb, tb)
-    ev1.record(st)
-    torch.cuda.synchronize()
-    t_fwd32_ms = ev0.elapsed_time(ev1) / 20
-    del X, T, D, xb, tb, db
+    del X, T, D, Xh, Th, Dh
     torch.cuda.empty_cache()
-    # evaluation on the 512^2 / 720-view Poisson workload
+    out = {"training": {"pairs": n_problems * iters_train, "images": f"{N}x{N}, {V} views", "data_s": t_data,
+                        "train_s": t_train, "epochs": epochs, "batch": bt,
+                        "heldout_loss_untrained": loss_untrained, "heldout_loss_trained": loss_trained,
+                        "loss_history": hist}}
     G, b_host = make_problem(0, dev)
     b = torch.tensor(b_host, device=dev)
-    net512 = S.CNN(WL["N"], WL["N"], max_batch=1, seed=11)
-    net512.set_params(params)
-    untrained512 = S.CNN(WL["N"], WL["N"], max_batch=1, seed=11)
-    xi = torch.rand(WL["N"], WL["N"], device=dev)
-    ti = torch.randn(WL["N"], WL["N"], device=dev)
-    for _ in range(3):
-        net512.forward(xi, ti)
-    ev0.record(st)
-    for _ in range(20):
-        net512.forward(xi, ti)
-    ev1.record(st)
-    torch.cuda.synchronize()
-    t_fwd512_ms = ev0.elapsed_time(ev1) / 20
+    nets = {}
+    for name in ("trained", "untrained"):
+        nn = S.CNN(N, N, max_batch=batch_problems, seed=11)
+        if name == "trained":
+            nn.set_params(params)
+        nets[name] = nn
+        with ClockSampler(dev.index or 0) as clk:
+            r = Lr.time_to_equal(G, b, nn, iters=steps, device=dev, warmup=warmup)
+        r["clocks"] = clk.summary()
+        out[name] = r
+    # the batched learned form over held-out problems of the same acquisition
+    geoms, bs = [], []
+    for c in range(batch_problems):
+        Gc, bc = Lr.make_problem(S, synth, N, V, 4950 + c, dev, noise="poisson")
+        geoms.append(Gc)
+        bs.append(bc)
+    with ClockSampler(dev.index or 0) as clk:
+        rb = Lr.batched_time_to_equal(geoms, bs, nets["trained"], iters=steps, device=dev, warmup=warmup)
+    rb["clocks"] = clk.summary()
+    out["batched_trained"] = rb
+    if timings:
+        st = torch.cuda.current_stream()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        xi = torch.rand(N, N, device=dev)
+        ti = torch.randn(N, N, device=dev)
+        nn = nets["trained"]
+        for _ in range(3):
+            nn.forward(xi, ti)
+        ev0.record(st)
+        for _ in range(20):
+            nn.forward(xi, ti)
+        ev1.record(st)
+        torch.cuda.synchronize()
+        xb = xi.expand(batch_problems, N, N).contiguous()
+        tb = ti.expand(batch_problems, N, N).contiguous()
+        t1 = ev0.elapsed_time(ev1) / 20
+        for _ in range(3):
+            nn.forward(xb, tb)
+        ev0.record(st)
+        for _ in range(20):
+            nn.forward(xb, tb)
+        ev1.record(st)
+        torch.cuda.synchronize()
+        tB = ev0.elapsed_time(ev1) / 20
+        for _ in range(3):
+            nn.train_step(xb, tb, tb, lr=1e-12, want_loss=False)
+        ev0.record(st)
+        for _ in range(10):
+            nn.train_step(xb, tb, tb, lr=1e-12, want_loss=False)
+        ev1.record(st)
+        torch.cuda.synchronize()
+        out["network_ms"] = {"inference_1x512x512": t1, f"inference_{batch_problems}x512x512": tB,
+                             f"train_step_{batch_problems}x512x512": ev0.elapsed_time(ev1) / 10,
+                             "flop_per_pixel_inference": 57024}
+    for g in geoms:
+        g.close()
+    out["params"] = params
+    return out
+
+
+def run_learned(args, dev):
+    import numpy as np
     warm = max(3, args.warmup)
-    res = Lr.time_to_equal(G, b, net512, iters=args.steps, device=dev, warmup=warm)
-    res_u = Lr.time_to_equal(G, b, untrained512, iters=args.steps, device=dev, warmup=warm)
+    r = learned_comparison(dev, args.steps, warm, n_problems=400, iters_train=50, epochs=2, timings=True)
+    params = r.pop("params")
     line = {
-        "metric": "time-to-equal (residual, TV): learned vs plain SupPCG", "value": res["speedup"],
+        "metric": "time-to-equal (residual, TV): learned vs plain SupPCG", "value": r["trained"]["speedup"],
         "unit": "x (plain time / learned time)", "n_gpus": 1, "steps": args.steps, "warmup": warm,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 (network bf16)",
         "data": "synthetic",
         "config": {"workload": "learned_512x512_720views_725bins_poisson1e5", "K": 40, "a": 1 - 1e-5,
-                   "gamma": 1e-2, "mu": 1e-5, "rho": 0.8, "train_pairs": 20000, "train_images": "128x128",
-                   "epochs": 2, "batch": 32},
-        "trained": res, "untrained_network": res_u,
-        "training": {"data_s": t_data, "train_s": t_train, "heldout_loss_untrained": loss_untrained,
-                     "heldout_loss_trained": loss_trained, "loss_history": hist},
-        "network_ms": {"inference_1x512x512": t_fwd512_ms, "inference_32x128x128": t_fwd32_ms,
-                       "train_step_32x128x128": t_step_ms},
+                   "gamma": 1e-2, "mu": 1e-5, "rho": 0.8, "train_pairs": 20000, "train_images": "512x512",
+                   "epochs": 2, "batch": 16},
     }
+    line.update(r)
     print(json.dumps(line), flush=True)
     if args.save_params:
         np.save(args.save_params, params)
@@ -747,6 +792,9 @@ def main():
     tte = None
     if rank == 0 and world == 1 and not args.no_time_to_equal:
         tte = {"batched_vs_sequential": batched_comparison(args.steps, args.warmup, dev)}
+        lc = learned_comparison(dev, args.steps, args.warmup, n_problems=64, iters_train=16, epochs=1)
+        lc.pop("params")
+        tte["learned_vs_plain"] = lc
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -21,10 +21,12 @@ import numpy as np
 TABLE1 = dict(K=40, a=1 - 1e-5, gamma=1e-2, mu=1e-5, rho=0.8)   # SupPCG row of Table 1
 
 
-def make_problem(S, synth, N, V, seed, device, noise="gaussian", level=0.01, I0=1e5, n_ell=15):
-    """Geometry and data b of one random-ellipse problem (the projector gives the clean data)."""
+def make_problem(S, synth, N, V, seed, device, noise="gaussian", level=0.01, I0=1e5, n_ell=15, G=None):
+    """Geometry (a new one unless G is given) and data b of one random-ellipse
+    problem (the projector gives the clean data)."""
     import torch
-    G = S.Geometry(N, n_views=V, n_bins=int(math.ceil(1.42 * N)))
+    if G is None:
+        G = S.Geometry(N, n_views=V, n_bins=int(math.ceil(1.42 * N)))
     x = synth.ellipse_phantom(N, n_ell, seed)
     clean = G.project(torch.tensor(x, dtype=torch.float32, device=device)).double().cpu().numpy()
     if noise == "poisson":
@@ -45,8 +47,9 @@ def make_training_set(n_problems, N=128, V=180, iters=50, seed0=4000, device="cu
     T = torch.empty_like(X)
     D = torch.empty_like(X)
     q = 0
+    G = S.Geometry(N, n_views=V, n_bins=int(math.ceil(1.42 * N)))   # one acquisition, many phantoms
     for c in range(n_problems):
-        G, b = make_problem(S, synth, N, V, seed0 + c, device)
+        G, b = make_problem(S, synth, N, V, seed0 + c, device, G=G)
         _, rep, log, trace = G.solve_trace(b, max_iter=iters, **kw)
         assert rep["status"] == 0, rep
         ell_in = [0] + [int(v) for v in log[:-1, 3].cpu().numpy()]
@@ -60,7 +63,7 @@ def make_training_set(n_problems, N=128, V=180, iters=50, seed0=4000, device="cu
             T[q].copy_(tb)
             D[q].copy_(y).sub_(xk)
             q += 1
-        G.close()
+    G.close()
     return X, T, D
 
 
@@ -93,13 +96,13 @@ def time_to_equal(G, b, net, iters=100, params=TABLE1, device="cuda", warmup=3):
     import paper_1807_10151_gb300 as S
     kw = dict(params)
     st = torch.cuda.current_stream()
-    # warm both graph paths
+    # each timed solve follows an untimed one of the same kind: a solve keeps one captured
+    # graph, re-captured when the kind (plain / learned, logged or not) changes
     G.solve(b, max_iter=warmup, **kw)
-    G.solve_learned(net, b, max_iter=warmup, **kw)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(st)
-    xp, rp, lp = G.solve(b, max_iter=iters, log=True, **kw)
+    xp, rp, _ = G.solve(b, max_iter=iters, **kw)
     e1.record(st)
     torch.cuda.synchronize()
     t_plain = e0.elapsed_time(e1) / 1000.0
@@ -115,6 +118,8 @@ def time_to_equal(G, b, net, iters=100, params=TABLE1, device="cuda", warmup=3):
         k_hit = int(hit[0]) + 1 if hit.size else None
         if k_hit is None:
             return None, None
+        G.solve_learned(net, b, max_iter=warmup, **kw)
+        torch.cuda.synchronize()
         e0.record(st)
         G.solve_learned(net, b, max_iter=k_hit, **kw)
         e1.record(st)
@@ -130,3 +135,61 @@ def time_to_equal(G, b, net, iters=100, params=TABLE1, device="cuda", warmup=3):
             "speedup_1pct": (t_plain / t_learned1) if t_learned1 else None,
             "learned_accepted": rl_all["n_learned"], "learned_fallbacks": rl_all["n_fallback"],
             "learned_f_last": rl_all["f_last"], "learned_tv_last": rl_all["tv_last"]}
+
+
+def batched_time_to_equal(geoms, bs, net, iters=100, params=TABLE1, device="cuda", warmup=3):
+    """The learned direction in the batched schedule against plain SupPCG on the
+    same problems.  Plain SupPCG (batched; the same iterates as one at a time)
+    for `iters` iterations sets every problem's target (f*, TV*); each
+    problem's first iteration with f <= f* and TV <= TV* under the learned
+    direction comes from its single learned solve's log (the batched learned
+    solve gives the same iterates bit for bit); the batched learned solve is
+    then timed for the largest of those iterations, so that every problem of
+    the batch has reached its target.  Returns a dict of the measurements."""
+    import torch
+    import paper_1807_10151_gb300 as S
+    kw = dict(params)
+    st = torch.cuda.current_stream()
+    xs = [torch.zeros(g.ny, g.nx, device=device) for g in geoms]
+    for g, b in zip(geoms, bs):
+        g.solve(b, max_iter=warmup, **kw)
+    S.solve_batched(geoms, bs, xs, max_iter=warmup, **kw)   # (each timed solve follows one of its kind)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+    for x in xs:
+        x.zero_()
+    ev[0].record(st)
+    reps = S.solve_batched(geoms, bs, xs, max_iter=iters, **kw)
+    ev[1].record(st)
+    ev[2].record(st)
+    for g, b in zip(geoms, bs):
+        g.solve(b, max_iter=iters, **kw)
+    ev[3].record(st)
+    torch.cuda.synchronize()
+    t_batched, t_seq = ev[0].elapsed_time(ev[1]) / 1000.0, ev[2].elapsed_time(ev[3]) / 1000.0
+    hits, accepted = [], []
+    for g, b, r in zip(geoms, bs, reps):
+        _, rl, ll = g.solve_learned(net, b, max_iter=4 * iters, log=True, **kw)
+        ll = ll.cpu().numpy()
+        hit = np.nonzero((ll[:, 0] <= r["f_last"]) & (ll[:, 2] <= r["tv_last"]))[0]
+        hits.append(int(hit[0]) + 1 if hit.size else None)
+        accepted.append(rl["n_learned"])
+    if any(h is None for h in hits):
+        return {"problems": len(geoms), "plain_iters": iters, "learned_hits": hits, "reached": False}
+    k_hit = max(hits)
+    S.solve_batched_learned(geoms, net, bs, xs, max_iter=warmup, **kw)
+    for x in xs:
+        x.zero_()
+    torch.cuda.synchronize()
+    ev[4].record(st)
+    lrep = S.solve_batched_learned(geoms, net, bs, xs, max_iter=k_hit, **kw)
+    ev[5].record(st)
+    torch.cuda.synchronize()
+    t_learned = ev[4].elapsed_time(ev[5]) / 1000.0
+    assert all(r["status"] == 0 for r in lrep), lrep
+    # (a problem's f and TV need not stay below its target after its first hit: TV grows as
+    # CG fits the data, so the batch's last iterate is not the criterion, the first hit is)
+    return {"problems": len(geoms), "plain_iters": iters, "learned_iters": k_hit, "learned_hits": hits,
+            "plain_batched_s": t_batched, "plain_sequential_s": t_seq, "learned_batched_s": t_learned,
+            "speedup_vs_plain_batched": t_batched / t_learned, "speedup_vs_plain_sequential": t_seq / t_learned,
+            "accepted_proposals": accepted}
