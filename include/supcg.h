@@ -79,6 +79,18 @@ int supcg_create_geometry(int nx, int ny, double pixel_size, int n_views, const 
 int supcg_set_tiling(supcg_geometry g, int fwd_bins_per_block);
 int supcg_get_tiling(supcg_geometry g, int *fwd_bins_per_block);
 
+/* Tiling of the backprojector: thread blocks per 32 x 32 pixel tile (1 .. 8,
+ * default 4), each summing a contiguous share of the views, combined per
+ * pixel in a fixed order by the tile's last block.  More parts give a grid of
+ * more, shorter blocks (a smaller idle tail when the last wave is partial) at
+ * the cost of more partial sums.  The choice changes the order in which a
+ * pixel's views are added, so results differ from one setting to another in
+ * the last bits (each setting is deterministic and stays the exact transpose
+ * of supcg_project).  Setting it frees the geometry's scratch.  Used by the
+ * autotuner.  Errors: SUPCG_ERR_ARG. */
+int supcg_set_bwd_parts(supcg_geometry g, int parts);
+int supcg_get_bwd_parts(supcg_geometry g, int *parts);
+
 /* Free the geometry and all scratch it owns (synchronises the device first). */
 int supcg_destroy_geometry(supcg_geometry g);
 

@@ -32,7 +32,8 @@ EXPORTED = ["supcg_create_geometry", "supcg_destroy_geometry", "supcg_project", 
             "supcg_cnn_get_params", "supcg_cnn_set_params", "supcg_cnn_forward", "supcg_cnn_gradients",
             "supcg_cnn_train_step", "supcg_solve_trace", "supcg_solve_learned", "supcg_set_tiling",
             "supcg_get_tiling", "supcg_solve_sweep", "supcg_art", "supcg_set_wait_limit",
-            "supcg_set_barrier_shortfall", "supcg_solve_batched_learned"]
+            "supcg_set_barrier_shortfall", "supcg_solve_batched_learned", "supcg_set_bwd_parts",
+            "supcg_get_bwd_parts"]
 KINDS = ["forward", "backward", "fft", "stv", "vector", "cnn"]
 
 _lock = threading.Lock()
@@ -128,6 +129,8 @@ def load(allow_build: bool = True):
         L.supcg_solve_batched_learned.argtypes = [C.POINTER(vp), vp, C.POINTER(vp), C.POINTER(vp), i,
                                                   C.POINTER(Params), C.POINTER(Report), vp]
         L.supcg_set_tiling.argtypes = [vp, i]
+        L.supcg_set_bwd_parts.argtypes = [vp, i]
+        L.supcg_get_bwd_parts.argtypes = [vp, C.POINTER(i)]
         L.supcg_get_tiling.argtypes = [vp, C.POINTER(i)]
         L.supcg_set_wait_limit.argtypes = [ll]
         L.supcg_set_barrier_shortfall.argtypes = [i]
@@ -290,6 +293,15 @@ class Geometry:
     def get_tiling(self):
         v = C.c_int()
         _check(load().supcg_get_tiling(self.handle, C.byref(v)), "supcg_get_tiling")
+        return v.value
+
+    def set_bwd_parts(self, parts):
+        """Backprojector view parts per pixel tile (supcg_set_bwd_parts); returns the status."""
+        return load().supcg_set_bwd_parts(self.handle, int(parts))
+
+    def get_bwd_parts(self):
+        v = C.c_int()
+        _check(load().supcg_get_bwd_parts(self.handle, C.byref(v)), "supcg_get_bwd_parts")
         return v.value
 
     @property

@@ -59,3 +59,38 @@ def tune(G, reps=5, cache=DEFAULT_CACHE, force=False):
     with open(cache, "w") as f:
         json.dump(db, f, indent=1, sort_keys=True)
     return rec
+
+
+BWD_CANDIDATES = (2, 3, 4, 5, 6, 8)
+
+
+def tune_bwd(G, b, iters=4, reps=2, cache=DEFAULT_CACHE, force=False):
+    """Choose and apply the backprojector's view parts per pixel tile for G by
+    timing the backprojections of short profiled solves on data b (the solve's
+    two-sinogram pass is what the setting serves); cached per geometry bucket.
+    Unlike the forward tile, the setting changes the order of each pixel's sums
+    (so the last bits of results).  Returns {"parts": p, "us": {...}}."""
+    db = _load(cache)
+    key = bucket(G) + "_bwd"
+    if key in db and not force:
+        G.set_bwd_parts(db[key]["parts"])
+        return db[key]
+    times = {}
+    for p in BWD_CANDIDATES:
+        if G.set_bwd_parts(p) != 0:
+            continue
+        G.solve_profiled(b, max_iter=1, graph=False)      # builds the workspace for this setting
+        best = float("inf")
+        for _ in range(reps):
+            _, _, kinds = G.solve_profiled(b, max_iter=iters, graph=False)
+            ms, n = kinds["backward"]
+            best = min(best, ms / max(n, 1))
+        times[p] = best * 1000.0
+    best = min(times, key=times.get)
+    G.set_bwd_parts(best)
+    rec = {"parts": best, "us": {str(k): v for k, v in times.items()}}
+    db[key] = rec
+    os.makedirs(os.path.dirname(cache), exist_ok=True)
+    with open(cache, "w") as f:
+        json.dump(db, f, indent=1, sort_keys=True)
+    return rec

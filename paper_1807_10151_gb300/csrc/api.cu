@@ -86,6 +86,7 @@ enum { KT_FWD, KT_BWD, KT_BWD2, KT_VEC, KT_TR, KT_ROWS, KT_COLS, KT_SINO, KT_STV
 struct Workspace {
     int count = 0;
     std::vector<supcg_geometry> geoms;
+    std::vector<unsigned> versions;   // the geometries' layout versions when this was built
     std::vector<Prob> hp;
     Prob *dp = nullptr;
     int *dprefix = nullptr;     // KT_COUNT x (count + 1)
@@ -154,6 +155,8 @@ struct supcg_geometry_s {
     Workspace *ws_solve = nullptr;  // single-problem solve
     Workspace *ws_batch = nullptr;  // batched solve owned by this (first) geometry
     std::vector<supcg_geometry> batch_key;
+    int bparts = kBwdViewParts;     // backprojector: view parts per pixel tile
+    unsigned layout_version = 0;    // changed with the tiling: workspaces built before are stale
 };
 
 // Forward projector box width: the inner indices that one warp's 64 rays can
@@ -424,11 +427,33 @@ extern "C" int supcg_set_tiling(supcg_geometry g, int fwd_bins_per_block)
     g->ntu = (g->U + g->BU - 1) / g->BU;
     int rc = upload_block_order(g);
     if (rc) return rc;
-    // workspaces hold launch shapes and TMA boxes of the old tiling
+    // workspaces hold launch shapes and TMA boxes of the old tiling (a batched workspace owned
+    // by another geometry sees the version change)
     free_ws(g->ws_ops);
     free_ws(g->ws_solve);
     free_ws(g->ws_batch);
     g->ops_batch = 0;
+    ++g->layout_version;
+    return SUPCG_OK;
+}
+
+extern "C" int supcg_set_bwd_parts(supcg_geometry g, int parts)
+{
+    if (!g || parts < 1 || parts > kBwdMaxParts) return SUPCG_ERR_ARG;
+    cudaDeviceSynchronize();
+    g->bparts = parts;
+    free_ws(g->ws_ops);
+    free_ws(g->ws_solve);
+    free_ws(g->ws_batch);
+    g->ops_batch = 0;
+    ++g->layout_version;
+    return SUPCG_OK;
+}
+
+extern "C" int supcg_get_bwd_parts(supcg_geometry g, int *parts)
+{
+    if (!g || !parts) return SUPCG_ERR_ARG;
+    *parts = g->bparts;
     return SUPCG_OK;
 }
 
@@ -466,6 +491,7 @@ static int ws_create(const std::vector<supcg_geometry> &gs, Workspace **out)
     if (!w) return SUPCG_ERR_NOMEM;
     w->count = (int)gs.size();
     w->geoms = gs;
+    for (const supcg_geometry g : gs) w->versions.push_back(g->layout_version);
     w->hp.resize(w->count);
     int dev = 0, nsm = 0, per_sm = 0;
     cudaGetDevice(&dev);
@@ -482,8 +508,8 @@ static int ws_create(const std::vector<supcg_geometry> &gs, Workspace **out)
     for (int c = 0; c < w->count; ++c) {
         const supcg_geometry g = gs[c];
         nb[KT_FWD][c] = (g->nfw + 1) / 2;
-        nb[KT_BWD][c] = backward_blocks(g->nx, g->ny, 0);
-        nb[KT_BWD2][c] = backward_blocks(g->nx, g->ny, 1);
+        nb[KT_BWD][c] = backward_blocks(g->nx, g->ny, 0, g->bparts);
+        nb[KT_BWD2][c] = backward_blocks(g->nx, g->ny, 1, g->bparts);
         nb[KT_VEC][c] = (int)(((long long)g->ny * g->nxp + 1023) / 1024);
         nb[KT_TR][c] = ((g->ny + 31) / 32) * ((g->nx + 31) / 32);
         // FFT: enough blocks to fill the device, each a few row pairs / stored columns
@@ -549,7 +575,7 @@ static int ws_create(const std::vector<supcg_geometry> &gs, Workspace **out)
         const size_t sizes[] = {img * 4, imgT * 4, img * 4, imgT * 4, img * 4, img * 4, img * 4, img * 4,
                                 sino * 4, sino * 4, sino * 4, (size_t)g->ny * g->nx * 16, sizeof(Scal),
                                 npart * 8, 16 * 4, 4 * 4, (size_t)(g->ny / 2 + 1) * (g->nx / 2 + 1) * 8,
-                                2 * (size_t)kBwdViewParts * img * 8,
+                                2 * (size_t)g->bparts * img * 8,
                                 (size_t)std::max(nb[KT_BWD][c], nb[KT_BWD2][c]) * 4, img * 4, img * 4};
         size_t total = 0;
         for (size_t s : sizes) total += al(s);
@@ -566,6 +592,7 @@ static int ws_create(const std::vector<supcg_geometry> &gs, Workspace **out)
         P.C = (double2 *)ptrs[11]; P.sc = (Scal *)ptrs[12]; P.partial = (double *)ptrs[13];
         P.counter = (unsigned *)ptrs[14]; P.bar = (unsigned *)ptrs[15]; P.Dtab = (float2 *)ptrs[16];
         P.bsplit = (float2 *)ptrs[17]; P.tilecnt = (unsigned *)ptrs[18]; P.xlo = (float *)ptrs[19];
+        P.bparts = g->bparts;
         P.glo = (float *)ptrs[20];
         P.border = g->dborder;
         P.nx = g->nx; P.ny = g->ny; P.V = g->V; P.U = g->U;
@@ -620,6 +647,17 @@ int supcg::func_attrs_once(const void *func, int max_dyn_smem, int carveout)
 // Bounded grid barriers: polls before giving up, and the test hook's extra blocks.
 static std::atomic<long long> g_wait_limit{kSpinLimit};
 static std::atomic<int> g_bar_extra{0};
+
+// The batched workspace of `owner` serves `key` if it was built for these geometries
+// at their current layout versions.
+static bool batch_ws_current(supcg_geometry owner, const std::vector<supcg_geometry> &key)
+{
+    const Workspace *w = owner->ws_batch;
+    if (!w || owner->batch_key != key) return false;
+    for (size_t c = 0; c < key.size(); ++c)
+        if (w->versions[c] != key[c]->layout_version) return false;
+    return true;
+}
 
 static int ws_upload(Workspace *w, cudaStream_t st)
 {
@@ -1208,7 +1246,7 @@ extern "C" int supcg_solve_batched(const supcg_geometry *gs, const float *const 
     if (rc) return rc;
     supcg_geometry owner = gs[0];
     std::vector<supcg_geometry> key(gs, gs + count);
-    if (!owner->ws_batch || owner->batch_key != key) {
+    if (!batch_ws_current(owner, key)) {
         free_ws(owner->ws_batch);
         if ((rc = ws_create(key, &owner->ws_batch))) return rc;
         owner->batch_key = key;
@@ -1233,7 +1271,7 @@ extern "C" int supcg_solve_batched_learned(const supcg_geometry *gs, supcg_cnn_s
     if (rc) return rc;
     supcg_geometry owner = gs[0];
     std::vector<supcg_geometry> key(gs, gs + count);
-    if (!owner->ws_batch || owner->batch_key != key) {
+    if (!batch_ws_current(owner, key)) {
         free_ws(owner->ws_batch);
         if ((rc = ws_create(key, &owner->ws_batch))) return rc;
         owner->batch_key = key;
@@ -1274,7 +1312,7 @@ extern "C" int supcg_solve_sweep(supcg_geometry g, const float *d_b, float *cons
             return SUPCG_ERR_ARG;
     }
     std::vector<supcg_geometry> key(count, g);
-    if (!g->ws_batch || g->batch_key != key) {
+    if (!batch_ws_current(g, key)) {
         free_ws(g->ws_batch);
         int rc = ws_create(key, &g->ws_batch);
         if (rc) return rc;

@@ -17,7 +17,8 @@ constexpr int kMaxStages = 24;       // FFT stages (radices) per length
 constexpr int kMaxRadix = 64;        // largest prime factor handled by the generic butterfly
 constexpr int kRowsPerChunk = 16;    // forward projector: image rows staged per TMA box
 constexpr int kBwdTileI = 32;        // backprojector pixel tile (rows)
-constexpr int kBwdViewParts = 4;     // backprojector: blocks per tile, each taking a quarter of the view chunks
+constexpr int kBwdViewParts = 4;     // backprojector: default blocks per tile (view parts), each a share of the view chunks
+constexpr int kBwdMaxParts = 8;      // backprojector: most view parts per tile (supcg_set_bwd_parts)
 constexpr int kBwdTileJ = 32;        // backprojector pixel tile (columns)
 constexpr int kBwdViewChunk = 32;    // backprojector: views staged per shared-memory chunk
 constexpr int kRedThreads = 256;     // block size of the reduction / vector kernels
@@ -231,7 +232,8 @@ struct Prob {
     float *r, *q, *bpad;
     double2 *C;            // FFT scratch [ny][nx] (FP64 complex)
     float2 *Dtab;          // h(w_r) / (nx ny) at (min(k1, ny-k1), min(k2, nx-k2)), double-float: [ny/2+1][nx/2+1]
-    float2 *bsplit;        // backprojector: each sinogram's and view part's pixel sums, double-float [2][kBwdViewParts][ny][nxp]
+    float2 *bsplit;        // backprojector: each sinogram's and view part's pixel sums, double-float [2][bparts][ny][nxp]
+    int bparts;            // backprojector: blocks per pixel tile, each taking a contiguous share of the view chunks
     double *art_u;         // ART: auxiliary value u_i per ray [V][U]
     double *art_rn;        // ART: 1 / (1 + r^2 ||R_i||^2) per ray [V][U]
     unsigned *tilecnt;     // backprojector: parts finished per tile (reset by the last one)
@@ -503,7 +505,7 @@ int launch_backward2(const Launch &L, int bwin);   // g from r and h from q in o
 int art_max_blocks(int *out);                                           // co-resident blocks of k_art
 int launch_art_init(const Prob *d_prob, double r, int blocks, cudaStream_t st);
 int launch_art(const Prob *d_prob, int cycles, double r, double lam, int S, int blocks, cudaStream_t st);
-int backward_blocks(int nx, int ny, int dual);
+int backward_blocks(int nx, int ny, int dual, int parts);
 int encode_tiled(CUtensorMap *m, CUtensorMapDataType type, int rank, void *base, const cuuint64_t *dims,
                  const cuuint64_t *strides_bytes, const cuuint32_t *box);
 int launch_transpose(const Launch &L, int which);          // x -> x^T (which 0) or p -> p^T (which 1)

@@ -16,8 +16,8 @@
 // columns nearest to its centre; each is weighted by the shared trapezoid.
 //
 // Backward (pixel-driven, gather over bins, no atomics).  A tile of 32 x 32
-// pixels is shared by kBwdViewParts blocks, each taking a contiguous part of
-// the view chunks; for chunks of 32 views the bins that the tile projects
+// pixels is shared by P.bparts blocks (the geometry's view parts, 1 .. 8),
+// each taking a contiguous part of the view chunks; for chunks of 32 views the bins that the tile projects
 // onto are staged in shared memory with 16-byte vector loads; every pixel
 // gathers the two (three) bins nearest to its projected centre with the same
 // weight evaluated on the same FP32 operands as the forward kernel.  The last
@@ -582,7 +582,8 @@ __global__ void __launch_bounds__(kBwdThreads, DUAL ? 2 : 3) k_backward(const Pr
     const int tiles_j = (P.nx + kBwdTileJ - 1) / kBwdTileJ;
     // part-major: every tile's first part, then its second, ...; the last part has the
     // fewest view chunks, so the grid's final (partial) wave holds the shortest blocks
-    const int ntiles_p = (prefix[pi + 1] - prefix[pi]) / kBwdViewParts;
+    const int parts = P.bparts;
+    const int ntiles_p = (prefix[pi + 1] - prefix[pi]) / parts;
     const int vpart = local / ntiles_p, tile = local - vpart * ntiles_p;   // this block's part of the views
     const int ti = tile / tiles_j, tj = tile - ti * tiles_j;
     const int i0 = ti * TI, j0 = tj * kBwdTileJ;
@@ -671,7 +672,7 @@ __global__ void __launch_bounds__(kBwdThreads, DUAL ? 2 : 3) k_backward(const Pr
         }
     };
 
-    const int per_part = (nchunks + kBwdViewParts - 1) / kBwdViewParts;
+    const int per_part = (nchunks + parts - 1) / parts;
     const int c_begin = min(nchunks, vpart * per_part), c_end = min(nchunks, c_begin + per_part);
     if (c_begin < c_end) stage(c_begin);
     __syncthreads();
@@ -757,12 +758,12 @@ __global__ void __launch_bounds__(kBwdThreads, DUAL ? 2 : 3) k_backward(const Pr
                 if (i < P.ny && j < P.nx) {
                     const float2 o2 = comb[(s * PX + e) * kBwdGroup + tg];
                     const df v = df_add(df{part[s * PX + e], -comp[s * PX + e]}, df{o2.x, o2.y});
-                    P.bsplit[(size_t)(s * kBwdViewParts + vpart) * img + (size_t)i * P.nxp + j] = make_float2(v.h, v.l);
+                    P.bsplit[(size_t)(s * parts + vpart) * img + (size_t)i * P.nxp + j] = make_float2(v.h, v.l);
                 }
             }
     if (t == 0 && bad_sh && P.sc) atomicExch(&P.sc->status, (int)SUPCG_ERR_UNSUPPORTED);
     __shared__ int last_sh;
-    if (!last_block(&P.tilecnt[tile], kBwdViewParts, &last_sh)) return;
+    if (!last_block(&P.tilecnt[tile], parts, &last_sh)) return;
     // output s: the gradient (g from r) or h from q
     const bool is_g[2] = {DUAL || mode != BWD_H, false};
     float *outs[2] = {(!DUAL && mode == BWD_H) ? P.h : P.g, P.h};
@@ -782,12 +783,14 @@ __global__ void __launch_bounds__(kBwdThreads, DUAL ? 2 : 3) k_backward(const Pr
                 const int i = i0 + ly + kBwdRowStep * e;
                 if (i < P.ny && j < P.nx) {
                     const size_t o = (size_t)i * P.nxp + j;
-                    float2 pv[kBwdViewParts];   // the other blocks' sums: read past L1
+                    float2 pv[kBwdMaxParts];   // the other blocks' sums: read past L1
 #pragma unroll
-                    for (int h = 0; h < kBwdViewParts; ++h) pv[h] = __ldcg(P.bsplit + (size_t)(s * kBwdViewParts + h) * img + o);
+                    for (int h = 0; h < kBwdMaxParts; ++h)
+                        if (h < parts) pv[h] = __ldcg(P.bsplit + (size_t)(s * parts + h) * img + o);
                     df vs = {0.0f, 0.0f};
 #pragma unroll
-                    for (int h = 0; h < kBwdViewParts; ++h) vs = df_add(vs, df{pv[h].x, pv[h].y});
+                    for (int h = 0; h < kBwdMaxParts; ++h)
+                        if (h < parts) vs = df_add(vs, df{pv[h].x, pv[h].y});
                     if (bayes) {
                         double v = (double)vs.h + (double)vs.l;
                         if (is_g[s]) {
@@ -821,7 +824,7 @@ __global__ void __launch_bounds__(kBwdThreads, DUAL ? 2 : 3) k_backward(const Pr
     // ||x - mu_X||^2, and SE = sqrt(sum over S)
     const double bs = block_sum<kBwdThreads>(sx, red);
     const double be = block_sum<kBwdThreads>(sse, red);
-    const int ntiles = (prefix[pi + 1] - prefix[pi]) / kBwdViewParts;
+    const int ntiles = (prefix[pi + 1] - prefix[pi]) / parts;
     if (t == 0) {
         P.partial[tile] = bs;
         P.partial[ntiles + tile] = be;
@@ -841,11 +844,11 @@ __global__ void __launch_bounds__(kBwdThreads, DUAL ? 2 : 3) k_backward(const Pr
     }
 }
 
-// Blocks per problem: kBwdViewParts per pixel tile.
-int backward_blocks(int nx, int ny, int dual)
+// Blocks per problem: `parts` per pixel tile.
+int backward_blocks(int nx, int ny, int dual, int parts)
 {
     const int ti = dual ? BwdShape<true>::TI : BwdShape<false>::TI;
-    return kBwdViewParts * ((ny + ti - 1) / ti) * ((nx + kBwdTileJ - 1) / kBwdTileJ);
+    return parts * ((ny + ti - 1) / ti) * ((nx + kBwdTileJ - 1) / kBwdTileJ);
 }
 
 int launch_backward(const Launch &L, int mode, int bwin)

@@ -80,10 +80,13 @@ def test_bin_size_limits():
         assert e.value.code == -8
 
 
-def test_backprojector_is_exact_transpose_bitwise():
-    """Entries of R read from forward columns equal entries read from backward rows, bit for bit."""
+@pytest.mark.parametrize("parts", [1, 2, 3, 4, 5, 8])
+def test_backprojector_is_exact_transpose_bitwise(parts):
+    """Entries of R read from forward columns equal entries read from backward rows,
+    bit for bit, for every split of the views among a tile's blocks."""
     og = O.Geometry(24, ny=20, V=13, U=33, off=0.004)
     G = gpu_geometry(og)
+    assert G.set_bwd_parts(parts) == 0 and G.get_bwd_parts() == parts
     pix = [(0, 0), (7, 11), (19, 23), (10, 3)]
     rays = [(0, 16), (3, 5), (6, 20), (12, 31), (9, 0)]
     cols = {}
@@ -322,6 +325,47 @@ def test_solve_large_config_properties():
     assert est == pytest.approx(rep["f_last"], rel=0.15)
 
 
+@pytest.mark.parametrize("parts", [1, 3, 6, 8])
+def test_backprojector_parts_match_oracle(parts):
+    """Any view split gives the oracle's R^T y (the sums' order changes, not the terms),
+    in the solve's two-sinogram pass too (a short SupPCG run stays on the oracle's path)."""
+    og = O.Geometry(130, ny=96, V=77, U=181, off=-0.02)
+    R = O.CSR(og)
+    G = gpu_geometry(og)
+    assert G.set_bwd_parts(parts) == 0
+    y = f32(np.random.default_rng(parts).standard_normal((og.V, og.U)))
+    assert rel_l2(G.backproject(to_dev(y)).double().cpu().numpy(), R.backproject(y)) <= 1e-5
+    og2, R2, x_true, b = config1_problem(seed=1007, N=48, V=60, U=70)
+    G2 = gpu_geometry(og2)
+    assert G2.set_bwd_parts(parts) == 0
+    kw = dict(K=1, a=0.995, gamma=0.5, mu=1e-5, rho=0.8, max_iter=10)
+    ref = O.suppcg(R2, f32(b), **kw)
+    x, rep, _ = G2.solve(to_dev(f32(b)), **kw)
+    assert rep["status"] == 0 and rep["ell"] == ref["ell"]
+    assert rel_l2(x.double().cpu().numpy(), ref["x_half"]) <= 1e-4
+    assert G2.set_bwd_parts(0) == -1 and G2.set_bwd_parts(9) == -1
+
+
+def test_batched_workspace_follows_a_changed_tiling():
+    """A batched solve after one of its geometries changed its tiling rebuilds the
+    batch's scratch (launch shapes, block order) instead of reusing it."""
+    import paper_1807_10151_gb300 as S
+    geoms, bs = [], []
+    for c, (N, V, U) in enumerate(((64, 90, 95), (48, 60, 70))):
+        og, R, x_true, b = config1_problem(seed=1300 + c, N=N, V=V, U=U)
+        geoms.append(gpu_geometry(og))
+        bs.append(to_dev(f32(b)))
+    kw = dict(K=1, a=0.995, gamma=0.5, max_iter=6)
+    xs = [torch.zeros(g.ny, g.nx, device="cuda") for g in geoms]
+    S.solve_batched(geoms, bs, xs, **kw)
+    assert geoms[1].set_tiling(32) == 0 and geoms[1].set_bwd_parts(3) == 0
+    xs2 = [torch.zeros(g.ny, g.nx, device="cuda") for g in geoms]
+    S.solve_batched(geoms, bs, xs2, **kw)
+    for g, b, x in zip(geoms, bs, xs2):     # each problem as solved alone with its current tiling
+        xr, _, _ = g.solve(b, **kw)
+        np.testing.assert_array_equal(x.cpu().numpy(), xr.cpu().numpy())
+
+
 def test_forward_tiles_give_identical_results_and_autotuner_picks_one(tmp_path):
     from paper_1807_10151_gb300 import autotune
     og = O.Geometry(160, V=120, U=228)
@@ -336,3 +380,7 @@ def test_forward_tiles_give_identical_results_and_autotuner_picks_one(tmp_path):
     rec = autotune.tune(G, reps=2, cache=str(tmp_path / "tiling.json"))
     assert rec["tile"] in (128, 96, 64, 32) and G.get_tiling() == rec["tile"]
     assert autotune.tune(G, cache=str(tmp_path / "tiling.json")) == rec      # cached
+    b = to_dev(np.random.default_rng(13).standard_normal((og.V, og.U)))
+    rb = autotune.tune_bwd(G, b, iters=2, reps=1, cache=str(tmp_path / "tiling.json"))
+    assert rb["parts"] in autotune.BWD_CANDIDATES and G.get_bwd_parts() == rb["parts"]
+    assert autotune.tune_bwd(G, b, cache=str(tmp_path / "tiling.json")) == rb
