@@ -94,6 +94,7 @@ struct Workspace {
     int smem_rows = 0, smem_cols = 0;
     int bwin = 0;
     int bw_max = 0;
+    int bparts = 0;             // view parts of every problem's backprojector, 0 if they differ
     std::vector<void *> allocs;
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t body_exec = nullptr;
@@ -114,6 +115,7 @@ struct Workspace {
         l.prefix = dprefix + kt * (count + 1);
         l.blocks = blocks[kt];
         l.bw_max = bw_max;
+        l.bparts = bparts;
         l.st = st;
         return l;
     }
@@ -593,6 +595,7 @@ static int ws_create(const std::vector<supcg_geometry> &gs, Workspace **out)
         P.counter = (unsigned *)ptrs[14]; P.bar = (unsigned *)ptrs[15]; P.Dtab = (float2 *)ptrs[16];
         P.bsplit = (float2 *)ptrs[17]; P.tilecnt = (unsigned *)ptrs[18]; P.xlo = (float *)ptrs[19];
         P.bparts = g->bparts;
+        w->bparts = (c == 0 || w->bparts == g->bparts) ? g->bparts : 0;
         P.glo = (float *)ptrs[20];
         P.border = g->dborder;
         P.nx = g->nx; P.ny = g->ny; P.V = g->V; P.U = g->U;

@@ -135,8 +135,7 @@ __global__ void __launch_bounds__(256) k_pupdate(const Prob *__restrict__ probs,
     const int pi = find_problem(prefix, count, blockIdx.x, &local);
     const Prob &P = probs[pi];
     if (P.sc->done) return;
-    const double beta_d = P.sc->init ? 0.0 : P.sc->beta;
-    const float beta = (float)beta_d;
+    const float beta = P.sc->init ? 0.0f : P.sc->beta_f;
     const float *z = P.precond ? P.z : P.g;   // M = I: z = g
     const int tiles_j = (P.nx + 31) / 32;
     const int ti = local / tiles_j, tj = local - ti * tiles_j;
@@ -173,8 +172,8 @@ __global__ void __launch_bounds__(256) k_pupdate(const Prob *__restrict__ probs,
         const int j = tj * 32 + r, i = ti * 32 + tx;
         if (j < P.nx && i < P.ny) P.pT[(size_t)j * P.nyp + i] = sh[tx][r];
     }
-    const double bs = block_sum<256>(df_to_double(s), red);
-    const double bp = block_sum<256>(df_to_double(spp), red);
+    const double bs = block_sum_df<256>(s, red);
+    const double bp = block_sum_df<256>(spp, red);
     const int nblk = prefix[pi + 1] - prefix[pi];
     if (threadIdx.x == 0) {
         P.partial[local] = bs;
@@ -186,7 +185,10 @@ __global__ void __launch_bounds__(256) k_pupdate(const Prob *__restrict__ probs,
         if (threadIdx.x == 0) {
             P.sc->gtp = tot_s;
             P.sc->pp = tot_p;
-            P.sc->beta = beta_d;
+            if (P.sc->init) {   // steps 2-7 of Algorithm 3: beta = 0
+                P.sc->beta = 0.0;
+                P.sc->beta_f = 0.0f;
+            }
             P.counter[1] = 0;
         }
     }
@@ -251,7 +253,7 @@ __global__ void __launch_bounds__(kRedThreads) k_beta(const Prob *__restrict__ p
     for (size_t e = (size_t)local * kVecPerBlock + threadIdx.x; e < tot && e < (size_t)(local + 1) * kVecPerBlock;
          e += kRedThreads)
         df_acc_prod(s, z[e], P.h[e]);
-    const double bs = block_sum<kRedThreads>(df_to_double(s), red);
+    const double bs = block_sum_df<kRedThreads>(s, red);
     if (threadIdx.x == 0) P.partial[local] = bs;
     const int nblk = prefix[pi + 1] - prefix[pi];
     if (last_block(&P.counter[2], nblk, &flag)) {
@@ -266,6 +268,7 @@ __global__ void __launch_bounds__(kRedThreads) k_beta(const Prob *__restrict__ p
                 if (!isfinite(b)) atomicExch(&sc->status, (int)SUPCG_ERR_BREAKDOWN);
                 sc->beta = isfinite(b) ? b : 0.0;
             }
+            sc->beta_f = (float)sc->beta;
             P.counter[2] = 0;
         }
     }
@@ -299,8 +302,7 @@ __global__ void __launch_bounds__(kRedThreads) k_xupdate(const Prob *__restrict_
         if (local == 0 && threadIdx.x == 0) sc->done = 2;   // 2: set during this launch
         return;
     }
-    const float al = (float)sc->alpha;
-    const float al_lo = (float)(sc->alpha - (double)al);   // alpha = al + al_lo to about 2^-48
+    const float al = sc->alpha_h, al_lo = sc->alpha_l;   // alpha = al + al_lo to about 2^-48
     const size_t tot = (size_t)P.ny * P.nxp;   // a multiple of 4: rows are padded to 16 bytes
     float *tr = P.trace ? P.trace + (size_t)sc->k * P.ny * P.nx : nullptr;
     // one float4 of x and of p per thread (kVecPerBlock = 4 x kRedThreads elements per block)

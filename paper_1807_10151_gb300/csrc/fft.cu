@@ -268,7 +268,7 @@ __global__ void __launch_bounds__(256) k_fft_rows(const Prob *__restrict__ probs
             __shared__ double red[40];
             __shared__ int flag;
             const int pi = find_problem(prefix, count, blockIdx.x, &local);
-            const double bs = block_sum<256>(df_to_double(s), red);
+            const double bs = block_sum_df<256>(s, red);
             if (threadIdx.x == 0) P.partial[local] = bs;
             const int nblk = prefix[pi + 1] - prefix[pi];
             if (last_block(&P.counter[2], nblk, &flag)) {
@@ -283,6 +283,7 @@ __global__ void __launch_bounds__(256) k_fft_rows(const Prob *__restrict__ probs
                         if (!isfinite(b)) atomicExch(&sc->status, (int)SUPCG_ERR_BREAKDOWN);
                         sc->beta = isfinite(b) ? b : 0.0;
                     }
+                    sc->beta_f = (float)sc->beta;
                     P.counter[2] = 0;
                 }
             }

@@ -185,7 +185,10 @@ struct Scal {
     int init;          // 1 while running steps 2-7 (beta forced to 0)
     int n_fallback;    // learned perturbation: proposals rejected by the nonascent test
     int n_learned;     // learned perturbation: proposals accepted
-    int pad[2];
+    // alpha as two FP32 parts (alpha_h + alpha_l to ~2^-48) and beta rounded to FP32, written
+    // with alpha and beta, so that the vector kernels read them without FP64 arithmetic
+    float alpha_h, alpha_l, beta_f;
+    int pad[1];
 };
 
 // ----------------------------------------------------------------- problem
@@ -334,6 +337,37 @@ __device__ __forceinline__ double block_sum(double v, double *sh)
     if (w == 0) {
         r = (l < NT / 32) ? sh[l] : 0.0;
         r = warp_sum(r);
+    }
+    __syncthreads();
+    return r;
+}
+
+// Block sum of per-thread double-float values in a fixed order, on the FP32 pipe:
+// shuffles of the pairs and double-float adds, one conversion to FP64 at the end
+// (this part's FP64 pipe is narrow).  Result valid in thread 0; sh holds >= NT/32
+// doubles.
+__device__ __forceinline__ df warp_sum_df(df v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const df w = {__shfl_down_sync(0xffffffffu, v.h, o), __shfl_down_sync(0xffffffffu, v.l, o)};
+        v = df_add(v, w);
+    }
+    return v;
+}
+template <int NT>
+__device__ __forceinline__ double block_sum_df(df v, double *sh)
+{
+    float2 *s2 = reinterpret_cast<float2 *>(sh);
+    v = warp_sum_df(v);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) s2[w] = make_float2(v.h, v.l);
+    __syncthreads();
+    double r = 0.0;
+    if (w == 0) {
+        df u = (l < NT / 32) ? df{s2[l].x, s2[l].y} : df{0.0f, 0.0f};
+        u = warp_sum_df(u);
+        if (l == 0) r = df_to_double(u);
     }
     __syncthreads();
     return r;
@@ -496,6 +530,7 @@ struct Launch {
     const int *prefix;     // device: block prefix for this kernel type, count+1 entries
     int blocks;            // total blocks
     int bw_max;            // widest forward box (floats) among the problems
+    int bparts;            // backprojector view parts shared by every problem, 0 if they differ
     cudaStream_t st;
 };
 

@@ -382,8 +382,8 @@ __global__ void __launch_bounds__(kFwdThreads, 10) k_forward(const Prob *__restr
     }
     if (bad) atomicExch(&bad_sh, 1);
 
-    // epilogue: store, fused residual / norm reduction
-    double s = 0.0;
+    // epilogue: store, fused residual / norm reduction (exact squares, double-float sums)
+    df s = df_make(0.0f);
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
         const int u = q ? uB : uA;
@@ -396,19 +396,19 @@ __global__ void __launch_bounds__(kFwdThreads, 10) k_forward(const Prob *__restr
             const size_t o = (size_t)v * P.Up + u;
             const float rr = (float)(acc[q] - (double)P.bpad[o]);   // r = R x - b, cancellation taken in FP64
             P.r[o] = rr;
-            s += (double)rr * (double)rr;
+            df_acc_prod(s, rr, rr);
         } else {
             const size_t o = (size_t)v * P.Up + u;
             const float qq = (float)acc[q];
             P.q[o] = qq;
-            s += (double)qq * (double)qq;
+            df_acc_prod(s, qq, qq);
         }
     }
     __syncthreads();
     if (t == 0 && bad_sh && P.sc) atomicExch(&P.sc->status, (int)SUPCG_ERR_UNSUPPORTED);
     if (mode == FWD_PLAIN) return;
 
-    const double bs = block_sum<kFwdThreads>(s, red);
+    const double bs = block_sum_df<kFwdThreads>(s, red);
     if (t == 0) P.partial[local] = bs;
     const int nblk = prefix[pi + 1] - prefix[pi];
     if (last_block(&P.counter[0], nblk, &flag)) {
@@ -429,8 +429,11 @@ __global__ void __launch_bounds__(kFwdThreads, 10) k_forward(const Prob *__restr
                 if (!(pth > 0.0) || !isfinite(al)) {
                     atomicExch(&sc->status, (int)SUPCG_ERR_BREAKDOWN);
                     sc->alpha = 0.0;
+                    sc->alpha_h = sc->alpha_l = 0.0f;
                 } else {
                     sc->alpha = al;
+                    sc->alpha_h = (float)al;
+                    sc->alpha_l = (float)(al - (double)sc->alpha_h);
                 }
                 // the end of the pass: after steps 1-9 of Algorithm 3 the loop begins; after a
                 // while-body, unless an error stopped it, its log entry and k <- k + 1 (step 14)
@@ -559,7 +562,9 @@ __device__ __forceinline__ void bwd_view_x2(const ViewP &vp, float pb0, const ui
 // BWD_PLAIN: y = the staged input into g), or, DUAL, over two in one pass:
 // g from r and h from q (h = A p for the beta of the next step of Algorithm 2,
 // deferred to this pass: alpha takes p^T A p from the forward projector's ||q||^2).
-template <bool DUAL>
+// FIXED_PARTS: the view parts per tile when every problem of the launch has that
+// (default) number, so the part arithmetic is compile-time; 0: each problem's own.
+template <bool DUAL, int FIXED_PARTS>
 __global__ void __launch_bounds__(kBwdThreads, DUAL ? 2 : 3) k_backward(const Prob *__restrict__ probs,
                                                           const int *__restrict__ prefix, int count, int mode)
 {
@@ -582,7 +587,7 @@ __global__ void __launch_bounds__(kBwdThreads, DUAL ? 2 : 3) k_backward(const Pr
     const int tiles_j = (P.nx + kBwdTileJ - 1) / kBwdTileJ;
     // part-major: every tile's first part, then its second, ...; the last part has the
     // fewest view chunks, so the grid's final (partial) wave holds the shortest blocks
-    const int parts = P.bparts;
+    const int parts = FIXED_PARTS ? FIXED_PARTS : P.bparts;
     const int ntiles_p = (prefix[pi + 1] - prefix[pi]) / parts;
     const int vpart = local / ntiles_p, tile = local - vpart * ntiles_p;   // this block's part of the views
     const int ti = tile / tiles_j, tj = tile - ti * tiles_j;
@@ -851,24 +856,27 @@ int backward_blocks(int nx, int ny, int dual, int parts)
     return parts * ((ny + ti - 1) / ti) * ((nx + kBwdTileJ - 1) / kBwdTileJ);
 }
 
-int launch_backward(const Launch &L, int mode, int bwin)
+template <bool DUAL, int FP>
+static int launch_bwd(const Launch &L, int mode, int bwin)
 {
-    int rc = func_attrs_once((const void *)k_backward<false>, 2 * kBwdViewChunk * 256 * 4);
+    const int smem = 2 * (DUAL ? 2 : 1) * kBwdViewChunk * bwin * 4;
+    int rc = func_attrs_once((const void *)k_backward<DUAL, FP>, 2 * (DUAL ? 2 : 1) * kBwdViewChunk * 256 * 4);
     if (rc) return rc;
-    k_backward<false><<<L.blocks, kBwdThreads, 2 * kBwdViewChunk * bwin * 4, L.st>>>(L.probs, L.prefix, L.count,
-                                                                                     mode);
+    k_backward<DUAL, FP><<<L.blocks, kBwdThreads, smem, L.st>>>(L.probs, L.prefix, L.count, mode);
     SUPCG_CUDA_TRY(cudaGetLastError());
     return SUPCG_OK;
 }
 
+int launch_backward(const Launch &L, int mode, int bwin)
+{
+    return L.bparts == kBwdViewParts ? launch_bwd<false, kBwdViewParts>(L, mode, bwin)
+                                     : launch_bwd<false, 0>(L, mode, bwin);
+}
+
 int launch_backward2(const Launch &L, int bwin)
 {
-    int rc = func_attrs_once((const void *)k_backward<true>, 2 * 2 * kBwdViewChunk * 256 * 4);
-    if (rc) return rc;
-    k_backward<true><<<L.blocks, kBwdThreads, 2 * 2 * kBwdViewChunk * bwin * 4, L.st>>>(L.probs, L.prefix, L.count,
-                                                                                       BWD_G);
-    SUPCG_CUDA_TRY(cudaGetLastError());
-    return SUPCG_OK;
+    return L.bparts == kBwdViewParts ? launch_bwd<true, kBwdViewParts>(L, BWD_G, bwin)
+                                     : launch_bwd<true, 0>(L, BWD_G, bwin);
 }
 
 } // namespace supcg

@@ -17,17 +17,44 @@ namespace supcg {
 
 constexpr int kTvThreads = 256;
 
-// tbar at pixel (i, j) of y (pitch ld); *Tb receives the root of the TV term
+// The seven values of y (pitch ld) that tbar at pixel (i, j) depends on: the pixel,
+// its lower and right neighbours, the upper row's pixel and its right neighbour,
+// the left pixel and its lower neighbour (0 where the term they belong to does not
+// exist).  Loading them apart from the arithmetic lets a thread issue the loads of
+// several pixels before it waits for any.
+struct Nb7 {
+    float c, d, r, u, ur, l, ld;
+};
+__device__ __forceinline__ Nb7 nb7_load(const float *__restrict__ y, int ld, int ny, int nx, int i, int j)
+{
+    Nb7 v = {};
+    const size_t p = (size_t)i * ld + j;
+    v.c = y[p];
+    if (i + 1 < ny && j + 1 < nx) {
+        v.d = y[p + ld];
+        v.r = y[p + 1];
+    }
+    if (i >= 1 && j + 1 < nx) {
+        v.u = y[p - ld];
+        v.ur = y[p - ld + 1];
+    }
+    if (j >= 1 && i + 1 < ny) {
+        v.l = y[p - 1];
+        v.ld = y[p + ld - 1];
+    }
+    return v;
+}
+
+// tbar at pixel (i, j) from its seven values; *Tb receives the root of the TV term
 // whose base is (i, j) (0 if that term does not exist).
-__device__ __forceinline__ float tbar_at(const float *__restrict__ y, int ld, int ny, int nx, int i, int j,
-                                         float *Tb)
+__device__ __forceinline__ float tbar_from(const Nb7 &v, int ny, int nx, int i, int j, float *Tb)
 {
     float g = 0.0f;
     bool undef = false;
     float tb = 0.0f;
-    const float yc = y[(size_t)i * ld + j];
+    const float yc = v.c;
     if (i + 1 < ny && j + 1 < nx) {
-        const float a = yc - y[(size_t)(i + 1) * ld + j], b = yc - y[(size_t)i * ld + j + 1];
+        const float a = yc - v.d, b = yc - v.r;
         if (a == 0.0f && b == 0.0f) undef = true;
         else {
             const float T = sqrtf(a * a + b * b);
@@ -36,20 +63,51 @@ __device__ __forceinline__ float tbar_at(const float *__restrict__ y, int ld, in
         }
     }
     if (i >= 1 && j + 1 < nx) {
-        const float yu = y[(size_t)(i - 1) * ld + j];
-        const float a = yu - yc, b = yu - y[(size_t)(i - 1) * ld + j + 1];
+        const float yu = v.u;
+        const float a = yu - yc, b = yu - v.ur;
         if (a == 0.0f && b == 0.0f) undef = true;
         else g -= a / sqrtf(a * a + b * b);
     }
     if (j >= 1 && i + 1 < ny) {
-        const float yl = y[(size_t)i * ld + j - 1];
-        const float a = yl - y[(size_t)(i + 1) * ld + j - 1], b = yl - yc;
+        const float yl = v.l;
+        const float a = yl - v.ld, b = yl - yc;
         if (a == 0.0f && b == 0.0f) undef = true;
         else g -= b / sqrtf(a * a + b * b);
     }
     *Tb = tb;
     return undef ? 0.0f : -g;
 }
+
+// tbar at pixel (i, j) of y (pitch ld); *Tb as for tbar_from.
+__device__ __forceinline__ float tbar_at(const float *__restrict__ y, int ld, int ny, int nx, int i, int j,
+                                         float *Tb)
+{
+    return tbar_from(nb7_load(y, ld, ny, nx, i, j), ny, nx, i, j, Tb);
+}
+
+// A thread's pixels e0, e0 + stride, ... of an ny x nx image as (i, j), stepped
+// without a division per pixel; S_TV's passes take them kStvGroup at a time, all
+// of a group's loads issued before its arithmetic.
+constexpr int kStvGroup = 2;
+struct PixWalk {
+    int i, j, si, sj, nx;
+    __device__ PixWalk(int e0, int stride, int nx_) : nx(nx_)
+    {
+        i = e0 / nx;
+        j = e0 - i * nx;
+        si = stride / nx;
+        sj = stride - si * nx;
+    }
+    __device__ __forceinline__ void next()
+    {
+        j += sj;
+        i += si;
+        if (j >= nx) {
+            j -= nx;
+            ++i;
+        }
+    }
+};
 
 // Root of the TV term based at (i, j) of y~ = y + c tbar (term must exist).
 __device__ __forceinline__ float trial_term(const float *__restrict__ y, const float *__restrict__ t, int ld,
@@ -100,8 +158,8 @@ __global__ void __launch_bounds__(kTvThreads) k_tv_tbar(const Prob *__restrict__
         df_acc(s_tv, Tb);
         df_acc_prod(s_nn, tb, tb);
     }
-    const double btv = block_sum<kTvThreads>(df_to_double(s_tv), red);
-    const double bnn = block_sum<kTvThreads>(df_to_double(s_nn), red);
+    const double btv = block_sum_df<kTvThreads>(s_tv, red);
+    const double bnn = block_sum_df<kTvThreads>(s_nn, red);
     if (threadIdx.x == 0) {
         P.partial[local] = btv;
         P.partial[nblk + local] = bnn;
@@ -124,11 +182,23 @@ int launch_tv_tbar(const Launch &L)
     return SUPCG_OK;
 }
 
-// Sum of the block partials of one phase, identical in every block.
+// Sum of the block partials of one phase, identical in every block (per-thread values
+// in FP64 or as double-float pairs).
+__device__ __forceinline__ double phase_sum_of(const Prob &P, int nb, int slot, int local, double bs, double *red,
+                                               int *flag, bool *ok);
+__device__ __forceinline__ double phase_sum(const Prob &P, int nb, int slot, int local, df v, double *red,
+                                            int *flag, bool *ok)
+{
+    return phase_sum_of(P, nb, slot, local, block_sum_df<kTvThreads>(v, red), red, flag, ok);
+}
 __device__ __forceinline__ double phase_sum(const Prob &P, int nb, int slot, int local, double v, double *red,
                                             int *flag, bool *ok)
 {
-    const double bs = block_sum<kTvThreads>(v, red);
+    return phase_sum_of(P, nb, slot, local, block_sum<kTvThreads>(v, red), red, flag, ok);
+}
+__device__ __forceinline__ double phase_sum_of(const Prob &P, int nb, int slot, int local, double bs, double *red,
+                                               int *flag, bool *ok)
+{
     if (threadIdx.x == 0) P.partial[(size_t)slot * nb + local] = bs;
     *ok = coop_barrier(P.bar, nb + P.bar_extra, &P.sc->status, flag, P.wait_limit);
     if (!*ok) return 0.0;
@@ -285,19 +355,32 @@ __global__ void __launch_bounds__(kTvThreads, 3) k_stv(const Prob *__restrict__ 
     for (int step = 0; plain && step < K && ok; ++step) {
         // t in the nonascending set at y (Sec. 3.1)
         df d_tv = df_make(0.0f), d_nn = df_make(0.0f);   // double-float sums, FP64 per thread
-        for (int e = e0; e < n; e += stride) {
-            const int i = e / nx, j = e - i * nx;
-            float Tb;
-            const float t = tbar_at(x, ld, ny, nx, i, j, &Tb);
-            tb[(size_t)i * ld + j] = t;
-            df_acc(d_tv, Tb);
-            df_acc_prod(d_nn, t, t);
+        for (PixWalk w(e0, stride, nx); w.i < ny;) {
+            int gi[kStvGroup], gj[kStvGroup];
+            Nb7 v[kStvGroup];
+#pragma unroll
+            for (int q = 0; q < kStvGroup; ++q) {
+                gi[q] = w.i;
+                gj[q] = w.j;
+                if (w.i < ny) v[q] = nb7_load(x, ld, ny, nx, w.i, w.j);
+                w.next();
+            }
+#pragma unroll
+            for (int q = 0; q < kStvGroup; ++q) {
+                if (gi[q] < ny) {
+                    float Tb;
+                    const float t = tbar_from(v[q], ny, nx, gi[q], gj[q], &Tb);
+                    tb[(size_t)gi[q] * ld + gj[q]] = t;
+                    df_acc(d_tv, Tb);
+                    df_acc_prod(d_nn, t, t);
+                }
+            }
         }
         double s_tv, s_nn;
         // two sums through one barrier: slots 2*slot and 2*slot+1
         {
-            const double b1 = block_sum<kTvThreads>(df_to_double(d_tv), red);
-            const double b2 = block_sum<kTvThreads>(df_to_double(d_nn), red);
+            const double b1 = block_sum_df<kTvThreads>(d_tv, red);
+            const double b2 = block_sum_df<kTvThreads>(d_nn, red);
             if (threadIdx.x == 0) {
                 P.partial[(size_t)(4 + 2 * slot) * nb + local] = b1;
                 P.partial[(size_t)(5 + 2 * slot) * nb + local] = b2;
@@ -328,11 +411,35 @@ __global__ void __launch_bounds__(kTvThreads, 3) k_stv(const Prob *__restrict__ 
             ++ell;
             ++trials;
             df s = df_make(0.0f);
-            for (int e = e0; e < n; e += stride) {
-                const int i = e / nx, j = e - i * nx;
-                if (i + 1 < ny && j + 1 < nx) df_acc(s, trial_term(x, tb, ld, i, j, c));
+            for (PixWalk w(e0, stride, nx); w.i < ny;) {
+                float yv[kStvGroup][3], tv[kStvGroup][3];
+                bool in[kStvGroup];
+#pragma unroll
+                for (int q = 0; q < kStvGroup; ++q) {
+                    in[q] = w.i + 1 < ny && w.j + 1 < nx;
+                    if (in[q]) {
+                        const size_t p = (size_t)w.i * ld + w.j;
+                        yv[q][0] = x[p];
+                        yv[q][1] = x[p + ld];
+                        yv[q][2] = x[p + 1];
+                        tv[q][0] = tb[p];
+                        tv[q][1] = tb[p + ld];
+                        tv[q][2] = tb[p + 1];
+                    }
+                    w.next();
+                }
+#pragma unroll
+                for (int q = 0; q < kStvGroup; ++q) {
+                    if (in[q]) {   // the root of the TV term of y~ = y + c tbar based at the pixel
+                        const float yc = __fmaf_rn(c, tv[q][0], yv[q][0]);
+                        const float yd = __fmaf_rn(c, tv[q][1], yv[q][1]);
+                        const float yr = __fmaf_rn(c, tv[q][2], yv[q][2]);
+                        const float a1 = yc - yd, b1 = yc - yr;
+                        df_acc(s, sqrtf(a1 * a1 + b1 * b1));
+                    }
+                }
             }
-            tv_t = phase_sum(P, nb, slot, local, df_to_double(s), red, &flag, &ok);
+            tv_t = phase_sum(P, nb, slot, local, s, red, &flag, &ok);
             slot ^= 1;
             if (!ok) break;
             if (tv_t <= tv_y) break;   // until TV(y~) <= TV(y)
@@ -366,10 +473,18 @@ __global__ void __launch_bounds__(kTvThreads, 3) k_stv(const Prob *__restrict__ 
             }
             xt_done = true;
         } else {
-            for (int e = e0; e < n; e += stride) {   // y <- y~
-                const int i = e / nx, j = e - i * nx;
-                const size_t p = (size_t)i * ld + j;
-                (void)x_step(x, xl, p, c, tb[p]);
+            for (PixWalk w(e0, stride, nx); w.i < ny;) {   // y <- y~
+                size_t gp[kStvGroup];
+                float tv[kStvGroup];
+#pragma unroll
+                for (int q = 0; q < kStvGroup; ++q) {
+                    gp[q] = (w.i < ny) ? (size_t)w.i * ld + w.j : ~(size_t)0;
+                    if (w.i < ny) tv[q] = tb[gp[q]];
+                    w.next();
+                }
+#pragma unroll
+                for (int q = 0; q < kStvGroup; ++q)
+                    if (gp[q] != ~(size_t)0) (void)x_step(x, xl, gp[q], c, tv[q]);
             }
             ok = coop_barrier(P.bar, nb + P.bar_extra, &sc->status, &flag, P.wait_limit);
         }
