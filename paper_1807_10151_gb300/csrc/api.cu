@@ -521,8 +521,8 @@ static int ws_create(const std::vector<supcg_geometry> &gs, Workspace **out)
         nb[KT_ROWS][c] = (npairs + rpb - 1) / rpb;
         nb[KT_COLS][c] = (hx + cw - 1) / cw;
         // (two transform buffers, then the twiddles when at most 2048 of them)
-        w->smem_rows = std::max(w->smem_rows, 2 * rpb * g->nx * 16 + (g->nx <= 2048 ? g->nx * 16 : 0));
-        w->smem_cols = std::max(w->smem_cols, 2 * cw * g->ny * 16 + (g->ny <= 2048 ? g->ny * 16 : 0));
+        w->smem_rows = std::max(w->smem_rows, 2 * rpb * g->nx * 16 + (g->nx <= kFftSmemTw ? g->nx * 16 : 0));
+        w->smem_cols = std::max(w->smem_cols, 2 * cw * g->ny * 16 + (g->ny <= kFftSmemTw ? g->ny * 16 : 0));
         nb[KT_SINO][c] = (int)(((long long)g->V * g->Up + 1023) / 1024);
         npx[c] = (long long)g->nx * g->ny;
         nb[KT_STV][c] = (int)std::max(1LL, std::min<long long>((npx[c] + 1023) / 1024, stv_cap));

@@ -108,9 +108,6 @@ __device__ __forceinline__ dfc twid_df(const float4 *tw, int e, bool inv)
     return inv ? dfc{{w.x, w.y}, {-w.z, -w.w}} : dfc{{w.x, w.y}, {w.z, w.w}};
 }
 
-// Twiddle tables of up to this many entries are copied to shared memory by each block.
-constexpr int kFftSmemTw = 2048;
-
 // The twiddles the block's transforms read: its shared copy (stw, room for
 // kFftSmemTw entries) when the length allows, else the global table.
 __device__ __forceinline__ const float4 *stage_twiddles(const FFTPlan &pl, float4 *stw)

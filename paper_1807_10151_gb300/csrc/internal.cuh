@@ -22,6 +22,9 @@ constexpr int kBwdMaxParts = 8;      // backprojector: most view parts per tile 
 constexpr int kBwdTileJ = 32;        // backprojector pixel tile (columns)
 constexpr int kBwdViewChunk = 32;    // backprojector: views staged per shared-memory chunk
 constexpr int kRedThreads = 256;     // block size of the reduction / vector kernels
+constexpr int kFftSmemTw = 1024;     // preconditioner: twiddle tables up to this length are staged per block
+                                     // (longer ones are read through L1: a 2048-point block then needs 64 KB
+                                     // instead of 96 KB, and three blocks fit on an SM instead of two)
 constexpr long long kSpinLimit = 1ll << 24;  // bounded waits (iterations of a ~100 ns poll); grid barriers: the
                                              // default of supcg_set_wait_limit
 
