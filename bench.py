@@ -9,7 +9,7 @@ Algorithm 3 (S_TV, forward projection with residual, backprojection,
 preconditioner, CG scalars and axpys, forward and back projection of p).
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                  [--workload plain512|batched64|large2048|learned512|sweep243|art512]
+                  [--workload plain512|batched64|large2048|learned512|sweep243|art512|memory2048|network512]
 
 --impl reference times the FP64 CPU oracle on the host cores on the same
 workload (it is the only other implementation of the method here).
@@ -38,6 +38,10 @@ after another.
 lambda = 1e-2; SupART K = 10, a = 1 - 1e-5, gamma = 1e-2, r = 5,
 lambda = 5e-2): cycles/s on the GPU, and one cycle of the FP64 oracle on the
 host cores.
+--workload memory2048: the memory-bound kernels (vector, preconditioner, S_TV)
+of a 2048^2 / 2880-view SupPCG iteration against the HBM peak.
+--workload network512: the network's convolutions (inference, training step)
+at 512^2 against the BF16 tensor peak.
 --workload large2048: 8 slices of 2048^2, 2880 views, 2900 bins (40 ellipses
 on a textured background, Poisson 1e4 photons): FP32- and BF16-stored
 projector pair timed on the batch, errors of both against the FP64 oracle on
@@ -418,17 +422,19 @@ def memory_bound_legs(G, b, N, peak_gbs):
     """Steady-state per-iteration time of the HBM-bound kernels of one SupPCG solve
     on an N x N slice (its working set, images, spectrum and sinograms, exceeds L2):
     the difference of two profiled solves (4 and 12 iterations) removes the one-off
-    staging and steps 1-9.  Algorithmic bytes per iteration (n = N^2):
-      vector: x update (read x, p; write x) 12n + p update (read p, z, g; write p, p^T) 20n;
-      fft: rows (read g 4n, write the half spectrum, 16 B per stored complex), columns
-           (read and write it, read the quarter table of D, 8 B per entry), inverse rows
-           (read it, write z, read h for z^T h);
+    staging and steps 1-9.  Algorithmic bytes per iteration (n = N^2; x and g are
+    double-float pairs, x + xlo and g + glo):
+      vector: x update (read x, xlo, p; write x, xlo) 20n + p update (read p, z, g, glo;
+           write p, p^T) 24n;
+      fft: rows (read g and glo 8n, write the half spectrum, 16 B per stored complex),
+           columns (read and write it, read the quarter table of D, 8 B per entry),
+           inverse rows (read it, write z, read h for z^T h);
       stv (K = 1): tbar pass (read x, write tbar) 8n, every trial (read x, tbar) 8n,
-           last step (read x, tbar; write x, x^T) 16n."""
+           last step (read x, xlo, tbar; write x, xlo, x^T) 24n."""
     n = N * N
     hx = N // 2 + 1
     spec = 16 * hx * N
-    fft_bytes = (4 * n + spec) + (2 * spec + 8 * (N // 2 + 1) * hx) + (spec + 8 * n)
+    fft_bytes = (8 * n + spec) + (2 * spec + 8 * (N // 2 + 1) * hx) + (spec + 8 * n)
     runs = {}
     for it in (4, 12):
         _, rep, kinds = G.solve_profiled(b, **solve_kw(it, graph=False))
@@ -437,8 +443,8 @@ def memory_bound_legs(G, b, N, peak_gbs):
     d_it = 8
     trials = runs[12][0]["ell"] - runs[4][0]["ell"]   # K = 1: l advances once per trial
     out = {}
-    for kind, launches, nbytes in (("vector", 2, 32 * n), ("fft", 3, fft_bytes),
-                                   ("stv", 1, 24 * n + 8 * n * trials / d_it)):
+    for kind, launches, nbytes in (("vector", 2, 44 * n), ("fft", 3, fft_bytes),
+                                   ("stv", 1, 32 * n + 8 * n * trials / d_it)):
         ms = (runs[12][1][kind][0] - runs[4][1][kind][0]) / d_it
         nl = (runs[12][1][kind][1] - runs[4][1][kind][1]) / d_it
         gbs = nbytes / (ms / 1000.0) / 1e9
@@ -473,16 +479,17 @@ def run_large(args, dev):
             G.backproject(Y, out=Z)
         torch.cuda.synchronize()
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-        ev[0].record(st)
-        for _ in range(args.steps):
-            G.project(Xs, out=Y)
-        ev[1].record(st)
-        for _ in range(args.steps):
-            G.backproject(Y, out=Z)
-        ev[2].record(st)
-        torch.cuda.synchronize()
+        with ClockSampler(dev.index or 0) as clk_p:
+            ev[0].record(st)
+            for _ in range(args.steps):
+                G.project(Xs, out=Y)
+            ev[1].record(st)
+            for _ in range(args.steps):
+                G.backproject(Y, out=Z)
+            ev[2].record(st)
+            torch.cuda.synchronize()
         res[storage] = {"project_ms": ev[0].elapsed_time(ev[1]) / args.steps,
-                        "backproject_ms": ev[1].elapsed_time(ev[2]) / args.steps}
+                        "backproject_ms": ev[1].elapsed_time(ev[2]) / args.steps, "clocks": clk_p.summary()}
         if storage == "f32":
             # one slice as a SupPCG problem: Poisson data with 1e4 incident photons per ray
             rng = np.random.default_rng(5200)
@@ -490,9 +497,11 @@ def run_large(args, dev):
             b0 = torch.tensor(-np.log(np.maximum(counts, 1) / 1e4), dtype=torch.float32, device=dev)
             G1 = S.Geometry(N, n_views=V, n_bins=U)
             peaks, peak_src = measured_peaks()
-            mem_legs = memory_bound_legs(G1, b0, N, peaks["hbm_gbs"])
+            with ClockSampler(dev.index or 0) as clk_m:
+                mem_legs = memory_bound_legs(G1, b0, N, peaks["hbm_gbs"])
             mem_legs["hbm_peak_gbs"] = peaks["hbm_gbs"]
             mem_legs["peak_source"] = peak_src
+            mem_legs["clocks"] = clk_m.summary()
             G1.close()
             del b0
         G.close()
@@ -632,6 +641,90 @@ def learned_comparison(dev, steps, warmup, n_problems, iters_train, epochs, batc
     return out
 
 
+def run_memory2048(args, dev):
+    """The kernels of a SupPCG iteration that are bound by memory rather than by
+    instruction issue, on one 2048^2 / 2880-view / 2900-bin slice (Poisson 1e4
+    data from the analytic sinogram of a 40-ellipse phantom), whose working set
+    exceeds L2: per-iteration time, algorithmic bytes and fraction of the HBM
+    peak (memory_bound_legs), with the clock record."""
+    import numpy as np
+    import torch
+    import paper_1807_10151_gb300 as S
+    from paper_1807_10151_gb300 import synth
+    N, V, U = 2048, 2880, 2900
+    clean = synth.ellipse_sinogram(40, 5000, V, U, 1.0 / N)
+    b = torch.tensor(synth.poisson_log(clean, 1e4, 5200), dtype=torch.float32, device=dev)
+    G = S.Geometry(N, n_views=V, n_bins=U)
+    G.solve(b, **solve_kw(2, graph=False))
+    peaks, peak_src = measured_peaks()
+    with ClockSampler(dev.index or 0) as clk:
+        legs = memory_bound_legs(G, b, N, peaks["hbm_gbs"])
+    line = {"metric": "memory-bound kernels of a 2048^2 SupPCG iteration, fraction of HBM peak",
+            "value": legs["vector"]["frac_of_hbm"], "unit": "fraction (vector kernels)", "n_gpus": 1,
+            "steps": 8, "warmup": 2, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "memory_2048x2048_2880views_2900bins_poisson1e4",
+                       "l2": "working set (images, spectrum, sinograms ~0.2 GB) exceeds L2"},
+            "kernels": legs, "hbm_peak_gbs": peaks["hbm_gbs"], "peak_source": peak_src, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    G.close()
+    return 0
+
+
+def run_network512(args, dev):
+    """The learned-direction network's convolutions on the tensor cores at the
+    512^2 evaluation size: inference of 1 and 8 images and one training step
+    (forward, loss, backward, Adam) of 8 images, CUDA events after warm-up,
+    against the measured BF16 peak.  FLOP per pixel of one inference: 2 x 9 x
+    (2 x 32 + 3 x 32 x 32 + 32 x 1) = 57 024 (the real channels; layer 0's
+    storage pads its 2 input channels to 16)."""
+    import torch
+    import paper_1807_10151_gb300 as S
+    N, B = 512, 8
+    net = S.CNN(N, N, max_batch=B, seed=11)
+    p = net.get_params()
+    rng = __import__("numpy").random.default_rng(3)
+    p[:] = 0.05 * rng.standard_normal(p.size).astype(p.dtype)
+    net.set_params(p)
+    st = torch.cuda.current_stream()
+    x = torch.rand(B, N, N, device=dev)
+    t = torch.randn(B, N, N, device=dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = max(args.steps, 5)
+
+    def timed(fn):
+        for _ in range(max(3, args.warmup)):
+            fn()
+        torch.cuda.synchronize()
+        ev0.record(st)
+        for _ in range(reps):
+            fn()
+        ev1.record(st)
+        torch.cuda.synchronize()
+        return ev0.elapsed_time(ev1) / reps
+
+    with ClockSampler(dev.index or 0) as clk:
+        t1 = timed(lambda: net.forward(x[:1], t[:1]))
+        tB = timed(lambda: net.forward(x, t))
+        tT = timed(lambda: net.train_step(x, t, t, lr=1e-12, want_loss=False))
+    flop_px = 57024
+    peaks, peak_src = measured_peaks()
+    peak = peaks.get("bf16_tflops", 1900.0)
+    achieved = B * N * N * flop_px / (tB / 1000.0) / 1e12
+    line = {"metric": "learned-direction network inference throughput (512^2, batch 8)", "value": achieved,
+            "unit": "TFLOP/s", "n_gpus": 1, "steps": reps, "warmup": max(3, args.warmup), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16 (fp32 accumulate)", "data": "synthetic",
+            "config": {"workload": "network_512x512", "layers": "3x3 convs 2->32->32->32->32->1", "batch": B,
+                       "l2": "activations of one layer (16 MB per image) stay L2-resident"},
+            "ms": {"inference_1x512x512": t1, f"inference_{B}x512x512": tB, f"train_step_{B}x512x512": tT},
+            "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "peak_source": peak_src,
+                         "basis": f"{flop_px} FLOP per pixel x {B} x {N}^2 pixels per inference"},
+            "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_learned(args, dev):
     import numpy as np
     warm = max(3, args.warmup)
@@ -686,7 +779,8 @@ def main():
                     help="skip the batched-vs-sequential time-to-equal measurement of the default workload")
     ap.add_argument("--save-params", default=None, help="learned512: write the trained network's parameters here")
     ap.add_argument("--workload", default="plain512",
-                    choices=["plain512", "batched64", "large2048", "learned512", "sweep243", "art512"])
+                    choices=["plain512", "batched64", "large2048", "learned512", "sweep243", "art512", "memory2048",
+                             "network512"])
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     world = env_int("WORLD_SIZE", 1)
@@ -719,6 +813,10 @@ def main():
         return run_sweep(args, dev)
     if args.workload == "art512":
         return run_art(args, dev)
+    if args.workload == "memory2048":
+        return run_memory2048(args, dev)
+    if args.workload == "network512":
+        return run_network512(args, dev)
     G, b_host = make_problem(rank, dev)
     b = torch.tensor(b_host, device=dev)
     from paper_1807_10151_gb300 import autotune, replicas
