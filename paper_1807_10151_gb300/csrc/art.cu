@@ -129,7 +129,7 @@ __global__ void __launch_bounds__(kArtRayThreads) k_art(const Prob *__restrict__
                                                         double lam, int S)
 {
     __shared__ int flag;
-    __shared__ double red[40];
+    __shared__ __align__(16) double red[40];
     __shared__ float sh_rc;
     const Prob &P = probs[0];
     Scal *sc = P.sc;

@@ -129,7 +129,7 @@ __global__ void __launch_bounds__(256) k_pupdate(const Prob *__restrict__ probs,
                                                  int count)
 {
     __shared__ float sh[32][33];
-    __shared__ double red[40];
+    __shared__ __align__(16) double red[40];
     __shared__ int flag;
     int local;
     const int pi = find_problem(prefix, count, blockIdx.x, &local);
@@ -172,8 +172,8 @@ __global__ void __launch_bounds__(256) k_pupdate(const Prob *__restrict__ probs,
         const int j = tj * 32 + r, i = ti * 32 + tx;
         if (j < P.nx && i < P.ny) P.pT[(size_t)j * P.nyp + i] = sh[tx][r];
     }
-    const double bs = block_sum_df<256>(s, red);
-    const double bp = block_sum_df<256>(spp, red);
+    double bs, bp;
+    block_sum_df2<256>(s, spp, red, &bs, &bp);
     const int nblk = prefix[pi + 1] - prefix[pi];
     if (threadIdx.x == 0) {
         P.partial[local] = bs;
@@ -200,7 +200,7 @@ __global__ void __launch_bounds__(256) k_pupdate(const Prob *__restrict__ probs,
 __global__ void __launch_bounds__(kRedThreads) k_gray(const Prob *__restrict__ probs, const int *__restrict__ prefix,
                                                       int count)
 {
-    __shared__ double red[40];
+    __shared__ __align__(16) double red[40];
     __shared__ int flag;
     int local;
     const int pi = find_problem(prefix, count, blockIdx.x, &local);
@@ -241,7 +241,7 @@ int launch_pupdate(const Launch &L)
 __global__ void __launch_bounds__(kRedThreads) k_beta(const Prob *__restrict__ probs,
                                                       const int *__restrict__ prefix, int count)
 {
-    __shared__ double red[40];
+    __shared__ __align__(16) double red[40];
     __shared__ int flag;
     int local;
     const int pi = find_problem(prefix, count, blockIdx.x, &local);

@@ -513,7 +513,7 @@ static int norm_blocks(long long n) { return (int)std::max(1ll, std::min<long lo
 __global__ void __launch_bounds__(256) k_norms(const float *x, const float *tb, long long n, double *part,
                                                unsigned *counter, float *scale)
 {
-    __shared__ double red[40];
+    __shared__ __align__(16) double red[40];
     __shared__ int sh_last;
     const int img = blockIdx.y, blk = blockIdx.x, nblk = gridDim.x;
     const long long per = (n + nblk - 1) / nblk;
@@ -565,7 +565,7 @@ __global__ void k_pack_input(const float *x, const float *tb, const float *scale
 __global__ void __launch_bounds__(256) k_loss(const float *out, const float *target, const float *tscale,
                                               long long n, long long total, __nv_bfloat16 *G5, double *partial)
 {
-    __shared__ double red[40];
+    __shared__ __align__(16) double red[40];
     double s = 0.0;
     const float scale = (float)(2.0 / (double)total);
     for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < total;

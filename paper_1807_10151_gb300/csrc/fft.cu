@@ -262,7 +262,7 @@ __global__ void __launch_bounds__(256) k_fft_rows(const Prob *__restrict__ probs
             }
         }
         if (!standalone) {
-            __shared__ double red[40];
+            __shared__ __align__(16) double red[40];
             __shared__ int flag;
             const int pi = find_problem(prefix, count, blockIdx.x, &local);
             const double bs = block_sum_df<256>(s, red);

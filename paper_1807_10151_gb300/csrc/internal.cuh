@@ -376,6 +376,30 @@ __device__ __forceinline__ double block_sum_df(df v, double *sh)
     return r;
 }
 
+// Two block sums in one pass (one sweep of shuffles, one shared-memory round): the
+// same values as two calls of block_sum_df.  Results valid in thread 0; sh holds
+// >= NT/16 doubles.
+template <int NT>
+__device__ __forceinline__ void block_sum_df2(df a, df b, double *sh, double *ra, double *rb)
+{
+    float4 *s4 = reinterpret_cast<float4 *>(sh);
+    a = warp_sum_df(a);
+    b = warp_sum_df(b);
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) s4[w] = make_float4(a.h, a.l, b.h, b.l);
+    __syncthreads();
+    *ra = *rb = 0.0;
+    if (w == 0) {
+        const float4 v = (l < NT / 32) ? s4[l] : make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        const df ua = warp_sum_df(df{v.x, v.y}), ub = warp_sum_df(df{v.z, v.w});
+        if (l == 0) {
+            *ra = df_to_double(ua);
+            *rb = df_to_double(ub);
+        }
+    }
+    __syncthreads();
+}
+
 // Sum partial[0..n) in a fixed order with the whole block; result in all threads.
 template <int NT>
 __device__ __forceinline__ double block_sum_array(const volatile double *partial, int n, double *sh)

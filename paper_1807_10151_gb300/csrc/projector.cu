@@ -322,7 +322,7 @@ __global__ void __launch_bounds__(kFwdThreads, 10) k_forward(const Prob *__restr
     // proj_dyn: [warp][kFwdBufs][kRowsPerChunk][BW]
     __shared__ __align__(8) uint64_t bars[kFwdBufs * (kFwdThreads / 32)];   // one per staged box
     __shared__ float4 rowtab[kFwdThreads / 32][kRowsPerChunk];             // each warp's row terms
-    __shared__ double red[40];
+    __shared__ __align__(16) double red[40];
     __shared__ int flag;
     __shared__ int bad_sh;
 
@@ -574,7 +574,7 @@ __global__ void __launch_bounds__(kBwdThreads, DUAL ? 2 : 3) k_backward(const Pr
     __shared__ int ulo_sh[2][kBwdViewChunk];
     __shared__ int kind_sh[2][kBwdViewChunk];   // variant: three bins (1) / two bins (2), + 3 if a window check is needed; axis 3
     __shared__ float2 comb[kBwdGroup * NS * PX];   // second group's sums, combined by the first
-    __shared__ double red[40];
+    __shared__ __align__(16) double red[40];
     __shared__ int bad_sh;
 
     int local;

@@ -142,7 +142,7 @@ __device__ __forceinline__ float x_step(float *__restrict__ x, float *__restrict
 __global__ void __launch_bounds__(kTvThreads) k_tv_tbar(const Prob *__restrict__ probs, const int *__restrict__ prefix,
                                                         int count)
 {
-    __shared__ double red[40];
+    __shared__ __align__(16) double red[40];
     __shared__ int flag;
     int local;
     const int pi = find_problem(prefix, count, blockIdx.x, &local);
@@ -158,8 +158,8 @@ __global__ void __launch_bounds__(kTvThreads) k_tv_tbar(const Prob *__restrict__
         df_acc(s_tv, Tb);
         df_acc_prod(s_nn, tb, tb);
     }
-    const double btv = block_sum_df<kTvThreads>(s_tv, red);
-    const double bnn = block_sum_df<kTvThreads>(s_nn, red);
+    double btv, bnn;
+    block_sum_df2<kTvThreads>(s_tv, s_nn, red, &btv, &bnn);
     if (threadIdx.x == 0) {
         P.partial[local] = btv;
         P.partial[nblk + local] = bnn;
@@ -214,7 +214,7 @@ __global__ void __launch_bounds__(kTvThreads, 3) k_stv(const Prob *__restrict__ 
                                                     const float *__restrict__ dir_all)
 {
     const float *dir = dir_all;
-    __shared__ double red[40];
+    __shared__ __align__(16) double red[40];
     __shared__ int flag;
     __shared__ double sh_inv;   // grid-uniform FP64 scalars: computed by thread 0, read by all
     __shared__ float sh_c;
@@ -379,8 +379,8 @@ __global__ void __launch_bounds__(kTvThreads, 3) k_stv(const Prob *__restrict__ 
         double s_tv, s_nn;
         // two sums through one barrier: slots 2*slot and 2*slot+1
         {
-            const double b1 = block_sum_df<kTvThreads>(d_tv, red);
-            const double b2 = block_sum_df<kTvThreads>(d_nn, red);
+            double b1, b2;
+            block_sum_df2<kTvThreads>(d_tv, d_nn, red, &b1, &b2);
             if (threadIdx.x == 0) {
                 P.partial[(size_t)(4 + 2 * slot) * nb + local] = b1;
                 P.partial[(size_t)(5 + 2 * slot) * nb + local] = b2;
