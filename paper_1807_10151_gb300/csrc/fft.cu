@@ -126,9 +126,13 @@ __device__ float4 *fft_smem_df(float4 *a, float4 *b, int nvec, const FFTPlan &pl
 {
     const int n = pl.n;
     const bool pow2 = (n & (n - 1)) == 0;
+    // power-of-two lengths: the host's factorisation is radix 4 while 4 divides, then one
+    // radix 2, so the radices follow from the length (no per-stage read of the plan)
+    const int lg = __ffs(n) - 1, n4 = lg >> 1;
+    const int nst = pow2 ? n4 + (lg & 1) : pl.nst;
     int Ns = 1;
-    for (int s = 0; s < pl.nst; ++s) {
-        const int R = pl.radix[s];
+    for (int s = 0; s < nst; ++s) {
+        const int R = pow2 ? (s < n4 ? 4 : 2) : pl.radix[s];
         const int m = n / R;
         const int stride = n / (Ns * R);
         const int lm = __ffs(m) - 1, lns = __ffs(Ns) - 1;   // log2 m, log2 Ns (power-of-two lengths)

@@ -5,8 +5,10 @@ Bar (the same for both): after 50 while-body executions the returned image
 x_{k-1/2} is within 1e-4 relative L2 of the oracle's, the l sequence is
 identical, the logged f(x_{k+1/2}) and TV(x_{k+1/2}) of every iteration are
 within 1e-4, and the reported final f is the residual of the returned image
-(1e-5) and near the oracle's final f (gpu_cases.F_LAST_REL).  Inputs come from the seeded generators;
-b is formed from the oracle's explicit R and fed identically to both sides.
+(1e-5) and near the oracle's final f (gpu_cases.F_LAST_REL).  Inputs come from
+the seeded generators and are fed identically to both sides: the benchmark's
+own b (analytic line integrals) for its workload, the oracle's explicit R for
+Table 1's case.
 """
 import numpy as np
 import pytest
