@@ -81,7 +81,7 @@ static int fft_factor(int n, int *rad)
 } // namespace supcg
 
 // ------------------------------------------------------------------ objects
-enum { KT_FWD, KT_BWD, KT_BWD2, KT_VEC, KT_TR, KT_ROWS, KT_COLS, KT_SINO, KT_STV, KT_TV, KT_COUNT };
+enum { KT_FWD, KT_FWDA, KT_BWD, KT_BWD2, KT_VEC, KT_TR, KT_ROWS, KT_COLS, KT_SINO, KT_STV, KT_TV, KT_COUNT };
 
 struct Workspace {
     int count = 0;
@@ -95,6 +95,7 @@ struct Workspace {
     int bwin = 0;
     int bw_max = 0;
     int bparts = 0;             // view parts of every problem's backprojector, 0 if they differ
+    int mirror = 0;             // 1: some problem has mirror pairs of views
     std::vector<void *> allocs;
     cudaStream_t cap_stream = nullptr;
     cudaGraphExec_t body_exec = nullptr;
@@ -116,6 +117,7 @@ struct Workspace {
         l.blocks = blocks[kt];
         l.bw_max = bw_max;
         l.bparts = bparts;
+        l.mirror = mirror;
         l.st = st;
         return l;
     }
@@ -141,13 +143,22 @@ struct supcg_geometry_s {
     int nA, nB;
     int BU, BW, ntu;
     int nfw = 0;                    // forward warp items (see upload_block_order)
+    int nfw_all = 0;                // the same when every view has its own items
     int nxp, nyp, Up;
     float cx, cy, uc, uc_hi, uc_lo;
     int bwin;
     FFTPlan fx, fy;
     ViewP *dviews = nullptr;
     int *dvlist = nullptr;
+    // mirror pairs of views: views v and w = mirror[v] with cos_w = -cos_v and sin_w = sin_v
+    // (theta and pi - theta).  Ray u of w meets pixel (i, nx-1-j) with the weight ray u of v
+    // gives pixel (i, j), so the forward projector evaluates the weights once for both.
+    // mirror[v] = w for the pair's first view (cos > 0), -2 for its second, -1 unpaired.
+    std::vector<int> mirror;
+    int *dmirror = nullptr;         // device copy: the partner of a pair's first view, else -1
+    int npairs = 0;
     int *dborder = nullptr;         // forward warp items in launch order, at most V x ceil(U / 32)
+    int *dborder_all = nullptr;     // the same with every view's items (no mirror pairing)
     float *host_db = nullptr, *host_dx = nullptr;   // supcg_solve_host's device copies of b and x (first use)
     double *art_u = nullptr, *art_rn = nullptr;     // ART's per-ray values (first use)
     int art_S = 1;                                  // ART: bin spacing of rays with disjoint pixels
@@ -179,8 +190,9 @@ static int fwd_box_width(const supcg_geometry_s *g)
 // grid starts the long blocks first and ends on short ones; with one block per
 // (view, tile) a block lasted as long as its slower warp and a view's long central
 // tiles could start last.  Entry: (vidx * ntu + tile) * 2 + half, vidx indexing the
-// class-A-then-class-B view list.
-static int upload_block_order(supcg_geometry_s *g)
+// class-A-then-class-B view list.  PAIRED: the second view of a mirror pair has no
+// items (its rays are summed by its first view's items); else every view has its own.
+static std::vector<int> block_order(const supcg_geometry_s *g, bool pair)
 {
     const int nv = g->V, ntu = g->ntu;
     const double uc = 0.5 * (g->U - 1) - g->off / g->ds;
@@ -188,7 +200,10 @@ static int upload_block_order(supcg_geometry_s *g)
     std::vector<double> cost;
     ord.reserve((size_t)nv * ntu * 2);
     for (int vi = 0; vi < nv; ++vi) {
-        const ViewP &vp = g->views[g->vlist[vi]];
+        const int v = g->vlist[vi];
+        if (pair && g->mirror[v] == -2) continue;   // the second view of a pair: projected with the first
+        const bool paired = pair && g->mirror[v] >= 0;
+        const ViewP &vp = g->views[v];
         const bool classB = vi >= g->nA;
         const int n_outer = classB ? g->nx : g->ny, n_inner = classB ? g->ny : g->nx;
         const double L = -(double)vp.hwq - 1.0, H = (double)n_inner + vp.hwq;
@@ -216,7 +231,8 @@ static int upload_block_order(supcg_geometry_s *g)
                 // per row: the packed path with two candidates; three candidates near the
                 // diagonal cost half as much again, and axis-aligned views take the scalar path
                 // (the warp's two rays one after the other)
-                const double per_row = (vp.flags & kViewAxis) ? 2.0 : ((vp.flags & kViewFwd3) ? 1.5 : 1.0);
+                const double per_row = ((vp.flags & kViewAxis) ? 2.0 : ((vp.flags & kViewFwd3) ? 1.5 : 1.0)) *
+                                       (paired ? 1.3 : 1.0);   // a pair: one more load and sum per candidate
                 ord.push_back((vi * ntu + t) * 2 + half);
                 cost.push_back(16.0 + per_row * (double)std::max(0, hi - lo + 1));
             }
@@ -227,8 +243,24 @@ static int upload_block_order(supcg_geometry_s *g)
     std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) { return cost[x] > cost[y]; });
     std::vector<int> sorted(ord.size());
     for (size_t i = 0; i < idx.size(); ++i) sorted[i] = ord[idx[i]];
-    g->nfw = (int)sorted.size();
-    SUPCG_CUDA_TRY(cudaMemcpy(g->dborder, sorted.data(), sizeof(int) * sorted.size(), cudaMemcpyHostToDevice));
+    return sorted;
+}
+
+// The forward projector's two item lists: with mirror pairs (the paired kernel) and
+// with every view (the residual pass, which projects x + xlo view by view).
+static int upload_block_order(supcg_geometry_s *g)
+{
+    const std::vector<int> all = block_order(g, false);
+    g->nfw_all = (int)all.size();
+    SUPCG_CUDA_TRY(cudaMemcpy(g->dborder_all, all.data(), sizeof(int) * all.size(), cudaMemcpyHostToDevice));
+    if (g->npairs == 0) {
+        g->nfw = g->nfw_all;
+        SUPCG_CUDA_TRY(cudaMemcpy(g->dborder, all.data(), sizeof(int) * all.size(), cudaMemcpyHostToDevice));
+        return SUPCG_OK;
+    }
+    const std::vector<int> paired = block_order(g, true);
+    g->nfw = (int)paired.size();
+    SUPCG_CUDA_TRY(cudaMemcpy(g->dborder, paired.data(), sizeof(int) * paired.size(), cudaMemcpyHostToDevice));
     return SUPCG_OK;
 }
 
@@ -289,6 +321,35 @@ extern "C" int supcg_create_geometry(int nx, int ny, double pixel_size, int n_vi
         g->theta[v] = angles ? angles[v] : (double)v * M_PI / (double)n_views;
         if (!isfinite(g->theta[v])) { delete g; return SUPCG_ERR_ARG; }
     }
+    // cos and sin of every view (exact on the axes), then the mirror pairs: a view with cos > 0
+    // and one with cos < 0 whose cos and sin agree up to sign within 1e-12 (for V angles
+    // v pi / V, v and V - v).  The second view's cos is set to exactly minus the first's, so
+    // that both views' per-view constants are exact negatives (the geometry moves by ~1e-16).
+    std::vector<double> vcos(n_views), vsin(n_views);
+    for (int v = 0; v < n_views; ++v) exact_cos_sin(g->theta[v], &vcos[v], &vsin[v]);
+    g->mirror.assign(n_views, -1);
+    {
+        std::vector<int> neg;
+        for (int v = 0; v < n_views; ++v)
+            if (vcos[v] < 0.0 && vsin[v] != 0.0) neg.push_back(v);
+        std::sort(neg.begin(), neg.end(), [&](int x, int y) { return vsin[x] < vsin[y]; });
+        for (int v = 0; v < n_views; ++v) {
+            if (!(vcos[v] > 0.0) || vsin[v] == 0.0) continue;
+            auto it = std::lower_bound(neg.begin(), neg.end(), vsin[v] - 1e-12,
+                                       [&](int w, double val) { return vsin[w] < val; });
+            for (; it != neg.end() && vsin[*it] <= vsin[v] + 1e-12; ++it) {
+                const int w = *it;
+                if (g->mirror[w] == -1 && fabs(vcos[w] + vcos[v]) <= 1e-12) {
+                    g->mirror[v] = w;
+                    g->mirror[w] = -2;
+                    vcos[w] = -vcos[v];
+                    vsin[w] = vsin[v];
+                    ++g->npairs;
+                    break;
+                }
+            }
+        }
+    }
     const double r = g->d / g->ds;
     const double cx = 0.5 * (nx - 1), cy = 0.5 * (ny - 1);
     const double uc = 0.5 * (n_bins - 1) - g->off / g->ds;
@@ -310,8 +371,7 @@ extern "C" int supcg_create_geometry(int nx, int ny, double pixel_size, int n_vi
     double maxE = 0.0, span_bwd = 0.0, max_small = fabs((double)g->uc_lo);
     double mcl = 0.0, msl = 0.0;
     for (int v = 0; v < n_views; ++v) {
-        double c, s;
-        exact_cos_sin(g->theta[v], &c, &s);
+        const double c = vcos[v], s = vsin[v];
         const double ac = fabs(c), as = fabs(s);
         const double a = std::max(ac, as), b = std::min(ac, as);
         ViewP vp = {};
@@ -399,13 +459,18 @@ extern "C" int supcg_create_geometry(int nx, int ny, double pixel_size, int n_vi
     g->fy.tw = nullptr;
     g->fx.twf = g->dtwx;
     g->fy.twf = g->dtwy;
+    std::vector<int> dm(n_views);
+    for (int v = 0; v < n_views; ++v) dm[v] = g->mirror[v] >= 0 ? g->mirror[v] : -1;
     if (cudaMalloc(&g->dviews, sizeof(ViewP) * n_views) != cudaSuccess ||
+        cudaMalloc(&g->dmirror, sizeof(int) * n_views) != cudaSuccess ||
         cudaMalloc(&g->dvlist, sizeof(int) * n_views) != cudaSuccess ||
-        cudaMalloc(&g->dborder, sizeof(int) * (size_t)n_views * ((n_bins + 31) / 32)) != cudaSuccess) {
+        cudaMalloc(&g->dborder, sizeof(int) * (size_t)n_views * ((n_bins + 31) / 32)) != cudaSuccess ||
+        cudaMalloc(&g->dborder_all, sizeof(int) * (size_t)n_views * ((n_bins + 31) / 32)) != cudaSuccess) {
         supcg_destroy_geometry(g);
         return SUPCG_ERR_NOMEM;
     }
     if (cudaMemcpy(g->dviews, g->views.data(), sizeof(ViewP) * n_views, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(g->dmirror, dm.data(), sizeof(int) * n_views, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(g->dvlist, g->vlist.data(), sizeof(int) * n_views, cudaMemcpyHostToDevice) != cudaSuccess) {
         supcg_destroy_geometry(g);
         return SUPCG_ERR_CUDA;
@@ -475,7 +540,9 @@ extern "C" int supcg_destroy_geometry(supcg_geometry g)
     free_ws(g->ws_batch);
     if (g->dviews) cudaFree(g->dviews);
     if (g->dvlist) cudaFree(g->dvlist);
+    if (g->dmirror) cudaFree(g->dmirror);
     if (g->dborder) cudaFree(g->dborder);
+    if (g->dborder_all) cudaFree(g->dborder_all);
     if (g->host_db) cudaFree(g->host_db);
     if (g->host_dx) cudaFree(g->host_dx);
     if (g->art_u) cudaFree(g->art_u);
@@ -510,6 +577,7 @@ static int ws_create(const std::vector<supcg_geometry> &gs, Workspace **out)
     for (int c = 0; c < w->count; ++c) {
         const supcg_geometry g = gs[c];
         nb[KT_FWD][c] = (g->nfw + 1) / 2;
+        nb[KT_FWDA][c] = (g->nfw_all + 1) / 2;
         nb[KT_BWD][c] = backward_blocks(g->nx, g->ny, 0, g->bparts);
         nb[KT_BWD2][c] = backward_blocks(g->nx, g->ny, 1, g->bparts);
         nb[KT_VEC][c] = (int)(((long long)g->ny * g->nxp + 1023) / 1024);
@@ -570,6 +638,7 @@ static int ws_create(const std::vector<supcg_geometry> &gs, Workspace **out)
         const supcg_geometry g = gs[c];
         Prob &P = w->hp[c];
         const size_t img = (size_t)g->ny * g->nxp, imgT = (size_t)g->nx * g->nyp, sino = (size_t)g->V * g->Up;
+        const size_t mir = g->npairs > 0 ? 1 : 0;   // mirrored images only with mirror pairs
         int maxblk = 0;
         for (int kt = 0; kt < KT_COUNT; ++kt) maxblk = std::max(maxblk, nb[kt][c]);
         const size_t npart = std::max<size_t>(12 * (size_t)nb[KT_STV][c], 2 * (size_t)maxblk) + 64;
@@ -578,16 +647,18 @@ static int ws_create(const std::vector<supcg_geometry> &gs, Workspace **out)
                                 sino * 4, sino * 4, sino * 4, (size_t)g->ny * g->nx * 16, sizeof(Scal),
                                 npart * 8, 16 * 4, 4 * 4, (size_t)(g->ny / 2 + 1) * (g->nx / 2 + 1) * 8,
                                 2 * (size_t)g->bparts * img * 8,
-                                (size_t)std::max(nb[KT_BWD][c], nb[KT_BWD2][c]) * 4, img * 4, img * 4};
+                                (size_t)std::max(nb[KT_BWD][c], nb[KT_BWD2][c]) * 4, img * 4, img * 4,
+                                mir * img * 4, mir * imgT * 4, mir * img * 4, mir * imgT * 4,
+                                imgT * 4, mir * img * 4, mir * imgT * 4};
         size_t total = 0;
         for (size_t s : sizes) total += al(s);
         char *base = nullptr;
         if (cudaMalloc(&base, total) != cudaSuccess) { delete w; return SUPCG_ERR_NOMEM; }
         w->allocs.push_back(base);
         if (cudaMemset(base, 0, total) != cudaSuccess) { delete w; return SUPCG_ERR_CUDA; }
-        char *ptrs[21];
+        char *ptrs[28];
         size_t off = 0;
-        for (int k = 0; k < 21; ++k) { ptrs[k] = base + off; off += al(sizes[k]); }
+        for (int k = 0; k < 28; ++k) { ptrs[k] = base + off; off += al(sizes[k]); }
         P.x = (float *)ptrs[0]; P.xT = (float *)ptrs[1]; P.p = (float *)ptrs[2]; P.pT = (float *)ptrs[3];
         P.g = (float *)ptrs[4]; P.z = (float *)ptrs[5]; P.h = (float *)ptrs[6]; P.tbar = (float *)ptrs[7];
         P.r = (float *)ptrs[8]; P.q = (float *)ptrs[9]; P.bpad = (float *)ptrs[10];
@@ -597,7 +668,18 @@ static int ws_create(const std::vector<supcg_geometry> &gs, Workspace **out)
         P.bparts = g->bparts;
         w->bparts = (c == 0 || w->bparts == g->bparts) ? g->bparts : 0;
         P.glo = (float *)ptrs[20];
+        P.xm = mir ? (float *)ptrs[21] : nullptr;
+        P.xmT = mir ? (float *)ptrs[22] : nullptr;
+        P.pm = mir ? (float *)ptrs[23] : nullptr;
+        P.pmT = mir ? (float *)ptrs[24] : nullptr;
+        P.mirror = mir ? g->dmirror : nullptr;
+        P.xloT = (float *)ptrs[25];
+        P.xmlo = mir ? (float *)ptrs[26] : nullptr;
+        P.xmloT = mir ? (float *)ptrs[27] : nullptr;
+        if (mir) w->mirror = 1;
         P.border = g->dborder;
+        P.border_all = g->dborder_all;
+        P.nfw_all = g->nfw_all;
         P.nx = g->nx; P.ny = g->ny; P.V = g->V; P.U = g->U;
         P.nxp = g->nxp; P.nyp = g->nyp; P.Up = g->Up;
         P.BU = g->BU; P.BW = g->BW; P.ntu = g->ntu; P.nfw = g->nfw; P.nA = g->nA; P.nB = g->nB;
@@ -617,6 +699,23 @@ static int ws_create(const std::vector<supcg_geometry> &gs, Workspace **out)
         e |= encode_map(&P.tm[1], P.xT, g->ny, g->nx, g->nyp, g->BW, kRowsPerChunk);
         e |= encode_map(&P.tm[2], P.p, g->nx, g->ny, g->nxp, g->BW, kRowsPerChunk);
         e |= encode_map(&P.tm[3], P.pT, g->ny, g->nx, g->nyp, g->BW, kRowsPerChunk);
+        const int RL = kRowsPerChunkLo;
+        e |= encode_map(&P.tm[8], P.x, g->nx, g->ny, g->nxp, g->BW, RL);
+        e |= encode_map(&P.tm[9], P.xT, g->ny, g->nx, g->nyp, g->BW, RL);
+        e |= encode_map(&P.tm[12], P.xlo, g->nx, g->ny, g->nxp, g->BW, RL);
+        e |= encode_map(&P.tm[13], P.xloT, g->ny, g->nx, g->nyp, g->BW, RL);
+        e |= encode_map(&P.tm[16], P.xlo, g->nx, g->ny, g->nxp, g->BW, kRowsPerChunk);
+        e |= encode_map(&P.tm[17], P.xloT, g->ny, g->nx, g->nyp, g->BW, kRowsPerChunk);
+        if (mir) {
+            e |= encode_map(&P.tm[4], P.xm, g->nx, g->ny, g->nxp, g->BW, kRowsPerChunk);
+            e |= encode_map(&P.tm[5], P.xmT, g->ny, g->nx, g->nyp, g->BW, kRowsPerChunk);
+            e |= encode_map(&P.tm[6], P.pm, g->nx, g->ny, g->nxp, g->BW, kRowsPerChunk);
+            e |= encode_map(&P.tm[7], P.pmT, g->ny, g->nx, g->nyp, g->BW, kRowsPerChunk);
+            e |= encode_map(&P.tm[10], P.xm, g->nx, g->ny, g->nxp, g->BW, RL);
+            e |= encode_map(&P.tm[11], P.xmT, g->ny, g->nx, g->nyp, g->BW, RL);
+            e |= encode_map(&P.tm[14], P.xmlo, g->nx, g->ny, g->nxp, g->BW, RL);
+            e |= encode_map(&P.tm[15], P.xmloT, g->ny, g->nx, g->nyp, g->BW, RL);
+        }
         if (e) { delete w; return SUPCG_ERR_CUDA; }
     }
     if (cudaMalloc(&w->dp, sizeof(Prob) * w->count) != cudaSuccess) { delete w; return SUPCG_ERR_NOMEM; }
@@ -704,7 +803,7 @@ extern "C" int supcg_project(supcg_geometry g, const void *d_x, void *d_y, int b
     }
     if ((rc = ws_upload(w, st))) return rc;
     if ((rc = launch_stage_in(w->L(KT_TR, st), 0))) return rc;
-    return launch_forward(w->L(KT_FWD, st), 0, FWD_PLAIN);
+    return launch_forward(w->L(KT_FWD, st), w->L(KT_FWDA, st), 0, FWD_PLAIN);
 }
 
 extern "C" int supcg_backproject(supcg_geometry g, const void *d_y, void *d_x, int batch, void *stream)
@@ -991,7 +1090,7 @@ static int enqueue_body(Workspace *w, const supcg_params *p, cudaStream_t st, in
                                               want_snorm, dir));
     else                                                                        // (S_TV writes x^T itself)
         LAUNCH(SUPCG_KIND_VECTOR, st, launch_transpose(w->L(KT_TR, st), 0));
-    LAUNCH(SUPCG_KIND_FORWARD, st, launch_forward(w->L(KT_FWD, st), 0, FWD_RESID));   // r = R x - b, f
+    LAUNCH(SUPCG_KIND_FORWARD, st, launch_forward(w->L(KT_FWD, st), w->L(KT_FWDA, st), 0, FWD_RESID));   // r = R x - b, f
     // g = R^T r, and h = R^T q of the previous step (A p for this step's beta; the previous alpha
     // took p^T A p from ||q||^2), one pass over the views for both
     LAUNCH(SUPCG_KIND_BACKWARD, st, launch_backward2(w->L(KT_BWD2, st), w->bwin));
@@ -1002,7 +1101,7 @@ static int enqueue_body(Workspace *w, const supcg_params *p, cudaStream_t st, in
     }
     LAUNCH(SUPCG_KIND_VECTOR, st, launch_pupdate(w->L(KT_TR, st)));             // p = -z + beta p, g^T p, p^T
     // q = R p, p^T h, alpha; its last block also logs the step and sets k <- k + 1 (step 14)
-    LAUNCH(SUPCG_KIND_FORWARD, st, launch_forward(w->L(KT_FWD, st), 1, FWD_NORM));
+    LAUNCH(SUPCG_KIND_FORWARD, st, launch_forward(w->L(KT_FWD, st), w->L(KT_FWDA, st), 1, FWD_NORM));
     return SUPCG_OK;
 }
 
@@ -1010,7 +1109,7 @@ static int enqueue_body(Workspace *w, const supcg_params *p, cudaStream_t st, in
 static int enqueue_init(Workspace *w, const supcg_params *p, cudaStream_t st)
 {
     int rc;
-    LAUNCH(SUPCG_KIND_FORWARD, st, launch_forward(w->L(KT_FWD, st), 0, FWD_RESID));
+    LAUNCH(SUPCG_KIND_FORWARD, st, launch_forward(w->L(KT_FWD, st), w->L(KT_FWDA, st), 0, FWD_RESID));
     LAUNCH(SUPCG_KIND_BACKWARD, st, launch_backward(w->L(KT_BWD, st), BWD_G, w->bwin));
     if (p->precondition) {
         if ((rc = enqueue_precond_k(w, st))) return rc;
@@ -1019,7 +1118,7 @@ static int enqueue_init(Workspace *w, const supcg_params *p, cudaStream_t st)
     }
     LAUNCH(SUPCG_KIND_VECTOR, st, launch_pupdate(w->L(KT_TR, st)));
     // (h = A p: in the next pass; the last block ends steps 1-9: init <- 0)
-    LAUNCH(SUPCG_KIND_FORWARD, st, launch_forward(w->L(KT_FWD, st), 1, FWD_NORM));
+    LAUNCH(SUPCG_KIND_FORWARD, st, launch_forward(w->L(KT_FWD, st), w->L(KT_FWDA, st), 1, FWD_NORM));
     return SUPCG_OK;
 }
 

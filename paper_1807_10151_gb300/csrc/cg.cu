@@ -19,7 +19,11 @@ __global__ void __launch_bounds__(256) k_transpose(const Prob *__restrict__ prob
     if (P.sc->done) return;
     const float *src = which ? P.p : P.x;
     float *dst = which ? P.pT : P.xT;
-    transpose_tile(src, P.nxp, dst, P.nyp, P.ny, P.nx, local, sh);
+    transpose_tile_m(src, P.nxp, dst, P.nyp, which ? P.pm : P.xm, which ? P.pmT : P.xmT, P.ny, P.nx, local, sh);
+    if (!which && P.xlo && P.xloT) {   // the iterate's low part, in the layouts the residual pass reads
+        __syncthreads();
+        transpose_tile_m(P.xlo, P.nxp, P.xloT, P.nyp, P.xmlo, P.xmloT, P.ny, P.nx, local, sh);
+    }
 }
 
 int launch_transpose(const Launch &L, int which)
@@ -52,6 +56,8 @@ __global__ void __launch_bounds__(256) k_stage_in(const Prob *__restrict__ probs
             v = load_user(P.in_user, (size_t)i * P.nx + j, P.storage);
             (which ? P.g : P.x)[(size_t)i * P.nxp + j] = v;
             if (!which && P.xlo) P.xlo[(size_t)i * P.nxp + j] = 0.0f;   // x_0 is exactly its FP32 value
+            if (!which && P.xm) P.xm[(size_t)i * P.nxp + (P.nx - 1 - j)] = v;
+            if (!which && P.xmlo) P.xmlo[(size_t)i * P.nxp + (P.nx - 1 - j)] = 0.0f;
         }
         sh[r][tx] = v;
     }
@@ -59,7 +65,12 @@ __global__ void __launch_bounds__(256) k_stage_in(const Prob *__restrict__ probs
     __syncthreads();
     for (int r = ty; r < 32; r += 8) {
         const int j = tj * 32 + r, i = ti * 32 + tx;
-        if (j < P.nx && i < P.ny) P.xT[(size_t)j * P.nyp + i] = sh[tx][r];
+        if (j < P.nx && i < P.ny) {
+            P.xT[(size_t)j * P.nyp + i] = sh[tx][r];
+            if (P.xmT) P.xmT[(size_t)(P.nx - 1 - j) * P.nyp + i] = sh[tx][r];
+            if (P.xloT) P.xloT[(size_t)j * P.nyp + i] = 0.0f;
+            if (P.xmloT) P.xmloT[(size_t)(P.nx - 1 - j) * P.nyp + i] = 0.0f;
+        }
     }
 }
 
@@ -161,6 +172,7 @@ __global__ void __launch_bounds__(256) k_pupdate(const Prob *__restrict__ probs,
         if (in[q]) {
             pn = __fmaf_rn(beta, pv[q], -zv[q]);
             P.p[(size_t)(ti * 32 + r) * P.nxp + tj * 32 + tx] = pn;
+            if (P.pm) P.pm[(size_t)(ti * 32 + r) * P.nxp + (P.nx - 1 - (tj * 32 + tx))] = pn;
             df_acc_prod(s, gv[q], pn);
             df_acc_prod(s, glv[q], pn);
             df_acc_prod(spp, pn, pn);
@@ -170,7 +182,10 @@ __global__ void __launch_bounds__(256) k_pupdate(const Prob *__restrict__ probs,
     __syncthreads();
     for (int r = ty; r < 32; r += 8) {
         const int j = tj * 32 + r, i = ti * 32 + tx;
-        if (j < P.nx && i < P.ny) P.pT[(size_t)j * P.nyp + i] = sh[tx][r];
+        if (j < P.nx && i < P.ny) {
+            P.pT[(size_t)j * P.nyp + i] = sh[tx][r];
+            if (P.pmT) P.pmT[(size_t)(P.nx - 1 - j) * P.nyp + i] = sh[tx][r];
+        }
     }
     double bs, bp;
     block_sum_df2<256>(s, spp, red, &bs, &bp);

@@ -16,6 +16,7 @@ namespace supcg {
 constexpr int kMaxStages = 24;       // FFT stages (radices) per length
 constexpr int kMaxRadix = 64;        // largest prime factor handled by the generic butterfly
 constexpr int kRowsPerChunk = 16;    // forward projector: image rows staged per TMA box
+constexpr int kRowsPerChunkLo = 8;   // the same for the residual pass, whose chunks also hold the low part
 constexpr int kBwdTileI = 32;        // backprojector pixel tile (rows)
 constexpr int kBwdViewParts = 4;     // backprojector: default blocks per tile (view parts), each a share of the view chunks
 constexpr int kBwdMaxParts = 8;      // backprojector: most view parts per tile (supcg_set_bwd_parts)
@@ -197,7 +198,10 @@ struct Scal {
 // ----------------------------------------------------------------- problem
 // One problem of a batched launch (device copy lives in global memory).
 struct Prob {
-    CUtensorMap tm[4];     // TMA maps: 0 = x, 1 = x^T, 2 = p, 3 = p^T (FP32, padded pitches)
+    CUtensorMap tm[18];    // TMA maps (FP32, padded pitches): 0 = x, 1 = x^T, 2 = p, 3 = p^T, 4-7 the same of
+                           // the mirrored images (only with mirror pairs); the residual pass's 8-row boxes:
+                           // 8 = x, 9 = x^T, 10 = xm, 11 = xm^T, 12 = xlo, 13 = xlo^T, 14 = xmlo, 15 = xmlo^T;
+                           // 16 = xlo, 17 = xlo^T in kRowsPerChunk-row boxes
     int nx, ny, V, U;
     int nxp, nyp, Up;      // pitches in elements: image, transposed image, sinogram
     int BU, BW, ntu;       // forward tiling: bins per tile, box width, bin tiles per view
@@ -208,8 +212,11 @@ struct Prob {
     int bwin;              // backprojector: bins staged per view and tile (multiple of 4)
     const ViewP *views;    // [V]
     const int *vlist;      // [nA + nB]: class-A views, then class-B views
+    const int *mirror;     // nullable [V]: the partner of a mirror pair's first view, else -1
     const int *border;     // [nfw]: forward warp items ((vidx * ntu + tile) * 2 + half), longest
                            // first; block b's warps take entries 2b and 2b + 1
+    const int *border_all; // [nfw_all]: the same with every view's items (border pairs mirror views)
+    int nfw_all;
     FFTPlan fx, fy;
     double mu, rho;
     double r2;             // r^2 of the Bayesian criterion (Eq. (2.3)); 0: least squares
@@ -235,6 +242,12 @@ struct Prob {
     // the preconditioner damps g's lowest frequencies by mu, so FP32 rounding of g alone
     // would dominate z = M g there; read by the first transform pass and by g^T p
     float *glo;
+    // with mirror pairs: x and p mirrored left-right (xm[i][j] = x[i][nx-1-j]) and their
+    // transposes, written with x^T and p^T for the forward projector (else null)
+    float *xm, *xmT, *pm, *pmT;
+    // the iterate's low part in the projector's layouts: xlo^T, and with mirror pairs xlo
+    // mirrored and its transpose; the residual pass projects x + xlo (null: not kept)
+    float *xloT, *xmlo, *xmloT;
     float *r, *q, *bpad;
     double2 *C;            // FFT scratch [ny][nx] (FP64 complex)
     float2 *Dtab;          // h(w_r) / (nx ny) at (min(k1, ny-k1), min(k2, nx-k2)), double-float: [ny/2+1][nx/2+1]
@@ -479,6 +492,30 @@ __device__ __forceinline__ void transpose_tile(const float *src, int sp, float *
     }
 }
 
+// transpose_tile that also writes the left-right mirror of src (m[i][nx-1-j] = src[i][j],
+// pitch sp) and its transpose (mT[nx-1-j][i], pitch dp) when m is not null.
+__device__ __forceinline__ void transpose_tile_m(const float *src, int sp, float *dst, int dp, float *m, float *mT,
+                                                 int ny, int nx, int tile, float (*sh)[33])
+{
+    const int tiles_j = (nx + 31) / 32;
+    const int ti = tile / tiles_j, tj = tile - ti * tiles_j;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 256 threads: 32 x 8
+    for (int r = ty; r < 32; r += 8) {
+        const int i = ti * 32 + r, j = tj * 32 + tx;
+        const float v = (i < ny && j < nx) ? src[(size_t)i * sp + j] : 0.0f;
+        sh[r][tx] = v;
+        if (m && i < ny && j < nx) m[(size_t)i * sp + (nx - 1 - j)] = v;
+    }
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+        const int j = tj * 32 + r, i = ti * 32 + tx;
+        if (j < nx && i < ny) {
+            dst[(size_t)j * dp + i] = sh[tx][r];
+            if (mT) mT[(size_t)(nx - 1 - j) * dp + i] = sh[tx][r];
+        }
+    }
+}
+
 // ----------------------------------------------------------------- TMA / mbarrier
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
@@ -558,10 +595,11 @@ struct Launch {
     int blocks;            // total blocks
     int bw_max;            // widest forward box (floats) among the problems
     int bparts;            // backprojector view parts shared by every problem, 0 if they differ
+    int mirror;            // 1: some problem has mirror pairs of views (the forward projector's paired variant)
     cudaStream_t st;
 };
 
-int launch_forward(const Launch &L, int which, int mode);
+int launch_forward(const Launch &L, const Launch &La, int which, int mode);   // La: every view's items
 int launch_backward(const Launch &L, int mode, int bwin);
 int launch_backward2(const Launch &L, int bwin);   // g from r and h from q in one pass
 int art_max_blocks(int *out);                                           // co-resident blocks of k_art

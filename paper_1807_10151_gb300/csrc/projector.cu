@@ -30,7 +30,7 @@ namespace supcg {
 // operand loads are plain shared-memory loads with 32-bit addresses.
 extern __shared__ __align__(128) float proj_dyn[];
 
-static_assert(kRowsPerChunk % 8 == 0, "chunks start at multiples of the 8-row fold groups");
+static_assert(kRowsPerChunk % 8 == 0 && kRowsPerChunkLo % 8 == 0, "chunks start at multiples of the 8-row fold groups");
 
 constexpr int kFwdBufs = 1;   // forward projector: staged boxes per warp (1: more resident warps hide the copies)
 
@@ -39,12 +39,22 @@ constexpr int kFwdBufs = 1;   // forward projector: staged boxes per warp (1: mo
 // row in the inner indices within hwq (half-width + margin) of its centre:
 // two of them, or three for views within about a degree of the diagonal
 // (NC = 3).  Each is weighted by weight(delta) with delta from the exact
-// split.  The row's terms are summed in FP32 and added to the ray's running
-// sum with Kahan compensation (sum, comp), so that the ray sum is accurate
-// to a few units in the last place of FP32 however many rows it crosses.
-template <bool CLASS_B, bool AXIS, int NC, bool CHECKED>
+// split.  The terms of a group of G rows are summed in FP32 and added to the
+// ray's running sum with Kahan compensation (sum, comp), so that the ray sum
+// is accurate to about one unit in the last place of FP32 however many rows
+// it crosses.  G = 8, and 4 in the residual pass (LO): there the sums'
+// rounding, about halved, enters r = R x - b and through it the gradient,
+// on which the solver's step lengths depend most.
+// MIR: the staged box is followed (moff floats later) by the same box of the
+// left-right mirrored image; each weight is also applied there, giving the ray
+// of the same bin in the mirror view (msum, mcomp: its compensated sum).
+// LO: the boxes of the iterate's low part follow (loff, lmoff floats later);
+// their weighted sums go to lsum (lmsum) in plain FP32: they are ~2^-24 of the
+// image's, so their own rounding is far below the image sum's.
+template <bool CLASS_B, bool AXIS, int NC, bool CHECKED, bool MIR, bool LO>
 __device__ __forceinline__ void fwd_rows(const Prob &P, const ViewP &vp, float tau_hi, float qm, int o0, int rb,
-                                         int re, int qs, int pbase, int *bad, float &sum, float &comp)
+                                         int re, int qs, int pbase, int moff, int loff, int lmoff, int *bad,
+                                         float &sum, float &comp, float &msum, float &mcomp, float &lsum, float &lmsum)
 {
     const int BW = P.BW;
     // outer coordinate of row o0 + rb (pixel units) and its change per row
@@ -61,6 +71,7 @@ __device__ __forceinline__ void fwd_rows(const Prob &P, const ViewP &vp, float t
     const float qh = __fsub_rn(qm, vp.hwq);
     const int prow = pbase - qs;   // proj_dyn index of inner index 0 of the box's first row
     float rs = 0.0f;   // FP32 sum of the rows of one 8-row group, then folded into (sum, comp)
+    float ms = 0.0f;   // the same for the mirror view
     auto row = [&](int r, float rf) {
         const float qc = ceil_magic(__fmaf_rn(rf, vp.b_o, qh));
         int q0 = magic_int(qc);
@@ -83,7 +94,11 @@ __device__ __forceinline__ void fwd_rows(const Prob &P, const ViewP &vp, float t
             if (k) I = __fadd_rn(I, dI);                                // exact half-integer
             const float big = __fmaf_rn(-hi_i, I, rbig);              // exact
             const float ad = fabsf(__fsub_rn(big, __fmaf_rn(lo_i, I, rsmall)));
-            rs = __fmaf_rn(weight_unit(ad, E, Sn, ESn, AXIS), pv[k], rs);
+            const float w = weight_unit(ad, E, Sn, ESn, AXIS);
+            rs = __fmaf_rn(w, pv[k], rs);
+            if (MIR) ms = __fmaf_rn(w, pv[k + moff], ms);
+            if (LO) lsum = __fmaf_rn(w, pv[k + loff], lsum);
+            if (LO && MIR) lmsum = __fmaf_rn(w, pv[k + lmoff], lmsum);
         }
     };
     // Kahan-compensated fold of a group's sum; a group that summed to exactly 0 is
@@ -96,16 +111,26 @@ __device__ __forceinline__ void fwd_rows(const Prob &P, const ViewP &vp, float t
             sum = tt;
         }
         rs = 0.0f;
+        if (MIR) {
+            if (ms != 0.0f) {
+                const float y = __fsub_rn(ms, mcomp);
+                const float tt = __fadd_rn(msum, y);
+                mcomp = __fsub_rn(__fsub_rn(tt, msum), y);
+                msum = tt;
+            }
+            ms = 0.0f;
+        }
     };
-    // groups of eight rows aligned to multiples of 8 of the outer index (o0 is one), so
+    // groups of G rows aligned to multiples of G of the outer index (o0 is one), so
     // that a ray's sum does not depend on the rows its warp walks beyond its own
+    constexpr int G = LO ? 4 : 8;
     int r = rb;
     float rf = __int2float_rn(rb);
     while (r < re) {
-        const int gend = min(re, (r & ~7) + 8);
-        if (gend - r == 8) {
+        const int gend = min(re, (r & ~(G - 1)) + G);
+        if (gend - r == G) {
 #pragma unroll
-            for (int k = 0; k < 8; ++k, rf = __fadd_rn(rf, 1.0f)) row(r + k, rf);
+            for (int k = 0; k < G; ++k, rf = __fadd_rn(rf, 1.0f)) row(r + k, rf);
         } else {
             for (int q = r; q < gend; ++q, rf = __fadd_rn(rf, 1.0f)) row(q, rf);
         }
@@ -118,9 +143,11 @@ __device__ __forceinline__ void fwd_rows(const Prob &P, const ViewP &vp, float t
 // for both: the candidate index, the exact-split coordinates and each
 // candidate's weight (lane for lane the scalar IEEE steps of fwd_rows, so
 // the weights are the same bits).  Only for boxes that hold every candidate.
-template <bool CLASS_B, bool AXIS, int NC>
+template <bool CLASS_B, bool AXIS, int NC, bool MIR, bool LO>
 __device__ __forceinline__ void fwd_rows2(const Prob &P, const ViewP &vp, uint64_t tau2, uint64_t qm2, int o0, int rb,
-                                          int re, int qs, int pbase, const float4 *rtab, float *sum, float *comp)
+                                          int re, int qs, int pbase, int moff, int loff, int lmoff, const float4 *rtab,
+                                          float *sum, float *comp, float *msum, float *mcomp, uint64_t &lacc2,
+                                          uint64_t &lmacc2)
 {
     const int BW = P.BW;
     const float hi_i = CLASS_B ? vp.su_hi : vp.cu_hi;   // coefficient of the inner coordinate
@@ -133,6 +160,7 @@ __device__ __forceinline__ void fwd_rows2(const Prob &P, const ViewP &vp, uint64
     const uint64_t qh2 = sub2_rn(qm2, pk2(vp.hwq, vp.hwq));
     const int prow = pbase - qs;   // proj_dyn index of inner index 0 of the box's first row
     uint64_t acc2 = pk2(0.0f, 0.0f);   // FP32 sums of up to 8 rows of A and B, then folded
+    uint64_t macc2 = pk2(0.0f, 0.0f);  // the same for the mirror view
     auto row = [&](int r, uint64_t qp2) {
         const uint64_t qc2 = add2_rp(qp2, mag2);   // first candidates, as magic floats
         float qcA, qcB;
@@ -152,6 +180,9 @@ __device__ __forceinline__ void fwd_rows2(const Prob &P, const ViewP &vp, uint64
             upk2(sub2_rn(big2, fma2_rn(loi2, I2, rsmall2)), dA, dB);
             const uint64_t w2 = pk2(weight_unit(fabsf(dA), E, Sn, ESn, AXIS), weight_unit(fabsf(dB), E, Sn, ESn, AXIS));
             acc2 = fma2_rn(w2, pk2(proj_dyn[pA + k], proj_dyn[pB + k]), acc2);
+            if (MIR) macc2 = fma2_rn(w2, pk2(proj_dyn[pA + k + moff], proj_dyn[pB + k + moff]), macc2);
+            if (LO) lacc2 = fma2_rn(w2, pk2(proj_dyn[pA + k + loff], proj_dyn[pB + k + loff]), lacc2);
+            if (LO && MIR) lmacc2 = fma2_rn(w2, pk2(proj_dyn[pA + k + lmoff], proj_dyn[pB + k + lmoff]), lmacc2);
         }
     };
     auto fold = [&]() {   // Kahan-compensated folds of the group's sums, as in fwd_rows
@@ -167,18 +198,32 @@ __device__ __forceinline__ void fwd_rows2(const Prob &P, const ViewP &vp, uint64
             }
         }
         acc2 = pk2(0.0f, 0.0f);
+        if (MIR) {
+            upk2(macc2, g[0], g[1]);
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                if (g[q] != 0.0f) {
+                    const float y = __fsub_rn(g[q], mcomp[q]);
+                    const float tt = __fadd_rn(msum[q], y);
+                    mcomp[q] = __fsub_rn(__fsub_rn(tt, msum[q]), y);
+                    msum[q] = tt;
+                }
+            }
+            macc2 = pk2(0.0f, 0.0f);
+        }
     };
+    constexpr int G = LO ? 4 : 8;   // rows per fold group, as in fwd_rows
     int r = rb;
-    while (r < re) {   // groups aligned to multiples of 8 of the outer index, as in fwd_rows
-        const int gend = min(re, (r & ~7) + 8);
+    while (r < re) {   // groups aligned to multiples of G of the outer index, as in fwd_rows
+        const int gend = min(re, (r & ~(G - 1)) + G);
         // the candidates' window start (centre - hwq) of row r, then stepped by b_o per row: it only
         // chooses the candidates (the weights decide), and eight steps stay ~1e-4 pixels from the
         // direct value, far inside the window's margin
         const float rf = __int2float_rn(r);
         uint64_t qp2 = fma2_rn(pk2(rf, rf), bo2, qh2);
-        if (gend - r == 8) {
+        if (gend - r == G) {
 #pragma unroll
-            for (int k = 0; k < 8; ++k, qp2 = add2_rn(qp2, bo2)) row(r + k, qp2);
+            for (int k = 0; k < G; ++k, qp2 = add2_rn(qp2, bo2)) row(r + k, qp2);
         } else {
             for (int q = r; q < gend; ++q, qp2 = add2_rn(qp2, bo2)) row(q, qp2);
         }
@@ -192,10 +237,10 @@ __device__ __forceinline__ void fwd_rows2(const Prob &P, const ViewP &vp, uint64
 // and s = lo_o O + uc_lo (rounded once), O the outer coordinate of row o0 + r, so that
 // a ray's row needs big = tau_hi + H (exact, the value of fma(-hi_o, O, tau_hi)) and s.
 // Written by lanes 0 .. RC-1 of the warp that reads it.
-template <bool CLASS_B>
+template <bool CLASS_B, int RC>
 __device__ __forceinline__ void fwd_row_terms(const Prob &P, const ViewP &vp, int o0, int lane, float4 *rtab)
 {
-    if (lane < kRowsPerChunk) {
+    if (lane < RC) {
         const float O = CLASS_B ? __fsub_rn(__int2float_rn(o0 + lane), P.cx) : __fsub_rn(P.cy, __int2float_rn(o0 + lane));
         const float H = __fmul_rn(CLASS_B ? -vp.cu_hi : -vp.su_hi, O);
         const float sm = __fmaf_rn(CLASS_B ? vp.cu_lo : vp.su_lo, O, P.uc_lo);
@@ -206,11 +251,12 @@ __device__ __forceinline__ void fwd_row_terms(const Prob &P, const ViewP &vp, in
 
 // Lower end (multiple of 4) of the inner range that chunk [o0, o0+RC) of the
 // block's rays [u_first, u_last] can touch.
+template <int RC>
 __device__ __forceinline__ int fwd_box_start(const ViewP &vp, float tf, float tl, int o0)
 {
     const float bf = __fmaf_rn(vp.a_tau, tf, vp.g0);
     const float bl = __fmaf_rn(vp.a_tau, tl, vp.g0);
-    const float o_a = __int2float_rn(o0), o_b = __int2float_rn(o0 + kRowsPerChunk - 1);
+    const float o_a = __int2float_rn(o0), o_b = __int2float_rn(o0 + RC - 1);
     float m = fminf(fminf(__fmaf_rn(vp.b_o, o_a, bf), __fmaf_rn(vp.b_o, o_b, bf)),
                     fminf(__fmaf_rn(vp.b_o, o_a, bl), __fmaf_rn(vp.b_o, o_b, bl)));
     int lo = __float2int_rd(m) - 3;
@@ -223,16 +269,39 @@ __device__ __forceinline__ int fwd_box_start(const ViewP &vp, float tf, float tl
 // only the chunks holding rows that one of its rays can meet, and within them
 // only those rows.  Rays past the block's last bin follow the last ray (inside
 // the box) and are dropped by the caller.
-template <bool CLASS_B, bool AXIS, int NC>
-__device__ __forceinline__ void fwd_ray2(const Prob &P, const ViewP &vp, const CUtensorMap *tm, int patch0,
+// MIR: each chunk also stages the same box of the mirrored image (tm_m) right after the
+// image's, and acc_m receives the sums of the same bins in the mirror view.
+// LO: the chunk's rows of the low part (tm_l, and of its mirror tm_lm) follow, and the
+// rays sum x + xlo; the chunks are then kRowsPerChunkLo rows high, so that the four
+// boxes take the shared memory of two.
+template <bool CLASS_B, bool AXIS, int NC, bool MIR, bool LO, int RC>
+__device__ __forceinline__ void fwd_ray2(const Prob &P, const ViewP &vp, const CUtensorMap *tm, const CUtensorMap *tm_m,
+                                         const CUtensorMap *tm_l, const CUtensorMap *tm_lm, int patch0,
                                          uint64_t *bars, float4 *rtab, int n_outer, int n_inner, int uA, int uB,
-                                         int u_last, float tf, float tl, int *bad, int *timed_out, double *acc)
+                                         int u_last, float tf, float tl, int *bad, int *timed_out, double *acc,
+                                         double *acc_m)
 {
-    const int RC = kRowsPerChunk, BW = P.BW;
+    constexpr int NBOX = (MIR ? 2 : 1) * (LO ? 2 : 1);
+    const int BW = P.BW;
     const int box_elems = RC * BW;
+    // one staged chunk: the image's box, the mirror's, the low part's, its mirror's
+    const int buf_elems = NBOX * box_elems;
+    const int moff = box_elems, loff = (MIR ? 2 : 1) * box_elems, lmoff = loff + box_elems;
     const int lane = threadIdx.x & 31;
     const int uc[2] = {min(uA, u_last), min(uB, u_last)};
     float tau_hi[2], base[2], sum[2] = {0.0f, 0.0f}, comp[2] = {0.0f, 0.0f};
+    float msum[2] = {0.0f, 0.0f}, mcomp[2] = {0.0f, 0.0f};
+    float lsum[2] = {0.0f, 0.0f}, lmsum[2] = {0.0f, 0.0f};
+    uint64_t lacc2 = pk2(0.0f, 0.0f), lmacc2 = pk2(0.0f, 0.0f);   // the packed path's low-part sums
+    // the chunk's boxes, in their order in the buffer
+    auto issue = [&](int slot, int qs, int c) {
+        float *dst = proj_dyn + patch0 + slot * buf_elems;
+        mbar_expect_tx(&bars[slot], buf_elems * 4);
+        tma_load_2d(dst, tm, qs, c * RC, &bars[slot]);
+        if (MIR) tma_load_2d(dst + moff, tm_m, qs, c * RC, &bars[slot]);
+        if (LO) tma_load_2d(dst + loff, tm_l, qs, c * RC, &bars[slot]);
+        if (LO && MIR) tma_load_2d(dst + lmoff, tm_lm, qs, c * RC, &bars[slot]);
+    };
     int r_lo = n_outer, r_hi = -1;
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
@@ -252,19 +321,15 @@ __device__ __forceinline__ void fwd_ray2(const Prob &P, const ViewP &vp, const C
     // each box's first inner index, computed once (every lane: the copy and the rows use it)
     int qs_buf[kFwdBufs];
 #pragma unroll
-    for (int ci = 0; ci < kFwdBufs; ++ci) qs_buf[ci] = fwd_box_start(vp, tf, tl, (c_first + ci) * RC);
+    for (int ci = 0; ci < kFwdBufs; ++ci) qs_buf[ci] = fwd_box_start<RC>(vp, tf, tl, (c_first + ci) * RC);
     if (lane == 0) {
-        for (int ci = 0; ci < kFwdBufs && ci < nch; ++ci) {
-            const int c = c_first + ci;
-            mbar_expect_tx(&bars[ci], box_elems * 4);
-            tma_load_2d(proj_dyn + patch0 + ci * box_elems, tm, qs_buf[ci], c * RC, &bars[ci]);
-        }
+        for (int ci = 0; ci < kFwdBufs && ci < nch; ++ci) issue(ci, qs_buf[ci], c_first + ci);
     }
     for (int ci = 0; ci < nch; ++ci) {
         const int buf = ci % kFwdBufs, c = c_first + ci;
         const bool ok = mbar_wait(&bars[buf], (ci / kFwdBufs) & 1);
         const int o0 = c * RC;
-        fwd_row_terms<CLASS_B>(P, vp, o0, lane, rtab);
+        fwd_row_terms<CLASS_B, RC>(P, vp, o0, lane, rtab);
         const int rows = min(RC, n_outer - o0);
         const int rb = max(0, w_lo - o0), re = min(rows, w_hi - o0 + 1);
         if (ok && rb < re) {
@@ -281,15 +346,18 @@ __device__ __forceinline__ void fwd_ray2(const Prob &P, const ViewP &vp, const C
                 const int qb = __float2int_ru(__fmaf_rn((float)(rows - 1), vp.b_o, qh)) - qs;
                 inside = inside && min(qa, qb) >= 1 && max(qa, qb) <= BW - NC - 1;
             }
-            const int pb = patch0 + buf * box_elems;
+            const int pb = patch0 + buf * buf_elems;
             // axis-aligned views (two in a uniform set) take the scalar path: no packed copy of
             // the row loop for them, less code competing for the instruction cache
             if (!AXIS && inside) {
-                fwd_rows2<CLASS_B, AXIS, NC>(P, vp, tau2, pk2(qm[0], qm[1]), o0, rb, re, qs, pb, rtab, sum, comp);
+                fwd_rows2<CLASS_B, AXIS, NC, MIR, LO>(P, vp, tau2, pk2(qm[0], qm[1]), o0, rb, re, qs, pb, moff, loff,
+                                                      lmoff, rtab, sum, comp, msum, mcomp, lacc2, lmacc2);
             } else {
 #pragma unroll
                 for (int q = 0; q < 2; ++q)
-                    fwd_rows<CLASS_B, AXIS, NC, true>(P, vp, tau_hi[q], qm[q], o0, rb, re, qs, pb, bad, sum[q], comp[q]);
+                    fwd_rows<CLASS_B, AXIS, NC, true, MIR, LO>(P, vp, tau_hi[q], qm[q], o0, rb, re, qs, pb, moff, loff,
+                                                               lmoff, bad, sum[q], comp[q], msum[q], mcomp[q], lsum[q],
+                                                               lmsum[q]);
             }
         }
         // every lane is done with this buffer; a timeout in any lane ends the warp's loop
@@ -303,23 +371,43 @@ __device__ __forceinline__ void fwd_ray2(const Prob &P, const ViewP &vp, const C
         }
         __syncwarp();
         if (ci + kFwdBufs < nch) {
-            qs_buf[buf] = fwd_box_start(vp, tf, tl, (c + kFwdBufs) * RC);
-            if (lane == 0) {
-                mbar_expect_tx(&bars[buf], box_elems * 4);
-                tma_load_2d(proj_dyn + patch0 + buf * box_elems, tm, qs_buf[buf], (c + kFwdBufs) * RC, &bars[buf]);
-            }
+            qs_buf[buf] = fwd_box_start<RC>(vp, tf, tl, (c + kFwdBufs) * RC);
+            if (lane == 0) issue(buf, qs_buf[buf], c + kFwdBufs);
+        }
+    }
+    if (LO) {   // the packed path's low-part sums join the scalar path's
+        float a, b;
+        upk2(lacc2, a, b);
+        lsum[0] = __fadd_rn(lsum[0], a);
+        lsum[1] = __fadd_rn(lsum[1], b);
+        if (MIR) {
+            upk2(lmacc2, a, b);
+            lmsum[0] = __fadd_rn(lmsum[0], a);
+            lmsum[1] = __fadd_rn(lmsum[1], b);
         }
     }
 #pragma unroll
-    for (int q = 0; q < 2; ++q) acc[q] = ((double)sum[q] - (double)comp[q]) * (double)vp.P;   // weights in units of P
+    for (int q = 0; q < 2; ++q) {   // weights in units of P
+        acc[q] = ((double)sum[q] - (double)comp[q] + (LO ? (double)lsum[q] : 0.0)) * (double)vp.P;
+        if (MIR) acc_m[q] = ((double)msum[q] - (double)mcomp[q] + (LO ? (double)lmsum[q] : 0.0)) * (double)vp.P;
+    }
 }
 
 constexpr int kFwdThreads = 64;   // two warps of 64 rays: 128 bins per block at most
 
-__global__ void __launch_bounds__(kFwdThreads, 10) k_forward(const Prob *__restrict__ probs, const int *__restrict__ prefix,
-                                                         int count, int which, int mode)
+// MIRK: some problem of the launch has mirror pairs of views.  An item of a pair's first
+// view then also sums the second view's rays from the mirrored image's boxes (two boxes
+// per chunk, so fewer blocks fit: this variant is compiled for 7 resident blocks, the
+// other for 10, 8 in the residual pass).  LO: the residual pass of a solve, which projects the iterate with its
+// low part (x + xlo); its chunks are half as high and hold twice the boxes, so the shared
+// memory per block is the same.
+template <bool MIRK, bool LO>
+__global__ void __launch_bounds__(kFwdThreads, MIRK ? 7 : (LO ? 8 : 10)) k_forward(const Prob *__restrict__ probs,
+                                                                    const int *__restrict__ prefix, int count,
+                                                                    int which, int mode)
 {
-    // proj_dyn: [warp][kFwdBufs][kRowsPerChunk][BW]
+    // proj_dyn: [warp][kFwdBufs][box: x, (MIRK) mirror, (LO) low part, (MIRK, LO) its mirror][RC][BW],
+    // RC = kRowsPerChunkLo rows with LO, else kRowsPerChunk
     __shared__ __align__(8) uint64_t bars[kFwdBufs * (kFwdThreads / 32)];   // one per staged box
     __shared__ float4 rowtab[kFwdThreads / 32][kRowsPerChunk];             // each warp's row terms
     __shared__ __align__(16) double red[40];
@@ -335,17 +423,27 @@ __global__ void __launch_bounds__(kFwdThreads, 10) k_forward(const Prob *__restr
     // first 64 bins of a (view, bin tile) or the rest of the tile
     const int t = threadIdx.x, warp = t >> 5, lane = t & 31;
     const int wi = 2 * local + warp;
-    const bool idle = wi >= P.nfw;   // the grid's last block may hold one item
-    const int item = idle ? 0 : P.border[wi];
+    // the paired kernel walks the item list without the mirror pairs' second views
+    const int nfw = MIRK ? P.nfw : P.nfw_all;
+    const bool idle = wi >= nfw;   // the grid's last block may hold one item
+    const int item = idle ? 0 : (MIRK ? P.border : P.border_all)[wi];
     const int half = item & 1, tv = item >> 1;
     const int vidx = tv / P.ntu, tile = tv - vidx * P.ntu;
     const bool classB = vidx >= P.nA;
     const int v = P.vlist[vidx];
+    const int vm = (MIRK && P.mirror && !idle) ? P.mirror[v] : -1;   // the mirror view, or -1
     const ViewP vp = P.views[v];
     const bool axis = (vp.flags & kViewAxis) != 0;
     const int n_outer = classB ? P.nx : P.ny, n_inner = classB ? P.ny : P.nx;
-    const CUtensorMap *tm = &P.tm[which * 2 + (classB ? 1 : 0)];
-    const int patch0 = warp * kFwdBufs * kRowsPerChunk * P.BW;   // this warp's boxes in proj_dyn
+    const int cb = classB ? 1 : 0;
+    const bool rc8 = MIRK && LO;
+    const CUtensorMap *tm = rc8 ? &P.tm[8 + cb] : &P.tm[which * 2 + cb];
+    const CUtensorMap *tm_m = rc8 ? &P.tm[10 + cb] : &P.tm[4 + which * 2 + cb];
+    const CUtensorMap *tm_l = rc8 ? &P.tm[12 + cb] : &P.tm[16 + cb], *tm_lm = &P.tm[14 + cb];
+    // rows per chunk: with both the mirror's and the low part's boxes, half as many
+    constexpr int RCK = (MIRK && LO) ? kRowsPerChunkLo : kRowsPerChunk;
+    // this warp's boxes in proj_dyn
+    const int patch0 = warp * kFwdBufs * (MIRK ? 2 : 1) * (LO ? 2 : 1) * RCK * P.BW;
     uint64_t *wbars = bars + kFwdBufs * warp;
 
     const int u_first = tile * P.BU;
@@ -362,18 +460,24 @@ __global__ void __launch_bounds__(kFwdThreads, 10) k_forward(const Prob *__restr
 
     int bad = 0;
     int timed_out = 0;   // a copy did not arrive (every lane of the warp sees it)
-    double acc[2] = {0.0, 0.0};
+    double acc[2] = {0.0, 0.0}, acc_m[2] = {0.0, 0.0};
     // axis-aligned views meet at most two pixels per row; near-diagonal ones up to three
     const bool three = (vp.flags & kViewFwd3) != 0;
-#define SUPCG_FWD(CB, AX, NC) \
-    fwd_ray2<CB, AX, NC>(P, vp, tm, patch0, wbars, rowtab[warp], n_outer, n_inner, uA, uB, u_last, tf, tl, &bad, \
-                         &timed_out, acc)
+#define SUPCG_FWD(CB, AX, NC, MIR) \
+    fwd_ray2<CB, AX, NC, MIR, LO, RCK>(P, vp, tm, tm_m, tm_l, tm_lm, patch0, wbars, rowtab[warp], n_outer, n_inner, uA, uB, \
+                                  u_last, tf, tl, &bad, &timed_out, acc, acc_m)
     if (idle) {
         // no item for this warp
+    } else if (MIRK && vm >= 0) {   // a pair (never axis-aligned: those have no mirror partner)
+        if (classB) {
+            if (three) SUPCG_FWD(true, false, 3, true); else SUPCG_FWD(true, false, 2, true);
+        } else {
+            if (three) SUPCG_FWD(false, false, 3, true); else SUPCG_FWD(false, false, 2, true);
+        }
     } else if (classB) {
-        if (axis) SUPCG_FWD(true, true, 2); else if (three) SUPCG_FWD(true, false, 3); else SUPCG_FWD(true, false, 2);
+        if (axis) SUPCG_FWD(true, true, 2, false); else if (three) SUPCG_FWD(true, false, 3, false); else SUPCG_FWD(true, false, 2, false);
     } else {
-        if (axis) SUPCG_FWD(false, true, 2); else if (three) SUPCG_FWD(false, false, 3); else SUPCG_FWD(false, false, 2);
+        if (axis) SUPCG_FWD(false, true, 2, false); else if (three) SUPCG_FWD(false, false, 3, false); else SUPCG_FWD(false, false, 2, false);
     }
 #undef SUPCG_FWD
     if (__syncthreads_or(timed_out)) {   // a warp's copy did not arrive: the whole block leaves
@@ -384,25 +488,30 @@ __global__ void __launch_bounds__(kFwdThreads, 10) k_forward(const Prob *__restr
 
     // epilogue: store, fused residual / norm reduction (exact squares, double-float sums)
     df s = df_make(0.0f);
+    // the item's view, then (a mirror pair) the partner view: the same bins, sums acc_m
+    auto emit = [&](int view, double a, int u) {
+        if (mode == FWD_PLAIN) {
+            const size_t o = (size_t)view * P.U + u;
+            if (P.storage == SUPCG_BF16) reinterpret_cast<__nv_bfloat16 *>(P.out_user)[o] = __double2bfloat16(a);
+            else reinterpret_cast<float *>(P.out_user)[o] = (float)a;
+        } else if (mode == FWD_RESID) {
+            const size_t o = (size_t)view * P.Up + u;
+            const float rr = (float)(a - (double)P.bpad[o]);   // r = R x - b, cancellation taken in FP64
+            P.r[o] = rr;
+            df_acc_prod(s, rr, rr);
+        } else {
+            const size_t o = (size_t)view * P.Up + u;
+            const float qq = (float)a;
+            P.q[o] = qq;
+            df_acc_prod(s, qq, qq);
+        }
+    };
 #pragma unroll
     for (int q = 0; q < 2; ++q) {
         const int u = q ? uB : uA;
         if (idle || u > uw1) continue;
-        if (mode == FWD_PLAIN) {
-            const size_t o = (size_t)v * P.U + u;
-            if (P.storage == SUPCG_BF16) reinterpret_cast<__nv_bfloat16 *>(P.out_user)[o] = __double2bfloat16(acc[q]);
-            else reinterpret_cast<float *>(P.out_user)[o] = (float)acc[q];
-        } else if (mode == FWD_RESID) {
-            const size_t o = (size_t)v * P.Up + u;
-            const float rr = (float)(acc[q] - (double)P.bpad[o]);   // r = R x - b, cancellation taken in FP64
-            P.r[o] = rr;
-            df_acc_prod(s, rr, rr);
-        } else {
-            const size_t o = (size_t)v * P.Up + u;
-            const float qq = (float)acc[q];
-            P.q[o] = qq;
-            df_acc_prod(s, qq, qq);
-        }
+        emit(v, acc[q], u);
+        if (MIRK && vm >= 0) emit(vm, acc_m[q], u);
     }
     __syncthreads();
     if (t == 0 && bad_sh && P.sc) atomicExch(&P.sc->status, (int)SUPCG_ERR_UNSUPPORTED);
@@ -461,15 +570,28 @@ __global__ void __launch_bounds__(kFwdThreads, 10) k_forward(const Prob *__restr
     }
 }
 
-int launch_forward(const Launch &L, int which, int mode)
+template <bool MIRK, bool LO>
+static int launch_forward_t(const Launch &L, int which, int mode)
 {
-    // every problem's BW <= 256, so the warps' box buffers never exceed this size
-    const int smem = (kFwdThreads / 32) * kFwdBufs * kRowsPerChunk * L.bw_max * 4;
-    int rc = func_attrs_once((const void *)k_forward, (kFwdThreads / 32) * kFwdBufs * kRowsPerChunk * 256 * 4);
+    // every problem's BW <= 256, so the warps' box buffers never exceed this size; with mirror
+    // pairs each chunk holds two boxes, and in the residual pass two more of half the rows
+    constexpr int rows = (MIRK && LO) ? 4 * kRowsPerChunkLo : (MIRK || LO) ? 2 * kRowsPerChunk : kRowsPerChunk;
+    const int per_warp = kFwdBufs * rows;
+    const int smem = (kFwdThreads / 32) * per_warp * L.bw_max * 4;
+    int rc = func_attrs_once((const void *)k_forward<MIRK, LO>, (kFwdThreads / 32) * per_warp * 256 * 4);
     if (rc) return rc;
-    k_forward<<<L.blocks, kFwdThreads, smem, L.st>>>(L.probs, L.prefix, L.count, which, mode);
+    k_forward<MIRK, LO><<<L.blocks, kFwdThreads, smem, L.st>>>(L.probs, L.prefix, L.count, which, mode);
     SUPCG_CUDA_TRY(cudaGetLastError());
     return SUPCG_OK;
+}
+
+int launch_forward(const Launch &L, const Launch &La, int which, int mode)
+{
+    // the solver's residual pass projects x + xlo (the iterate's low part is kept by every solve)
+    const bool lo = mode == FWD_RESID && which == 0;
+    if (L.mirror)
+        return lo ? launch_forward_t<true, true>(L, which, mode) : launch_forward_t<true, false>(L, which, mode);
+    return lo ? launch_forward_t<false, true>(La, which, mode) : launch_forward_t<false, false>(La, which, mode);
 }
 
 // ============================================================ backward

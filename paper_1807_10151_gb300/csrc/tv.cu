@@ -124,16 +124,19 @@ __device__ __forceinline__ float trial_term(const float *__restrict__ y, const f
 // y <- y + c t at element p of the iterate: in double-float arithmetic on the pair
 // (x, xlo) when the low part exists (the exact product c t added to it), else one
 // FP32 FMA.  Returns the new FP32 image value x = RN(x + xlo).
-__device__ __forceinline__ float x_step(float *__restrict__ x, float *__restrict__ xlo, size_t p, float c, float t)
+__device__ __forceinline__ float x_step(float *__restrict__ x, float *__restrict__ xlo, size_t p, float c, float t,
+                                        float *lo_out = nullptr)
 {
     if (!xlo) {
         const float v = __fmaf_rn(c, t, x[p]);
         x[p] = v;
+        if (lo_out) *lo_out = 0.0f;
         return v;
     }
     const df v = df_add(df{x[p], xlo[p]}, df_prod(c, t));
     x[p] = v.h;
     xlo[p] = v.l;
+    if (lo_out) *lo_out = v.l;
     return v.h;
 }
 
@@ -219,6 +222,7 @@ __global__ void __launch_bounds__(kTvThreads, 3) k_stv(const Prob *__restrict__ 
     __shared__ double sh_inv;   // grid-uniform FP64 scalars: computed by thread 0, read by all
     __shared__ float sh_c;
     __shared__ float sh_t[32][33];   // tile transposes of x
+    __shared__ float sh_l[32][33];   // and of its low part
     bool xt_done = false;            // the last step wrote x^T
     int local;
     const int pi = find_problem(prefix, count, blockIdx.x, &local);
@@ -457,17 +461,25 @@ __global__ void __launch_bounds__(kTvThreads, 3) k_stv(const Prob *__restrict__ 
                 const int ti = tile / tiles_j, tj = tile - ti * tiles_j;
                 for (int r = ty; r < 32; r += 8) {
                     const int i = ti * 32 + r, j = tj * 32 + tx;
-                    float v = 0.0f;
+                    float v = 0.0f, vl = 0.0f;
                     if (i < ny && j < nx) {
                         const size_t p = (size_t)i * ld + j;
-                        v = x_step(x, xl, p, c, tb[p]);
+                        v = x_step(x, xl, p, c, tb[p], &vl);
+                        if (P.xm) P.xm[(size_t)i * ld + (nx - 1 - j)] = v;
+                        if (P.xmlo) P.xmlo[(size_t)i * ld + (nx - 1 - j)] = vl;
                     }
                     sh_t[r][tx] = v;
+                    sh_l[r][tx] = vl;
                 }
                 __syncthreads();
                 for (int r = ty; r < 32; r += 8) {
                     const int j = tj * 32 + r, i = ti * 32 + tx;
-                    if (j < nx && i < ny) P.xT[(size_t)j * P.nyp + i] = sh_t[tx][r];
+                    if (j < nx && i < ny) {
+                        P.xT[(size_t)j * P.nyp + i] = sh_t[tx][r];
+                        if (P.xmT) P.xmT[(size_t)(nx - 1 - j) * P.nyp + i] = sh_t[tx][r];
+                        if (P.xloT) P.xloT[(size_t)j * P.nyp + i] = sh_l[tx][r];
+                        if (P.xmloT) P.xmloT[(size_t)(nx - 1 - j) * P.nyp + i] = sh_l[tx][r];
+                    }
                 }
                 __syncthreads();
             }
@@ -513,7 +525,8 @@ __global__ void __launch_bounds__(kTvThreads, 3) k_stv(const Prob *__restrict__ 
     if (ok && !xt_done) {
         const int tiles = ((ny + 31) / 32) * ((nx + 31) / 32);
         for (int tile = local; tile < tiles; tile += nb) {
-            transpose_tile(x, ld, P.xT, P.nyp, ny, nx, tile, sh_t);
+            transpose_tile_m(x, ld, P.xT, P.nyp, P.xm, P.xmT, ny, nx, tile, sh_t);
+            if (xl && P.xloT) transpose_tile_m(xl, ld, P.xloT, P.nyp, P.xmlo, P.xmloT, ny, nx, tile, sh_l);
             __syncthreads();
         }
     }
