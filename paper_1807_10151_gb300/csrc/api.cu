@@ -179,7 +179,9 @@ static int fwd_box_width(const supcg_geometry_s *g)
     double span = 0.0;
     for (const ViewP &vp : g->views)
         span = std::max(span, fabs((double)vp.a_tau) * 63.0 + fabs((double)vp.b_o) * (kRowsPerChunk - 1));
-    return round_up((int)ceil(span + 11.0), 4);
+    // a multiple of 4 floats (16-byte rows), and of 32 / kRowsPerChunkLo so that every staged
+    // box (kRowsPerChunkLo or kRowsPerChunk rows of BW floats) starts 128-byte aligned
+    return round_up((int)ceil(span + 11.0), std::max(4, 32 / kRowsPerChunkLo));
 }
 
 // Forward warp items in launch order, longest first.  An item is one warp's rays: the

@@ -30,7 +30,7 @@ namespace supcg {
 // operand loads are plain shared-memory loads with 32-bit addresses.
 extern __shared__ __align__(128) float proj_dyn[];
 
-static_assert(kRowsPerChunk % 8 == 0 && kRowsPerChunkLo % 8 == 0, "chunks start at multiples of the 8-row fold groups");
+static_assert(kRowsPerChunk % 8 == 0 && kRowsPerChunkLo % 4 == 0, "chunks start at multiples of the fold groups");
 
 constexpr int kFwdBufs = 1;   // forward projector: staged boxes per warp (1: more resident warps hide the copies)
 
