@@ -91,6 +91,15 @@ int supcg_get_tiling(supcg_geometry g, int *fwd_bins_per_block);
 int supcg_set_bwd_parts(supcg_geometry g, int parts);
 int supcg_get_bwd_parts(supcg_geometry g, int *parts);
 
+/* Mirror pairs of views found at creation: views theta and pi - theta (cos of
+ * opposite sign, sin equal, both within 1e-12; for the default angles v pi / V,
+ * views v and V - v).  Such a pair's rays meet the left-right mirrored image
+ * with the same weights, so the forward projector evaluates them once for both
+ * views (the second view's cos is set to exactly minus the first's, a change of
+ * at most 1e-12 in the geometry).  *pairs receives their number (0: none).
+ * Errors: SUPCG_ERR_ARG. */
+int supcg_get_mirror_pairs(supcg_geometry g, int *pairs);
+
 /* Free the geometry and all scratch it owns (synchronises the device first). */
 int supcg_destroy_geometry(supcg_geometry g);
 

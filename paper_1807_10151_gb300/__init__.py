@@ -33,7 +33,7 @@ EXPORTED = ["supcg_create_geometry", "supcg_destroy_geometry", "supcg_project", 
             "supcg_cnn_train_step", "supcg_solve_trace", "supcg_solve_learned", "supcg_set_tiling",
             "supcg_get_tiling", "supcg_solve_sweep", "supcg_art", "supcg_set_wait_limit",
             "supcg_set_barrier_shortfall", "supcg_solve_batched_learned", "supcg_set_bwd_parts",
-            "supcg_get_bwd_parts"]
+            "supcg_get_bwd_parts", "supcg_get_mirror_pairs"]
 KINDS = ["forward", "backward", "fft", "stv", "vector", "cnn"]
 
 _lock = threading.Lock()
@@ -131,6 +131,7 @@ def load(allow_build: bool = True):
         L.supcg_set_tiling.argtypes = [vp, i]
         L.supcg_set_bwd_parts.argtypes = [vp, i]
         L.supcg_get_bwd_parts.argtypes = [vp, C.POINTER(i)]
+        L.supcg_get_mirror_pairs.argtypes = [vp, C.POINTER(i)]
         L.supcg_get_tiling.argtypes = [vp, C.POINTER(i)]
         L.supcg_set_wait_limit.argtypes = [ll]
         L.supcg_set_barrier_shortfall.argtypes = [i]
@@ -302,6 +303,12 @@ class Geometry:
     def get_bwd_parts(self):
         v = C.c_int()
         _check(load().supcg_get_bwd_parts(self.handle, C.byref(v)), "supcg_get_bwd_parts")
+        return v.value
+
+    def mirror_pairs(self):
+        """Mirror pairs of views (theta, pi - theta) the forward projector evaluates together."""
+        v = C.c_int()
+        _check(load().supcg_get_mirror_pairs(self.handle, C.byref(v)), "supcg_get_mirror_pairs")
         return v.value
 
     @property

@@ -526,6 +526,13 @@ extern "C" int supcg_get_bwd_parts(supcg_geometry g, int *parts)
     return SUPCG_OK;
 }
 
+extern "C" int supcg_get_mirror_pairs(supcg_geometry g, int *pairs)
+{
+    if (!g || !pairs) return SUPCG_ERR_ARG;
+    *pairs = g->npairs;
+    return SUPCG_OK;
+}
+
 extern "C" int supcg_get_tiling(supcg_geometry g, int *fwd_bins_per_block)
 {
     if (!g || !fwd_bins_per_block) return SUPCG_ERR_ARG;

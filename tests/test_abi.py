@@ -41,6 +41,7 @@ def test_argument_errors_are_status_codes():
     assert L.supcg_create_geometry(0, 4, 0.25, 4, None, 5, 0.0, 0.0, 0, C.byref(h)) == -1
     assert L.supcg_create_geometry(4, 4, -1.0, 4, None, 5, 0.0, 0.0, 0, C.byref(h)) == -1
     assert L.supcg_create_geometry(4, 4, 0.25, 4, None, 5, 0.0, 0.0, 7, C.byref(h)) == -1
+    assert L.supcg_get_mirror_pairs(None, C.byref(C.c_int())) == -1
     assert S.supcg_status_string(-5).startswith("S_TV")
     assert S.supcg_status_string(0) == "ok"
 

@@ -59,6 +59,40 @@ def test_project_and_backproject_match_oracle(nx, ny, V, U, off, dsf):
         assert abs(lhs - rhs) <= 1e-6 * np.linalg.norm(gx) * np.linalg.norm(yy)
 
 
+@pytest.mark.parametrize("V,pairs", [(720, 359), (90, 44), (13, 6), (5, 2), (2, 0), (1, 0)])
+def test_mirror_pairs_of_the_default_angles(V, pairs):
+    """Views v pi / V and (V - v) pi / V pair up; 0 and pi / 2 stay single."""
+    og = O.Geometry(16, V=V, U=23)
+    assert gpu_geometry(og).mirror_pairs() == pairs
+
+
+def test_projection_with_paired_and_single_views_matches_oracle():
+    """A view set with one mirror pair (0.3, pi - 0.3) among single views, at
+    angles the default set does not have: the paired kernel sums the pair's
+    rays together, the others alone, every ray within 1e-5 of the oracle's
+    explicit R, and the pair still the exact transpose of the backprojector."""
+    angles = np.array([0.3, 0.9, np.pi - 0.3, 1.7, 2.2])
+    og = O.Geometry(53, ny=41, V=5, U=71, theta=angles)
+    R = O.CSR(og)
+    G = gpu_geometry(og)
+    assert G.mirror_pairs() == 1
+    rng = np.random.default_rng(77)
+    x = f32(rng.uniform(size=(41, 53)))
+    gx = G.project(to_dev(x)).double().cpu().numpy()
+    assert rel_l2(gx, R.project(x)) <= 1e-5
+    for v in range(5):
+        assert rel_l2(gx[v], R.project(x)[v]) <= 1e-5
+    e = np.zeros((41, 53), np.float32)
+    e[20, 7] = 1
+    col = G.project(to_dev(e)).cpu().numpy()
+    for v in range(5):
+        u = int(np.argmax(col[v]))
+        assert col[v, u] > 0
+        s = np.zeros((5, 71), np.float32)
+        s[v, u] = 1
+        assert G.backproject(to_dev(s)).cpu().numpy()[20, 7] == col[v, u]
+
+
 def test_bin_size_limits():
     """Bins up to about 2.5 times coarser than pixels are projected with oracle parity;
     much coarser or much finer bins are refused (SUPCG_ERR_UNSUPPORTED), not computed wrongly.
