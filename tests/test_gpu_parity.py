@@ -272,19 +272,21 @@ def test_solve_config1_50_iterations_match_oracle(seed):
     assert errs[0] <= 1e-4, errs[0]
 
 
-@pytest.mark.parametrize("perturb,precond", [(False, True), (False, False), (True, False)])
-def test_solve_variants_match_oracle(perturb, precond):
-    """PCG (no S_TV), CG (M = I) and SupCG (M = I with S_TV), 6 iterations.
+@pytest.mark.parametrize("perturb,precond,iters", [(False, True, 10), (False, False, 6), (True, False, 50)])
+def test_solve_variants_match_oracle(perturb, precond, iters):
+    """PCG (no S_TV) over 10 iterations, CG (M = I) over 6 and SupCG (M = I
+    with S_TV) over 50.
 
     Without the TV perturbation, CG with FP32 vectors parts from CG with FP64
-    vectors once its residual has dropped by two orders (loss of conjugacy:
-    an FP32-rounded numpy CG on this problem is 3e-4 away at 10 iterations
-    for M = I, 8e-6 at 12 for the preconditioned one), so iterate parity is
-    checked over 6 iterations; longer runs are checked by properties below."""
+    vectors once its residual has collapsed (loss of conjugacy): on this
+    problem the GPU's PCG is 7e-7 from the oracle at 10 iterations and 6e-2 at
+    20, its CG 3e-6 at 6 and 1e-2 at 10.  So the unperturbed variants' iterate
+    parity stops there, and longer runs are checked by properties below.  The
+    perturbed SupCG stays within 1e-6 over the 50 iterations."""
     og, R, x_true, b = config1_problem(seed=1002, N=48, V=60, U=70)
     G = gpu_geometry(og)
     b32 = f32(b)
-    kw = dict(K=2, a=0.9, gamma=0.05, mu=1e-3, rho=0.6, max_iter=6)
+    kw = dict(K=2, a=0.9, gamma=0.05, mu=1e-3, rho=0.6, max_iter=iters)
     D = None if precond else np.ones((og.ny, og.nx))
     ref = O.suppcg(R, b32, perturb=perturb, D=D, **kw)
     x, rep, _ = G.solve(to_dev(b32), perturb=perturb, precondition=precond, **kw)
