@@ -109,20 +109,26 @@ __device__ __forceinline__ dfc twid_df(const float4 *tw, int e, bool inv)
 }
 
 // The twiddles the block's transforms read: its shared copy (stw, room for
-// kFftSmemTw entries) when the length allows, else the global table.
+// kFftSmemTw entries) when the length allows, else the global table.  The copy
+// is only issued here: the caller's barrier after its own loads completes it, so
+// both sets of loads are in flight together.
 __device__ __forceinline__ const float4 *stage_twiddles(const FFTPlan &pl, float4 *stw)
 {
     if (pl.n > kFftSmemTw) return pl.twf;
     for (int e = threadIdx.x; e < pl.n; e += blockDim.x) stw[e] = __ldg(pl.twf + e);
-    __syncthreads();
     return stw;
 }
+
+// Elements per thread of a 256-thread pass whose h (rows) or D (columns) is read before
+// the transform (nvec x n <= 2048 gives at most 8; the columns keep 4 in registers)
+constexpr int kFftPerThread = 8;
+constexpr int kFftPerThreadD = 4;
 
 // Transforms `nvec` contiguous vectors of length pl.n held in a (b is scratch
 // of the same size), in double-float, with the twiddles tw (shared or global);
 // returns the buffer that holds the result.  The same mixed-radix Stockham
 // schedule as fft_smem; for power-of-two lengths the index arithmetic is shifts.
-__device__ float4 *fft_smem_df(float4 *a, float4 *b, int nvec, const FFTPlan &pl, const float4 *tw, bool inv)
+__device__ __forceinline__ float4 *fft_smem_df(float4 *a, float4 *b, int nvec, const FFTPlan &pl, const float4 *tw, bool inv)
 {
     const int n = pl.n;
     const bool pow2 = (n & (n - 1)) == 0;
@@ -238,6 +244,21 @@ __global__ void __launch_bounds__(256) k_fft_rows(const Prob *__restrict__ probs
             a[e] = dfc_st(dfc{df_sub(ya.r, yb.i), df_add(ya.i, yb.r)});   // ya + i yb
         }
     }
+    // the inverse pass's h (for z^T h), read before the transform so that its loads
+    // overlap the butterflies instead of following them
+    float hA[kFftPerThread], hB[kFftPerThread];
+    const bool want_h = inverse && !standalone;
+#pragma unroll
+    for (int k = 0; k < kFftPerThread; ++k) {
+        const int e = threadIdx.x + k * blockDim.x;
+        hA[k] = hB[k] = 0.0f;
+        if (want_h && e < np * nx) {
+            const int pr = e / nx, q = e - pr * nx;
+            const int ra = 2 * (p0 + pr), rb = ra + 1;
+            hA[k] = P.h[(size_t)ra * P.nxp + q];
+            if (rb < ny) hB[k] = P.h[(size_t)rb * P.nxp + q];
+        }
+    }
     __syncthreads();
     float4 *res = fft_smem_df(a, b, np, P.fx, tw, inverse != 0);
     if (!inverse) {
@@ -251,19 +272,33 @@ __global__ void __launch_bounds__(256) k_fft_rows(const Prob *__restrict__ probs
     } else {
         // z, and inside a solve also z^T h for beta = z^T h / p^T h (Algorithm 2 step 3)
         df s = df_make(0.0f);   // z^T h: exact products, double-float sums
-        for (int e = threadIdx.x; e < np * nx; e += blockDim.x) {
+        // element e = threadIdx.x + k blockDim.x; the first kFftPerThread of a thread use the
+        // prefetched h (indexed at compile time, so it stays in registers), any further ones
+        // read it here
+        auto put_z = [&](int e, float ha, float hb) {
             const int pr = e / nx, q = e - pr * nx;
             const int ra = 2 * (p0 + pr), rb = ra + 1;
             const size_t ia = (size_t)ra * P.nxp + q, ib = (size_t)rb * P.nxp + q;
             const float4 v = res[e];
             const float za = __fadd_rn(v.x, v.y);   // the pair rounded to FP32
             P.z[ia] = za;
-            if (!standalone) df_acc_prod(s, za, P.h[ia]);
+            if (!standalone) df_acc_prod(s, za, ha);
             if (rb < ny) {
                 const float zb = __fadd_rn(v.z, v.w);
                 P.z[ib] = zb;
-                if (!standalone) df_acc_prod(s, zb, P.h[ib]);
+                if (!standalone) df_acc_prod(s, zb, hb);
             }
+        };
+#pragma unroll
+        for (int k = 0; k < kFftPerThread; ++k) {
+            const int e = threadIdx.x + k * blockDim.x;
+            if (e < np * nx) put_z(e, hA[k], hB[k]);
+        }
+        for (int e = threadIdx.x + kFftPerThread * blockDim.x; e < np * nx; e += blockDim.x) {
+            const int pr = e / nx, q = e - pr * nx;
+            const int ra = 2 * (p0 + pr), rb = ra + 1;
+            put_z(e, standalone ? 0.0f : P.h[(size_t)ra * P.nxp + q],
+                  (standalone || rb >= ny) ? 0.0f : P.h[(size_t)rb * P.nxp + q]);
         }
         if (!standalone) {
             __shared__ __align__(16) double red[40];
@@ -312,15 +347,33 @@ __global__ void __launch_bounds__(256) k_fft_cols(const Prob *__restrict__ probs
         const int k1 = e / nc, c = e - k1 * nc;   // consecutive threads read consecutive columns
         a[c * ny + k1] = S[(size_t)k1 * hx + c0 + c];
     }
+    // D for this thread's elements, read before the transform so that its loads overlap it
+    float2 dpre[kFftPerThreadD];
+#pragma unroll
+    for (int k = 0; k < kFftPerThreadD; ++k) {
+        const int e = threadIdx.x + k * blockDim.x;
+        dpre[k] = make_float2(0.0f, 0.0f);
+        if (e < nc * ny) {
+            const int c = e / ny, k1 = e - c * ny;
+            dpre[k] = __ldg(P.Dtab + (size_t)min(k1, ny - k1) * hx + c0 + c);   // k2 <= nx/2
+        }
+    }
     __syncthreads();
     float4 *res = fft_smem_df(a, b, nc, P.fy, tw, false);
     float4 *oth = (res == a) ? b : a;
-    for (int e = threadIdx.x; e < nc * ny; e += blockDim.x) {
-        const int c = e / ny, k1 = e - c * ny;
-        const float2 hd = __ldg(P.Dtab + (size_t)min(k1, ny - k1) * hx + c0 + c);   // k2 <= nx/2
+    auto apply_d = [&](int e, float2 hd) {
         const df D = {hd.x, hd.y};
         const dfc v = dfc_ld(res[e]);
         res[e] = dfc_st(dfc{df_mul(v.r, D), df_mul(v.i, D)});
+    };
+#pragma unroll
+    for (int k = 0; k < kFftPerThreadD; ++k) {   // the prefetched D (compile-time index: registers)
+        const int e = threadIdx.x + k * blockDim.x;
+        if (e < nc * ny) apply_d(e, dpre[k]);
+    }
+    for (int e = threadIdx.x + kFftPerThreadD * blockDim.x; e < nc * ny; e += blockDim.x) {
+        const int c = e / ny, k1 = e - c * ny;
+        apply_d(e, __ldg(P.Dtab + (size_t)min(k1, ny - k1) * hx + c0 + c));   // k2 <= nx/2
     }
     __syncthreads();
     float4 *fin = fft_smem_df(res, oth, nc, P.fy, tw, true);
