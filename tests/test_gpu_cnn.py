@@ -4,7 +4,12 @@ The GPU stores weights and activations in BF16 and accumulates in FP32; the
 reference here applies the same BF16 roundings (weights, the input tensor,
 every hidden activation and every stored gradient) around the oracle's FP64
 convolutions, so the remaining differences are FP32-vs-FP64 accumulation and
-rare one-ulp BF16 flips."""
+rare one-ulp BF16 flips.  BF16's unit is 2^-8 (3.9e-3 relative): a flipped
+element of a stored gradient moves the layers below it by about that much,
+and the bounds allow two such flips in the gradients (1e-2) and a quarter
+unit in the forward pass (1e-3).  Measured: forward 2e-5 to 1.6e-4 over four
+seeds; gradients 1e-8, or 4e-3 when one stored gradient flips (this test's
+case)."""
 import numpy as np
 import pytest
 
@@ -68,7 +73,7 @@ def test_forward_matches_oracle_layers():
     tb = rng.standard_normal((count, ny, nx)).astype(np.float32)
     out = net.forward(torch.tensor(x, device="cuda"), torch.tensor(tb, device="cuda")).cpu().numpy()
     ref, _, _ = reference_forward(p, x, tb)
-    assert rel_l2(out, ref) <= 5e-3
+    assert rel_l2(out, ref) <= 1e-3
     # an untrained network (last layer zero) returns the scaled input direction
     net2 = S.CNN(ny, nx, max_batch=4, seed=5)
     out2 = net2.forward(torch.tensor(x, device="cuda"), torch.tensor(tb, device="cuda")).cpu().numpy()
@@ -106,8 +111,8 @@ def test_gradients_match_oracle_backward():
                 G = bf16(dx * (acts[k][li] > 0))                # dL/dz of the layer below, stored in BF16
     gl = S.CNN.unflatten(g.astype(np.float64))
     for li in range(5):
-        assert rel_l2(gl[li][0], ref[0][li]) <= 3e-2, li
-        assert rel_l2(gl[li][1], ref[1][li]) <= 3e-2, li
+        assert rel_l2(gl[li][0], ref[0][li]) <= 1e-2, li
+        assert rel_l2(gl[li][1], ref[1][li]) <= 1e-2, li
 
 
 def test_training_reduces_the_loss():
