@@ -423,17 +423,17 @@ def memory_bound_legs(G, b, N, peak_gbs):
     on an N x N slice (its working set, images, spectrum and sinograms, exceeds L2):
     the difference of two profiled solves (4 and 12 iterations) removes the one-off
     staging and steps 1-9.  Bytes per iteration (n = N^2; x and g are double-float
-    pairs, x + xlo and g + glo; the layouts the forward projector reads, x^T, p^T,
-    xlo^T and with mirror pairs of views the left-right mirrored images, are
-    written by the kernels that produce x and p):
+    pairs, x + xlo and g + glo; the layouts the forward projector reads, p^T, the
+    S_TV displacement d and d^T, and with mirror pairs of views the left-right
+    mirrored images, are written by the kernels that produce p and d):
       vector: x update (read x, xlo, p; write x, xlo) 20n + p update (read p, z, g, glo;
            write p, p^T, with mirror pairs also p mirrored and its transpose) 24n (32n);
       fft: rows (read g and glo 8n, write the half spectrum, 16 B per stored complex),
            columns (read and write it, read the quarter table of D, 8 B per entry),
            inverse rows (read it, write z, read h for z^T h);
       stv (K = 1): tbar pass (read x, write tbar) 8n, every trial (read x, tbar) 8n,
-           last step (read x, xlo, tbar; write x, xlo, x^T, xlo^T, with mirror pairs also
-           x and xlo mirrored and their transposes) 28n (44n)."""
+           last step (read x, xlo, tbar; write x, xlo, d, d^T, with mirror pairs also d
+           mirrored and its transpose) 28n (36n)."""
     n = N * N
     mir = G.mirror_pairs() > 0
     hx = N // 2 + 1
@@ -448,7 +448,7 @@ def memory_bound_legs(G, b, N, peak_gbs):
     trials = runs[12][0]["ell"] - runs[4][0]["ell"]   # K = 1: l advances once per trial
     out = {}
     vec_bytes = (20 + (32 if mir else 24)) * n
-    stv_bytes = (8 + (44 if mir else 28)) * n + 8 * n * trials / d_it
+    stv_bytes = (8 + (36 if mir else 28)) * n + 8 * n * trials / d_it
     for kind, launches, nbytes in (("vector", 2, vec_bytes), ("fft", 3, fft_bytes), ("stv", 1, stv_bytes)):
         ms = (runs[12][1][kind][0] - runs[4][1][kind][0]) / d_it
         nl = (runs[12][1][kind][1] - runs[4][1][kind][1]) / d_it

@@ -179,9 +179,10 @@ static int fwd_box_width(const supcg_geometry_s *g)
     double span = 0.0;
     for (const ViewP &vp : g->views)
         span = std::max(span, fabs((double)vp.a_tau) * 63.0 + fabs((double)vp.b_o) * (kRowsPerChunk - 1));
-    // a multiple of 4 floats (16-byte rows), and of 32 / kRowsPerChunkLo so that every staged
-    // box (kRowsPerChunkLo or kRowsPerChunk rows of BW floats) starts 128-byte aligned
-    return round_up((int)ceil(span + 11.0), std::max(4, 32 / kRowsPerChunkLo));
+    // a multiple of 4 floats (16-byte rows), so that every staged box (kRowsPerChunk rows of
+    // BW floats) starts 128-byte aligned
+    static_assert((4 * kRowsPerChunk * 4) % 128 == 0, "boxes of 4k floats per row start 128-byte aligned");
+    return round_up((int)ceil(span + 11.0), 4);
 }
 
 // Forward warp items in launch order, longest first.  An item is one warp's rays: the
@@ -658,16 +659,17 @@ static int ws_create(const std::vector<supcg_geometry> &gs, Workspace **out)
                                 2 * (size_t)g->bparts * img * 8,
                                 (size_t)std::max(nb[KT_BWD][c], nb[KT_BWD2][c]) * 4, img * 4, img * 4,
                                 mir * img * 4, mir * imgT * 4, mir * img * 4, mir * imgT * 4,
-                                imgT * 4, mir * img * 4, mir * imgT * 4};
+                                img * 4, imgT * 4, mir * img * 4, mir * imgT * 4, sino * 8, sino * 8};
+        constexpr int kPieces = sizeof(sizes) / sizeof(sizes[0]);
         size_t total = 0;
         for (size_t s : sizes) total += al(s);
         char *base = nullptr;
         if (cudaMalloc(&base, total) != cudaSuccess) { delete w; return SUPCG_ERR_NOMEM; }
         w->allocs.push_back(base);
         if (cudaMemset(base, 0, total) != cudaSuccess) { delete w; return SUPCG_ERR_CUDA; }
-        char *ptrs[28];
+        char *ptrs[kPieces];
         size_t off = 0;
-        for (int k = 0; k < 28; ++k) { ptrs[k] = base + off; off += al(sizes[k]); }
+        for (int k = 0; k < kPieces; ++k) { ptrs[k] = base + off; off += al(sizes[k]); }
         P.x = (float *)ptrs[0]; P.xT = (float *)ptrs[1]; P.p = (float *)ptrs[2]; P.pT = (float *)ptrs[3];
         P.g = (float *)ptrs[4]; P.z = (float *)ptrs[5]; P.h = (float *)ptrs[6]; P.tbar = (float *)ptrs[7];
         P.r = (float *)ptrs[8]; P.q = (float *)ptrs[9]; P.bpad = (float *)ptrs[10];
@@ -682,9 +684,12 @@ static int ws_create(const std::vector<supcg_geometry> &gs, Workspace **out)
         P.pm = mir ? (float *)ptrs[23] : nullptr;
         P.pmT = mir ? (float *)ptrs[24] : nullptr;
         P.mirror = mir ? g->dmirror : nullptr;
-        P.xloT = (float *)ptrs[25];
-        P.xmlo = mir ? (float *)ptrs[26] : nullptr;
-        P.xmloT = mir ? (float *)ptrs[27] : nullptr;
+        P.d = (float *)ptrs[25];
+        P.dT = (float *)ptrs[26];
+        P.dm = mir ? (float *)ptrs[27] : nullptr;
+        P.dmT = mir ? (float *)ptrs[28] : nullptr;
+        P.rd = (double *)ptrs[29];
+        P.qd = (double *)ptrs[30];
         if (mir) w->mirror = 1;
         P.border = g->dborder;
         P.border_all = g->dborder_all;
@@ -704,26 +709,16 @@ static int ws_create(const std::vector<supcg_geometry> &gs, Workspace **out)
         P.r2 = 0.0;
         P.gray_scale = g->ds / ((double)g->V * g->nx * g->ny * g->d * g->d);
         int e = 0;
-        e |= encode_map(&P.tm[0], P.x, g->nx, g->ny, g->nxp, g->BW, kRowsPerChunk);
-        e |= encode_map(&P.tm[1], P.xT, g->ny, g->nx, g->nyp, g->BW, kRowsPerChunk);
-        e |= encode_map(&P.tm[2], P.p, g->nx, g->ny, g->nxp, g->BW, kRowsPerChunk);
-        e |= encode_map(&P.tm[3], P.pT, g->ny, g->nx, g->nyp, g->BW, kRowsPerChunk);
-        const int RL = kRowsPerChunkLo;
-        e |= encode_map(&P.tm[8], P.x, g->nx, g->ny, g->nxp, g->BW, RL);
-        e |= encode_map(&P.tm[9], P.xT, g->ny, g->nx, g->nyp, g->BW, RL);
-        e |= encode_map(&P.tm[12], P.xlo, g->nx, g->ny, g->nxp, g->BW, RL);
-        e |= encode_map(&P.tm[13], P.xloT, g->ny, g->nx, g->nyp, g->BW, RL);
-        e |= encode_map(&P.tm[16], P.xlo, g->nx, g->ny, g->nxp, g->BW, kRowsPerChunk);
-        e |= encode_map(&P.tm[17], P.xloT, g->ny, g->nx, g->nyp, g->BW, kRowsPerChunk);
-        if (mir) {
-            e |= encode_map(&P.tm[4], P.xm, g->nx, g->ny, g->nxp, g->BW, kRowsPerChunk);
-            e |= encode_map(&P.tm[5], P.xmT, g->ny, g->nx, g->nyp, g->BW, kRowsPerChunk);
-            e |= encode_map(&P.tm[6], P.pm, g->nx, g->ny, g->nxp, g->BW, kRowsPerChunk);
-            e |= encode_map(&P.tm[7], P.pmT, g->ny, g->nx, g->nyp, g->BW, kRowsPerChunk);
-            e |= encode_map(&P.tm[10], P.xm, g->nx, g->ny, g->nxp, g->BW, RL);
-            e |= encode_map(&P.tm[11], P.xmT, g->ny, g->nx, g->nyp, g->BW, RL);
-            e |= encode_map(&P.tm[14], P.xmlo, g->nx, g->ny, g->nxp, g->BW, RL);
-            e |= encode_map(&P.tm[15], P.xmloT, g->ny, g->nx, g->nyp, g->BW, RL);
+        // 2 w + c: image w (x, p, d) in layout c (rows, transposed); 6 + 2 w + c: its mirror
+        float *imgs[3][2] = {{P.x, P.xT}, {P.p, P.pT}, {P.d, P.dT}};
+        float *mimgs[3][2] = {{P.xm, P.xmT}, {P.pm, P.pmT}, {P.dm, P.dmT}};
+        for (int wi = 0; wi < 3; ++wi) {
+            e |= encode_map(&P.tm[2 * wi], imgs[wi][0], g->nx, g->ny, g->nxp, g->BW, kRowsPerChunk);
+            e |= encode_map(&P.tm[2 * wi + 1], imgs[wi][1], g->ny, g->nx, g->nyp, g->BW, kRowsPerChunk);
+            if (mir) {
+                e |= encode_map(&P.tm[6 + 2 * wi], mimgs[wi][0], g->nx, g->ny, g->nxp, g->BW, kRowsPerChunk);
+                e |= encode_map(&P.tm[7 + 2 * wi], mimgs[wi][1], g->ny, g->nx, g->nyp, g->BW, kRowsPerChunk);
+            }
         }
         if (e) { delete w; return SUPCG_ERR_CUDA; }
     }
@@ -1094,12 +1089,16 @@ static int enqueue_body(Workspace *w, const supcg_params *p, cudaStream_t st, in
         }
         dir = cnn_output(net);
     }
-    if (p->perturb && p->K > 0)                                                 // steps 11-12
+    // r = R x - b and f at x_{k+1/2}: r moves with x, by alpha q for step 7 (q = R p from the
+    // previous norm pass) and by R d for the displacement d of S_TV, which S_TV writes in the
+    // projector's layouts; the same sums as projecting x, in one pass over d
+    if (p->perturb && p->K > 0) {                                               // steps 11-12
         LAUNCH(SUPCG_KIND_STV, st, launch_stv(w->L(KT_STV, st), p->K, p->a, p->gamma, p->max_trials, nullptr,
                                               want_snorm, dir));
-    else                                                                        // (S_TV writes x^T itself)
-        LAUNCH(SUPCG_KIND_VECTOR, st, launch_transpose(w->L(KT_TR, st), 0));
-    LAUNCH(SUPCG_KIND_FORWARD, st, launch_forward(w->L(KT_FWD, st), w->L(KT_FWDA, st), 0, FWD_RESID));   // r = R x - b, f
+        LAUNCH(SUPCG_KIND_FORWARD, st, launch_forward(w->L(KT_FWD, st), w->L(KT_FWDA, st), 2, FWD_RUPD));
+    } else {
+        LAUNCH(SUPCG_KIND_VECTOR, st, launch_rupdate(w->L(KT_SINO, st)));
+    }
     // g = R^T r, and h = R^T q of the previous step (A p for this step's beta; the previous alpha
     // took p^T A p from ||q||^2), one pass over the views for both
     LAUNCH(SUPCG_KIND_BACKWARD, st, launch_backward2(w->L(KT_BWD2, st), w->bwin));

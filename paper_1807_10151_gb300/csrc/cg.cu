@@ -10,29 +10,6 @@ constexpr int kVecPerThread = 4;
 constexpr int kVecPerBlock = kRedThreads * kVecPerThread;   // elements per block of the vector kernels
 
 // ------------------------------------------------------------ layout staging
-__global__ void __launch_bounds__(256) k_transpose(const Prob *__restrict__ probs, const int *__restrict__ prefix,
-                                                   int count, int which)
-{
-    __shared__ float sh[32][33];
-    int local;
-    const Prob &P = probs[find_problem(prefix, count, blockIdx.x, &local)];
-    if (P.sc->done) return;
-    const float *src = which ? P.p : P.x;
-    float *dst = which ? P.pT : P.xT;
-    transpose_tile_m(src, P.nxp, dst, P.nyp, which ? P.pm : P.xm, which ? P.pmT : P.xmT, P.ny, P.nx, local, sh);
-    if (!which && P.xlo && P.xloT) {   // the iterate's low part, in the layouts the residual pass reads
-        __syncthreads();
-        transpose_tile_m(P.xlo, P.nxp, P.xloT, P.nyp, P.xmlo, P.xmloT, P.ny, P.nx, local, sh);
-    }
-}
-
-int launch_transpose(const Launch &L, int which)
-{
-    k_transpose<<<L.blocks, 256, 0, L.st>>>(L.probs, L.prefix, L.count, which);
-    SUPCG_CUDA_TRY(cudaGetLastError());
-    return SUPCG_OK;
-}
-
 __device__ __forceinline__ float load_user(const void *p, size_t i, int storage)
 {
     return storage == SUPCG_BF16 ? __bfloat162float(reinterpret_cast<const __nv_bfloat16 *>(p)[i])
@@ -57,7 +34,6 @@ __global__ void __launch_bounds__(256) k_stage_in(const Prob *__restrict__ probs
             (which ? P.g : P.x)[(size_t)i * P.nxp + j] = v;
             if (!which && P.xlo) P.xlo[(size_t)i * P.nxp + j] = 0.0f;   // x_0 is exactly its FP32 value
             if (!which && P.xm) P.xm[(size_t)i * P.nxp + (P.nx - 1 - j)] = v;
-            if (!which && P.xmlo) P.xmlo[(size_t)i * P.nxp + (P.nx - 1 - j)] = 0.0f;
         }
         sh[r][tx] = v;
     }
@@ -68,8 +44,6 @@ __global__ void __launch_bounds__(256) k_stage_in(const Prob *__restrict__ probs
         if (j < P.nx && i < P.ny) {
             P.xT[(size_t)j * P.nyp + i] = sh[tx][r];
             if (P.xmT) P.xmT[(size_t)(P.nx - 1 - j) * P.nyp + i] = sh[tx][r];
-            if (P.xloT) P.xloT[(size_t)j * P.nyp + i] = 0.0f;
-            if (P.xmloT) P.xmloT[(size_t)(P.nx - 1 - j) * P.nyp + i] = 0.0f;
         }
     }
 }
@@ -100,6 +74,50 @@ __global__ void __launch_bounds__(256) k_stage_sino(const Prob *__restrict__ pro
 int launch_stage_sino(const Launch &L, int which)
 {
     k_stage_sino<<<L.blocks, kRedThreads, 0, L.st>>>(L.probs, L.prefix, L.count, which);
+    SUPCG_CUDA_TRY(cudaGetLastError());
+    return SUPCG_OK;
+}
+
+// The residual of a while-body without S_TV (x_{k+1/2} = x_k): step 7 moved x by
+// alpha p, so r = R x - b moves by alpha q (q = R p, kept in FP64 by the norm pass),
+// and f = ||r||^2 (r^2 ||r||^2 + ||x - mu_X||^2 with the Bayesian criterion, completed
+// by the backprojector).  Sinogram grid (kVecPerBlock entries per block).
+__global__ void __launch_bounds__(kRedThreads) k_rupdate(const Prob *__restrict__ probs,
+                                                         const int *__restrict__ prefix, int count)
+{
+    __shared__ __align__(16) double red[40];
+    __shared__ int flag;
+    int local;
+    const int pi = find_problem(prefix, count, blockIdx.x, &local);
+    const Prob &P = probs[pi];
+    if (P.sc->done) return;
+    const double al = P.sc->alpha;
+    const size_t tot = (size_t)P.V * P.Up;   // padding bins stay 0: q is 0 there
+    df s = df_make(0.0f);
+    for (size_t e = (size_t)local * kVecPerBlock + threadIdx.x; e < tot && e < (size_t)(local + 1) * kVecPerBlock;
+         e += kRedThreads) {
+        const double rn = fma(al, P.qd[e], P.rd[e]);
+        const float rr = (float)rn;
+        P.rd[e] = rn;
+        P.r[e] = rr;
+        df_acc_prod(s, rr, rr);
+    }
+    const double bs = block_sum_df<kRedThreads>(s, red);
+    if (threadIdx.x == 0) P.partial[local] = bs;
+    const int nblk = prefix[pi + 1] - prefix[pi];
+    if (last_block(&P.counter[6], nblk, &flag)) {
+        const double tot_s = block_sum_array<kRedThreads>(P.partial, nblk, red);
+        if (threadIdx.x == 0) {
+            if (P.r2 > 0.0) P.sc->f_ls = tot_s;
+            else P.sc->f = tot_s;
+            P.counter[6] = 0;
+        }
+    }
+}
+
+int launch_rupdate(const Launch &L)
+{
+    k_rupdate<<<L.blocks, kRedThreads, 0, L.st>>>(L.probs, L.prefix, L.count);
     SUPCG_CUDA_TRY(cudaGetLastError());
     return SUPCG_OK;
 }

@@ -16,7 +16,6 @@ namespace supcg {
 constexpr int kMaxStages = 24;       // FFT stages (radices) per length
 constexpr int kMaxRadix = 64;        // largest prime factor handled by the generic butterfly
 constexpr int kRowsPerChunk = 16;    // forward projector: image rows staged per TMA box
-constexpr int kRowsPerChunkLo = 8;   // the same for the residual pass, whose chunks also hold the low part
 constexpr int kBwdTileI = 32;        // backprojector pixel tile (rows)
 constexpr int kBwdViewParts = 4;     // backprojector: default blocks per tile (view parts), each a share of the view chunks
 constexpr int kBwdMaxParts = 8;      // backprojector: most view parts per tile (supcg_set_bwd_parts)
@@ -198,10 +197,9 @@ struct Scal {
 // ----------------------------------------------------------------- problem
 // One problem of a batched launch (device copy lives in global memory).
 struct Prob {
-    CUtensorMap tm[18];    // TMA maps (FP32, padded pitches): 0 = x, 1 = x^T, 2 = p, 3 = p^T, 4-7 the same of
-                           // the mirrored images (only with mirror pairs); the residual pass's 8-row boxes:
-                           // 8 = x, 9 = x^T, 10 = xm, 11 = xm^T, 12 = xlo, 13 = xlo^T, 14 = xmlo, 15 = xmlo^T;
-                           // 16 = xlo, 17 = xlo^T in kRowsPerChunk-row boxes
+    CUtensorMap tm[12];    // TMA maps (FP32, padded pitches) of the projected images: 2 w + c for image w
+                           // (0 = x, 1 = p, 2 = d) in layout c (0 = rows, 1 = transposed); 6 + 2 w + c the
+                           // same of the mirrored images (only with mirror pairs)
     int nx, ny, V, U;
     int nxp, nyp, Up;      // pitches in elements: image, transposed image, sinogram
     int BU, BW, ntu;       // forward tiling: bins per tile, box width, bin tiles per view
@@ -245,10 +243,14 @@ struct Prob {
     // with mirror pairs: x and p mirrored left-right (xm[i][j] = x[i][nx-1-j]) and their
     // transposes, written with x^T and p^T for the forward projector (else null)
     float *xm, *xmT, *pm, *pmT;
-    // the iterate's low part in the projector's layouts: xlo^T, and with mirror pairs xlo
-    // mirrored and its transpose; the residual pass projects x + xlo (null: not kept)
-    float *xloT, *xmlo, *xmloT;
+    // the displacement d = x_{k+1/2} - x_k of S_TV (steps 11-12 of Algorithm 3) in the
+    // projector's layouts (dm, dmT only with mirror pairs): a while-body projects d, not x
+    float *d, *dT, *dm, *dmT;
+    // r = R x - b (FP32, read by the backprojector) and q = R p; rd and qd are the same in
+    // FP64, where the solve carries the residual from step to step:
+    // r_{k+1/2} = r_{k-1/2} + alpha_{k-1} q_{k-1} + R d_k, with the same sums as R x - b
     float *r, *q, *bpad;
+    double *rd, *qd;
     double2 *C;            // FFT scratch [ny][nx] (FP64 complex)
     float2 *Dtab;          // h(w_r) / (nx ny) at (min(k1, ny-k1), min(k2, nx-k2)), double-float: [ny/2+1][nx/2+1]
     float2 *bsplit;        // backprojector: each sinogram's and view part's pixel sums, double-float [2][bparts][ny][nxp]
@@ -473,49 +475,6 @@ __device__ __forceinline__ bool coop_barrier(unsigned *bar, unsigned nblocks, in
     return *sh_flag;
 }
 
-// 32 x 32 tile transpose through shared memory (256 threads).  src [ny][sp] ->
-// dst [nx][dp].  A caller looping over tiles syncs before reusing sh.
-__device__ __forceinline__ void transpose_tile(const float *src, int sp, float *dst, int dp, int ny, int nx,
-                                               int tile, float (*sh)[33])
-{
-    const int tiles_j = (nx + 31) / 32;
-    const int ti = tile / tiles_j, tj = tile - ti * tiles_j;
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 256 threads: 32 x 8
-    for (int r = ty; r < 32; r += 8) {
-        const int i = ti * 32 + r, j = tj * 32 + tx;
-        sh[r][tx] = (i < ny && j < nx) ? src[(size_t)i * sp + j] : 0.0f;
-    }
-    __syncthreads();
-    for (int r = ty; r < 32; r += 8) {
-        const int j = tj * 32 + r, i = ti * 32 + tx;
-        if (j < nx && i < ny) dst[(size_t)j * dp + i] = sh[tx][r];
-    }
-}
-
-// transpose_tile that also writes the left-right mirror of src (m[i][nx-1-j] = src[i][j],
-// pitch sp) and its transpose (mT[nx-1-j][i], pitch dp) when m is not null.
-__device__ __forceinline__ void transpose_tile_m(const float *src, int sp, float *dst, int dp, float *m, float *mT,
-                                                 int ny, int nx, int tile, float (*sh)[33])
-{
-    const int tiles_j = (nx + 31) / 32;
-    const int ti = tile / tiles_j, tj = tile - ti * tiles_j;
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 256 threads: 32 x 8
-    for (int r = ty; r < 32; r += 8) {
-        const int i = ti * 32 + r, j = tj * 32 + tx;
-        const float v = (i < ny && j < nx) ? src[(size_t)i * sp + j] : 0.0f;
-        sh[r][tx] = v;
-        if (m && i < ny && j < nx) m[(size_t)i * sp + (nx - 1 - j)] = v;
-    }
-    __syncthreads();
-    for (int r = ty; r < 32; r += 8) {
-        const int j = tj * 32 + r, i = ti * 32 + tx;
-        if (j < nx && i < ny) {
-            dst[(size_t)j * dp + i] = sh[tx][r];
-            if (mT) mT[(size_t)(nx - 1 - j) * dp + i] = sh[tx][r];
-        }
-    }
-}
-
 // ----------------------------------------------------------------- TMA / mbarrier
 __device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
@@ -585,7 +544,9 @@ int current_device(int *dev);
 
 // Launchers (defined in the kernel translation units).  Each enqueues one
 // kernel over all `count` problems of `probs` (device array) on `st`.
-enum FwdMode { FWD_RESID = 0, FWD_NORM = 1, FWD_PLAIN = 2 };
+// FWD_RESID: r = R x - b (steps 1-9); FWD_NORM: q = R p and alpha; FWD_PLAIN: the caller's
+// projection; FWD_RUPD: r <- r + alpha q + R d (a while-body with S_TV)
+enum FwdMode { FWD_RESID = 0, FWD_NORM = 1, FWD_PLAIN = 2, FWD_RUPD = 3 };
 enum BwdMode { BWD_G = 0, BWD_H = 1, BWD_PLAIN = 2 };
 
 struct Launch {
@@ -608,7 +569,6 @@ int launch_art(const Prob *d_prob, int cycles, double r, double lam, int S, int 
 int backward_blocks(int nx, int ny, int dual, int parts);
 int encode_tiled(CUtensorMap *m, CUtensorMapDataType type, int rank, void *base, const cuuint64_t *dims,
                  const cuuint64_t *strides_bytes, const cuuint32_t *box);
-int launch_transpose(const Launch &L, int which);          // x -> x^T (which 0) or p -> p^T (which 1)
 int launch_stage_in(const Launch &L, int which);           // caller image -> x and x^T (0) or g (1)
 int launch_stage_sino(const Launch &L, int which);         // caller sinogram -> r (0, in_user) or bpad (1, in_user2)
 int launch_store_out(const Launch &L, int which);          // padded image (0 x, 1 g, 2 z, 3 tbar) -> caller
@@ -619,6 +579,7 @@ int launch_gray(const Launch &L);                           // sc->muX from bpad
 int launch_pupdate(const Launch &L);
 int launch_beta(const Launch &L);
 int launch_xupdate(const Launch &L);
+int launch_rupdate(const Launch &L);   // r <- r + alpha q and f (a while-body without S_TV)
 int launch_gather_xt(const Launch &L, float *xs, float *ts);   // x, tbar of every problem -> [count][ny][nx]
 int launch_stv(const Launch &L, int K, double a, double gamma, long long max_trials, int *trials_out,
                int want_snorm, const float *dir = nullptr);

@@ -22,7 +22,7 @@ namespace supcg {
 // operand loads are plain shared-memory loads with 32-bit addresses.
 extern __shared__ __align__(128) float proj_dyn[];
 
-static_assert(kRowsPerChunk % 8 == 0 && kRowsPerChunkLo % 4 == 0, "chunks start at multiples of the fold groups");
+static_assert(kRowsPerChunk % 8 == 0, "chunks start at multiples of the fold groups");
 
 constexpr int kFwdBufs = 1;   // forward projector: staged boxes per warp (1: more resident warps hide the copies)
 
@@ -34,19 +34,14 @@ constexpr int kFwdBufs = 1;   // forward projector: staged boxes per warp (1: mo
 // split.  The terms of a group of G rows are summed in FP32 and added to the
 // ray's running sum with Kahan compensation (sum, comp), so that the ray sum
 // is accurate to about one unit in the last place of FP32 however many rows
-// it crosses.  G = 8, and 4 in the residual pass (LO): there the sums'
-// rounding, about halved, enters r = R x - b and through it the gradient,
-// on which the solver's step lengths depend most.
+// it crosses (groups of G = 8 rows).
 // MIR: the staged box is followed (moff floats later) by the same box of the
 // left-right mirrored image; each weight is also applied there, giving the ray
 // of the same bin in the mirror view (msum, mcomp: its compensated sum).
-// LO: the boxes of the iterate's low part follow (loff, lmoff floats later);
-// their weighted sums go to lsum (lmsum) in plain FP32: they are ~2^-24 of the
-// image's, so their own rounding is far below the image sum's.
-template <bool CLASS_B, bool AXIS, int NC, bool CHECKED, bool MIR, bool LO>
+template <bool CLASS_B, bool AXIS, int NC, bool CHECKED, bool MIR>
 __device__ __forceinline__ void fwd_rows(const Prob &P, const ViewP &vp, float tau_hi, float qm, int o0, int rb,
-                                         int re, int qs, int pbase, int moff, int loff, int lmoff, int *bad,
-                                         float &sum, float &comp, float &msum, float &mcomp, float &lsum, float &lmsum)
+                                         int re, int qs, int pbase, int moff, int *bad,
+                                         float &sum, float &comp, float &msum, float &mcomp)
 {
     const int BW = P.BW;
     // outer coordinate of row o0 + rb (pixel units) and its change per row
@@ -89,8 +84,6 @@ __device__ __forceinline__ void fwd_rows(const Prob &P, const ViewP &vp, float t
             const float w = weight_unit(ad, E, Sn, ESn, AXIS);
             rs = __fmaf_rn(w, pv[k], rs);
             if (MIR) ms = __fmaf_rn(w, pv[k + moff], ms);
-            if (LO) lsum = __fmaf_rn(w, pv[k + loff], lsum);
-            if (LO && MIR) lmsum = __fmaf_rn(w, pv[k + lmoff], lmsum);
         }
     };
     // Kahan-compensated fold of a group's sum; a group that summed to exactly 0 is
@@ -115,7 +108,7 @@ __device__ __forceinline__ void fwd_rows(const Prob &P, const ViewP &vp, float t
     };
     // groups of G rows aligned to multiples of G of the outer index (o0 is one), so
     // that a ray's sum does not depend on the rows its warp walks beyond its own
-    constexpr int G = LO ? 4 : 8;
+    constexpr int G = 8;
     int r = rb;
     float rf = __int2float_rn(rb);
     while (r < re) {
@@ -135,11 +128,10 @@ __device__ __forceinline__ void fwd_rows(const Prob &P, const ViewP &vp, float t
 // for both: the candidate index, the exact-split coordinates and each
 // candidate's weight (lane for lane the scalar IEEE steps of fwd_rows, so
 // the weights are the same bits).  Only for boxes that hold every candidate.
-template <bool CLASS_B, bool AXIS, int NC, bool MIR, bool LO>
+template <bool CLASS_B, bool AXIS, int NC, bool MIR>
 __device__ __forceinline__ void fwd_rows2(const Prob &P, const ViewP &vp, uint64_t tau2, uint64_t qm2, int o0, int rb,
-                                          int re, int qs, int pbase, int moff, int loff, int lmoff, const float4 *rtab,
-                                          float *sum, float *comp, float *msum, float *mcomp, uint64_t &lacc2,
-                                          uint64_t &lmacc2)
+                                          int re, int qs, int pbase, int moff, const float4 *rtab,
+                                          float *sum, float *comp, float *msum, float *mcomp)
 {
     const int BW = P.BW;
     const float hi_i = CLASS_B ? vp.su_hi : vp.cu_hi;   // coefficient of the inner coordinate
@@ -173,8 +165,6 @@ __device__ __forceinline__ void fwd_rows2(const Prob &P, const ViewP &vp, uint64
             const uint64_t w2 = pk2(weight_unit(fabsf(dA), E, Sn, ESn, AXIS), weight_unit(fabsf(dB), E, Sn, ESn, AXIS));
             acc2 = fma2_rn(w2, pk2(proj_dyn[pA + k], proj_dyn[pB + k]), acc2);
             if (MIR) macc2 = fma2_rn(w2, pk2(proj_dyn[pA + k + moff], proj_dyn[pB + k + moff]), macc2);
-            if (LO) lacc2 = fma2_rn(w2, pk2(proj_dyn[pA + k + loff], proj_dyn[pB + k + loff]), lacc2);
-            if (LO && MIR) lmacc2 = fma2_rn(w2, pk2(proj_dyn[pA + k + lmoff], proj_dyn[pB + k + lmoff]), lmacc2);
         }
     };
     auto fold = [&]() {   // Kahan-compensated folds of the group's sums, as in fwd_rows
@@ -204,7 +194,7 @@ __device__ __forceinline__ void fwd_rows2(const Prob &P, const ViewP &vp, uint64
             macc2 = pk2(0.0f, 0.0f);
         }
     };
-    constexpr int G = LO ? 4 : 8;   // rows per fold group, as in fwd_rows
+    constexpr int G = 8;   // rows per fold group, as in fwd_rows
     int r = rb;
     while (r < re) {   // groups aligned to multiples of G of the outer index, as in fwd_rows
         const int gend = min(re, (r & ~(G - 1)) + G);
@@ -263,36 +253,28 @@ __device__ __forceinline__ int fwd_box_start(const ViewP &vp, float tf, float tl
 // the box) and are dropped by the caller.
 // MIR: each chunk also stages the same box of the mirrored image (tm_m) right after the
 // image's, and acc_m receives the sums of the same bins in the mirror view.
-// LO: the chunk's rows of the low part (tm_l, and of its mirror tm_lm) follow, and the
-// rays sum x + xlo; the chunks are then kRowsPerChunkLo rows high, so that the four
-// boxes take the shared memory of two.
-template <bool CLASS_B, bool AXIS, int NC, bool MIR, bool LO, int RC>
+template <bool CLASS_B, bool AXIS, int NC, bool MIR>
 __device__ __forceinline__ void fwd_ray2(const Prob &P, const ViewP &vp, const CUtensorMap *tm, const CUtensorMap *tm_m,
-                                         const CUtensorMap *tm_l, const CUtensorMap *tm_lm, int patch0,
-                                         uint64_t *bars, float4 *rtab, int n_outer, int n_inner, int uA, int uB,
-                                         int u_last, float tf, float tl, int *bad, int *timed_out, double *acc,
+                                         int patch0, uint64_t *bars, float4 *rtab, int n_outer, int n_inner, int uA,
+                                         int uB, int u_last, float tf, float tl, int *bad, int *timed_out, double *acc,
                                          double *acc_m)
 {
-    constexpr int NBOX = (MIR ? 2 : 1) * (LO ? 2 : 1);
+    constexpr int RC = kRowsPerChunk;
     const int BW = P.BW;
     const int box_elems = RC * BW;
-    // one staged chunk: the image's box, the mirror's, the low part's, its mirror's
-    const int buf_elems = NBOX * box_elems;
-    const int moff = box_elems, loff = (MIR ? 2 : 1) * box_elems, lmoff = loff + box_elems;
+    // one staged chunk: the image's box, then the mirror's
+    const int buf_elems = (MIR ? 2 : 1) * box_elems;
+    const int moff = box_elems;
     const int lane = threadIdx.x & 31;
     const int uc[2] = {min(uA, u_last), min(uB, u_last)};
     float tau_hi[2], base[2], sum[2] = {0.0f, 0.0f}, comp[2] = {0.0f, 0.0f};
     float msum[2] = {0.0f, 0.0f}, mcomp[2] = {0.0f, 0.0f};
-    float lsum[2] = {0.0f, 0.0f}, lmsum[2] = {0.0f, 0.0f};
-    uint64_t lacc2 = pk2(0.0f, 0.0f), lmacc2 = pk2(0.0f, 0.0f);   // the packed path's low-part sums
     // the chunk's boxes, in their order in the buffer
     auto issue = [&](int slot, int qs, int c) {
         float *dst = proj_dyn + patch0 + slot * buf_elems;
         mbar_expect_tx(&bars[slot], buf_elems * 4);
         tma_load_2d(dst, tm, qs, c * RC, &bars[slot]);
         if (MIR) tma_load_2d(dst + moff, tm_m, qs, c * RC, &bars[slot]);
-        if (LO) tma_load_2d(dst + loff, tm_l, qs, c * RC, &bars[slot]);
-        if (LO && MIR) tma_load_2d(dst + lmoff, tm_lm, qs, c * RC, &bars[slot]);
     };
     int r_lo = n_outer, r_hi = -1;
 #pragma unroll
@@ -342,14 +324,13 @@ __device__ __forceinline__ void fwd_ray2(const Prob &P, const ViewP &vp, const C
             // axis-aligned views (two in a uniform set) take the scalar path: no packed copy of
             // the row loop for them, less code competing for the instruction cache
             if (!AXIS && inside) {
-                fwd_rows2<CLASS_B, AXIS, NC, MIR, LO>(P, vp, tau2, pk2(qm[0], qm[1]), o0, rb, re, qs, pb, moff, loff,
-                                                      lmoff, rtab, sum, comp, msum, mcomp, lacc2, lmacc2);
+                fwd_rows2<CLASS_B, AXIS, NC, MIR>(P, vp, tau2, pk2(qm[0], qm[1]), o0, rb, re, qs, pb, moff, rtab, sum,
+                                                  comp, msum, mcomp);
             } else {
 #pragma unroll
                 for (int q = 0; q < 2; ++q)
-                    fwd_rows<CLASS_B, AXIS, NC, true, MIR, LO>(P, vp, tau_hi[q], qm[q], o0, rb, re, qs, pb, moff, loff,
-                                                               lmoff, bad, sum[q], comp[q], msum[q], mcomp[q], lsum[q],
-                                                               lmsum[q]);
+                    fwd_rows<CLASS_B, AXIS, NC, true, MIR>(P, vp, tau_hi[q], qm[q], o0, rb, re, qs, pb, moff, bad, sum[q],
+                                                           comp[q], msum[q], mcomp[q]);
             }
         }
         // every lane is done with this buffer; a timeout in any lane ends the warp's loop
@@ -367,21 +348,10 @@ __device__ __forceinline__ void fwd_ray2(const Prob &P, const ViewP &vp, const C
             if (lane == 0) issue(buf, qs_buf[buf], c + kFwdBufs);
         }
     }
-    if (LO) {   // the packed path's low-part sums join the scalar path's
-        float a, b;
-        upk2(lacc2, a, b);
-        lsum[0] = __fadd_rn(lsum[0], a);
-        lsum[1] = __fadd_rn(lsum[1], b);
-        if (MIR) {
-            upk2(lmacc2, a, b);
-            lmsum[0] = __fadd_rn(lmsum[0], a);
-            lmsum[1] = __fadd_rn(lmsum[1], b);
-        }
-    }
 #pragma unroll
     for (int q = 0; q < 2; ++q) {   // weights in units of P
-        acc[q] = ((double)sum[q] - (double)comp[q] + (LO ? (double)lsum[q] : 0.0)) * (double)vp.P;
-        if (MIR) acc_m[q] = ((double)msum[q] - (double)mcomp[q] + (LO ? (double)lmsum[q] : 0.0)) * (double)vp.P;
+        acc[q] = ((double)sum[q] - (double)comp[q]) * (double)vp.P;
+        if (MIR) acc_m[q] = ((double)msum[q] - (double)mcomp[q]) * (double)vp.P;
     }
 }
 
@@ -390,16 +360,13 @@ constexpr int kFwdThreads = 64;   // two warps of 64 rays: 128 bins per block at
 // MIRK: some problem of the launch has mirror pairs of views.  An item of a pair's first
 // view then also sums the second view's rays from the mirrored image's boxes (two boxes
 // per chunk, so fewer blocks fit: this variant is compiled for 7 resident blocks, the
-// other for 10, 8 in the residual pass).  LO: the residual pass of a solve, which projects the iterate with its
-// low part (x + xlo); its chunks are half as high and hold twice the boxes, so the shared
-// memory per block is the same.
-template <bool MIRK, bool LO>
-__global__ void __launch_bounds__(kFwdThreads, MIRK ? 7 : (LO ? 8 : 10)) k_forward(const Prob *__restrict__ probs,
-                                                                    const int *__restrict__ prefix, int count,
-                                                                    int which, int mode)
+// other for 10).  which: the image projected (0 = x, 1 = p, 2 = d); mode: FwdMode.
+template <bool MIRK>
+__global__ void __launch_bounds__(kFwdThreads, MIRK ? 7 : 10) k_forward(const Prob *__restrict__ probs,
+                                                                        const int *__restrict__ prefix, int count,
+                                                                        int which, int mode)
 {
-    // proj_dyn: [warp][kFwdBufs][box: x, (MIRK) mirror, (LO) low part, (MIRK, LO) its mirror][RC][BW],
-    // RC = kRowsPerChunkLo rows with LO, else kRowsPerChunk
+    // proj_dyn: [warp][kFwdBufs][box: the image, (MIRK) its mirror][kRowsPerChunk][BW]
     __shared__ __align__(8) uint64_t bars[kFwdBufs * (kFwdThreads / 32)];   // one per staged box
     __shared__ float4 rowtab[kFwdThreads / 32][kRowsPerChunk];             // each warp's row terms
     __shared__ __align__(16) double red[40];
@@ -428,14 +395,10 @@ __global__ void __launch_bounds__(kFwdThreads, MIRK ? 7 : (LO ? 8 : 10)) k_forwa
     const bool axis = (vp.flags & kViewAxis) != 0;
     const int n_outer = classB ? P.nx : P.ny, n_inner = classB ? P.ny : P.nx;
     const int cb = classB ? 1 : 0;
-    const bool rc8 = MIRK && LO;
-    const CUtensorMap *tm = rc8 ? &P.tm[8 + cb] : &P.tm[which * 2 + cb];
-    const CUtensorMap *tm_m = rc8 ? &P.tm[10 + cb] : &P.tm[4 + which * 2 + cb];
-    const CUtensorMap *tm_l = rc8 ? &P.tm[12 + cb] : &P.tm[16 + cb], *tm_lm = &P.tm[14 + cb];
-    // rows per chunk: with both the mirror's and the low part's boxes, half as many
-    constexpr int RCK = (MIRK && LO) ? kRowsPerChunkLo : kRowsPerChunk;
+    const CUtensorMap *tm = &P.tm[which * 2 + cb];
+    const CUtensorMap *tm_m = &P.tm[6 + which * 2 + cb];
     // this warp's boxes in proj_dyn
-    const int patch0 = warp * kFwdBufs * (MIRK ? 2 : 1) * (LO ? 2 : 1) * RCK * P.BW;
+    const int patch0 = warp * kFwdBufs * (MIRK ? 2 : 1) * kRowsPerChunk * P.BW;
     uint64_t *wbars = bars + kFwdBufs * warp;
 
     const int u_first = tile * P.BU;
@@ -456,8 +419,8 @@ __global__ void __launch_bounds__(kFwdThreads, MIRK ? 7 : (LO ? 8 : 10)) k_forwa
     // axis-aligned views meet at most two pixels per row; near-diagonal ones up to three
     const bool three = (vp.flags & kViewFwd3) != 0;
 #define SUPCG_FWD(CB, AX, NC, MIR) \
-    fwd_ray2<CB, AX, NC, MIR, LO, RCK>(P, vp, tm, tm_m, tm_l, tm_lm, patch0, wbars, rowtab[warp], n_outer, n_inner, uA, uB, \
-                                  u_last, tf, tl, &bad, &timed_out, acc, acc_m)
+    fwd_ray2<CB, AX, NC, MIR>(P, vp, tm, tm_m, patch0, wbars, rowtab[warp], n_outer, n_inner, uA, uB, u_last, tf, tl, \
+                              &bad, &timed_out, acc, acc_m)
     if (idle) {
         // no item for this warp
     } else if (MIRK && vm >= 0) {   // a pair (never axis-aligned: those have no mirror partner)
@@ -480,22 +443,28 @@ __global__ void __launch_bounds__(kFwdThreads, MIRK ? 7 : (LO ? 8 : 10)) k_forwa
 
     // epilogue: store, fused residual / norm reduction (exact squares, double-float sums)
     df s = df_make(0.0f);
+    const double al = (mode == FWD_RUPD) ? P.sc->alpha : 0.0;   // alpha of the step x just took
     // the item's view, then (a mirror pair) the partner view: the same bins, sums acc_m
     auto emit = [&](int view, double a, int u) {
         if (mode == FWD_PLAIN) {
             const size_t o = (size_t)view * P.U + u;
             if (P.storage == SUPCG_BF16) reinterpret_cast<__nv_bfloat16 *>(P.out_user)[o] = __double2bfloat16(a);
             else reinterpret_cast<float *>(P.out_user)[o] = (float)a;
-        } else if (mode == FWD_RESID) {
-            const size_t o = (size_t)view * P.Up + u;
-            const float rr = (float)(a - (double)P.bpad[o]);   // r = R x - b, cancellation taken in FP64
-            P.r[o] = rr;
-            df_acc_prod(s, rr, rr);
-        } else {
+        } else if (mode == FWD_NORM) {
             const size_t o = (size_t)view * P.Up + u;
             const float qq = (float)a;
             P.q[o] = qq;
+            P.qd[o] = a;
             df_acc_prod(s, qq, qq);
+        } else {
+            // FWD_RESID: r = R x - b, the cancellation taken in FP64; FWD_RUPD: x moved by
+            // alpha p (step 7) and then by d (S_TV), so r moves by alpha q + R d
+            const size_t o = (size_t)view * P.Up + u;
+            const double rn = (mode == FWD_RESID) ? a - (double)P.bpad[o] : fma(al, P.qd[o], P.rd[o]) + a;
+            const float rr = (float)rn;
+            P.rd[o] = rn;
+            P.r[o] = rr;
+            df_acc_prod(s, rr, rr);
         }
     };
 #pragma unroll
@@ -516,7 +485,7 @@ __global__ void __launch_bounds__(kFwdThreads, MIRK ? 7 : (LO ? 8 : 10)) k_forwa
         const double tot = block_sum_array<kFwdThreads>(P.partial, nblk, red);
         if (t == 0) {
             Scal *sc = P.sc;
-            if (mode == FWD_RESID) {
+            if (mode != FWD_NORM) {
                 if (P.r2 > 0.0) {
                     sc->f_ls = tot;   // f = r^2 ||r||^2 + ||x - mu_X||^2 is completed by the backprojector
                 } else {
@@ -562,28 +531,24 @@ __global__ void __launch_bounds__(kFwdThreads, MIRK ? 7 : (LO ? 8 : 10)) k_forwa
     }
 }
 
-template <bool MIRK, bool LO>
+template <bool MIRK>
 static int launch_forward_t(const Launch &L, int which, int mode)
 {
     // every problem's BW <= 256, so the warps' box buffers never exceed this size; with mirror
-    // pairs each chunk holds two boxes, and in the residual pass two more of half the rows
-    constexpr int rows = (MIRK && LO) ? 4 * kRowsPerChunkLo : (MIRK || LO) ? 2 * kRowsPerChunk : kRowsPerChunk;
+    // pairs each chunk holds two boxes
+    constexpr int rows = (MIRK ? 2 : 1) * kRowsPerChunk;
     const int per_warp = kFwdBufs * rows;
     const int smem = (kFwdThreads / 32) * per_warp * L.bw_max * 4;
-    int rc = func_attrs_once((const void *)k_forward<MIRK, LO>, (kFwdThreads / 32) * per_warp * 256 * 4);
+    int rc = func_attrs_once((const void *)k_forward<MIRK>, (kFwdThreads / 32) * per_warp * 256 * 4);
     if (rc) return rc;
-    k_forward<MIRK, LO><<<L.blocks, kFwdThreads, smem, L.st>>>(L.probs, L.prefix, L.count, which, mode);
+    k_forward<MIRK><<<L.blocks, kFwdThreads, smem, L.st>>>(L.probs, L.prefix, L.count, which, mode);
     SUPCG_CUDA_TRY(cudaGetLastError());
     return SUPCG_OK;
 }
 
 int launch_forward(const Launch &L, const Launch &La, int which, int mode)
 {
-    // the solver's residual pass projects x + xlo (the iterate's low part is kept by every solve)
-    const bool lo = mode == FWD_RESID && which == 0;
-    if (L.mirror)
-        return lo ? launch_forward_t<true, true>(L, which, mode) : launch_forward_t<true, false>(L, which, mode);
-    return lo ? launch_forward_t<false, true>(La, which, mode) : launch_forward_t<false, false>(La, which, mode);
+    return L.mirror ? launch_forward_t<true>(L, which, mode) : launch_forward_t<false>(La, which, mode);
 }
 
 } // namespace supcg

@@ -211,6 +211,9 @@ __device__ __forceinline__ double phase_sum_of(const Prob &P, int nb, int slot, 
 // S_TV(x, l, a, gamma, K), Algorithm 1, in place on P.x (one cooperative launch).
 // trials_out (nullable): [count][K] trials of every nonascending step.  dir (nullable):
 // the learned proposals, [count][ny][nx] (every problem of the launch has the same size).
+// Also writes the displacement d = x_{k+1/2} - x_k in the forward projector's layouts
+// (P.d, P.dT and, with mirror pairs, P.dm, P.dmT), which a while-body projects to move
+// the residual.
 __global__ void __launch_bounds__(kTvThreads, 3) k_stv(const Prob *__restrict__ probs, const int *__restrict__ prefix,
                                                     int count, int K_arg, double a_arg, double gamma_arg,
                                                     long long max_trials, int *trials_out, int want_snorm,
@@ -221,9 +224,8 @@ __global__ void __launch_bounds__(kTvThreads, 3) k_stv(const Prob *__restrict__ 
     __shared__ int flag;
     __shared__ double sh_inv;   // grid-uniform FP64 scalars: computed by thread 0, read by all
     __shared__ float sh_c;
-    __shared__ float sh_t[32][33];   // tile transposes of x
-    __shared__ float sh_l[32][33];   // and of its low part
-    bool xt_done = false;            // the last step wrote x^T
+    __shared__ float sh_t[32][33];   // tile transposes of d
+    bool d_done = false;             // the last step wrote d
     int local;
     const int pi = find_problem(prefix, count, blockIdx.x, &local);
     const Prob &P = probs[pi];
@@ -247,10 +249,53 @@ __global__ void __launch_bounds__(kTvThreads, 3) k_stv(const Prob *__restrict__ 
     double tv_first = 0.0, tv_last = 0.0;
     int slot = 0;   // partial buffers alternate between two slots (pairs of slots for 2-value phases)
     bool ok = true;
+    // x_k is saved before the steps unless one plain step (K = 1) gives d as c tbar itself
+    const bool saved = want_snorm || dir || K != 1;
+    // d on the 32 x 32 tiles this block owns, in the row layout and transposed (and mirrored
+    // with mirror pairs).  step: the last step y <- y + c tbar is taken here, pixel by pixel
+    // (no block reads another's pixels after it, so no grid barrier follows); zero: no step
+    // moved x.  Otherwise d = x - x_k from the copy saved before the steps, which a grid
+    // barrier separates from here.
+    auto write_d = [&](bool step, bool zero, float c) {
+        const int tiles_j = (nx + 31) / 32, tiles = ((ny + 31) / 32) * tiles_j;
+        const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 256 threads: 32 x 8
+        for (int tile = local; tile < tiles; tile += nb) {
+            const int ti = tile / tiles_j, tj = tile - ti * tiles_j;
+            for (int r = ty; r < 32; r += 8) {
+                const int i = ti * 32 + r, j = tj * 32 + tx;
+                float dv = 0.0f;
+                if (i < ny && j < nx) {
+                    const size_t p = (size_t)i * ld + j;
+                    float v, vl;
+                    if (step) {
+                        const float t = tb[p];
+                        v = x_step(x, xl, p, c, t, &vl);
+                        if (!saved) dv = __fmul_rn(c, t);
+                    } else {
+                        v = x[p];
+                        vl = xl ? xl[p] : 0.0f;
+                    }
+                    if (saved && !zero) dv = __fadd_rn(__fsub_rn(v, P.z[p]), __fsub_rn(vl, P.g[p]));
+                    P.d[p] = dv;
+                    if (P.dm) P.dm[(size_t)i * ld + (nx - 1 - j)] = dv;
+                }
+                sh_t[r][tx] = dv;
+            }
+            __syncthreads();
+            for (int r = ty; r < 32; r += 8) {
+                const int j = tj * 32 + r, i = ti * 32 + tx;
+                if (j < nx && i < ny) {
+                    P.dT[(size_t)j * P.nyp + i] = sh_t[tx][r];
+                    if (P.dmT) P.dmT[(size_t)(nx - 1 - j) * P.nyp + i] = sh_t[tx][r];
+                }
+            }
+            __syncthreads();
+        }
+    };
 
-    // ||s_k||^2 for the log: the iterate before the steps (high part in z, low part in g;
-    // both are recomputed after S_TV in a while body)
-    if (want_snorm)
+    // the iterate before the steps, high part in z and low part in g (both are recomputed
+    // after S_TV in a while-body), for ||s_k||^2 of the log and for d
+    if (saved)
         for (int e = e0; e < n; e += stride) {
             const int i = e / nx, j = e - i * nx;
             const size_t p = (size_t)i * ld + j;
@@ -451,39 +496,9 @@ __global__ void __launch_bounds__(kTvThreads, 3) k_stv(const Prob *__restrict__ 
         total_trials += trials;
         if (!ok) break;
         if (trials_out && local == 0 && threadIdx.x == 0) trials_out[(size_t)pi * K + step] = (int)trials;
-        if (step == K - 1 && !want_snorm) {
-            // the last step: y <- y~ on 32 x 32 tiles this block owns, written in both layouts
-            // (x^T for the forward projector); no block reads another's pixels after it, so no
-            // grid barrier follows
-            const int tiles_j = (nx + 31) / 32, tiles = ((ny + 31) / 32) * tiles_j;
-            const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 256 threads: 32 x 8
-            for (int tile = local; tile < tiles; tile += nb) {
-                const int ti = tile / tiles_j, tj = tile - ti * tiles_j;
-                for (int r = ty; r < 32; r += 8) {
-                    const int i = ti * 32 + r, j = tj * 32 + tx;
-                    float v = 0.0f, vl = 0.0f;
-                    if (i < ny && j < nx) {
-                        const size_t p = (size_t)i * ld + j;
-                        v = x_step(x, xl, p, c, tb[p], &vl);
-                        if (P.xm) P.xm[(size_t)i * ld + (nx - 1 - j)] = v;
-                        if (P.xmlo) P.xmlo[(size_t)i * ld + (nx - 1 - j)] = vl;
-                    }
-                    sh_t[r][tx] = v;
-                    sh_l[r][tx] = vl;
-                }
-                __syncthreads();
-                for (int r = ty; r < 32; r += 8) {
-                    const int j = tj * 32 + r, i = ti * 32 + tx;
-                    if (j < nx && i < ny) {
-                        P.xT[(size_t)j * P.nyp + i] = sh_t[tx][r];
-                        if (P.xmT) P.xmT[(size_t)(nx - 1 - j) * P.nyp + i] = sh_t[tx][r];
-                        if (P.xloT) P.xloT[(size_t)j * P.nyp + i] = sh_l[tx][r];
-                        if (P.xmloT) P.xmloT[(size_t)(nx - 1 - j) * P.nyp + i] = sh_l[tx][r];
-                    }
-                }
-                __syncthreads();
-            }
-            xt_done = true;
+        if (step == K - 1 && !want_snorm) {   // the last step, with d
+            write_d(true, false, c);
+            d_done = true;
         } else {
             for (PixWalk w(e0, stride, nx); w.i < ny;) {   // y <- y~
                 size_t gp[kStvGroup];
@@ -520,16 +535,9 @@ __global__ void __launch_bounds__(kTvThreads, 3) k_stv(const Prob *__restrict__ 
         sc->tv_half = (K > 0) ? tv_last : tv_first;
         sc->snorm2 = sn;
     }
-    // x^T of x_{k+1/2} for the forward projector's column-walking views, unless the last
-    // step wrote it (after the last barrier every block sees the final x)
-    if (ok && !xt_done) {
-        const int tiles = ((ny + 31) / 32) * ((nx + 31) / 32);
-        for (int tile = local; tile < tiles; tile += nb) {
-            transpose_tile_m(x, ld, P.xT, P.nyp, P.xm, P.xmT, ny, nx, tile, sh_t);
-            if (xl && P.xloT) transpose_tile_m(xl, ld, P.xloT, P.nyp, P.xmlo, P.xmloT, ny, nx, tile, sh_l);
-            __syncthreads();
-        }
-    }
+    // d, unless the last step wrote it (after the last barrier every block sees the final x);
+    // no step ran when the plain loop had none (K = 0), and then no barrier either
+    if (ok && !d_done) write_d(false, plain && K == 0, 0.0f);
 }
 
 int stv_max_blocks_per_sm(int *out)
