@@ -250,7 +250,7 @@ static std::vector<int> block_order(const supcg_geometry_s *g, bool pair)
 }
 
 // The forward projector's two item lists: with mirror pairs (the paired kernel) and
-// with every view (the residual pass, which projects x + xlo view by view).
+// with every view (the unpaired kernel, for launches in which no problem has mirror pairs).
 static int upload_block_order(supcg_geometry_s *g)
 {
     const std::vector<int> all = block_order(g, false);

@@ -177,7 +177,7 @@ struct Scal {
     double tv_k, tv_half;  // TV(x_k), TV(x_{k+1/2}) of the last S_TV call
     double snorm2;     // ||s_k||^2 of the last S_TV call (accumulated in FP64)
     double eps;
-    double f_ls;       // Bayesian criterion: ||R x - b||^2 of the most recent residual projection
+    double f_ls;       // Bayesian criterion: ||R x - b||^2 of the current residual
     double muX;        // Bayesian criterion: the gray level mu_X of Eq. (2.3)
     double pp;         // ||p||^2 of the current p (h = r^2 R^T R p + p for the Bayesian criterion)
     long long ell;     // l of Algorithm 1/3
