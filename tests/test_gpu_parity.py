@@ -279,8 +279,9 @@ def test_solve_variants_match_oracle(perturb, precond, iters):
 
     Without the TV perturbation, CG with FP32 vectors parts from CG with FP64
     vectors once its residual has collapsed (loss of conjugacy): on this
-    problem the GPU's PCG is 7e-7 from the oracle at 10 iterations and 6e-2 at
-    20, its CG 3e-6 at 6 and 1e-2 at 10.  So the unperturbed variants' iterate
+    problem the GPU's PCG is 1.3e-6 from the oracle at 10 iterations, 3.9e-4 at
+    15 and 5.6e-2 at 20, its CG 2.7e-7 at 6 and 1.3e-3 at 10 (the FP32 p, z, q
+    and h, not the residual, which is carried in FP64).  So the unperturbed variants' iterate
     parity stops there, and longer runs are checked by properties below.  The
     perturbed SupCG stays within 1e-6 over the 50 iterations."""
     og, R, x_true, b = config1_problem(seed=1002, N=48, V=60, U=70)
