@@ -188,10 +188,15 @@ struct Scal {
     int init;          // 1 while running steps 2-7 (beta forced to 0)
     int n_fallback;    // learned perturbation: proposals rejected by the nonascent test
     int n_learned;     // learned perturbation: proposals accepted
+    // a^l of Algorithm 1 for l = apow_ell and a = apow_a (valid when apow_ok), advanced by
+    // one factor a per S_TV trial, so that a call needs no FP64 pow (slow on the narrow FP64
+    // pipe, and on the critical path of every trial) unless l or a changed elsewhere
+    double apow, apow_a;
+    long long apow_ell;
+    int apow_ok;
     // alpha as two FP32 parts (alpha_h + alpha_l to ~2^-48) and beta rounded to FP32, written
     // with alpha and beta, so that the vector kernels read them without FP64 arithmetic
     float alpha_h, alpha_l, beta_f;
-    int pad[1];
 };
 
 // ----------------------------------------------------------------- problem
@@ -427,6 +432,57 @@ __device__ __forceinline__ double block_sum_array(const volatile double *partial
     double r = sh[32];
     __syncthreads();
     return r;
+}
+
+// Two such sums in one pass (both arrays' loads in flight together, one reduction sweep):
+// the same values as two calls of block_sum_array.  Results in all threads.
+template <int NT>
+__device__ __forceinline__ void block_sum_array2(const volatile double *pa, const volatile double *pb, int n, double *sh,
+                                                 double *ra, double *rb)
+{
+    double va = 0.0, vb = 0.0;
+    for (int i = threadIdx.x; i < n; i += NT) {
+        va += pa[i];
+        vb += pb[i];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        va += __shfl_down_sync(0xffffffffu, va, o);
+        vb += __shfl_down_sync(0xffffffffu, vb, o);
+    }
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    if (l == 0) {
+        sh[w] = va;
+        sh[16 + w] = vb;
+    }
+    __syncthreads();
+    if (w == 0) {
+        double a = (l < NT / 32) ? sh[l] : 0.0, b = (l < NT / 32) ? sh[16 + l] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_down_sync(0xffffffffu, a, o);
+            b += __shfl_down_sync(0xffffffffu, b, o);
+        }
+        if (l == 0) {
+            sh[32] = a;
+            sh[33] = b;
+        }
+    }
+    __syncthreads();
+    *ra = sh[32];
+    *rb = sh[33];
+    __syncthreads();
+}
+
+// 1 / sqrt(s) for s > 0: an FP32 seed and two Newton steps in FP64 (multiplies and FMAs
+// only; the FP64 square root and division routines are long on the narrow FP64 pipe)
+__device__ __forceinline__ double rsqrt_fp64(double s)
+{
+    if (!(s > 1e-30 && s < 1e30)) return 1.0 / sqrt(s);   // outside the FP32 seed's range
+    double y = (double)rsqrtf((float)s);
+    y = y * fma(-0.5 * s, y * y, 1.5);
+    y = y * fma(-0.5 * s, y * y, 1.5);
+    return y;
 }
 
 // Last-block-done ticket: true in every thread of the block that finishes last.

@@ -245,6 +245,14 @@ __global__ void __launch_bounds__(kTvThreads, 3) k_stv(const Prob *__restrict__ 
     if (dir) dir += (size_t)pi * ny * nx;
     float *tb = P.tbar;
     long long ell = sc->ell;
+    // a^ell, carried from trial to trial and from call to call (Scal::apow); thread 0's, kept
+    // in shared memory so that it takes no registers through the passes
+    __shared__ double sh_apow;
+    __shared__ int sh_apow_ok;
+    if (threadIdx.x == 0) {
+        sh_apow_ok = sc->apow_ok && sc->apow_ell == ell && sc->apow_a == a;
+        sh_apow = sh_apow_ok ? sc->apow : 0.0;
+    }
     long long total_trials = 0;
     double tv_first = 0.0, tv_last = 0.0;
     int slot = 0;   // partial buffers alternate between two slots (pairs of slots for 2-value phases)
@@ -350,7 +358,7 @@ __global__ void __launch_bounds__(kTvThreads, 3) k_stv(const Prob *__restrict__ 
             plain = false;
             // the step scalars are the same in every thread: thread 0 evaluates the FP64
             // functions and the block reads the result (the FP64 pipe is narrow)
-            if (threadIdx.x == 0) sh_inv = 1.0 / sqrt(s_nn);
+            if (threadIdx.x == 0) sh_inv = rsqrt_fp64(s_nn);
             long long j = 0;
             float c = 0.0f;
             double tv_t = 0.0;
@@ -391,6 +399,7 @@ __global__ void __launch_bounds__(kTvThreads, 3) k_stv(const Prob *__restrict__ 
                 }
                 ok = coop_barrier(P.bar, nb + P.bar_extra, &sc->status, &flag, P.wait_limit);
                 ell += (long long)K + (j - 1);
+                if (threadIdx.x == 0) sh_apow_ok = 0;
                 total_trials = j;
                 tv_first = s_tv;
                 tv_last = tv_t;
@@ -436,15 +445,15 @@ __global__ void __launch_bounds__(kTvThreads, 3) k_stv(const Prob *__restrict__ 
             }
             ok = coop_barrier(P.bar, nb + P.bar_extra, &sc->status, &flag, P.wait_limit);
             if (!ok) break;
-            s_tv = block_sum_array<kTvThreads>(P.partial + (size_t)(4 + 2 * slot) * nb, nb, red);
-            s_nn = block_sum_array<kTvThreads>(P.partial + (size_t)(5 + 2 * slot) * nb, nb, red);
+            block_sum_array2<kTvThreads>(P.partial + (size_t)(4 + 2 * slot) * nb, P.partial + (size_t)(5 + 2 * slot) * nb,
+                                         nb, red, &s_tv, &s_nn);
             slot ^= 1;
         }
         const double tv_y = s_tv;
         if (step == 0) tv_first = tv_y;
         // the step scalars are the same in every thread: thread 0 evaluates the FP64
         // functions and the block reads the result (the FP64 pipe is narrow)
-        if (threadIdx.x == 0) sh_inv = (s_nn > 0.0) ? 1.0 / sqrt(s_nn) : 0.0;
+        if (threadIdx.x == 0) sh_inv = (s_nn > 0.0) ? rsqrt_fp64(s_nn) : 0.0;
         long long trials = 0;
         float c = 0.0f;
         double tv_t = 0.0;
@@ -454,7 +463,12 @@ __global__ void __launch_bounds__(kTvThreads, 3) k_stv(const Prob *__restrict__ 
                 ok = false;
                 break;
             }
-            if (threadIdx.x == 0) sh_c = (float)(gamma * pow(a, (double)ell) * sh_inv);   // gamma a^l / ||tbar||
+            if (threadIdx.x == 0) {
+                const double ap = sh_apow_ok ? sh_apow : pow(a, (double)ell);
+                sh_c = (float)(gamma * ap * sh_inv);   // gamma a^l / ||tbar||
+                sh_apow = ap * a;                      // a^(l + 1), for the next trial
+                sh_apow_ok = 1;
+            }
             __syncthreads();
             c = sh_c;                                                                     // y~ = y + c tbar
             ++ell;
@@ -530,6 +544,10 @@ __global__ void __launch_bounds__(kTvThreads, 3) k_stv(const Prob *__restrict__ 
     }
     if (local == 0 && threadIdx.x == 0) {
         sc->ell = ell;
+        sc->apow = sh_apow;
+        sc->apow_a = a;
+        sc->apow_ell = ell;
+        sc->apow_ok = sh_apow_ok;
         sc->trials = total_trials;
         sc->tv_k = tv_first;
         sc->tv_half = (K > 0) ? tv_last : tv_first;
