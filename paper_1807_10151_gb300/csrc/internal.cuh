@@ -420,12 +420,23 @@ __device__ __forceinline__ void block_sum_df2(df a, df b, double *sh, double *ra
     __syncthreads();
 }
 
-// Sum partial[0..n) in a fixed order with the whole block; result in all threads.
+// Sum partial[0..n) in a fixed order with the whole block; result in all threads.  The
+// partials come from other blocks (published by a grid barrier or the last-block ticket,
+// both fenced): they are read from L2 (__ldcg, not the non-coherent L1), eight per thread
+// in flight, and added in the same order as one by one.
 template <int NT>
-__device__ __forceinline__ double block_sum_array(const volatile double *partial, int n, double *sh)
+__device__ __forceinline__ double block_sum_array(const double *partial, int n, double *sh)
 {
     double v = 0.0;
-    for (int i = threadIdx.x; i < n; i += NT) v += partial[i];
+    int i = threadIdx.x;
+    for (; i + 7 * NT < n; i += 8 * NT) {
+        double t[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) t[k] = __ldcg(partial + i + k * NT);
+#pragma unroll
+        for (int k = 0; k < 8; ++k) v += t[k];
+    }
+    for (; i < n; i += NT) v += __ldcg(partial + i);
     v = block_sum<NT>(v, sh);
     if (threadIdx.x == 0) sh[32] = v;
     __syncthreads();
@@ -437,13 +448,27 @@ __device__ __forceinline__ double block_sum_array(const volatile double *partial
 // Two such sums in one pass (both arrays' loads in flight together, one reduction sweep):
 // the same values as two calls of block_sum_array.  Results in all threads.
 template <int NT>
-__device__ __forceinline__ void block_sum_array2(const volatile double *pa, const volatile double *pb, int n, double *sh,
-                                                 double *ra, double *rb)
+__device__ __forceinline__ void block_sum_array2(const double *pa, const double *pb, int n, double *sh, double *ra,
+                                                 double *rb)
 {
     double va = 0.0, vb = 0.0;
-    for (int i = threadIdx.x; i < n; i += NT) {
-        va += pa[i];
-        vb += pb[i];
+    int i = threadIdx.x;
+    for (; i + 3 * NT < n; i += 4 * NT) {
+        double ta[4], tb[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            ta[k] = __ldcg(pa + i + k * NT);
+            tb[k] = __ldcg(pb + i + k * NT);
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            va += ta[k];
+            vb += tb[k];
+        }
+    }
+    for (; i < n; i += NT) {
+        va += __ldcg(pa + i);
+        vb += __ldcg(pb + i);
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
