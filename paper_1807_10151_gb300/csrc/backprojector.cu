@@ -379,8 +379,8 @@ __global__ void __launch_bounds__(kBwdThreads, DUAL ? 2 : 3) k_backward(const Pr
         P.partial[ntiles + tile] = be;
     }
     if (last_block(&P.counter[4], ntiles, &last_sh)) {
-        const double tot = block_sum_array<kBwdThreads>(P.partial, ntiles, red);
-        const double tse = block_sum_array<kBwdThreads>(P.partial + ntiles, ntiles, red);
+        double tot, tse;
+        block_sum_array2<kBwdThreads>(P.partial, P.partial + ntiles, ntiles, red, &tot, &tse);
         if (t == 0) {
             Scal *sc = P.sc;
             if (bayes) {

@@ -213,8 +213,8 @@ __global__ void __launch_bounds__(256) k_pupdate(const Prob *__restrict__ probs,
         P.partial[nblk + local] = bp;
     }
     if (last_block(&P.counter[1], nblk, &flag)) {
-        const double tot_s = block_sum_array<256>(P.partial, nblk, red);
-        const double tot_p = block_sum_array<256>(P.partial + nblk, nblk, red);
+        double tot_s, tot_p;
+        block_sum_array2<256>(P.partial, P.partial + nblk, nblk, red, &tot_s, &tot_p);
         if (threadIdx.x == 0) {
             P.sc->gtp = tot_s;
             P.sc->pp = tot_p;

@@ -168,8 +168,8 @@ __global__ void __launch_bounds__(kTvThreads) k_tv_tbar(const Prob *__restrict__
         P.partial[nblk + local] = bnn;
     }
     if (last_block(&P.counter[3], nblk, &flag)) {
-        const double tv = block_sum_array<kTvThreads>(P.partial, nblk, red);
-        const double nn = block_sum_array<kTvThreads>(P.partial + nblk, nblk, red);
+        double tv, nn;
+        block_sum_array2<kTvThreads>(P.partial, P.partial + nblk, nblk, red, &tv, &nn);
         if (threadIdx.x == 0) {
             P.sc->tv_k = tv;
             P.sc->snorm2 = nn;
