@@ -886,8 +886,11 @@ def main():
         try:
             import hashlib
             rec = json.load(open(tf)).get("k_forward", {})
-            src = open(os.path.join(ROOT, "paper_1807_10151_gb300", "csrc", "projector.cu"), "rb").read()
-            if rec.get("projector_sha1") == hashlib.sha1(src).hexdigest():
+            # the kernel's sources: the projector and the shared header it inlines
+            h = hashlib.sha1()
+            for f in ("projector.cu", "internal.cuh"):
+                h.update(open(os.path.join(ROOT, "paper_1807_10151_gb300", "csrc", f), "rb").read())
+            if rec.get("sources_sha1") == h.hexdigest():
                 traffic = rec.get("bytes_per_launch")
         except (ValueError, OSError):
             traffic = None
