@@ -446,11 +446,13 @@ __device__ __forceinline__ double block_sum_array(const double *partial, int n, 
 }
 
 // Two such sums in one pass (both arrays' loads in flight together, one reduction sweep):
-// the same values as two calls of block_sum_array.  Results in all threads.
+// the same values as two calls of block_sum_array.  Results in all threads; sh holds >= 34
+// doubles.
 template <int NT>
 __device__ __forceinline__ void block_sum_array2(const double *pa, const double *pb, int n, double *sh, double *ra,
                                                  double *rb)
 {
+    static_assert(NT % 32 == 0 && NT <= 512, "at most 16 warps: their sums sit at sh[0..15] and sh[16..31]");
     double va = 0.0, vb = 0.0;
     int i = threadIdx.x;
     for (; i + 3 * NT < n; i += 4 * NT) {
